@@ -1,0 +1,280 @@
+"""FP64 CPU oracle for the SFHK high-harmonic path (test infrastructure).
+
+This package is TEST INFRASTRUCTURE.  Only ``tests/``, the package smoke
+check and the CPU-baseline leg of ``bench.py`` may import it; the product
+library never does.  It wraps ``sfhk_oracle.c`` (plain C, double precision,
+written step by step from the paper's equations) with ctypes and numpy.
+
+Functions that are pinned only by the paper's own figures (the spectra
+themselves) are "parity unpinned": the figures are placeholders in the
+source, the fitted GTO coefficients are not printed and there is no TDSE
+data.  Every other function is pinned by the tests in ``tests/test_oracle_*``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sfhk_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NFIELDS = 12      # n0 | q0[3] | p0[3] | nhat[3] | w_re w_im
+NFINAL = 47       # q[3] p[3] M[36] S C_re C_im theta status
+NY = 43
+
+POT_MOLECULE = 0
+POT_HARMONIC = 1
+ALIGN_FIXED, ALIGN_ISO, ALIGN_COS2 = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no fast-math, no FMA contraction)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-std=gnu11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+class PulseIn(C.Structure):
+    _fields_ = [("lambda_nm", C.c_double), ("intensity", C.c_double),
+                ("n_cycles", C.c_double), ("cep", C.c_double), ("dt", C.c_double)]
+
+
+class TargetIn(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_prim", C.c_int), ("R", C.c_double),
+                ("Zinf", C.c_double), ("Z0", C.c_double), ("alpha", C.c_double),
+                ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
+                ("pexp", C.c_double * 8), ("pcoef", C.c_double * 8)]
+
+
+_dp = C.POINTER(C.c_double)
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        u32p = C.POINTER(C.c_uint32)
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_uniforms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, _dp]
+        L.or_pulse_derive.argtypes = [C.POINTER(PulseIn), _dp, C.POINTER(C.c_int)]
+        L.or_pulse_A_real.argtypes = [C.POINTER(PulseIn), C.c_double]
+        L.or_pulse_A_real.restype = C.c_double
+        L.or_pulse_E_real.argtypes = [C.POINTER(PulseIn), C.c_double]
+        L.or_pulse_E_real.restype = C.c_double
+        L.or_pulse_E_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
+        L.or_pulse_A_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
+        L.or_potential.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp]
+        L.or_trajectory.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), _dp, _dp,
+                                    C.c_double, C.c_double, C.c_int, _dp]
+        L.or_hk_det.argtypes = [_dp, C.c_double, _dp]
+        L.or_orbital_norm.argtypes = [C.POINTER(TargetIn)]
+        L.or_orbital_norm.restype = C.c_double
+        L.or_orbital_value.argtypes = [C.POINTER(TargetIn), _dp, _dp]
+        L.or_orbital_value.restype = C.c_double
+        L.or_recomb.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp, C.c_double, _dp]
+        L.or_dipole_matrix_element.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp, _dp]
+        L.or_saddle.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double, _dp]
+        L.or_saddle.restype = C.c_int
+        L.or_tunnel.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
+                                _dp, _dp]
+        L.or_adk_table.argtypes = [C.POINTER(PulseIn), C.c_double, _dp, _dp]
+        L.or_sample.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int, C.c_double,
+                                C.c_double, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint64,
+                                _dp, _dp]
+        L.or_sample.restype = C.c_int
+        L.or_propagate.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
+                                   C.c_double, _dp, C.c_uint64, C.c_double, _dp, _dp, C.c_int]
+        L.or_propagate.restype = C.c_int
+        L.or_spectrum.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                  _dp, _dp, _dp, _dp, _dp]
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- inputs
+def pulse_in(p) -> PulseIn:
+    """p: mapping with lambda_nm, intensity, n_cycles, cep, dt."""
+    return PulseIn(p["lambda_nm"], p["intensity"], p["n_cycles"], p.get("cep", 0.0), p["dt"])
+
+
+def target_in(t) -> TargetIn:
+    """t: mapping with R, Zinf, Z0, alpha, soft_a, Ip, pexp, pcoef (+ kind, ho_omega)."""
+    T = TargetIn()
+    T.kind = int(t.get("kind", POT_MOLECULE))
+    T.n_prim = len(t.get("pexp", ()))
+    for name in ("R", "Zinf", "Z0", "alpha", "soft_a", "Ip", "ho_omega"):
+        setattr(T, name, float(t.get(name, 0.0)))
+    for i, (e, c) in enumerate(zip(t.get("pexp", ()), t.get("pcoef", ()))):
+        T.pexp[i] = e
+        T.pcoef[i] = c
+    return T
+
+
+# ---------------------------------------------------------------- wrappers
+def philox(ctr, key):
+    a = (C.c_uint32 * 4)(*ctr)
+    k = (C.c_uint32 * 2)(*key)
+    o = (C.c_uint32 * 4)()
+    lib().or_philox4x32_10(a, k, o)
+    return list(o)
+
+
+def uniforms(seed, instance, j):
+    u = np.zeros(6)
+    lib().or_uniforms(seed, instance, j, _p(u))
+    return u
+
+
+def pulse_derived(p):
+    out = np.zeros(6)
+    nt = C.c_int()
+    lib().or_pulse_derive(C.byref(pulse_in(p)), _p(out), C.byref(nt))
+    return dict(omega=out[0], E0=out[1], Tp=out[2], cep=out[3], dt=out[4],
+                t_origin=out[5], nt=nt.value)
+
+
+def pulse_A(p, t):
+    P = pulse_in(p)
+    return np.array([lib().or_pulse_A_real(C.byref(P), float(x)) for x in np.atleast_1d(t)])
+
+
+def pulse_E(p, t):
+    P = pulse_in(p)
+    return np.array([lib().or_pulse_E_real(C.byref(P), float(x)) for x in np.atleast_1d(t)])
+
+
+def pulse_A_complex(p, tau):
+    out = np.zeros(2)
+    lib().or_pulse_A_complex(C.byref(pulse_in(p)), tau.real, tau.imag, _p(out))
+    return complex(out[0], out[1])
+
+
+def pulse_E_complex(p, tau):
+    out = np.zeros(2)
+    lib().or_pulse_E_complex(C.byref(pulse_in(p)), tau.real, tau.imag, _p(out))
+    return complex(out[0], out[1])
+
+
+def potential(t, nhat, q):
+    """Returns V, grad[3], hess[3,3]."""
+    out = np.zeros(13)
+    lib().or_potential(C.byref(target_in(t)), _p(np.asarray(nhat, float).copy()),
+                       _p(np.asarray(q, float).copy()), _p(out))
+    return out[0], out[1:4].copy(), out[4:13].reshape(3, 3).copy()
+
+
+def trajectory(t, p, nhat, y0, t_start, h, n_steps):
+    out = np.zeros((n_steps + 1, NY))
+    lib().or_trajectory(C.byref(target_in(t)), C.byref(pulse_in(p)),
+                        _p(np.asarray(nhat, float).copy()), _p(np.asarray(y0, float).copy()),
+                        t_start, h, n_steps, _p(out))
+    return out
+
+
+def initial_state(q0, p0):
+    y = np.zeros(NY)
+    y[0:3] = q0
+    y[3:6] = p0
+    y[6:42] = np.eye(6).ravel()
+    return y
+
+
+def hk_det(M, gamma):
+    out = np.zeros(2)
+    lib().or_hk_det(_p(np.ascontiguousarray(M, dtype=float).ravel().copy()), gamma, _p(out))
+    return complex(out[0], out[1])
+
+
+def orbital_norm(t):
+    return lib().or_orbital_norm(C.byref(target_in(t)))
+
+
+def orbital_value(t, nhat, r):
+    return lib().or_orbital_value(C.byref(target_in(t)), _p(np.asarray(nhat, float).copy()),
+                                  _p(np.asarray(r, float).copy()))
+
+
+def recomb(t, nhat, q, p, gamma):
+    out = np.zeros(2)
+    lib().or_recomb(C.byref(target_in(t)), _p(np.asarray(nhat, float).copy()),
+                    _p(np.asarray(q, float).copy()), _p(np.asarray(p, float).copy()),
+                    gamma, _p(out))
+    return complex(out[0], out[1])
+
+
+def dipole_matrix_element(t, nhat, kappa):
+    kappa = np.asarray(kappa, complex)
+    out = np.zeros(2)
+    lib().or_dipole_matrix_element(C.byref(target_in(t)), _p(np.asarray(nhat, float).copy()),
+                                   _p(kappa.real.copy()), _p(kappa.imag.copy()), _p(out))
+    return complex(out[0], out[1])
+
+
+def saddle(p, Ip, t0, kperp2):
+    out = np.zeros(2)
+    rc = lib().or_saddle(C.byref(pulse_in(p)), Ip, t0, kperp2, _p(out))
+    return rc, out[0], out[1]
+
+
+def tunnel(p, Ip, t0, tt, k):
+    out = np.zeros(3)
+    lib().or_tunnel(C.byref(pulse_in(p)), Ip, t0, tt, _p(np.asarray(k, float).copy()), _p(out))
+    return out[0], complex(out[1], out[2])
+
+
+def adk_table(p, Ip):
+    nt = pulse_derived(p)["nt"]
+    W = np.zeros(nt)
+    cdf = np.zeros(nt)
+    lib().or_adk_table(C.byref(pulse_in(p)), Ip, _p(W), _p(cdf))
+    return W, cdf
+
+
+def sample(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance=0, j_begin=0, n=1):
+    """Initial ensemble as a (12, n) field-major array plus aux (tt, S_down)."""
+    soa = np.zeros((NFIELDS, n))
+    aux = np.zeros((3, n))
+    bad = lib().or_sample(C.byref(target_in(t)), C.byref(pulse_in(p)), int(align[0]),
+                          float(align[1]), float(align[2]), seed, instance, j_begin, n,
+                          _p(soa), _p(aux))
+    return soa, aux, bad
+
+
+def propagate(t, p, soa, gamma, cutoff=0.0, n_norm=0.0, want_final=False, n_threads=0):
+    soa = np.ascontiguousarray(soa, dtype=np.float64)
+    n = soa.shape[1]
+    nt = pulse_derived(p)["nt"]
+    vz = np.zeros(nt)
+    fin = np.zeros((NFINAL, n)) if want_final else None
+    bad = lib().or_propagate(C.byref(target_in(t)), C.byref(pulse_in(p)), gamma, cutoff,
+                             _p(soa), n, float(n_norm), _p(vz),
+                             _p(fin) if fin is not None else None, n_threads)
+    return vz, fin, bad
+
+
+def spectrum(vz, dt, t_origin, tau_H, n_out):
+    vz = np.ascontiguousarray(vz, dtype=np.float64)
+    om, y, ph, vr, vi = (np.zeros(n_out) for _ in range(5))
+    lib().or_spectrum(_p(vz), len(vz), dt, t_origin, tau_H, n_out, _p(om), _p(y), _p(ph),
+                      _p(vr), _p(vi))
+    return om, y, ph, vr + 1j * vi

@@ -1,0 +1,75 @@
+"""Symmetry and additivity pins of the oracle's dipole sum (CPU only).
+
+* Rotating the molecular axis and the transverse momenta together about the
+  polarisation axis z leaves every contribution unchanged (the laser and the
+  dipole component are along z).
+* Swapping the two centres (n -> -n) leaves a sigma_g orbital, and hence every
+  contribution, unchanged.
+* The estimator is additive over any partition of the ensemble.
+The symmetry checks run with the prefactor filter at |C| > 1e4: beyond it
+trajectories are chaotic (|M| > ~1e3), and there a last-bit rounding
+difference (the rotated arithmetic) grows to O(1).
+"""
+import math
+
+import numpy as np
+
+import oracle as O
+from paper_2608_13686_b300 import workloads as W
+
+CUT = 1e4
+
+
+def _ensemble(n=48, seed=4):
+    t, p = W.TARGETS["N2"], W.pulse(800.0, 1.5e14, 2)
+    soa, _, bad = O.sample(t, p, W.fixed(35.0, 20.0), seed=seed, n=n)
+    assert bad == 0
+    return t, p, soa
+
+
+def test_rotation_about_polarisation_axis():
+    t, p, soa = _ensemble()
+    vz, _, _ = O.propagate(t, p, soa, 0.5, cutoff=CUT, n_threads=4)
+    a = 0.9
+    rot = np.array([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]])
+    s2 = soa.copy()
+    s2[4:6] = rot @ soa[4:6]
+    s2[1:3] = rot @ soa[1:3]
+    s2[7:9] = rot @ soa[7:9]
+    vz2, _, _ = O.propagate(t, p, s2, 0.5, cutoff=CUT, n_threads=4)
+    assert np.max(np.abs(vz2 - vz)) < 1e-9 * np.max(np.abs(vz))
+    assert np.max(np.abs(vz)) > 0
+
+
+def test_centre_swap():
+    t, p, soa = _ensemble()
+    vz, _, _ = O.propagate(t, p, soa, 0.5, cutoff=CUT, n_threads=4)
+    s2 = soa.copy()
+    s2[7:10] = -soa[7:10]
+    vz2, _, _ = O.propagate(t, p, s2, 0.5, cutoff=CUT, n_threads=4)
+    assert np.max(np.abs(vz2 - vz)) < 1e-9 * np.max(np.abs(vz))
+
+
+def test_additive_over_partitions():
+    t, p, soa = _ensemble(n=60)
+    vz, _, _ = O.propagate(t, p, soa, 0.5, n_threads=4)
+    va, _, _ = O.propagate(t, p, np.ascontiguousarray(soa[:, :25]), 0.5, n_norm=60, n_threads=2)
+    vb, _, _ = O.propagate(t, p, np.ascontiguousarray(soa[:, 25:]), 0.5, n_norm=60, n_threads=3)
+    assert np.max(np.abs(va + vb - vz)) < 1e-12 * np.max(np.abs(vz))
+
+
+def test_contribution_starts_at_birth():
+    t, p, soa = _ensemble(n=1)
+    vz, _, _ = O.propagate(t, p, soa, 0.5)
+    n0 = int(soa[0, 0])
+    assert np.all(vz[:n0] == 0.0)
+    assert vz[n0] != 0.0
+
+
+def test_prefactor_filter_drops_from_threshold_on():
+    t, p, soa = _ensemble(n=16)
+    _, fin, bad0 = O.propagate(t, p, soa, 0.5, want_final=True)
+    cmax = np.abs(fin[43] + 1j * fin[44])
+    cut = float(np.median(cmax)) * 0.999
+    vz_f, fin_f, bad = O.propagate(t, p, soa, 0.5, cutoff=cut, want_final=True)
+    assert bad >= 1 and np.all(fin_f[46][fin_f[46] != 0] == 1)
