@@ -1,0 +1,256 @@
+/*
+ * sfhk.h -- C ABI of the B300 strong-field Herman-Kluk (SFHK) high-harmonic
+ * library: Monte Carlo ensemble of classical trajectories launched at the
+ * tunnel exit, propagated with their stability matrix, action and
+ * Herman-Kluk prefactor through a two-centre molecular potential plus the
+ * laser, and reduced on the GPU into the dipole velocity and its spectrum.
+ *
+ * Method: "Strong-field Herman-Kluk propagator method for high-harmonic
+ * generation in molecules" (Tran, Truong, Goetz, Le).  Each entry point
+ * cites the passage that defines what it computes.
+ *
+ * Conventions for every call
+ *   - Return value: SFHK_OK (0) or a negative SFHK_E_* code;
+ *     sfhk_strerror() gives its text.  On error no output is written and no
+ *     handle is created; a handle passed in stays valid.
+ *   - Atomic units throughout (time, length, momentum, energy); the laser is
+ *     linearly polarised along z, time is centred on the pulse
+ *     (t in [-Tp/2, Tp/2]) and sampled on t_n = -Tp/2 + n dt, n = 0..Nt-1,
+ *     Nt = floor(Tp/dt) + 1.
+ *   - Ownership: the library owns all device memory and all handles (freed by
+ *     the matching sfhk_destroy_*); the caller owns every host buffer and
+ *     passes its size explicitly.  Host pointers are only read or written
+ *     during the call.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls that take a stream enqueue their device work on
+ *     it and return without waiting unless stated otherwise.
+ *   - A context is not thread-safe; use one per host thread, or the server
+ *     (sfhk_server_*), which serialises its own calls.
+ *   - There is no CPU fallback: every computing call needs a CUDA device with
+ *     compute capability 10.3 and fails with SFHK_E_CUDA otherwise.
+ */
+#ifndef SFHK_H
+#define SFHK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SFHK_API __attribute__((visibility("default")))
+#else
+#define SFHK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define SFHK_OK           0
+#define SFHK_E_INVAL     -1  /* bad argument, size or descriptor            */
+#define SFHK_E_NOMEM     -2  /* device-memory budget or allocation exceeded */
+#define SFHK_E_CUDA      -3  /* CUDA runtime error or no suitable device    */
+#define SFHK_E_TIMEOUT   -4  /* a bounded wait expired                      */
+#define SFHK_E_NUMERIC   -5  /* non-finite trajectories above the limit     */
+#define SFHK_E_BUSY      -6  /* result not ready yet                        */
+#define SFHK_E_NOTFOUND  -7  /* unknown request id                          */
+
+#define SFHK_MAX_PRIM     8  /* s-type Gaussian primitives per centre       */
+
+/* ---------------------------------------------------------------- handles */
+typedef struct sfhk_ctx sfhk_ctx;
+typedef struct sfhk_target sfhk_target;
+typedef struct sfhk_pulse sfhk_pulse;
+typedef struct sfhk_ensemble sfhk_ensemble;
+typedef struct sfhk_server sfhk_server;
+
+/* ---------------------------------------------------------------- descriptors */
+enum { SFHK_POT_MOLECULE = 0, SFHK_POT_HARMONIC = 1 };
+enum { SFHK_ALIGN_FIXED = 0, SFHK_ALIGN_ISOTROPIC = 1, SFHK_ALIGN_COS2 = 2 };
+enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
+
+/* Target (Eq. 7, Tables I-II): two centres at +-(R/2) n, n the molecular axis,
+ * V(r) = -sum_i [Z_inf + (Z0 - Z_inf) exp(-alpha s_i)] / s_i with the softened
+ * distance s_i = sqrt(|r - R_i|^2 + soft_a^2).  The initial orbital is the
+ * sigma_g combination  N sum_centres sum_k prim_coef[k] exp(-prim_exp[k] |r-R_c|^2)
+ * (normalised by the library).  kind = SFHK_POT_HARMONIC replaces V by the
+ * test potential ho_omega^2 |r|^2 / 2 (closed-form checks). */
+typedef struct {
+    int kind;
+    int n_prim;                       /* 1..SFHK_MAX_PRIM */
+    double R, Z_inf, Z0, alpha, soft_a;
+    double Ip;                        /* ionization potential (> 0 for sampling) */
+    double ho_omega;
+    double prim_exp[SFHK_MAX_PRIM];   /* > 0 */
+    double prim_coef[SFHK_MAX_PRIM];
+} sfhk_target_desc;
+
+/* Pulse (Sec. II.D / III.A): wavelength (nm), peak intensity (W/cm^2),
+ * number of cycles of the sin^2 envelope, CEP (rad), time step (a.u.).
+ * omega = 45.5633525/lambda_nm, E0 = sqrt(I/3.50944758e16),
+ * Tp = n_cycles 2 pi / omega, A(t) = -(E0/omega) cos^2(pi t/Tp) sin(omega t + cep),
+ * E = -dA/dt.  n_cycles >= 1.5. */
+typedef struct {
+    double lambda_nm, intensity_Wcm2, n_cycles, cep, dt;
+} sfhk_pulse_desc;
+
+/* Orientation distribution (Eqs. 5-6): FIXED axis n(theta, phi); ISOTROPIC;
+ * COS2 = axis density proportional to cos^2 theta (<cos^2> = 3/5). */
+typedef struct {
+    int kind;
+    double theta, phi;                /* radians, FIXED only */
+} sfhk_align_desc;
+
+/* Propagation options.
+ *   precision        SFHK_FP64: every step in double precision.
+ *                    SFHK_MIXED: position, momentum and stability matrix in
+ *                    single precision with compensated (two-float) state
+ *                    updates; action, phase reduction, prefactor branch and
+ *                    the dipole reduction in two-float / double.
+ *   gamma            coherent-state width (Sec. II.A; the paper uses 1).
+ *   prefactor_cutoff 0 = off; else a trajectory stops contributing from the
+ *                    first step with |C| > cutoff (the paper is silent).
+ *   dump_final       keep each trajectory's final state for sfhk_final_state.
+ *   block_threads,   launch shape; 0 = the autotuned choice.
+ *   blocks_per_sm
+ */
+typedef struct {
+    int precision;
+    double gamma;
+    double prefactor_cutoff;
+    int dump_final;
+    int block_threads;
+    int blocks_per_sm;
+} sfhk_run_opts;
+
+/* Per-ensemble counters of the last propagation. */
+typedef struct {
+    uint64_t n_traj;          /* trajectories in the ensemble                 */
+    uint64_t n_invalid;       /* saddle without root: weight 0                */
+    uint64_t n_filtered;      /* stopped by the prefactor filter              */
+    uint64_t n_nonfinite;     /* stopped on a non-finite state or prefactor   */
+    uint64_t traj_steps;      /* RK4 steps actually integrated                */
+    int nt;                   /* time-grid length                             */
+    float kernel_ms;          /* duration of the propagation kernel (events)  */
+} sfhk_stats;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on CUDA device `device` that may hold at most
+ * `device_mem_budget` bytes of library allocations (0 = no limit).
+ * Errors: SFHK_E_INVAL (null out), SFHK_E_CUDA (no such device, or not
+ * compute capability 10.3). */
+SFHK_API int sfhk_create(sfhk_ctx** out, int device, size_t device_mem_budget);
+SFHK_API int sfhk_destroy(sfhk_ctx* ctx);
+/* Bytes of device memory the context holds now. */
+SFHK_API int sfhk_mem_used(const sfhk_ctx* ctx, size_t* bytes);
+
+/* Target descriptor -> device-resident target (Eq. 7, Tables I-II, Sec. II.A
+ * GTO expansion).  Errors: SFHK_E_INVAL (n_prim outside 1..8, non-positive
+ * exponent, negative softening, unknown kind). */
+SFHK_API int sfhk_create_target(sfhk_ctx* ctx, const sfhk_target_desc* desc, sfhk_target** out);
+SFHK_API int sfhk_destroy_target(sfhk_target* t);
+
+/* Pulse descriptor -> device tables of E(t) at every half step and the time
+ * grid (Sec. III.A laser; Eq. 3 window uses tau_H = Tp/2).  Runs a kernel
+ * on the legacy default stream and waits for it.
+ * Errors: SFHK_E_INVAL (non-positive lambda/dt, n_cycles < 1.5, negative
+ * intensity, more than 2^26 steps). */
+SFHK_API int sfhk_set_pulse(sfhk_ctx* ctx, const sfhk_pulse_desc* desc, sfhk_pulse** out);
+SFHK_API int sfhk_destroy_pulse(sfhk_pulse* p);
+/* Time grid of a pulse: Nt, t_0 = -Tp/2, dt, Tp (any output may be NULL). */
+SFHK_API int sfhk_pulse_grid(const sfhk_pulse* p, int* nt, double* t_origin, double* dt, double* Tp);
+
+/* Initial ensemble (Sec. II.A, Eqs. 1-2, 6), sampled on the device:
+ * t0 on the time grid with probability p_n proportional to
+ * exp(-2 (2 Ip)^{3/2} / (3 |E(t_n)|)), k_x, k_y ~ N(0, |E(t0)| / (2 sqrt(2 Ip))),
+ * the molecular axis from `align`; then per trajectory the saddle point
+ * t_s = t0 + i t_t of Eq. 2 (smallest positive root), k_z, the tunnel exit
+ * q0 = Re int_{t_s}^{t0} A, the tunnelling action S_down, the amplitude
+ * a = <kappa| z E(t_s) |psi0> / sqrt(E(t_s) kappa_z) e^{i(S_down + k.q0)}
+ * and the weight w = a / pdf.  Random numbers: Philox4x32-10 with key = seed
+ * and counter (j, instance, draw), so every trajectory is reproducible on its
+ * own.  Trajectories whose saddle has no root get w = 0.  The ensemble keeps
+ * references to `target` and `pulse`, which must outlive it.
+ * Errors: SFHK_E_INVAL (n_traj = 0 or > 2^31-1, Ip <= 0, zero field),
+ * SFHK_E_NOMEM. */
+SFHK_API int sfhk_sample_initial(sfhk_ctx* ctx, const sfhk_target* target, const sfhk_pulse* pulse,
+                        const sfhk_align_desc* align, uint64_t n_traj, uint64_t seed,
+                        uint32_t instance, sfhk_ensemble** out, void* stream);
+
+/* Re-draw the initial points of an existing sampled ensemble in place (same
+ * target, pulse and size; new alignment, seed and instance), reusing its
+ * device buffers: no allocation, asynchronous on `stream`.  Same method and
+ * errors as sfhk_sample_initial. */
+SFHK_API int sfhk_sample_into(sfhk_ctx* ctx, sfhk_ensemble* e, const sfhk_align_desc* align,
+                              uint64_t seed, uint32_t instance, void* stream);
+
+/* Ensemble from caller-given initial points (tests, external samplers).
+ * soa_host: 12 x n_traj doubles, field-major (soa[f * n_traj + j]):
+ *   0 grid index n0 of t0 (integer valued, 0..Nt-1) | 1-3 q0 | 4-6 p0 |
+ *   7-9 molecular axis n (unit) | 10-11 weight w (re, im).
+ * n_norm: N of the 1/N normalisation of the dipole (0 = n_traj).
+ * Errors: SFHK_E_INVAL (n0 out of range, non-finite entries), SFHK_E_NOMEM. */
+SFHK_API int sfhk_load_ensemble(sfhk_ctx* ctx, const sfhk_target* target, const sfhk_pulse* pulse,
+                       const double* soa_host, uint64_t n_traj, double n_norm,
+                       sfhk_ensemble** out);
+/* Copy the initial points (same 12-field layout) to the host; synchronous. */
+SFHK_API int sfhk_ensemble_read(sfhk_ensemble* e, double* soa_host, uint64_t n_traj);
+SFHK_API int sfhk_destroy_ensemble(sfhk_ensemble* e);
+
+/* Continuum propagation and dipole (Sec. II.A, Eq. 4): every trajectory runs
+ * from its grid point n0 to Nt-1 with RK4 through Hamilton's equations in
+ * V + z E(t), with its 6x6 stability matrix, action S = int (p.qdot - H) and
+ * prefactor C = sqrt(det[(M_qq + M_pp - i gamma M_qp + (i/gamma) M_pq)/2])
+ * on a continuous branch; the GPU reduces
+ *   v_z(t_n) = -(2/N) sum_j Re[w_j C_j e^{i(S_j - Ip t_n)} <psi0^{(j)}|k_z|p_j,q_j>]
+ * over trajectories with n >= n0_j, without writing any per-trajectory time
+ * series.  Overwrites the ensemble's dipole accumulator.  Asynchronous.
+ * Errors: SFHK_E_INVAL (gamma <= 0, bad precision), SFHK_E_NOMEM (dump). */
+SFHK_API int sfhk_propagate(sfhk_ctx* ctx, sfhk_ensemble* e, const sfhk_run_opts* opts, void* stream);
+
+/* The same for several ensembles (any mix of targets, pulses, sizes and
+ * alignments) in ONE persistent launch: the warps pull work items of 32
+ * trajectories, longest first, from a shared queue; each ensemble gets its
+ * own dipole.  Asynchronous. */
+SFHK_API int sfhk_propagate_batch(sfhk_ctx* ctx, sfhk_ensemble* const* ens, int n_ens,
+                         const sfhk_run_opts* opts, void* stream);
+
+/* Dipole v_z(t_n), n = 0..Nt-1, of the last propagation, copied to the host
+ * after waiting for it.  nt must equal the pulse's Nt.  Also returns the
+ * grid origin and step (either may be NULL).  Errors: SFHK_E_INVAL. */
+SFHK_API int sfhk_dipole(sfhk_ctx* ctx, sfhk_ensemble* e, double* vz_host, size_t nt,
+                double* t_origin, double* dt);
+/* Device pointer of the same dipole (valid until the ensemble is destroyed or
+ * propagated again). */
+SFHK_API int sfhk_dipole_device(sfhk_ensemble* e, const double** vz_dev, size_t* nt);
+/* Counters of the last propagation (waits for it). */
+SFHK_API int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out);
+/* Final per-trajectory state of the last propagation run with dump_final,
+ * 47 x n_traj doubles, field-major: q[3] p[3] M[36] (6x6 row-major,
+ * M_ab = d a_t / d b_0 for (q,p)) S C_re C_im branch_sign status
+ * (0 ok, 1 filtered, 2 non-finite).  For a stopped
+ * trajectory the state is the one at the step where it stopped.  Synchronous.
+ * Errors: SFHK_E_INVAL (no dump taken). */
+SFHK_API int sfhk_final_state(sfhk_ensemble* e, double* host, uint64_t n_traj);
+
+/* Spectrum (Eq. 3): v(omega_k) = sum_n v_z(t_n) W_H(t_n) e^{i omega_k t_n} dt,
+ * W_H(t) = [1 + cos(pi t / tau_H)]/2 for |t| <= tau_H (else 0),
+ * omega_k = 2 pi k / (Nt dt), k = 0..n_out-1; yield = omega^2 |v|^2,
+ * phase = arg v.  Computed by a DFT kernel on the GPU.  device_ptrs = 0: all
+ * arrays are host memory and the call is synchronous; 1: all are device
+ * memory and the call is asynchronous on `stream`.  Any output may be NULL.
+ * Errors: SFHK_E_INVAL (nt < 2, n_out > nt, dt <= 0). */
+SFHK_API int sfhk_spectrum(const double* vz, size_t nt, double dt, double t_origin, double tau_H,
+                  double* omega_out, double* yield_out, double* phase_out, size_t n_out,
+                  int device_ptrs, void* stream);
+
+SFHK_API const char* sfhk_strerror(int code);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts).  For accounting of launches in a timed region. */
+SFHK_API int sfhk_launch_count(uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFHK_H */

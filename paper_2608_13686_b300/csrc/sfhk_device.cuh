@@ -1,0 +1,225 @@
+// sfhk_device.cuh -- device-side building blocks of libsfhk: counter-based
+// random numbers, complex and two-float arithmetic, the sin^2 pulse in closed
+// form (real and complex time), and the potential of Eq. 7 with its gradient
+// and Hessian.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cstdint>
+
+namespace sfhk {
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32->64-bit
+// multiplies (0xD2511F53, 0xCD9E8D57) with the Weyl key schedule
+// (0x9E3779B9, 0xBB67AE85).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// 53-bit uniform in (0,1): ((a >> 5) 2^26 + (b >> 6) + 1/2) 2^-53.
+__device__ __forceinline__ double u01(uint32_t a, uint32_t b)
+{
+    return (__uint2double_rn(a >> 5) * 67108864.0 + __uint2double_rn(b >> 6) + 0.5) *
+           (1.0 / 9007199254740992.0);
+}
+
+// ------------------------------------------------------------------ complex (double2)
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b)
+{
+    // Smith's algorithm
+    if (fabs(b.x) >= fabs(b.y)) {
+        const double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    }
+    const double r = b.x / b.y, d = b.y + b.x * r;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+// e^{z}
+__device__ __forceinline__ double2 cexp_(double2 z)
+{
+    double s, c;
+    sincos(z.y, &s, &c);
+    const double m = exp(z.x);
+    return make_double2(m * c, m * s);
+}
+// principal square root
+__device__ __forceinline__ double2 csqrt_(double2 z)
+{
+    const double r = hypot(z.x, z.y);
+    if (r == 0.0) return make_double2(0.0, 0.0);
+    if (z.x >= 0.0) {
+        const double t = sqrt(0.5 * (r + z.x));
+        return make_double2(t, 0.5 * z.y / t);
+    }
+    const double t = sqrt(0.5 * (r - z.x));
+    return make_double2(0.5 * fabs(z.y) / t, copysign(t, z.y));
+}
+// sin and cos of a + i b
+__device__ __forceinline__ void csincos(double a, double b, double2* s, double2* c)
+{
+    double sa, ca;
+    sincos(a, &sa, &ca);
+    const double sh = sinh(b), ch = cosh(b);
+    *s = make_double2(sa * ch, ca * sh);
+    *c = make_double2(ca * ch, -sa * sh);
+}
+
+// ------------------------------------------------------------------ two-float
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += x, renormalised (Dekker's FastTwoSum at the end).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x)
+{
+    float s, e;
+    two_sum(hi, x, s, e);
+    e = __fadd_rn(e, lo);
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// ------------------------------------------------------------------ pulse
+// A(t) = -(E0/w) cos^2(pi t/Tp) sin(w t + cep)
+//      = sum_m a_m sin(k_m t + cep),  (a, k) = (-E0/(2w), w), (-E0/(4w), w+W),
+//        (-E0/(4w), w-W), W = 2 pi / Tp  (cos^2 x = (1 + cos 2x)/2, product to sum).
+struct PulseTerms {
+    double a[3], k[3], cep;
+};
+
+__host__ __device__ inline PulseTerms pulse_terms(double omega, double E0, double Tp, double cep)
+{
+    const double W = 2.0 * 3.14159265358979323846 / Tp;
+    PulseTerms P;
+    P.a[0] = -E0 / (2.0 * omega);
+    P.a[1] = -E0 / (4.0 * omega);
+    P.a[2] = -E0 / (4.0 * omega);
+    P.k[0] = omega;
+    P.k[1] = omega + W;
+    P.k[2] = omega - W;
+    P.cep = cep;
+    return P;
+}
+
+// E(t) = -dA/dt for real t inside the pulse.
+__device__ __forceinline__ double pulse_E(const PulseTerms& P, double t)
+{
+    double e = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) e -= P.a[m] * P.k[m] * cos(P.k[m] * t + P.cep);
+    return e;
+}
+__device__ __forceinline__ double pulse_A(const PulseTerms& P, double t)
+{
+    double a = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) a += P.a[m] * sin(P.k[m] * t + P.cep);
+    return a;
+}
+
+// ------------------------------------------------------------------ potential
+// Eq. 7 per centre with the softened distance s = sqrt(|d|^2 + a^2), u = 1/s:
+//   V    = -(Zinf + dZ e) u,                     e = exp(-alpha s)
+//   grad = g1 d,     g1 = Zinf u^3 + dZ e (alpha u^2 + u^3)
+//   Hess = g1 I + g2 d d^T,
+//          g2 = -u^2 (3 Zinf u^3 + dZ e u (alpha^2 + 3 alpha u + 3 u^2))
+// (from f(s) = -(Zinf + dZ e^{-alpha s})/s: g1 = f'/s, g2 = (f'' - f'/s)/s^2).
+template <typename R>
+struct Sym3 {
+    R xx, yy, zz, xy, xz, yz;
+};
+
+template <typename R>
+__device__ __forceinline__ R rsqrt_t(R x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+template <typename R>
+__device__ __forceinline__ R exp_t(R x);
+template <>
+__device__ __forceinline__ float exp_t<float>(float x) { return __expf(x); }
+template <>
+__device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+
+template <typename R>
+struct PotConst {
+    R cx, cy, cz;          // centre offset (R/2) n
+    R Zinf, dZ, alpha, a2, w2;
+    int kind, screened;
+};
+
+// V, force F = -grad V and Hessian at q (both centres, +-(R/2)n).
+template <typename R>
+__device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz, R& V, R& Fx,
+                                          R& Fy, R& Fz, Sym3<R>& H)
+{
+    if (K.kind != 0) {            // harmonic test potential
+        V = R(0.5) * K.w2 * (qx * qx + qy * qy + qz * qz);
+        Fx = -K.w2 * qx;
+        Fy = -K.w2 * qy;
+        Fz = -K.w2 * qz;
+        H.xx = H.yy = H.zz = K.w2;
+        H.xy = H.xz = H.yz = R(0);
+        return;
+    }
+    V = Fx = Fy = Fz = R(0);
+    H.xx = H.yy = H.zz = H.xy = H.xz = H.yz = R(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const R dx = c == 0 ? qx - K.cx : qx + K.cx;
+        const R dy = c == 0 ? qy - K.cy : qy + K.cy;
+        const R dz = c == 0 ? qz - K.cz : qz + K.cz;
+        const R s2 = dx * dx + dy * dy + dz * dz + K.a2;
+        const R u = rsqrt_t<R>(s2);
+        const R u2 = u * u, u3 = u2 * u;
+        R g1, g2;
+        if (K.screened) {
+            const R e = exp_t<R>(-K.alpha * (s2 * u));
+            const R de = K.dZ * e;
+            V -= (K.Zinf + de) * u;
+            g1 = K.Zinf * u3 + de * (K.alpha * u2 + u3);
+            g2 = -u2 * (R(3) * K.Zinf * u3 +
+                        de * u * (K.alpha * K.alpha + R(3) * K.alpha * u + R(3) * u2));
+        } else {
+            V -= K.Zinf * u;
+            g1 = K.Zinf * u3;
+            g2 = R(-3) * K.Zinf * u3 * u2;
+        }
+        Fx -= g1 * dx;
+        Fy -= g1 * dy;
+        Fz -= g1 * dz;
+        const R gx = g2 * dx, gy = g2 * dy;
+        H.xx += g1 + gx * dx;
+        H.yy += g1 + gy * dy;
+        H.zz += g1 + g2 * dz * dz;
+        H.xy += gx * dy;
+        H.xz += gx * dz;
+        H.yz += gy * dz;
+    }
+}
+
+}  // namespace sfhk

@@ -1,0 +1,160 @@
+// sfhk_internal.h -- library-internal types shared by the host runtime and
+// the kernels of libsfhk (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "../../include/sfhk.h"
+
+namespace sfhk {
+
+constexpr int kWarp = 32;
+constexpr int kFinalFields = 47;   // see sfhk_final_state
+constexpr int kSoaFields = 12;     // see sfhk_load_ensemble
+
+// ------------------------------------------------------------------ device views
+// Target constants as the kernels use them.  Recombination constants per
+// primitive k (coherent-state width gamma, b = gamma/2, c = a_k + b):
+//   <phi_k(.-A)| k_z |p,q> = K4 (p_z - i gamma d_z) exp(K1 |d|^2 + K2 |p|^2 + i K3 p.d),
+//   d = q - A, K1 = -a b / c, K2 = -1/(4c), K3 = -a/c,
+//   K4 = N coef_k (gamma/pi)^{3/4} (pi/c)^{3/2} a/c.
+struct DevTarget {
+    int kind;
+    int n_prim;
+    int screened;          // Z0 != Z_inf
+    double half_R, Zinf, dZ, alpha, a2, Ip, w2;
+    double norm;           // orbital normalisation N
+    double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
+};
+
+struct DevRecomb {
+    double K1[SFHK_MAX_PRIM], K2[SFHK_MAX_PRIM], K3[SFHK_MAX_PRIM], K4[SFHK_MAX_PRIM];
+    float K1f[SFHK_MAX_PRIM], K2f[SFHK_MAX_PRIM], K3f[SFHK_MAX_PRIM], K4f[SFHK_MAX_PRIM];
+};
+
+// One ensemble as seen by the propagation kernel.
+struct DevInstance {
+    DevTarget tgt;
+    DevRecomb rec;
+    const double* Eh;      // E at half steps, 2 Nt - 1 entries (FP64)
+    const float* Ehf;      // same, FP32
+    const double2* ph;     // exp(-i Ip t_n), Nt entries
+    const float2* phf;
+    const double* soa;     // 12 x n field-major
+    const int* perm;       // sorted position -> trajectory index
+    const int* n0;         // per trajectory grid index of t0
+    double* vz;            // Nt dipole accumulator
+    double* dump;          // 47 x n or null
+    unsigned long long* counters;   // [filtered, nonfinite, steps]
+    long long n;
+    int nt;
+    double dt, t_origin;
+    double scale;          // -2 / N
+    double gamma, inv_gamma;
+    double cutoff2;        // cutoff^2 on |det| (0 = off), |C|^2 = |det|
+};
+
+struct WorkItem {
+    int inst;              // index into the instance array
+    int first;             // first sorted position
+    int count;             // 1..32
+    int n_start;           // grid index of the earliest birth in the item
+};
+
+// ------------------------------------------------------------------ host objects
+struct Ctx;
+
+struct DeviceBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    std::mutex mu;
+    // tuned launch shape per precision: [block_threads, blocks_per_sm]
+    int tuned[2][2] = {{128, 0}, {128, 0}};
+    int alloc(DeviceBuf& b, size_t bytes);
+    void release(DeviceBuf& b);
+};
+
+struct Target {
+    Ctx* ctx;
+    sfhk_target_desc desc;
+    DevTarget dev;
+};
+
+struct Pulse {
+    Ctx* ctx;
+    sfhk_pulse_desc desc;
+    double omega, E0, Tp, t_origin, dt;
+    int nt;
+    DeviceBuf Eh, Ehf;     // 2 nt - 1 entries
+};
+
+struct Ensemble {
+    Ctx* ctx;
+    const Target* tgt;
+    const Pulse* pulse;
+    long long n = 0;
+    double n_norm = 0;
+    DeviceBuf soa, n0, perm, items, ph, phf, vz, dump, counters;
+    int n_items = 0;
+    unsigned long long n_invalid = 0;
+    bool dumped = false;
+    bool have_result = false;
+    bool sampled = false;          // created by the device sampler
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr, ev_done = nullptr;
+};
+
+// ------------------------------------------------------------------ launchers
+// every launcher adds the number of kernels it enqueued
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(int k = 1) { g_launches.fetch_add((unsigned long long)k); }
+
+// sample / sort (sfhk_sample.cu)
+int launch_field_table(const Pulse& P, double* Eh, float* Ehf, cudaStream_t s);
+int launch_phase_table(const Pulse& P, double Ip, double2* ph, float2* phf, cudaStream_t s);
+int launch_adk_cdf(const Pulse& P, double Ip, double* cdf, cudaStream_t s);
+int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, long long n,
+                  uint64_t seed, uint32_t instance, const double* cdf, double* soa, int* n0,
+                  unsigned long long* n_invalid, cudaStream_t s);
+int launch_n0_from_soa(const double* soa, long long n, int* n0, cudaStream_t s);
+// counting sort of keys in [0, K): writes perm (sorted position -> index)
+int launch_counting_sort(const int* keys, long long n, int K, int* perm, int* scratch_hist,
+                         cudaStream_t s);
+int launch_build_items(const int* perm, const int* n0, long long n, int inst, WorkItem* items,
+                       cudaStream_t s);
+int launch_sort_items(const WorkItem* in, int n_items, const int* inst_nt, WorkItem* out,
+                      int* scratch_keys, int* scratch_perm, int* scratch_hist, int K,
+                      cudaStream_t s);
+// propagate (sfhk_propagate.cu)
+int launch_propagate(int precision, const DevInstance* insts, const WorkItem* items,
+                     int n_items, unsigned int* item_counter, int block_threads,
+                     int blocks_per_sm, int sm_count, cudaStream_t s);
+int propagate_occupancy(int precision, int block_threads, int* blocks_per_sm);
+// spectrum (sfhk_spectrum.cu)
+int launch_spectrum(const double* vz, int nt, double dt, double t_origin, double tau_H,
+                    double* omega, double* yield, double* phase, int n_out, double2* twiddle,
+                    cudaStream_t s);
+
+}  // namespace sfhk
+
+#define SFHK_CUDA_TRY(expr)                                                         \
+    do {                                                                            \
+        cudaError_t _e = (expr);                                                    \
+        if (_e != cudaSuccess) {                                                    \
+            std::fprintf(stderr, "sfhk: %s failed: %s (%s:%d)\n", #expr,            \
+                         cudaGetErrorString(_e), __FILE__, __LINE__);               \
+            return SFHK_E_CUDA;                                                     \
+        }                                                                           \
+    } while (0)

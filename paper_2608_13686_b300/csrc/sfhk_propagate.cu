@@ -1,0 +1,479 @@
+// sfhk_propagate.cu -- the persistent trajectory integrator with the fused
+// Herman-Kluk prefactor, recombination element and dipole reduction
+// (Sec. II.A and Eq. 4).
+//
+// One lane = one trajectory; a warp takes a work item of 32 trajectories
+// sorted by birth time from a global queue (atomic counter), longest first,
+// and walks the time grid from the item's earliest birth in chunks of 32
+// steps.  Per step and lane:
+//   1. prefactor C = sqrt(det[(M_qq + M_pp - i g M_qp + (i/g) M_pq)/2]) on a
+//      continuous branch (sign chosen so that C moves by less than a right
+//      angle from the previous step), the finiteness check and the prefactor
+//      filter;
+//   2. contribution x = Re[w C e^{iS} e^{-i Ip t_n} <psi0|k_z|p,q>];
+//   3. warp sum of x (shuffles), kept by lane (n mod 32);
+//   4. one RK4 step of (q, p, S) collecting the four stage Hessians, then the
+//      six stability-matrix columns advanced by the same RK4 with those
+//      Hessians (identical to RK4 on the full 43-component system because the
+//      columns obey the linear system dMq/dt = Mp, dMp/dt = -Hess V(q(t)) Mq).
+// After each chunk every lane adds its bin, scaled by -2/N, into the FP64
+// dipole with one atomic: no per-trajectory time series reaches HBM.  The
+// field E at the chunk's half steps and e^{-i Ip t_n} are loaded once per
+// chunk (one element per lane) and broadcast by shuffles.
+//
+// Precision policies
+//   FP64:  everything in double.
+//   MIXED: q, p, M, the stage arithmetic, the determinant and the
+//          recombination element in float; q and p accumulated as two-float
+//          pairs (compensated RK4 update), the action S as a two-float pair,
+//          its phase reduced modulo 2 pi in two-float before sincos, the warp
+//          sum as two-float, the cross-warp reduction in FP64 atomics.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "sfhk_device.cuh"
+#include "sfhk_internal.h"
+
+namespace sfhk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename R>
+struct C2 {
+    R x, y;
+};
+
+template <typename R>
+__device__ __forceinline__ C2<R> cm(C2<R> a, C2<R> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+template <typename R>
+__device__ __forceinline__ R hypot_t(R a, R b);
+template <>
+__device__ __forceinline__ float hypot_t<float>(float a, float b) { return hypotf(a, b); }
+template <>
+__device__ __forceinline__ double hypot_t<double>(double a, double b) { return hypot(a, b); }
+
+template <typename R>
+__device__ __forceinline__ R sqrt_t(R a);
+template <>
+__device__ __forceinline__ float sqrt_t<float>(float a) { return sqrtf(a); }
+template <>
+__device__ __forceinline__ double sqrt_t<double>(double a) { return sqrt(a); }
+
+// principal square root of a complex number
+template <typename R>
+__device__ __forceinline__ C2<R> csqrt_p(C2<R> z)
+{
+    const R r = hypot_t<R>(z.x, z.y);
+    if (r == R(0)) return {R(0), R(0)};
+    if (z.x >= R(0)) {
+        const R t = sqrt_t<R>(R(0.5) * (r + z.x));
+        return {t, R(0.5) * z.y / t};
+    }
+    const R t = sqrt_t<R>(R(0.5) * (r - z.x));
+    return {R(0.5) * fabs(z.y) / t, copysign(t, z.y)};
+}
+
+// y (3-vector) = -H x
+template <typename R>
+__device__ __forceinline__ void neg_hx(const Sym3<R>& H, const R x[3], R y[3])
+{
+    y[0] = -(H.xx * x[0] + H.xy * x[1] + H.xz * x[2]);
+    y[1] = -(H.xy * x[0] + H.yy * x[1] + H.yz * x[2]);
+    y[2] = -(H.xz * x[0] + H.yz * x[1] + H.zz * x[2]);
+}
+
+template <typename R>
+__device__ __forceinline__ R shfl(R v, int src)
+{
+    return __shfl_sync(kFull, v, src);
+}
+
+template <bool MIXED>
+__device__ __forceinline__ void process_item(const DevInstance& I, const WorkItem& W, int lane)
+{
+    using R = typename std::conditional<MIXED, float, double>::type;
+
+    const int nt = I.nt;
+    const bool has = lane < W.count;
+    const long long n = I.n;
+    const int j = has ? I.perm[W.first + lane] : 0;
+    const int n0 = has ? I.n0[j] : nt;
+
+    // ---- per-trajectory inputs (FP64 in memory)
+    const double* soa = I.soa;
+    double qd[3], pd[3], nh[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        qd[a] = has ? soa[(1 + a) * n + j] : 0.0;
+        pd[a] = has ? soa[(4 + a) * n + j] : 0.0;
+        nh[a] = has ? soa[(7 + a) * n + j] : 0.0;
+    }
+    const double wr = has ? soa[10 * n + j] : 0.0, wi = has ? soa[11 * n + j] : 0.0;
+
+    PotConst<R> K;
+    K.cx = R(I.tgt.half_R * nh[0]);
+    K.cy = R(I.tgt.half_R * nh[1]);
+    K.cz = R(I.tgt.half_R * nh[2]);
+    K.Zinf = R(I.tgt.Zinf);
+    K.dZ = R(I.tgt.dZ);
+    K.alpha = R(I.tgt.alpha);
+    K.a2 = R(I.tgt.a2);
+    K.w2 = R(I.tgt.w2);
+    K.kind = I.tgt.kind;
+    K.screened = I.tgt.screened;
+    const int n_prim = I.tgt.n_prim;
+    const R gam = R(I.gamma), igam = R(I.inv_gamma);
+    const R wR = R(wr), wI = R(wi);
+    const double cutoff2 = I.cutoff2;
+
+    // ---- state
+    R q[3], p[3], ql[3], pl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        q[a] = R(qd[a]);
+        p[a] = R(pd[a]);
+        ql[a] = R(qd[a] - double(q[a]));
+        pl[a] = R(pd[a] - double(p[a]));
+    }
+    R Mq[6][3], Mp[6][3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            Mq[c][r] = (c == r) ? R(1) : R(0);
+            Mp[c][r] = (c == r + 3) ? R(1) : R(0);
+        }
+    R S = R(0), Sl = R(0);          // action (two-float in MIXED, Sl unused in FP64)
+    C2<R> Cp = {R(1), R(0)};        // prefactor at the previous step
+    int status = 0;                 // 0 alive, 1 filtered, 2 non-finite
+    unsigned long long steps = 0;
+
+    const R h = R(I.dt), h2 = R(0.5 * I.dt), h6 = R(I.dt / 6.0);
+    const int nE = 2 * nt - 1;
+
+    for (int nb = W.n_start; nb < nt; nb += kWarp) {
+        // chunk tables: one element per lane, broadcast later
+        const int nl = nb + lane;
+        R e0, e1, e2;
+        C2<R> phl;
+        if constexpr (MIXED) {
+            e0 = I.Ehf[min(2 * nl, nE - 1)];
+            e1 = I.Ehf[min(2 * nl + 1, nE - 1)];
+            e2 = I.Ehf[min(2 * nl + 2, nE - 1)];
+            const float2 t = I.phf[min(nl, nt - 1)];
+            phl = {t.x, t.y};
+        } else {
+            e0 = I.Eh[min(2 * nl, nE - 1)];
+            e1 = I.Eh[min(2 * nl + 1, nE - 1)];
+            e2 = I.Eh[min(2 * nl + 2, nE - 1)];
+            const double2 t = I.ph[min(nl, nt - 1)];
+            phl = {t.x, t.y};
+        }
+        double bin = 0.0;
+        const int send = min(kWarp, nt - nb);
+        for (int s = 0; s < send; ++s) {
+            const int nn = nb + s;
+            const R E1 = shfl(e0, s), E2 = shfl(e1, s), E4 = shfl(e2, s);
+            const C2<R> ph = {shfl(phl.x, s), shfl(phl.y, s)};
+            bool alive = (nn >= n0) && status == 0;
+            R x = R(0);
+            if (alive) {
+                // ---- 1. prefactor with continuous branch
+                C2<R> C = Cp;
+                if (nn > n0) {
+                    C2<R> B[9];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            B[3 * r + c] = {R(0.5) * (Mq[c][r] + Mp[3 + c][r]),
+                                            R(0.5) * (igam * Mp[c][r] - gam * Mq[3 + c][r])};
+                    const C2<R> m0 = cm(B[4], B[8]), m1 = cm(B[5], B[7]);
+                    const C2<R> m2 = cm(B[3], B[8]), m3 = cm(B[5], B[6]);
+                    const C2<R> m4 = cm(B[3], B[7]), m5 = cm(B[4], B[6]);
+                    const C2<R> c0 = cm(B[0], {m0.x - m1.x, m0.y - m1.y});
+                    const C2<R> c1 = cm(B[1], {m2.x - m3.x, m2.y - m3.y});
+                    const C2<R> c2 = cm(B[2], {m4.x - m5.x, m4.y - m5.y});
+                    const C2<R> det = {c0.x - c1.x + c2.x, c0.y - c1.y + c2.y};
+                    C = csqrt_p(det);
+                    if (C.x * Cp.x + C.y * Cp.y < R(0)) {
+                        C.x = -C.x;
+                        C.y = -C.y;
+                    }
+                    const bool fin = isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) &&
+                                     isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) &&
+                                     isfinite(S) && isfinite(det.x) && isfinite(det.y);
+                    if (!fin) {
+                        status = 2;
+                    } else if (cutoff2 > 0.0 &&
+                               double(hypot_t<R>(det.x, det.y)) > cutoff2) {
+                        status = 1;
+                    }
+                    Cp = C;
+                }
+                alive = status == 0;
+                if (alive) {
+                    // ---- 2. recombination element <psi0| k_z |p,q>
+                    const R pp = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+                    C2<R> Rk = {R(0), R(0)};
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const R dx = c == 0 ? q[0] - K.cx : q[0] + K.cx;
+                        const R dy = c == 0 ? q[1] - K.cy : q[1] + K.cy;
+                        const R dz = c == 0 ? q[2] - K.cz : q[2] + K.cz;
+                        const R dd = dx * dx + dy * dy + dz * dz;
+                        const R pdd = p[0] * dx + p[1] * dy + p[2] * dz;
+#pragma unroll 1
+                        for (int k = 0; k < n_prim; ++k) {
+                            R K1, K2, K3, K4;
+                            if constexpr (MIXED) {
+                                K1 = I.rec.K1f[k]; K2 = I.rec.K2f[k];
+                                K3 = I.rec.K3f[k]; K4 = I.rec.K4f[k];
+                            } else {
+                                K1 = I.rec.K1[k]; K2 = I.rec.K2[k];
+                                K3 = I.rec.K3[k]; K4 = I.rec.K4[k];
+                            }
+                            const R ex = K1 * dd + K2 * pp;
+                            if (ex > (MIXED ? R(-80) : R(-200))) {
+                                const R mag = K4 * exp_t<R>(ex);
+                                R sn, cs;
+                                if constexpr (MIXED) __sincosf(K3 * pdd, &sn, &cs);
+                                else sincos(K3 * pdd, &sn, &cs);
+                                // mag (p_z - i g d_z)(cs + i sn)
+                                const R ar = mag * p[2], ai = -mag * gam * dz;
+                                Rk.x += ar * cs - ai * sn;
+                                Rk.y += ar * sn + ai * cs;
+                            }
+                        }
+                    }
+                    if (Rk.x != R(0) || Rk.y != R(0)) {
+                        // ---- e^{iS}
+                        R sn, cs;
+                        if constexpr (MIXED) {
+                            // two-float reduction of S modulo 2 pi (Cody-Waite split)
+                            const float k = rintf(S * 0.15915494309189535f);
+                            float r = fmaf(-k, 6.28318548202514648f, S);
+                            r = fmaf(-k, -1.7484555314695172e-07f, r);
+                            r += Sl;
+                            __sincosf(r, &sn, &cs);
+                        } else {
+                            sincos(S, &sn, &cs);
+                        }
+                        const C2<R> eS = {cs, sn};
+                        const C2<R> wC = cm(C2<R>{wR, wI}, C);
+                        const C2<R> a = cm(wC, eS);
+                        const C2<R> b = cm(a, ph);
+                        x = b.x * Rk.x - b.y * Rk.y;
+                    }
+                }
+            }
+            // ---- 3. warp sum (skipped when no lane contributes)
+            if (__any_sync(kFull, x != R(0))) {
+                double tot;
+                if constexpr (MIXED) {
+                    float sv = x, ev = 0.0f;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const float so = __shfl_xor_sync(kFull, sv, off);
+                        const float eo = __shfl_xor_sync(kFull, ev, off);
+                        float t;
+                        two_sum(sv, so, sv, t);
+                        ev = ev + eo + t;
+                    }
+                    tot = double(sv) + double(ev);
+                } else {
+                    double sv = x;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(kFull, sv, off);
+                    tot = sv;
+                }
+                if (lane == s) bin = tot;
+            }
+            // ---- 4. RK4 step to t_{n+1}
+            if (alive && nn < nt - 1) {
+                ++steps;
+                Sym3<R> H1, H2, H3, H4;
+                R V, F[3];
+                potential<R>(K, q[0], q[1], q[2], V, F[0], F[1], F[2], H1);
+                R k1p[3] = {F[0], F[1], F[2] - E1};
+                const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
+                R q2[3], p2[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    q2[a] = q[a] + h2 * p[a];
+                    p2[a] = p[a] + h2 * k1p[a];
+                }
+                potential<R>(K, q2[0], q2[1], q2[2], V, F[0], F[1], F[2], H2);
+                R k2p[3] = {F[0], F[1], F[2] - E2};
+                const R k2s = R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - q2[2] * E2;
+                R q3[3], p3[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    q3[a] = q[a] + h2 * p2[a];
+                    p3[a] = p[a] + h2 * k2p[a];
+                }
+                potential<R>(K, q3[0], q3[1], q3[2], V, F[0], F[1], F[2], H3);
+                R k3p[3] = {F[0], F[1], F[2] - E2};
+                const R k3s = R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - q3[2] * E2;
+                R q4[3], p4[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    q4[a] = q[a] + h * p3[a];
+                    p4[a] = p[a] + h * k3p[a];
+                }
+                potential<R>(K, q4[0], q4[1], q4[2], V, F[0], F[1], F[2], H4);
+                const R k4s = R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - q4[2] * E4;
+                const R dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const R k4p = F[a] - (a == 2 ? E4 : R(0));
+                    const R dq = h6 * (p[a] + R(2) * (p2[a] + p3[a]) + p4[a]);
+                    const R dp = h6 * (k1p[a] + R(2) * (k2p[a] + k3p[a]) + k4p);
+                    if constexpr (MIXED) {
+                        df_add(q[a], ql[a], dq);
+                        df_add(p[a], pl[a], dp);
+                    } else {
+                        q[a] += dq;
+                        p[a] += dp;
+                    }
+                }
+                if constexpr (MIXED) df_add(S, Sl, dS);
+                else S += dS;
+                // stability-matrix columns with the four stage Hessians
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    R x0[3], v0[3], a1[3], xs[3], vs[3], a2[3], a3[3], a4[3], v2[3], v3[3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        x0[r] = Mq[c][r];
+                        v0[r] = Mp[c][r];
+                    }
+                    neg_hx(H1, x0, a1);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        xs[r] = x0[r] + h2 * v0[r];
+                        v2[r] = v0[r] + h2 * a1[r];
+                    }
+                    neg_hx(H2, xs, a2);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        xs[r] = x0[r] + h2 * v2[r];
+                        v3[r] = v0[r] + h2 * a2[r];
+                    }
+                    neg_hx(H3, xs, a3);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        xs[r] = x0[r] + h * v3[r];
+                        vs[r] = v0[r] + h * a3[r];
+                    }
+                    neg_hx(H4, xs, a4);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        Mq[c][r] = x0[r] + h6 * (v0[r] + R(2) * (v2[r] + v3[r]) + vs[r]);
+                        Mp[c][r] = v0[r] + h6 * (a1[r] + R(2) * (a2[r] + a3[r]) + a4[r]);
+                    }
+                }
+            }
+        }
+        if (lane < send && bin != 0.0) atomicAdd(&I.vz[nb + lane], I.scale * bin);
+        if (!__any_sync(kFull, has && status == 0)) break;
+    }
+
+    // ---- counters and optional final state
+    const unsigned filt = __ballot_sync(kFull, has && status == 1);
+    const unsigned nonf = __ballot_sync(kFull, has && status == 2);
+    unsigned long long st = steps;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) st += __shfl_xor_sync(kFull, st, off);
+    if (lane == 0) {
+        if (filt) atomicAdd(&I.counters[0], (unsigned long long)__popc(filt));
+        if (nonf) atomicAdd(&I.counters[1], (unsigned long long)__popc(nonf));
+        atomicAdd(&I.counters[2], st);
+    }
+    if (I.dump != nullptr && has) {
+        double* d = I.dump;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            d[(size_t)a * n + j] = double(q[a]) + double(ql[a]) * (MIXED ? 1.0 : 0.0);
+            d[(size_t)(3 + a) * n + j] = double(p[a]) + double(pl[a]) * (MIXED ? 1.0 : 0.0);
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                d[(size_t)(6 + 6 * r + c) * n + j] = double(Mq[c][r]);
+                d[(size_t)(6 + 6 * (r + 3) + c) * n + j] = double(Mp[c][r]);
+            }
+        d[(size_t)42 * n + j] = double(S) + (MIXED ? double(Sl) : 0.0);
+        d[(size_t)43 * n + j] = double(Cp.x);
+        d[(size_t)44 * n + j] = double(Cp.y);
+        d[(size_t)45 * n + j] = 0.0;
+        d[(size_t)46 * n + j] = double(status);
+    }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_propagate(const DevInstance* __restrict__ insts,
+                                                   const WorkItem* __restrict__ items, int n_items,
+                                                   unsigned int* __restrict__ counter)
+{
+    const int lane = threadIdx.x & (kWarp - 1);
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;
+        const WorkItem W = items[it];
+        process_item<MIXED>(insts[W.inst], W, lane);
+    }
+}
+
+}  // namespace
+
+int propagate_occupancy(int precision, int block_threads, int* blocks_per_sm)
+{
+    cudaError_t e;
+    if (precision == SFHK_MIXED)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true>,
+                                                          block_threads, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<false>,
+                                                          block_threads, 0);
+    SFHK_CUDA_TRY(e);
+    return SFHK_OK;
+}
+
+int launch_propagate(int precision, const DevInstance* insts, const WorkItem* items, int n_items,
+                     unsigned int* item_counter, int block_threads, int blocks_per_sm,
+                     int sm_count, cudaStream_t s)
+{
+    if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
+    int occ = 0;
+    int rc = propagate_occupancy(precision, block_threads, &occ);
+    if (rc) return rc;
+    if (occ < 1) occ = 1;
+    const int bps = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
+    const int warps_needed = n_items;
+    const int warps_per_block = block_threads / kWarp;
+    int grid = sm_count * bps;
+    const int grid_cap = (warps_needed + warps_per_block - 1) / warps_per_block;
+    if (grid > grid_cap) grid = grid_cap;
+    if (grid < 1) grid = 1;
+    SFHK_CUDA_TRY(cudaMemsetAsync(item_counter, 0, sizeof(unsigned int), s));
+    count_launch();
+    if (precision == SFHK_MIXED)
+        k_propagate<true><<<grid, block_threads, 0, s>>>(insts, items, n_items, item_counter);
+    else
+        k_propagate<false><<<grid, block_threads, 0, s>>>(insts, items, n_items, item_counter);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+}  // namespace sfhk

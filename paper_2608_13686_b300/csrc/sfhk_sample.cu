@@ -1,0 +1,492 @@
+// sfhk_sample.cu -- pulse tables, the ionization step (initial ensemble) and
+// the counting sorts that order trajectories by birth time.
+//
+// Ionization step (Sec. II.A, Eqs. 1-2, 6), one thread per trajectory, FP64:
+//   t0 on the time grid by inverse CDF of p_n ~ exp(-2 (2Ip)^{3/2}/(3|E(t_n)|)),
+//   k_perp ~ N(0, |E(t0)| / (2 sqrt(2 Ip))) per component (Box-Muller),
+//   molecular axis per trajectory (Eq. 6) from the alignment distribution,
+//   saddle t_s = t0 + i tt of Eq. 2 by safeguarded Newton on
+//     Y(tt) = Im A(t0 + i tt) = -sgn(E(t0)) sqrt(2 Ip + k_perp^2),
+//   k_z = -Re[A(t_s) - A(t0)], exit q0 = Re int_{t_s}^{t0} A, tunnelling action
+//   S_down = Ip t_s - int_{t_s}^{t0} [k + A - A(t0)]^2/2, all in closed form
+//   from the three-sinusoid form of the sin^2 pulse, and the amplitude
+//   a = <kappa| z E(t_s) |psi0> / sqrt(E(t_s) kappa_z) e^{i(S_down + k.q0)}
+//   with the analytic Fourier transform of the Gaussian orbital; w = a / pdf.
+#include <cuda_runtime.h>
+
+#include "sfhk_device.cuh"
+#include "sfhk_internal.h"
+
+namespace sfhk {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// E(t) from its definition E = -dA/dt of A = -(E0/w) cos^2(pi t/Tp) sin(w t + cep).
+__device__ double field_direct(double omega, double E0, double Tp, double cep, double t)
+{
+    if (fabs(t) > 0.5 * Tp) return 0.0;
+    const double c = cos(kPi * t / Tp);
+    const double ph = omega * t + cep;
+    return E0 * c * c * cos(ph) - (E0 * kPi / (omega * Tp)) * sin(2.0 * kPi * t / Tp) * sin(ph);
+}
+
+__global__ void k_field_table(double omega, double E0, double Tp, double cep, double t_origin,
+                              double dt, int nt, double* Eh, float* Ehf)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= 2 * nt - 1) return;
+    const int n = m >> 1;
+    double t = t_origin + n * dt;
+    if (m & 1) t += 0.5 * dt;
+    const double e = field_direct(omega, E0, Tp, cep, t);
+    Eh[m] = e;
+    Ehf[m] = (float)e;
+}
+
+__global__ void k_phase_table(double Ip, double t_origin, double dt, int nt, double2* ph,
+                              float2* phf)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nt) return;
+    double s, c;
+    sincos(Ip * (t_origin + n * dt), &s, &c);
+    ph[n] = make_double2(c, -s);
+    phf[n] = make_float2((float)c, (float)-s);
+}
+
+// ADK weights and their inclusive prefix sum, one block of 1024 threads:
+// contiguous chunks, chunk totals scanned in shared memory.
+__global__ void __launch_bounds__(1024) k_adk_cdf(double omega, double E0, double Tp, double cep,
+                                                  double t_origin, double dt, int nt, double Ip,
+                                                  double* cdf)
+{
+    __shared__ double part[1024];
+    const int tid = threadIdx.x;
+    const int chunk = (nt + 1023) / 1024;
+    const int b = tid * chunk, e = min(nt, b + chunk);
+    const double cst = 2.0 * pow(2.0 * Ip, 1.5) / 3.0;
+    double acc = 0.0;
+    for (int n = b; n < e; ++n) {
+        const double f = fabs(field_direct(omega, E0, Tp, cep, t_origin + n * dt));
+        const double w = f > 0.0 ? exp(-cst / f) : 0.0;
+        acc += w;
+        cdf[n] = acc;
+    }
+    part[tid] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double run = 0.0;
+        for (int i = 0; i < 1024; ++i) {
+            const double v = part[i];
+            part[i] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    const double off = part[tid];
+    for (int n = b; n < e; ++n) cdf[n] += off;
+}
+
+struct SampleParams {
+    PulseTerms P;
+    double omega, E0, Tp, t_origin, dt;
+    int nt;
+    double Ip;
+    int align_kind;
+    double theta, phi;
+    uint64_t seed;
+    uint32_t instance;
+    long long n;
+    double R;
+    int n_prim;
+    double norm;
+    double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
+};
+
+// int_0^T sin(th + i k s) ds and int_0^T cos(al + i be s) ds
+__device__ __forceinline__ double2 int_sin(double th, double k, double T)
+{
+    if (k == 0.0) return make_double2(T * sin(th), 0.0);
+    double s, c;
+    sincos(th, &s, &c);
+    const double x = k * T;
+    const double cm1 = 2.0 * sinh(0.5 * x) * sinh(0.5 * x);   // cosh x - 1
+    return make_double2(s * sinh(x) / k, c * cm1 / k);
+}
+__device__ __forceinline__ double2 int_cos(double al, double be, double T)
+{
+    if (be == 0.0) return make_double2(T * cos(al), 0.0);
+    double s, c;
+    sincos(al, &s, &c);
+    const double x = be * T;
+    const double cm1 = 2.0 * sinh(0.5 * x) * sinh(0.5 * x);
+    return make_double2(c * sinh(x) / be, -s * cm1 / be);
+}
+
+__global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double* __restrict__ soa,
+                         int* __restrict__ n0_out, unsigned long long* n_invalid)
+{
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j >= S.n) return;
+    const long long n = S.n;
+    // ---- random numbers: Philox4x32-10, key = seed, counter = (j, instance, draw)
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+    double u[6];
+#pragma unroll
+    for (uint32_t d = 0; d < 3; ++d) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)(j >> 32), S.instance, d), key);
+        u[2 * d] = u01(r.x, r.y);
+        u[2 * d + 1] = u01(r.z, r.w);
+    }
+    // ---- birth time: smallest m with cdf[m] > u0 * total
+    const double total = cdf[S.nt - 1];
+    const double thr = u[0] * total;
+    int lo = 0, hi = S.nt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cdf[mid] > thr) hi = mid; else lo = mid + 1;
+    }
+    const int m = lo;
+    const double t0 = S.t_origin + m * S.dt;
+    const double Et0 = field_direct(S.omega, S.E0, S.Tp, S.P.cep, t0);
+    const double sqrt2Ip = sqrt(2.0 * S.Ip);
+    const double sigma = sqrt(fabs(Et0) / (2.0 * sqrt2Ip));
+    const double rr = sqrt(-2.0 * log(u[1]));
+    double sb, cb;
+    sincos(2.0 * kPi * u[2], &sb, &cb);
+    const double kx = sigma * rr * cb, ky = sigma * rr * sb;
+    // ---- molecular axis (Eq. 6)
+    double th = S.theta, phv = S.phi;
+    if (S.align_kind == SFHK_ALIGN_ISOTROPIC) {
+        th = acos(2.0 * u[3] - 1.0);
+        phv = 2.0 * kPi * u[4];
+    } else if (S.align_kind == SFHK_ALIGN_COS2) {
+        th = acos(cbrt(2.0 * u[3] - 1.0));
+        phv = 2.0 * kPi * u[4];
+    }
+    double sth, cth, sph, cph;
+    sincos(th, &sth, &cth);
+    sincos(phv, &sph, &cph);
+    const double nx = sth * cph, ny = sth * sph, nz = cth;
+
+    double qz = 0.0, kz = 0.0;
+    double2 w = make_double2(0.0, 0.0);
+    bool ok = fabs(Et0) > 0.0;
+    double tt = 0.0;
+    double cthm[3], sthm[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sincos(S.P.k[q] * t0 + S.P.cep, &sthm[q], &cthm[q]);
+    const double kp2 = kx * kx + ky * ky;
+    const double target = 2.0 * S.Ip + kp2;
+    if (ok) {
+        // ---- saddle point: g(s) = Y(s) - Y*, Y(s) = sum a cos(th) sinh(k s)
+        const double Ystar = (Et0 > 0.0 ? -1.0 : 1.0) * sqrt(target);
+        auto g = [&](double s, double* dg) {
+            double y = 0.0, yp = 0.0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const double ks = S.P.k[q] * s;
+                y += S.P.a[q] * cthm[q] * sinh(ks);
+                yp += S.P.a[q] * S.P.k[q] * cthm[q] * cosh(ks);
+            }
+            *dg = yp;
+            return y - Ystar;
+        };
+        const double s0 = sqrt(target) / fabs(Et0);
+        const double sg0 = -Ystar;     // g(0)
+        double slo = 0.0, shi = s0, dg;
+        double ghi = g(shi, &dg);
+        ok = false;
+        for (int it = 0; it < 64; ++it) {
+            if ((ghi > 0.0) != (sg0 > 0.0) || ghi == 0.0) { ok = true; break; }
+            slo = shi;
+            shi *= 1.25;
+            if (shi > 64.0 * s0) break;
+            ghi = g(shi, &dg);
+        }
+        if (ok) {
+            double s = 0.5 * (slo + shi);
+            for (int it = 0; it < 200; ++it) {
+                const double gs = g(s, &dg);
+                if (gs == 0.0) { slo = shi = s; break; }
+                if ((gs > 0.0) == (sg0 > 0.0)) slo = s; else shi = s;
+                double sn = s - gs / dg;
+                if (!(sn > slo && sn < shi)) sn = 0.5 * (slo + shi);
+                if (fabs(sn - s) <= 4e-16 * s || shi - slo <= 4e-16 * shi) { s = sn; break; }
+                s = sn;
+            }
+            tt = s;
+            // ---- k_z, exit and action in closed form
+            double At0 = 0.0, dRe = 0.0, q0 = 0.0, Yt = 0.0;
+            double2 Es = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const double a = S.P.a[q], k = S.P.k[q], x = k * tt;
+                const double sh = sinh(x), cm1 = 2.0 * sinh(0.5 * x) * sinh(0.5 * x);
+                At0 += a * sthm[q];
+                dRe += a * sthm[q] * cm1;                  // Re A(t_s) - A(t0)
+                Yt += a * cthm[q] * sh;                    // Im A(t_s)
+                if (k != 0.0) q0 += a * cthm[q] * cm1 / k; // int_0^tt Im A(t0+is) ds
+                // E(t_s) = -sum a k cos(th + i k tt)
+                Es.x -= a * k * cthm[q] * (cm1 + 1.0);
+                Es.y += a * k * sthm[q] * sh;
+            }
+            kz = -dRe;
+            qz = q0;
+            const double2 kapz = make_double2(kz + dRe, Yt);
+            // int_0^tt B(s)^2 ds, B = c' + sum a sin(th + i k s), c' = kz - A(t0)
+            const double cp = kz - At0;
+            double2 IB = make_double2(cp * cp * tt, 0.0);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const double2 is = int_sin(S.P.k[q] * t0 + S.P.cep, S.P.k[q], tt);
+                IB = cadd(IB, cscale(is, 2.0 * cp * S.P.a[q]));
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const double thq = S.P.k[q] * t0 + S.P.cep, thr = S.P.k[r] * t0 + S.P.cep;
+                    const double2 d1 = int_cos(thq - thr, S.P.k[q] - S.P.k[r], tt);
+                    const double2 d2 = int_cos(thq + thr, S.P.k[q] + S.P.k[r], tt);
+                    IB = cadd(IB, cscale(csub(d1, d2), 0.5 * S.P.a[q] * S.P.a[r]));
+                }
+            }
+            // S_down = Ip (t0 + i tt) + (i/2)(kp2 tt + IB)
+            const double2 Sd = make_double2(S.Ip * t0 - 0.5 * IB.y, S.Ip * tt + 0.5 * (kp2 * tt + IB.x));
+            // <kappa| z |psi0>, kappa = (kx, ky, kapz)
+            const double2 kk = make_double2(kp2 + kapz.x * kapz.x - kapz.y * kapz.y,
+                                            2.0 * kapz.x * kapz.y);
+            double2 mz = make_double2(0.0, 0.0);
+            for (int c = 0; c < 2; ++c) {
+                const double sgn = c == 0 ? 1.0 : -1.0;
+                const double Ax = sgn * 0.5 * S.R * nx, Ay = sgn * 0.5 * S.R * ny,
+                             Az = sgn * 0.5 * S.R * nz;
+                // kappa.A (complex)
+                const double2 kA = make_double2(kx * Ax + ky * Ay + kapz.x * Az, kapz.y * Az);
+                for (int p = 0; p < S.n_prim; ++p) {
+                    const double a = S.pexp[p];
+                    // -i kappa.A - kappa.kappa / (4a)
+                    const double2 ex = make_double2(kA.y - kk.x / (4.0 * a), -kA.x - kk.y / (4.0 * a));
+                    const double2 F = cscale(cexp_(ex), S.pcoef[p] * pow(kPi / a, 1.5));
+                    // (A_z - i kappa_z / (2a))
+                    const double2 f = make_double2(Az + kapz.y / (2.0 * a), -kapz.x / (2.0 * a));
+                    mz = cadd(mz, cmul(F, f));
+                }
+            }
+            mz = cscale(mz, S.norm * pow(2.0 * kPi, -1.5));
+            // amplitude and weight
+            const double2 num = cmul(Es, mz);
+            const double2 den = csqrt_(cmul(Es, kapz));
+            const double2 Z = make_double2(Sd.x + kz * qz, Sd.y);     // S_down + k.q0
+            const double2 eiz = cexp_(make_double2(-Z.y, Z.x));        // e^{iZ}
+            const double2 amp = cmul(cdiv(num, den), eiz);
+            const double cst = 2.0 * pow(2.0 * S.Ip, 1.5) / 3.0;
+            const double Wm = exp(-cst / fabs(Et0));
+            const double pdf = (Wm / total) / S.dt * exp(-kp2 / (2.0 * sigma * sigma)) /
+                               (2.0 * kPi * sigma * sigma);
+            w = make_double2(amp.x / pdf, amp.y / pdf);
+        }
+    }
+    if (!ok) atomicAdd(n_invalid, 1ull);
+    soa[0 * n + j] = (double)m;
+    soa[1 * n + j] = 0.0;
+    soa[2 * n + j] = 0.0;
+    soa[3 * n + j] = qz;
+    soa[4 * n + j] = kx;
+    soa[5 * n + j] = ky;
+    soa[6 * n + j] = kz;
+    soa[7 * n + j] = nx;
+    soa[8 * n + j] = ny;
+    soa[9 * n + j] = nz;
+    soa[10 * n + j] = w.x;
+    soa[11 * n + j] = w.y;
+    n0_out[j] = m;
+}
+
+__global__ void k_n0_from_soa(const double* soa, long long n, int* n0)
+{
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j < n) n0[j] = (int)soa[j];
+}
+
+// ------------------------------------------------------------------ counting sort
+__global__ void k_hist(const int* keys, long long n, int* hist)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&hist[keys[j]], 1);
+}
+
+// exclusive scan of K ints in one block (chunked)
+__global__ void __launch_bounds__(1024) k_exscan(int* a, int K)
+{
+    __shared__ long long part[1024];
+    const int tid = threadIdx.x;
+    const int chunk = (K + 1023) / 1024;
+    const int b = tid * chunk, e = min(K, b + chunk);
+    long long acc = 0;
+    for (int i = b; i < e; ++i) acc += a[i];
+    part[tid] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        long long run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const long long v = part[i];
+            part[i] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    long long run = part[tid];
+    for (int i = b; i < e; ++i) {
+        const int v = a[i];
+        a[i] = (int)run;
+        run += v;
+    }
+}
+
+__global__ void k_scatter(const int* keys, long long n, int* cursor, int* perm)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x)
+        perm[atomicAdd(&cursor[keys[j]], 1)] = (int)j;
+}
+
+__global__ void k_build_items(const int* perm, const int* n0, long long n, int inst,
+                              WorkItem* items)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long first = i * kWarp;
+    if (first >= n) return;
+    WorkItem it;
+    it.inst = inst;
+    it.first = (int)first;
+    it.count = (int)min((long long)kWarp, n - first);
+    // the smallest n0 of the item (counting sort orders by n0)
+    int m = n0[perm[first]];
+    for (int k = 1; k < it.count; ++k) m = min(m, n0[perm[first + k]]);
+    it.n_start = m;
+    items[i] = it;
+}
+
+__global__ void k_item_keys(const WorkItem* items, int n_items, const int* inst_nt, int K,
+                            int* keys)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_items) return;
+    const WorkItem it = items[i];
+    const int len = inst_nt[it.inst] - it.n_start;      // 1..K
+    keys[i] = K - len;                                   // longest first
+}
+
+__global__ void k_gather_items(const WorkItem* in, const int* perm, int n_items, WorkItem* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_items) out[i] = in[perm[i]];
+}
+
+int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+
+}  // namespace
+
+int launch_field_table(const Pulse& P, double* Eh, float* Ehf, cudaStream_t s)
+{
+    const int m = 2 * P.nt - 1;
+    count_launch();
+    k_field_table<<<grid_for(m, 256), 256, 0, s>>>(P.omega, P.E0, P.Tp, P.desc.cep, P.t_origin,
+                                                    P.dt, P.nt, Eh, Ehf);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+int launch_phase_table(const Pulse& P, double Ip, double2* ph, float2* phf, cudaStream_t s)
+{
+    count_launch();
+    k_phase_table<<<grid_for(P.nt, 256), 256, 0, s>>>(Ip, P.t_origin, P.dt, P.nt, ph, phf);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+int launch_adk_cdf(const Pulse& P, double Ip, double* cdf, cudaStream_t s)
+{
+    count_launch();
+    k_adk_cdf<<<1, 1024, 0, s>>>(P.omega, P.E0, P.Tp, P.desc.cep, P.t_origin, P.dt, P.nt, Ip, cdf);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, long long n,
+                  uint64_t seed, uint32_t instance, const double* cdf, double* soa, int* n0,
+                  unsigned long long* n_invalid, cudaStream_t s)
+{
+    SampleParams S;
+    S.P = pulse_terms(P.omega, P.E0, P.Tp, P.desc.cep);
+    S.omega = P.omega;
+    S.E0 = P.E0;
+    S.Tp = P.Tp;
+    S.t_origin = P.t_origin;
+    S.dt = P.dt;
+    S.nt = P.nt;
+    S.Ip = T.desc.Ip;
+    S.align_kind = al.kind;
+    S.theta = al.theta;
+    S.phi = al.phi;
+    S.seed = seed;
+    S.instance = instance;
+    S.n = n;
+    S.R = T.desc.R;
+    S.n_prim = T.desc.n_prim;
+    S.norm = T.dev.norm;
+    for (int k = 0; k < SFHK_MAX_PRIM; ++k) {
+        S.pexp[k] = T.desc.prim_exp[k];
+        S.pcoef[k] = T.desc.prim_coef[k];
+    }
+    count_launch();
+    k_sample<<<grid_for(n, 128), 128, 0, s>>>(S, cdf, soa, n0, n_invalid);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+int launch_n0_from_soa(const double* soa, long long n, int* n0, cudaStream_t s)
+{
+    count_launch();
+    k_n0_from_soa<<<grid_for(n, 256), 256, 0, s>>>(soa, n, n0);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+int launch_counting_sort(const int* keys, long long n, int K, int* perm, int* hist, cudaStream_t s)
+{
+    SFHK_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * K, s));
+    const int g = (int)std::min<long long>(grid_for(n, 256), 148 * 16);
+    count_launch(3);
+    k_hist<<<g, 256, 0, s>>>(keys, n, hist);
+    k_exscan<<<1, 1024, 0, s>>>(hist, K);
+    k_scatter<<<g, 256, 0, s>>>(keys, n, hist, perm);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+int launch_build_items(const int* perm, const int* n0, long long n, int inst, WorkItem* items,
+                       cudaStream_t s)
+{
+    const long long n_items = (n + kWarp - 1) / kWarp;
+    count_launch();
+    k_build_items<<<grid_for(n_items, 128), 128, 0, s>>>(perm, n0, n, inst, items);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+int launch_sort_items(const WorkItem* in, int n_items, const int* inst_nt, WorkItem* out,
+                      int* keys, int* perm, int* hist, int K, cudaStream_t s)
+{
+    count_launch(2);
+    k_item_keys<<<grid_for(n_items, 256), 256, 0, s>>>(in, n_items, inst_nt, K, keys);
+    int rc = launch_counting_sort(keys, n_items, K, perm, hist, s);
+    if (rc) return rc;
+    k_gather_items<<<grid_for(n_items, 256), 256, 0, s>>>(in, perm, n_items, out);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+}  // namespace sfhk

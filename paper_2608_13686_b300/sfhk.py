@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libsfhk (include/sfhk.h), same names as the C ABI.
+
+Argument marshalling only: every step of the SFHK path runs in the library's
+CUDA kernels.  Importing this module loads ``libsfhk.so`` from the package
+directory and raises if it is missing (there is no CPU fallback); build it
+with ``python -m paper_2608_13686_b300._build``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsfhk.so")
+
+SFHK_OK = 0
+SFHK_E_INVAL, SFHK_E_NOMEM, SFHK_E_CUDA = -1, -2, -3
+SFHK_E_TIMEOUT, SFHK_E_NUMERIC, SFHK_E_BUSY, SFHK_E_NOTFOUND = -4, -5, -6, -7
+SFHK_MAX_PRIM = 8
+SFHK_POT_MOLECULE, SFHK_POT_HARMONIC = 0, 1
+SFHK_ALIGN_FIXED, SFHK_ALIGN_ISOTROPIC, SFHK_ALIGN_COS2 = 0, 1, 2
+SFHK_FP64, SFHK_MIXED = 0, 1
+SOA_FIELDS = 12
+FINAL_FIELDS = 47
+
+
+class SfhkError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class sfhk_target_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_prim", C.c_int), ("R", C.c_double),
+                ("Z_inf", C.c_double), ("Z0", C.c_double), ("alpha", C.c_double),
+                ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
+                ("prim_exp", C.c_double * SFHK_MAX_PRIM), ("prim_coef", C.c_double * SFHK_MAX_PRIM)]
+
+
+class sfhk_pulse_desc(C.Structure):
+    _fields_ = [("lambda_nm", C.c_double), ("intensity_Wcm2", C.c_double),
+                ("n_cycles", C.c_double), ("cep", C.c_double), ("dt", C.c_double)]
+
+
+class sfhk_align_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("theta", C.c_double), ("phi", C.c_double)]
+
+
+class sfhk_run_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("gamma", C.c_double), ("prefactor_cutoff", C.c_double),
+                ("dump_final", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int)]
+
+
+class sfhk_stats(C.Structure):
+    _fields_ = [("n_traj", C.c_uint64), ("n_invalid", C.c_uint64), ("n_filtered", C.c_uint64),
+                ("n_nonfinite", C.c_uint64), ("traj_steps", C.c_uint64), ("nt", C.c_int),
+                ("kernel_ms", C.c_float)]
+
+
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2608_13686_b300._build` (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "sfhk_strerror": ([C.c_int], C.c_char_p),
+        "sfhk_create": ([C.POINTER(_vp), C.c_int, C.c_size_t], C.c_int),
+        "sfhk_destroy": ([_vp], C.c_int),
+        "sfhk_mem_used": ([_vp, C.POINTER(C.c_size_t)], C.c_int),
+        "sfhk_create_target": ([_vp, C.POINTER(sfhk_target_desc), C.POINTER(_vp)], C.c_int),
+        "sfhk_destroy_target": ([_vp], C.c_int),
+        "sfhk_set_pulse": ([_vp, C.POINTER(sfhk_pulse_desc), C.POINTER(_vp)], C.c_int),
+        "sfhk_destroy_pulse": ([_vp], C.c_int),
+        "sfhk_pulse_grid": ([_vp, C.POINTER(C.c_int), _dp, _dp, _dp], C.c_int),
+        "sfhk_sample_initial": ([_vp, _vp, _vp, C.POINTER(sfhk_align_desc), C.c_uint64, C.c_uint64,
+                                 C.c_uint32, C.POINTER(_vp), _vp], C.c_int),
+        "sfhk_sample_into": ([_vp, _vp, C.POINTER(sfhk_align_desc), C.c_uint64, C.c_uint32, _vp],
+                             C.c_int),
+        "sfhk_launch_count": ([C.POINTER(C.c_uint64)], C.c_int),
+        "sfhk_load_ensemble": ([_vp, _vp, _vp, _dp, C.c_uint64, C.c_double, C.POINTER(_vp)],
+                               C.c_int),
+        "sfhk_ensemble_read": ([_vp, _dp, C.c_uint64], C.c_int),
+        "sfhk_destroy_ensemble": ([_vp], C.c_int),
+        "sfhk_propagate": ([_vp, _vp, C.POINTER(sfhk_run_opts), _vp], C.c_int),
+        "sfhk_propagate_batch": ([_vp, C.POINTER(_vp), C.c_int, C.POINTER(sfhk_run_opts), _vp],
+                                 C.c_int),
+        "sfhk_dipole": ([_vp, _vp, _dp, C.c_size_t, _dp, _dp], C.c_int),
+        "sfhk_dipole_device": ([_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)], C.c_int),
+        "sfhk_stats_get": ([_vp, C.POINTER(sfhk_stats)], C.c_int),
+        "sfhk_final_state": ([_vp, _dp, C.c_uint64], C.c_int),
+        "sfhk_spectrum": ([_vp, C.c_size_t, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp,
+                           C.c_size_t, C.c_int, _vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def lib():
+    return _load()
+
+
+def strerror(code: int) -> str:
+    return _load().sfhk_strerror(code).decode()
+
+
+def _check(rc, where):
+    if rc != SFHK_OK:
+        raise SfhkError(rc, where)
+
+
+def _p(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+# ------------------------------------------------------------------ descriptors
+def target_desc(t: dict) -> sfhk_target_desc:
+    d = sfhk_target_desc()
+    d.kind = int(t.get("kind", SFHK_POT_MOLECULE))
+    pe, pc = list(t["pexp"]), list(t["pcoef"])
+    d.n_prim = len(pe)
+    d.R, d.Z_inf, d.Z0 = float(t["R"]), float(t["Zinf"]), float(t["Z0"])
+    d.alpha, d.soft_a, d.Ip = float(t["alpha"]), float(t["soft_a"]), float(t["Ip"])
+    d.ho_omega = float(t.get("ho_omega", 0.0))
+    for i, (e, c) in enumerate(zip(pe, pc)):
+        d.prim_exp[i] = e
+        d.prim_coef[i] = c
+    return d
+
+
+def pulse_desc(p: dict) -> sfhk_pulse_desc:
+    return sfhk_pulse_desc(p["lambda_nm"], p["intensity"], p["n_cycles"], p.get("cep", 0.0),
+                           p["dt"])
+
+
+def align_desc(a) -> sfhk_align_desc:
+    return sfhk_align_desc(int(a[0]), float(a[1]), float(a[2]))
+
+
+def run_opts(precision=SFHK_FP64, gamma=0.5, cutoff=0.0, dump=False, block_threads=0,
+             blocks_per_sm=0) -> sfhk_run_opts:
+    return sfhk_run_opts(precision, gamma, cutoff, int(dump), block_threads, blocks_per_sm)
+
+
+# ------------------------------------------------------------------ C-ABI calls
+def sfhk_create(device=0, budget=0):
+    h = _vp()
+    _check(_load().sfhk_create(C.byref(h), device, budget), "sfhk_create")
+    return h
+
+
+def sfhk_destroy(ctx):
+    _check(_load().sfhk_destroy(ctx), "sfhk_destroy")
+
+
+def sfhk_mem_used(ctx):
+    v = C.c_size_t()
+    _check(_load().sfhk_mem_used(ctx, C.byref(v)), "sfhk_mem_used")
+    return v.value
+
+
+def sfhk_create_target(ctx, t: dict):
+    h = _vp()
+    d = target_desc(t)
+    _check(_load().sfhk_create_target(ctx, C.byref(d), C.byref(h)), "sfhk_create_target")
+    return h
+
+
+def sfhk_destroy_target(h):
+    _check(_load().sfhk_destroy_target(h), "sfhk_destroy_target")
+
+
+def sfhk_set_pulse(ctx, p: dict):
+    h = _vp()
+    d = pulse_desc(p)
+    _check(_load().sfhk_set_pulse(ctx, C.byref(d), C.byref(h)), "sfhk_set_pulse")
+    return h
+
+
+def sfhk_destroy_pulse(h):
+    _check(_load().sfhk_destroy_pulse(h), "sfhk_destroy_pulse")
+
+
+def sfhk_pulse_grid(h):
+    nt, t0, dt, tp = C.c_int(), C.c_double(), C.c_double(), C.c_double()
+    _check(_load().sfhk_pulse_grid(h, C.byref(nt), C.byref(t0), C.byref(dt), C.byref(tp)),
+           "sfhk_pulse_grid")
+    return dict(nt=nt.value, t_origin=t0.value, dt=dt.value, Tp=tp.value)
+
+
+def sfhk_sample_initial(ctx, target, pulse, align, n_traj, seed=0, instance=0, stream=None):
+    h = _vp()
+    a = align_desc(align)
+    _check(_load().sfhk_sample_initial(ctx, target, pulse, C.byref(a), n_traj, seed, instance,
+                                       C.byref(h), stream), "sfhk_sample_initial")
+    return h
+
+
+def sfhk_sample_into(ctx, ens, align, seed=0, instance=0, stream=None):
+    a = align_desc(align)
+    _check(_load().sfhk_sample_into(ctx, ens, C.byref(a), seed, instance, stream),
+           "sfhk_sample_into")
+
+
+def sfhk_launch_count():
+    v = C.c_uint64()
+    _check(_load().sfhk_launch_count(C.byref(v)), "sfhk_launch_count")
+    return v.value
+
+
+def sfhk_load_ensemble(ctx, target, pulse, soa: np.ndarray, n_norm=0.0):
+    soa = np.ascontiguousarray(soa, dtype=np.float64)
+    assert soa.shape[0] == SOA_FIELDS
+    h = _vp()
+    _check(_load().sfhk_load_ensemble(ctx, target, pulse, _p(soa), soa.shape[1], n_norm,
+                                      C.byref(h)), "sfhk_load_ensemble")
+    return h
+
+
+def sfhk_ensemble_read(ens, n):
+    out = np.zeros((SOA_FIELDS, n))
+    _check(_load().sfhk_ensemble_read(ens, _p(out), n), "sfhk_ensemble_read")
+    return out
+
+
+def sfhk_destroy_ensemble(h):
+    _check(_load().sfhk_destroy_ensemble(h), "sfhk_destroy_ensemble")
+
+
+def sfhk_propagate(ctx, ens, opts: sfhk_run_opts, stream=None):
+    _check(_load().sfhk_propagate(ctx, ens, C.byref(opts), stream), "sfhk_propagate")
+
+
+def sfhk_propagate_batch(ctx, ens_list, opts: sfhk_run_opts, stream=None):
+    arr = (_vp * len(ens_list))(*[e.value if isinstance(e, _vp) else e for e in ens_list])
+    _check(_load().sfhk_propagate_batch(ctx, arr, len(ens_list), C.byref(opts), stream),
+           "sfhk_propagate_batch")
+
+
+def sfhk_dipole(ctx, ens, nt):
+    vz = np.zeros(nt)
+    t0, dt = C.c_double(), C.c_double()
+    _check(_load().sfhk_dipole(ctx, ens, _p(vz), nt, C.byref(t0), C.byref(dt)), "sfhk_dipole")
+    return vz
+
+
+def sfhk_dipole_device(ens):
+    p, nt = _vp(), C.c_size_t()
+    _check(_load().sfhk_dipole_device(ens, C.byref(p), C.byref(nt)), "sfhk_dipole_device")
+    return p.value, nt.value
+
+
+def sfhk_stats_get(ens):
+    s = sfhk_stats()
+    _check(_load().sfhk_stats_get(ens, C.byref(s)), "sfhk_stats_get")
+    return {f: getattr(s, f) for f, _ in sfhk_stats._fields_}
+
+
+def sfhk_final_state(ens, n):
+    out = np.zeros((FINAL_FIELDS, n))
+    _check(_load().sfhk_final_state(ens, _p(out), n), "sfhk_final_state")
+    return out
+
+
+def sfhk_spectrum(vz, dt, t_origin, tau_H, n_out):
+    """Host-buffer form: returns (omega, yield, phase)."""
+    vz = np.ascontiguousarray(vz, dtype=np.float64)
+    om, y, ph = np.zeros(n_out), np.zeros(n_out), np.zeros(n_out)
+    _check(_load().sfhk_spectrum(vz.ctypes.data, len(vz), dt, t_origin, tau_H, om.ctypes.data,
+                                 y.ctypes.data, ph.ctypes.data, n_out, 0, None), "sfhk_spectrum")
+    return om, y, ph
+
+
+def sfhk_spectrum_device(vz_ptr, nt, dt, t_origin, tau_H, om_ptr, y_ptr, ph_ptr, n_out,
+                         stream=None):
+    """Device-buffer form (raw device pointers, asynchronous on `stream`)."""
+    _check(_load().sfhk_spectrum(vz_ptr, nt, dt, t_origin, tau_H, om_ptr, y_ptr, ph_ptr, n_out, 1,
+                                 stream), "sfhk_spectrum")
+
+
+EXPORTED = [
+    "sfhk_create", "sfhk_destroy", "sfhk_mem_used", "sfhk_create_target", "sfhk_destroy_target",
+    "sfhk_set_pulse", "sfhk_destroy_pulse", "sfhk_pulse_grid", "sfhk_sample_initial",
+    "sfhk_load_ensemble", "sfhk_ensemble_read", "sfhk_destroy_ensemble", "sfhk_propagate",
+    "sfhk_propagate_batch", "sfhk_dipole", "sfhk_dipole_device", "sfhk_stats_get",
+    "sfhk_final_state", "sfhk_spectrum", "sfhk_strerror", "sfhk_sample_into",
+    "sfhk_launch_count",
+]
