@@ -124,7 +124,8 @@ def oracle_sample_run(n_per_angle, angles, seed_base=0):
     steps = 0
     for k, ang in enumerate(angles):
         soa, _, _ = O.sample(t, p, W.fixed(ang), seed=seed_base, instance=k, n=n_per_angle)
-        vz, fin, _ = O.propagate(t, p, soa, W.GAMMA, cutoff=W.CUTOFF, want_final=False)
+        vz, fin, _ = O.propagate(t, p, soa, W.GAMMA, cutoff=W.CUTOFF, want_final=False,
+                                 stab_cutoff=W.STAB_CUTOFF)
         O.spectrum(vz, d["dt"], d["t_origin"], 0.5 * d["Tp"], d["nt"] // 2)
         steps += int(np.sum(d["nt"] - 1 - soa[0]))
     return time.perf_counter() - t0, steps
@@ -225,7 +226,7 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    mixed = S.run_opts(S.SFHK_MIXED, cfg["gamma"], W.CUTOFF)
+    mixed = S.run_opts(S.SFHK_MIXED, cfg["gamma"], W.CUTOFF, stab_cutoff=W.STAB_CUTOFF)
     for w in range(args.warmup):
         step(mixed, w)
     barrier()
@@ -292,7 +293,7 @@ def run_ours(args):
     # the plain FP64 GPU path on the same workload, and the dipole difference
     fp64 = None
     if not args.no_fp64:
-        o64 = S.run_opts(S.SFHK_FP64, cfg["gamma"], W.CUTOFF)
+        o64 = S.run_opts(S.SFHK_FP64, cfg["gamma"], W.CUTOFF, stab_cutoff=W.STAB_CUTOFF)
         step(o64, 0)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -323,7 +324,7 @@ def run_ours(args):
                 "config": {"workload": cfg["name"], "target": cfg["target"],
                            "angles_deg": list(angles), "n_traj_per_angle": n,
                            "nt": nt, "dt": dt, "gamma": cfg["gamma"],
-                           "prefactor_cutoff": W.CUTOFF,
+                           "prefactor_cutoff": W.CUTOFF, "stability_cutoff": W.STAB_CUTOFF,
                            "traj_steps_per_step": traj_steps,
                            "l2": "inputs larger than L2 (trajectory SoA 3 x 96 MB)",
                            "parallelism": f"replicas x{world}"},
@@ -332,7 +333,8 @@ def run_ours(args):
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "fp64_path": fp64, "gpu_launches": launches // args.steps,
                 "clocks": clk,
-                "filtered_frac": sum(s["n_filtered"] for s in st) / (len(angles) * n)}
+                "filtered_frac": sum(s["n_filtered"] + s["n_unstable"] for s in st)
+                / (len(angles) * n)}
         print(json.dumps(line), flush=True)
     for e in ens:
         S.sfhk_destroy_ensemble(e)

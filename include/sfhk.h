@@ -113,6 +113,11 @@ typedef struct {
  *   dump_final       keep each trajectory's final state for sfhk_final_state.
  *   block_threads,   launch shape; 0 = the autotuned choice.
  *   blocks_per_sm
+ *   stability_cutoff 0 = off; else a trajectory stops contributing from the
+ *                    first step at which the largest element of its
+ *                    stability matrix exceeds the cutoff (chaotic
+ *                    trajectories; the paper is silent).
+ * The per-step checks run in the order: finiteness, prefactor, stability.
  */
 typedef struct {
     int precision;
@@ -121,6 +126,7 @@ typedef struct {
     int dump_final;
     int block_threads;
     int blocks_per_sm;
+    double stability_cutoff;
 } sfhk_run_opts;
 
 /* Per-ensemble counters of the last propagation. */
@@ -129,6 +135,7 @@ typedef struct {
     uint64_t n_invalid;       /* saddle without root: weight 0                */
     uint64_t n_filtered;      /* stopped by the prefactor filter              */
     uint64_t n_nonfinite;     /* stopped on a non-finite state or prefactor   */
+    uint64_t n_unstable;      /* stopped by the stability filter              */
     uint64_t traj_steps;      /* RK4 steps actually integrated                */
     int nt;                   /* time-grid length                             */
     float kernel_ms;          /* duration of the propagation kernel (events)  */
@@ -228,7 +235,7 @@ SFHK_API int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out);
 /* Final per-trajectory state of the last propagation run with dump_final,
  * 47 x n_traj doubles, field-major: q[3] p[3] M[36] (6x6 row-major,
  * M_ab = d a_t / d b_0 for (q,p)) S C_re C_im branch_sign status
- * (0 ok, 1 filtered, 2 non-finite).  For a stopped
+ * (0 ok, 1 prefactor-filtered, 2 non-finite, 3 stability-filtered).  For a stopped
  * trajectory the state is the one at the step where it stopped.  Synchronous.
  * Errors: SFHK_E_INVAL (no dump taken). */
 SFHK_API int sfhk_final_state(sfhk_ensemble* e, double* host, uint64_t n_traj);

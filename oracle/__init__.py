@@ -103,7 +103,8 @@ def lib():
                                 _dp, _dp]
         L.or_sample.restype = C.c_int
         L.or_propagate.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
-                                   C.c_double, _dp, C.c_uint64, C.c_double, _dp, _dp, C.c_int]
+                                   C.c_double, C.c_double, _dp, C.c_uint64, C.c_double, _dp, _dp,
+                                   C.c_int]
         L.or_propagate.restype = C.c_int
         L.or_spectrum.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                                   _dp, _dp, _dp, _dp, _dp]
@@ -260,14 +261,15 @@ def sample(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance=0, j_begin=0, n
     return soa, aux, bad
 
 
-def propagate(t, p, soa, gamma, cutoff=0.0, n_norm=0.0, want_final=False, n_threads=0):
+def propagate(t, p, soa, gamma, cutoff=0.0, n_norm=0.0, want_final=False, n_threads=0,
+              stab_cutoff=0.0):
     soa = np.ascontiguousarray(soa, dtype=np.float64)
     n = soa.shape[1]
     nt = pulse_derived(p)["nt"]
     vz = np.zeros(nt)
     fin = np.zeros((NFINAL, n)) if want_final else None
     bad = lib().or_propagate(C.byref(target_in(t)), C.byref(pulse_in(p)), gamma, cutoff,
-                             _p(soa), n, float(n_norm), _p(vz),
+                             float(stab_cutoff), _p(soa), n, float(n_norm), _p(vz),
                              _p(fin) if fin is not None else None, n_threads)
     return vz, fin, bad
 

@@ -703,16 +703,20 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
 /* bra <psi0 e^{i Ip t}| conjugates to e^{-i Ip t}.  Each trajectory     */
 /* starts at grid point n0 with C = 1, S = 0, M = identity, contributes  */
 /* at t_{n0}, then alternates one RK4 step and one contribution up to     */
-/* t_{Nt-1}.  Optional prefactor filter (the paper is silent; default    */
-/* off): once |C| > cutoff the trajectory contributes nothing from that  */
-/* step on.  final_state (optional): per trajectory, field-major,        */
-/*   q[3] p[3] M[36] S C_re C_im status  (47 fields)                      */
-/* status: 0 ok, 1 filtered, 2 non-finite.                               */
+/* t_{Nt-1}.  Optional filters (the paper is silent; both default off):  */
+/* once |C| > cutoff (prefactor filter), or once the largest element of  */
+/* the stability matrix exceeds stab_cutoff (stability filter: a chaotic */
+/* trajectory), the trajectory contributes nothing from that step on.    */
+/* The checks run in this order after each step: finiteness, |C|, |M|.   */
+/* final_state (optional): per trajectory, field-major,                  */
+/*   q[3] p[3] M[36] S C_re C_im theta status  (47 fields)                */
+/* status: 0 ok, 1 prefactor-filtered, 2 non-finite, 3 stability-filtered.*/
 /* ------------------------------------------------------------------ */
 #define OR_NFINAL 47
 
 static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm,
-                          double gamma, double cutoff, const double* soa, uint64_t n,
+                          double gamma, double cutoff, double stab_cutoff,
+                          const double* soa, uint64_t n,
                           uint64_t j, double scale, double* vz, double* final_state)
 {
     int n0 = (int)soa[j];
@@ -742,6 +746,11 @@ static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm
         for (int a = 0; a < OR_NY; ++a) if (!isfinite(y[a])) finite = 0;
         if (!finite) { status = 2; break; }
         if (cutoff > 0.0 && cabs(C) > cutoff) { status = 1; break; }
+        if (stab_cutoff > 0.0) {
+            double mmax = 0.0;
+            for (int a = 0; a < 36; ++a) if (fabs(y[6 + a]) > mmax) mmax = fabs(y[6 + a]);
+            if (mmax > stab_cutoff) { status = 3; break; }
+        }
         cplx R = recomb(T, Nnorm, nhat, y, y + 3, gamma);
         cplx X = w * C * cexp(I * (y[42] - T->Ip * t)) * R;
         vz[m] += -2.0 * scale * creal(X);
@@ -758,9 +767,9 @@ static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm
 
 /* vz_out[nt] receives the dipole; n_norm is N of the 1/N normalisation
  * (0 -> n).  n_threads <= 0 uses all cores.  Returns the count of
- * trajectories that were filtered or non-finite.                        */
+ * trajectories that were filtered (either filter) or non-finite.        */
 int or_propagate(const or_target_in* T, const or_pulse_in* Pin, double gamma, double cutoff,
-                 const double* soa, uint64_t n, double n_norm, double* vz_out,
+                 double stab_cutoff, const double* soa, uint64_t n, double n_norm, double* vz_out,
                  double* final_state, int n_threads)
 {
     or_pulse P = or_make_pulse(Pin);
@@ -780,7 +789,7 @@ int or_propagate(const or_target_in* T, const or_pulse_in* Pin, double gamma, do
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        propagate_one(T, &P, Nnorm, gamma, cutoff, soa, n, (uint64_t)j, scale,
+        propagate_one(T, &P, Nnorm, gamma, cutoff, stab_cutoff, soa, n, (uint64_t)j, scale,
                       part + (size_t)tid * P.nt, final_state);
     }
     for (int t = 0; t < nthr; ++t)

@@ -109,7 +109,7 @@ int ensemble_alloc(sfhk_ensemble* e, long long n, int nt)
     if ((rc = c->alloc(e->ph, sizeof(double2) * nt))) return rc;
     if ((rc = c->alloc(e->phf, sizeof(float2) * nt))) return rc;
     if ((rc = c->alloc(e->vz, sizeof(double) * nt))) return rc;
-    if ((rc = c->alloc(e->counters, sizeof(unsigned long long) * 4))) return rc;
+    if ((rc = c->alloc(e->counters, sizeof(unsigned long long) * 8))) return rc;
     if ((rc = c->alloc(e->cdf, sizeof(double) * nt))) return rc;
     if ((rc = c->alloc(e->hist, sizeof(int) * nt))) return rc;
     if ((rc = c->alloc(e->inst, sizeof(DevInstance)))) return rc;
@@ -170,6 +170,7 @@ DevInstance make_instance(sfhk_ensemble* e, const sfhk_run_opts& o)
     I.gamma = o.gamma;
     I.inv_gamma = 1.0 / o.gamma;
     I.cutoff2 = o.prefactor_cutoff > 0.0 ? o.prefactor_cutoff * o.prefactor_cutoff : 0.0;
+    I.stab_cut = o.stability_cutoff > 0.0 ? o.stability_cutoff : 0.0;
     return I;
 }
 
@@ -178,7 +179,7 @@ int check_opts(const sfhk_run_opts* o)
     if (!o) return SFHK_E_INVAL;
     if (o->precision != SFHK_FP64 && o->precision != SFHK_MIXED) return SFHK_E_INVAL;
     if (!(o->gamma > 0.0) || !std::isfinite(o->gamma)) return SFHK_E_INVAL;
-    if (o->prefactor_cutoff < 0.0) return SFHK_E_INVAL;
+    if (o->prefactor_cutoff < 0.0 || o->stability_cutoff < 0.0) return SFHK_E_INVAL;
     if (o->block_threads < 0 || o->block_threads > 128 || o->block_threads % 32) return SFHK_E_INVAL;
     if (o->blocks_per_sm < 0) return SFHK_E_INVAL;
     return SFHK_OK;
@@ -194,6 +195,8 @@ int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s)
     }
     SFHK_CUDA_TRY(cudaMemsetAsync(e->vz.p, 0, sizeof(double) * e->pulse->nt, s));
     SFHK_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(unsigned long long) * 3, s));
+    SFHK_CUDA_TRY(cudaMemsetAsync((unsigned long long*)e->counters.p + 4, 0,
+                                  sizeof(unsigned long long), s));
     e->dumped = o.dump_final != 0;
     return SFHK_OK;
 }
@@ -390,7 +393,7 @@ int sfhk_sample_initial(sfhk_ctx* c, const sfhk_target* t, const sfhk_pulse* p,
     }
     cudaStream_t s = as_stream(stream);
     unsigned long long* cnt = (unsigned long long*)e->counters.p;
-    if (cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4, s) != cudaSuccess) rc = SFHK_E_CUDA;
+    if (cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 8, s) != cudaSuccess) rc = SFHK_E_CUDA;
     if (!rc) rc = launch_adk_cdf(*p, t->desc.Ip, (double*)e->cdf.p, s);
     if (!rc)
         rc = launch_sample(*t, *p, *al, e->n, seed, instance, (const double*)e->cdf.p,
@@ -463,7 +466,7 @@ int sfhk_load_ensemble(sfhk_ctx* c, const sfhk_target* t, const sfhk_pulse* p,
     }
     if (cudaMemcpy(e->soa.p, soa_host, sizeof(double) * kSoaFields * n, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
-        cudaMemset(e->counters.p, 0, sizeof(unsigned long long) * 4) != cudaSuccess)
+        cudaMemset(e->counters.p, 0, sizeof(unsigned long long) * 8) != cudaSuccess)
         rc = SFHK_E_CUDA;
     if (!rc) rc = launch_n0_from_soa((const double*)e->soa.p, n, (int*)e->n0.p, 0);
     if (!rc) rc = ensemble_finish(e, 0);
@@ -626,7 +629,7 @@ int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out)
     int rc = set_device(e->ctx->device);
     if (rc) return rc;
     std::memset(out, 0, sizeof *out);
-    unsigned long long h[4] = {0, 0, 0, 0};
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
     if (e->have_result) SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_done));
     SFHK_CUDA_TRY(cudaDeviceSynchronize());
     SFHK_CUDA_TRY(cudaMemcpy(h, e->counters.p, sizeof h, cudaMemcpyDeviceToHost));
@@ -635,6 +638,7 @@ int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out)
     out->n_nonfinite = h[1];
     out->traj_steps = h[2];
     out->n_invalid = h[3];
+    out->n_unstable = h[4];
     out->nt = e->pulse->nt;
     float ms = 0.0f;
     if (e->have_result && cudaEventElapsedTime(&ms, e->ev_start, e->ev_stop) == cudaSuccess)
@@ -672,13 +676,15 @@ int sfhk_spectrum(const double* vz, size_t nt, double dt, double t_origin, doubl
         cudaFreeAsync(tw, s);
         return rc;
     }
+    // layout: twiddle (double2, at the allocation's alignment) | windowed
+    // samples | dipole | omega | yield | phase
     void* buf = nullptr;
-    const size_t bytes = sizeof(double) * N + (sizeof(double2) + sizeof(double)) * N +
+    const size_t bytes = (sizeof(double2) + sizeof(double)) * N + sizeof(double) * N +
                          3 * sizeof(double) * K;
     SFHK_CUDA_TRY(cudaMallocAsync(&buf, bytes, s));
-    double* dvz = (double*)buf;
-    double2* tw = (double2*)(dvz + N);
-    double* om = (double*)((char*)tw + (sizeof(double2) + sizeof(double)) * N);
+    double2* tw = (double2*)buf;
+    double* dvz = (double*)(tw + N) + N;
+    double* om = dvz + N;
     double* yl = om + K;
     double* phs = yl + K;
     int rc = SFHK_OK;

@@ -172,16 +172,20 @@ struct PotConst {
     int kind, screened;
 };
 
-// V, force F = -grad V and Hessian at q (both centres, +-(R/2)n).
-template <typename R>
-__device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz, R& V, R& Fx,
-                                          R& Fy, R& Fz, Sym3<R>& H)
+// V, force F = -grad V and Hessian at q + l (both centres, +-(R/2)n).  l is
+// the low part of a two-float position (zero in FP64): it is added after the
+// centre is subtracted, so the distance to a nearby nucleus keeps the
+// position's full two-float precision.
+template <typename R, bool LO>
+__device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz, R lx, R ly,
+                                          R lz, R& V, R& Fx, R& Fy, R& Fz, Sym3<R>& H)
 {
     if (K.kind != 0) {            // harmonic test potential
-        V = R(0.5) * K.w2 * (qx * qx + qy * qy + qz * qz);
-        Fx = -K.w2 * qx;
-        Fy = -K.w2 * qy;
-        Fz = -K.w2 * qz;
+        const R x = LO ? qx + lx : qx, y = LO ? qy + ly : qy, z = LO ? qz + lz : qz;
+        V = R(0.5) * K.w2 * (x * x + y * y + z * z);
+        Fx = -K.w2 * x;
+        Fy = -K.w2 * y;
+        Fz = -K.w2 * z;
         H.xx = H.yy = H.zz = K.w2;
         H.xy = H.xz = H.yz = R(0);
         return;
@@ -190,9 +194,14 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz
     H.xx = H.yy = H.zz = H.xy = H.xz = H.yz = R(0);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        const R dx = c == 0 ? qx - K.cx : qx + K.cx;
-        const R dy = c == 0 ? qy - K.cy : qy + K.cy;
-        const R dz = c == 0 ? qz - K.cz : qz + K.cz;
+        R dx = c == 0 ? qx - K.cx : qx + K.cx;
+        R dy = c == 0 ? qy - K.cy : qy + K.cy;
+        R dz = c == 0 ? qz - K.cz : qz + K.cz;
+        if (LO) {
+            dx += lx;
+            dy += ly;
+            dz += lz;
+        }
         const R s2 = dx * dx + dy * dy + dz * dz + K.a2;
         const R u = rsqrt_t<R>(s2);
         const R u2 = u * u, u3 = u2 * u;

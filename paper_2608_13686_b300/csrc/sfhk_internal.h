@@ -51,13 +51,14 @@ struct DevInstance {
     const int* n0;         // per trajectory grid index of t0
     double* vz;            // Nt dipole accumulator
     double* dump;          // 47 x n or null
-    unsigned long long* counters;   // [filtered, nonfinite, steps]
+    unsigned long long* counters;   // [filtered, nonfinite, steps, invalid, unstable]
     long long n;
     int nt;
     double dt, t_origin;
     double scale;          // -2 / N
     double gamma, inv_gamma;
     double cutoff2;        // cutoff^2 on |det| (0 = off), |C|^2 = |det|
+    double stab_cut;       // cutoff on max |M_ij| (0 = off)
 };
 
 struct WorkItem {

@@ -132,6 +132,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     const R gam = R(I.gamma), igam = R(I.inv_gamma);
     const R wR = R(wr), wI = R(wi);
     const double cutoff2 = I.cutoff2;
+    const R stab = R(I.stab_cut);
 
     // ---- state
     R q[3], p[3], ql[3], pl[3];
@@ -152,7 +153,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         }
     R S = R(0), Sl = R(0);          // action (two-float in MIXED, Sl unused in FP64)
     C2<R> Cp = {R(1), R(0)};        // prefactor at the previous step
-    int status = 0;                 // 0 alive, 1 filtered, 2 non-finite
+    int status = 0;                 // 0 alive, 1 prefactor filter, 2 non-finite, 3 stability filter
     unsigned long long steps = 0;
 
     const R h = R(I.dt), h2 = R(0.5 * I.dt), h6 = R(I.dt / 6.0);
@@ -215,6 +216,14 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     } else if (cutoff2 > 0.0 &&
                                double(hypot_t<R>(det.x, det.y)) > cutoff2) {
                         status = 1;
+                    } else if (stab > R(0)) {
+                        R mx = R(0);
+#pragma unroll
+                        for (int c = 0; c < 6; ++c)
+#pragma unroll
+                            for (int r = 0; r < 3; ++r)
+                                mx = fmax(mx, fmax(fabs(Mq[c][r]), fabs(Mp[c][r])));
+                        if (mx > stab) status = 3;
                     }
                     Cp = C;
                 }
@@ -301,7 +310,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                 ++steps;
                 Sym3<R> H1, H2, H3, H4;
                 R V, F[3];
-                potential<R>(K, q[0], q[1], q[2], V, F[0], F[1], F[2], H1);
+                potential<R, MIXED>(K, q[0], q[1], q[2], ql[0], ql[1], ql[2], V, F[0], F[1], F[2], H1);
                 R k1p[3] = {F[0], F[1], F[2] - E1};
                 const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
                 R q2[3], p2[3];
@@ -310,7 +319,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     q2[a] = q[a] + h2 * p[a];
                     p2[a] = p[a] + h2 * k1p[a];
                 }
-                potential<R>(K, q2[0], q2[1], q2[2], V, F[0], F[1], F[2], H2);
+                potential<R, MIXED>(K, q2[0], q2[1], q2[2], ql[0], ql[1], ql[2], V, F[0], F[1], F[2], H2);
                 R k2p[3] = {F[0], F[1], F[2] - E2};
                 const R k2s = R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - q2[2] * E2;
                 R q3[3], p3[3];
@@ -319,7 +328,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     q3[a] = q[a] + h2 * p2[a];
                     p3[a] = p[a] + h2 * k2p[a];
                 }
-                potential<R>(K, q3[0], q3[1], q3[2], V, F[0], F[1], F[2], H3);
+                potential<R, MIXED>(K, q3[0], q3[1], q3[2], ql[0], ql[1], ql[2], V, F[0], F[1], F[2], H3);
                 R k3p[3] = {F[0], F[1], F[2] - E2};
                 const R k3s = R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - q3[2] * E2;
                 R q4[3], p4[3];
@@ -328,7 +337,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     q4[a] = q[a] + h * p3[a];
                     p4[a] = p[a] + h * k3p[a];
                 }
-                potential<R>(K, q4[0], q4[1], q4[2], V, F[0], F[1], F[2], H4);
+                potential<R, MIXED>(K, q4[0], q4[1], q4[2], ql[0], ql[1], ql[2], V, F[0], F[1], F[2], H4);
                 const R k4s = R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - q4[2] * E4;
                 const R dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
 #pragma unroll
@@ -389,12 +398,14 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     // ---- counters and optional final state
     const unsigned filt = __ballot_sync(kFull, has && status == 1);
     const unsigned nonf = __ballot_sync(kFull, has && status == 2);
+    const unsigned unst = __ballot_sync(kFull, has && status == 3);
     unsigned long long st = steps;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) st += __shfl_xor_sync(kFull, st, off);
     if (lane == 0) {
         if (filt) atomicAdd(&I.counters[0], (unsigned long long)__popc(filt));
         if (nonf) atomicAdd(&I.counters[1], (unsigned long long)__popc(nonf));
+        if (unst) atomicAdd(&I.counters[4], (unsigned long long)__popc(unst));
         atomicAdd(&I.counters[2], st);
     }
     if (I.dump != nullptr && has) {

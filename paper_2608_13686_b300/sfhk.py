@@ -50,12 +50,14 @@ class sfhk_align_desc(C.Structure):
 
 class sfhk_run_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("gamma", C.c_double), ("prefactor_cutoff", C.c_double),
-                ("dump_final", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int)]
+                ("dump_final", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
+                ("stability_cutoff", C.c_double)]
 
 
 class sfhk_stats(C.Structure):
     _fields_ = [("n_traj", C.c_uint64), ("n_invalid", C.c_uint64), ("n_filtered", C.c_uint64),
-                ("n_nonfinite", C.c_uint64), ("traj_steps", C.c_uint64), ("nt", C.c_int),
+                ("n_nonfinite", C.c_uint64), ("n_unstable", C.c_uint64),
+                ("traj_steps", C.c_uint64), ("nt", C.c_int),
                 ("kernel_ms", C.c_float)]
 
 
@@ -152,8 +154,9 @@ def align_desc(a) -> sfhk_align_desc:
 
 
 def run_opts(precision=SFHK_FP64, gamma=0.5, cutoff=0.0, dump=False, block_threads=0,
-             blocks_per_sm=0) -> sfhk_run_opts:
-    return sfhk_run_opts(precision, gamma, cutoff, int(dump), block_threads, blocks_per_sm)
+             blocks_per_sm=0, stab_cutoff=0.0) -> sfhk_run_opts:
+    return sfhk_run_opts(precision, gamma, cutoff, int(dump), block_threads, blocks_per_sm,
+                         stab_cutoff)
 
 
 # ------------------------------------------------------------------ C-ABI calls

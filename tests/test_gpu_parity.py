@@ -24,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 GAMMA = W.GAMMA
 CUT = W.CUTOFF
+STAB = W.STAB_CUTOFF
 
 
 @pytest.fixture(scope="module")
@@ -84,10 +85,10 @@ def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
 
 
 # ------------------------------------------------------------------ propagation
-def _run(S, ctx, t, p, soa, precision, cutoff=CUT, dump=True, n_norm=0.0):
+def _run(S, ctx, t, p, soa, precision, cutoff=CUT, dump=True, n_norm=0.0, stab=STAB):
     th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, p)
     e = S.sfhk_load_ensemble(ctx, th, ph, soa, n_norm)
-    S.sfhk_propagate(ctx, e, S.run_opts(precision, GAMMA, cutoff, dump))
+    S.sfhk_propagate(ctx, e, S.run_opts(precision, GAMMA, cutoff, dump, stab_cutoff=stab))
     nt = S.sfhk_pulse_grid(ph)["nt"]
     vz = S.sfhk_dipole(ctx, e, nt)
     fin = S.sfhk_final_state(e, soa.shape[1]) if dump else None
@@ -122,22 +123,24 @@ def _compare_final(fin_g, fin_o, tol):
 def test_fp64_propagation_per_trajectory_and_dipole(S, ctx, name, pulse, align, n):
     t = W.TARGETS[name]
     soa, _, _ = O.sample(t, pulse, align, seed=11, n=n)
-    vz_o, fin_o, bad_o = O.propagate(t, pulse, soa, GAMMA, cutoff=CUT, want_final=True)
+    vz_o, fin_o, bad_o = O.propagate(t, pulse, soa, GAMMA, cutoff=CUT, want_final=True,
+                                         stab_cutoff=STAB)
     vz_g, fin_g, st = _run(S, ctx, t, pulse, soa, S.SFHK_FP64)
     frac = _compare_final(fin_g, fin_o, 1e-10)
     assert frac > 0.9
-    assert st["n_filtered"] + st["n_nonfinite"] == bad_o
+    assert st["n_filtered"] + st["n_nonfinite"] + st["n_unstable"] == bad_o
     assert _rel_l2(vz_g, vz_o) <= 1e-9
 
 
 @pytest.mark.parametrize("name,pulse,align,n", [
     ("H2", W.PULSE_800, W.fixed(0.0), 1000),
+    ("H2", W.PULSE_800, W.fixed(45.0), 1000),
     ("N2", W.PULSE_1200, W.COS2, 600),
 ])
 def test_mixed_precision_dipole(S, ctx, name, pulse, align, n):
     t = W.TARGETS[name]
     soa, _, _ = O.sample(t, pulse, align, seed=12, n=n)
-    vz_o, _, _ = O.propagate(t, pulse, soa, GAMMA, cutoff=CUT)
+    vz_o, _, _ = O.propagate(t, pulse, soa, GAMMA, cutoff=CUT, stab_cutoff=STAB)
     vz_g, _, _ = _run(S, ctx, t, pulse, soa, S.SFHK_MIXED, dump=False)
     err = _rel_l2(vz_g, vz_o)
     print(f"mixed rel-L2 {name}: {err:.3e}")
@@ -150,7 +153,7 @@ def test_prefactor_filter_off_matches(S, ctx):
     t = W.TARGETS["H2"]
     soa, _, _ = O.sample(t, W.PULSE_800, W.fixed(45.0), seed=3, n=200)
     vz_o, fin_o, _ = O.propagate(t, W.PULSE_800, soa, GAMMA, cutoff=0.0, want_final=True)
-    vz_g, fin_g, _ = _run(S, ctx, t, W.PULSE_800, soa, S.SFHK_FP64, cutoff=0.0)
+    vz_g, fin_g, _ = _run(S, ctx, t, W.PULSE_800, soa, S.SFHK_FP64, cutoff=0.0, stab=0.0)
     M = np.abs(fin_o[6:42]).max(axis=0)
     tame = M < 1e4
     C_g, C_o = fin_g[43] + 1j * fin_g[44], fin_o[43] + 1j * fin_o[44]
@@ -166,11 +169,12 @@ def test_single_trajectory_and_last_grid_point(S, ctx):
     soa[0, 2] = 0               # born at the first grid point: the whole pulse
     for n in (1, 3):
         s = np.ascontiguousarray(soa[:, :n])
-        vz_o, fin_o, _ = O.propagate(t, p, s, GAMMA, cutoff=CUT, want_final=True)
+        vz_o, fin_o, _ = O.propagate(t, p, s, GAMMA, cutoff=CUT, want_final=True,
+                                      stab_cutoff=STAB)
         vz_g, fin_g, st = _run(S, ctx, t, p, s, S.SFHK_FP64)
         assert _rel_l2(vz_g, vz_o) <= 1e-9
         _compare_final(fin_g, fin_o, 1e-10)
-    if st["n_filtered"] == 0 and st["n_nonfinite"] == 0:
+    if st["n_filtered"] == 0 and st["n_nonfinite"] == 0 and st["n_unstable"] == 0:
         assert st["traj_steps"] == (nt - 1 - int(soa[0, 0])) + 0 + (nt - 1)
 
 
@@ -246,7 +250,7 @@ def test_batch_equals_separate(S, ctx):
         ens.append(S.sfhk_sample_initial(ctx, th, ph, al, n, seed, seed))
         nts.append(S.sfhk_pulse_grid(ph)["nt"])
     for prec in (S.SFHK_FP64, S.SFHK_MIXED):
-        opts = S.run_opts(prec, GAMMA, CUT)
+        opts = S.run_opts(prec, GAMMA, CUT, stab_cutoff=STAB)
         alone = []
         for e, nt in zip(ens, nts):
             S.sfhk_propagate(ctx, e, opts)
