@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--block", type=int, default=0, help="pin the integrator's block size")
+    ap.add_argument("--kernel-variant", type=int, default=0, help="pin the register-cap variant")
     return ap.parse_args()
 
 
@@ -226,7 +229,13 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    mixed = S.run_opts(S.SFHK_MIXED, cfg["gamma"], W.CUTOFF, stab_cutoff=W.STAB_CUTOFF)
+    mixed = S.run_opts(S.SFHK_MIXED, cfg["gamma"], W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                       block_threads=args.block, kernel_variant=args.kernel_variant)
+    # launch shape (block size x register-cap variant) chosen by the autotuner
+    # on the first angle's ensemble, untimed
+    tuned = None
+    if not args.no_tune and not (args.block and args.kernel_variant):
+        tuned = S.sfhk_autotune(ctx, ens[0], mixed, max_items=8192)
     for w in range(args.warmup):
         step(mixed, w)
     barrier()
@@ -332,6 +341,7 @@ def run_ours(args):
                 "ms_per_step_all": ms_steps,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "fp64_path": fp64, "gpu_launches": launches // args.steps,
+                "autotuned": tuned,
                 "clocks": clk,
                 "filtered_frac": sum(s["n_filtered"] + s["n_unstable"] for s in st)
                 / (len(angles) * n)}

@@ -111,8 +111,9 @@ typedef struct {
  *   prefactor_cutoff 0 = off; else a trajectory stops contributing from the
  *                    first step with |C| > cutoff (the paper is silent).
  *   dump_final       keep each trajectory's final state for sfhk_final_state.
- *   block_threads,   launch shape; 0 = the autotuned choice.
- *   blocks_per_sm
+ *   block_threads    threads per block of the integrator (32, 64 or 128);
+ *                    0 = the context's tuned choice (see sfhk_autotune).
+ *   blocks_per_sm    resident blocks per SM to launch; 0 = as many as fit.
  *   stability_cutoff 0 = off; else a trajectory stops contributing from the
  *                    first step at which the largest element of its
  *                    stability matrix exceeds the cutoff (chaotic
@@ -127,6 +128,9 @@ typedef struct {
     int block_threads;
     int blocks_per_sm;
     double stability_cutoff;
+    int kernel_variant;               /* register-cap variant 1..5 (no cap, then at
+                                         least 2..5 blocks of 128 threads per SM);
+                                         0 = the context's tuned choice */
 } sfhk_run_opts;
 
 /* Per-ensemble counters of the last propagation. */
@@ -221,6 +225,18 @@ SFHK_API int sfhk_propagate(sfhk_ctx* ctx, sfhk_ensemble* e, const sfhk_run_opts
  * own dipole.  Asynchronous. */
 SFHK_API int sfhk_propagate_batch(sfhk_ctx* ctx, sfhk_ensemble* const* ens, int n_ens,
                          const sfhk_run_opts* opts, void* stream);
+
+/* Autotuner of the integrator's launch shape (block size x register-cap
+ * variant), run on the caller's ensemble: every candidate propagates the
+ * first `max_items` work items of 32 trajectories (0 = all) twice, the second
+ * launch is timed with CUDA events, and the fastest becomes the context's
+ * default for `opts->precision` (used whenever block_threads or
+ * kernel_variant is 0).  choice (may be NULL) receives
+ * {block_threads, kernel_variant, min blocks per SM of that variant}.
+ * Synchronous, on the legacy default stream; the ensemble's dipole is
+ * overwritten.  Not a method step: launch configuration only. */
+SFHK_API int sfhk_autotune(sfhk_ctx* ctx, sfhk_ensemble* e, const sfhk_run_opts* opts,
+                           int max_items, int* choice);
 
 /* Dipole v_z(t_n), n = 0..Nt-1, of the last propagation, copied to the host
  * after waiting for it.  nt must equal the pulse's Nt.  Also returns the

@@ -182,6 +182,7 @@ int check_opts(const sfhk_run_opts* o)
     if (o->prefactor_cutoff < 0.0 || o->stability_cutoff < 0.0) return SFHK_E_INVAL;
     if (o->block_threads < 0 || o->block_threads > 128 || o->block_threads % 32) return SFHK_E_INVAL;
     if (o->blocks_per_sm < 0) return SFHK_E_INVAL;
+    if (o->kernel_variant < 0 || o->kernel_variant > kPropVariants) return SFHK_E_INVAL;
     return SFHK_OK;
 }
 
@@ -201,10 +202,11 @@ int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s)
     return SFHK_OK;
 }
 
-void shape(Ctx* c, const sfhk_run_opts& o, int* bt, int* bps)
+void shape(Ctx* c, const sfhk_run_opts& o, int* bt, int* var, int* bps)
 {
     *bt = o.block_threads > 0 ? o.block_threads : c->tuned[o.precision][0];
-    *bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : c->tuned[o.precision][1];
+    *var = o.kernel_variant > 0 ? o.kernel_variant - 1 : c->tuned[o.precision][1];
+    *bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : c->tuned[o.precision][2];
 }
 
 }  // namespace
@@ -509,11 +511,12 @@ int sfhk_propagate(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, void* 
     if ((rc = prepare_outputs(e, *o, s))) return rc;
     const DevInstance I = make_instance(e, *o);
     SFHK_CUDA_TRY(cudaMemcpyAsync(e->inst.p, &I, sizeof I, cudaMemcpyHostToDevice, s));
-    int bt, bps;
-    shape(c, *o, &bt, &bps);
+    int bt, var, bps;
+    shape(c, *o, &bt, &var, &bps);
     SFHK_CUDA_TRY(cudaEventRecord(e->ev_start, s));
-    rc = launch_propagate(o->precision, (const DevInstance*)e->inst.p, (const WorkItem*)e->items.p,
-                          e->n_items, (unsigned int*)e->qctr.p, bt, bps, c->sm_count, s);
+    rc = launch_propagate(o->precision, var, (const DevInstance*)e->inst.p,
+                          (const WorkItem*)e->items.p, e->n_items, (unsigned int*)e->qctr.p, bt,
+                          bps, c->sm_count, s);
     if (rc) return rc;
     SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, s));
     SFHK_CUDA_TRY(cudaEventRecord(e->ev_done, s));
@@ -585,13 +588,13 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
     if (!rc)
         rc = launch_sort_items(d_items, (int)total_items, d_nt, d_sorted, d_keys, d_perm, d_hist,
                                max_nt, s);
-    int bt, bps;
-    shape(c, *o, &bt, &bps);
+    int bt, var, bps;
+    shape(c, *o, &bt, &var, &bps);
     for (int i = 0; i < n_ens && !rc; ++i)
         if (cudaEventRecord(ens[i]->ev_start, s) != cudaSuccess) rc = SFHK_E_CUDA;
     if (!rc)
-        rc = launch_propagate(o->precision, d_inst, d_sorted, (int)total_items, d_ctr, bt, bps,
-                              c->sm_count, s);
+        rc = launch_propagate(o->precision, var, d_inst, d_sorted, (int)total_items, d_ctr, bt,
+                              bps, c->sm_count, s);
     for (int i = 0; i < n_ens && !rc; ++i) {
         if (cudaEventRecord(ens[i]->ev_stop, s) != cudaSuccess ||
             cudaEventRecord(ens[i]->ev_done, s) != cudaSuccess)
@@ -600,6 +603,53 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
     }
     cudaFreeAsync(scratch, s);
     return rc;
+}
+
+int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max_items,
+                  int* choice)
+{
+    if (!c || !e || e->ctx != c) return SFHK_E_INVAL;
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if ((rc = set_device(c->device))) return rc;
+    const int items = (max_items > 0 && max_items < e->n_items) ? max_items : e->n_items;
+    sfhk_run_opts oo = *o;
+    oo.dump_final = 0;
+    if ((rc = prepare_outputs(e, oo, 0))) return rc;
+    const DevInstance I = make_instance(e, oo);
+    SFHK_CUDA_TRY(cudaMemcpy(e->inst.p, &I, sizeof I, cudaMemcpyHostToDevice));
+    const int blocks[3] = {32, 64, 128};
+    float best = 3.4e38f;
+    int bb = c->tuned[o->precision][0], bv = c->tuned[o->precision][1];
+    for (int v = 0; v < kPropVariants; ++v)
+        for (int b : blocks) {
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {      // first launch warms up
+                SFHK_CUDA_TRY(cudaEventRecord(e->ev_start, 0));
+                rc = launch_propagate(o->precision, v, (const DevInstance*)e->inst.p,
+                                      (const WorkItem*)e->items.p, items,
+                                      (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0);
+                if (rc) return rc;
+                SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, 0));
+                SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_stop));
+                SFHK_CUDA_TRY(cudaEventElapsedTime(&ms, e->ev_start, e->ev_stop));
+            }
+            if (ms < best) {
+                best = ms;
+                bb = b;
+                bv = v;
+            }
+        }
+    c->tuned[o->precision][0] = bb;
+    c->tuned[o->precision][1] = bv;
+    c->tuned[o->precision][2] = 0;
+    e->have_result = false;
+    if (choice) {
+        choice[0] = bb;
+        choice[1] = bv + 1;
+        choice[2] = propagate_variant_minb(bv);
+    }
+    return SFHK_OK;
 }
 
 int sfhk_dipole(sfhk_ctx* c, sfhk_ensemble* e, double* vz_host, size_t nt, double* t_origin,

@@ -82,8 +82,9 @@ struct Ctx {
     size_t budget = 0;
     std::atomic<size_t> used{0};
     std::mutex mu;
-    // tuned launch shape per precision: [block_threads, blocks_per_sm]
-    int tuned[2][2] = {{128, 0}, {128, 0}};
+    // tuned launch shape per precision: [block_threads, variant, blocks_per_sm]
+    // (before tuning: 128 threads, the variant capped at 3 blocks per SM)
+    int tuned[2][3] = {{128, 2, 0}, {128, 2, 0}};
     int alloc(DeviceBuf& b, size_t bytes);
     void release(DeviceBuf& b);
 };
@@ -139,10 +140,12 @@ int launch_sort_items(const WorkItem* in, int n_items, const int* inst_nt, WorkI
                       int* scratch_keys, int* scratch_perm, int* scratch_hist, int K,
                       cudaStream_t s);
 // propagate (sfhk_propagate.cu)
-int launch_propagate(int precision, const DevInstance* insts, const WorkItem* items,
-                     int n_items, unsigned int* item_counter, int block_threads,
-                     int blocks_per_sm, int sm_count, cudaStream_t s);
-int propagate_occupancy(int precision, int block_threads, int* blocks_per_sm);
+constexpr int kPropVariants = 5;   // register-cap variants of the integrator
+int launch_propagate(int precision, int variant_index, const DevInstance* insts,
+                     const WorkItem* items, int n_items, unsigned int* item_counter,
+                     int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s);
+int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm);
+int propagate_variant_minb(int variant_index);
 // spectrum (sfhk_spectrum.cu)
 int launch_spectrum(const double* vz, int nt, double dt, double t_origin, double tau_H,
                     double* omega, double* yield, double* phase, int n_out, double2* twiddle,

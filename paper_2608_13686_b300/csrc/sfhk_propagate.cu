@@ -66,18 +66,59 @@ __device__ __forceinline__ float sqrt_t<float>(float a) { return sqrtf(a); }
 template <>
 __device__ __forceinline__ double sqrt_t<double>(double a) { return sqrt(a); }
 
-// principal square root of a complex number
+// principal square root of z, given r = |z|:  sqrt(z) = (t, y/(2t)) with
+// t = sqrt((r + x)/2) for x >= 0, and the mirrored form for x < 0.
 template <typename R>
-__device__ __forceinline__ C2<R> csqrt_p(C2<R> z)
+__device__ __forceinline__ C2<R> csqrt_p(C2<R> z, R r)
 {
-    const R r = hypot_t<R>(z.x, z.y);
     if (r == R(0)) return {R(0), R(0)};
-    if (z.x >= R(0)) {
-        const R t = sqrt_t<R>(R(0.5) * (r + z.x));
-        return {t, R(0.5) * z.y / t};
+    const R a = R(0.5) * (r + fabs(z.x));
+    const R ra = rsqrt_t<R>(a);
+    const R t = a * ra;                      // sqrt(a)
+    const R u = R(0.5) * fabs(z.y) * ra;     // |y| / (2 sqrt(a))
+    if (z.x >= R(0)) return {t, copysign(u, z.y)};
+    return {u, copysign(t, z.y)};
+}
+
+// max(a, b, c) in one instruction on sm_100+
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ double fmax3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+
+// largest |element| of the stability matrix
+template <typename R>
+__device__ __forceinline__ R max_abs_M(const R Mq[6][3], const R Mp[6][3])
+{
+    R m[12];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        m[2 * c] = fmax3(fabs(Mq[c][0]), fabs(Mq[c][1]), fabs(Mq[c][2]));
+        m[2 * c + 1] = fmax3(fabs(Mp[c][0]), fabs(Mp[c][1]), fabs(Mp[c][2]));
     }
-    const R t = sqrt_t<R>(R(0.5) * (r - z.x));
-    return {R(0.5) * fabs(z.y) / t, copysign(t, z.y)};
+    const R a = fmax3(m[0], m[1], m[2]), b = fmax3(m[3], m[4], m[5]);
+    const R c = fmax3(m[6], m[7], m[8]), d = fmax3(m[9], m[10], m[11]);
+    return fmax3(a, b, fmax(c, d));
+}
+
+// (hi, lo) += x with Dekker's FastTwoSum; lo is left unnormalised (it only
+// collects rounding errors, a few ulp of hi per chunk) and folded back by
+// renorm() once per chunk.
+__device__ __forceinline__ void acc2(float& hi, float& lo, float x)
+{
+    const float s = __fadd_rn(hi, x);
+    const float e = __fsub_rn(x, __fsub_rn(s, hi));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+__device__ __forceinline__ void renorm(float& hi, float& lo)
+{
+    const float s = __fadd_rn(hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(s, hi));
+    hi = s;
 }
 
 // y (3-vector) = -H x
@@ -131,8 +172,16 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     const int n_prim = I.tgt.n_prim;
     const R gam = R(I.gamma), igam = R(I.inv_gamma);
     const R wR = R(wr), wI = R(wi);
-    const double cutoff2 = I.cutoff2;
+    const R cut2 = R(I.cutoff2);            // |det| = |C|^2 threshold (0 = off)
     const R stab = R(I.stab_cut);
+    // far-field bound of the recombination exponent over the primitives:
+    // K1 |d|^2 + K2 |p|^2 <= K1max |d|^2 + K2max |p|^2 (all K1, K2 < 0)
+    R K1max = R(-1e30), K2max = R(-1e30);
+    for (int k = 0; k < n_prim; ++k) {
+        K1max = fmax(K1max, R(I.rec.K1[k]));
+        K2max = fmax(K2max, R(I.rec.K2[k]));
+    }
+    constexpr R kSkip = MIXED ? R(-80) : R(-200);
 
     // ---- state
     R q[3], p[3], ql[3], pl[3];
@@ -177,7 +226,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             const double2 t = I.ph[min(nl, nt - 1)];
             phl = {t.x, t.y};
         }
-        double bin = 0.0;
+        R bin = R(0), binlo = R(0);    // this lane's step of the chunk (two-float in MIXED)
         const int send = min(kWarp, nt - nb);
         for (int s = 0; s < send; ++s) {
             const int nn = nb + s;
@@ -203,27 +252,21 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     const C2<R> c1 = cm(B[1], {m2.x - m3.x, m2.y - m3.y});
                     const C2<R> c2 = cm(B[2], {m4.x - m5.x, m4.y - m5.y});
                     const C2<R> det = {c0.x - c1.x + c2.x, c0.y - c1.y + c2.y};
-                    C = csqrt_p(det);
+                    const R rdet = hypot_t<R>(det.x, det.y);
+                    C = csqrt_p(det, rdet);
                     if (C.x * Cp.x + C.y * Cp.y < R(0)) {
                         C.x = -C.x;
                         C.y = -C.y;
                     }
                     const bool fin = isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) &&
                                      isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) &&
-                                     isfinite(S) && isfinite(det.x) && isfinite(det.y);
+                                     isfinite(S) && isfinite(rdet);
                     if (!fin) {
                         status = 2;
-                    } else if (cutoff2 > 0.0 &&
-                               double(hypot_t<R>(det.x, det.y)) > cutoff2) {
+                    } else if (cut2 > R(0) && rdet > cut2) {
                         status = 1;
-                    } else if (stab > R(0)) {
-                        R mx = R(0);
-#pragma unroll
-                        for (int c = 0; c < 6; ++c)
-#pragma unroll
-                            for (int r = 0; r < 3; ++r)
-                                mx = fmax(mx, fmax(fabs(Mq[c][r]), fabs(Mp[c][r])));
-                        if (mx > stab) status = 3;
+                    } else if (stab > R(0) && max_abs_M(Mq, Mp) > stab) {
+                        status = 3;
                     }
                     Cp = C;
                 }
@@ -238,6 +281,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                         const R dy = c == 0 ? q[1] - K.cy : q[1] + K.cy;
                         const R dz = c == 0 ? q[2] - K.cz : q[2] + K.cz;
                         const R dd = dx * dx + dy * dy + dz * dz;
+                        if (K1max * dd + K2max * pp <= kSkip) continue;   // far from this centre
                         const R pdd = p[0] * dx + p[1] * dy + p[2] * dz;
 #pragma unroll 1
                         for (int k = 0; k < n_prim; ++k) {
@@ -250,7 +294,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                                 K3 = I.rec.K3[k]; K4 = I.rec.K4[k];
                             }
                             const R ex = K1 * dd + K2 * pp;
-                            if (ex > (MIXED ? R(-80) : R(-200))) {
+                            if (ex > kSkip) {
                                 const R mag = K4 * exp_t<R>(ex);
                                 R sn, cs;
                                 if constexpr (MIXED) __sincosf(K3 * pdd, &sn, &cs);
@@ -285,7 +329,6 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             }
             // ---- 3. warp sum (skipped when no lane contributes)
             if (__any_sync(kFull, x != R(0))) {
-                double tot;
                 if constexpr (MIXED) {
                     float sv = x, ev = 0.0f;
 #pragma unroll
@@ -296,14 +339,16 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                         two_sum(sv, so, sv, t);
                         ev = ev + eo + t;
                     }
-                    tot = double(sv) + double(ev);
+                    if (lane == s) {
+                        bin = sv;
+                        binlo = ev;
+                    }
                 } else {
                     double sv = x;
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(kFull, sv, off);
-                    tot = sv;
+                    if (lane == s) bin = sv;
                 }
-                if (lane == s) bin = tot;
             }
             // ---- 4. RK4 step to t_{n+1}
             if (alive && nn < nt - 1) {
@@ -346,14 +391,14 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     const R dq = h6 * (p[a] + R(2) * (p2[a] + p3[a]) + p4[a]);
                     const R dp = h6 * (k1p[a] + R(2) * (k2p[a] + k3p[a]) + k4p);
                     if constexpr (MIXED) {
-                        df_add(q[a], ql[a], dq);
-                        df_add(p[a], pl[a], dp);
+                        acc2(q[a], ql[a], dq);
+                        acc2(p[a], pl[a], dp);
                     } else {
                         q[a] += dq;
                         p[a] += dp;
                     }
                 }
-                if constexpr (MIXED) df_add(S, Sl, dS);
+                if constexpr (MIXED) acc2(S, Sl, dS);
                 else S += dS;
                 // stability-matrix columns with the four stage Hessians
 #pragma unroll
@@ -391,7 +436,16 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                 }
             }
         }
-        if (lane < send && bin != 0.0) atomicAdd(&I.vz[nb + lane], I.scale * bin);
+        if (lane < send && bin != R(0))
+            atomicAdd(&I.vz[nb + lane], I.scale * (double(bin) + double(binlo)));
+        if constexpr (MIXED) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                renorm(q[a], ql[a]);
+                renorm(p[a], pl[a]);
+            }
+            renorm(S, Sl);
+        }
         if (!__any_sync(kFull, has && status == 0)) break;
     }
 
@@ -430,10 +484,13 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     }
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(128) k_propagate(const DevInstance* __restrict__ insts,
-                                                   const WorkItem* __restrict__ items, int n_items,
-                                                   unsigned int* __restrict__ counter)
+// MINB caps the registers (launch bounds: at least MINB blocks of 128 threads
+// per SM); the autotuner picks among the variants.
+template <bool MIXED, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_propagate(const DevInstance* __restrict__ insts,
+                                                         const WorkItem* __restrict__ items,
+                                                         int n_items,
+                                                         unsigned int* __restrict__ counter)
 {
     const int lane = threadIdx.x & (kWarp - 1);
     for (;;) {
@@ -446,43 +503,54 @@ __global__ void __launch_bounds__(128) k_propagate(const DevInstance* __restrict
     }
 }
 
+using KernelFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*);
+
+// variants: index 0 = no register cap, then MINB = 2, 3, 4, 5
+constexpr int kVariantMinb[kPropVariants] = {1, 2, 3, 4, 5};
+
+KernelFn variant(int precision, int v)
+{
+    static const KernelFn mixed[kPropVariants] = {
+        k_propagate<true, 1>, k_propagate<true, 2>, k_propagate<true, 3>, k_propagate<true, 4>,
+        k_propagate<true, 5>};
+    static const KernelFn fp64[kPropVariants] = {
+        k_propagate<false, 1>, k_propagate<false, 2>, k_propagate<false, 3>,
+        k_propagate<false, 4>, k_propagate<false, 5>};
+    return precision == SFHK_MIXED ? mixed[v] : fp64[v];
+}
+
 }  // namespace
 
-int propagate_occupancy(int precision, int block_threads, int* blocks_per_sm)
+int propagate_variant_minb(int v) { return (v >= 0 && v < kPropVariants) ? kVariantMinb[v] : 0; }
+
+int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm)
 {
-    cudaError_t e;
-    if (precision == SFHK_MIXED)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true>,
-                                                          block_threads, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<false>,
-                                                          block_threads, 0);
-    SFHK_CUDA_TRY(e);
+    if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
+    SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, variant(precision, variant_index), block_threads, 0));
     return SFHK_OK;
 }
 
-int launch_propagate(int precision, const DevInstance* insts, const WorkItem* items, int n_items,
-                     unsigned int* item_counter, int block_threads, int blocks_per_sm,
-                     int sm_count, cudaStream_t s)
+int launch_propagate(int precision, int variant_index, const DevInstance* insts,
+                     const WorkItem* items, int n_items, unsigned int* item_counter,
+                     int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s)
 {
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
+    if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
     int occ = 0;
-    int rc = propagate_occupancy(precision, block_threads, &occ);
+    int rc = propagate_occupancy(precision, variant_index, block_threads, &occ);
     if (rc) return rc;
     if (occ < 1) occ = 1;
     const int bps = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
-    const int warps_needed = n_items;
     const int warps_per_block = block_threads / kWarp;
     int grid = sm_count * bps;
-    const int grid_cap = (warps_needed + warps_per_block - 1) / warps_per_block;
+    const int grid_cap = (n_items + warps_per_block - 1) / warps_per_block;
     if (grid > grid_cap) grid = grid_cap;
     if (grid < 1) grid = 1;
     SFHK_CUDA_TRY(cudaMemsetAsync(item_counter, 0, sizeof(unsigned int), s));
     count_launch();
-    if (precision == SFHK_MIXED)
-        k_propagate<true><<<grid, block_threads, 0, s>>>(insts, items, n_items, item_counter);
-    else
-        k_propagate<false><<<grid, block_threads, 0, s>>>(insts, items, n_items, item_counter);
+    variant(precision, variant_index)<<<grid, block_threads, 0, s>>>(insts, items, n_items,
+                                                                    item_counter);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
 }

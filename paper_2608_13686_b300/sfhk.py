@@ -51,7 +51,7 @@ class sfhk_align_desc(C.Structure):
 class sfhk_run_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("gamma", C.c_double), ("prefactor_cutoff", C.c_double),
                 ("dump_final", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
-                ("stability_cutoff", C.c_double)]
+                ("stability_cutoff", C.c_double), ("kernel_variant", C.c_int)]
 
 
 class sfhk_stats(C.Structure):
@@ -97,6 +97,8 @@ def _load():
         "sfhk_propagate_batch": ([_vp, C.POINTER(_vp), C.c_int, C.POINTER(sfhk_run_opts), _vp],
                                  C.c_int),
         "sfhk_dipole": ([_vp, _vp, _dp, C.c_size_t, _dp, _dp], C.c_int),
+        "sfhk_autotune": ([_vp, _vp, C.POINTER(sfhk_run_opts), C.c_int, C.POINTER(C.c_int)],
+                          C.c_int),
         "sfhk_dipole_device": ([_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)], C.c_int),
         "sfhk_stats_get": ([_vp, C.POINTER(sfhk_stats)], C.c_int),
         "sfhk_final_state": ([_vp, _dp, C.c_uint64], C.c_int),
@@ -154,9 +156,9 @@ def align_desc(a) -> sfhk_align_desc:
 
 
 def run_opts(precision=SFHK_FP64, gamma=0.5, cutoff=0.0, dump=False, block_threads=0,
-             blocks_per_sm=0, stab_cutoff=0.0) -> sfhk_run_opts:
+             blocks_per_sm=0, stab_cutoff=0.0, kernel_variant=0) -> sfhk_run_opts:
     return sfhk_run_opts(precision, gamma, cutoff, int(dump), block_threads, blocks_per_sm,
-                         stab_cutoff)
+                         stab_cutoff, kernel_variant)
 
 
 # ------------------------------------------------------------------ C-ABI calls
@@ -254,6 +256,12 @@ def sfhk_propagate_batch(ctx, ens_list, opts: sfhk_run_opts, stream=None):
            "sfhk_propagate_batch")
 
 
+def sfhk_autotune(ctx, ens, opts: sfhk_run_opts, max_items=0):
+    choice = (C.c_int * 3)()
+    _check(_load().sfhk_autotune(ctx, ens, C.byref(opts), max_items, choice), "sfhk_autotune")
+    return dict(block_threads=choice[0], kernel_variant=choice[1], min_blocks=choice[2])
+
+
 def sfhk_dipole(ctx, ens, nt):
     vz = np.zeros(nt)
     t0, dt = C.c_double(), C.c_double()
@@ -301,5 +309,5 @@ EXPORTED = [
     "sfhk_load_ensemble", "sfhk_ensemble_read", "sfhk_destroy_ensemble", "sfhk_propagate",
     "sfhk_propagate_batch", "sfhk_dipole", "sfhk_dipole_device", "sfhk_stats_get",
     "sfhk_final_state", "sfhk_spectrum", "sfhk_strerror", "sfhk_sample_into",
-    "sfhk_launch_count",
+    "sfhk_launch_count", "sfhk_autotune",
 ]
