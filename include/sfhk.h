@@ -267,6 +267,29 @@ SFHK_API int sfhk_spectrum(const double* vz, size_t nt, double dt, double t_orig
                   double* omega_out, double* yield_out, double* phase_out, size_t n_out,
                   int device_ptrs, void* stream);
 
+/* Spectrum without allocation.  No counterpart in the paper: a variant of
+ * sfhk_spectrum with device pointers for callers that must not allocate
+ * device memory during the call -- for instance a latency-bound serving loop
+ * that cannot take the device synchronisation an allocation may cause, or a
+ * process whose device memory is reserved up front by another framework's
+ * caching allocator.  Same computation and outputs as sfhk_spectrum
+ * (device_ptrs = 1); the caller passes device buffers for vz (nt doubles) and
+ * for every output it wants (n_out doubles each; NULL skips one).
+ * Scratch: a fixed file-scope device array of SFHK_NOALLOC_MAX_NT x 24 bytes
+ * (768 KiB), held on every GPU that loads the library until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (once per device, with the device current); it calls no allocator.  Every
+ * call shares the one array, so calls that overlap on the GPU (different
+ * streams, or other host threads) race on it; serialise them.  Each call
+ * overwrites all the scratch it reads, so no state carries over.
+ * Asynchronous on `stream`.  Errors: SFHK_E_INVAL (nt < 2,
+ * nt > SFHK_NOALLOC_MAX_NT, n_out = 0 or > nt, dt or tau_H <= 0),
+ * SFHK_E_CUDA. */
+#define SFHK_NOALLOC_MAX_NT 32768
+SFHK_API int sfhk_spectrum_noalloc(const double* vz_dev, size_t nt, double dt, double t_origin,
+                                   double tau_H, double* omega_dev, double* yield_dev,
+                                   double* phase_dev, size_t n_out, void* stream);
+
 SFHK_API const char* sfhk_strerror(int code);
 
 /* Number of CUDA kernels this library has launched in the process so far

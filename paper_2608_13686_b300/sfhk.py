@@ -97,6 +97,8 @@ def _load():
         "sfhk_propagate_batch": ([_vp, C.POINTER(_vp), C.c_int, C.POINTER(sfhk_run_opts), _vp],
                                  C.c_int),
         "sfhk_dipole": ([_vp, _vp, _dp, C.c_size_t, _dp, _dp], C.c_int),
+        "sfhk_spectrum_noalloc": ([_vp, C.c_size_t, C.c_double, C.c_double, C.c_double, _vp,
+                                   _vp, _vp, C.c_size_t, _vp], C.c_int),
         "sfhk_autotune": ([_vp, _vp, C.POINTER(sfhk_run_opts), C.c_int, C.POINTER(C.c_int)],
                           C.c_int),
         "sfhk_dipole_device": ([_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)], C.c_int),
@@ -303,11 +305,22 @@ def sfhk_spectrum_device(vz_ptr, nt, dt, t_origin, tau_H, om_ptr, y_ptr, ph_ptr,
                                  stream), "sfhk_spectrum")
 
 
+SFHK_NOALLOC_MAX_NT = 32768
+
+
+def sfhk_spectrum_noalloc(vz_ptr, nt, dt, t_origin, tau_H, om_ptr, y_ptr, ph_ptr, n_out,
+                          stream=None):
+    """Device-buffer spectrum that allocates nothing (fixed scratch of
+    SFHK_NOALLOC_MAX_NT points shared by all calls; serialise overlapping calls)."""
+    _check(_load().sfhk_spectrum_noalloc(vz_ptr, nt, dt, t_origin, tau_H, om_ptr, y_ptr, ph_ptr,
+                                         n_out, stream), "sfhk_spectrum_noalloc")
+
+
 EXPORTED = [
     "sfhk_create", "sfhk_destroy", "sfhk_mem_used", "sfhk_create_target", "sfhk_destroy_target",
     "sfhk_set_pulse", "sfhk_destroy_pulse", "sfhk_pulse_grid", "sfhk_sample_initial",
     "sfhk_load_ensemble", "sfhk_ensemble_read", "sfhk_destroy_ensemble", "sfhk_propagate",
     "sfhk_propagate_batch", "sfhk_dipole", "sfhk_dipole_device", "sfhk_stats_get",
     "sfhk_final_state", "sfhk_spectrum", "sfhk_strerror", "sfhk_sample_into",
-    "sfhk_launch_count", "sfhk_autotune",
+    "sfhk_launch_count", "sfhk_autotune", "sfhk_spectrum_noalloc",
 ]
