@@ -49,13 +49,26 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-traj", type=int, default=W.H2_ANGLES["n_traj"])
+    ap.add_argument("--workload", default="h2-angles",
+                    choices=["h2-angles", "n2-cos2", "batched", "served"])
+    ap.add_argument("--n-traj", type=int, default=0,
+                    help="trajectories per ensemble (0 = the workload's own)")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="served: arrival window (s)")
+    ap.add_argument("--max-requests", type=int, default=0)
+    ap.add_argument("--sweep-rates", type=float, nargs="*", default=[])
+    ap.add_argument("--sweep-seconds", type=float, default=20.0)
+    ap.add_argument("--slice-ms", type=float, default=50.0)
+    ap.add_argument("--max-pending", type=int, default=4096)
+    ap.add_argument("--serve-budget", type=int, default=16 << 30)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--block", type=int, default=0, help="pin the integrator's block size")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="launch the step eagerly instead of replaying its CUDA graph")
     ap.add_argument("--kernel-variant", type=int, default=0, help="pin the register-cap variant")
     return ap.parse_args()
 
@@ -116,17 +129,47 @@ def dist_setup():
     return world, rank, local
 
 
+# ------------------------------------------------------------------ workloads
+def workload_instances(name, n_traj=None):
+    """(label, config, [instance dicts]) of a workload.  An instance is one
+    ensemble: target, pulse, alignment, trajectory count, seed, Philox instance."""
+    if name == "h2-angles":
+        cfg = W.H2_ANGLES
+        n = n_traj or cfg["n_traj"]
+        inst = [dict(target=cfg["target"], pulse=cfg["pulse"], align=W.fixed(a), n_traj=n,
+                     seed=cfg["seed"], instance=k) for k, a in enumerate(cfg["angles"])]
+        conf = {"workload": cfg["name"], "target": cfg["target"],
+                "angles_deg": list(cfg["angles"]), "n_traj_per_angle": n}
+        return cfg["name"], conf, inst
+    if name == "n2-cos2":
+        cfg = W.N2_COS2
+        n = n_traj or cfg["n_traj"]
+        inst = [dict(target=cfg["target"], pulse=cfg["pulse"], align=cfg["align"], n_traj=n,
+                     seed=cfg["seed"], instance=0)]
+        return cfg["name"], {"workload": cfg["name"], "target": "N2", "n_traj": n}, inst
+    if name == "batched":
+        inst = W.batched_instances(256, seed=0)
+        if n_traj:
+            for i in inst:
+                i["n_traj"] = max(1, int(i["n_traj"] * n_traj / 1e6))
+        tot = sum(i["n_traj"] for i in inst)
+        label = "256 H2/N2 instances, N log-uniform 1e4-1e6, 800-1600 nm, 2-4 cycles, one launch"
+        return label, {"workload": label, "instances": len(inst), "n_traj_total": tot}, inst
+    raise SystemExit(f"unknown workload {name}")
+
+
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample_run(n_per_angle, angles, seed_base=0):
-    """The oracle over the first n_per_angle trajectories of each angle:
-    sampling, propagation and spectrum.  Returns (seconds, traj_steps)."""
+def oracle_sample_run(instances, n_per):
+    """The oracle over the first n_per trajectories of each instance: sampling,
+    propagation, dipole and spectrum.  Returns (seconds, traj_steps)."""
     import oracle as O
-    t, p = W.TARGETS["H2"], W.PULSE_800
-    d = O.pulse_derived(p)
     t0 = time.perf_counter()
     steps = 0
-    for k, ang in enumerate(angles):
-        soa, _, _ = O.sample(t, p, W.fixed(ang), seed=seed_base, instance=k, n=n_per_angle)
+    for i in instances:
+        t, p = W.TARGETS[i["target"]], i["pulse"]
+        d = O.pulse_derived(p)
+        m = min(n_per, i["n_traj"])
+        soa, _, _ = O.sample(t, p, i["align"], seed=i["seed"], instance=i["instance"], n=m)
         vz, fin, _ = O.propagate(t, p, soa, W.GAMMA, cutoff=W.CUTOFF, want_final=False,
                                  stab_cutoff=W.STAB_CUTOFF)
         O.spectrum(vz, d["dt"], d["t_origin"], 0.5 * d["Tp"], d["nt"] // 2)
@@ -134,17 +177,18 @@ def oracle_sample_run(n_per_angle, angles, seed_base=0):
     return time.perf_counter() - t0, steps
 
 
-def cpu_baseline(target_s, angles):
+def cpu_baseline(target_s, instances):
     import oracle as O
     O.build()
-    n = 64
-    sec, st = oracle_sample_run(n, angles)
-    n = int(max(64, min(200000, n * target_s / max(sec, 1e-3))))
-    sec, st = oracle_sample_run(n, angles)
+    inst = instances[:3]
+    n = 32
+    sec, st = oracle_sample_run(inst, n)
+    n = int(max(32, min(200000, n * target_s / max(sec, 1e-3))))
+    sec, st = oracle_sample_run(inst, n)
     cores = os.cpu_count()
     return {"value": st / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"H2 workload, first {n} trajectories of each of {len(angles)} angles "
-                      f"(sampling + FP64 RK4 propagation + dipole + DFT), {sec:.1f} s, "
+            "sample": f"first {n} trajectories of each of the first {len(inst)} ensembles of the "
+                      f"workload (sampling + FP64 RK4 propagation + dipole + DFT), {sec:.1f} s, "
                       f"OpenMP over {cores} host threads",
             "seconds": sec, "traj_steps": st}
 
@@ -153,32 +197,35 @@ def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    angles = W.H2_ANGLES["angles"]
+    label, conf, instances = workload_instances(args.workload, args.n_traj)
+    instances = instances[:3]
     import oracle as O
     O.build()
-    n = 64
-    sec, _ = oracle_sample_run(n, angles)
+    n = 32
+    sec, _ = oracle_sample_run(instances, n)
     # each step a bounded sample sized so the whole run stays within minutes
     per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
-    n = int(max(32, min(100000, n * per_step_s / max(sec, 1e-3))))
+    n = int(max(16, min(100000, n * per_step_s / max(sec, 1e-3))))
     for _ in range(args.warmup):
-        oracle_sample_run(n, angles)
+        oracle_sample_run(instances, n)
     times, steps = [], 0
     for _ in range(args.steps):
-        s, st = oracle_sample_run(n, angles)
+        s, st = oracle_sample_run(instances, n)
         times.append(s)
         steps += st
     total = sum(times)
     value = steps / total
     cores = os.cpu_count()
+    conf = dict(conf)
+    conf.update({"sample_per_ensemble": n, "parallelism": "none (CPU oracle)"})
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W.H2_ANGLES["name"], "sample_per_angle": n,
-                       "parallelism": "none (CPU oracle)"},
+            "config": conf,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {n} trajectories of each angle per step"},
+                             "sample": f"first {n} trajectories of each of the first "
+                                       f"{len(instances)} ensembles per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -197,31 +244,33 @@ def run_ours(args):
     _build.build()
     from paper_2608_13686_b300 import sfhk as S
 
-    cfg = W.H2_ANGLES
-    angles = cfg["angles"]
-    n = args.n_traj
+    label, conf, instances = workload_instances(args.workload, args.n_traj)
     ctx = S.sfhk_create(local, 0)
-    tgt = S.sfhk_create_target(ctx, W.TARGETS[cfg["target"]])
-    pul = S.sfhk_set_pulse(ctx, cfg["pulse"])
-    grid = S.sfhk_pulse_grid(pul)
-    nt, dt, t_or, tau = grid["nt"], grid["dt"], grid["t_origin"], 0.5 * grid["Tp"]
-    n_out = nt // 2
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
-    seed = cfg["seed"] + 1000 * rank
-    ens = [S.sfhk_sample_initial(ctx, tgt, pul, W.fixed(a), n, seed, k, sp)
-           for k, a in enumerate(angles)]
-    spec = [torch.empty((3, n_out), dtype=torch.float64, device="cuda") for _ in angles]
+    targets = {nm: S.sfhk_create_target(ctx, W.TARGETS[nm])
+               for nm in sorted({i["target"] for i in instances})}
+    pulses, grids, ens, spec = [], [], [], []
+    for i in instances:
+        ph = S.sfhk_set_pulse(ctx, i["pulse"])
+        g = S.sfhk_pulse_grid(ph)
+        pulses.append(ph)
+        grids.append(g)
+        # per rank its own Philox key: weak scaling over independent samples
+        ens.append(S.sfhk_sample_initial(ctx, targets[i["target"]], ph, i["align"], i["n_traj"],
+                                         i["seed"] + 1000 * rank, i["instance"], sp))
+        spec.append(torch.empty((3, g["nt"] // 2), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
 
-    def step(opts, k_step):
-        for k, a in enumerate(angles):
-            S.sfhk_sample_into(ctx, ens[k], W.fixed(a), seed, k, sp)
-        S.sfhk_propagate_batch(ctx, ens, opts, sp)
-        for k in range(len(angles)):
-            vz_ptr, _ = S.sfhk_dipole_device(ens[k])
-            o = spec[k]
-            S.sfhk_spectrum_device(vz_ptr, nt, dt, t_or, tau, o[0].data_ptr(), o[1].data_ptr(),
-                                   o[2].data_ptr(), n_out, sp)
+    def step(batch):
+        for i, e in zip(instances, ens):
+            S.sfhk_sample_into(ctx, e, i["align"], i["seed"] + 1000 * rank, i["instance"], sp)
+        S.sfhk_batch_launch(batch, sp)
+        for e, g, o in zip(ens, grids, spec):
+            vz_ptr, _ = S.sfhk_dipole_device(e)
+            S.sfhk_spectrum_device(vz_ptr, g["nt"], g["dt"], g["t_origin"], 0.5 * g["Tp"],
+                                   o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(),
+                                   g["nt"] // 2, sp)
 
     def barrier():
         torch.cuda.synchronize()
@@ -229,32 +278,48 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    mixed = S.run_opts(S.SFHK_MIXED, cfg["gamma"], W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+    mixed = S.run_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
                        block_threads=args.block, kernel_variant=args.kernel_variant)
     # launch shape (block size x register-cap variant) chosen by the autotuner
-    # on the first angle's ensemble, untimed
+    # on the first ensemble, untimed
     tuned = None
     if not args.no_tune and not (args.block and args.kernel_variant):
         tuned = S.sfhk_autotune(ctx, ens[0], mixed, max_items=8192)
-    for w in range(args.warmup):
-        step(mixed, w)
+    # a prepared batch: each step only enqueues device work
+    batch = S.sfhk_batch_create(ctx, ens, mixed)
+    for _ in range(args.warmup):
+        step(batch)
     barrier()
+    graph = None
+    if args.graph:
+        # the whole step (re-sampling, batched propagation, spectra) as one CUDA graph
+        l_cap = S.sfhk_launch_count()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            step(batch)
+        launches_per_step = S.sfhk_launch_count() - l_cap
+        graph.replay()
+        barrier()
     clock = ClockSampler(local)
     clock.start()
     l0 = S.sfhk_launch_count()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    prop_ms = []
     barrier()
     ev[0].record(stream)
     for k in range(args.steps):
-        step(mixed, k)
+        if graph is not None:
+            graph.replay()
+        else:
+            step(batch)
         ev[k + 1].record(stream)
     barrier()
     launches = (S.sfhk_launch_count() - l0)
+    if graph is not None:
+        launches = launches_per_step * args.steps      # replays launch the captured kernels
     clk = clock.stop()
     ms_steps = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     st = [S.sfhk_stats_get(e) for e in ens]
-    traj_steps = sum(s["traj_steps"] for s in st)       # per step (deterministic)
+    traj_steps = sum(s["traj_steps"] for s in st)       # per step (the same every step)
     prop_ms = st[0]["kernel_ms"]                        # the batch launch of the last step
     ms = float(np.mean(ms_steps))
     if world > 1:
@@ -263,93 +328,102 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * traj_steps / (ms * 1e-3)
-    spectra_per_s = world * len(angles) / (ms * 1e-3)
-    vz_mixed = [S.sfhk_dipole(ctx, e, nt) for e in ens]
+    spectra_per_s = world * len(instances) / (ms * 1e-3)
+    vz_mixed = [S.sfhk_dipole(ctx, e, g["nt"]) for e, g in zip(ens, grids)]
 
     # roofline of the propagation kernel (FP32 FMA pipe)
-    flops = costs.FLOPS_PER_STEP[cfg["target"]] * traj_steps
+    flops = sum(costs.FLOPS_PER_STEP[i["target"]] * s["traj_steps"]
+                for i, s in zip(instances, st))
     achieved = flops / (prop_ms * 1e-3) / 1e12
     peak = costs.fp32_peak_tflops()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": costs.TRAFFIC.get(args.workload),
             "kernel": "k_propagate<mixed>", "kernel_ms": prop_ms,
-            "flops_per_traj_step": costs.FLOPS_PER_STEP[cfg["target"]],
+            "flops_per_traj_step": {nm: costs.FLOPS_PER_STEP[nm] for nm in targets},
             "peak_basis": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (unit counts, max clock)"}
     if clk.get("sm_mhz"):
         roof["peak_at_median_clock"] = costs.fp32_peak_tflops(clk["sm_mhz"])
 
     # e2e through the public API with host buffers (dipole and spectrum to host)
     def e2e_step():
-        for k, a in enumerate(angles):
-            S.sfhk_sample_into(ctx, ens[k], W.fixed(a), seed, k, sp)
-        S.sfhk_propagate_batch(ctx, ens, mixed, sp)
-        for k in range(len(angles)):
-            vz = S.sfhk_dipole(ctx, ens[k], nt)
-            S.sfhk_spectrum(vz, dt, t_or, tau, n_out)
+        for i, e in zip(instances, ens):
+            S.sfhk_sample_into(ctx, e, i["align"], i["seed"] + 1000 * rank, i["instance"], sp)
+        S.sfhk_batch_launch(batch, sp)
+        for e, g in zip(ens, grids):
+            vz = S.sfhk_dipole(ctx, e, g["nt"])
+            S.sfhk_spectrum(vz, g["dt"], g["t_origin"], 0.5 * g["Tp"], g["nt"] // 2)
 
     e2e_step()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    n_e2e = max(1, min(args.steps, 3))
+    for _ in range(n_e2e):
         e2e_step()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    h2d = len(angles) * (nt * 8 + 24) + 48
-    d2h = len(angles) * (nt * 8 + 3 * n_out * 8)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    nts = [g["nt"] for g in grids]
+    h2d = sum(nt * 8 + 24 for nt in nts) + 48 * len(nts)
+    d2h = sum(nt * 8 + 3 * (nt // 2) * 8 for nt in nts)
     e2e = {"value": world * traj_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3, "steps": n_e2e}
 
     # the plain FP64 GPU path on the same workload, and the dipole difference
     fp64 = None
     if not args.no_fp64:
-        o64 = S.run_opts(S.SFHK_FP64, cfg["gamma"], W.CUTOFF, stab_cutoff=W.STAB_CUTOFF)
-        step(o64, 0)
+        o64 = S.run_opts(S.SFHK_FP64, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF)
+        b64 = S.sfhk_batch_create(ctx, ens, o64)
+        step(b64)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step(o64, 1)
+        step(b64)
         e1.record(stream)
         barrier()
         ms64 = e0.elapsed_time(e1)
         st64 = [S.sfhk_stats_get(e) for e in ens]
         ts64 = sum(s["traj_steps"] for s in st64)
-        vz64 = [S.sfhk_dipole(ctx, e, nt) for e in ens]
+        vz64 = [S.sfhk_dipole(ctx, e, g["nt"]) for e, g in zip(ens, grids)]
+        S.sfhk_batch_destroy(b64)
         errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(vz_mixed, vz64)]
         fp64 = {"value": world * ts64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                 "kernel_ms": st64[0]["kernel_ms"], "steps": 1, "warmup": 1,
-                "dipole_rel_l2_mixed_vs_fp64": errs,
+                "dipole_rel_l2_mixed_vs_fp64": errs if len(errs) <= 8 else
+                {"max": max(errs), "median": float(np.median(errs))},
                 "speedup_mixed_over_fp64": (traj_steps / ms) / (ts64 / ms64)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_seconds, angles)
+        cpu = cpu_baseline(args.cpu_seconds, instances)
 
     if rank == 0:
+        conf = dict(conf)
+        conf.update({"dt": grids[0]["dt"], "gamma": W.GAMMA, "prefactor_cutoff": W.CUTOFF,
+                     "stability_cutoff": W.STAB_CUTOFF, "traj_steps_per_step": traj_steps,
+                     "l2": "inputs larger than L2 (trajectory SoA, 96 B per trajectory)",
+                     "cuda_graph": graph is not None,
+                     "parallelism": f"replicas x{world}"})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64 (mixed: f32 state, two-float action/phase, f64 reduction)",
-                "data": "synthetic",
-                "config": {"workload": cfg["name"], "target": cfg["target"],
-                           "angles_deg": list(angles), "n_traj_per_angle": n,
-                           "nt": nt, "dt": dt, "gamma": cfg["gamma"],
-                           "prefactor_cutoff": W.CUTOFF, "stability_cutoff": W.STAB_CUTOFF,
-                           "traj_steps_per_step": traj_steps,
-                           "l2": "inputs larger than L2 (trajectory SoA 3 x 96 MB)",
-                           "parallelism": f"replicas x{world}"},
+                "data": "synthetic", "config": conf,
                 "spectra_per_s": spectra_per_s,
                 "ms_per_step_all": ms_steps,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "fp64_path": fp64, "gpu_launches": launches // args.steps,
-                "autotuned": tuned,
-                "clocks": clk,
+                "autotuned": tuned, "clocks": clk,
                 "filtered_frac": sum(s["n_filtered"] + s["n_unstable"] for s in st)
-                / (len(angles) * n)}
+                / sum(i["n_traj"] for i in instances)}
         print(json.dumps(line), flush=True)
+    if graph is not None:
+        del graph
+    S.sfhk_batch_destroy(batch)
     for e in ens:
         S.sfhk_destroy_ensemble(e)
-    S.sfhk_destroy_pulse(pul)
-    S.sfhk_destroy_target(tgt)
+    for ph in pulses:
+        S.sfhk_destroy_pulse(ph)
+    for th in targets.values():
+        S.sfhk_destroy_target(th)
     S.sfhk_destroy(ctx)
     if world > 1:
         import torch.distributed as dist
@@ -357,10 +431,77 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ served stream
+def run_served(args):
+    """Poisson request stream through the continuous-batching server; latency
+    percentiles, spectra/s and trajectory-steps/s.  Rank 0 only."""
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_2608_13686_b300 import _build
+    _build.build()
+    from paper_2608_13686_b300 import sfhk as S
+    import threading as th
+
+    def one_run(rate, duration, max_requests=None):
+        reqs = W.request_stream(rate_hz=rate, duration_s=duration, seed=0)
+        if max_requests:
+            reqs = reqs[:max_requests]
+        srv = S.sfhk_server_create(local, S.server_opts(
+            S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF, budget=args.serve_budget,
+            slice_ms=args.slice_ms, max_pending=args.max_pending))
+        ids, rejected = [], 0
+        t0 = time.perf_counter()
+        for r in reqs:
+            wait = r["arrival_s"] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            try:
+                ids.append(S.sfhk_submit(srv, S.request(W.TARGETS[r["target"]], r["pulse"],
+                                                        r["align"], r["n_traj"], r["seed"],
+                                                        r["instance"])))
+            except S.SfhkError:
+                rejected += 1
+        lat, steps, done = [], 0, 0
+        res = S.Result()
+        for i in ids:
+            out = S.sfhk_wait(srv, i, 3600.0, res)
+            if out["status"] == S.SFHK_OK:
+                lat.append(out["t_done"] - out["t_submit"])
+                steps += out["traj_steps"]
+                done += 1
+        wall = time.perf_counter() - t0
+        stt = S.sfhk_server_stats_get(srv)
+        S.sfhk_server_destroy(srv)
+        lat = np.array(lat) if lat else np.array([np.nan])
+        return {"rate_hz": rate, "requests": len(reqs), "completed": done,
+                "rejected": rejected, "wall_s": wall,
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "spectra_per_s": done / wall, "traj_steps_per_s": steps / wall,
+                "gpu_busy_frac": stt["gpu_busy_s"] / max(stt["uptime_s"], 1e-9),
+                "slices": stt["slices"]}
+
+    sweep = [one_run(r, args.sweep_seconds) for r in args.sweep_rates]
+    main = one_run(args.rate, args.duration, args.max_requests)
+    line = {"metric": METRIC, "value": main["traj_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": main["requests"], "warmup": 0, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (mixed)", "data": "synthetic",
+            "config": {"workload": f"Poisson {args.rate} req/s for {args.duration} s, requests "
+                                   "drawn like the 256-instance batch, mixed precision",
+                       "slice_ms": args.slice_ms, "budget_bytes": args.serve_budget},
+            "p50_s": main["p50_s"], "p99_s": main["p99_s"],
+            "spectra_per_s": main["spectra_per_s"], "served": main, "rate_sweep": sweep}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_ours(args)
 
 

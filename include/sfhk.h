@@ -54,6 +54,7 @@ extern "C" {
 #define SFHK_E_NUMERIC   -5  /* non-finite trajectories above the limit     */
 #define SFHK_E_BUSY      -6  /* result not ready yet                        */
 #define SFHK_E_NOTFOUND  -7  /* unknown request id                          */
+#define SFHK_E_CANCELLED -8  /* the request was cancelled                   */
 
 #define SFHK_MAX_PRIM     8  /* s-type Gaussian primitives per centre       */
 
@@ -226,6 +227,21 @@ SFHK_API int sfhk_propagate(sfhk_ctx* ctx, sfhk_ensemble* e, const sfhk_run_opts
 SFHK_API int sfhk_propagate_batch(sfhk_ctx* ctx, sfhk_ensemble* const* ens, int n_ens,
                          const sfhk_run_opts* opts, void* stream);
 
+/* A prepared batch: the instance table and the work-item buffers of a fixed
+ * set of ensembles, built once, so that each launch only enqueues device
+ * work (zeroing the dipoles, rebuilding and sorting the work items from the
+ * ensembles' current samples, one persistent propagation launch) -- no host
+ * synchronisation, allocation or host-to-device copy.  A step made of
+ * sfhk_sample_into, sfhk_batch_launch and the device-pointer sfhk_spectrum can
+ * therefore be captured once in a CUDA graph and replayed.  The ensembles must
+ * outlive the batch and keep their sizes; opts are fixed at creation
+ * (dump_final is ignored).  Errors: as sfhk_propagate_batch. */
+typedef struct sfhk_batch sfhk_batch;
+SFHK_API int sfhk_batch_create(sfhk_ctx* ctx, sfhk_ensemble* const* ens, int n_ens,
+                               const sfhk_run_opts* opts, sfhk_batch** out);
+SFHK_API int sfhk_batch_launch(sfhk_batch* b, void* stream);
+SFHK_API int sfhk_batch_destroy(sfhk_batch* b);
+
 /* Autotuner of the integrator's launch shape (block size x register-cap
  * variant), run on the caller's ensemble: every candidate propagates the
  * first `max_items` work items of 32 trajectories (0 = all) twice, the second
@@ -266,6 +282,91 @@ SFHK_API int sfhk_final_state(sfhk_ensemble* e, double* host, uint64_t n_traj);
 SFHK_API int sfhk_spectrum(const double* vz, size_t nt, double dt, double t_origin, double tau_H,
                   double* omega_out, double* yield_out, double* phase_out, size_t n_out,
                   int device_ptrs, void* stream);
+
+/* ---------------------------------------------------------------- serving */
+/* A spectrum server with continuous batching (not in the paper, which runs
+ * its trajectories as independent CPU jobs).  A host thread owned by the
+ * server admits submitted requests (one target, pulse, alignment and
+ * trajectory count each) in arrival order while its device-memory budget,
+ * its instance slots and its work ring have room, samples each admitted
+ * request on the device, and appends its work items (32 trajectories, longest
+ * first) to one device ring.  The GPU runs the integrator as a sequence of
+ * persistent slices over that ring: a slice's warps stop taking new items
+ * once `slice_ms` has passed (an item once taken runs to its end) and every
+ * request that arrived meanwhile joins the next slice, so the work of
+ * requests of different sizes, targets and pulses runs on the device
+ * together.  A request is done when all its items are; the server then
+ * copies its dipole (and spectrum) to host memory and frees its device state,
+ * which admits the next requests.  No kernel ever waits on another thread.
+ * The server owns its own context on `device`; all calls are thread-safe. */
+typedef struct {
+    size_t device_mem_budget;   /* bytes of device state it may hold (0 = no limit) */
+    int max_pending;            /* queued, not yet admitted requests (0 = 4096)     */
+    int max_active;             /* requests resident at once (0 = 512)              */
+    int precision;              /* SFHK_FP64 | SFHK_MIXED                          */
+    double gamma, prefactor_cutoff, stability_cutoff;   /* as in sfhk_run_opts     */
+    double slice_ms;            /* slice length (0 = 50 ms)                         */
+    int spectrum;               /* also compute yield and phase of each result      */
+    int fifo;                   /* 1: work items in arrival order; 0 (default): a
+                                   request whose work (items x Nt) is smaller than
+                                   the work still queued goes to the front of the
+                                   ring, so short requests overtake long ones      */
+} sfhk_server_opts;
+
+typedef struct {
+    sfhk_target_desc target;
+    sfhk_pulse_desc pulse;
+    sfhk_align_desc align;
+    uint64_t n_traj, seed;
+    uint32_t instance;          /* Philox counter word: the same (seed, instance)
+                                   gives the same ensemble as sfhk_sample_initial */
+} sfhk_request;
+
+/* Result of a finished request.  The caller sets vz / yield / phase (host
+ * buffers, may be NULL) and their capacities; sfhk_poll / sfhk_wait fill them
+ * (vz: nt values; yield, phase: n_out = nt/2 values; truncated to capacity)
+ * and every other field.  Times are seconds on the server's clock. */
+typedef struct {
+    int status;                 /* SFHK_OK, SFHK_E_CANCELLED or the failing code */
+    int nt;
+    double t_origin, dt;
+    size_t n_out;
+    double* vz;
+    size_t vz_capacity;
+    double* yield;
+    double* phase;
+    size_t spec_capacity;
+    double t_submit, t_admit, t_done;
+    uint64_t traj_steps, n_filtered, n_unstable;
+} sfhk_result;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, cancelled, failed, slices;
+    uint64_t traj_steps;
+    int pending, active;
+    double gpu_busy_s, uptime_s;
+    uint64_t device_bytes;      /* device memory the server holds now */
+} sfhk_server_stats;
+
+/* Errors: SFHK_E_INVAL (bad options), SFHK_E_CUDA (device). */
+SFHK_API int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** out);
+/* Stops the server thread after its current slice; unfinished requests are dropped. */
+SFHK_API int sfhk_server_destroy(sfhk_server* s);
+/* Queue a request; returns at once with its id.  Errors: SFHK_E_INVAL (bad
+ * descriptor), SFHK_E_NOMEM (admission refused: the queue is full, or the
+ * request alone needs more than the device-memory budget). */
+SFHK_API int sfhk_submit(sfhk_server* s, const sfhk_request* req, uint64_t* req_id);
+/* SFHK_E_BUSY while the request is queued or running; once it has ended,
+ * fills *result, forgets the request and returns SFHK_OK (result->status says
+ * how it ended).  SFHK_E_NOTFOUND for an unknown (or already polled) id. */
+SFHK_API int sfhk_poll(sfhk_server* s, uint64_t req_id, sfhk_result* result);
+/* As sfhk_poll, but blocks up to timeout_s seconds; SFHK_E_TIMEOUT if it has
+ * not ended by then. */
+SFHK_API int sfhk_wait(sfhk_server* s, uint64_t req_id, double timeout_s, sfhk_result* result);
+/* Cancel a queued or running request (a running one stops at its next work
+ * items).  SFHK_E_NOTFOUND if unknown or already ended. */
+SFHK_API int sfhk_cancel(sfhk_server* s, uint64_t req_id);
+SFHK_API int sfhk_server_stats_get(sfhk_server* s, sfhk_server_stats* out);
 
 /* Spectrum without allocation.  No counterpart in the paper: a variant of
  * sfhk_spectrum with device pointers for callers that must not allocate

@@ -37,3 +37,9 @@ MAX_SM_MHZ = 2032.0
 
 def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from the last ncu capture, per workload (None until captured for the
+# current kernel)
+TRAFFIC = {}

@@ -11,12 +11,6 @@
 #include "sfhk_device.cuh"
 #include "sfhk_internal.h"
 
-struct sfhk_ctx : public sfhk::Ctx {};
-struct sfhk_target : public sfhk::Target {};
-struct sfhk_pulse : public sfhk::Pulse {};
-struct sfhk_ensemble : public sfhk::Ensemble {
-    sfhk::DeviceBuf cdf, hist, inst, qctr;
-};
 
 namespace sfhk {
 
@@ -146,6 +140,8 @@ int ensemble_finish(sfhk_ensemble* e, cudaStream_t s)
     return launch_phase_table(*e->pulse, e->tgt->desc.Ip, (double2*)e->ph.p, (float2*)e->phf.p, s);
 }
 
+}  // namespace
+
 DevInstance make_instance(sfhk_ensemble* e, const sfhk_run_opts& o)
 {
     DevInstance I;
@@ -171,8 +167,12 @@ DevInstance make_instance(sfhk_ensemble* e, const sfhk_run_opts& o)
     I.inv_gamma = 1.0 / o.gamma;
     I.cutoff2 = o.prefactor_cutoff > 0.0 ? o.prefactor_cutoff * o.prefactor_cutoff : 0.0;
     I.stab_cut = o.stability_cutoff > 0.0 ? o.stability_cutoff : 0.0;
+    I.done_items = nullptr;
+    I.cancel = nullptr;
     return I;
 }
+
+namespace {
 
 int check_opts(const sfhk_run_opts* o)
 {
@@ -185,6 +185,8 @@ int check_opts(const sfhk_run_opts* o)
     if (o->kernel_variant < 0 || o->kernel_variant > kPropVariants) return SFHK_E_INVAL;
     return SFHK_OK;
 }
+
+}  // namespace
 
 // prepare one ensemble for a launch: zero outputs, dump buffer
 int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s)
@@ -201,6 +203,8 @@ int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s)
     e->dumped = o.dump_final != 0;
     return SFHK_OK;
 }
+
+namespace {
 
 void shape(Ctx* c, const sfhk_run_opts& o, int* bt, int* var, int* bps)
 {
@@ -603,6 +607,125 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
     }
     cudaFreeAsync(scratch, s);
     return rc;
+}
+
+}  // extern "C"
+
+struct sfhk_batch {
+    sfhk_ctx* ctx = nullptr;
+    std::vector<sfhk_ensemble*> ens;
+    sfhk_run_opts opts;
+    sfhk::DeviceBuf buf;
+    sfhk::DevInstance* d_inst = nullptr;
+    sfhk::WorkItem *d_items = nullptr, *d_sorted = nullptr;
+    int *d_keys = nullptr, *d_perm = nullptr, *d_hist = nullptr, *d_nt = nullptr;
+    unsigned int* d_ctr = nullptr;
+    long long total_items = 0;
+    int max_nt = 1;
+};
+
+extern "C" {
+
+int sfhk_batch_create(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens, const sfhk_run_opts* o,
+                      sfhk_batch** out)
+{
+    if (!c || !ens || n_ens < 1 || !out) return SFHK_E_INVAL;
+    for (int i = 0; i < n_ens; ++i)
+        if (!ens[i] || ens[i]->ctx != c) return SFHK_E_INVAL;
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if ((rc = set_device(c->device))) return rc;
+    sfhk_batch* b = new (std::nothrow) sfhk_batch;
+    if (!b) return SFHK_E_NOMEM;
+    b->ctx = c;
+    b->ens.assign(ens, ens + n_ens);
+    b->opts = *o;
+    b->opts.dump_final = 0;
+    for (int i = 0; i < n_ens; ++i) {
+        b->total_items += ens[i]->n_items;
+        b->max_nt = std::max(b->max_nt, ens[i]->pulse->nt);
+    }
+    if (b->total_items > 2147483647ll) {
+        delete b;
+        return SFHK_E_INVAL;
+    }
+    const size_t bytes = sizeof(DevInstance) * n_ens + 2 * sizeof(WorkItem) * b->total_items +
+                         2 * sizeof(int) * b->total_items + sizeof(int) * (b->max_nt + 1) +
+                         sizeof(int) * n_ens + 4096;
+    if ((rc = c->alloc(b->buf, bytes))) {
+        delete b;
+        return rc;
+    }
+    char* base = (char*)b->buf.p;
+    auto take = [&](size_t n) {
+        char* r = base;
+        base += (n + 255) & ~size_t(255);
+        return (void*)r;
+    };
+    b->d_inst = (DevInstance*)take(sizeof(DevInstance) * n_ens);
+    b->d_items = (WorkItem*)take(sizeof(WorkItem) * b->total_items);
+    b->d_sorted = (WorkItem*)take(sizeof(WorkItem) * b->total_items);
+    b->d_keys = (int*)take(sizeof(int) * b->total_items);
+    b->d_perm = (int*)take(sizeof(int) * b->total_items);
+    b->d_hist = (int*)take(sizeof(int) * (b->max_nt + 1));
+    b->d_nt = (int*)take(sizeof(int) * n_ens);
+    b->d_ctr = (unsigned int*)take(sizeof(unsigned int) * 4);
+    std::vector<DevInstance> hI(n_ens);
+    std::vector<int> hnt(n_ens);
+    for (int i = 0; i < n_ens; ++i) {
+        hI[i] = make_instance(ens[i], b->opts);
+        hnt[i] = ens[i]->pulse->nt;
+    }
+    if (cudaMemcpy(b->d_inst, hI.data(), sizeof(DevInstance) * n_ens, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->d_nt, hnt.data(), sizeof(int) * n_ens, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        c->release(b->buf);
+        delete b;
+        return SFHK_E_CUDA;
+    }
+    *out = b;
+    return SFHK_OK;
+}
+
+int sfhk_batch_launch(sfhk_batch* b, void* stream)
+{
+    if (!b) return SFHK_E_INVAL;
+    int rc = set_device(b->ctx->device);
+    if (rc) return rc;
+    cudaStream_t s = as_stream(stream);
+    long long off = 0;
+    for (size_t i = 0; i < b->ens.size(); ++i) {
+        sfhk_ensemble* e = b->ens[i];
+        SFHK_CUDA_TRY(cudaMemsetAsync(e->vz.p, 0, sizeof(double) * e->pulse->nt, s));
+        SFHK_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(unsigned long long) * 3, s));
+        SFHK_CUDA_TRY(cudaMemsetAsync((unsigned long long*)e->counters.p + 4, 0,
+                                      sizeof(unsigned long long), s));
+        rc = launch_build_items((const int*)e->perm.p, (const int*)e->n0.p, e->n, (int)i,
+                                b->d_items + off, s);
+        if (rc) return rc;
+        off += e->n_items;
+        e->dumped = false;
+        e->have_result = true;
+    }
+    rc = launch_sort_items(b->d_items, (int)b->total_items, b->d_nt, b->d_sorted, b->d_keys,
+                           b->d_perm, b->d_hist, b->max_nt, s);
+    if (rc) return rc;
+    int bt, var, bps;
+    shape(b->ctx, b->opts, &bt, &var, &bps);
+    rc = launch_propagate(b->opts.precision, var, b->d_inst, b->d_sorted, (int)b->total_items,
+                          b->d_ctr, bt, bps, b->ctx->sm_count, s);
+    return rc;
+}
+
+int sfhk_batch_destroy(sfhk_batch* b)
+{
+    if (!b) return SFHK_E_INVAL;
+    set_device(b->ctx->device);
+    cudaDeviceSynchronize();
+    b->ctx->release(b->buf);
+    delete b;
+    return SFHK_OK;
 }
 
 int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max_items,

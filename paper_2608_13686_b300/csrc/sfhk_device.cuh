@@ -172,16 +172,21 @@ struct PotConst {
     int kind, screened;
 };
 
-// V, force F = -grad V and Hessian at q + l (both centres, +-(R/2)n).  l is
-// the low part of a two-float position (zero in FP64): it is added after the
-// centre is subtracted, so the distance to a nearby nucleus keeps the
-// position's full two-float precision.
+// V, force F = -grad V and Hessian at the stage point q + o + l (both centres,
+// +-(R/2)n): q is the (high part of the) step's base position, o the RK4 stage
+// offset and l the low part of a two-float position (LO; zero in FP64).  In
+// two-float mode the centre is subtracted from q first (exact near a nucleus)
+// and o and l are added to that small difference, so the distance to a nearby
+// nucleus keeps the full two-float precision of the position.
 template <typename R, bool LO>
-__device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz, R lx, R ly,
-                                          R lz, R& V, R& Fx, R& Fy, R& Fz, Sym3<R>& H)
+__device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz, R ox, R oy,
+                                          R oz, R lx, R ly, R lz, R& V, R& Fx, R& Fy, R& Fz,
+                                          Sym3<R>& H)
 {
     if (K.kind != 0) {            // harmonic test potential
-        const R x = LO ? qx + lx : qx, y = LO ? qy + ly : qy, z = LO ? qz + lz : qz;
+        const R x = LO ? (qx + ox) + lx : qx + ox;
+        const R y = LO ? (qy + oy) + ly : qy + oy;
+        const R z = LO ? (qz + oz) + lz : qz + oz;
         V = R(0.5) * K.w2 * (x * x + y * y + z * z);
         Fx = -K.w2 * x;
         Fy = -K.w2 * y;
@@ -194,16 +199,19 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz
     H.xx = H.yy = H.zz = H.xy = H.xz = H.yz = R(0);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        R dx = c == 0 ? qx - K.cx : qx + K.cx;
-        R dy = c == 0 ? qy - K.cy : qy + K.cy;
-        R dz = c == 0 ? qz - K.cz : qz + K.cz;
+        R dx, dy, dz;
         if (LO) {
-            dx += lx;
-            dy += ly;
-            dz += lz;
+            dx = ((c == 0 ? qx - K.cx : qx + K.cx) + ox) + lx;
+            dy = ((c == 0 ? qy - K.cy : qy + K.cy) + oy) + ly;
+            dz = ((c == 0 ? qz - K.cz : qz + K.cz) + oz) + lz;
+        } else {
+            dx = (qx + ox) - (c == 0 ? K.cx : -K.cx);
+            dy = (qy + oy) - (c == 0 ? K.cy : -K.cy);
+            dz = (qz + oz) - (c == 0 ? K.cz : -K.cz);
         }
         const R s2 = dx * dx + dy * dy + dz * dz + K.a2;
-        const R u = rsqrt_t<R>(s2);
+        R u = rsqrt_t<R>(s2);
+        if (LO) u = u * (R(1.5) - (R(0.5) * s2 * u) * u);   // one Newton step on 1/sqrt
         const R u2 = u * u, u3 = u2 * u;
         R g1, g2;
         if (K.screened) {

@@ -59,6 +59,8 @@ struct DevInstance {
     double gamma, inv_gamma;
     double cutoff2;        // cutoff^2 on |det| (0 = off), |C|^2 = |det|
     double stab_cut;       // cutoff on max |M_ij| (0 = off)
+    unsigned int* done_items;   // server: work items of this instance finished (or null)
+    const int* cancel;          // server: nonzero = skip the remaining items (or null)
 };
 
 struct WorkItem {
@@ -146,11 +148,34 @@ int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s);
 int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm);
 int propagate_variant_minb(int variant_index);
+// server slice: items ring[(base + i) & mask], i < n_items; warps stop pulling
+// new items slice_ns after the first warp started (0 = no limit); *t0 must be
+// zero before the launch; *counter ends >= the number of items taken
+int launch_propagate_slice(int precision, int variant_index, const DevInstance* insts,
+                           const WorkItem* ring, unsigned int mask, unsigned int base,
+                           int n_items, unsigned int* counter, unsigned long long slice_ns,
+                           unsigned long long* t0, int block_threads, int sm_count,
+                           cudaStream_t s);
+
 // spectrum (sfhk_spectrum.cu)
 int launch_spectrum(const double* vz, int nt, double dt, double t_origin, double tau_H,
                     double* omega, double* yield, double* phase, int n_out, double2* twiddle,
                     cudaStream_t s);
 
+}  // namespace sfhk
+
+// the opaque C handles
+struct sfhk_ctx : public sfhk::Ctx {};
+struct sfhk_target : public sfhk::Target {};
+struct sfhk_pulse : public sfhk::Pulse {};
+struct sfhk_ensemble : public sfhk::Ensemble {
+    sfhk::DeviceBuf cdf, hist, inst, qctr;
+};
+
+namespace sfhk {
+// helpers of sfhk_api.cu shared with the server
+DevInstance make_instance(sfhk_ensemble* e, const sfhk_run_opts& o);
+int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s);
 }  // namespace sfhk
 
 #define SFHK_CUDA_TRY(expr)                                                         \

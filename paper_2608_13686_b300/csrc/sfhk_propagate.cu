@@ -59,13 +59,6 @@ __device__ __forceinline__ float hypot_t<float>(float a, float b) { return hypot
 template <>
 __device__ __forceinline__ double hypot_t<double>(double a, double b) { return hypot(a, b); }
 
-template <typename R>
-__device__ __forceinline__ R sqrt_t(R a);
-template <>
-__device__ __forceinline__ float sqrt_t<float>(float a) { return sqrtf(a); }
-template <>
-__device__ __forceinline__ double sqrt_t<double>(double a) { return sqrt(a); }
-
 // principal square root of z, given r = |z|:  sqrt(z) = (t, y/(2t)) with
 // t = sqrt((r + x)/2) for x >= 0, and the mirrored form for x < 0.
 template <typename R>
@@ -134,6 +127,140 @@ template <typename R>
 __device__ __forceinline__ R shfl(R v, int src)
 {
     return __shfl_sync(kFull, v, src);
+}
+
+
+// One RK4 step's stage evaluations from (q, p) (high part q, low part ql):
+// the four stage Hessians and the increments dq, dp, dS of the step.  Stage
+// points are formed as base + offset (see potential()).
+template <typename R, bool MIXED>
+__device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], const R ql[3],
+                                           const R p[3], R E1, R E2, R E4, R h, R h2, R h6,
+                                           Sym3<R> H[4], R dq[3], R dp[3], R& dS)
+{
+    R V, F[3];
+    const R z0 = R(0);
+    potential<R, MIXED>(K, q[0], q[1], q[2], z0, z0, z0, ql[0], ql[1], ql[2], V, F[0], F[1],
+                        F[2], H[0]);
+    const R k1p[3] = {F[0], F[1], F[2] - E1};
+    const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
+    R o[3], p2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = h2 * p[a];
+        p2[a] = p[a] + h2 * k1p[a];
+    }
+    potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
+                        F[1], F[2], H[1]);
+    const R k2p[3] = {F[0], F[1], F[2] - E2};
+    const R k2s =
+        R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - (q[2] + o[2]) * E2;
+    R p3[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = h2 * p2[a];
+        p3[a] = p[a] + h2 * k2p[a];
+    }
+    potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
+                        F[1], F[2], H[2]);
+    const R k3p[3] = {F[0], F[1], F[2] - E2};
+    const R k3s =
+        R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - (q[2] + o[2]) * E2;
+    R p4[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = h * p3[a];
+        p4[a] = p[a] + h * k3p[a];
+    }
+    potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
+                        F[1], F[2], H[3]);
+    const R k4s =
+        R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - (q[2] + o[2]) * E4;
+    dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R k4p = F[a] - (a == 2 ? E4 : R(0));
+        dq[a] = h6 * (p[a] + R(2) * (p2[a] + p3[a]) + p4[a]);
+        dp[a] = h6 * (k1p[a] + R(2) * (k2p[a] + k3p[a]) + k4p);
+    }
+}
+
+// The six stability-matrix columns advanced by the same RK4 step with the
+// four stage Hessians (dMq/dt = Mp, dMp/dt = -Hess V Mq).
+template <typename R>
+__device__ __forceinline__ void m_update(R Mq[6][3], R Mp[6][3], const Sym3<R> H[4], R h, R h2,
+                                         R h6)
+{
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        R x0[3], v0[3], a1[3], xs[3], vs[3], a2[3], a3[3], a4[3], v2[3], v3[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            x0[r] = Mq[c][r];
+            v0[r] = Mp[c][r];
+        }
+        neg_hx(H[0], x0, a1);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            xs[r] = x0[r] + h2 * v0[r];
+            v2[r] = v0[r] + h2 * a1[r];
+        }
+        neg_hx(H[1], xs, a2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            xs[r] = x0[r] + h2 * v2[r];
+            v3[r] = v0[r] + h2 * a2[r];
+        }
+        neg_hx(H[2], xs, a3);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            xs[r] = x0[r] + h * v3[r];
+            vs[r] = v0[r] + h * a3[r];
+        }
+        neg_hx(H[3], xs, a4);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            Mq[c][r] = x0[r] + h6 * (v0[r] + R(2) * (v2[r] + v3[r]) + vs[r]);
+            Mp[c][r] = v0[r] + h6 * (a1[r] + R(2) * (a2[r] + a3[r]) + a4[r]);
+        }
+    }
+}
+
+// Prefactor of the current M on the continuous branch (sign kept within a
+// right angle of the previous C), then the per-step checks in the order:
+// finiteness, prefactor filter, stability filter.
+template <typename R>
+__device__ __forceinline__ void prefactor_and_checks(const R Mq[6][3], const R Mp[6][3], R gam,
+                                                     R igam, C2<R>& Cp, const R q[3],
+                                                     const R p[3], R S, R cut2, R stab,
+                                                     int& status)
+{
+    C2<R> B[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            B[3 * r + c] = {R(0.5) * (Mq[c][r] + Mp[3 + c][r]),
+                            R(0.5) * (igam * Mp[c][r] - gam * Mq[3 + c][r])};
+    const C2<R> m0 = cm(B[4], B[8]), m1 = cm(B[5], B[7]);
+    const C2<R> m2 = cm(B[3], B[8]), m3 = cm(B[5], B[6]);
+    const C2<R> m4 = cm(B[3], B[7]), m5 = cm(B[4], B[6]);
+    const C2<R> c0 = cm(B[0], {m0.x - m1.x, m0.y - m1.y});
+    const C2<R> c1 = cm(B[1], {m2.x - m3.x, m2.y - m3.y});
+    const C2<R> c2 = cm(B[2], {m4.x - m5.x, m4.y - m5.y});
+    const C2<R> det = {c0.x - c1.x + c2.x, c0.y - c1.y + c2.y};
+    const R rdet = hypot_t<R>(det.x, det.y);
+    C2<R> C = csqrt_p(det, rdet);
+    if (C.x * Cp.x + C.y * Cp.y < R(0)) {
+        C.x = -C.x;
+        C.y = -C.y;
+    }
+    Cp = C;
+    const bool fin = isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(p[0]) &&
+                     isfinite(p[1]) && isfinite(p[2]) && isfinite(S) && isfinite(rdet);
+    if (!fin) status = 2;
+    else if (cut2 > R(0) && rdet > cut2) status = 1;
+    else if (stab > R(0) && max_abs_M(Mq, Mp) > stab) status = 3;
 }
 
 template <bool MIXED>
@@ -208,21 +335,33 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     const R h = R(I.dt), h2 = R(0.5 * I.dt), h6 = R(I.dt / 6.0);
     const int nE = 2 * nt - 1;
 
+    // The step is software-pipelined: the stage evaluations (potentials along
+    // the four RK4 stages, a latency-bound chain) of step n+1 are computed in
+    // the same block as the stability-matrix update of step n (independent,
+    // ILP-rich), so the scheduler interleaves them.  Carried between steps:
+    // the stage Hessians Hs and increments (dq, dp, dS) of the next step.
+    Sym3<R> Hs[4];
+    R dq[3], dp[3], dS;
     for (int nb = W.n_start; nb < nt; nb += kWarp) {
-        // chunk tables: one element per lane, broadcast later
+        // chunk tables: E at the half steps of steps nb+lane and nb+lane+1,
+        // e^{-i Ip t} at nb+lane; broadcast by shuffles
         const int nl = nb + lane;
-        R e0, e1, e2;
+        R e0, e1, e2, e3, e4;
         C2<R> phl;
         if constexpr (MIXED) {
             e0 = I.Ehf[min(2 * nl, nE - 1)];
             e1 = I.Ehf[min(2 * nl + 1, nE - 1)];
             e2 = I.Ehf[min(2 * nl + 2, nE - 1)];
+            e3 = I.Ehf[min(2 * nl + 3, nE - 1)];
+            e4 = I.Ehf[min(2 * nl + 4, nE - 1)];
             const float2 t = I.phf[min(nl, nt - 1)];
             phl = {t.x, t.y};
         } else {
             e0 = I.Eh[min(2 * nl, nE - 1)];
             e1 = I.Eh[min(2 * nl + 1, nE - 1)];
             e2 = I.Eh[min(2 * nl + 2, nE - 1)];
+            e3 = I.Eh[min(2 * nl + 3, nE - 1)];
+            e4 = I.Eh[min(2 * nl + 4, nE - 1)];
             const double2 t = I.ph[min(nl, nt - 1)];
             phl = {t.x, t.y};
         }
@@ -230,104 +369,70 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         const int send = min(kWarp, nt - nb);
         for (int s = 0; s < send; ++s) {
             const int nn = nb + s;
-            const R E1 = shfl(e0, s), E2 = shfl(e1, s), E4 = shfl(e2, s);
+            const R E1 = shfl(e0, s), E2 = shfl(e1, s), E4 = shfl(e2, s);     // step nn
+            const R E2n = shfl(e3, s), E4n = shfl(e4, s);                     // step nn+1
             const C2<R> ph = {shfl(phl.x, s), shfl(phl.y, s)};
-            bool alive = (nn >= n0) && status == 0;
+            const bool live = (nn >= n0) && status == 0;
+            // ---- birth: checks at t0 (C = 1) and the stage data of the first step
+            if (live && nn == n0) {
+                prefactor_and_checks(Mq, Mp, gam, igam, Cp, q, p, S, cut2, stab, status);
+                stage_eval<R, MIXED>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS);
+            }
+            // ---- contribution at t_nn: Re[w C e^{iS} e^{-i Ip t} <psi0|k_z|p,q>]
             R x = R(0);
-            if (alive) {
-                // ---- 1. prefactor with continuous branch
-                C2<R> C = Cp;
-                if (nn > n0) {
-                    C2<R> B[9];
+            if (live && status == 0) {
+                const R pp = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+                C2<R> Rk = {R(0), R(0)};
 #pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            B[3 * r + c] = {R(0.5) * (Mq[c][r] + Mp[3 + c][r]),
-                                            R(0.5) * (igam * Mp[c][r] - gam * Mq[3 + c][r])};
-                    const C2<R> m0 = cm(B[4], B[8]), m1 = cm(B[5], B[7]);
-                    const C2<R> m2 = cm(B[3], B[8]), m3 = cm(B[5], B[6]);
-                    const C2<R> m4 = cm(B[3], B[7]), m5 = cm(B[4], B[6]);
-                    const C2<R> c0 = cm(B[0], {m0.x - m1.x, m0.y - m1.y});
-                    const C2<R> c1 = cm(B[1], {m2.x - m3.x, m2.y - m3.y});
-                    const C2<R> c2 = cm(B[2], {m4.x - m5.x, m4.y - m5.y});
-                    const C2<R> det = {c0.x - c1.x + c2.x, c0.y - c1.y + c2.y};
-                    const R rdet = hypot_t<R>(det.x, det.y);
-                    C = csqrt_p(det, rdet);
-                    if (C.x * Cp.x + C.y * Cp.y < R(0)) {
-                        C.x = -C.x;
-                        C.y = -C.y;
-                    }
-                    const bool fin = isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) &&
-                                     isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) &&
-                                     isfinite(S) && isfinite(rdet);
-                    if (!fin) {
-                        status = 2;
-                    } else if (cut2 > R(0) && rdet > cut2) {
-                        status = 1;
-                    } else if (stab > R(0) && max_abs_M(Mq, Mp) > stab) {
-                        status = 3;
-                    }
-                    Cp = C;
-                }
-                alive = status == 0;
-                if (alive) {
-                    // ---- 2. recombination element <psi0| k_z |p,q>
-                    const R pp = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
-                    C2<R> Rk = {R(0), R(0)};
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const R dx = c == 0 ? q[0] - K.cx : q[0] + K.cx;
-                        const R dy = c == 0 ? q[1] - K.cy : q[1] + K.cy;
-                        const R dz = c == 0 ? q[2] - K.cz : q[2] + K.cz;
-                        const R dd = dx * dx + dy * dy + dz * dz;
-                        if (K1max * dd + K2max * pp <= kSkip) continue;   // far from this centre
-                        const R pdd = p[0] * dx + p[1] * dy + p[2] * dz;
+                for (int c = 0; c < 2; ++c) {
+                    const R dx = c == 0 ? q[0] - K.cx : q[0] + K.cx;
+                    const R dy = c == 0 ? q[1] - K.cy : q[1] + K.cy;
+                    const R dz = c == 0 ? q[2] - K.cz : q[2] + K.cz;
+                    const R dd = dx * dx + dy * dy + dz * dz;
+                    if (K1max * dd + K2max * pp <= kSkip) continue;   // far from this centre
+                    const R pdd = p[0] * dx + p[1] * dy + p[2] * dz;
 #pragma unroll 1
-                        for (int k = 0; k < n_prim; ++k) {
-                            R K1, K2, K3, K4;
-                            if constexpr (MIXED) {
-                                K1 = I.rec.K1f[k]; K2 = I.rec.K2f[k];
-                                K3 = I.rec.K3f[k]; K4 = I.rec.K4f[k];
-                            } else {
-                                K1 = I.rec.K1[k]; K2 = I.rec.K2[k];
-                                K3 = I.rec.K3[k]; K4 = I.rec.K4[k];
-                            }
-                            const R ex = K1 * dd + K2 * pp;
-                            if (ex > kSkip) {
-                                const R mag = K4 * exp_t<R>(ex);
-                                R sn, cs;
-                                if constexpr (MIXED) __sincosf(K3 * pdd, &sn, &cs);
-                                else sincos(K3 * pdd, &sn, &cs);
-                                // mag (p_z - i g d_z)(cs + i sn)
-                                const R ar = mag * p[2], ai = -mag * gam * dz;
-                                Rk.x += ar * cs - ai * sn;
-                                Rk.y += ar * sn + ai * cs;
-                            }
-                        }
-                    }
-                    if (Rk.x != R(0) || Rk.y != R(0)) {
-                        // ---- e^{iS}
-                        R sn, cs;
+                    for (int k = 0; k < n_prim; ++k) {
+                        R K1, K2, K3, K4;
                         if constexpr (MIXED) {
-                            // two-float reduction of S modulo 2 pi (Cody-Waite split)
-                            const float k = rintf(S * 0.15915494309189535f);
-                            float r = fmaf(-k, 6.28318548202514648f, S);
-                            r = fmaf(-k, -1.7484555314695172e-07f, r);
-                            r += Sl;
-                            __sincosf(r, &sn, &cs);
+                            K1 = I.rec.K1f[k]; K2 = I.rec.K2f[k];
+                            K3 = I.rec.K3f[k]; K4 = I.rec.K4f[k];
                         } else {
-                            sincos(S, &sn, &cs);
+                            K1 = I.rec.K1[k]; K2 = I.rec.K2[k];
+                            K3 = I.rec.K3[k]; K4 = I.rec.K4[k];
                         }
-                        const C2<R> eS = {cs, sn};
-                        const C2<R> wC = cm(C2<R>{wR, wI}, C);
-                        const C2<R> a = cm(wC, eS);
-                        const C2<R> b = cm(a, ph);
-                        x = b.x * Rk.x - b.y * Rk.y;
+                        const R ex = K1 * dd + K2 * pp;
+                        if (ex > kSkip) {
+                            const R mag = K4 * exp_t<R>(ex);
+                            R sn, cs;
+                            if constexpr (MIXED) __sincosf(K3 * pdd, &sn, &cs);
+                            else sincos(K3 * pdd, &sn, &cs);
+                            // mag (p_z - i g d_z)(cs + i sn)
+                            const R ar = mag * p[2], ai = -mag * gam * dz;
+                            Rk.x += ar * cs - ai * sn;
+                            Rk.y += ar * sn + ai * cs;
+                        }
                     }
+                }
+                if (Rk.x != R(0) || Rk.y != R(0)) {
+                    R sn, cs;
+                    if constexpr (MIXED) {
+                        // two-float reduction of S modulo 2 pi (Cody-Waite split)
+                        const float k = rintf(S * 0.15915494309189535f);
+                        float r = fmaf(-k, 6.28318548202514648f, S);
+                        r = fmaf(-k, -1.7484555314695172e-07f, r);
+                        r += Sl;
+                        __sincosf(r, &sn, &cs);
+                    } else {
+                        sincos(S, &sn, &cs);
+                    }
+                    const C2<R> eS = {cs, sn};
+                    const C2<R> a = cm(cm(C2<R>{wR, wI}, Cp), eS);
+                    const C2<R> b = cm(a, ph);
+                    x = b.x * Rk.x - b.y * Rk.y;
                 }
             }
-            // ---- 3. warp sum (skipped when no lane contributes)
+            // ---- warp sum (skipped when no lane contributes)
             if (__any_sync(kFull, x != R(0))) {
                 if constexpr (MIXED) {
                     float sv = x, ev = 0.0f;
@@ -350,90 +455,28 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     if (lane == s) bin = sv;
                 }
             }
-            // ---- 4. RK4 step to t_{n+1}
-            if (alive && nn < nt - 1) {
+            // ---- step to t_{nn+1}: apply the increments, advance M with the
+            // carried Hessians, evaluate the stages of the next step (same
+            // block), then the prefactor and checks at t_{nn+1}
+            if (live && status == 0 && nn < nt - 1) {
                 ++steps;
-                Sym3<R> H1, H2, H3, H4;
-                R V, F[3];
-                potential<R, MIXED>(K, q[0], q[1], q[2], ql[0], ql[1], ql[2], V, F[0], F[1], F[2], H1);
-                R k1p[3] = {F[0], F[1], F[2] - E1};
-                const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
-                R q2[3], p2[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    q2[a] = q[a] + h2 * p[a];
-                    p2[a] = p[a] + h2 * k1p[a];
-                }
-                potential<R, MIXED>(K, q2[0], q2[1], q2[2], ql[0], ql[1], ql[2], V, F[0], F[1], F[2], H2);
-                R k2p[3] = {F[0], F[1], F[2] - E2};
-                const R k2s = R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - q2[2] * E2;
-                R q3[3], p3[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    q3[a] = q[a] + h2 * p2[a];
-                    p3[a] = p[a] + h2 * k2p[a];
-                }
-                potential<R, MIXED>(K, q3[0], q3[1], q3[2], ql[0], ql[1], ql[2], V, F[0], F[1], F[2], H3);
-                R k3p[3] = {F[0], F[1], F[2] - E2};
-                const R k3s = R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - q3[2] * E2;
-                R q4[3], p4[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    q4[a] = q[a] + h * p3[a];
-                    p4[a] = p[a] + h * k3p[a];
-                }
-                potential<R, MIXED>(K, q4[0], q4[1], q4[2], ql[0], ql[1], ql[2], V, F[0], F[1], F[2], H4);
-                const R k4s = R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - q4[2] * E4;
-                const R dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const R k4p = F[a] - (a == 2 ? E4 : R(0));
-                    const R dq = h6 * (p[a] + R(2) * (p2[a] + p3[a]) + p4[a]);
-                    const R dp = h6 * (k1p[a] + R(2) * (k2p[a] + k3p[a]) + k4p);
                     if constexpr (MIXED) {
-                        acc2(q[a], ql[a], dq);
-                        acc2(p[a], pl[a], dp);
+                        acc2(q[a], ql[a], dq[a]);
+                        acc2(p[a], pl[a], dp[a]);
                     } else {
-                        q[a] += dq;
-                        p[a] += dp;
+                        q[a] += dq[a];
+                        p[a] += dp[a];
                     }
                 }
                 if constexpr (MIXED) acc2(S, Sl, dS);
                 else S += dS;
-                // stability-matrix columns with the four stage Hessians
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    R x0[3], v0[3], a1[3], xs[3], vs[3], a2[3], a3[3], a4[3], v2[3], v3[3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        x0[r] = Mq[c][r];
-                        v0[r] = Mp[c][r];
-                    }
-                    neg_hx(H1, x0, a1);
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        xs[r] = x0[r] + h2 * v0[r];
-                        v2[r] = v0[r] + h2 * a1[r];
-                    }
-                    neg_hx(H2, xs, a2);
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        xs[r] = x0[r] + h2 * v2[r];
-                        v3[r] = v0[r] + h2 * a2[r];
-                    }
-                    neg_hx(H3, xs, a3);
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        xs[r] = x0[r] + h * v3[r];
-                        vs[r] = v0[r] + h * a3[r];
-                    }
-                    neg_hx(H4, xs, a4);
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        Mq[c][r] = x0[r] + h6 * (v0[r] + R(2) * (v2[r] + v3[r]) + vs[r]);
-                        Mp[c][r] = v0[r] + h6 * (a1[r] + R(2) * (a2[r] + a3[r]) + a4[r]);
-                    }
-                }
+                const Sym3<R> H0 = Hs[0], H1 = Hs[1], H2 = Hs[2], H3 = Hs[3];
+                const Sym3<R> Hc[4] = {H0, H1, H2, H3};
+                stage_eval<R, MIXED>(K, q, ql, p, E4, E2n, E4n, h, h2, h6, Hs, dq, dp, dS);
+                m_update(Mq, Mp, Hc, h, h2, h6);
+                prefactor_and_checks(Mq, Mp, gam, igam, Cp, q, p, S, cut2, stab, status);
             }
         }
         if (lane < send && bin != R(0))
@@ -503,7 +546,48 @@ __global__ void __launch_bounds__(128, MINB) k_propagate(const DevInstance* __re
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Server slice of the same integrator: items come from a ring, warps stop
+// taking new items once the slice's time is up (an item, once taken, always
+// runs to its end), count finished items per instance, and skip the items of
+// cancelled instances.  No thread waits on another: a warp only ever reads
+// the clock and an atomic counter.
+template <bool MIXED, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+    k_propagate_slice(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ ring,
+                      unsigned int mask, unsigned int base, int n_items,
+                      unsigned int* __restrict__ counter, unsigned long long slice_ns,
+                      unsigned long long* __restrict__ t0)
+{
+    const int lane = threadIdx.x & (kWarp - 1);
+    unsigned long long deadline = 0;
+    if (lane == 0 && slice_ns) {
+        const unsigned long long now = global_ns();
+        const unsigned long long prev = atomicCAS(t0, 0ull, now);
+        deadline = (prev == 0ull ? now : prev) + slice_ns;
+    }
+    deadline = __shfl_sync(kFull, deadline, 0);
+    for (;;) {
+        int it = n_items;
+        if (lane == 0 && (slice_ns == 0 || global_ns() < deadline)) it = (int)atomicAdd(counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;
+        const WorkItem W = ring[(base + (unsigned int)it) & mask];
+        const DevInstance& I = insts[W.inst];
+        if (I.cancel == nullptr || *I.cancel == 0) process_item<MIXED>(I, W, lane);
+        if (lane == 0 && I.done_items != nullptr) atomicAdd(I.done_items, 1u);
+    }
+}
+
 using KernelFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*);
+using SliceFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, unsigned int, int,
+                         unsigned int*, unsigned long long, unsigned long long*);
 
 // variants: index 0 = no register cap, then MINB = 2, 3, 4, 5
 constexpr int kVariantMinb[kPropVariants] = {1, 2, 3, 4, 5};
@@ -519,7 +603,43 @@ KernelFn variant(int precision, int v)
     return precision == SFHK_MIXED ? mixed[v] : fp64[v];
 }
 
+SliceFn slice_variant(int precision, int v)
+{
+    static const SliceFn mixed[kPropVariants] = {
+        k_propagate_slice<true, 1>, k_propagate_slice<true, 2>, k_propagate_slice<true, 3>,
+        k_propagate_slice<true, 4>, k_propagate_slice<true, 5>};
+    static const SliceFn fp64[kPropVariants] = {
+        k_propagate_slice<false, 1>, k_propagate_slice<false, 2>, k_propagate_slice<false, 3>,
+        k_propagate_slice<false, 4>, k_propagate_slice<false, 5>};
+    return precision == SFHK_MIXED ? mixed[v] : fp64[v];
+}
+
 }  // namespace
+
+int launch_propagate_slice(int precision, int variant_index, const DevInstance* insts,
+                           const WorkItem* ring, unsigned int mask, unsigned int base,
+                           int n_items, unsigned int* counter, unsigned long long slice_ns,
+                           unsigned long long* t0, int block_threads, int sm_count,
+                           cudaStream_t s)
+{
+    if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
+    if (variant_index < 0 || variant_index >= kPropVariants || n_items <= 0) return SFHK_E_INVAL;
+    int occ = 0;
+    SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, slice_variant(precision, variant_index), block_threads, 0));
+    if (occ < 1) occ = 1;
+    const int warps_per_block = block_threads / kWarp;
+    int grid = sm_count * occ;
+    const int grid_cap = (n_items + warps_per_block - 1) / warps_per_block;
+    if (grid > grid_cap) grid = grid_cap;
+    SFHK_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+    SFHK_CUDA_TRY(cudaMemsetAsync(t0, 0, sizeof(unsigned long long), s));
+    count_launch();
+    slice_variant(precision, variant_index)<<<grid, block_threads, 0, s>>>(
+        insts, ring, mask, base, n_items, counter, slice_ns, t0);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
 
 int propagate_variant_minb(int v) { return (v >= 0 && v < kPropVariants) ? kVariantMinb[v] : 0; }
 

@@ -61,6 +61,39 @@ class sfhk_stats(C.Structure):
                 ("kernel_ms", C.c_float)]
 
 
+class sfhk_server_opts(C.Structure):
+    _fields_ = [("device_mem_budget", C.c_size_t), ("max_pending", C.c_int),
+                ("max_active", C.c_int), ("precision", C.c_int), ("gamma", C.c_double),
+                ("prefactor_cutoff", C.c_double), ("stability_cutoff", C.c_double),
+                ("slice_ms", C.c_double), ("spectrum", C.c_int), ("fifo", C.c_int)]
+
+
+class sfhk_request(C.Structure):
+    _fields_ = [("target", sfhk_target_desc), ("pulse", sfhk_pulse_desc),
+                ("align", sfhk_align_desc), ("n_traj", C.c_uint64), ("seed", C.c_uint64),
+                ("instance", C.c_uint32)]
+
+
+class sfhk_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("nt", C.c_int), ("t_origin", C.c_double),
+                ("dt", C.c_double), ("n_out", C.c_size_t), ("vz", C.POINTER(C.c_double)),
+                ("vz_capacity", C.c_size_t), ("yield_", C.POINTER(C.c_double)),
+                ("phase", C.POINTER(C.c_double)), ("spec_capacity", C.c_size_t),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("traj_steps", C.c_uint64), ("n_filtered", C.c_uint64),
+                ("n_unstable", C.c_uint64)]
+
+
+class sfhk_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("cancelled", C.c_uint64), ("failed", C.c_uint64), ("slices", C.c_uint64),
+                ("traj_steps", C.c_uint64), ("pending", C.c_int), ("active", C.c_int),
+                ("gpu_busy_s", C.c_double), ("uptime_s", C.c_double),
+                ("device_bytes", C.c_uint64)]
+
+
+SFHK_E_CANCELLED = -8
+
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _lib = None
@@ -99,6 +132,17 @@ def _load():
         "sfhk_dipole": ([_vp, _vp, _dp, C.c_size_t, _dp, _dp], C.c_int),
         "sfhk_spectrum_noalloc": ([_vp, C.c_size_t, C.c_double, C.c_double, C.c_double, _vp,
                                    _vp, _vp, C.c_size_t, _vp], C.c_int),
+        "sfhk_server_create": ([C.c_int, C.POINTER(sfhk_server_opts), C.POINTER(_vp)], C.c_int),
+        "sfhk_server_destroy": ([_vp], C.c_int),
+        "sfhk_submit": ([_vp, C.POINTER(sfhk_request), C.POINTER(C.c_uint64)], C.c_int),
+        "sfhk_poll": ([_vp, C.c_uint64, C.POINTER(sfhk_result)], C.c_int),
+        "sfhk_wait": ([_vp, C.c_uint64, C.c_double, C.POINTER(sfhk_result)], C.c_int),
+        "sfhk_cancel": ([_vp, C.c_uint64], C.c_int),
+        "sfhk_server_stats_get": ([_vp, C.POINTER(sfhk_server_stats)], C.c_int),
+        "sfhk_batch_create": ([_vp, C.POINTER(_vp), C.c_int, C.POINTER(sfhk_run_opts),
+                               C.POINTER(_vp)], C.c_int),
+        "sfhk_batch_launch": ([_vp, _vp], C.c_int),
+        "sfhk_batch_destroy": ([_vp], C.c_int),
         "sfhk_autotune": ([_vp, _vp, C.POINTER(sfhk_run_opts), C.c_int, C.POINTER(C.c_int)],
                           C.c_int),
         "sfhk_dipole_device": ([_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)], C.c_int),
@@ -258,6 +302,22 @@ def sfhk_propagate_batch(ctx, ens_list, opts: sfhk_run_opts, stream=None):
            "sfhk_propagate_batch")
 
 
+def sfhk_batch_create(ctx, ens_list, opts: sfhk_run_opts):
+    arr = (_vp * len(ens_list))(*[e.value if isinstance(e, _vp) else e for e in ens_list])
+    h = _vp()
+    _check(_load().sfhk_batch_create(ctx, arr, len(ens_list), C.byref(opts), C.byref(h)),
+           "sfhk_batch_create")
+    return h
+
+
+def sfhk_batch_launch(batch, stream=None):
+    _check(_load().sfhk_batch_launch(batch, stream), "sfhk_batch_launch")
+
+
+def sfhk_batch_destroy(batch):
+    _check(_load().sfhk_batch_destroy(batch), "sfhk_batch_destroy")
+
+
 def sfhk_autotune(ctx, ens, opts: sfhk_run_opts, max_items=0):
     choice = (C.c_int * 3)()
     _check(_load().sfhk_autotune(ctx, ens, C.byref(opts), max_items, choice), "sfhk_autotune")
@@ -308,6 +368,84 @@ def sfhk_spectrum_device(vz_ptr, nt, dt, t_origin, tau_H, om_ptr, y_ptr, ph_ptr,
 SFHK_NOALLOC_MAX_NT = 32768
 
 
+# ------------------------------------------------------------------ serving
+def server_opts(precision=SFHK_MIXED, gamma=0.5, cutoff=0.0, stab_cutoff=0.0, budget=0,
+                max_pending=0, max_active=0, slice_ms=0.0, spectrum=True, fifo=False):
+    return sfhk_server_opts(budget, max_pending, max_active, precision, gamma, cutoff,
+                            stab_cutoff, slice_ms, int(spectrum), int(fifo))
+
+
+def request(target: dict, pulse: dict, align, n_traj, seed=0, instance=0) -> sfhk_request:
+    return sfhk_request(target_desc(target), pulse_desc(pulse), align_desc(align), n_traj, seed,
+                        instance)
+
+
+def sfhk_server_create(device=0, opts: sfhk_server_opts = None):
+    h = _vp()
+    o = opts if opts is not None else server_opts()
+    _check(_load().sfhk_server_create(device, C.byref(o), C.byref(h)), "sfhk_server_create")
+    return h
+
+
+def sfhk_server_destroy(h):
+    _check(_load().sfhk_server_destroy(h), "sfhk_server_destroy")
+
+
+def sfhk_submit(server, req: sfhk_request):
+    rid = C.c_uint64()
+    _check(_load().sfhk_submit(server, C.byref(req), C.byref(rid)), "sfhk_submit")
+    return rid.value
+
+
+class Result:
+    """Host buffers for one server result and the fields sfhk_poll/sfhk_wait fill."""
+
+    def __init__(self, nt_max=1 << 16):
+        self.vz = np.zeros(nt_max)
+        self.yield_ = np.zeros(nt_max // 2)
+        self.phase = np.zeros(nt_max // 2)
+        self.c = sfhk_result()
+        self.c.vz = _p(self.vz)
+        self.c.vz_capacity = nt_max
+        self.c.yield_ = _p(self.yield_)
+        self.c.phase = _p(self.phase)
+        self.c.spec_capacity = nt_max // 2
+
+    def as_dict(self):
+        c = self.c
+        return dict(status=c.status, nt=c.nt, t_origin=c.t_origin, dt=c.dt,
+                    vz=self.vz[:c.nt].copy(), yield_=self.yield_[:c.n_out].copy(),
+                    phase=self.phase[:c.n_out].copy(), t_submit=c.t_submit, t_admit=c.t_admit,
+                    t_done=c.t_done, traj_steps=c.traj_steps, n_filtered=c.n_filtered,
+                    n_unstable=c.n_unstable)
+
+
+def sfhk_poll(server, rid, res: Result = None):
+    """None while the request is running; its result dict once it has ended."""
+    res = res or Result()
+    rc = _load().sfhk_poll(server, rid, C.byref(res.c))
+    if rc == SFHK_E_BUSY:
+        return None
+    _check(rc, "sfhk_poll")
+    return res.as_dict()
+
+
+def sfhk_wait(server, rid, timeout_s=60.0, res: Result = None):
+    res = res or Result()
+    _check(_load().sfhk_wait(server, rid, timeout_s, C.byref(res.c)), "sfhk_wait")
+    return res.as_dict()
+
+
+def sfhk_cancel(server, rid):
+    _check(_load().sfhk_cancel(server, rid), "sfhk_cancel")
+
+
+def sfhk_server_stats_get(server):
+    st = sfhk_server_stats()
+    _check(_load().sfhk_server_stats_get(server, C.byref(st)), "sfhk_server_stats_get")
+    return {f: getattr(st, f) for f, _ in sfhk_server_stats._fields_}
+
+
 def sfhk_spectrum_noalloc(vz_ptr, nt, dt, t_origin, tau_H, om_ptr, y_ptr, ph_ptr, n_out,
                           stream=None):
     """Device-buffer spectrum that allocates nothing (fixed scratch of
@@ -322,5 +460,7 @@ EXPORTED = [
     "sfhk_load_ensemble", "sfhk_ensemble_read", "sfhk_destroy_ensemble", "sfhk_propagate",
     "sfhk_propagate_batch", "sfhk_dipole", "sfhk_dipole_device", "sfhk_stats_get",
     "sfhk_final_state", "sfhk_spectrum", "sfhk_strerror", "sfhk_sample_into",
-    "sfhk_launch_count", "sfhk_autotune", "sfhk_spectrum_noalloc",
+    "sfhk_launch_count", "sfhk_autotune", "sfhk_spectrum_noalloc", "sfhk_server_create",
+    "sfhk_server_destroy", "sfhk_submit", "sfhk_poll", "sfhk_wait", "sfhk_cancel",
+    "sfhk_server_stats_get", "sfhk_batch_create", "sfhk_batch_launch", "sfhk_batch_destroy",
 ]

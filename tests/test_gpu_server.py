@@ -1,0 +1,143 @@
+"""The continuous-batching server (sfhk_server_* / sfhk_submit / sfhk_poll).
+
+* every request's result equals the same request run alone through
+  sfhk_sample_initial + sfhk_propagate (FP64: to the rounding of the
+  reduction order; mixed precision: 1e-5, the slice kernel being a separate
+  compilation of the same integrator);
+* requests that arrive while another one is running join the running work
+  (admitted before the long one ends) and finish first when they are short;
+* admission follows the device-memory budget; a request larger than the
+  budget is refused at submission; cancellation ends a request.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2608_13686_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2608_13686_b300 import _build
+    _build.build()
+    from paper_2608_13686_b300 import sfhk
+    return sfhk
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+MIX = [("H2", W.PULSE_800, W.fixed(10.0), 3000, 1),
+       ("N2", W.pulse(1000.0, 1.6e14, 2), W.COS2, 2500, 2),
+       ("H2", W.pulse(1400.0, 1.0e14, 4), W.fixed(70.0), 700, 3),
+       ("N2", W.PULSE_1200, W.fixed(40.0), 4100, 4),
+       ("H2", W.pulse(900.0, 1.9e14, 3), W.COS2, 33, 5)]
+
+
+def _alone(S, ctx, name, pulse, align, n, inst, prec):
+    th, ph = S.sfhk_create_target(ctx, W.TARGETS[name]), S.sfhk_set_pulse(ctx, pulse)
+    e = S.sfhk_sample_initial(ctx, th, ph, align, n, 7, inst)
+    S.sfhk_propagate(ctx, e, S.run_opts(prec, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF))
+    vz = S.sfhk_dipole(ctx, e, S.sfhk_pulse_grid(ph)["nt"])
+    S.sfhk_destroy_ensemble(e)
+    S.sfhk_destroy_pulse(ph)
+    S.sfhk_destroy_target(th)
+    return vz
+
+
+@pytest.mark.parametrize("prec_name,tol", [("FP64", 1e-12), ("MIXED", 1e-5)])
+def test_results_in_the_mix_equal_alone(S, prec_name, tol):
+    prec = getattr(S, "SFHK_" + prec_name)
+    srv = S.sfhk_server_create(0, S.server_opts(prec, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
+                                                slice_ms=5.0))
+    ids = [S.sfhk_submit(srv, S.request(W.TARGETS[nm], p, al, n, 7, inst))
+           for nm, p, al, n, inst in MIX]
+    res = [S.sfhk_wait(srv, i, 300.0) for i in ids]
+    st = S.sfhk_server_stats_get(srv)
+    S.sfhk_server_destroy(srv)
+    assert st["completed"] == len(MIX) and st["failed"] == 0
+    ctx = S.sfhk_create(0, 0)
+    for (nm, p, al, n, inst), r in zip(MIX, res):
+        assert r["status"] == S.SFHK_OK
+        ref = _alone(S, ctx, nm, p, al, n, inst, prec)
+        assert r["nt"] == len(ref)
+        assert _rel(r["vz"], ref) <= tol, (nm, n)
+        # the server's spectrum is the spectrum of its dipole
+        om, y, ph = S.sfhk_spectrum(r["vz"], r["dt"], r["t_origin"], -r["t_origin"],
+                                    r["nt"] // 2)
+        assert np.max(np.abs(r["yield_"] - y)) <= 1e-10 * max(y.max(), 1e-300)
+        assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+        assert r["traj_steps"] > 0
+    S.sfhk_destroy(ctx)
+
+
+def test_short_request_joins_a_running_long_one(S):
+    """Short-first admission (the default): a short request submitted while a
+    long one runs is put in front of the long one's queued work items and
+    finishes first; with fifo it waits behind them."""
+    srv = S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
+                                                slice_ms=10.0))
+    long_id = S.sfhk_submit(srv, S.request(W.TARGETS["N2"], W.pulse(1600.0, 1.0e14, 4), W.COS2,
+                                           1_000_000, 1, 0))
+    t0 = time.time()
+    while S.sfhk_server_stats_get(srv)["active"] < 1 and time.time() - t0 < 60:
+        time.sleep(0.005)
+    short_id = S.sfhk_submit(srv, S.request(W.TARGETS["H2"], W.PULSE_800, W.fixed(0.0), 2000,
+                                            1, 1))
+    short = S.sfhk_wait(srv, short_id, 300.0)
+    long = S.sfhk_wait(srv, long_id, 300.0)
+    S.sfhk_server_destroy(srv)
+    assert short["status"] == S.SFHK_OK and long["status"] == S.SFHK_OK
+    assert short["t_admit"] < long["t_done"]      # admitted while the long one ran
+    assert short["t_done"] < long["t_done"]       # and finished first
+    assert long["t_done"] - short["t_done"] > 0.3 * (long["t_done"] - long["t_admit"])
+
+
+def test_admission_by_memory_budget_and_refusal(S):
+    n = 200_000
+    per = n * 110                                   # a request's device state, roughly
+    probe = S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF,
+                                                  W.STAB_CUTOFF))
+    base = S.sfhk_server_stats_get(probe)["device_bytes"]   # the server's own buffers
+    S.sfhk_server_destroy(probe)
+    # room for one request of 200k trajectories, not two
+    budget = base + int(1.5 * per)
+    srv = S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
+                                                budget=budget, slice_ms=10.0))
+    with pytest.raises(S.SfhkError) as e:
+        S.sfhk_submit(srv, S.request(W.TARGETS["H2"], W.PULSE_800, W.fixed(0.0), 10 * n, 1, 0))
+    assert e.value.code == S.SFHK_E_NOMEM
+    ids = [S.sfhk_submit(srv, S.request(W.TARGETS["H2"], W.PULSE_800, W.fixed(a), n, 1, k))
+           for k, a in enumerate((0.0, 30.0, 60.0))]
+    res = [S.sfhk_wait(srv, i, 300.0) for i in ids]
+    st = S.sfhk_server_stats_get(srv)
+    S.sfhk_server_destroy(srv)
+    assert all(r["status"] == S.SFHK_OK for r in res)
+    assert st["rejected"] == 1
+    # only one fits at a time: each is admitted after the previous one is done
+    assert res[1]["t_admit"] >= res[0]["t_done"] - 1e-6
+    assert res[2]["t_admit"] >= res[1]["t_done"] - 1e-6
+
+
+def test_cancel(S):
+    srv = S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
+                                                slice_ms=5.0))
+    big = S.sfhk_submit(srv, S.request(W.TARGETS["N2"], W.pulse(1600.0, 1.0e14, 4), W.COS2,
+                                       1_000_000, 2, 0))
+    queued = S.sfhk_submit(srv, S.request(W.TARGETS["H2"], W.PULSE_800, W.fixed(0.0), 1000, 2, 1))
+    S.sfhk_cancel(srv, queued)
+    S.sfhk_cancel(srv, big)
+    r_big = S.sfhk_wait(srv, big, 300.0)
+    r_q = S.sfhk_wait(srv, queued, 300.0)
+    assert r_big["status"] == S.SFHK_E_CANCELLED and r_q["status"] == S.SFHK_E_CANCELLED
+    # the server keeps serving
+    ok = S.sfhk_submit(srv, S.request(W.TARGETS["H2"], W.PULSE_800, W.fixed(0.0), 500, 2, 2))
+    assert S.sfhk_wait(srv, ok, 300.0)["status"] == S.SFHK_OK
+    with pytest.raises(S.SfhkError) as e:
+        S.sfhk_poll(srv, 987654321)
+    assert e.value.code == S.SFHK_E_NOTFOUND
+    S.sfhk_server_destroy(srv)
