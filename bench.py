@@ -298,7 +298,8 @@ def run_ours(args):
         with torch.cuda.graph(graph, stream=stream):
             step(batch)
         launches_per_step = S.sfhk_launch_count() - l_cap
-        graph.replay()
+        with torch.cuda.stream(stream):
+            graph.replay()
         barrier()
     clock = ClockSampler(local)
     clock.start()
@@ -308,7 +309,8 @@ def run_ours(args):
     ev[0].record(stream)
     for k in range(args.steps):
         if graph is not None:
-            graph.replay()
+            with torch.cuda.stream(stream):     # replay on the stream the events time
+                graph.replay()
         else:
             step(batch)
         ev[k + 1].record(stream)
@@ -337,7 +339,10 @@ def run_ours(args):
     achieved = flops / (prop_ms * 1e-3) / 1e12
     peak = costs.fp32_peak_tflops()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": costs.TRAFFIC.get(args.workload),
+            "frac": achieved / peak,
+            "traffic": (costs.TRAFFIC.get((args.workload, tuned["kernel_variant"] if tuned
+                                           else args.kernel_variant))
+                        if args.n_traj in (0, 1_000_000) else None),
             "kernel": "k_propagate<mixed>", "kernel_ms": prop_ms,
             "flops_per_traj_step": {nm: costs.FLOPS_PER_STEP[nm] for nm in targets},
             "peak_basis": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (unit counts, max clock)"}

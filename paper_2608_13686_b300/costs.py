@@ -39,7 +39,8 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from the last ncu capture, per workload (None until captured for the
-# current kernel)
-TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per full-size launch of the
+# dominant kernel, keyed by (workload, kernel variant), from an ncu capture of
+# the current kernel: H2 0/45/90 deg captured at 3 x 2e5 trajectories (80.5 MB
+# read + 6.8 MB written) and scaled by trajectories to 3 x 1e6.
+TRAFFIC = {("h2-angles", 4): 437.0e6}

@@ -517,13 +517,13 @@ int sfhk_propagate(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, void* 
     SFHK_CUDA_TRY(cudaMemcpyAsync(e->inst.p, &I, sizeof I, cudaMemcpyHostToDevice, s));
     int bt, var, bps;
     shape(c, *o, &bt, &var, &bps);
-    SFHK_CUDA_TRY(cudaEventRecord(e->ev_start, s));
+    SFHK_CUDA_TRY(record_event(e->ev_start, s));
     rc = launch_propagate(o->precision, var, (const DevInstance*)e->inst.p,
                           (const WorkItem*)e->items.p, e->n_items, (unsigned int*)e->qctr.p, bt,
                           bps, c->sm_count, s);
     if (rc) return rc;
-    SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, s));
-    SFHK_CUDA_TRY(cudaEventRecord(e->ev_done, s));
+    SFHK_CUDA_TRY(record_event(e->ev_stop, s));
+    SFHK_CUDA_TRY(record_event(e->ev_done, s));
     e->have_result = true;
     return SFHK_OK;
 }
@@ -595,13 +595,13 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
     int bt, var, bps;
     shape(c, *o, &bt, &var, &bps);
     for (int i = 0; i < n_ens && !rc; ++i)
-        if (cudaEventRecord(ens[i]->ev_start, s) != cudaSuccess) rc = SFHK_E_CUDA;
+        if (record_event(ens[i]->ev_start, s) != cudaSuccess) rc = SFHK_E_CUDA;
     if (!rc)
         rc = launch_propagate(o->precision, var, d_inst, d_sorted, (int)total_items, d_ctr, bt,
                               bps, c->sm_count, s);
     for (int i = 0; i < n_ens && !rc; ++i) {
-        if (cudaEventRecord(ens[i]->ev_stop, s) != cudaSuccess ||
-            cudaEventRecord(ens[i]->ev_done, s) != cudaSuccess)
+        if (record_event(ens[i]->ev_stop, s) != cudaSuccess ||
+            record_event(ens[i]->ev_done, s) != cudaSuccess)
             rc = SFHK_E_CUDA;
         ens[i]->have_result = true;
     }
@@ -713,9 +713,16 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
     if (rc) return rc;
     int bt, var, bps;
     shape(b->ctx, b->opts, &bt, &var, &bps);
+    // the kernel is timed with the ensembles' events (also inside a captured graph)
+    for (sfhk_ensemble* e : b->ens) SFHK_CUDA_TRY(record_event(e->ev_start, s));
     rc = launch_propagate(b->opts.precision, var, b->d_inst, b->d_sorted, (int)b->total_items,
                           b->d_ctr, bt, bps, b->ctx->sm_count, s);
-    return rc;
+    if (rc) return rc;
+    for (sfhk_ensemble* e : b->ens) {
+        SFHK_CUDA_TRY(record_event(e->ev_stop, s));
+        SFHK_CUDA_TRY(record_event(e->ev_done, s));
+    }
+    return SFHK_OK;
 }
 
 int sfhk_batch_destroy(sfhk_batch* b)

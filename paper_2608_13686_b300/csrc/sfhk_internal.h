@@ -178,12 +178,28 @@ DevInstance make_instance(sfhk_ensemble* e, const sfhk_run_opts& o);
 int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s);
 }  // namespace sfhk
 
+// On failure: report, clear the runtime's last-error state (so a later,
+// unrelated launch check does not see it again) and return SFHK_E_CUDA.
 #define SFHK_CUDA_TRY(expr)                                                         \
     do {                                                                            \
         cudaError_t _e = (expr);                                                    \
         if (_e != cudaSuccess) {                                                    \
             std::fprintf(stderr, "sfhk: %s failed: %s (%s:%d)\n", #expr,            \
                          cudaGetErrorString(_e), __FILE__, __LINE__);               \
+            cudaGetLastError();                                                     \
             return SFHK_E_CUDA;                                                     \
         }                                                                           \
     } while (0)
+
+namespace sfhk {
+// Record an event on s; inside a stream capture as an external event node, so
+// that replays of the captured graph record it too.
+inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return cudaGetLastError();
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+               : cudaEventRecord(ev, s);
+}
+}  // namespace sfhk

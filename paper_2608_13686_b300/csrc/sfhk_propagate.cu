@@ -98,8 +98,8 @@ __device__ __forceinline__ R max_abs_M(const R Mq[6][3], const R Mp[6][3])
 }
 
 // (hi, lo) += x with Dekker's FastTwoSum; lo is left unnormalised (it only
-// collects rounding errors, a few ulp of hi per chunk) and folded back by
-// renorm() once per chunk.
+// collects rounding errors, a few ulp of hi) and folded back by renorm()
+// every 32 steps of the trajectory.
 __device__ __forceinline__ void acc2(float& hi, float& lo, float x)
 {
     const float s = __fadd_rn(hi, x);
@@ -335,33 +335,25 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     const R h = R(I.dt), h2 = R(0.5 * I.dt), h6 = R(I.dt / 6.0);
     const int nE = 2 * nt - 1;
 
-    // The step is software-pipelined: the stage evaluations (potentials along
-    // the four RK4 stages, a latency-bound chain) of step n+1 are computed in
-    // the same block as the stability-matrix update of step n (independent,
-    // ILP-rich), so the scheduler interleaves them.  Carried between steps:
-    // the stage Hessians Hs and increments (dq, dp, dS) of the next step.
+    // Carried only within a step: the stage Hessians and increments.
     Sym3<R> Hs[4];
     R dq[3], dp[3], dS;
     for (int nb = W.n_start; nb < nt; nb += kWarp) {
-        // chunk tables: E at the half steps of steps nb+lane and nb+lane+1,
-        // e^{-i Ip t} at nb+lane; broadcast by shuffles
+        // chunk tables: E at the half steps of step nb+lane, e^{-i Ip t} at
+        // nb+lane; broadcast by shuffles
         const int nl = nb + lane;
-        R e0, e1, e2, e3, e4;
+        R e0, e1, e2;
         C2<R> phl;
         if constexpr (MIXED) {
             e0 = I.Ehf[min(2 * nl, nE - 1)];
             e1 = I.Ehf[min(2 * nl + 1, nE - 1)];
             e2 = I.Ehf[min(2 * nl + 2, nE - 1)];
-            e3 = I.Ehf[min(2 * nl + 3, nE - 1)];
-            e4 = I.Ehf[min(2 * nl + 4, nE - 1)];
             const float2 t = I.phf[min(nl, nt - 1)];
             phl = {t.x, t.y};
         } else {
             e0 = I.Eh[min(2 * nl, nE - 1)];
             e1 = I.Eh[min(2 * nl + 1, nE - 1)];
             e2 = I.Eh[min(2 * nl + 2, nE - 1)];
-            e3 = I.Eh[min(2 * nl + 3, nE - 1)];
-            e4 = I.Eh[min(2 * nl + 4, nE - 1)];
             const double2 t = I.ph[min(nl, nt - 1)];
             phl = {t.x, t.y};
         }
@@ -369,15 +361,11 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         const int send = min(kWarp, nt - nb);
         for (int s = 0; s < send; ++s) {
             const int nn = nb + s;
-            const R E1 = shfl(e0, s), E2 = shfl(e1, s), E4 = shfl(e2, s);     // step nn
-            const R E2n = shfl(e3, s), E4n = shfl(e4, s);                     // step nn+1
+            const R E1 = shfl(e0, s), E2 = shfl(e1, s), E4 = shfl(e2, s);
             const C2<R> ph = {shfl(phl.x, s), shfl(phl.y, s)};
             const bool live = (nn >= n0) && status == 0;
-            // ---- birth: checks at t0 (C = 1) and the stage data of the first step
-            if (live && nn == n0) {
-                prefactor_and_checks(Mq, Mp, gam, igam, Cp, q, p, S, cut2, stab, status);
-                stage_eval<R, MIXED>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS);
-            }
+            // ---- prefactor at t_nn (C = 1 at birth) and the checks
+            if (live) prefactor_and_checks(Mq, Mp, gam, igam, Cp, q, p, S, cut2, stab, status);
             // ---- contribution at t_nn: Re[w C e^{iS} e^{-i Ip t} <psi0|k_z|p,q>]
             R x = R(0);
             if (live && status == 0) {
@@ -455,11 +443,10 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     if (lane == s) bin = sv;
                 }
             }
-            // ---- step to t_{nn+1}: apply the increments, advance M with the
-            // carried Hessians, evaluate the stages of the next step (same
-            // block), then the prefactor and checks at t_{nn+1}
+            // ---- one RK4 step to t_{nn+1}
             if (live && status == 0 && nn < nt - 1) {
                 ++steps;
+                stage_eval<R, MIXED>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     if constexpr (MIXED) {
@@ -470,25 +457,26 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                         p[a] += dp[a];
                     }
                 }
-                if constexpr (MIXED) acc2(S, Sl, dS);
-                else S += dS;
-                const Sym3<R> H0 = Hs[0], H1 = Hs[1], H2 = Hs[2], H3 = Hs[3];
-                const Sym3<R> Hc[4] = {H0, H1, H2, H3};
-                stage_eval<R, MIXED>(K, q, ql, p, E4, E2n, E4n, h, h2, h6, Hs, dq, dp, dS);
-                m_update(Mq, Mp, Hc, h, h2, h6);
-                prefactor_and_checks(Mq, Mp, gam, igam, Cp, q, p, S, cut2, stab, status);
+                if constexpr (MIXED) {
+                    acc2(S, Sl, dS);
+                    // fold the low parts back every 32 of this trajectory's own
+                    // steps, so its arithmetic does not depend on its work item
+                    if ((steps & 31) == 0) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            renorm(q[a], ql[a]);
+                            renorm(p[a], pl[a]);
+                        }
+                        renorm(S, Sl);
+                    }
+                } else {
+                    S += dS;
+                }
+                m_update(Mq, Mp, Hs, h, h2, h6);
             }
         }
         if (lane < send && bin != R(0))
             atomicAdd(&I.vz[nb + lane], I.scale * (double(bin) + double(binlo)));
-        if constexpr (MIXED) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                renorm(q[a], ql[a]);
-                renorm(p[a], pl[a]);
-            }
-            renorm(S, Sl);
-        }
         if (!__any_sync(kFull, has && status == 0)) break;
     }
 
