@@ -67,7 +67,9 @@ typedef struct sfhk_server sfhk_server;
 
 /* ---------------------------------------------------------------- descriptors */
 enum { SFHK_POT_MOLECULE = 0, SFHK_POT_HARMONIC = 1 };
-enum { SFHK_ALIGN_FIXED = 0, SFHK_ALIGN_ISOTROPIC = 1, SFHK_ALIGN_COS2 = 2 };
+enum { SFHK_ALIGN_FIXED = 0, SFHK_ALIGN_ISOTROPIC = 1, SFHK_ALIGN_COS2 = 2,
+       SFHK_ALIGN_QUADRATURE = 3 };
+#define SFHK_MAX_QUAD_NODES 64
 enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
 
 /* Target (Eq. 7, Tables I-II): two centres at +-(R/2) n, n the molecular axis,
@@ -95,11 +97,20 @@ typedef struct {
     double lambda_nm, intensity_Wcm2, n_cycles, cep, dt;
 } sfhk_pulse_desc;
 
-/* Orientation distribution (Eqs. 5-6): FIXED axis n(theta, phi); ISOTROPIC;
- * COS2 = axis density proportional to cos^2 theta (<cos^2> = 3/5). */
+/* Orientation distribution (Eqs. 5-6): FIXED axis n(theta, phi); ISOTROPIC
+ * (the joint Monte Carlo over the axis of Eq. 6, one axis per trajectory);
+ * COS2 = axis density proportional to cos^2 theta (<cos^2> = 3/5);
+ * QUADRATURE = the isotropic average done as Eq. 5 with n_nodes fixed
+ * angles: trajectory j sits at cos theta = x_{j mod K}, the K-node
+ * Gauss-Legendre rule on [0, 1] with nodes in descending x (by the
+ * cylindrical and inversion symmetry of a homonuclear diatomic in a linearly
+ * polarised field the average over the axis is int_0^1 f(arccos x) dx), phi
+ * uniform, and its weight is multiplied by K W_{j mod K} (weights summing to
+ * 1), so that the ensemble dipole is sum_k W_k <v_z>_k. */
 typedef struct {
     int kind;
     double theta, phi;                /* radians, FIXED only */
+    int n_nodes;                      /* QUADRATURE only: 1..SFHK_MAX_QUAD_NODES */
 } sfhk_align_desc;
 
 /* Propagation options.
@@ -129,9 +140,9 @@ typedef struct {
     int block_threads;
     int blocks_per_sm;
     double stability_cutoff;
-    int kernel_variant;               /* register-cap variant 1..5 (no cap, then at
-                                         least 2..5 blocks of 128 threads per SM);
-                                         0 = the context's tuned choice */
+    int kernel_variant;               /* register-cap variant 1..6 (no cap, then at
+                                         most 168, 152, 144, 136, 128 registers per
+                                         thread); 0 = the context's tuned choice */
 } sfhk_run_opts;
 
 /* Per-ensemble counters of the last propagation. */
@@ -248,7 +259,7 @@ SFHK_API int sfhk_batch_destroy(sfhk_batch* b);
  * launch is timed with CUDA events, and the fastest becomes the context's
  * default for `opts->precision` (used whenever block_threads or
  * kernel_variant is 0).  choice (may be NULL) receives
- * {block_threads, kernel_variant, min blocks per SM of that variant}.
+ * {block_threads, kernel_variant, register cap of that variant (0 = none)}.
  * Synchronous, on the legacy default stream; the ensemble's dipole is
  * overwritten.  Not a method step: launch configuration only. */
 SFHK_API int sfhk_autotune(sfhk_ctx* ctx, sfhk_ensemble* e, const sfhk_run_opts* opts,
@@ -266,9 +277,10 @@ SFHK_API int sfhk_dipole_device(sfhk_ensemble* e, const double** vz_dev, size_t*
 SFHK_API int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out);
 /* Final per-trajectory state of the last propagation run with dump_final,
  * 47 x n_traj doubles, field-major: q[3] p[3] M[36] (6x6 row-major,
- * M_ab = d a_t / d b_0 for (q,p)) S C_re C_im branch_sign status
- * (0 ok, 1 prefactor-filtered, 2 non-finite, 3 stability-filtered).  For a stopped
- * trajectory the state is the one at the step where it stopped.  Synchronous.
+ * M_ab = d a_t / d b_0 for (q,p)) S C_re C_im n_state status, where n_state is
+ * the time index of the stored state and status is 0 ok, 1 prefactor-filtered,
+ * 2 non-finite, 3 stability-filtered.  For a stopped trajectory the state is the
+ * one at the step where it stopped (n_state = that step).  Synchronous.
  * Errors: SFHK_E_INVAL (no dump taken). */
 SFHK_API int sfhk_final_state(sfhk_ensemble* e, double* host, uint64_t n_traj);
 

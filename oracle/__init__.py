@@ -31,7 +31,7 @@ NY = 43
 
 POT_MOLECULE = 0
 POT_HARMONIC = 1
-ALIGN_FIXED, ALIGN_ISO, ALIGN_COS2 = 0, 1, 2
+ALIGN_FIXED, ALIGN_ISO, ALIGN_COS2, ALIGN_QUAD = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -99,8 +99,9 @@ def lib():
                                 _dp, _dp]
         L.or_adk_table.argtypes = [C.POINTER(PulseIn), C.c_double, _dp, _dp]
         L.or_sample.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int, C.c_double,
-                                C.c_double, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint64,
-                                _dp, _dp]
+                                C.c_double, C.c_int, C.c_uint64, C.c_uint32, C.c_uint64,
+                                C.c_uint64, _dp, _dp]
+        L.or_quad_nodes.argtypes = [C.c_int, _dp, _dp]
         L.or_sample.restype = C.c_int
         L.or_propagate.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
                                    C.c_double, C.c_double, _dp, C.c_uint64, C.c_double, _dp, _dp,
@@ -252,13 +253,26 @@ def adk_table(p, Ip):
 
 
 def sample(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance=0, j_begin=0, n=1):
-    """Initial ensemble as a (12, n) field-major array plus aux (tt, S_down)."""
+    """Initial ensemble as a (12, n) field-major array plus aux (tt, S_down).
+    align = (kind, theta, phi[, n_nodes]); n_nodes is the K of the quadrature
+    kind."""
     soa = np.zeros((NFIELDS, n))
     aux = np.zeros((3, n))
+    k = int(align[3]) if len(align) > 3 else 0
     bad = lib().or_sample(C.byref(target_in(t)), C.byref(pulse_in(p)), int(align[0]),
-                          float(align[1]), float(align[2]), seed, instance, j_begin, n,
+                          float(align[1]), float(align[2]), k, seed, instance, j_begin, n,
                           _p(soa), _p(aux))
+    if bad < 0:
+        raise ValueError("bad alignment")
     return soa, aux, bad
+
+
+def quad_nodes(K):
+    """The oracle's K-node rule on x = cos(theta) in [0, 1] (descending x,
+    weights summing to 1)."""
+    x, w = np.zeros(K), np.zeros(K)
+    lib().or_quad_nodes(K, _p(x), _p(w))
+    return x, w
 
 
 def propagate(t, p, soa, gamma, cutoff=0.0, n_norm=0.0, want_final=False, n_threads=0,

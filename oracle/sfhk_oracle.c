@@ -486,15 +486,10 @@ void or_dipole_matrix_element(const or_target_in* T, const double nhat[3],
     out[0] = creal(m); out[1] = cimag(m);
 }
 
-/* Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on P_n.    */
-#define OR_GL 64
-static double gl_x[OR_GL], gl_w[OR_GL];
-static int gl_ready = 0;
-
-static void gl_init(void)
+/* Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on P_n,     */
+/* nodes in descending order.                                            */
+static void gauss_legendre(int n, double* xs, double* ws)
 {
-    if (gl_ready) return;
-    int n = OR_GL;
     for (int i = 0; i < n; ++i) {
         double x = cos(OR_PI * (i + 0.75) / (n + 0.5));
         double dp = 1.0;
@@ -509,10 +504,41 @@ static void gl_init(void)
             x -= dx;
             if (fabs(dx) < 1e-16) break;
         }
-        gl_x[i] = x;
-        gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+        /* P_n'(x) at the converged node */
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) {
+            double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1; p1 = pk;
+        }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        xs[i] = x;
+        ws[i] = 2.0 / ((1.0 - x * x) * dp * dp);
     }
+}
+
+#define OR_GL 64
+static double gl_x[OR_GL], gl_w[OR_GL];
+static int gl_ready = 0;
+
+static void gl_init(void)
+{
+    if (gl_ready) return;
+    gauss_legendre(OR_GL, gl_x, gl_w);
     gl_ready = 1;
+}
+
+/* K-node Gauss-Legendre rule on x = cos(theta) in [0, 1] (Eq. 5 with the  */
+/* cylindrical and inversion symmetry of a homonuclear diatomic in a      */
+/* linearly polarised field: the isotropic average over the axis reduces  */
+/* to int_0^1 dx f(arccos x)); node k = 0..K-1 in descending x, weights    */
+/* summing to 1.                                                          */
+void or_quad_nodes(int K, double* x01, double* w01)
+{
+    gauss_legendre(K, x01, w01);
+    for (int k = 0; k < K; ++k) {
+        x01[k] = 0.5 * (x01[k] + 1.0);
+        w01[k] = 0.5 * w01[k];
+    }
 }
 
 /* Saddle point (Eq. 2) for t_s = t0 + i tt with given k_perp:           */
@@ -601,7 +627,9 @@ void or_tunnel(const or_pulse_in* Pin, double Ip, double t0, double tt, const do
 /* by inverse CDF (smallest n with CDF_n > u sum W, sequential sums);    */
 /* k_x, k_y ~ N(0, sigma^2), sigma = sqrt(|E(t0)| / (2 sqrt(2 Ip))),     */
 /* by Box-Muller; orientation per trajectory: fixed, isotropic           */
-/* (cos th = 2u-1) or cos^2 (cos th = cbrt(2u-1)), phi = 2 pi u.         */
+/* (cos th = 2u-1) or cos^2 (cos th = cbrt(2u-1)), phi = 2 pi u, or the   */
+/* K-node quadrature of Eq. 5 (cos th = x_{j mod K}, phi = 2 pi u, weight */
+/* times K W_{j mod K}; or_quad_nodes).  Returns -1 for a bad K.          */
 /* The amplitude of the second line of Eq. 1,                            */
 /*   a = <kappa| r.E(t_s) |psi0> / sqrt(E(t_s).kappa) e^{i(S_down + k.q0)}, */
 /* kappa = k + A(t_s) - A(t0), principal square root (reading), and the  */
@@ -610,7 +638,8 @@ void or_tunnel(const or_pulse_in* Pin, double Ip, double t0, double tt, const do
 /*   0 n0 | 1-3 q0 | 4-6 p0 | 7-9 nhat | 10-11 w (re, im).               */
 /* A trajectory whose saddle has no root gets w = 0 (it still counts in N).*/
 /* ------------------------------------------------------------------ */
-enum { OR_ALIGN_FIXED = 0, OR_ALIGN_ISO = 1, OR_ALIGN_COS2 = 2 };
+enum { OR_ALIGN_FIXED = 0, OR_ALIGN_ISO = 1, OR_ALIGN_COS2 = 2, OR_ALIGN_QUAD = 3 };
+#define OR_MAX_QUAD 64
 
 void or_adk_table(const or_pulse_in* Pin, double Ip, double* W, double* cdf)
 {
@@ -626,10 +655,15 @@ void or_adk_table(const or_pulse_in* Pin, double Ip, double* W, double* cdf)
 }
 
 int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
-              double theta, double phi, uint64_t seed, uint32_t instance,
+              double theta, double phi, int n_nodes, uint64_t seed, uint32_t instance,
               uint64_t j_begin, uint64_t n, double* soa, double* aux)
 {
     or_pulse P = or_make_pulse(Pin);
+    double qx[OR_MAX_QUAD], qw[OR_MAX_QUAD];
+    if (align_kind == OR_ALIGN_QUAD) {
+        if (n_nodes < 1 || n_nodes > OR_MAX_QUAD) return -1;
+        or_quad_nodes(n_nodes, qx, qw);
+    }
     double* W = (double*)malloc(sizeof(double) * P.nt);
     double* cdf = (double*)malloc(sizeof(double) * P.nt);
     or_adk_table(Pin, T->Ip, W, cdf);
@@ -659,6 +693,10 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
         } else if (align_kind == OR_ALIGN_COS2) {
             th = acos(cbrt(2.0 * u[3] - 1.0));
             ph = 2.0 * OR_PI * u[4];
+        } else if (align_kind == OR_ALIGN_QUAD) {
+            /* Eq. 5 by quadrature: trajectory j sits at node j mod K */
+            th = acos(qx[j % (uint64_t)n_nodes]);
+            ph = 2.0 * OR_PI * u[4];
         }
         double nhat[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
         /* saddle, exit, action, amplitude */
@@ -677,6 +715,8 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
                          * exp(-(kx * kx + ky * ky) / (2.0 * sigma * sigma))
                          / (2.0 * OR_PI * sigma * sigma);
             w = a / pdf;
+            /* node weight, times K for the 1/N over all K nodes' trajectories */
+            if (align_kind == OR_ALIGN_QUAD) w *= n_nodes * qw[j % (uint64_t)n_nodes];
         } else {
             ++bad;
         }

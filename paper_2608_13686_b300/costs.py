@@ -5,29 +5,32 @@ One trajectory-step = one RK4 step of (q, p, S) with the four stage
 potential/gradient/Hessian evaluations, the six stability-matrix columns
 advanced with the stage Hessians, the Herman-Kluk determinant and its
 continuous square root, and the far-field test of the recombination element.
-Counted from the arithmetic the method needs (FMA = 2 flops, add/mul = 1;
-rsqrt/exp/sincos/sqrt on the special-function unit not counted):
+Counted from the arithmetic of the formulation the kernel uses (FMA = 2
+flops, add/mul = 1; rsqrt/exp/sincos on the special-function unit and the
+Newton step that refines rsqrt are not counted):
 
-  potential at one point, two centres            2 x 40 =  80  (x4 stages = 320)
-    (difference 3, |d|^2 + a^2 6, u^2 u^3 2, V 2, g1 1, g2 2, force 6,
-     g2 d_x, g2 d_y 2, diagonal Hessian 10, off-diagonal 6)
-  stage points, derivatives, actions, RK4 sums               111
-  two-float (compensated) updates of q, p, S: 7 x 10           70
-  stability matrix: 6 columns x (4 Hessian products 60,
-     stage vectors 36, RK4 sums 36)                          792
-  prefactor: B (9 x 6), complex 3x3 determinant 64, root
-     and branch test 9, filter test 4                        131
+  potential at one point, two centres                              68  (x4 stages = 272)
+    per centre 15: difference 3, |d|^2 + a^2 6, u^2 u^3 2, V 1, g1 1, g2 2;
+    sum over centres 38: V 1, force 9, sum of g1 1, g2 d 6,
+    diagonal Hessian 12, off-diagonal 9
+  stage points, derivatives, actions, RK4 sums                    111
+  two-float (compensated) updates of q, p, S: 7 x 10                70
+  stability matrix, 6 columns x 114: stage points 12, four
+    Hessian products 60, stage corrections 12, the two RK4
+    sums 30 (Mq' = Mq + h Mp - h^2/6 sum a, Mp' = Mp - h/6 sum a)  684
+  prefactor: B (9 x 4), complex 3x3 determinant 64 and scale 2,
+    |det| 4, root and branch test 9, filter test 4                 119
   recombination far-field test (|p|^2, d, |d|^2, p.d per
-     centre, exponent per primitive)                          43
+    centre, exponent per primitive)                                 43
   ---------------------------------------------------------------
-  H2 (unscreened centres)                                   1467
-  N2 (screened centres: exp(-alpha s) terms, +30 per point)  1587
+  H2 (unscreened centres)                                         1299
+  N2 (screened centres: exp(-alpha s) terms, +30 per point)       1419
 
 Steps near a nucleus also evaluate the Gaussian overlaps, the phase and the
-warp reduction; they are not counted, so the figure is a lower bound.
+per-step contribution; they are not counted, so the figure is a lower bound.
 """
 
-FLOPS_PER_STEP = {"H2": 1467, "N2": 1587}
+FLOPS_PER_STEP = {"H2": 1299, "N2": 1419}
 
 # FP32 FMA pipe of a B300: 148 SMs x 128 lanes x 2 flops x 2.032 GHz (max SM clock)
 SMS = 148
@@ -41,6 +44,7 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 
 # dram__bytes_read.sum + dram__bytes_write.sum per full-size launch of the
 # dominant kernel, keyed by (workload, kernel variant), from an ncu capture of
-# the current kernel: H2 0/45/90 deg captured at 3 x 2e5 trajectories (80.5 MB
-# read + 6.8 MB written) and scaled by trajectories to 3 x 1e6.
-TRAFFIC = {("h2-angles", 4): 437.0e6}
+# the current kernel: H2 0/45/90 deg captured at 3 x 2e5 trajectories with the
+# 128-register variant (84.6 MB read + 7.4 MB written) and scaled by
+# trajectories to 3 x 1e6.
+TRAFFIC = {("h2-angles", 6): 460.0e6}

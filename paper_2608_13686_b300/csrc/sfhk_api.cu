@@ -383,7 +383,7 @@ int sfhk_sample_initial(sfhk_ctx* c, const sfhk_target* t, const sfhk_pulse* p,
     if (!c || !t || !p || !al || !out) return SFHK_E_INVAL;
     if (n_traj == 0 || n_traj > 2147483647ull) return SFHK_E_INVAL;
     if (!(t->desc.Ip > 0.0) || !(p->E0 > 0.0)) return SFHK_E_INVAL;
-    if (al->kind < SFHK_ALIGN_FIXED || al->kind > SFHK_ALIGN_COS2) return SFHK_E_INVAL;
+    if (!align_valid(*al)) return SFHK_E_INVAL;
     int rc = set_device(c->device);
     if (rc) return rc;
     sfhk_ensemble* e = new (std::nothrow) sfhk_ensemble;
@@ -419,7 +419,7 @@ int sfhk_sample_into(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_align_desc* al, u
                      uint32_t instance, void* stream)
 {
     if (!c || !e || !al || e->ctx != c || !e->sampled) return SFHK_E_INVAL;
-    if (al->kind < SFHK_ALIGN_FIXED || al->kind > SFHK_ALIGN_COS2) return SFHK_E_INVAL;
+    if (!align_valid(*al)) return SFHK_E_INVAL;
     int rc = set_device(c->device);
     if (rc) return rc;
     cudaStream_t s = as_stream(stream);
@@ -777,7 +777,7 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
     if (choice) {
         choice[0] = bb;
         choice[1] = bv + 1;
-        choice[2] = propagate_variant_minb(bv);
+        choice[2] = propagate_variant_maxreg(bv);
     }
     return SFHK_OK;
 }

@@ -178,11 +178,13 @@ struct PotConst {
 // two-float mode the centre is subtracted from q first (exact near a nucleus)
 // and o and l are added to that small difference, so the distance to a nearby
 // nucleus keeps the full two-float precision of the position.
-template <typename R, bool LO>
+// OFS = false: the stage point is the base point itself (o ignored).
+template <typename R, bool LO, bool OFS = true>
 __device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz, R ox, R oy,
                                           R oz, R lx, R ly, R lz, R& V, R& Fx, R& Fy, R& Fz,
                                           Sym3<R>& H)
 {
+    if (!OFS) ox = oy = oz = R(0);
     if (K.kind != 0) {            // harmonic test potential
         const R x = LO ? (qx + ox) + lx : qx + ox;
         const R y = LO ? (qy + oy) + ly : qy + oy;
@@ -195,48 +197,64 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz
         H.xy = H.xz = H.yz = R(0);
         return;
     }
-    V = Fx = Fy = Fz = R(0);
-    H.xx = H.yy = H.zz = H.xy = H.xz = H.yz = R(0);
+    R d[2][3], g1[2], g2[2], vc[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         R dx, dy, dz;
-        if (LO) {
+        if (LO && !OFS) {
+            dx = (c == 0 ? qx - K.cx : qx + K.cx) + lx;
+            dy = (c == 0 ? qy - K.cy : qy + K.cy) + ly;
+            dz = (c == 0 ? qz - K.cz : qz + K.cz) + lz;
+        } else if (LO) {
             dx = ((c == 0 ? qx - K.cx : qx + K.cx) + ox) + lx;
             dy = ((c == 0 ? qy - K.cy : qy + K.cy) + oy) + ly;
             dz = ((c == 0 ? qz - K.cz : qz + K.cz) + oz) + lz;
+        } else if (!OFS) {
+            dx = qx - (c == 0 ? K.cx : -K.cx);
+            dy = qy - (c == 0 ? K.cy : -K.cy);
+            dz = qz - (c == 0 ? K.cz : -K.cz);
         } else {
             dx = (qx + ox) - (c == 0 ? K.cx : -K.cx);
             dy = (qy + oy) - (c == 0 ? K.cy : -K.cy);
             dz = (qz + oz) - (c == 0 ? K.cz : -K.cz);
         }
+        d[c][0] = dx;
+        d[c][1] = dy;
+        d[c][2] = dz;
         const R s2 = dx * dx + dy * dy + dz * dz + K.a2;
         R u = rsqrt_t<R>(s2);
-        if (LO) u = u * (R(1.5) - (R(0.5) * s2 * u) * u);   // one Newton step on 1/sqrt
         const R u2 = u * u, u3 = u2 * u;
-        R g1, g2;
         if (K.screened) {
             const R e = exp_t<R>(-K.alpha * (s2 * u));
             const R de = K.dZ * e;
-            V -= (K.Zinf + de) * u;
-            g1 = K.Zinf * u3 + de * (K.alpha * u2 + u3);
-            g2 = -u2 * (R(3) * K.Zinf * u3 +
-                        de * u * (K.alpha * K.alpha + R(3) * K.alpha * u + R(3) * u2));
+            vc[c] = (K.Zinf + de) * u;
+            g1[c] = K.Zinf * u3 + de * (K.alpha * u2 + u3);
+            g2[c] = -u2 * (R(3) * K.Zinf * u3 +
+                           de * u * (K.alpha * K.alpha + R(3) * K.alpha * u + R(3) * u2));
         } else {
-            V -= K.Zinf * u;
-            g1 = K.Zinf * u3;
-            g2 = R(-3) * K.Zinf * u3 * u2;
+            vc[c] = K.Zinf * u;
+            g1[c] = K.Zinf * u3;
+            g2[c] = R(-3) * K.Zinf * u3 * u2;
         }
-        Fx -= g1 * dx;
-        Fy -= g1 * dy;
-        Fz -= g1 * dz;
-        const R gx = g2 * dx, gy = g2 * dy;
-        H.xx += g1 + gx * dx;
-        H.yy += g1 + gy * dy;
-        H.zz += g1 + g2 * dz * dz;
-        H.xy += gx * dy;
-        H.xz += gx * dz;
-        H.yz += gy * dz;
     }
+    // sum over the two centres: V = -sum vc, F = -sum g1 d,
+    // H = (sum g1) I + sum g2 d d^T
+    V = -(vc[0] + vc[1]);
+    Fx = -(g1[0] * d[0][0] + g1[1] * d[1][0]);
+    Fy = -(g1[0] * d[0][1] + g1[1] * d[1][1]);
+    Fz = -(g1[0] * d[0][2] + g1[1] * d[1][2]);
+    const R gs = g1[0] + g1[1];
+    R gd[2][3];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gd[c][a] = g2[c] * d[c][a];
+    H.xx = gd[0][0] * d[0][0] + (gd[1][0] * d[1][0] + gs);
+    H.yy = gd[0][1] * d[0][1] + (gd[1][1] * d[1][1] + gs);
+    H.zz = gd[0][2] * d[0][2] + (gd[1][2] * d[1][2] + gs);
+    H.xy = gd[0][0] * d[0][1] + gd[1][0] * d[1][1];
+    H.xz = gd[0][0] * d[0][2] + gd[1][0] * d[1][2];
+    H.yz = gd[0][1] * d[0][2] + gd[1][1] * d[1][2];
 }
 
 }  // namespace sfhk

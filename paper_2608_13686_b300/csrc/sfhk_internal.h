@@ -129,6 +129,8 @@ inline void count_launch(int k = 1) { g_launches.fetch_add((unsigned long long)k
 int launch_field_table(const Pulse& P, double* Eh, float* Ehf, cudaStream_t s);
 int launch_phase_table(const Pulse& P, double Ip, double2* ph, float2* phf, cudaStream_t s);
 int launch_adk_cdf(const Pulse& P, double Ip, double* cdf, cudaStream_t s);
+// alignment descriptor within its documented ranges
+bool align_valid(const sfhk_align_desc& al);
 int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, long long n,
                   uint64_t seed, uint32_t instance, const double* cdf, double* soa, int* n0,
                   unsigned long long* n_invalid, cudaStream_t s);
@@ -142,12 +144,12 @@ int launch_sort_items(const WorkItem* in, int n_items, const int* inst_nt, WorkI
                       int* scratch_keys, int* scratch_perm, int* scratch_hist, int K,
                       cudaStream_t s);
 // propagate (sfhk_propagate.cu)
-constexpr int kPropVariants = 5;   // register-cap variants of the integrator
+constexpr int kPropVariants = 6;   // register-cap variants of the integrator
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s);
 int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm);
-int propagate_variant_minb(int variant_index);
+int propagate_variant_maxreg(int variant_index);   // 0 = no cap
 // server slice: items ring[(base + i) & mask], i < n_items; warps stop pulling
 // new items slice_ns after the first warp started (0 = no limit); *t0 must be
 // zero before the launch; *counter ends >= the number of items taken

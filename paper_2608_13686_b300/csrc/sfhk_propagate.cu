@@ -114,15 +114,6 @@ __device__ __forceinline__ void renorm(float& hi, float& lo)
     hi = s;
 }
 
-// y (3-vector) = -H x
-template <typename R>
-__device__ __forceinline__ void neg_hx(const Sym3<R>& H, const R x[3], R y[3])
-{
-    y[0] = -(H.xx * x[0] + H.xy * x[1] + H.xz * x[2]);
-    y[1] = -(H.xy * x[0] + H.yy * x[1] + H.yz * x[2]);
-    y[2] = -(H.xz * x[0] + H.yz * x[1] + H.zz * x[2]);
-}
-
 template <typename R>
 __device__ __forceinline__ R shfl(R v, int src)
 {
@@ -140,8 +131,8 @@ __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], c
 {
     R V, F[3];
     const R z0 = R(0);
-    potential<R, MIXED>(K, q[0], q[1], q[2], z0, z0, z0, ql[0], ql[1], ql[2], V, F[0], F[1],
-                        F[2], H[0]);
+    potential<R, MIXED, false>(K, q[0], q[1], q[2], z0, z0, z0, ql[0], ql[1], ql[2], V, F[0],
+                               F[1], F[2], H[0]);
     const R k1p[3] = {F[0], F[1], F[2] - E1};
     const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
     R o[3], p2[3];
@@ -186,42 +177,48 @@ __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], c
 }
 
 // The six stability-matrix columns advanced by the same RK4 step with the
-// four stage Hessians (dMq/dt = Mp, dMp/dt = -Hess V Mq).
+// four stage Hessians H1..H4 (dMq/dt = Mp, dMp/dt = -Hess V Mq).  With
+// a_i = H_i x_i the stage accelerations (x_1 = Mq, x_2 = Mq + h/2 Mp,
+// x_3 = x_2 - h^2/4 a_1, x_4 = Mq + h Mp - h^2/2 a_2), the RK4 sums collapse to
+//   Mq' = Mq + h Mp - h^2/6 (a_1 + a_2 + a_3)
+//   Mp' = Mp - h/6 (a_1 + 2 a_2 + 2 a_3 + a_4),
+// the same step up to rounding order; every Hessian term enters as a small
+// correction added to the larger part last, so it keeps its own precision.
+template <typename R>
+__device__ __forceinline__ void hx(const Sym3<R>& H, const R x[3], R y[3])
+{
+    y[0] = H.xx * x[0] + H.xy * x[1] + H.xz * x[2];
+    y[1] = H.xy * x[0] + H.yy * x[1] + H.yz * x[2];
+    y[2] = H.xz * x[0] + H.yz * x[1] + H.zz * x[2];
+}
+
 template <typename R>
 __device__ __forceinline__ void m_update(R Mq[6][3], R Mp[6][3], const Sym3<R> H[4], R h, R h2,
-                                         R h6)
+                                         R h6, R hh4, R hh2, R hh6)
 {
+    // hh4 = h^2/4, hh2 = h^2/2, hh6 = h^2/6
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        R x0[3], v0[3], a1[3], xs[3], vs[3], a2[3], a3[3], a4[3], v2[3], v3[3];
+        R x0[3], v0[3], xs[3], xb[3], a1[3], a2[3], a3[3], a4[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             x0[r] = Mq[c][r];
             v0[r] = Mp[c][r];
-        }
-        neg_hx(H[0], x0, a1);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
             xs[r] = x0[r] + h2 * v0[r];
-            v2[r] = v0[r] + h2 * a1[r];
+            xb[r] = x0[r] + h * v0[r];
         }
-        neg_hx(H[1], xs, a2);
+        hx(H[0], x0, a1);
+        hx(H[1], xs, a2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) xs[r] = xs[r] - hh4 * a1[r];
+        hx(H[2], xs, a3);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) xs[r] = xb[r] - hh2 * a2[r];
+        hx(H[3], xs, a4);
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            xs[r] = x0[r] + h2 * v2[r];
-            v3[r] = v0[r] + h2 * a2[r];
-        }
-        neg_hx(H[2], xs, a3);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            xs[r] = x0[r] + h * v3[r];
-            vs[r] = v0[r] + h * a3[r];
-        }
-        neg_hx(H[3], xs, a4);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            Mq[c][r] = x0[r] + h6 * (v0[r] + R(2) * (v2[r] + v3[r]) + vs[r]);
-            Mp[c][r] = v0[r] + h6 * (a1[r] + R(2) * (a2[r] + a3[r]) + a4[r]);
+            Mq[c][r] = xb[r] - hh6 * ((a1[r] + a2[r]) + a3[r]);
+            Mp[c][r] = v0[r] - h6 * ((a1[r] + a4[r]) + R(2) * (a2[r] + a3[r]));
         }
     }
 }
@@ -240,16 +237,20 @@ __device__ __forceinline__ void prefactor_and_checks(const R Mq[6][3], const R M
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            B[3 * r + c] = {R(0.5) * (Mq[c][r] + Mp[3 + c][r]),
-                            R(0.5) * (igam * Mp[c][r] - gam * Mq[3 + c][r])};
+            B[3 * r + c] = {Mq[c][r] + Mp[3 + c][r], igam * Mp[c][r] - gam * Mq[3 + c][r]};
     const C2<R> m0 = cm(B[4], B[8]), m1 = cm(B[5], B[7]);
     const C2<R> m2 = cm(B[3], B[8]), m3 = cm(B[5], B[6]);
     const C2<R> m4 = cm(B[3], B[7]), m5 = cm(B[4], B[6]);
     const C2<R> c0 = cm(B[0], {m0.x - m1.x, m0.y - m1.y});
     const C2<R> c1 = cm(B[1], {m2.x - m3.x, m2.y - m3.y});
     const C2<R> c2 = cm(B[2], {m4.x - m5.x, m4.y - m5.y});
-    const C2<R> det = {c0.x - c1.x + c2.x, c0.y - c1.y + c2.y};
-    const R rdet = hypot_t<R>(det.x, det.y);
+    // det of the half-sum matrix = det(B) / 8
+    const C2<R> det = {R(0.125) * (c0.x - c1.x + c2.x), R(0.125) * (c0.y - c1.y + c2.y)};
+    // |det| from its square where that neither overflows nor underflows
+    R rdet;
+    const R r2 = det.x * det.x + det.y * det.y;
+    if (r2 > R(1e-30) && r2 < R(1e30)) rdet = r2 * rsqrt_t<R>(r2);
+    else rdet = hypot_t<R>(det.x, det.y);
     C2<R> C = csqrt_p(det, rdet);
     if (C.x * Cp.x + C.y * Cp.y < R(0)) {
         C.x = -C.x;
@@ -263,8 +264,14 @@ __device__ __forceinline__ void prefactor_and_checks(const R Mq[6][3], const R M
     else if (stab > R(0) && max_abs_M(Mq, Mp) > stab) status = 3;
 }
 
+// per-warp buffer of the chunk's contributions: 32 steps x 32 trajectories,
+// row stride 33
+constexpr int kRedStride = kWarp + 1;
+constexpr int kRedElems = kWarp * kRedStride;
+
 template <bool MIXED>
-__device__ __forceinline__ void process_item(const DevInstance& I, const WorkItem& W, int lane)
+__device__ __forceinline__ void process_item(const DevInstance& I, const WorkItem& W, int lane,
+                                             typename std::conditional<MIXED, float, double>::type* red)
 {
     using R = typename std::conditional<MIXED, float, double>::type;
 
@@ -308,7 +315,10 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         K1max = fmax(K1max, R(I.rec.K1[k]));
         K2max = fmax(K2max, R(I.rec.K2[k]));
     }
-    constexpr R kSkip = MIXED ? R(-80) : R(-200);
+    // a Gaussian overlap below e^kSkip of its peak is not evaluated: in MIXED
+    // such a term is below 1e-13 of the same trajectory's terms near the
+    // nucleus, far under the FP32 resolution of the sum
+    constexpr R kSkip = MIXED ? R(-30) : R(-200);
 
     // ---- state
     R q[3], p[3], ql[3], pl[3];
@@ -333,6 +343,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     unsigned long long steps = 0;
 
     const R h = R(I.dt), h2 = R(0.5 * I.dt), h6 = R(I.dt / 6.0);
+    const R hh4 = R(I.dt * I.dt / 4.0), hh2 = R(I.dt * I.dt / 2.0), hh6 = R(I.dt * I.dt / 6.0);
     const int nE = 2 * nt - 1;
 
     // Carried only within a step: the stage Hessians and increments.
@@ -357,7 +368,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             const double2 t = I.ph[min(nl, nt - 1)];
             phl = {t.x, t.y};
         }
-        R bin = R(0), binlo = R(0);    // this lane's step of the chunk (two-float in MIXED)
+        bool contributed = false;
         const int send = min(kWarp, nt - nb);
         for (int s = 0; s < send; ++s) {
             const int nn = nb + s;
@@ -420,29 +431,9 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     x = b.x * Rk.x - b.y * Rk.y;
                 }
             }
-            // ---- warp sum (skipped when no lane contributes)
-            if (__any_sync(kFull, x != R(0))) {
-                if constexpr (MIXED) {
-                    float sv = x, ev = 0.0f;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const float so = __shfl_xor_sync(kFull, sv, off);
-                        const float eo = __shfl_xor_sync(kFull, ev, off);
-                        float t;
-                        two_sum(sv, so, sv, t);
-                        ev = ev + eo + t;
-                    }
-                    if (lane == s) {
-                        bin = sv;
-                        binlo = ev;
-                    }
-                } else {
-                    double sv = x;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(kFull, sv, off);
-                    if (lane == s) bin = sv;
-                }
-            }
+            // ---- this step's contribution, summed over the warp after the chunk
+            red[s * kRedStride + lane] = x;
+            contributed |= (x != R(0));
             // ---- one RK4 step to t_{nn+1}
             if (live && status == 0 && nn < nt - 1) {
                 ++steps;
@@ -472,11 +463,33 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                 } else {
                     S += dS;
                 }
-                m_update(Mq, Mp, Hs, h, h2, h6);
+                m_update(Mq, Mp, Hs, h, h2, h6, hh4, hh2, hh6);
             }
         }
-        if (lane < send && bin != R(0))
-            atomicAdd(&I.vz[nb + lane], I.scale * (double(bin) + double(binlo)));
+        // lane l sums row l (step nb + l) over the 32 trajectories: two-float
+        // in MIXED; rows are 33 apart so that both the writes above and these
+        // reads hit 32 different banks
+        __syncwarp();
+        if (__any_sync(kFull, contributed) && lane < send) {
+            const R* row = red + lane * kRedStride;
+            if constexpr (MIXED) {
+                float sv = 0.0f, ev = 0.0f;
+#pragma unroll 8
+                for (int k = 0; k < kWarp; ++k) {
+                    float t;
+                    two_sum(sv, row[k], sv, t);
+                    ev += t;
+                }
+                if (sv != 0.0f || ev != 0.0f)
+                    atomicAdd(&I.vz[nb + lane], I.scale * (double(sv) + double(ev)));
+            } else {
+                double sv = 0.0;
+#pragma unroll 8
+                for (int k = 0; k < kWarp; ++k) sv += row[k];
+                if (sv != 0.0) atomicAdd(&I.vz[nb + lane], I.scale * sv);
+            }
+        }
+        __syncwarp();
         if (!__any_sync(kFull, has && status == 0)) break;
     }
 
@@ -510,19 +523,20 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         d[(size_t)42 * n + j] = double(S) + (MIXED ? double(Sl) : 0.0);
         d[(size_t)43 * n + j] = double(Cp.x);
         d[(size_t)44 * n + j] = double(Cp.y);
-        d[(size_t)45 * n + j] = 0.0;
+        d[(size_t)45 * n + j] = double(n0 + (long long)steps);   // time index of this state
         d[(size_t)46 * n + j] = double(status);
     }
 }
 
-// MINB caps the registers (launch bounds: at least MINB blocks of 128 threads
-// per SM); the autotuner picks among the variants.
-template <bool MIXED, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_propagate(const DevInstance* __restrict__ insts,
-                                                         const WorkItem* __restrict__ items,
-                                                         int n_items,
-                                                         unsigned int* __restrict__ counter)
+// The persistent loop over the work-item queue.
+template <bool MIXED>
+__device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
+                                          const WorkItem* __restrict__ items, int n_items,
+                                          unsigned int* __restrict__ counter)
 {
+    using R = typename std::conditional<MIXED, float, double>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* red = reinterpret_cast<R*>(smem_raw) + (threadIdx.x / kWarp) * kRedElems;
     const int lane = threadIdx.x & (kWarp - 1);
     for (;;) {
         int it = 0;
@@ -530,7 +544,7 @@ __global__ void __launch_bounds__(128, MINB) k_propagate(const DevInstance* __re
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const WorkItem W = items[it];
-        process_item<MIXED>(insts[W.inst], W, lane);
+        process_item<MIXED>(insts[W.inst], W, lane, red);
     }
 }
 
@@ -546,13 +560,17 @@ __device__ __forceinline__ unsigned long long global_ns()
 // runs to its end), count finished items per instance, and skip the items of
 // cancelled instances.  No thread waits on another: a warp only ever reads
 // the clock and an atomic counter.
-template <bool MIXED, int MINB>
-__global__ void __launch_bounds__(128, MINB)
-    k_propagate_slice(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ ring,
-                      unsigned int mask, unsigned int base, int n_items,
-                      unsigned int* __restrict__ counter, unsigned long long slice_ns,
-                      unsigned long long* __restrict__ t0)
+template <bool MIXED>
+__device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
+                                          const WorkItem* __restrict__ ring, unsigned int mask,
+                                          unsigned int base, int n_items,
+                                          unsigned int* __restrict__ counter,
+                                          unsigned long long slice_ns,
+                                          unsigned long long* __restrict__ t0)
 {
+    using R = typename std::conditional<MIXED, float, double>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* red = reinterpret_cast<R*>(smem_raw) + (threadIdx.x / kWarp) * kRedElems;
     const int lane = threadIdx.x & (kWarp - 1);
     unsigned long long deadline = 0;
     if (lane == 0 && slice_ns) {
@@ -568,38 +586,83 @@ __global__ void __launch_bounds__(128, MINB)
         if (it >= n_items) break;
         const WorkItem W = ring[(base + (unsigned int)it) & mask];
         const DevInstance& I = insts[W.inst];
-        if (I.cancel == nullptr || *I.cancel == 0) process_item<MIXED>(I, W, lane);
+        if (I.cancel == nullptr || *I.cancel == 0) process_item<MIXED>(I, W, lane, red);
         if (lane == 0 && I.done_items != nullptr) atomicAdd(I.done_items, 1u);
     }
+}
+
+// Register-cap variants of both kernels: no cap, or at most MAXREG registers
+// per thread (more resident warps, possibly spills); the autotuner picks.
+template <bool MIXED>
+__global__ void __launch_bounds__(128)
+    k_propagate_nocap(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ items,
+                      int n_items, unsigned int* __restrict__ counter)
+{
+    run_queue<MIXED>(insts, items, n_items, counter);
+}
+template <bool MIXED, int MAXREG>
+__global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
+    k_propagate(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ items,
+                int n_items, unsigned int* __restrict__ counter)
+{
+    run_queue<MIXED>(insts, items, n_items, counter);
+}
+template <bool MIXED>
+__global__ void __launch_bounds__(128)
+    k_propagate_slice_nocap(const DevInstance* __restrict__ insts,
+                            const WorkItem* __restrict__ ring, unsigned int mask,
+                            unsigned int base, int n_items, unsigned int* __restrict__ counter,
+                            unsigned long long slice_ns, unsigned long long* __restrict__ t0)
+{
+    run_slice<MIXED>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
+}
+template <bool MIXED, int MAXREG>
+__global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
+    k_propagate_slice(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ ring,
+                      unsigned int mask, unsigned int base, int n_items,
+                      unsigned int* __restrict__ counter, unsigned long long slice_ns,
+                      unsigned long long* __restrict__ t0)
+{
+    run_slice<MIXED>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
 }
 
 using KernelFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*);
 using SliceFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, unsigned int, int,
                          unsigned int*, unsigned long long, unsigned long long*);
 
-// variants: index 0 = no register cap, then MINB = 2, 3, 4, 5
-constexpr int kVariantMinb[kPropVariants] = {1, 2, 3, 4, 5};
+// variants: index 0 = no register cap, then at most 168, 152, 144, 136, 128
+// registers per thread (12 to 16 resident warps per SM)
+constexpr int kVariantMaxReg[kPropVariants] = {0, 168, 152, 144, 136, 128};
 
 KernelFn variant(int precision, int v)
 {
     static const KernelFn mixed[kPropVariants] = {
-        k_propagate<true, 1>, k_propagate<true, 2>, k_propagate<true, 3>, k_propagate<true, 4>,
-        k_propagate<true, 5>};
+        k_propagate_nocap<true>, k_propagate<true, 168>, k_propagate<true, 152>,
+        k_propagate<true, 144>, k_propagate<true, 136>, k_propagate<true, 128>};
     static const KernelFn fp64[kPropVariants] = {
-        k_propagate<false, 1>, k_propagate<false, 2>, k_propagate<false, 3>,
-        k_propagate<false, 4>, k_propagate<false, 5>};
+        k_propagate_nocap<false>, k_propagate<false, 168>, k_propagate<false, 152>,
+        k_propagate<false, 144>, k_propagate<false, 136>, k_propagate<false, 128>};
     return precision == SFHK_MIXED ? mixed[v] : fp64[v];
 }
 
 SliceFn slice_variant(int precision, int v)
 {
     static const SliceFn mixed[kPropVariants] = {
-        k_propagate_slice<true, 1>, k_propagate_slice<true, 2>, k_propagate_slice<true, 3>,
-        k_propagate_slice<true, 4>, k_propagate_slice<true, 5>};
+        k_propagate_slice_nocap<true>, k_propagate_slice<true, 168>,
+        k_propagate_slice<true, 152>, k_propagate_slice<true, 144>,
+        k_propagate_slice<true, 136>, k_propagate_slice<true, 128>};
     static const SliceFn fp64[kPropVariants] = {
-        k_propagate_slice<false, 1>, k_propagate_slice<false, 2>, k_propagate_slice<false, 3>,
-        k_propagate_slice<false, 4>, k_propagate_slice<false, 5>};
+        k_propagate_slice_nocap<false>, k_propagate_slice<false, 168>,
+        k_propagate_slice<false, 152>, k_propagate_slice<false, 144>,
+        k_propagate_slice<false, 136>, k_propagate_slice<false, 128>};
     return precision == SFHK_MIXED ? mixed[v] : fp64[v];
+}
+
+// dynamic shared memory of a block: one contribution buffer per warp
+size_t red_bytes(int precision, int block_threads)
+{
+    const size_t elem = precision == SFHK_MIXED ? sizeof(float) : sizeof(double);
+    return size_t(block_threads / kWarp) * kRedElems * elem;
 }
 
 }  // namespace
@@ -613,8 +676,9 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     if (variant_index < 0 || variant_index >= kPropVariants || n_items <= 0) return SFHK_E_INVAL;
     int occ = 0;
+    const size_t smem = red_bytes(precision, block_threads);
     SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, slice_variant(precision, variant_index), block_threads, 0));
+        &occ, slice_variant(precision, variant_index), block_threads, smem));
     if (occ < 1) occ = 1;
     const int warps_per_block = block_threads / kWarp;
     int grid = sm_count * occ;
@@ -623,19 +687,21 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
     SFHK_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
     SFHK_CUDA_TRY(cudaMemsetAsync(t0, 0, sizeof(unsigned long long), s));
     count_launch();
-    slice_variant(precision, variant_index)<<<grid, block_threads, 0, s>>>(
+    slice_variant(precision, variant_index)<<<grid, block_threads, smem, s>>>(
         insts, ring, mask, base, n_items, counter, slice_ns, t0);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
 }
 
-int propagate_variant_minb(int v) { return (v >= 0 && v < kPropVariants) ? kVariantMinb[v] : 0; }
+int propagate_variant_maxreg(int v) { return (v >= 0 && v < kPropVariants) ? kVariantMaxReg[v] : 0; }
 
 int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm)
 {
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
+    if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, variant(precision, variant_index), block_threads, 0));
+        blocks_per_sm, variant(precision, variant_index), block_threads,
+        red_bytes(precision, block_threads)));
     return SFHK_OK;
 }
 
@@ -657,8 +723,8 @@ int launch_propagate(int precision, int variant_index, const DevInstance* insts,
     if (grid < 1) grid = 1;
     SFHK_CUDA_TRY(cudaMemsetAsync(item_counter, 0, sizeof(unsigned int), s));
     count_launch();
-    variant(precision, variant_index)<<<grid, block_threads, 0, s>>>(insts, items, n_items,
-                                                                    item_counter);
+    variant(precision, variant_index)<<<grid, block_threads, red_bytes(precision, block_threads),
+                                        s>>>(insts, items, n_items, item_counter);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
 }

@@ -14,6 +14,8 @@
 //   with the analytic Fourier transform of the Gaussian orbital; w = a / pdf.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "sfhk_device.cuh"
 #include "sfhk_internal.h"
 
@@ -96,6 +98,8 @@ struct SampleParams {
     double Ip;
     int align_kind;
     double theta, phi;
+    int n_nodes;                              // quadrature: K, nodes x_k and weights K W_k
+    double qx[SFHK_MAX_QUAD_NODES], qkw[SFHK_MAX_QUAD_NODES];
     uint64_t seed;
     uint32_t instance;
     long long n;
@@ -105,24 +109,22 @@ struct SampleParams {
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
 };
 
-// int_0^T sin(th + i k s) ds and int_0^T cos(al + i be s) ds
-__device__ __forceinline__ double2 int_sin(double th, double k, double T)
+// sinh x and cosh x - 1 from em = e^x - 1, without cancellation
+__device__ __forceinline__ void sh_cm1(double em, double& sh, double& cm1)
 {
-    if (k == 0.0) return make_double2(T * sin(th), 0.0);
-    double s, c;
-    sincos(th, &s, &c);
-    const double x = k * T;
-    const double cm1 = 2.0 * sinh(0.5 * x) * sinh(0.5 * x);   // cosh x - 1
-    return make_double2(s * sinh(x) / k, c * cm1 / k);
+    const double d = 0.5 / (em + 1.0);
+    sh = em * (em + 2.0) * d;
+    cm1 = em * em * d;
 }
-__device__ __forceinline__ double2 int_cos(double al, double be, double T)
+
+// int_0^T cos(al + i be s) ds = (cos(al) sinh(x) - i sin(al) (cosh x - 1)) / be,
+// x = be T, given cos(al), sin(al) and em = e^x - 1
+__device__ __forceinline__ double2 int_cos(double ca, double sa, double be, double em, double T)
 {
-    if (be == 0.0) return make_double2(T * cos(al), 0.0);
-    double s, c;
-    sincos(al, &s, &c);
-    const double x = be * T;
-    const double cm1 = 2.0 * sinh(0.5 * x) * sinh(0.5 * x);
-    return make_double2(c * sinh(x) / be, -s * cm1 / be);
+    if (be == 0.0) return make_double2(T * ca, 0.0);
+    double sh, cm1;
+    sh_cm1(em, sh, cm1);
+    return make_double2(ca * sh / be, -sa * cm1 / be);
 }
 
 __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double* __restrict__ soa,
@@ -165,6 +167,9 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
     } else if (S.align_kind == SFHK_ALIGN_COS2) {
         th = acos(cbrt(2.0 * u[3] - 1.0));
         phv = 2.0 * kPi * u[4];
+    } else if (S.align_kind == SFHK_ALIGN_QUADRATURE) {
+        th = acos(S.qx[j % S.n_nodes]);
+        phv = 2.0 * kPi * u[4];
     }
     double sth, cth, sph, cph;
     sincos(th, &sth, &cth);
@@ -183,16 +188,20 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
     if (ok) {
         // ---- saddle point: g(s) = Y(s) - Y*, Y(s) = sum a cos(th) sinh(k s)
         const double Ystar = (Et0 > 0.0 ? -1.0 : 1.0) * sqrt(target);
+        double ac[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ac[q] = S.P.a[q] * cthm[q];
+        // Y(s) - Y* and Y'(s), sinh and cosh from one exponential per term
         auto g = [&](double s, double* dg) {
             double y = 0.0, yp = 0.0;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const double ks = S.P.k[q] * s;
-                y += S.P.a[q] * cthm[q] * sinh(ks);
-                yp += S.P.a[q] * S.P.k[q] * cthm[q] * cosh(ks);
+                const double e = exp(S.P.k[q] * s), ie = 1.0 / e;
+                y += ac[q] * (e - ie);
+                yp += ac[q] * S.P.k[q] * (e + ie);
             }
-            *dg = yp;
-            return y - Ystar;
+            *dg = 0.5 * yp;
+            return 0.5 * y - Ystar;
         };
         const double s0 = sqrt(target) / fabs(Et0);
         const double sg0 = -Ystar;     // g(0)
@@ -207,24 +216,31 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
             ghi = g(shi, &dg);
         }
         if (ok) {
-            double s = 0.5 * (slo + shi);
+            // safeguarded Newton from the bracket's upper end, where g and g'
+            // are already known
+            double s = shi, gs = ghi;
             for (int it = 0; it < 200; ++it) {
-                const double gs = g(s, &dg);
-                if (gs == 0.0) { slo = shi = s; break; }
+                if (gs == 0.0) break;
                 if ((gs > 0.0) == (sg0 > 0.0)) slo = s; else shi = s;
                 double sn = s - gs / dg;
                 if (!(sn > slo && sn < shi)) sn = 0.5 * (slo + shi);
-                if (fabs(sn - s) <= 4e-16 * s || shi - slo <= 4e-16 * shi) { s = sn; break; }
+                const bool done = fabs(sn - s) <= 4e-16 * s || shi - slo <= 4e-16 * shi;
                 s = sn;
+                if (done) break;
+                gs = g(s, &dg);
             }
             tt = s;
-            // ---- k_z, exit and action in closed form
+            // ---- k_z, exit and action in closed form; em[q] = e^{k_q tt} - 1
+            double em[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) em[q] = expm1(S.P.k[q] * tt);
             double At0 = 0.0, dRe = 0.0, q0 = 0.0, Yt = 0.0;
             double2 Es = make_double2(0.0, 0.0);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const double a = S.P.a[q], k = S.P.k[q], x = k * tt;
-                const double sh = sinh(x), cm1 = 2.0 * sinh(0.5 * x) * sinh(0.5 * x);
+                const double a = S.P.a[q], k = S.P.k[q];
+                double sh, cm1;
+                sh_cm1(em[q], sh, cm1);
                 At0 += a * sthm[q];
                 dRe += a * sthm[q] * cm1;                  // Re A(t_s) - A(t0)
                 Yt += a * cthm[q] * sh;                    // Im A(t_s)
@@ -238,17 +254,34 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
             const double2 kapz = make_double2(kz + dRe, Yt);
             // int_0^tt B(s)^2 ds, B = c' + sum a sin(th + i k s), c' = kz - A(t0)
             const double cp = kz - At0;
+            // int_0^tt sin(th + i k s) ds = (sin th sinh x + i cos th (cosh x - 1)) / k
+            // with x = k tt; the products sin(th_q + i k_q s) sin(th_r + i k_r s)
+            // = [cos(difference) - cos(sum)] / 2, the (q, r) and (r, q) terms
+            // equal, e^{(k_q -+ k_r) tt} - 1 formed from em[q] and em[r].
             double2 IB = make_double2(cp * cp * tt, 0.0);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const double2 is = int_sin(S.P.k[q] * t0 + S.P.cep, S.P.k[q], tt);
+                const double k = S.P.k[q];
+                double2 is;
+                if (k == 0.0) {
+                    is = make_double2(tt * sthm[q], 0.0);
+                } else {
+                    double sh, cm1;
+                    sh_cm1(em[q], sh, cm1);
+                    is = make_double2(sthm[q] * sh / k, cthm[q] * cm1 / k);
+                }
                 IB = cadd(IB, cscale(is, 2.0 * cp * S.P.a[q]));
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    const double thq = S.P.k[q] * t0 + S.P.cep, thr = S.P.k[r] * t0 + S.P.cep;
-                    const double2 d1 = int_cos(thq - thr, S.P.k[q] - S.P.k[r], tt);
-                    const double2 d2 = int_cos(thq + thr, S.P.k[q] + S.P.k[r], tt);
-                    IB = cadd(IB, cscale(csub(d1, d2), 0.5 * S.P.a[q] * S.P.a[r]));
+                for (int r = q; r < 3; ++r) {
+                    const double cc = cthm[q] * cthm[r], ss = sthm[q] * sthm[r];
+                    const double sc = sthm[q] * cthm[r], cs = cthm[q] * sthm[r];
+                    const double emd = (em[q] - em[r]) / (1.0 + em[r]);
+                    const double ems = em[q] + em[r] + em[q] * em[r];
+                    const double2 d1 = q == r ? make_double2(tt, 0.0)
+                                              : int_cos(cc + ss, sc - cs, S.P.k[q] - S.P.k[r], emd, tt);
+                    const double2 d2 = int_cos(cc - ss, sc + cs, S.P.k[q] + S.P.k[r], ems, tt);
+                    const double f = (q == r ? 0.5 : 1.0) * S.P.a[q] * S.P.a[r];
+                    IB = cadd(IB, cscale(csub(d1, d2), f));
                 }
             }
             // S_down = Ip (t0 + i tt) + (i/2)(kp2 tt + IB)
@@ -284,7 +317,9 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
             const double Wm = exp(-cst / fabs(Et0));
             const double pdf = (Wm / total) / S.dt * exp(-kp2 / (2.0 * sigma * sigma)) /
                                (2.0 * kPi * sigma * sigma);
-            w = make_double2(amp.x / pdf, amp.y / pdf);
+            // the quadrature node's weight K W_k (1 otherwise)
+            const double f = S.align_kind == SFHK_ALIGN_QUADRATURE ? S.qkw[j % S.n_nodes] : 1.0;
+            w = make_double2(f * amp.x / pdf, f * amp.y / pdf);
         }
     }
     if (!ok) atomicAdd(n_invalid, 1ull);
@@ -415,11 +450,61 @@ int launch_adk_cdf(const Pulse& P, double Ip, double* cdf, cudaStream_t s)
     return SFHK_OK;
 }
 
+bool align_valid(const sfhk_align_desc& al)
+{
+    if (al.kind == SFHK_ALIGN_QUADRATURE)
+        return al.n_nodes >= 1 && al.n_nodes <= SFHK_MAX_QUAD_NODES;
+    return al.kind == SFHK_ALIGN_FIXED || al.kind == SFHK_ALIGN_ISOTROPIC ||
+           al.kind == SFHK_ALIGN_COS2;
+}
+
+// K-point Gauss-Legendre rule on [0, 1]: the roots of P_K by Newton's method
+// from the estimate cos(pi (i + 3/4) / (K + 1/2)), P_K and P_K' by the
+// three-term recurrence, weights 2 / ((1 - x^2) P_K'(x)^2) on [-1, 1], then
+// mapped to [0, 1] (x -> (1 + x)/2, w -> w/2); nodes in descending order.
+void quadrature_nodes(int K, double* x01, double* w01)
+{
+    for (int i = 0; i < K; ++i) {
+        double x = std::cos(kPi * (i + 0.75) / (K + 0.5));
+        double pk = 0.0, dpk = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double pm = 1.0;
+            pk = x;
+            for (int m = 2; m <= K; ++m) {
+                const double pn = ((2 * m - 1) * x * pk - (m - 1) * pm) / m;
+                pm = pk;
+                pk = pn;
+            }
+            dpk = K * (pm - x * pk) / (1.0 - x * x);
+            const double step = pk / dpk;
+            x -= step;
+            if (std::fabs(step) <= 1e-16) break;
+        }
+        double pm = 1.0;
+        pk = x;
+        for (int m = 2; m <= K; ++m) {
+            const double pn = ((2 * m - 1) * x * pk - (m - 1) * pm) / m;
+            pm = pk;
+            pk = pn;
+        }
+        dpk = K * (pm - x * pk) / (1.0 - x * x);
+        x01[i] = 0.5 * (1.0 + x);
+        w01[i] = 1.0 / ((1.0 - x * x) * dpk * dpk);
+    }
+}
+
 int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, long long n,
                   uint64_t seed, uint32_t instance, const double* cdf, double* soa, int* n0,
                   unsigned long long* n_invalid, cudaStream_t s)
 {
+    if (!align_valid(al)) return SFHK_E_INVAL;
     SampleParams S;
+    S.n_nodes = al.kind == SFHK_ALIGN_QUADRATURE ? al.n_nodes : 1;
+    for (int k = 0; k < SFHK_MAX_QUAD_NODES; ++k) S.qx[k] = S.qkw[k] = 0.0;
+    if (al.kind == SFHK_ALIGN_QUADRATURE) {
+        quadrature_nodes(al.n_nodes, S.qx, S.qkw);
+        for (int k = 0; k < al.n_nodes; ++k) S.qkw[k] *= al.n_nodes;
+    }
     S.P = pulse_terms(P.omega, P.E0, P.Tp, P.desc.cep);
     S.omega = P.omega;
     S.E0 = P.E0;

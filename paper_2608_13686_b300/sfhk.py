@@ -20,7 +20,7 @@ SFHK_E_INVAL, SFHK_E_NOMEM, SFHK_E_CUDA = -1, -2, -3
 SFHK_E_TIMEOUT, SFHK_E_NUMERIC, SFHK_E_BUSY, SFHK_E_NOTFOUND = -4, -5, -6, -7
 SFHK_MAX_PRIM = 8
 SFHK_POT_MOLECULE, SFHK_POT_HARMONIC = 0, 1
-SFHK_ALIGN_FIXED, SFHK_ALIGN_ISOTROPIC, SFHK_ALIGN_COS2 = 0, 1, 2
+SFHK_ALIGN_FIXED, SFHK_ALIGN_ISOTROPIC, SFHK_ALIGN_COS2, SFHK_ALIGN_QUADRATURE = 0, 1, 2, 3
 SFHK_FP64, SFHK_MIXED = 0, 1
 SOA_FIELDS = 12
 FINAL_FIELDS = 47
@@ -45,7 +45,8 @@ class sfhk_pulse_desc(C.Structure):
 
 
 class sfhk_align_desc(C.Structure):
-    _fields_ = [("kind", C.c_int), ("theta", C.c_double), ("phi", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("theta", C.c_double), ("phi", C.c_double),
+                ("n_nodes", C.c_int)]
 
 
 class sfhk_run_opts(C.Structure):
@@ -198,7 +199,8 @@ def pulse_desc(p: dict) -> sfhk_pulse_desc:
 
 
 def align_desc(a) -> sfhk_align_desc:
-    return sfhk_align_desc(int(a[0]), float(a[1]), float(a[2]))
+    """(kind, theta, phi[, n_nodes])"""
+    return sfhk_align_desc(int(a[0]), float(a[1]), float(a[2]), int(a[3]) if len(a) > 3 else 0)
 
 
 def run_opts(precision=SFHK_FP64, gamma=0.5, cutoff=0.0, dump=False, block_threads=0,
@@ -321,7 +323,7 @@ def sfhk_batch_destroy(batch):
 def sfhk_autotune(ctx, ens, opts: sfhk_run_opts, max_items=0):
     choice = (C.c_int * 3)()
     _check(_load().sfhk_autotune(ctx, ens, C.byref(opts), max_items, choice), "sfhk_autotune")
-    return dict(block_threads=choice[0], kernel_variant=choice[1], min_blocks=choice[2])
+    return dict(block_threads=choice[0], kernel_variant=choice[1], max_registers=choice[2])
 
 
 def sfhk_dipole(ctx, ens, nt):

@@ -74,11 +74,16 @@ CUTOFF = 1.0e4
 # unfiltered dipole norm, and their rounding error is amplified by |M|, so no
 # finite precision reproduces them.
 STAB_CUTOFF = 1.0e3
-ALIGN_FIXED, ALIGN_ISO, ALIGN_COS2 = 0, 1, 2
+ALIGN_FIXED, ALIGN_ISO, ALIGN_COS2, ALIGN_QUAD = 0, 1, 2, 3
 
 
 def fixed(theta_deg, phi_deg=0.0):
     return (ALIGN_FIXED, math.radians(theta_deg), math.radians(phi_deg))
+
+
+def quadrature(n_nodes=10):
+    """Isotropic average by an n-node rule in cos(theta) (Eq. 5)."""
+    return (ALIGN_QUAD, 0.0, 0.0, int(n_nodes))
 
 
 COS2 = (ALIGN_COS2, 0.0, 0.0)

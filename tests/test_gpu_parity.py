@@ -64,6 +64,8 @@ def test_pulse_grid_matches_oracle(S, ctx):
     ("H2", W.PULSE_800, W.fixed(45.0, 30.0), 777, 5, 3),
     ("N2", W.PULSE_1200, W.COS2, 1000, 1, 7),
     ("N2", W.pulse(1500.0, 0.9e14, 2), W.ISO, 333, 2, 1),
+    ("H2", W.PULSE_800, W.quadrature(10), 1001, 3, 2),
+    ("N2", W.PULSE_1200, W.quadrature(7), 500, 4, 0),
 ])
 def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
     t = W.TARGETS[name]
@@ -128,6 +130,11 @@ def test_fp64_propagation_per_trajectory_and_dipole(S, ctx, name, pulse, align, 
     vz_g, fin_g, st = _run(S, ctx, t, pulse, soa, S.SFHK_FP64)
     frac = _compare_final(fin_g, fin_o, 1e-10)
     assert frac > 0.9
+    # time index of the stored state: the last grid point for a trajectory
+    # that ran to the end, never before its birth
+    nt = O.pulse_derived(pulse)["nt"]
+    assert np.all(fin_g[45][fin_g[46] == 0] == nt - 1)
+    assert np.all((fin_g[45] >= soa[0]) & (fin_g[45] <= nt - 1))
     assert st["n_filtered"] + st["n_nonfinite"] + st["n_unstable"] == bad_o
     assert _rel_l2(vz_g, vz_o) <= 1e-9
 
@@ -292,7 +299,7 @@ def test_autotuner_choice_is_valid_and_result_independent(S, ctx):
     nt = S.sfhk_pulse_grid(ph)["nt"]
     for prec, tol in ((S.SFHK_MIXED, 1e-5), (S.SFHK_FP64, 1e-12)):
         ref = None
-        for var in range(1, 6):
+        for var in range(1, 7):
             for bt in ((32, 64, 128) if prec == S.SFHK_MIXED else (64,)):
                 S.sfhk_propagate(ctx, e, S.run_opts(prec, GAMMA, CUT, block_threads=bt,
                                                     stab_cutoff=STAB, kernel_variant=var))
@@ -301,6 +308,6 @@ def test_autotuner_choice_is_valid_and_result_independent(S, ctx):
                     ref = vz
                 assert _rel_l2(vz, ref) <= tol, (prec, var, bt)
     choice = S.sfhk_autotune(ctx, e, S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB))
-    assert choice["block_threads"] in (32, 64, 128) and 1 <= choice["kernel_variant"] <= 5
+    assert choice["block_threads"] in (32, 64, 128) and 1 <= choice["kernel_variant"] <= 6
     S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB))
     S.sfhk_destroy_ensemble(e)
