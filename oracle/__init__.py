@@ -294,3 +294,22 @@ def spectrum(vz, dt, t_origin, tau_H, n_out):
     lib().or_spectrum(_p(vz), len(vz), dt, t_origin, tau_H, n_out, _p(om), _p(y), _p(ph),
                       _p(vr), _p(vi))
     return om, y, ph, vr + 1j * vi
+
+
+def gabor(vz, dt, t_origin, sigma, t_centres, omegas):
+    """Gabor time-frequency map of the dipole velocity (the analysis of
+    Sec. III.D), straight from its definition on the time grid:
+
+        G(t_m, w_k) = | sum_n v_z(t_n) exp(-(t_n - t_m)^2 / (2 sigma^2))
+                                 exp(i w_k t_n) dt |^2,
+
+    t_n = t_origin + n dt, no truncation of the Gaussian.  Returns an
+    (len(t_centres), len(omegas)) array."""
+    vz = np.asarray(vz, dtype=np.float64)
+    t = t_origin + dt * np.arange(len(vz))
+    out = np.zeros((len(t_centres), len(omegas)))
+    phase = np.exp(1j * np.outer(np.asarray(omegas, dtype=np.float64), t))   # (n_w, nt)
+    for m, tm in enumerate(t_centres):
+        u = vz * np.exp(-(t - tm) ** 2 / (2.0 * sigma * sigma)) * dt
+        out[m] = np.abs(phase @ u) ** 2
+    return out
