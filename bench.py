@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gabor", action="store_true", help="skip the Gabor-map measurement")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--block", type=int, default=0, help="pin the integrator's block size")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
@@ -401,6 +402,48 @@ def run_ours(args):
                 {"max": max(errs), "median": float(np.median(errs))},
                 "speedup_mixed_over_fp64": (traj_steps / ms) / (ts64 / ms64)}
 
+    # Gabor time-frequency maps of the step's dipoles (Sec. III.D analysis,
+    # outside the timed step): 512 window centres over the pulse x 512
+    # frequencies up to 40 w0, sigma = 1/(3 w0), FP64
+    gabor = None
+    if not args.no_gabor:
+        n_t = n_w = 512
+        gmaps = [torch.empty((n_t, n_w), dtype=torch.float64, device="cuda") for _ in ens]
+        gpar = []
+        for i, g in zip(instances, grids):
+            w0 = 45.5633525 / i["pulse"]["lambda_nm"]
+            gpar.append((1.0 / (3.0 * w0), g["t_origin"], g["Tp"] / (n_t - 1), 0.5 * w0,
+                         40.0 * w0 / n_w))
+
+        def gabor_all():
+            for e, g, o, (sg, tf, ts, wf, ws) in zip(ens, grids, gmaps, gpar):
+                vz_ptr, _ = S.sfhk_dipole_device(e)
+                S.sfhk_gabor_device(vz_ptr, g["nt"], g["dt"], g["t_origin"], sg, tf, ts, n_t, wf,
+                                    ws, n_w, o.data_ptr(), sp)
+        gabor_all()
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        g0.record(stream)
+        for _ in range(reps):
+            gabor_all()
+        g1.record(stream)
+        barrier()
+        gms = g0.elapsed_time(g1) / reps
+        # FP64 work: per (centre, frequency, sample in the window) 2 FMA for
+        # the sum and 2 FMA + 2 MUL for the phase recurrence = 10 flop
+        samples = 0
+        for g, (sg, tf, ts, wf, ws) in zip(grids, gpar):
+            tm = tf + ts * np.arange(n_t)
+            lo = np.clip(np.ceil((tm - 8.6 * sg - g["t_origin"]) / g["dt"]), 0, g["nt"])
+            hi = np.clip(np.floor((tm + 8.6 * sg - g["t_origin"]) / g["dt"]), -1, g["nt"] - 1)
+            samples += int(np.sum(np.maximum(hi - lo + 1, 0)))
+        gfl = 10.0 * samples * n_w
+        gabor = {"ms": gms, "maps": len(ens), "map": [n_t, n_w], "sigma": "1/(3 w0)",
+                 "kernel": "k_gabor (FP64)", "achieved_tflops": gfl / (gms * 1e-3) / 1e12,
+                 "fp64_peak_nominal_tflops": 1.25,
+                 "frac_of_fp64_nominal": gfl / (gms * 1e-3) / 1e12 / 1.25}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds, instances)
@@ -420,7 +463,7 @@ def run_ours(args):
                 "spectra_per_s": spectra_per_s,
                 "ms_per_step_all": ms_steps,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "fp64_path": fp64, "gpu_launches": launches // args.steps,
+                "fp64_path": fp64, "gabor": gabor, "gpu_launches": launches // args.steps,
                 "autotuned": tuned, "clocks": clk,
                 "filtered_frac": sum(s["n_filtered"] + s["n_unstable"] for s in st)
                 / sum(i["n_traj"] for i in instances)}

@@ -77,7 +77,15 @@ enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
  * distance s_i = sqrt(|r - R_i|^2 + soft_a^2).  The initial orbital is the
  * sigma_g combination  N sum_centres sum_k prim_coef[k] exp(-prim_exp[k] |r-R_c|^2)
  * (normalised by the library).  kind = SFHK_POT_HARMONIC replaces V by the
- * test potential ho_omega^2 |r|^2 / 2 (closed-form checks). */
+ * test potential ho_omega^2 |r|^2 / 2 (closed-form checks).
+ * ionization selects the ionization step of the sampler: SFHK_IONIZE_SFA is
+ * the saddle point of Eq. 2 (SFHK1); SFHK_IONIZE_MODIFIED is SFHK2
+ * (Sec. III.D): each trajectory leaves from one centre, eta = +1 (the centre
+ * at -(R/2) n) or -1 (at +(R/2) n) with probability 1/2 each and weight x 2,
+ * through the saddle [k + A(t_s) - A(t0)]^2/2 + Ip - eta E(t_s).(R/2) n = 0,
+ * with that centre's part of the dipole element and the Gaussian-integration
+ * factor 1/sqrt(E(t_s) kappa_z + eta (R/2) n_z dE/dt(t_s)). */
+enum { SFHK_IONIZE_SFA = 0, SFHK_IONIZE_MODIFIED = 1 };
 typedef struct {
     int kind;
     int n_prim;                       /* 1..SFHK_MAX_PRIM */
@@ -86,6 +94,7 @@ typedef struct {
     double ho_omega;
     double prim_exp[SFHK_MAX_PRIM];   /* > 0 */
     double prim_coef[SFHK_MAX_PRIM];
+    int ionization;                   /* SFHK_IONIZE_SFA or SFHK_IONIZE_MODIFIED */
 } sfhk_target_desc;
 
 /* Pulse (Sec. II.D / III.A): wavelength (nm), peak intensity (W/cm^2),
@@ -294,6 +303,21 @@ SFHK_API int sfhk_final_state(sfhk_ensemble* e, double* host, uint64_t n_traj);
 SFHK_API int sfhk_spectrum(const double* vz, size_t nt, double dt, double t_origin, double tau_H,
                   double* omega_out, double* yield_out, double* phase_out, size_t n_out,
                   int device_ptrs, void* stream);
+
+/* Gabor time-frequency map of the dipole velocity (the analysis of Sec. III.D):
+ *   G(t_m, w_k) = | sum_n v_z(t_n) exp(-(t_n - t_m)^2 / (2 sigma^2)) e^{i w_k t_n} dt |^2,
+ * t_n = t_origin + n dt (n < nt), t_m = t_first + m t_step (m < n_t),
+ * w_k = omega_first + k omega_step (k < n_w); out[m * n_w + k].  Samples with
+ * |t_n - t_m| > 8.6 sigma (window factor below 1e-16) are skipped.  The paper
+ * does not give sigma; 1/(3 omega_0) is the usual choice.  device_ptrs = 1:
+ * vz and out are device pointers and the call is asynchronous on `stream`;
+ * 0: host buffers, synchronous.  FP64.
+ * Errors: SFHK_E_INVAL (null pointer, nt, n_t or n_w = 0 or too large,
+ * dt <= 0, sigma <= 0, a non-finite argument), SFHK_E_CUDA. */
+SFHK_API int sfhk_gabor(const double* vz, size_t nt, double dt, double t_origin, double sigma,
+                        double t_first, double t_step, size_t n_t, double omega_first,
+                        double omega_step, size_t n_w, double* out, int device_ptrs,
+                        void* stream);
 
 /* ---------------------------------------------------------------- serving */
 /* A spectrum server with continuous batching (not in the paper, which runs

@@ -57,7 +57,7 @@ class TargetIn(C.Structure):
     _fields_ = [("kind", C.c_int), ("n_prim", C.c_int), ("R", C.c_double),
                 ("Zinf", C.c_double), ("Z0", C.c_double), ("alpha", C.c_double),
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
-                ("pexp", C.c_double * 8), ("pcoef", C.c_double * 8)]
+                ("pexp", C.c_double * 8), ("pcoef", C.c_double * 8), ("ionization", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -99,9 +99,13 @@ def lib():
                                 _dp, _dp]
         L.or_adk_table.argtypes = [C.POINTER(PulseIn), C.c_double, _dp, _dp]
         L.or_sample.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int, C.c_double,
-                                C.c_double, C.c_int, C.c_uint64, C.c_uint32, C.c_uint64,
+                                C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_uint64,
                                 C.c_uint64, _dp, _dp]
         L.or_quad_nodes.argtypes = [C.c_int, _dp, _dp]
+        L.or_saddle_modified.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
+                                         C.c_double, _dp]
+        L.or_saddle_modified.restype = C.c_int
+        L.or_pulse_Edot_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
         L.or_sample.restype = C.c_int
         L.or_propagate.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
                                    C.c_double, C.c_double, _dp, C.c_uint64, C.c_double, _dp, _dp,
@@ -123,6 +127,7 @@ def target_in(t) -> TargetIn:
     """t: mapping with R, Zinf, Z0, alpha, soft_a, Ip, pexp, pcoef (+ kind, ho_omega)."""
     T = TargetIn()
     T.kind = int(t.get("kind", POT_MOLECULE))
+    T.ionization = int(t.get("ionization", 0))
     T.n_prim = len(t.get("pexp", ()))
     for name in ("R", "Zinf", "Z0", "alpha", "soft_a", "Ip", "ho_omega"):
         setattr(T, name, float(t.get(name, 0.0)))
@@ -252,16 +257,18 @@ def adk_table(p, Ip):
     return W, cdf
 
 
-def sample(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance=0, j_begin=0, n=1):
+def sample(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance=0, j_begin=0, n=1,
+           eta_force=0):
     """Initial ensemble as a (12, n) field-major array plus aux (tt, S_down).
     align = (kind, theta, phi[, n_nodes]); n_nodes is the K of the quadrature
-    kind."""
+    kind.  eta_force = +-1 fixes the emitting side of the modified saddle
+    (target ionization 1) with weight 1 instead of drawing it."""
     soa = np.zeros((NFIELDS, n))
     aux = np.zeros((3, n))
     k = int(align[3]) if len(align) > 3 else 0
     bad = lib().or_sample(C.byref(target_in(t)), C.byref(pulse_in(p)), int(align[0]),
-                          float(align[1]), float(align[2]), k, seed, instance, j_begin, n,
-                          _p(soa), _p(aux))
+                          float(align[1]), float(align[2]), k, int(eta_force), seed, instance,
+                          j_begin, n, _p(soa), _p(aux))
     if bad < 0:
         raise ValueError("bad alignment")
     return soa, aux, bad
@@ -313,3 +320,17 @@ def gabor(vz, dt, t_origin, sigma, t_centres, omegas):
         u = vz * np.exp(-(t - tm) ** 2 / (2.0 * sigma * sigma)) * dt
         out[m] = np.abs(phase @ u) ** 2
     return out
+
+
+def saddle_modified(p, Ip, t0, kperp2, c):
+    """SFHK2 saddle with c = eta (R/2) n_z: (rc, tt, kz), rc = 0 on success."""
+    out = np.zeros(2)
+    rc = lib().or_saddle_modified(C.byref(pulse_in(p)), Ip, t0, kperp2, c, _p(out))
+    return rc, out[0], out[1]
+
+
+def pulse_Edot_complex(p, tau):
+    out = np.zeros(2)
+    lib().or_pulse_Edot_complex(C.byref(pulse_in(p)), float(np.real(tau)), float(np.imag(tau)),
+                                _p(out))
+    return out[0] + 1j * out[1]

@@ -71,6 +71,8 @@ typedef struct {
     double ho_omega;    /* harmonic test potential V = w^2 r^2 / 2        */
     double pexp[8];     /* primitive exponents                            */
     double pcoef[8];    /* primitive coefficients (un-normalised)         */
+    int ionization;     /* 0: SFA saddle (Eq. 2); 1: modified saddle      */
+                        /* with -eta E(t_s).r0 (SFHK2, Sec. III.D)        */
 } or_target_in;
 
 /* ------------------------------------------------------------------ */
@@ -170,6 +172,26 @@ static cplx pulse_E(const or_pulse* P, cplx tau)
     cplx s2 = csin(2.0 * OR_PI * tau / P->Tp);
     cplx ph = P->omega * tau + P->cep;
     return P->E0 * c * c * ccos(ph) - (P->E0 * OR_PI / (P->omega * P->Tp)) * s2 * csin(ph);
+}
+
+/* dE/dtau, differentiated by hand from pulse_E:
+ *   -E0 w cos^2(pi tau/Tp) sin(ph) - 2 E0 (pi/Tp) sin(2 pi tau/Tp) cos(ph)
+ *   - (2 pi^2 E0 / (w Tp^2)) cos(2 pi tau/Tp) sin(ph),  ph = w tau + cep.   */
+static cplx pulse_Edot(const or_pulse* P, cplx tau)
+{
+    cplx c = ccos(OR_PI * tau / P->Tp);
+    cplx s2 = csin(2.0 * OR_PI * tau / P->Tp);
+    cplx c2 = ccos(2.0 * OR_PI * tau / P->Tp);
+    cplx ph = P->omega * tau + P->cep;
+    return -P->E0 * P->omega * c * c * csin(ph) - 2.0 * P->E0 * (OR_PI / P->Tp) * s2 * ccos(ph)
+           - (2.0 * OR_PI * OR_PI * P->E0 / (P->omega * P->Tp * P->Tp)) * c2 * csin(ph);
+}
+
+void or_pulse_Edot_complex(const or_pulse_in* in, double tr, double ti, double out[2])
+{
+    or_pulse P = or_make_pulse(in);
+    cplx e = pulse_Edot(&P, tr + I * ti);
+    out[0] = creal(e); out[1] = cimag(e);
 }
 
 double or_pulse_A_real(const or_pulse_in* in, double t)
@@ -457,12 +479,14 @@ void or_recomb(const or_target_in* T, const double nhat[3], const double q[3],
 /*   int e^{-i kappa.r} e^{-a|r-A|^2} = (pi/a)^{3/2} e^{-i kappa.A - kappa.kappa/(4a)}, */
 /*   int e^{-i kappa.r} z e^{-a|r-A|^2} = (A_z - i kappa_z/(2a)) x (above). */
 /* ------------------------------------------------------------------ */
+/* only: -1 both centres; 0 the centre at +(R/2) n; 1 the one at -(R/2) n  */
 static void dipole_matrix_element(const or_target_in* T, double N, const double nhat[3],
-                                  const cplx kappa[3], cplx* mz)
+                                  const cplx kappa[3], int only, cplx* mz)
 {
     cplx kk = kappa[0] * kappa[0] + kappa[1] * kappa[1] + kappa[2] * kappa[2];
     cplx tot = 0.0;
     for (int ctr = 0; ctr < 2; ++ctr) {
+        if (only >= 0 && ctr != only) continue;
         double sign = (ctr == 0) ? 1.0 : -1.0;
         double A[3];
         for (int a = 0; a < 3; ++a) A[a] = sign * 0.5 * T->R * nhat[a];
@@ -482,7 +506,7 @@ void or_dipole_matrix_element(const or_target_in* T, const double nhat[3],
     cplx kap[3];
     for (int a = 0; a < 3; ++a) kap[a] = kre[a] + I * kim[a];
     cplx m;
-    dipole_matrix_element(T, orbital_norm(T), nhat, kap, &m);
+    dipole_matrix_element(T, orbital_norm(T), nhat, kap, -1, &m);
     out[0] = creal(m); out[1] = cimag(m);
 }
 
@@ -587,6 +611,61 @@ int or_saddle(const or_pulse_in* Pin, double Ip, double t0, double kperp2, doubl
     return saddle(&P, Ip, t0, kperp2, &out[0], &out[1]);
 }
 
+/* Modified saddle point (SFHK2, Sec. III.D):                            */
+/*   [k + A(t_s) - A(t0)]^2 / 2 + Ip - eta E(t_s).r0 = 0,  r0 = (R/2) n,  */
+/* with E along z: c = eta (R/2) n_z.  With Y = Im A(t_s), E(t_s) =       */
+/* E_r + i E_i, the imaginary part gives X = k_z + Re A(t_s) - A(t0)      */
+/*   = c E_i / Y, and the real part                                      */
+/*   F(tt) = Y^2 - X^2 - 2 Ip - k_perp^2 + 2 c E_r = 0.                  */
+/* Reading: tt is the smallest positive root, found as in saddle() by    */
+/* marching to the first sign change of F and bisecting.  c = 0 gives     */
+/* the standard saddle.  Returns 0 on success, -1 if no root.            */
+static int saddle_modified(const or_pulse* P, double Ip, double t0, double kperp2, double c,
+                           double* tt_out, double* kz_out)
+{
+    double target = 2.0 * Ip + kperp2;
+    double E0 = fabs(pulse_E_real(P, t0));
+    if (!(E0 > 0.0)) return -1;
+    double sqs = sqrt(target) / E0;
+    double h = sqs / 64.0;
+    double s_lo = 0.0, s_hi = 0.0;
+    int found = 0;
+#define OR_F_MOD(s_, f_)                                                       \
+    do {                                                                       \
+        cplx A_ = pulse_A(P, t0 + I * (s_));                                   \
+        cplx E_ = pulse_E(P, t0 + I * (s_));                                   \
+        double Y_ = cimag(A_), X_ = c * cimag(E_) / Y_;                        \
+        (f_) = Y_ * Y_ - X_ * X_ - target + 2.0 * c * creal(E_);               \
+    } while (0)
+    for (int k = 1; k <= 64 * 64; ++k) {
+        double s = k * h, f;
+        OR_F_MOD(s, f);
+        if (f >= 0.0) { s_hi = s; found = 1; break; }
+        s_lo = s;
+    }
+    if (!found) return -1;
+    for (int it = 0; it < 200; ++it) {
+        double sm = 0.5 * (s_lo + s_hi), f;
+        if (sm <= s_lo || sm >= s_hi) break;
+        OR_F_MOD(sm, f);
+        if (f >= 0.0) s_hi = sm; else s_lo = sm;
+    }
+#undef OR_F_MOD
+    double tt = 0.5 * (s_lo + s_hi);
+    cplx A = pulse_A(P, t0 + I * tt);
+    cplx E = pulse_E(P, t0 + I * tt);
+    *tt_out = tt;
+    *kz_out = c * cimag(E) / cimag(A) - (creal(A) - creal(pulse_A(P, t0)));
+    return 0;
+}
+
+int or_saddle_modified(const or_pulse_in* Pin, double Ip, double t0, double kperp2, double c,
+                       double out[2])
+{
+    or_pulse P = or_make_pulse(Pin);
+    return saddle_modified(&P, Ip, t0, kperp2, c, &out[0], &out[1]);
+}
+
 /* Tunnel exit q_{t0} = Re int_{t_s}^{t0} A(tau) dtau along tau = t0 + i s
  * (s from tt down to 0, dtau = i ds), and the tunnelling action
  *   S_down = Ip t_s - int_{t_s}^{t0} [k + A(tau) - A(t0)]^2 / 2 dtau,
@@ -655,8 +734,8 @@ void or_adk_table(const or_pulse_in* Pin, double Ip, double* W, double* cdf)
 }
 
 int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
-              double theta, double phi, int n_nodes, uint64_t seed, uint32_t instance,
-              uint64_t j_begin, uint64_t n, double* soa, double* aux)
+              double theta, double phi, int n_nodes, int eta_force, uint64_t seed,
+              uint32_t instance, uint64_t j_begin, uint64_t n, double* soa, double* aux)
 {
     or_pulse P = or_make_pulse(Pin);
     double qx[OR_MAX_QUAD], qw[OR_MAX_QUAD];
@@ -699,18 +778,37 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
             ph = 2.0 * OR_PI * u[4];
         }
         double nhat[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
-        /* saddle, exit, action, amplitude */
+        /* saddle, exit, action, amplitude.  SFHK2: the electron leaves     */
+        /* from one centre, eta = +1 (the centre at -(R/2) n) or -1 (the     */
+        /* centre at +(R/2) n) with probability 1/2 each (weight x 2), the   */
+        /* modified saddle, that centre's part of the dipole element (its    */
+        /* factor e^{-i kappa.R_c} is the phase whose t_s-derivative is the  */
+        /* extra term), and the Gaussian-integration factor from the         */
+        /* curvature of the whole phase, E kappa_z + c dE/dt.                */
         double tt = 0.0, kz = 0.0, qz = 0.0;
         cplx w = 0.0, Sd = 0.0;
-        if (saddle(&P, T->Ip, t0, kx * kx + ky * ky, &tt, &kz) == 0) {
+        int only = -1;
+        double cmod = 0.0, side_w = 1.0;
+        if (T->ionization == 1) {
+            /* eta_force = +-1 fixes the side (test hook, weight x 1) */
+            double eta = eta_force ? (double)eta_force : ((u[5] < 0.5) ? 1.0 : -1.0);
+            only = (eta > 0.0) ? 1 : 0;
+            cmod = eta * 0.5 * T->R * cos(th);
+            side_w = eta_force ? 1.0 : 2.0;
+        }
+        int sok = (T->ionization == 1)
+                      ? saddle_modified(&P, T->Ip, t0, kx * kx + ky * ky, cmod, &tt, &kz)
+                      : saddle(&P, T->Ip, t0, kx * kx + ky * ky, &tt, &kz);
+        if (sok == 0) {
             double k[3] = {kx, ky, kz};
             tunnel_exit_and_action(&P, T->Ip, t0, tt, k, &qz, &Sd);
             cplx ts = t0 + I * tt;
             cplx Es = pulse_E(&P, ts);
             cplx kap[3] = {kx, ky, kz + pulse_A(&P, ts) - creal(pulse_A(&P, t0))};
             cplx mz;
-            dipole_matrix_element(T, N, nhat, kap, &mz);
-            cplx a = Es * mz / csqrt(Es * kap[2]) * cexp(I * (Sd + kz * qz));
+            dipole_matrix_element(T, N, nhat, kap, only, &mz);
+            cplx curv = Es * kap[2] + cmod * pulse_Edot(&P, ts);
+            cplx a = side_w * Es * mz / csqrt(curv) * cexp(I * (Sd + kz * qz));
             double pdf = (W[n0] / total) / P.dt
                          * exp(-(kx * kx + ky * ky) / (2.0 * sigma * sigma))
                          / (2.0 * OR_PI * sigma * sigma);

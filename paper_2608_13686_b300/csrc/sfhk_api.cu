@@ -275,6 +275,8 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
     if (!c || !d || !out) return SFHK_E_INVAL;
     if (d->kind != SFHK_POT_MOLECULE && d->kind != SFHK_POT_HARMONIC) return SFHK_E_INVAL;
     if (d->n_prim < 1 || d->n_prim > SFHK_MAX_PRIM) return SFHK_E_INVAL;
+    if (d->ionization != SFHK_IONIZE_SFA && d->ionization != SFHK_IONIZE_MODIFIED)
+        return SFHK_E_INVAL;
     for (int k = 0; k < d->n_prim; ++k)
         if (!(d->prim_exp[k] > 0.0) || !std::isfinite(d->prim_coef[k])) return SFHK_E_INVAL;
     if (d->soft_a < 0.0 || d->R < 0.0 || d->alpha < 0.0 || !std::isfinite(d->Ip)) return SFHK_E_INVAL;

@@ -160,6 +160,10 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
                            cudaStream_t s);
 
 // spectrum (sfhk_spectrum.cu)
+// Gabor map (sfhk_gabor.cu)
+int launch_gabor(const double* vz, int nt, double dt, double t_origin, double sigma,
+                 double t_first, double t_step, int n_t, double w_first, double w_step, int n_w,
+                 double* out, cudaStream_t s);
 int launch_spectrum(const double* vz, int nt, double dt, double t_origin, double tau_H,
                     double* omega, double* yield, double* phase, int n_out, double2* twiddle,
                     cudaStream_t s);

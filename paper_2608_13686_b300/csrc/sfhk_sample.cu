@@ -105,6 +105,7 @@ struct SampleParams {
     long long n;
     double R;
     int n_prim;
+    int ionization;                           // SFHK_IONIZE_SFA / SFHK_IONIZE_MODIFIED
     double norm;
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
 };
@@ -175,6 +176,16 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
     sincos(th, &sth, &cth);
     sincos(phv, &sph, &cph);
     const double nx = sth * cph, ny = sth * sph, nz = cth;
+    // SFHK2: the emitting centre (eta = +1: the one at -(R/2) n, drawn with
+    // probability 1/2, weight x 2) and the saddle's offset c = eta (R/2) n_z
+    int only = -1;
+    double cmod = 0.0, side_w = 1.0;
+    if (S.ionization == SFHK_IONIZE_MODIFIED) {
+        const double eta = u[5] < 0.5 ? 1.0 : -1.0;
+        only = eta > 0.0 ? 1 : 0;
+        cmod = eta * 0.5 * S.R * nz;
+        side_w = 2.0;
+    }
 
     double qz = 0.0, kz = 0.0;
     double2 w = make_double2(0.0, 0.0);
@@ -203,21 +214,46 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
             *dg = 0.5 * yp;
             return 0.5 * y - Ystar;
         };
-        const double s0 = sqrt(target) / fabs(Et0);
-        const double sg0 = -Ystar;     // g(0)
-        double slo = 0.0, shi = s0, dg;
-        double ghi = g(shi, &dg);
-        ok = false;
-        for (int it = 0; it < 64; ++it) {
-            if ((ghi > 0.0) != (sg0 > 0.0) || ghi == 0.0) { ok = true; break; }
-            slo = shi;
-            shi *= 1.25;
-            if (shi > 64.0 * s0) break;
-            ghi = g(shi, &dg);
-        }
-        if (ok) {
-            // safeguarded Newton from the bracket's upper end, where g and g'
-            // are already known
+        // SFHK2 (Sec. III.D): with E(t_s) = E_r + i E_i the imaginary part of
+        // the modified saddle gives X = k_z + Re A(t_s) - A(t0) = c E_i / Y and
+        // the real part F(s) = Y^2 - X^2 - target + 2 c E_r = 0, F(0+) < 0;
+        // Y' = -E_r, E_r' = -Im dE/dt, E_i' = Re dE/dt along t0 + i s
+        double Xlast = 0.0;
+        auto gmod = [&](double s, double* dF) {
+            double Y = 0.0, dY = 0.0, Ei = 0.0, dEr = 0.0, dEi = 0.0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const double k = S.P.k[q], a = S.P.a[q];
+                const double e = exp(k * s), ie = 1.0 / e;
+                const double sh = 0.5 * (e - ie), ch = 0.5 * (e + ie);
+                Y += a * cthm[q] * sh;
+                dY += a * k * cthm[q] * ch;
+                Ei += a * k * sthm[q] * sh;
+                dEr -= a * k * k * cthm[q] * sh;
+                dEi += a * k * k * sthm[q] * ch;
+            }
+            const double Er = -dY;
+            const double X = cmod * Ei / Y;
+            const double dX = cmod * (dEi * Y - Ei * dY) / (Y * Y);
+            Xlast = X;
+            *dF = 2.0 * Y * dY - 2.0 * X * dX + 2.0 * cmod * dEr;
+            return Y * Y - X * X - target + 2.0 * cmod * Er;
+        };
+        // first sign change by marching up from the quasi-static estimate,
+        // then safeguarded Newton from the bracket's upper end
+        auto solve = [&](auto&& fn, double sg0, double* s_out) -> bool {
+            const double s0 = sqrt(target) / fabs(Et0);
+            double slo = 0.0, shi = s0, dg;
+            double ghi = fn(shi, &dg);
+            bool found = false;
+            for (int it = 0; it < 64; ++it) {
+                if ((ghi > 0.0) != (sg0 > 0.0) || ghi == 0.0) { found = true; break; }
+                slo = shi;
+                shi *= 1.25;
+                if (shi > 64.0 * s0) break;
+                ghi = fn(shi, &dg);
+            }
+            if (!found) return false;
             double s = shi, gs = ghi;
             for (int it = 0; it < 200; ++it) {
                 if (gs == 0.0) break;
@@ -227,9 +263,23 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
                 const bool done = fabs(sn - s) <= 4e-16 * s || shi - slo <= 4e-16 * shi;
                 s = sn;
                 if (done) break;
-                gs = g(s, &dg);
+                gs = fn(s, &dg);
             }
-            tt = s;
+            *s_out = s;
+            return true;
+        };
+        double Xs = 0.0;
+        if (S.ionization == SFHK_IONIZE_MODIFIED) {
+            ok = solve(gmod, -1.0, &tt);
+            if (ok) {
+                double d;
+                gmod(tt, &d);
+                Xs = Xlast;
+            }
+        } else {
+            ok = solve(g, -Ystar, &tt);     // g(0) = -Y*
+        }
+        if (ok) {
             // ---- k_z, exit and action in closed form; em[q] = e^{k_q tt} - 1
             double em[3];
 #pragma unroll
@@ -249,7 +299,7 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
                 Es.x -= a * k * cthm[q] * (cm1 + 1.0);
                 Es.y += a * k * sthm[q] * sh;
             }
-            kz = -dRe;
+            kz = Xs - dRe;
             qz = q0;
             const double2 kapz = make_double2(kz + dRe, Yt);
             // int_0^tt B(s)^2 ds, B = c' + sum a sin(th + i k s), c' = kz - A(t0)
@@ -291,6 +341,7 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
                                             2.0 * kapz.x * kapz.y);
             double2 mz = make_double2(0.0, 0.0);
             for (int c = 0; c < 2; ++c) {
+                if (only >= 0 && c != only) continue;
                 const double sgn = c == 0 ? 1.0 : -1.0;
                 const double Ax = sgn * 0.5 * S.R * nx, Ay = sgn * 0.5 * S.R * ny,
                              Az = sgn * 0.5 * S.R * nz;
@@ -309,7 +360,21 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
             mz = cscale(mz, S.norm * pow(2.0 * kPi, -1.5));
             // amplitude and weight
             const double2 num = cmul(Es, mz);
-            const double2 den = csqrt_(cmul(Es, kapz));
+            double2 curv = cmul(Es, kapz);
+            if (S.ionization == SFHK_IONIZE_MODIFIED) {
+                // + c dE/dt(t_s), dE/dt = sum a k^2 sin(th + i k tt)
+                double2 Ed = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    double sh, cm1;
+                    sh_cm1(em[q], sh, cm1);
+                    const double ak2 = S.P.a[q] * S.P.k[q] * S.P.k[q];
+                    Ed.x += ak2 * sthm[q] * (cm1 + 1.0);
+                    Ed.y += ak2 * cthm[q] * sh;
+                }
+                curv = cadd(curv, cscale(Ed, cmod));
+            }
+            const double2 den = csqrt_(curv);
             const double2 Z = make_double2(Sd.x + kz * qz, Sd.y);     // S_down + k.q0
             const double2 eiz = cexp_(make_double2(-Z.y, Z.x));        // e^{iZ}
             const double2 amp = cmul(cdiv(num, den), eiz);
@@ -318,7 +383,8 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
             const double pdf = (Wm / total) / S.dt * exp(-kp2 / (2.0 * sigma * sigma)) /
                                (2.0 * kPi * sigma * sigma);
             // the quadrature node's weight K W_k (1 otherwise)
-            const double f = S.align_kind == SFHK_ALIGN_QUADRATURE ? S.qkw[j % S.n_nodes] : 1.0;
+            const double f = side_w *
+                             (S.align_kind == SFHK_ALIGN_QUADRATURE ? S.qkw[j % S.n_nodes] : 1.0);
             w = make_double2(f * amp.x / pdf, f * amp.y / pdf);
         }
     }
@@ -521,6 +587,7 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
     S.n = n;
     S.R = T.desc.R;
     S.n_prim = T.desc.n_prim;
+    S.ionization = T.desc.ionization;
     S.norm = T.dev.norm;
     for (int k = 0; k < SFHK_MAX_PRIM; ++k) {
         S.pexp[k] = T.desc.prim_exp[k];

@@ -80,8 +80,10 @@ struct sfhk_server {
     cudaStream_t s = nullptr;
     sfhk::DeviceBuf insts, ring, done, cancelf, ctr, t0, spec;
     unsigned int ring_cap = 0, mask = 0;
-    uint64_t head = 0, tail = 0;     // ring positions (monotonic; head may step back
-                                     // when a short request is put in front)
+    // ring positions, monotonic except that head steps back when a short
+    // request is put in front; they start far from zero so that this is
+    // possible even before the first slice has taken anything
+    uint64_t head = uint64_t(1) << 40, tail = uint64_t(1) << 40;
     double queued_work = 0;          // items x Nt not yet taken (estimate)
     std::vector<int> free_slots;
     std::vector<uint64_t> slot_req;

@@ -36,7 +36,8 @@ class sfhk_target_desc(C.Structure):
     _fields_ = [("kind", C.c_int), ("n_prim", C.c_int), ("R", C.c_double),
                 ("Z_inf", C.c_double), ("Z0", C.c_double), ("alpha", C.c_double),
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
-                ("prim_exp", C.c_double * SFHK_MAX_PRIM), ("prim_coef", C.c_double * SFHK_MAX_PRIM)]
+                ("prim_exp", C.c_double * SFHK_MAX_PRIM), ("prim_coef", C.c_double * SFHK_MAX_PRIM),
+                ("ionization", C.c_int)]
 
 
 class sfhk_pulse_desc(C.Structure):
@@ -151,6 +152,9 @@ def _load():
         "sfhk_final_state": ([_vp, _dp, C.c_uint64], C.c_int),
         "sfhk_spectrum": ([_vp, C.c_size_t, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp,
                            C.c_size_t, C.c_int, _vp], C.c_int),
+        "sfhk_gabor": ([_vp, C.c_size_t, C.c_double, C.c_double, C.c_double, C.c_double,
+                        C.c_double, C.c_size_t, C.c_double, C.c_double, C.c_size_t, _vp, C.c_int,
+                        _vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -187,6 +191,7 @@ def target_desc(t: dict) -> sfhk_target_desc:
     d.R, d.Z_inf, d.Z0 = float(t["R"]), float(t["Zinf"]), float(t["Z0"])
     d.alpha, d.soft_a, d.Ip = float(t["alpha"]), float(t["soft_a"]), float(t["Ip"])
     d.ho_omega = float(t.get("ho_omega", 0.0))
+    d.ionization = int(t.get("ionization", 0))
     for i, (e, c) in enumerate(zip(pe, pc)):
         d.prim_exp[i] = e
         d.prim_coef[i] = c
@@ -456,6 +461,23 @@ def sfhk_spectrum_noalloc(vz_ptr, nt, dt, t_origin, tau_H, om_ptr, y_ptr, ph_ptr
                                          n_out, stream), "sfhk_spectrum_noalloc")
 
 
+def sfhk_gabor(vz, dt, t_origin, sigma, t_first, t_step, n_t, omega_first, omega_step, n_w):
+    """Host-buffer form: returns the (n_t, n_w) Gabor map."""
+    vz = np.ascontiguousarray(vz, dtype=np.float64)
+    out = np.zeros((n_t, n_w))
+    _check(_load().sfhk_gabor(vz.ctypes.data, len(vz), dt, t_origin, sigma, t_first, t_step, n_t,
+                              omega_first, omega_step, n_w, out.ctypes.data, 0, None),
+           "sfhk_gabor")
+    return out
+
+
+def sfhk_gabor_device(vz_ptr, nt, dt, t_origin, sigma, t_first, t_step, n_t, omega_first,
+                      omega_step, n_w, out_ptr, stream=None):
+    """Device-buffer form (raw device pointers, asynchronous on `stream`)."""
+    _check(_load().sfhk_gabor(vz_ptr, nt, dt, t_origin, sigma, t_first, t_step, n_t, omega_first,
+                              omega_step, n_w, out_ptr, 1, stream), "sfhk_gabor")
+
+
 EXPORTED = [
     "sfhk_create", "sfhk_destroy", "sfhk_mem_used", "sfhk_create_target", "sfhk_destroy_target",
     "sfhk_set_pulse", "sfhk_destroy_pulse", "sfhk_pulse_grid", "sfhk_sample_initial",
@@ -465,4 +487,5 @@ EXPORTED = [
     "sfhk_launch_count", "sfhk_autotune", "sfhk_spectrum_noalloc", "sfhk_server_create",
     "sfhk_server_destroy", "sfhk_submit", "sfhk_poll", "sfhk_wait", "sfhk_cancel",
     "sfhk_server_stats_get", "sfhk_batch_create", "sfhk_batch_launch", "sfhk_batch_destroy",
+    "sfhk_gabor",
 ]

@@ -43,6 +43,13 @@ TARGETS = {
 }
 
 
+def sfhk2(target):
+    """The same target with the modified saddle point of SFHK2 (Sec. III.D)."""
+    t = dict(target)
+    t["ionization"] = 1
+    return t
+
+
 def harmonic_target(omega, prims=_H2_PRIMS, Ip=0.0):
     """Isotropic harmonic test potential V = omega^2 r^2 / 2 (closed forms)."""
     t = _target(0.0, 0.0, 0.0, 0.0, 0.0, Ip, prims)

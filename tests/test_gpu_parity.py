@@ -66,9 +66,13 @@ def test_pulse_grid_matches_oracle(S, ctx):
     ("N2", W.pulse(1500.0, 0.9e14, 2), W.ISO, 333, 2, 1),
     ("H2", W.PULSE_800, W.quadrature(10), 1001, 3, 2),
     ("N2", W.PULSE_1200, W.quadrature(7), 500, 4, 0),
+    ("N2+sfhk2", W.PULSE_1200, W.fixed(0.0), 800, 5, 0),
+    ("N2+sfhk2", W.PULSE_PAPER, W.fixed(30.0, 10.0), 600, 6, 1),
+    ("H2+sfhk2", W.PULSE_800, W.ISO, 700, 7, 2),
 ])
 def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
-    t = W.TARGETS[name]
+    base, _, variant = name.partition("+")
+    t = W.TARGETS[base] if not variant else W.sfhk2(W.TARGETS[base])
     th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, pulse)
     e = S.sfhk_sample_initial(ctx, th, ph, align, n, seed, inst)
     g = S.sfhk_ensemble_read(e, n)
@@ -311,3 +315,19 @@ def test_autotuner_choice_is_valid_and_result_independent(S, ctx):
     assert choice["block_threads"] in (32, 64, 128) and 1 <= choice["kernel_variant"] <= 6
     S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB))
     S.sfhk_destroy_ensemble(e)
+
+
+def test_sfhk2_dipole_end_to_end(S, ctx):
+    """SFHK2 (modified saddle, Sec. III.D): each side samples its own ensemble
+    (device sampler vs the oracle's) and propagates it; FP64 dipoles agree."""
+    t, p = W.sfhk2(W.TARGETS["N2"]), W.PULSE_1200
+    th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, p)
+    e = S.sfhk_sample_initial(ctx, th, ph, W.fixed(0.0), 600, 9, 0)
+    S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_FP64, GAMMA, CUT, stab_cutoff=STAB))
+    vz = S.sfhk_dipole(ctx, e, S.sfhk_pulse_grid(ph)["nt"])
+    soa, _, _ = O.sample(t, p, W.fixed(0.0), seed=9, n=600)
+    vz_o, _, _ = O.propagate(t, p, soa, GAMMA, cutoff=CUT, stab_cutoff=STAB)
+    assert _rel_l2(vz, vz_o) <= 1e-9
+    S.sfhk_destroy_ensemble(e)
+    S.sfhk_destroy_pulse(ph)
+    S.sfhk_destroy_target(th)
