@@ -5,6 +5,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <type_traits>
 #include <math_constants.h>
 
 #include <cstdint>
@@ -197,7 +199,7 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz
         H.xy = H.xz = H.yz = R(0);
         return;
     }
-    R d[2][3], g1[2], g2[2], vc[2];
+    R d[2][3];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         R dx, dy, dz;
@@ -221,40 +223,88 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz
         d[c][0] = dx;
         d[c][1] = dy;
         d[c][2] = dz;
-        const R s2 = dx * dx + dy * dy + dz * dz + K.a2;
-        R u = rsqrt_t<R>(s2);
-        const R u2 = u * u, u3 = u2 * u;
-        if (K.screened) {
-            const R e = exp_t<R>(-K.alpha * (s2 * u));
-            const R de = K.dZ * e;
-            vc[c] = (K.Zinf + de) * u;
-            g1[c] = K.Zinf * u3 + de * (K.alpha * u2 + u3);
-            g2[c] = -u2 * (R(3) * K.Zinf * u3 +
-                           de * u * (K.alpha * K.alpha + R(3) * K.alpha * u + R(3) * u2));
-        } else {
-            vc[c] = K.Zinf * u;
-            g1[c] = K.Zinf * u3;
-            g2[c] = R(-3) * K.Zinf * u3 * u2;
-        }
     }
-    // sum over the two centres: V = -sum vc, F = -sum g1 d,
-    // H = (sum g1) I + sum g2 d d^T
-    V = -(vc[0] + vc[1]);
-    Fx = -(g1[0] * d[0][0] + g1[1] * d[1][0]);
-    Fy = -(g1[0] * d[0][1] + g1[1] * d[1][1]);
-    Fz = -(g1[0] * d[0][2] + g1[1] * d[1][2]);
-    const R gs = g1[0] + g1[1];
-    R gd[2][3];
+    if constexpr (std::is_same<R, float>::value) {
+        // FP32: the two centres side by side in the lanes of float2 values,
+        // so that each per-centre operation is one f32x2 instruction
+        const float2 dx = make_float2(d[0][0], d[1][0]), dy = make_float2(d[0][1], d[1][1]),
+                     dz = make_float2(d[0][2], d[1][2]);
+        const float2 s2 = __ffma2_rn(
+            dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(K.a2, K.a2))));
+        const float2 u = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
+        const float2 u2 = __fmul2_rn(u, u), u3 = __fmul2_rn(u2, u);
+        const float2 zi = make_float2(K.Zinf, K.Zinf);
+        float2 vc, g1, g2n;        // g2n = -g2
+        if (K.screened) {
+            const float2 sr = __fmul2_rn(s2, u);
+            const float2 e = make_float2(__expf(-K.alpha * sr.x), __expf(-K.alpha * sr.y));
+            const float2 de = __fmul2_rn(make_float2(K.dZ, K.dZ), e);
+            const float2 al = make_float2(K.alpha, K.alpha);
+            vc = __fmul2_rn(__fadd2_rn(zi, de), u);
+            g1 = __ffma2_rn(de, __ffma2_rn(al, u2, u3), __fmul2_rn(zi, u3));
+            const float2 poly = __ffma2_rn(make_float2(3.0f, 3.0f), u2,
+                                           __ffma2_rn(make_float2(3.0f * K.alpha, 3.0f * K.alpha),
+                                                      u, __fmul2_rn(al, al)));
+            g2n = __fmul2_rn(u2, __ffma2_rn(__fmul2_rn(de, u), poly,
+                                            __fmul2_rn(make_float2(3.0f * K.Zinf, 3.0f * K.Zinf),
+                                                       u3)));
+        } else {
+            vc = __fmul2_rn(zi, u);
+            g1 = __fmul2_rn(zi, u3);
+            g2n = __fmul2_rn(make_float2(3.0f * K.Zinf, 3.0f * K.Zinf), __fmul2_rn(u3, u2));
+        }
+        V = -(vc.x + vc.y);
+        Fx = -(g1.x * dx.x + g1.y * dx.y);
+        Fy = -(g1.x * dy.x + g1.y * dy.y);
+        Fz = -(g1.x * dz.x + g1.y * dz.y);
+        const float gs = g1.x + g1.y;
+        const float2 gx = __fmul2_rn(g2n, dx), gy = __fmul2_rn(g2n, dy), gz = __fmul2_rn(g2n, dz);
+        H.xx = gs - (gx.x * dx.x + gx.y * dx.y);
+        H.yy = gs - (gy.x * dy.x + gy.y * dy.y);
+        H.zz = gs - (gz.x * dz.x + gz.y * dz.y);
+        H.xy = -(gx.x * dy.x + gx.y * dy.y);
+        H.xz = -(gx.x * dz.x + gx.y * dz.y);
+        H.yz = -(gy.x * dz.x + gy.y * dz.y);
+    } else {
+        R g1[2], g2[2], vc[2];
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < 2; ++c) {
+            const R dx = d[c][0], dy = d[c][1], dz = d[c][2];
+            const R s2 = dx * dx + dy * dy + dz * dz + K.a2;
+            R u = rsqrt_t<R>(s2);
+            const R u2 = u * u, u3 = u2 * u;
+            if (K.screened) {
+                const R e = exp_t<R>(-K.alpha * (s2 * u));
+                const R de = K.dZ * e;
+                vc[c] = (K.Zinf + de) * u;
+                g1[c] = K.Zinf * u3 + de * (K.alpha * u2 + u3);
+                g2[c] = -u2 * (R(3) * K.Zinf * u3 +
+                               de * u * (K.alpha * K.alpha + R(3) * K.alpha * u + R(3) * u2));
+            } else {
+                vc[c] = K.Zinf * u;
+                g1[c] = K.Zinf * u3;
+                g2[c] = R(-3) * K.Zinf * u3 * u2;
+            }
+        }
+        // sum over the two centres: V = -sum vc, F = -sum g1 d,
+        // H = (sum g1) I + sum g2 d d^T
+        V = -(vc[0] + vc[1]);
+        Fx = -(g1[0] * d[0][0] + g1[1] * d[1][0]);
+        Fy = -(g1[0] * d[0][1] + g1[1] * d[1][1]);
+        Fz = -(g1[0] * d[0][2] + g1[1] * d[1][2]);
+        const R gs = g1[0] + g1[1];
+        R gd[2][3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) gd[c][a] = g2[c] * d[c][a];
-    H.xx = gd[0][0] * d[0][0] + (gd[1][0] * d[1][0] + gs);
-    H.yy = gd[0][1] * d[0][1] + (gd[1][1] * d[1][1] + gs);
-    H.zz = gd[0][2] * d[0][2] + (gd[1][2] * d[1][2] + gs);
-    H.xy = gd[0][0] * d[0][1] + gd[1][0] * d[1][1];
-    H.xz = gd[0][0] * d[0][2] + gd[1][0] * d[1][2];
-    H.yz = gd[0][1] * d[0][2] + gd[1][1] * d[1][2];
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) gd[c][a] = g2[c] * d[c][a];
+        H.xx = gd[0][0] * d[0][0] + (gd[1][0] * d[1][0] + gs);
+        H.yy = gd[0][1] * d[0][1] + (gd[1][1] * d[1][1] + gs);
+        H.zz = gd[0][2] * d[0][2] + (gd[1][2] * d[1][2] + gs);
+        H.xy = gd[0][0] * d[0][1] + gd[1][0] * d[1][1];
+        H.xz = gd[0][0] * d[0][2] + gd[1][0] * d[1][2];
+        H.yz = gd[0][1] * d[0][2] + gd[1][1] * d[1][2];
+    }
 }
 
 }  // namespace sfhk

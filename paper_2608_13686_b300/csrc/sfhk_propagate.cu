@@ -52,6 +52,49 @@ __device__ __forceinline__ C2<R> cm(C2<R> a, C2<R> b)
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
+// Stability matrix storage.  Column c of M (c < 3: d/dq0_c, c >= 3:
+// d/dp0_{c-3}) has the q rows Q(c, r) and the p rows P(c, r), r = 0..2.
+template <typename R>
+struct Mono {
+    R q[6][3], p[6][3];
+    __device__ __forceinline__ R Q(int c, int r) const { return q[c][r]; }
+    __device__ __forceinline__ R P(int c, int r) const { return p[c][r]; }
+    __device__ __forceinline__ void identity()
+    {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                q[c][r] = (c == r) ? R(1) : R(0);
+                p[c][r] = (c == r + 3) ? R(1) : R(0);
+            }
+    }
+};
+// FP32: columns k and k + 3 share one float2, so that the RK4 update runs on
+// packed pairs (two FP32 operations per f32x2 instruction).
+template <>
+struct Mono<float> {
+    float2 q[3][3], p[3][3];
+    __device__ __forceinline__ float Q(int c, int r) const
+    {
+        return c < 3 ? q[c][r].x : q[c - 3][r].y;
+    }
+    __device__ __forceinline__ float P(int c, int r) const
+    {
+        return c < 3 ? p[c][r].x : p[c - 3][r].y;
+    }
+    __device__ __forceinline__ void identity()
+    {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                q[k][r] = make_float2(k == r ? 1.0f : 0.0f, 0.0f);
+                p[k][r] = make_float2(0.0f, k == r ? 1.0f : 0.0f);
+            }
+    }
+};
+
 template <typename R>
 __device__ __forceinline__ R hypot_t(R a, R b);
 template <>
@@ -84,13 +127,13 @@ __device__ __forceinline__ double fmax3(double a, double b, double c) { return f
 
 // largest |element| of the stability matrix
 template <typename R>
-__device__ __forceinline__ R max_abs_M(const R Mq[6][3], const R Mp[6][3])
+__device__ __forceinline__ R max_abs_M(const Mono<R>& M)
 {
     R m[12];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        m[2 * c] = fmax3(fabs(Mq[c][0]), fabs(Mq[c][1]), fabs(Mq[c][2]));
-        m[2 * c + 1] = fmax3(fabs(Mp[c][0]), fabs(Mp[c][1]), fabs(Mp[c][2]));
+        m[2 * c] = fmax3(fabs(M.Q(c, 0)), fabs(M.Q(c, 1)), fabs(M.Q(c, 2)));
+        m[2 * c + 1] = fmax3(fabs(M.P(c, 0)), fabs(M.P(c, 1)), fabs(M.P(c, 2)));
     }
     const R a = fmax3(m[0], m[1], m[2]), b = fmax3(m[3], m[4], m[5]);
     const R c = fmax3(m[6], m[7], m[8]), d = fmax3(m[9], m[10], m[11]);
@@ -107,6 +150,21 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, float x)
     hi = s;
     lo = __fadd_rn(lo, e);
 }
+// the same for two pairs at once (f32x2); s - hi and x - t as FMAs with -1,
+// which round exactly like the subtractions
+__device__ __forceinline__ void acc2x2(float& h0, float& h1, float& l0, float& l1, float x0,
+                                       float x1)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 hi = make_float2(h0, h1), x = make_float2(x0, x1);
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 e = __ffma2_rn(__ffma2_rn(hi, m1, s), m1, x);
+    const float2 lo = __fadd2_rn(make_float2(l0, l1), e);
+    h0 = s.x;
+    h1 = s.y;
+    l0 = lo.x;
+    l1 = lo.y;
+}
 __device__ __forceinline__ void renorm(float& hi, float& lo)
 {
     const float s = __fadd_rn(hi, lo);
@@ -120,6 +178,61 @@ __device__ __forceinline__ R shfl(R v, int src)
     return __shfl_sync(kFull, v, src);
 }
 
+
+// 3-vector helpers of the stage arithmetic; in FP32 the (x, y) components go
+// through one f32x2 instruction and z through a scalar one.
+template <typename R>
+__device__ __forceinline__ void scale3(R a, const R x[3], R y[3])      // y = a x
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = a * x[i];
+}
+template <typename R>
+__device__ __forceinline__ void axpy3(R a, const R x[3], const R y[3], R z[3])   // z = y + a x
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) z[i] = y[i] + a * x[i];
+}
+// z = a ((u + 2 (v + w)) + x)
+template <typename R>
+__device__ __forceinline__ void rk4sum3(R a, const R u[3], const R v[3], const R w[3],
+                                        const R x[3], R z[3])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) z[i] = a * (u[i] + R(2) * (v[i] + w[i]) + x[i]);
+}
+template <>
+__device__ __forceinline__ void scale3<float>(float a, const float x[3], float y[3])
+{
+    const float2 r = __fmul2_rn(make_float2(a, a), make_float2(x[0], x[1]));
+    y[0] = r.x;
+    y[1] = r.y;
+    y[2] = a * x[2];
+}
+template <>
+__device__ __forceinline__ void axpy3<float>(float a, const float x[3], const float y[3],
+                                             float z[3])
+{
+    const float2 r =
+        __ffma2_rn(make_float2(a, a), make_float2(x[0], x[1]), make_float2(y[0], y[1]));
+    z[0] = r.x;
+    z[1] = r.y;
+    z[2] = y[2] + a * x[2];
+}
+template <>
+__device__ __forceinline__ void rk4sum3<float>(float a, const float u[3], const float v[3],
+                                               const float w[3], const float x[3], float z[3])
+{
+    const float2 t = __fadd2_rn(
+        __ffma2_rn(make_float2(2.0f, 2.0f),
+                   __fadd2_rn(make_float2(v[0], v[1]), make_float2(w[0], w[1])),
+                   make_float2(u[0], u[1])),
+        make_float2(x[0], x[1]));
+    const float2 r = __fmul2_rn(make_float2(a, a), t);
+    z[0] = r.x;
+    z[1] = r.y;
+    z[2] = a * (u[2] + 2.0f * (v[2] + w[2]) + x[2]);
+}
 
 // One RK4 step's stage evaluations from (q, p) (high part q, low part ql):
 // the four stage Hessians and the increments dq, dp, dS of the step.  Stage
@@ -136,44 +249,32 @@ __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], c
     const R k1p[3] = {F[0], F[1], F[2] - E1};
     const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
     R o[3], p2[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        o[a] = h2 * p[a];
-        p2[a] = p[a] + h2 * k1p[a];
-    }
+    scale3(h2, p, o);
+    axpy3(h2, k1p, p, p2);
     potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
                         F[1], F[2], H[1]);
     const R k2p[3] = {F[0], F[1], F[2] - E2};
     const R k2s =
         R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - (q[2] + o[2]) * E2;
     R p3[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        o[a] = h2 * p2[a];
-        p3[a] = p[a] + h2 * k2p[a];
-    }
+    scale3(h2, p2, o);
+    axpy3(h2, k2p, p, p3);
     potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
                         F[1], F[2], H[2]);
     const R k3p[3] = {F[0], F[1], F[2] - E2};
     const R k3s =
         R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - (q[2] + o[2]) * E2;
     R p4[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        o[a] = h * p3[a];
-        p4[a] = p[a] + h * k3p[a];
-    }
+    scale3(h, p3, o);
+    axpy3(h, k3p, p, p4);
     potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
                         F[1], F[2], H[3]);
     const R k4s =
         R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - (q[2] + o[2]) * E4;
     dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const R k4p = F[a] - (a == 2 ? E4 : R(0));
-        dq[a] = h6 * (p[a] + R(2) * (p2[a] + p3[a]) + p4[a]);
-        dp[a] = h6 * (k1p[a] + R(2) * (k2p[a] + k3p[a]) + k4p);
-    }
+    const R k4p[3] = {F[0], F[1], F[2] - E4};
+    rk4sum3(h6, p, p2, p3, p4, dq);
+    rk4sum3(h6, k1p, k2p, k3p, k4p, dp);
 }
 
 // The six stability-matrix columns advanced by the same RK4 step with the
@@ -193,8 +294,8 @@ __device__ __forceinline__ void hx(const Sym3<R>& H, const R x[3], R y[3])
 }
 
 template <typename R>
-__device__ __forceinline__ void m_update(R Mq[6][3], R Mp[6][3], const Sym3<R> H[4], R h, R h2,
-                                         R h6, R hh4, R hh2, R hh6)
+__device__ __forceinline__ void m_update(Mono<R>& M, const Sym3<R> H[4], R h, R h2, R h6, R hh4,
+                                         R hh2, R hh6)
 {
     // hh4 = h^2/4, hh2 = h^2/2, hh6 = h^2/6
 #pragma unroll
@@ -202,8 +303,8 @@ __device__ __forceinline__ void m_update(R Mq[6][3], R Mp[6][3], const Sym3<R> H
         R x0[3], v0[3], xs[3], xb[3], a1[3], a2[3], a3[3], a4[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            x0[r] = Mq[c][r];
-            v0[r] = Mp[c][r];
+            x0[r] = M.q[c][r];
+            v0[r] = M.p[c][r];
             xs[r] = x0[r] + h2 * v0[r];
             xb[r] = x0[r] + h * v0[r];
         }
@@ -217,8 +318,51 @@ __device__ __forceinline__ void m_update(R Mq[6][3], R Mp[6][3], const Sym3<R> H
         hx(H[3], xs, a4);
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            Mq[c][r] = xb[r] - hh6 * ((a1[r] + a2[r]) + a3[r]);
-            Mp[c][r] = v0[r] - h6 * ((a1[r] + a4[r]) + R(2) * (a2[r] + a3[r]));
+            M.q[c][r] = xb[r] - hh6 * ((a1[r] + a2[r]) + a3[r]);
+            M.p[c][r] = v0[r] - h6 * ((a1[r] + a4[r]) + R(2) * (a2[r] + a3[r]));
+        }
+    }
+}
+
+// The same update on packed column pairs: every operation is one f32x2
+// instruction for two columns, in the same order as the scalar form.
+__device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ void hx2(const Sym3<float>& H, const float2 x[3], float2 y[3])
+{
+    y[0] = __ffma2_rn(bc(H.xz), x[2], __ffma2_rn(bc(H.xy), x[1], __fmul2_rn(bc(H.xx), x[0])));
+    y[1] = __ffma2_rn(bc(H.yz), x[2], __ffma2_rn(bc(H.yy), x[1], __fmul2_rn(bc(H.xy), x[0])));
+    y[2] = __ffma2_rn(bc(H.zz), x[2], __ffma2_rn(bc(H.yz), x[1], __fmul2_rn(bc(H.xz), x[0])));
+}
+
+__device__ __forceinline__ void m_update(Mono<float>& M, const Sym3<float> H[4], float h,
+                                         float h2, float h6, float hh4, float hh2, float hh6)
+{
+    const float2 vh = bc(h), vh2 = bc(h2), mh6 = bc(-h6), mhh4 = bc(-hh4), mhh2 = bc(-hh2),
+                 mhh6 = bc(-hh6), two = bc(2.0f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float2 x0[3], v0[3], xs[3], xb[3], a1[3], a2[3], a3[3], a4[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            x0[r] = M.q[k][r];
+            v0[r] = M.p[k][r];
+            xs[r] = __ffma2_rn(vh2, v0[r], x0[r]);
+            xb[r] = __ffma2_rn(vh, v0[r], x0[r]);
+        }
+        hx2(H[0], x0, a1);
+        hx2(H[1], xs, a2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) xs[r] = __ffma2_rn(mhh4, a1[r], xs[r]);
+        hx2(H[2], xs, a3);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) xs[r] = __ffma2_rn(mhh2, a2[r], xb[r]);
+        hx2(H[3], xs, a4);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            M.q[k][r] = __ffma2_rn(mhh6, __fadd2_rn(__fadd2_rn(a1[r], a2[r]), a3[r]), xb[r]);
+            M.p[k][r] = __ffma2_rn(
+                mh6, __ffma2_rn(two, __fadd2_rn(a2[r], a3[r]), __fadd2_rn(a1[r], a4[r])), v0[r]);
         }
     }
 }
@@ -227,7 +371,7 @@ __device__ __forceinline__ void m_update(R Mq[6][3], R Mp[6][3], const Sym3<R> H
 // right angle of the previous C), then the per-step checks in the order:
 // finiteness, prefactor filter, stability filter.
 template <typename R>
-__device__ __forceinline__ void prefactor_and_checks(const R Mq[6][3], const R Mp[6][3], R gam,
+__device__ __forceinline__ void prefactor_and_checks(const Mono<R>& M, R gam,
                                                      R igam, C2<R>& Cp, const R q[3],
                                                      const R p[3], R S, R cut2, R stab,
                                                      int& status)
@@ -237,7 +381,7 @@ __device__ __forceinline__ void prefactor_and_checks(const R Mq[6][3], const R M
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            B[3 * r + c] = {Mq[c][r] + Mp[3 + c][r], igam * Mp[c][r] - gam * Mq[3 + c][r]};
+            B[3 * r + c] = {M.Q(c, r) + M.P(3 + c, r), igam * M.P(c, r) - gam * M.Q(3 + c, r)};
     const C2<R> m0 = cm(B[4], B[8]), m1 = cm(B[5], B[7]);
     const C2<R> m2 = cm(B[3], B[8]), m3 = cm(B[5], B[6]);
     const C2<R> m4 = cm(B[3], B[7]), m5 = cm(B[4], B[6]);
@@ -261,7 +405,7 @@ __device__ __forceinline__ void prefactor_and_checks(const R Mq[6][3], const R M
                      isfinite(p[1]) && isfinite(p[2]) && isfinite(S) && isfinite(rdet);
     if (!fin) status = 2;
     else if (cut2 > R(0) && rdet > cut2) status = 1;
-    else if (stab > R(0) && max_abs_M(Mq, Mp) > stab) status = 3;
+    else if (stab > R(0) && max_abs_M(M) > stab) status = 3;
 }
 
 // per-warp buffer of the chunk's contributions: 32 steps x 32 trajectories,
@@ -329,14 +473,8 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         ql[a] = R(qd[a] - double(q[a]));
         pl[a] = R(pd[a] - double(p[a]));
     }
-    R Mq[6][3], Mp[6][3];
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            Mq[c][r] = (c == r) ? R(1) : R(0);
-            Mp[c][r] = (c == r + 3) ? R(1) : R(0);
-        }
+    Mono<R> M;
+    M.identity();
     R S = R(0), Sl = R(0);          // action (two-float in MIXED, Sl unused in FP64)
     C2<R> Cp = {R(1), R(0)};        // prefactor at the previous step
     int status = 0;                 // 0 alive, 1 prefactor filter, 2 non-finite, 3 stability filter
@@ -376,7 +514,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             const C2<R> ph = {shfl(phl.x, s), shfl(phl.y, s)};
             const bool live = (nn >= n0) && status == 0;
             // ---- prefactor at t_nn (C = 1 at birth) and the checks
-            if (live) prefactor_and_checks(Mq, Mp, gam, igam, Cp, q, p, S, cut2, stab, status);
+            if (live) prefactor_and_checks(M, gam, igam, Cp, q, p, S, cut2, stab, status);
             // ---- contribution at t_nn: Re[w C e^{iS} e^{-i Ip t} <psi0|k_z|p,q>]
             R x = R(0);
             if (live && status == 0) {
@@ -438,12 +576,13 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             if (live && status == 0 && nn < nt - 1) {
                 ++steps;
                 stage_eval<R, MIXED>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS);
+                if constexpr (MIXED) {
+                    acc2x2(q[0], q[1], ql[0], ql[1], dq[0], dq[1]);
+                    acc2x2(p[0], p[1], pl[0], pl[1], dp[0], dp[1]);
+                    acc2x2(q[2], p[2], ql[2], pl[2], dq[2], dp[2]);
+                } else {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if constexpr (MIXED) {
-                        acc2(q[a], ql[a], dq[a]);
-                        acc2(p[a], pl[a], dp[a]);
-                    } else {
+                    for (int a = 0; a < 3; ++a) {
                         q[a] += dq[a];
                         p[a] += dp[a];
                     }
@@ -463,7 +602,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                 } else {
                     S += dS;
                 }
-                m_update(Mq, Mp, Hs, h, h2, h6, hh4, hh2, hh6);
+                m_update(M, Hs, h, h2, h6, hh4, hh2, hh6);
             }
         }
         // lane l sums row l (step nb + l) over the 32 trajectories: two-float
@@ -517,8 +656,8 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                d[(size_t)(6 + 6 * r + c) * n + j] = double(Mq[c][r]);
-                d[(size_t)(6 + 6 * (r + 3) + c) * n + j] = double(Mp[c][r]);
+                d[(size_t)(6 + 6 * r + c) * n + j] = double(M.Q(c, r));
+                d[(size_t)(6 + 6 * (r + 3) + c) * n + j] = double(M.P(c, r));
             }
         d[(size_t)42 * n + j] = double(S) + (MIXED ? double(Sl) : 0.0);
         d[(size_t)43 * n + j] = double(Cp.x);
