@@ -44,7 +44,5 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 
 # dram__bytes_read.sum + dram__bytes_write.sum per full-size launch of the
 # dominant kernel, keyed by (workload, kernel variant), from an ncu capture of
-# the current kernel: H2 0/45/90 deg captured at 3 x 2e5 trajectories with the
-# 128-register variant (84.6 MB read + 7.4 MB written) and scaled by
-# trajectories to 3 x 1e6.
-TRAFFIC = {("h2-angles", 6): 460.0e6}
+# the current kernel (empty: not yet captured since the last kernel change).
+TRAFFIC = {}

@@ -408,6 +408,53 @@ __device__ __forceinline__ void prefactor_and_checks(const Mono<R>& M, R gam,
     else if (stab > R(0) && max_abs_M(M) > stab) status = 3;
 }
 
+// <psi0|k_z|p,q> summed over both centres and the primitives, FP32, with the
+// two centres in the lanes of float2 values (one f32x2 instruction per
+// per-centre operation).  Both centres are evaluated unless both are beyond
+// the far-field bound; a primitive whose exponent is below kSkipMixed is
+// dropped in its lane.  Per centre and primitive the term is
+//   K4 e^{K1 |d|^2 + K2 |p|^2} (p_z - i g d_z) e^{i K3 p.d}.
+constexpr float kSkipMixed = -30.0f;
+
+__device__ __forceinline__ C2<float> recomb_pair(const DevInstance& I, const PotConst<float>& K,
+                                                 const float q[3], const float p[3], float pp,
+                                                 float gam, float K1max, float K2max, int n_prim)
+{
+    const float2 dx = make_float2(q[0] - K.cx, q[0] + K.cx);
+    const float2 dy = make_float2(q[1] - K.cy, q[1] + K.cy);
+    const float2 dz = make_float2(q[2] - K.cz, q[2] + K.cz);
+    const float2 dd = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    const float2 far = __ffma2_rn(make_float2(K1max, K1max), dd, make_float2(K2max * pp, K2max * pp));
+    C2<float> Rk = {0.0f, 0.0f};
+    if (far.x <= kSkipMixed && far.y <= kSkipMixed) return Rk;
+    const float2 pdd = __ffma2_rn(make_float2(p[2], p[2]), dz,
+                                  __ffma2_rn(make_float2(p[1], p[1]), dy,
+                                             __fmul2_rn(make_float2(p[0], p[0]), dx)));
+    const float2 gdz = __fmul2_rn(make_float2(-gam, -gam), dz);     // -g d_z
+    float2 P = make_float2(0.0f, 0.0f), Q = P, U = P, Wv = P;
+#pragma unroll 1
+    for (int k = 0; k < n_prim; ++k) {
+        const float K1 = I.rec.K1f[k], K2 = I.rec.K2f[k], K3 = I.rec.K3f[k], K4 = I.rec.K4f[k];
+        const float2 ex = __ffma2_rn(make_float2(K1, K1), dd, make_float2(K2 * pp, K2 * pp));
+        const float2 arg = __fmul2_rn(make_float2(K3, K3), pdd);
+        float2 mag, sn, cs;
+        mag.x = ex.x > kSkipMixed ? K4 * __expf(ex.x) : 0.0f;
+        mag.y = ex.y > kSkipMixed ? K4 * __expf(ex.y) : 0.0f;
+        __sincosf(arg.x, &sn.x, &cs.x);
+        __sincosf(arg.y, &sn.y, &cs.y);
+        const float2 A = __fmul2_rn(mag, make_float2(p[2], p[2]));   // mag p_z
+        const float2 B = __fmul2_rn(mag, gdz);                       // -mag g d_z
+        // (A + i B)(cs + i sn) = (A cs - B sn) + i (A sn + B cs)
+        P = __ffma2_rn(A, cs, P);
+        Q = __ffma2_rn(B, sn, Q);
+        U = __ffma2_rn(A, sn, U);
+        Wv = __ffma2_rn(B, cs, Wv);
+    }
+    Rk.x = (P.x + P.y) - (Q.x + Q.y);
+    Rk.y = (U.x + U.y) + (Wv.x + Wv.y);
+    return Rk;
+}
+
 // per-warp buffer of the chunk's contributions: 32 steps x 32 trajectories,
 // row stride 33
 constexpr int kRedStride = kWarp + 1;
@@ -462,7 +509,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     // a Gaussian overlap below e^kSkip of its peak is not evaluated: in MIXED
     // such a term is below 1e-13 of the same trajectory's terms near the
     // nucleus, far under the FP32 resolution of the sum
-    constexpr R kSkip = MIXED ? R(-30) : R(-200);
+    constexpr R kSkip = MIXED ? R(kSkipMixed) : R(-200);
 
     // ---- state
     R q[3], p[3], ql[3], pl[3];
@@ -520,6 +567,9 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             if (live && status == 0) {
                 const R pp = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
                 C2<R> Rk = {R(0), R(0)};
+                if constexpr (MIXED) {
+                    Rk = recomb_pair(I, K, q, p, pp, gam, K1max, K2max, n_prim);
+                } else {
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const R dx = c == 0 ? q[0] - K.cx : q[0] + K.cx;
@@ -550,6 +600,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                             Rk.y += ar * sn + ai * cs;
                         }
                     }
+                }
                 }
                 if (Rk.x != R(0) || Rk.y != R(0)) {
                     R sn, cs;
