@@ -36,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2608_13686_b300 import costs  # noqa: E402
+from paper_2608_13686_b300 import replicas  # noqa: E402
 from paper_2608_13686_b300 import workloads as W  # noqa: E402
 
 METRIC = W.METRIC if hasattr(W, "METRIC") else (
@@ -264,13 +265,14 @@ def run_ours(args):
         grids.append(g)
         # per rank its own Philox key: weak scaling over independent samples
         ens.append(S.sfhk_sample_initial(ctx, targets[i["target"]], ph, i["align"], i["n_traj"],
-                                         i["seed"] + 1000 * rank, i["instance"], sp))
+                                         replicas.rank_seed(i["seed"], rank), i["instance"], sp))
         spec.append(torch.empty((3, g["nt"] // 2), dtype=torch.float64, device="cuda"))
     torch.cuda.synchronize()
 
     def step(batch):
         for i, e in zip(instances, ens):
-            S.sfhk_sample_into(ctx, e, i["align"], i["seed"] + 1000 * rank, i["instance"], sp)
+            S.sfhk_sample_into(ctx, e, i["align"], replicas.rank_seed(i["seed"], rank),
+                               i["instance"], sp)
         S.sfhk_batch_launch(batch, sp)
         for e, g, o in zip(ens, grids, spec):
             vz_ptr, _ = S.sfhk_dipole_device(e)
@@ -330,11 +332,7 @@ def run_ours(args):
     traj_steps = sum(s["traj_steps"] for s in st)       # per step (the same every step)
     prop_ms = st[0]["kernel_ms"]                        # the batch launch of the last step
     ms = float(np.mean(ms_steps))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms)                   # the slowest rank's step time
     value = world * traj_steps / (ms * 1e-3)
     spectra_per_s = world * len(instances) / (ms * 1e-3)
     vz_mixed = [S.sfhk_dipole(ctx, e, g["nt"]) for e, g in zip(ens, grids)]
@@ -358,7 +356,8 @@ def run_ours(args):
     # e2e through the public API with host buffers (dipole and spectrum to host)
     def e2e_step():
         for i, e in zip(instances, ens):
-            S.sfhk_sample_into(ctx, e, i["align"], i["seed"] + 1000 * rank, i["instance"], sp)
+            S.sfhk_sample_into(ctx, e, i["align"], replicas.rank_seed(i["seed"], rank),
+                               i["instance"], sp)
         S.sfhk_batch_launch(batch, sp)
         for e, g in zip(ens, grids):
             vz = S.sfhk_dipole(ctx, e, g["nt"])

@@ -174,23 +174,36 @@ struct PotConst {
     int kind, screened;
 };
 
-// V, force F = -grad V and Hessian at the stage point q + o + l (both centres,
-// +-(R/2)n): q is the (high part of the) step's base position, o the RK4 stage
-// offset and l the low part of a two-float position (LO; zero in FP64).  In
-// two-float mode the centre is subtracted from q first (exact near a nucleus)
-// and o and l are added to that small difference, so the distance to a nearby
-// nucleus keeps the full two-float precision of the position.
-// OFS = false: the stage point is the base point itself (o ignored).
-template <typename R, bool LO, bool OFS = true>
-__device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz, R ox, R oy,
-                                          R oz, R lx, R ly, R lz, R& V, R& Fx, R& Fy, R& Fz,
-                                          Sym3<R>& H)
+// Differences of a step's base point from the two centres +-(R/2)n,
+// e_c = (q - c_c) + l, with l the low part of a two-float position (LO; zero
+// in FP64).  The centre is subtracted from the high part first (exact near a
+// nucleus) and the low part added to that small difference, so the distance
+// to a nearby nucleus keeps the two-float precision of the position.  They
+// are formed once per RK4 step and shared by its four stages.
+template <typename R, bool LO>
+__device__ __forceinline__ void centre_diffs(const PotConst<R>& K, const R q[3], const R l[3],
+                                             R e[2][3])
 {
-    if (!OFS) ox = oy = oz = R(0);
+    const R c[3] = {K.cx, K.cy, K.cz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        e[0][a] = LO ? (q[a] - c[a]) + l[a] : q[a] - c[a];
+        e[1][a] = LO ? (q[a] + c[a]) + l[a] : q[a] + c[a];
+    }
+}
+
+// V, force F = -grad V and Hessian at the stage point base + o, given the
+// base point's centre differences e (centre_diffs) and the RK4 stage offset
+// o; OFS = false: the stage point is the base point itself (o ignored).  The
+// harmonic test potential (R = 0) reads the position from e[0].
+template <typename R, bool OFS = true>
+__device__ __forceinline__ void potential(const PotConst<R>& K, const R e[2][3], R ox, R oy,
+                                          R oz, R& V, R& Fx, R& Fy, R& Fz, Sym3<R>& H)
+{
     if (K.kind != 0) {            // harmonic test potential
-        const R x = LO ? (qx + ox) + lx : qx + ox;
-        const R y = LO ? (qy + oy) + ly : qy + oy;
-        const R z = LO ? (qz + oz) + lz : qz + oz;
+        const R x = OFS ? e[0][0] + ox : e[0][0];
+        const R y = OFS ? e[0][1] + oy : e[0][1];
+        const R z = OFS ? e[0][2] + oz : e[0][2];
         V = R(0.5) * K.w2 * (x * x + y * y + z * z);
         Fx = -K.w2 * x;
         Fy = -K.w2 * y;
@@ -199,36 +212,16 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz
         H.xy = H.xz = H.yz = R(0);
         return;
     }
-    R d[2][3];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        R dx, dy, dz;
-        if (LO && !OFS) {
-            dx = (c == 0 ? qx - K.cx : qx + K.cx) + lx;
-            dy = (c == 0 ? qy - K.cy : qy + K.cy) + ly;
-            dz = (c == 0 ? qz - K.cz : qz + K.cz) + lz;
-        } else if (LO) {
-            dx = ((c == 0 ? qx - K.cx : qx + K.cx) + ox) + lx;
-            dy = ((c == 0 ? qy - K.cy : qy + K.cy) + oy) + ly;
-            dz = ((c == 0 ? qz - K.cz : qz + K.cz) + oz) + lz;
-        } else if (!OFS) {
-            dx = qx - (c == 0 ? K.cx : -K.cx);
-            dy = qy - (c == 0 ? K.cy : -K.cy);
-            dz = qz - (c == 0 ? K.cz : -K.cz);
-        } else {
-            dx = (qx + ox) - (c == 0 ? K.cx : -K.cx);
-            dy = (qy + oy) - (c == 0 ? K.cy : -K.cy);
-            dz = (qz + oz) - (c == 0 ? K.cz : -K.cz);
-        }
-        d[c][0] = dx;
-        d[c][1] = dy;
-        d[c][2] = dz;
-    }
     if constexpr (std::is_same<R, float>::value) {
         // FP32: the two centres side by side in the lanes of float2 values,
         // so that each per-centre operation is one f32x2 instruction
-        const float2 dx = make_float2(d[0][0], d[1][0]), dy = make_float2(d[0][1], d[1][1]),
-                     dz = make_float2(d[0][2], d[1][2]);
+        float2 dx = make_float2(e[0][0], e[1][0]), dy = make_float2(e[0][1], e[1][1]),
+               dz = make_float2(e[0][2], e[1][2]);
+        if (OFS) {
+            dx = __fadd2_rn(dx, make_float2(ox, ox));
+            dy = __fadd2_rn(dy, make_float2(oy, oy));
+            dz = __fadd2_rn(dz, make_float2(oz, oz));
+        }
         const float2 s2 = __ffma2_rn(
             dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(K.a2, K.a2))));
         const float2 u = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
@@ -266,6 +259,12 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, R qx, R qy, R qz
         H.xz = -(gx.x * dz.x + gx.y * dz.y);
         H.yz = -(gy.x * dz.x + gy.y * dz.y);
     } else {
+        const R o[3] = {ox, oy, oz};
+        R d[2][3];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) d[c][a] = OFS ? e[c][a] + o[a] : e[c][a];
         R g1[2], g2[2], vc[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {

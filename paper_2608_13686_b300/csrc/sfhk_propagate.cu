@@ -242,33 +242,30 @@ __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], c
                                            const R p[3], R E1, R E2, R E4, R h, R h2, R h6,
                                            Sym3<R> H[4], R dq[3], R dp[3], R& dS)
 {
-    R V, F[3];
+    R V, F[3], e[2][3];
+    centre_diffs<R, MIXED>(K, q, ql, e);
     const R z0 = R(0);
-    potential<R, MIXED, false>(K, q[0], q[1], q[2], z0, z0, z0, ql[0], ql[1], ql[2], V, F[0],
-                               F[1], F[2], H[0]);
+    potential<R, false>(K, e, z0, z0, z0, V, F[0], F[1], F[2], H[0]);
     const R k1p[3] = {F[0], F[1], F[2] - E1};
     const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
     R o[3], p2[3];
     scale3(h2, p, o);
     axpy3(h2, k1p, p, p2);
-    potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
-                        F[1], F[2], H[1]);
+    potential<R>(K, e, o[0], o[1], o[2], V, F[0], F[1], F[2], H[1]);
     const R k2p[3] = {F[0], F[1], F[2] - E2};
     const R k2s =
         R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - (q[2] + o[2]) * E2;
     R p3[3];
     scale3(h2, p2, o);
     axpy3(h2, k2p, p, p3);
-    potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
-                        F[1], F[2], H[2]);
+    potential<R>(K, e, o[0], o[1], o[2], V, F[0], F[1], F[2], H[2]);
     const R k3p[3] = {F[0], F[1], F[2] - E2};
     const R k3s =
         R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - (q[2] + o[2]) * E2;
     R p4[3];
     scale3(h, p3, o);
     axpy3(h, k3p, p, p4);
-    potential<R, MIXED>(K, q[0], q[1], q[2], o[0], o[1], o[2], ql[0], ql[1], ql[2], V, F[0],
-                        F[1], F[2], H[3]);
+    potential<R>(K, e, o[0], o[1], o[2], V, F[0], F[1], F[2], H[3]);
     const R k4s =
         R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - (q[2] + o[2]) * E4;
     dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
@@ -525,7 +522,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     R S = R(0), Sl = R(0);          // action (two-float in MIXED, Sl unused in FP64)
     C2<R> Cp = {R(1), R(0)};        // prefactor at the previous step
     int status = 0;                 // 0 alive, 1 prefactor filter, 2 non-finite, 3 stability filter
-    unsigned long long steps = 0;
+    unsigned int steps = 0;          // RK4 steps taken (< Nt)
 
     const R h = R(I.dt), h2 = R(0.5 * I.dt), h6 = R(I.dt / 6.0);
     const R hh4 = R(I.dt * I.dt / 4.0), hh2 = R(I.dt * I.dt / 2.0), hh6 = R(I.dt * I.dt / 6.0);
