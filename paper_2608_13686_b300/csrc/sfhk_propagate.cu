@@ -321,8 +321,14 @@ __device__ __forceinline__ void m_update(Mono<R>& M, const Sym3<R> H[4], R h, R 
     }
 }
 
-// The same update on packed column pairs: every operation is one f32x2
-// instruction for two columns, in the same order as the scalar form.
+// The same update on packed column pairs, every operation one f32x2
+// instruction for two columns.  The stage sums are accumulated inside the
+// Hessian products instead of after them (hxa: y = H x + acc), which saves
+// the separate adds:
+//   s12 = a1 + a2,  sA = H3 x3 + s12 = a1 + a2 + a3,
+//   Mq' = xb - h^2/6 sA,
+//   Mp' = v0 - h/6 (H4 x4 + (2 sA - a1)) = v0 - h/6 (a1 + 2 a2 + 2 a3 + a4).
+// a1 is formed negated (from -H1), so that all three of its uses are FMAs.
 __device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
 
 __device__ __forceinline__ void hx2(const Sym3<float>& H, const float2 x[3], float2 y[3])
@@ -332,14 +338,23 @@ __device__ __forceinline__ void hx2(const Sym3<float>& H, const float2 x[3], flo
     y[2] = __ffma2_rn(bc(H.zz), x[2], __ffma2_rn(bc(H.yz), x[1], __fmul2_rn(bc(H.xz), x[0])));
 }
 
+__device__ __forceinline__ void hxa2(const Sym3<float>& H, const float2 x[3], const float2 acc[3],
+                                     float2 y[3])
+{
+    y[0] = __ffma2_rn(bc(H.xz), x[2], __ffma2_rn(bc(H.xy), x[1], __ffma2_rn(bc(H.xx), x[0], acc[0])));
+    y[1] = __ffma2_rn(bc(H.yz), x[2], __ffma2_rn(bc(H.yy), x[1], __ffma2_rn(bc(H.xy), x[0], acc[1])));
+    y[2] = __ffma2_rn(bc(H.zz), x[2], __ffma2_rn(bc(H.yz), x[1], __ffma2_rn(bc(H.xz), x[0], acc[2])));
+}
+
 __device__ __forceinline__ void m_update(Mono<float>& M, const Sym3<float> H[4], float h,
                                          float h2, float h6, float hh4, float hh2, float hh6)
 {
-    const float2 vh = bc(h), vh2 = bc(h2), mh6 = bc(-h6), mhh4 = bc(-hh4), mhh2 = bc(-hh2),
-                 mhh6 = bc(-hh6), two = bc(2.0f);
+    const float2 vh = bc(h), vh2 = bc(h2), mh6 = bc(-h6), phh4 = bc(hh4), mhh2 = bc(-hh2),
+                 mhh6 = bc(-hh6), two = bc(2.0f), m1 = bc(-1.0f);
+    const Sym3<float> nH1 = {-H[0].xx, -H[0].yy, -H[0].zz, -H[0].xy, -H[0].xz, -H[0].yz};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float2 x0[3], v0[3], xs[3], xb[3], a1[3], a2[3], a3[3], a4[3];
+        float2 x0[3], v0[3], xs[3], xb[3], a1[3], a2[3], t[3];   // a1 holds -a1
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             x0[r] = M.q[k][r];
@@ -347,20 +362,23 @@ __device__ __forceinline__ void m_update(Mono<float>& M, const Sym3<float> H[4],
             xs[r] = __ffma2_rn(vh2, v0[r], x0[r]);
             xb[r] = __ffma2_rn(vh, v0[r], x0[r]);
         }
-        hx2(H[0], x0, a1);
+        hx2(nH1, x0, a1);                               // -a1
         hx2(H[1], xs, a2);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) xs[r] = __ffma2_rn(mhh4, a1[r], xs[r]);
-        hx2(H[2], xs, a3);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) xs[r] = __ffma2_rn(mhh2, a2[r], xb[r]);
-        hx2(H[3], xs, a4);
+        for (int r = 0; r < 3; ++r) {
+            xs[r] = __ffma2_rn(phh4, a1[r], xs[r]);     // x3 = x2 - h^2/4 a1
+            t[r] = __ffma2_rn(m1, a1[r], a2[r]);        // s12 = a1 + a2
+        }
+        hxa2(H[2], xs, t, t);                           // sA
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            M.q[k][r] = __ffma2_rn(mhh6, __fadd2_rn(__fadd2_rn(a1[r], a2[r]), a3[r]), xb[r]);
-            M.p[k][r] = __ffma2_rn(
-                mh6, __ffma2_rn(two, __fadd2_rn(a2[r], a3[r]), __fadd2_rn(a1[r], a4[r])), v0[r]);
+            xs[r] = __ffma2_rn(mhh2, a2[r], xb[r]);     // x4
+            M.q[k][r] = __ffma2_rn(mhh6, t[r], xb[r]);
+            t[r] = __ffma2_rn(two, t[r], a1[r]);        // 2 sA - a1
         }
+        hxa2(H[3], xs, t, t);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) M.p[k][r] = __ffma2_rn(mh6, t[r], v0[r]);
     }
 }
 
