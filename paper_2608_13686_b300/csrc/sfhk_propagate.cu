@@ -59,7 +59,7 @@ struct Mono {
     R q[6][3], p[6][3];
     __device__ __forceinline__ R Q(int c, int r) const { return q[c][r]; }
     __device__ __forceinline__ R P(int c, int r) const { return p[c][r]; }
-    __device__ __forceinline__ void identity()
+    __device__ __forceinline__ void identity(R)
     {
 #pragma unroll
         for (int c = 0; c < 6; ++c)
@@ -71,26 +71,32 @@ struct Mono {
     }
 };
 // FP32: columns k and k + 3 share one float2, so that the RK4 update runs on
-// packed pairs (two FP32 operations per f32x2 instruction).
+// packed pairs (two FP32 operations per f32x2 instruction), and column k + 3
+// is stored times -gamma: a float2 is then (Re, Im) of a column of
+// Y = M [I; -i gamma I], from which the prefactor matrix
+// B = Y_q + (i/gamma) Y_p takes two FMAs per element.  The update is linear
+// and column by column, so the scaling does not change it.
 template <>
 struct Mono<float> {
     float2 q[3][3], p[3][3];
+    float nig;                      // -1/gamma
     __device__ __forceinline__ float Q(int c, int r) const
     {
-        return c < 3 ? q[c][r].x : q[c - 3][r].y;
+        return c < 3 ? q[c][r].x : q[c - 3][r].y * nig;
     }
     __device__ __forceinline__ float P(int c, int r) const
     {
-        return c < 3 ? p[c][r].x : p[c - 3][r].y;
+        return c < 3 ? p[c][r].x : p[c - 3][r].y * nig;
     }
-    __device__ __forceinline__ void identity()
+    __device__ __forceinline__ void identity(float gam)
     {
+        nig = -1.0f / gam;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 q[k][r] = make_float2(k == r ? 1.0f : 0.0f, 0.0f);
-                p[k][r] = make_float2(0.0f, k == r ? 1.0f : 0.0f);
+                p[k][r] = make_float2(0.0f, k == r ? -gam : 0.0f);
             }
     }
 };
@@ -126,6 +132,22 @@ __device__ __forceinline__ float fmax3(float a, float b, float c)
 __device__ __forceinline__ double fmax3(double a, double b, double c) { return fmax(fmax(a, b), c); }
 
 // largest |element| of the stability matrix
+__device__ __forceinline__ float max_abs_M(const Mono<float>& M)
+{
+    // unscaled columns from .x, the -gamma-scaled ones from .y
+    float mx[6], my[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        mx[2 * k] = fmax3(fabsf(M.q[k][0].x), fabsf(M.q[k][1].x), fabsf(M.q[k][2].x));
+        mx[2 * k + 1] = fmax3(fabsf(M.p[k][0].x), fabsf(M.p[k][1].x), fabsf(M.p[k][2].x));
+        my[2 * k] = fmax3(fabsf(M.q[k][0].y), fabsf(M.q[k][1].y), fabsf(M.q[k][2].y));
+        my[2 * k + 1] = fmax3(fabsf(M.p[k][0].y), fabsf(M.p[k][1].y), fabsf(M.p[k][2].y));
+    }
+    const float ax = fmax3(fmax3(mx[0], mx[1], mx[2]), mx[3], fmax(mx[4], mx[5]));
+    const float ay = fmax3(fmax3(my[0], my[1], my[2]), my[3], fmax(my[4], my[5]));
+    return fmax(ax, ay * fabsf(M.nig));
+}
+
 template <typename R>
 __device__ __forceinline__ R max_abs_M(const Mono<R>& M)
 {
@@ -382,6 +404,21 @@ __device__ __forceinline__ void m_update(Mono<float>& M, const Sym3<float> H[4],
     }
 }
 
+// Element (r, c) of 2 x the prefactor matrix, M_qq + M_pp + i (M_pq / g - g M_qp).
+template <typename R>
+__device__ __forceinline__ C2<R> b_elem(const Mono<R>& M, int r, int c, R gam, R igam)
+{
+    return {M.Q(c, r) + M.P(3 + c, r), igam * M.P(c, r) - gam * M.Q(3 + c, r)};
+}
+// FP32 (column c + 3 stored times -g): Re = Q_c + P_{c+3} = q.x - p.y / g,
+// Im = P_c / g - g Q_{c+3} = p.x / g + q.y
+__device__ __forceinline__ C2<float> b_elem(const Mono<float>& M, int r, int c, float,
+                                            float igam)
+{
+    const float2 q = M.q[c][r], p = M.p[c][r];
+    return {fmaf(-igam, p.y, q.x), fmaf(igam, p.x, q.y)};
+}
+
 // Prefactor of the current M on the continuous branch (sign kept within a
 // right angle of the previous C), then the per-step checks in the order:
 // finiteness, prefactor filter, stability filter.
@@ -396,7 +433,7 @@ __device__ __forceinline__ void prefactor_and_checks(const Mono<R>& M, R gam,
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            B[3 * r + c] = {M.Q(c, r) + M.P(3 + c, r), igam * M.P(c, r) - gam * M.Q(3 + c, r)};
+            B[3 * r + c] = b_elem(M, r, c, gam, igam);
     const C2<R> m0 = cm(B[4], B[8]), m1 = cm(B[5], B[7]);
     const C2<R> m2 = cm(B[3], B[8]), m3 = cm(B[5], B[6]);
     const C2<R> m4 = cm(B[3], B[7]), m5 = cm(B[4], B[6]);
@@ -536,7 +573,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         pl[a] = R(pd[a] - double(p[a]));
     }
     Mono<R> M;
-    M.identity();
+    M.identity(gam);
     R S = R(0), Sl = R(0);          // action (two-float in MIXED, Sl unused in FP64)
     C2<R> Cp = {R(1), R(0)};        // prefactor at the previous step
     int status = 0;                 // 0 alive, 1 prefactor filter, 2 non-finite, 3 stability filter
