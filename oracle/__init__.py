@@ -102,6 +102,10 @@ def lib():
                                 C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_uint64,
                                 C.c_uint64, _dp, _dp]
         L.or_quad_nodes.argtypes = [C.c_int, _dp, _dp]
+        L.or_propagate_returns.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
+                                           C.c_double, C.c_double, _dp, C.c_uint64, C.c_double,
+                                           _dp, C.c_double, C.c_double, _dp, C.c_int]
+        L.or_propagate_returns.restype = C.c_int
         L.or_saddle_modified.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
                                          C.c_double, _dp]
         L.or_saddle_modified.restype = C.c_int
@@ -334,3 +338,19 @@ def pulse_Edot_complex(p, tau):
     lib().or_pulse_Edot_complex(C.byref(pulse_in(p)), float(np.real(tau)), float(np.imag(tau)),
                                 _p(out))
     return out[0] + 1j * out[1]
+
+
+def propagate_returns(t, p, soa, gamma, cutoff=0.0, stab_cutoff=0.0, r_out=5.0, r_in=2.0,
+                      n_norm=0.0, n_threads=0):
+    """propagate() that also records each trajectory's first return: the first
+    grid step with |q_z| < r_in (along the polarisation axis, measured from
+    the molecular centre) after one with |q_z| > r_out, and |p|^2/2 there.
+    Returns (vz, steps, energies); step -1 = no return."""
+    soa = np.ascontiguousarray(soa, dtype=np.float64)
+    n = soa.shape[1]
+    vz = np.zeros(pulse_derived(p)["nt"])
+    ret = np.zeros((2, n))
+    lib().or_propagate_returns(C.byref(target_in(t)), C.byref(pulse_in(p)), gamma, cutoff,
+                               float(stab_cutoff), _p(soa), n, float(n_norm), _p(vz), r_out, r_in,
+                               _p(ret), n_threads)
+    return vz, ret[0].astype(int), ret[1]

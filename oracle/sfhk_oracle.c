@@ -852,11 +852,28 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
 /* ------------------------------------------------------------------ */
 #define OR_NFINAL 47
 
+/* First return (for the long/short trajectory analysis of Sec. III.D;    */
+/* reading): the first grid step at which the electron is closer than     */
+/* r_in to the molecular centre along the polarisation axis (|q_z| < r_in) */
+/* after having been farther than r_out (|q_z| > r_out), and its kinetic  */
+/* energy |p|^2/2 there.  returns[j] = step (-1: none), returns[n + j] =  */
+/* energy.                                                                */
+typedef struct {
+    double r_out, r_in;
+    double* returns;
+} or_return_opts;
+
 static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm,
                           double gamma, double cutoff, double stab_cutoff,
                           const double* soa, uint64_t n,
-                          uint64_t j, double scale, double* vz, double* final_state)
+                          uint64_t j, double scale, double* vz, double* final_state,
+                          const or_return_opts* ro)
 {
+    int left = 0, returned = 0;
+    if (ro && ro->returns) {
+        ro->returns[j] = -1.0;
+        ro->returns[n + j] = 0.0;
+    }
     int n0 = (int)soa[j];
     double nhat[3] = {soa[7 * n + j], soa[8 * n + j], soa[9 * n + j]};
     cplx w = soa[10 * n + j] + I * soa[11 * n + j];
@@ -889,6 +906,15 @@ static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm
             for (int a = 0; a < 36; ++a) if (fabs(y[6 + a]) > mmax) mmax = fabs(y[6 + a]);
             if (mmax > stab_cutoff) { status = 3; break; }
         }
+        if (ro && ro->returns && !returned) {
+            double az = fabs(y[2]);
+            if (az > ro->r_out) left = 1;
+            else if (left && az < ro->r_in) {
+                returned = 1;
+                ro->returns[j] = (double)m;
+                ro->returns[n + j] = 0.5 * (y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
+            }
+        }
         cplx R = recomb(T, Nnorm, nhat, y, y + 3, gamma);
         cplx X = w * C * cexp(I * (y[42] - T->Ip * t)) * R;
         vz[m] += -2.0 * scale * creal(X);
@@ -906,9 +932,34 @@ static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm
 /* vz_out[nt] receives the dipole; n_norm is N of the 1/N normalisation
  * (0 -> n).  n_threads <= 0 uses all cores.  Returns the count of
  * trajectories that were filtered (either filter) or non-finite.        */
+static int propagate_all(const or_target_in* T, const or_pulse_in* Pin, double gamma,
+                         double cutoff, double stab_cutoff, const double* soa, uint64_t n,
+                         double n_norm, double* vz_out, double* final_state, int n_threads,
+                         const or_return_opts* ro);
+
 int or_propagate(const or_target_in* T, const or_pulse_in* Pin, double gamma, double cutoff,
                  double stab_cutoff, const double* soa, uint64_t n, double n_norm, double* vz_out,
                  double* final_state, int n_threads)
+{
+    return propagate_all(T, Pin, gamma, cutoff, stab_cutoff, soa, n, n_norm, vz_out, final_state,
+                         n_threads, NULL);
+}
+
+/* The same, also recording each trajectory's first return (returns: 2 x n). */
+int or_propagate_returns(const or_target_in* T, const or_pulse_in* Pin, double gamma,
+                         double cutoff, double stab_cutoff, const double* soa, uint64_t n,
+                         double n_norm, double* vz_out, double r_out, double r_in,
+                         double* returns, int n_threads)
+{
+    or_return_opts ro = {r_out, r_in, returns};
+    return propagate_all(T, Pin, gamma, cutoff, stab_cutoff, soa, n, n_norm, vz_out, NULL,
+                         n_threads, &ro);
+}
+
+static int propagate_all(const or_target_in* T, const or_pulse_in* Pin, double gamma,
+                         double cutoff, double stab_cutoff, const double* soa, uint64_t n,
+                         double n_norm, double* vz_out, double* final_state, int n_threads,
+                         const or_return_opts* ro)
 {
     or_pulse P = or_make_pulse(Pin);
     double Nnorm = orbital_norm(T);
@@ -928,7 +979,7 @@ int or_propagate(const or_target_in* T, const or_pulse_in* Pin, double gamma, do
         tid = omp_get_thread_num();
 #endif
         propagate_one(T, &P, Nnorm, gamma, cutoff, stab_cutoff, soa, n, (uint64_t)j, scale,
-                      part + (size_t)tid * P.nt, final_state);
+                      part + (size_t)tid * P.nt, final_state, ro);
     }
     for (int t = 0; t < nthr; ++t)
         for (int m = 0; m < P.nt; ++m) vz_out[m] += part[(size_t)t * P.nt + m];
