@@ -152,6 +152,12 @@ typedef struct {
     int kernel_variant;               /* register-cap variant 1..6 (no cap, then at
                                          most 168, 152, 144, 136, 128 registers per
                                          thread); 0 = the context's tuned choice */
+    int record_returns;               /* keep each trajectory's first return for
+                                         sfhk_returns (long/short trajectories,
+                                         Sec. III.D) */
+    double return_r_out, return_r_in; /* the return: first step with |q_z| <
+                                         r_in after one with |q_z| > r_out
+                                         (0 < r_in < r_out) */
 } sfhk_run_opts;
 
 /* Per-ensemble counters of the last propagation. */
@@ -292,6 +298,16 @@ SFHK_API int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out);
  * one at the step where it stopped (n_state = that step).  Synchronous.
  * Errors: SFHK_E_INVAL (no dump taken). */
 SFHK_API int sfhk_final_state(sfhk_ensemble* e, double* host, uint64_t n_traj);
+
+/* First returns of the last propagation run with record_returns: 2 x n_traj
+ * doubles, host[j] = the grid step of trajectory j's first return (-1: none),
+ * host[n_traj + j] = its kinetic energy |p|^2/2 there.  The return is the
+ * first step at which the electron is closer than r_in to the molecular
+ * centre along the polarisation axis (|q_z| < r_in) after one with
+ * |q_z| > r_out, while the trajectory is alive (not filtered).  Histograms of
+ * birth step against return step separate the long and short trajectories of
+ * Sec. III.D.  Synchronous.  Errors: SFHK_E_INVAL (not recorded, wrong n). */
+SFHK_API int sfhk_returns(sfhk_ensemble* e, double* host, uint64_t n_traj);
 
 /* Spectrum (Eq. 3): v(omega_k) = sum_n v_z(t_n) W_H(t_n) e^{i omega_k t_n} dt,
  * W_H(t) = [1 + cos(pi t / tau_H)]/2 for |t| <= tau_H (else 0),

@@ -120,7 +120,8 @@ void ensemble_free(sfhk_ensemble* e)
     if (!e) return;
     Ctx* c = e->ctx;
     for (DeviceBuf* b : {&e->soa, &e->n0, &e->perm, &e->items, &e->ph, &e->phf, &e->vz,
-                         &e->dump, &e->counters, &e->cdf, &e->hist, &e->inst, &e->qctr})
+                         &e->dump, &e->counters, &e->cdf, &e->hist, &e->inst, &e->qctr,
+                         &e->returns})
         c->release(*b);
     if (e->ev_start) cudaEventDestroy(e->ev_start);
     if (e->ev_stop) cudaEventDestroy(e->ev_stop);
@@ -157,6 +158,9 @@ DevInstance make_instance(sfhk_ensemble* e, const sfhk_run_opts& o)
     I.n0 = (const int*)e->n0.p;
     I.vz = (double*)e->vz.p;
     I.dump = o.dump_final ? (double*)e->dump.p : nullptr;
+    I.returns = o.record_returns ? (double*)e->returns.p : nullptr;
+    I.ret_out = o.return_r_out;
+    I.ret_in = o.return_r_in;
     I.counters = (unsigned long long*)e->counters.p;
     I.n = e->n;
     I.nt = e->pulse->nt;
@@ -183,6 +187,9 @@ int check_opts(const sfhk_run_opts* o)
     if (o->block_threads < 0 || o->block_threads > 128 || o->block_threads % 32) return SFHK_E_INVAL;
     if (o->blocks_per_sm < 0) return SFHK_E_INVAL;
     if (o->kernel_variant < 0 || o->kernel_variant > kPropVariants) return SFHK_E_INVAL;
+    if (o->record_returns && !(o->return_r_in > 0.0 && o->return_r_out > o->return_r_in &&
+                               std::isfinite(o->return_r_out)))
+        return SFHK_E_INVAL;
     return SFHK_OK;
 }
 
@@ -196,6 +203,11 @@ int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s)
         int rc = c->alloc(e->dump, sizeof(double) * kFinalFields * (size_t)e->n);
         if (rc) return rc;
     }
+    if (o.record_returns && !e->returns.p) {
+        int rc = c->alloc(e->returns, sizeof(double) * 2 * (size_t)e->n);
+        if (rc) return rc;
+    }
+    e->returns_kept = o.record_returns != 0;
     SFHK_CUDA_TRY(cudaMemsetAsync(e->vz.p, 0, sizeof(double) * e->pulse->nt, s));
     SFHK_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(unsigned long long) * 3, s));
     SFHK_CUDA_TRY(cudaMemsetAsync((unsigned long long*)e->counters.p + 4, 0,
@@ -643,6 +655,7 @@ int sfhk_batch_create(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens, const s
     b->ens.assign(ens, ens + n_ens);
     b->opts = *o;
     b->opts.dump_final = 0;
+    b->opts.record_returns = 0;
     for (int i = 0; i < n_ens; ++i) {
         b->total_items += ens[i]->n_items;
         b->max_nt = std::max(b->max_nt, ens[i]->pulse->nt);
@@ -747,6 +760,7 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
     const int items = (max_items > 0 && max_items < e->n_items) ? max_items : e->n_items;
     sfhk_run_opts oo = *o;
     oo.dump_final = 0;
+    oo.record_returns = 0;
     if ((rc = prepare_outputs(e, oo, 0))) return rc;
     const DevInstance I = make_instance(e, oo);
     SFHK_CUDA_TRY(cudaMemcpy(e->inst.p, &I, sizeof I, cudaMemcpyHostToDevice));
@@ -827,6 +841,18 @@ int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out)
         out->kernel_ms = ms;
     else
         cudaGetLastError();
+    return SFHK_OK;
+}
+
+int sfhk_returns(sfhk_ensemble* e, double* host, uint64_t n_traj)
+{
+    if (!e || !host || (long long)n_traj != e->n || !e->returns_kept || !e->returns.p)
+        return SFHK_E_INVAL;
+    int rc = set_device(e->ctx->device);
+    if (rc) return rc;
+    SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_done));
+    SFHK_CUDA_TRY(cudaMemcpy(host, e->returns.p, sizeof(double) * 2 * e->n,
+                             cudaMemcpyDeviceToHost));
     return SFHK_OK;
 }
 

@@ -51,6 +51,8 @@ struct DevInstance {
     const int* n0;         // per trajectory grid index of t0
     double* vz;            // Nt dipole accumulator
     double* dump;          // 47 x n or null
+    double* returns;       // 2 x n first returns (step, energy) or null
+    double ret_out, ret_in;
     unsigned long long* counters;   // [filtered, nonfinite, steps, invalid, unstable]
     long long n;
     int nt;
@@ -111,10 +113,11 @@ struct Ensemble {
     const Pulse* pulse;
     long long n = 0;
     double n_norm = 0;
-    DeviceBuf soa, n0, perm, items, ph, phf, vz, dump, counters;
+    DeviceBuf soa, n0, perm, items, ph, phf, vz, dump, counters, returns;
     int n_items = 0;
     unsigned long long n_invalid = 0;
     bool dumped = false;
+    bool returns_kept = false;
     bool have_result = false;
     bool sampled = false;          // created by the device sampler
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr, ev_done = nullptr;

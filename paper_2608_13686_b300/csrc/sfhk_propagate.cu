@@ -574,6 +574,11 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     }
     Mono<R> M;
     M.identity(gam);
+    double* const ret = I.returns;  // first returns (optional)
+    const R r_out = R(I.ret_out), r_in = R(I.ret_in);
+    bool left = false;
+    int n_ret = -1;
+    R e_ret = R(0);
     R S = R(0), Sl = R(0);          // action (two-float in MIXED, Sl unused in FP64)
     C2<R> Cp = {R(1), R(0)};        // prefactor at the previous step
     int status = 0;                 // 0 alive, 1 prefactor filter, 2 non-finite, 3 stability filter
@@ -618,6 +623,15 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             R x = R(0);
             if (live && status == 0) {
                 const R pp = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+                // first return along the polarisation axis (optional)
+                if (ret != nullptr && n_ret < 0) {
+                    const R az = fabs(q[2]);
+                    if (az > r_out) left = true;
+                    else if (left && az < r_in) {
+                        n_ret = nn;
+                        e_ret = R(0.5) * pp;
+                    }
+                }
                 C2<R> Rk = {R(0), R(0)};
                 if constexpr (MIXED) {
                     Rk = recomb_pair(I, K, q, p, pp, gam, K1max, K2max, n_prim);
@@ -747,6 +761,10 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         if (nonf) atomicAdd(&I.counters[1], (unsigned long long)__popc(nonf));
         if (unst) atomicAdd(&I.counters[4], (unsigned long long)__popc(unst));
         atomicAdd(&I.counters[2], st);
+    }
+    if (ret != nullptr && has) {
+        ret[j] = double(n_ret);
+        ret[n + j] = double(e_ret);
     }
     if (I.dump != nullptr && has) {
         double* d = I.dump;

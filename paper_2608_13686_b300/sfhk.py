@@ -53,7 +53,9 @@ class sfhk_align_desc(C.Structure):
 class sfhk_run_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("gamma", C.c_double), ("prefactor_cutoff", C.c_double),
                 ("dump_final", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
-                ("stability_cutoff", C.c_double), ("kernel_variant", C.c_int)]
+                ("stability_cutoff", C.c_double), ("kernel_variant", C.c_int),
+                ("record_returns", C.c_int), ("return_r_out", C.c_double),
+                ("return_r_in", C.c_double)]
 
 
 class sfhk_stats(C.Structure):
@@ -150,6 +152,7 @@ def _load():
         "sfhk_dipole_device": ([_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)], C.c_int),
         "sfhk_stats_get": ([_vp, C.POINTER(sfhk_stats)], C.c_int),
         "sfhk_final_state": ([_vp, _dp, C.c_uint64], C.c_int),
+        "sfhk_returns": ([_vp, _dp, C.c_uint64], C.c_int),
         "sfhk_spectrum": ([_vp, C.c_size_t, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp,
                            C.c_size_t, C.c_int, _vp], C.c_int),
         "sfhk_gabor": ([_vp, C.c_size_t, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -209,9 +212,11 @@ def align_desc(a) -> sfhk_align_desc:
 
 
 def run_opts(precision=SFHK_FP64, gamma=0.5, cutoff=0.0, dump=False, block_threads=0,
-             blocks_per_sm=0, stab_cutoff=0.0, kernel_variant=0) -> sfhk_run_opts:
+             blocks_per_sm=0, stab_cutoff=0.0, kernel_variant=0, returns=None) -> sfhk_run_opts:
+    """returns = (r_out, r_in) records each trajectory's first return."""
+    r_out, r_in = returns if returns else (0.0, 0.0)
     return sfhk_run_opts(precision, gamma, cutoff, int(dump), block_threads, blocks_per_sm,
-                         stab_cutoff, kernel_variant)
+                         stab_cutoff, kernel_variant, int(bool(returns)), r_out, r_in)
 
 
 # ------------------------------------------------------------------ C-ABI calls
@@ -348,6 +353,13 @@ def sfhk_stats_get(ens):
     s = sfhk_stats()
     _check(_load().sfhk_stats_get(ens, C.byref(s)), "sfhk_stats_get")
     return {f: getattr(s, f) for f, _ in sfhk_stats._fields_}
+
+
+def sfhk_returns(ens, n):
+    """(steps, energies) of the first returns; step -1 = none."""
+    out = np.zeros((2, n))
+    _check(_load().sfhk_returns(ens, _p(out), n), "sfhk_returns")
+    return out[0].astype(int), out[1]
 
 
 def sfhk_final_state(ens, n):
@@ -487,5 +499,5 @@ EXPORTED = [
     "sfhk_launch_count", "sfhk_autotune", "sfhk_spectrum_noalloc", "sfhk_server_create",
     "sfhk_server_destroy", "sfhk_submit", "sfhk_poll", "sfhk_wait", "sfhk_cancel",
     "sfhk_server_stats_get", "sfhk_batch_create", "sfhk_batch_launch", "sfhk_batch_destroy",
-    "sfhk_gabor",
+    "sfhk_gabor", "sfhk_returns",
 ]

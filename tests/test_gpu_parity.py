@@ -331,3 +331,35 @@ def test_sfhk2_dipole_end_to_end(S, ctx):
     S.sfhk_destroy_ensemble(e)
     S.sfhk_destroy_pulse(ph)
     S.sfhk_destroy_target(th)
+
+
+def test_first_returns_match_oracle(S, ctx):
+    """First returns (long/short trajectory analysis, Sec. III.D): FP64 steps
+    equal the oracle's and energies agree; mixed precision agrees except at
+    threshold ties."""
+    t, p = W.TARGETS["N2"], W.PULSE_1200
+    soa, _, _ = O.sample(t, p, W.fixed(0.0), seed=17, n=700)
+    _, st_o, en_o = O.propagate_returns(t, p, soa, GAMMA, cutoff=CUT, stab_cutoff=STAB,
+                                        r_out=6.0, r_in=2.0)
+    th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, p)
+    e = S.sfhk_load_ensemble(ctx, th, ph, soa, 0.0)
+    for prec in (S.SFHK_FP64, S.SFHK_MIXED):
+        S.sfhk_propagate(ctx, e, S.run_opts(prec, GAMMA, CUT, stab_cutoff=STAB,
+                                            returns=(6.0, 2.0)))
+        st, en = S.sfhk_returns(e, soa.shape[1])
+        if prec == S.SFHK_FP64:
+            assert np.array_equal(st, st_o)
+            ok = st_o >= 0
+            assert np.allclose(en[ok], en_o[ok], rtol=1e-9, atol=1e-12)
+        else:
+            assert np.mean(st == st_o) >= 0.99
+            both = (st == st_o) & (st_o >= 0)
+            assert np.allclose(en[both], en_o[both], rtol=1e-3, atol=1e-6)
+    assert (st_o >= 0).sum() >= 50
+    # without the option the call is refused
+    S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB))
+    with pytest.raises(RuntimeError):
+        S.sfhk_returns(e, soa.shape[1])
+    S.sfhk_destroy_ensemble(e)
+    S.sfhk_destroy_pulse(ph)
+    S.sfhk_destroy_target(th)
