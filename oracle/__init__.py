@@ -57,7 +57,8 @@ class TargetIn(C.Structure):
     _fields_ = [("kind", C.c_int), ("n_prim", C.c_int), ("R", C.c_double),
                 ("Zinf", C.c_double), ("Z0", C.c_double), ("alpha", C.c_double),
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
-                ("pexp", C.c_double * 8), ("pcoef", C.c_double * 8), ("ionization", C.c_int)]
+                ("pexp", C.c_double * 8), ("pcoef", C.c_double * 8), ("ionization", C.c_int),
+                ("sampling", C.c_int), ("sampling_factor", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -106,6 +107,9 @@ def lib():
                                            C.c_double, C.c_double, _dp, C.c_uint64, C.c_double,
                                            _dp, C.c_double, C.c_double, _dp, C.c_int]
         L.or_propagate_returns.restype = C.c_int
+        L.or_abs_sampling_constants.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int,
+                                                C.c_double, C.c_double, C.c_int, C.c_uint64,
+                                                C.c_uint32, _dp]
         L.or_saddle_modified.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
                                          C.c_double, _dp]
         L.or_saddle_modified.restype = C.c_int
@@ -132,6 +136,8 @@ def target_in(t) -> TargetIn:
     T = TargetIn()
     T.kind = int(t.get("kind", POT_MOLECULE))
     T.ionization = int(t.get("ionization", 0))
+    T.sampling = int(t.get("sampling", 0))
+    T.sampling_factor = float(t.get("sampling_factor", 0.0))
     T.n_prim = len(t.get("pexp", ()))
     for name in ("R", "Zinf", "Z0", "alpha", "soft_a", "Ip", "ho_omega"):
         setattr(T, name, float(t.get(name, 0.0)))
@@ -354,3 +360,13 @@ def propagate_returns(t, p, soa, gamma, cutoff=0.0, stab_cutoff=0.0, r_out=5.0, 
                                float(stab_cutoff), _p(soa), n, float(n_norm), _p(vz), r_out, r_in,
                                _p(ret), n_threads)
     return vz, ret[0].astype(int), ret[1]
+
+
+def abs_sampling_constants(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance=0):
+    """(M, P) of the |a|-proportional sampler: acceptance min(1, |w|/M),
+    accepted weight P w / alpha."""
+    out = np.zeros(2)
+    k = int(align[3]) if len(align) > 3 else 0
+    lib().or_abs_sampling_constants(C.byref(target_in(t)), C.byref(pulse_in(p)), int(align[0]),
+                                    float(align[1]), float(align[2]), k, seed, instance, _p(out))
+    return out[0], out[1]

@@ -73,6 +73,9 @@ typedef struct {
     double pcoef[8];    /* primitive coefficients (un-normalised)         */
     int ionization;     /* 0: SFA saddle (Eq. 2); 1: modified saddle      */
                         /* with -eta E(t_s).r0 (SFHK2, Sec. III.D)        */
+    int sampling;       /* 0: proposal with weights a/pdf; 1: initial    */
+                        /* points distributed ~ |a| (Sec. II.B)           */
+    double sampling_factor; /* kappa of the |a| sampler (<= 0: 5)         */
 } or_target_in;
 
 /* ------------------------------------------------------------------ */
@@ -112,16 +115,21 @@ static double or_u01(uint32_t a, uint32_t b)
 /* The uniforms of trajectory j of instance `instance`: counter
  * (j mod 2^32, j div 2^32, instance, draw), key (seed mod 2^32, seed div 2^32).
  * draw 0 -> (u_time, u_bm1), draw 1 -> (u_bm2, u_al1), draw 2 -> (u_al2, -). */
-void or_uniforms(uint64_t seed, uint32_t instance, uint64_t j, double u[6])
+static void uniforms_at(uint64_t seed, uint32_t instance, uint64_t j, uint32_t d0, double u[6])
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (uint32_t d = 0; d < 3; ++d) {
-        uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(j >> 32), instance, d};
+        uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(j >> 32), instance, d0 + d};
         uint32_t r[4];
         or_philox4x32_10(ctr, key, r);
         u[2 * d] = or_u01(r[0], r[1]);
         u[2 * d + 1] = or_u01(r[2], r[3]);
     }
+}
+
+void or_uniforms(uint64_t seed, uint32_t instance, uint64_t j, double u[6])
+{
+    uniforms_at(seed, instance, j, 0u, u);
 }
 
 /* ------------------------------------------------------------------ */
@@ -733,93 +741,211 @@ void or_adk_table(const or_pulse_in* Pin, double Ip, double* W, double* cdf)
     }
 }
 
+/* One draw of the proposal and its amplitude: t0, k_perp, axis from the  */
+/* six uniforms u, then saddle, exit, action, amplitude and the weight     */
+/* w = a / pdf (node weight of the quadrature alignment included).         */
+/* f receives the 12 SoA fields (w zero without a saddle root); returns 0, */
+/* or 1 when the saddle has no root.                                       */
+typedef struct {
+    const or_target_in* T;
+    or_pulse P;
+    const double *W, *cdf;
+    double total, N;
+    int align_kind, n_nodes, eta_force;
+    double theta, phi;
+    const double *qx, *qw;
+} or_proposal;
+
+static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f[12],
+                   double* tt_out, cplx* Sd_out)
+{
+    const or_target_in* T = Q->T;
+    const or_pulse* Pp = &Q->P;
+    /* time index */
+    int n0 = Pp->nt - 1;
+    double thr = u[0] * Q->total;
+    for (int m = 0; m < Pp->nt; ++m)
+        if (Q->cdf[m] > thr) { n0 = m; break; }
+    double t0 = Pp->t_origin + n0 * Pp->dt;
+    double Et0 = pulse_E_real(Pp, t0);
+    double sigma = sqrt(fabs(Et0) / (2.0 * sqrt(2.0 * T->Ip)));
+    double r = sqrt(-2.0 * log(u[1]));
+    double kx = sigma * r * cos(2.0 * OR_PI * u[2]);
+    double ky = sigma * r * sin(2.0 * OR_PI * u[2]);
+    /* orientation */
+    double th = Q->theta, ph = Q->phi;
+    if (Q->align_kind == OR_ALIGN_ISO) {
+        th = acos(2.0 * u[3] - 1.0);
+        ph = 2.0 * OR_PI * u[4];
+    } else if (Q->align_kind == OR_ALIGN_COS2) {
+        th = acos(cbrt(2.0 * u[3] - 1.0));
+        ph = 2.0 * OR_PI * u[4];
+    } else if (Q->align_kind == OR_ALIGN_QUAD) {
+        /* Eq. 5 by quadrature: trajectory j sits at node j mod K */
+        th = acos(Q->qx[j % (uint64_t)Q->n_nodes]);
+        ph = 2.0 * OR_PI * u[4];
+    }
+    double nhat[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+    /* saddle, exit, action, amplitude.  SFHK2: the electron leaves     */
+    /* from one centre, eta = +1 (the centre at -(R/2) n) or -1 (the     */
+    /* centre at +(R/2) n) with probability 1/2 each (weight x 2), the   */
+    /* modified saddle, that centre's part of the dipole element (its    */
+    /* factor e^{-i kappa.R_c} is the phase whose t_s-derivative is the  */
+    /* extra term), and the Gaussian-integration factor from the         */
+    /* curvature of the whole phase, E kappa_z + c dE/dt.                */
+    double tt = 0.0, kz = 0.0, qz = 0.0;
+    cplx w = 0.0, Sd = 0.0;
+    int only = -1;
+    double cmod = 0.0, side_w = 1.0;
+    if (T->ionization == 1) {
+        /* eta_force = +-1 fixes the side (test hook, weight x 1) */
+        double eta = Q->eta_force ? (double)Q->eta_force : ((u[5] < 0.5) ? 1.0 : -1.0);
+        only = (eta > 0.0) ? 1 : 0;
+        cmod = eta * 0.5 * T->R * cos(th);
+        side_w = Q->eta_force ? 1.0 : 2.0;
+    }
+    int sok = (T->ionization == 1)
+                  ? saddle_modified(Pp, T->Ip, t0, kx * kx + ky * ky, cmod, &tt, &kz)
+                  : saddle(Pp, T->Ip, t0, kx * kx + ky * ky, &tt, &kz);
+    if (sok == 0) {
+        double k[3] = {kx, ky, kz};
+        tunnel_exit_and_action(Pp, T->Ip, t0, tt, k, &qz, &Sd);
+        cplx ts = t0 + I * tt;
+        cplx Es = pulse_E(Pp, ts);
+        cplx kap[3] = {kx, ky, kz + pulse_A(Pp, ts) - creal(pulse_A(Pp, t0))};
+        cplx mz;
+        dipole_matrix_element(T, Q->N, nhat, kap, only, &mz);
+        cplx curv = Es * kap[2] + cmod * pulse_Edot(Pp, ts);
+        cplx a = side_w * Es * mz / csqrt(curv) * cexp(I * (Sd + kz * qz));
+        double pdf = (Q->W[n0] / Q->total) / Pp->dt
+                     * exp(-(kx * kx + ky * ky) / (2.0 * sigma * sigma))
+                     / (2.0 * OR_PI * sigma * sigma);
+        w = a / pdf;
+        /* node weight, times K for the 1/N over all K nodes' trajectories */
+        if (Q->align_kind == OR_ALIGN_QUAD) w *= Q->n_nodes * Q->qw[j % (uint64_t)Q->n_nodes];
+    }
+    double g[12] = {(double)n0, 0.0, 0.0, qz, kx, ky, kz,
+                    nhat[0], nhat[1], nhat[2], creal(w), cimag(w)};
+    for (int q = 0; q < 12; ++q) f[q] = g[q];
+    *tt_out = tt;
+    *Sd_out = Sd;
+    return sok == 0 ? 0 : 1;
+}
+
+/* Initial points distributed ~ |a| (target sampling 1; the sampling of   */
+/* Sec. II.B, "distributed according to |sin(beta) <W|r.E|psi0>|", with    */
+/* the axis measure in the proposal).  Exact rejection with weight        */
+/* correction on top of the proposal: a draw with weight w is accepted    */
+/* with alpha = min(1, |w|/M) and then carries P alpha-corrected weight    */
+/*   omega = P w / alpha,  P = E[alpha]  (= P M w/|w| whenever |w| <= M),   */
+/* so that E[omega f] over accepted draws is the integral of a f for any  */
+/* M.  M is kappa times the mean |w| over the first half of a pilot of     */
+/* proposal draws (kappa = sampling_factor; M >= max |w| would give the   */
+/* exact |a| distribution at a sampling cost of max/mean draws per point)  */
+/* and P the mean alpha over its second half (independent of M).  Draws:   */
+/* attempt k of trajectory j uses draws 3k..3k+2 (attempt 0 = the plain    */
+/* sampler's), its acceptance uniform draw OR_ACC_BASE + k, pilot draw i   */
+/* the trajectory index i with draws OR_PILOT_BASE.. .  A trajectory with */
+/* no acceptance in OR_ATTEMPTS attempts gets w = 0 (invalid).            */
+#define OR_PILOT 16384
+#define OR_ATTEMPTS 256
+#define OR_ACC_BASE (1u << 20)
+#define OR_PILOT_BASE (1u << 24)
+
+static double acc_uniform(uint64_t seed, uint32_t instance, uint64_t j, uint32_t k)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(j >> 32), instance, OR_ACC_BASE + k};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    return or_u01(r[0], r[1]);
+}
+
+/* M and P of the |a|-proportional sampler (out[0] = M, out[1] = P). */
+static void abs_sampling_constants(const or_proposal* Q, uint64_t seed, uint32_t instance,
+                                   double out[2])
+{
+    double u[6], f[12], tt, sum = 0.0;
+    cplx Sd;
+    for (uint64_t i = 0; i < OR_PILOT / 2; ++i) {
+        uniforms_at(seed, instance, i, OR_PILOT_BASE, u);
+        propose(Q, i, u, f, &tt, &Sd);
+        sum += hypot(f[10], f[11]);
+    }
+    double kappa = Q->T->sampling_factor > 0.0 ? Q->T->sampling_factor : 5.0;
+    double M = kappa * sum / (OR_PILOT / 2);
+    double asum = 0.0;
+    for (uint64_t i = OR_PILOT / 2; i < OR_PILOT; ++i) {
+        uniforms_at(seed, instance, i, OR_PILOT_BASE, u);
+        propose(Q, i, u, f, &tt, &Sd);
+        double aw = hypot(f[10], f[11]);
+        asum += (M > 0.0) ? fmin(1.0, aw / M) : 0.0;
+    }
+    out[0] = M;
+    out[1] = asum / (OR_PILOT / 2);
+}
+
+void or_abs_sampling_constants(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
+                               double theta, double phi, int n_nodes, uint64_t seed,
+                               uint32_t instance, double out[2]);
+
 int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
               double theta, double phi, int n_nodes, int eta_force, uint64_t seed,
               uint32_t instance, uint64_t j_begin, uint64_t n, double* soa, double* aux)
 {
-    or_pulse P = or_make_pulse(Pin);
     double qx[OR_MAX_QUAD], qw[OR_MAX_QUAD];
     if (align_kind == OR_ALIGN_QUAD) {
         if (n_nodes < 1 || n_nodes > OR_MAX_QUAD) return -1;
         or_quad_nodes(n_nodes, qx, qw);
     }
-    double* W = (double*)malloc(sizeof(double) * P.nt);
-    double* cdf = (double*)malloc(sizeof(double) * P.nt);
+    or_proposal Q;
+    Q.T = T;
+    Q.P = or_make_pulse(Pin);
+    double* W = (double*)malloc(sizeof(double) * Q.P.nt);
+    double* cdf = (double*)malloc(sizeof(double) * Q.P.nt);
     or_adk_table(Pin, T->Ip, W, cdf);
-    double total = cdf[P.nt - 1];
-    double N = orbital_norm(T);
+    Q.W = W;
+    Q.cdf = cdf;
+    Q.total = cdf[Q.P.nt - 1];
+    Q.N = orbital_norm(T);
+    Q.align_kind = align_kind;
+    Q.n_nodes = n_nodes;
+    Q.eta_force = eta_force;
+    Q.theta = theta;
+    Q.phi = phi;
+    Q.qx = qx;
+    Q.qw = qw;
+    double MP[2] = {0.0, 0.0};
+    if (T->sampling == 1) abs_sampling_constants(&Q, seed, instance, MP);
     int bad = 0;
     for (uint64_t jj = 0; jj < n; ++jj) {
         uint64_t j = j_begin + jj;
-        double u[6];
-        or_uniforms(seed, instance, j, u);
-        /* time index */
-        int n0 = P.nt - 1;
-        double thr = u[0] * total;
-        for (int m = 0; m < P.nt; ++m)
-            if (cdf[m] > thr) { n0 = m; break; }
-        double t0 = P.t_origin + n0 * P.dt;
-        double Et0 = pulse_E_real(&P, t0);
-        double sigma = sqrt(fabs(Et0) / (2.0 * sqrt(2.0 * T->Ip)));
-        double r = sqrt(-2.0 * log(u[1]));
-        double kx = sigma * r * cos(2.0 * OR_PI * u[2]);
-        double ky = sigma * r * sin(2.0 * OR_PI * u[2]);
-        /* orientation */
-        double th = theta, ph = phi;
-        if (align_kind == OR_ALIGN_ISO) {
-            th = acos(2.0 * u[3] - 1.0);
-            ph = 2.0 * OR_PI * u[4];
-        } else if (align_kind == OR_ALIGN_COS2) {
-            th = acos(cbrt(2.0 * u[3] - 1.0));
-            ph = 2.0 * OR_PI * u[4];
-        } else if (align_kind == OR_ALIGN_QUAD) {
-            /* Eq. 5 by quadrature: trajectory j sits at node j mod K */
-            th = acos(qx[j % (uint64_t)n_nodes]);
-            ph = 2.0 * OR_PI * u[4];
-        }
-        double nhat[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
-        /* saddle, exit, action, amplitude.  SFHK2: the electron leaves     */
-        /* from one centre, eta = +1 (the centre at -(R/2) n) or -1 (the     */
-        /* centre at +(R/2) n) with probability 1/2 each (weight x 2), the   */
-        /* modified saddle, that centre's part of the dipole element (its    */
-        /* factor e^{-i kappa.R_c} is the phase whose t_s-derivative is the  */
-        /* extra term), and the Gaussian-integration factor from the         */
-        /* curvature of the whole phase, E kappa_z + c dE/dt.                */
-        double tt = 0.0, kz = 0.0, qz = 0.0;
-        cplx w = 0.0, Sd = 0.0;
-        int only = -1;
-        double cmod = 0.0, side_w = 1.0;
-        if (T->ionization == 1) {
-            /* eta_force = +-1 fixes the side (test hook, weight x 1) */
-            double eta = eta_force ? (double)eta_force : ((u[5] < 0.5) ? 1.0 : -1.0);
-            only = (eta > 0.0) ? 1 : 0;
-            cmod = eta * 0.5 * T->R * cos(th);
-            side_w = eta_force ? 1.0 : 2.0;
-        }
-        int sok = (T->ionization == 1)
-                      ? saddle_modified(&P, T->Ip, t0, kx * kx + ky * ky, cmod, &tt, &kz)
-                      : saddle(&P, T->Ip, t0, kx * kx + ky * ky, &tt, &kz);
-        if (sok == 0) {
-            double k[3] = {kx, ky, kz};
-            tunnel_exit_and_action(&P, T->Ip, t0, tt, k, &qz, &Sd);
-            cplx ts = t0 + I * tt;
-            cplx Es = pulse_E(&P, ts);
-            cplx kap[3] = {kx, ky, kz + pulse_A(&P, ts) - creal(pulse_A(&P, t0))};
-            cplx mz;
-            dipole_matrix_element(T, N, nhat, kap, only, &mz);
-            cplx curv = Es * kap[2] + cmod * pulse_Edot(&P, ts);
-            cplx a = side_w * Es * mz / csqrt(curv) * cexp(I * (Sd + kz * qz));
-            double pdf = (W[n0] / total) / P.dt
-                         * exp(-(kx * kx + ky * ky) / (2.0 * sigma * sigma))
-                         / (2.0 * OR_PI * sigma * sigma);
-            w = a / pdf;
-            /* node weight, times K for the 1/N over all K nodes' trajectories */
-            if (align_kind == OR_ALIGN_QUAD) w *= n_nodes * qw[j % (uint64_t)n_nodes];
+        double u[6], f[12], tt = 0.0;
+        cplx Sd = 0.0;
+        int inval;
+        if (T->sampling == 1) {
+            inval = 1;
+            for (uint32_t k = 0; k < OR_ATTEMPTS; ++k) {
+                uniforms_at(seed, instance, j, 3u * k, u);
+                if (propose(&Q, j, u, f, &tt, &Sd)) continue;
+                double aw = hypot(f[10], f[11]);
+                double alpha = (MP[0] > 0.0) ? fmin(1.0, aw / MP[0]) : 0.0;
+                if (!(alpha > 0.0) || acc_uniform(seed, instance, j, k) >= alpha) continue;
+                f[10] *= MP[1] / alpha;
+                f[11] *= MP[1] / alpha;
+                inval = 0;
+                break;
+            }
+            if (inval) {
+                f[10] = f[11] = 0.0;
+                tt = 0.0;
+                Sd = 0.0;
+            }
         } else {
-            ++bad;
+            or_uniforms(seed, instance, j, u);
+            inval = propose(&Q, j, u, f, &tt, &Sd);
         }
-        double f[12] = {(double)n0, 0.0, 0.0, qz, kx, ky, kz,
-                        nhat[0], nhat[1], nhat[2], creal(w), cimag(w)};
+        bad += inval;
         for (int q = 0; q < 12; ++q) soa[(size_t)q * n + jj] = f[q];
         if (aux) {
             aux[(size_t)0 * n + jj] = tt;
@@ -830,6 +956,34 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
     free(W);
     free(cdf);
     return bad;
+}
+
+void or_abs_sampling_constants(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
+                               double theta, double phi, int n_nodes, uint64_t seed,
+                               uint32_t instance, double out[2])
+{
+    double qx[OR_MAX_QUAD], qw[OR_MAX_QUAD];
+    if (align_kind == OR_ALIGN_QUAD) or_quad_nodes(n_nodes, qx, qw);
+    or_proposal Q;
+    Q.T = T;
+    Q.P = or_make_pulse(Pin);
+    double* W = (double*)malloc(sizeof(double) * Q.P.nt);
+    double* cdf = (double*)malloc(sizeof(double) * Q.P.nt);
+    or_adk_table(Pin, T->Ip, W, cdf);
+    Q.W = W;
+    Q.cdf = cdf;
+    Q.total = cdf[Q.P.nt - 1];
+    Q.N = orbital_norm(T);
+    Q.align_kind = align_kind;
+    Q.n_nodes = n_nodes;
+    Q.eta_force = 0;
+    Q.theta = theta;
+    Q.phi = phi;
+    Q.qx = qx;
+    Q.qw = qw;
+    abs_sampling_constants(&Q, seed, instance, out);
+    free(W);
+    free(cdf);
 }
 
 /* ------------------------------------------------------------------ */

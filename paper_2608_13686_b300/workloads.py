@@ -50,6 +50,15 @@ def sfhk2(target):
     return t
 
 
+def abs_sampled(target, kappa=5.0):
+    """The same target with initial points distributed ~ |a| (Sec. II.B),
+    by rejection with envelope kappa x mean |a/pdf|."""
+    t = dict(target)
+    t["sampling"] = 1
+    t["sampling_factor"] = float(kappa)
+    return t
+
+
 def harmonic_target(omega, prims=_H2_PRIMS, Ip=0.0):
     """Isotropic harmonic test potential V = omega^2 r^2 / 2 (closed forms)."""
     t = _target(0.0, 0.0, 0.0, 0.0, 0.0, Ip, prims)
