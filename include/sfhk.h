@@ -84,8 +84,18 @@ enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
  * at -(R/2) n) or -1 (at +(R/2) n) with probability 1/2 each and weight x 2,
  * through the saddle [k + A(t_s) - A(t0)]^2/2 + Ip - eta E(t_s).(R/2) n = 0,
  * with that centre's part of the dipole element and the Gaussian-integration
- * factor 1/sqrt(E(t_s) kappa_z + eta (R/2) n_z dE/dt(t_s)). */
+ * factor 1/sqrt(E(t_s) kappa_z + eta (R/2) n_z dE/dt(t_s)).
+ * sampling selects how the initial points are drawn: SFHK_SAMPLE_PROPOSAL
+ * draws them from the ADK-time x Gaussian-k_perp x alignment proposal with
+ * weight w = a/pdf; SFHK_SAMPLE_ABS_AMPLITUDE distributes them ~ |a|
+ * (Sec. II.B) by exact rejection with weight correction on that proposal: a
+ * draw is kept with probability alpha = min(1, |w|/M) and weighs P w/alpha,
+ * M = sampling_factor x mean |w| and P = mean alpha from a pilot of 16384
+ * draws; every weighted mean stays unbiased for any factor, larger factors
+ * give more nearly equal weights (lower variance per propagated trajectory)
+ * at about 1/P proposal draws per point. */
 enum { SFHK_IONIZE_SFA = 0, SFHK_IONIZE_MODIFIED = 1 };
+enum { SFHK_SAMPLE_PROPOSAL = 0, SFHK_SAMPLE_ABS_AMPLITUDE = 1 };
 typedef struct {
     int kind;
     int n_prim;                       /* 1..SFHK_MAX_PRIM */
@@ -95,6 +105,8 @@ typedef struct {
     double prim_exp[SFHK_MAX_PRIM];   /* > 0 */
     double prim_coef[SFHK_MAX_PRIM];
     int ionization;                   /* SFHK_IONIZE_SFA or SFHK_IONIZE_MODIFIED */
+    int sampling;                     /* SFHK_SAMPLE_PROPOSAL or SFHK_SAMPLE_ABS_AMPLITUDE */
+    double sampling_factor;           /* kappa of the |a| sampler (<= 0: 5) */
 } sfhk_target_desc;
 
 /* Pulse (Sec. II.D / III.A): wavelength (nm), peak intensity (W/cm^2),

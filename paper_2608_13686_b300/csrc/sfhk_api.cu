@@ -121,7 +121,7 @@ void ensemble_free(sfhk_ensemble* e)
     Ctx* c = e->ctx;
     for (DeviceBuf* b : {&e->soa, &e->n0, &e->perm, &e->items, &e->ph, &e->phf, &e->vz,
                          &e->dump, &e->counters, &e->cdf, &e->hist, &e->inst, &e->qctr,
-                         &e->returns})
+                         &e->returns, &e->pilot})
         c->release(*b);
     if (e->ev_start) cudaEventDestroy(e->ev_start);
     if (e->ev_stop) cudaEventDestroy(e->ev_stop);
@@ -289,6 +289,9 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
     if (d->n_prim < 1 || d->n_prim > SFHK_MAX_PRIM) return SFHK_E_INVAL;
     if (d->ionization != SFHK_IONIZE_SFA && d->ionization != SFHK_IONIZE_MODIFIED)
         return SFHK_E_INVAL;
+    if ((d->sampling != SFHK_SAMPLE_PROPOSAL && d->sampling != SFHK_SAMPLE_ABS_AMPLITUDE) ||
+        !std::isfinite(d->sampling_factor))
+        return SFHK_E_INVAL;
     for (int k = 0; k < d->n_prim; ++k)
         if (!(d->prim_exp[k] > 0.0) || !std::isfinite(d->prim_coef[k])) return SFHK_E_INVAL;
     if (d->soft_a < 0.0 || d->R < 0.0 || d->alpha < 0.0 || !std::isfinite(d->Ip)) return SFHK_E_INVAL;
@@ -407,7 +410,9 @@ int sfhk_sample_initial(sfhk_ctx* c, const sfhk_target* t, const sfhk_pulse* p,
     e->pulse = p;
     e->n = (long long)n_traj;
     e->n_norm = (double)n_traj;
-    if ((rc = ensemble_alloc(e, e->n, p->nt))) {
+    if ((rc = ensemble_alloc(e, e->n, p->nt)) ||
+        (t->desc.sampling == SFHK_SAMPLE_ABS_AMPLITUDE &&
+         (rc = c->alloc(e->pilot, sizeof(double) * sample_pilot_doubles())))) {
         ensemble_free(e);
         return rc;
     }
@@ -417,7 +422,7 @@ int sfhk_sample_initial(sfhk_ctx* c, const sfhk_target* t, const sfhk_pulse* p,
     if (!rc) rc = launch_adk_cdf(*p, t->desc.Ip, (double*)e->cdf.p, s);
     if (!rc)
         rc = launch_sample(*t, *p, *al, e->n, seed, instance, (const double*)e->cdf.p,
-                           (double*)e->soa.p, (int*)e->n0.p, cnt + 3, s);
+                           (double*)e->soa.p, (int*)e->n0.p, cnt + 3, (double*)e->pilot.p, s);
     if (!rc) rc = ensemble_finish(e, s);
     e->sampled = true;
     if (rc) {
@@ -440,7 +445,7 @@ int sfhk_sample_into(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_align_desc* al, u
     unsigned long long* cnt = (unsigned long long*)e->counters.p;
     SFHK_CUDA_TRY(cudaMemsetAsync(cnt + 3, 0, sizeof(unsigned long long), s));
     rc = launch_sample(*e->tgt, *e->pulse, *al, e->n, seed, instance, (const double*)e->cdf.p,
-                       (double*)e->soa.p, (int*)e->n0.p, cnt + 3, s);
+                       (double*)e->soa.p, (int*)e->n0.p, cnt + 3, (double*)e->pilot.p, s);
     if (rc) return rc;
     rc = launch_counting_sort((const int*)e->n0.p, e->n, e->pulse->nt, (int*)e->perm.p,
                               (int*)e->hist.p, s);

@@ -113,7 +113,7 @@ struct Ensemble {
     const Pulse* pulse;
     long long n = 0;
     double n_norm = 0;
-    DeviceBuf soa, n0, perm, items, ph, phf, vz, dump, counters, returns;
+    DeviceBuf soa, n0, perm, items, ph, phf, vz, dump, counters, returns, pilot;
     int n_items = 0;
     unsigned long long n_invalid = 0;
     bool dumped = false;
@@ -134,9 +134,12 @@ int launch_phase_table(const Pulse& P, double Ip, double2* ph, float2* phf, cuda
 int launch_adk_cdf(const Pulse& P, double Ip, double* cdf, cudaStream_t s);
 // alignment descriptor within its documented ranges
 bool align_valid(const sfhk_align_desc& al);
+// pilot: sample_pilot_doubles() doubles of scratch, used when the target
+// samples ~ |a| (null otherwise)
 int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, long long n,
                   uint64_t seed, uint32_t instance, const double* cdf, double* soa, int* n0,
-                  unsigned long long* n_invalid, cudaStream_t s);
+                  unsigned long long* n_invalid, double* pilot, cudaStream_t s);
+size_t sample_pilot_doubles();
 int launch_n0_from_soa(const double* soa, long long n, int* n0, cudaStream_t s);
 // counting sort of keys in [0, K): writes perm (sorted position -> index)
 int launch_counting_sort(const int* keys, long long n, int K, int* perm, int* scratch_hist,

@@ -106,6 +106,7 @@ struct SampleParams {
     double R;
     int n_prim;
     int ionization;                           // SFHK_IONIZE_SFA / SFHK_IONIZE_MODIFIED
+    int sampling;                             // SFHK_SAMPLE_PROPOSAL / SFHK_SAMPLE_ABS_AMPLITUDE
     double norm;
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
 };
@@ -128,21 +129,13 @@ __device__ __forceinline__ double2 int_cos(double ca, double sa, double be, doub
     return make_double2(ca * sh / be, -sa * cm1 / be);
 }
 
-__global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double* __restrict__ soa,
-                         int* __restrict__ n0_out, unsigned long long* n_invalid)
+// One draw of the proposal from the six uniforms u (trajectory index j for
+// the quadrature node) and its amplitude: f receives the 12 SoA fields
+// (n0 | q0[3] | p0[3] | axis[3] | w_re w_im, w = a / pdf, zero without a
+// saddle root); returns whether the saddle has a root.
+__device__ __forceinline__ bool propose(const SampleParams& S, long long j, const double u[6],
+                                        const double* __restrict__ cdf, double f[12])
 {
-    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (j >= S.n) return;
-    const long long n = S.n;
-    // ---- random numbers: Philox4x32-10, key = seed, counter = (j, instance, draw)
-    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-    double u[6];
-#pragma unroll
-    for (uint32_t d = 0; d < 3; ++d) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)(j >> 32), S.instance, d), key);
-        u[2 * d] = u01(r.x, r.y);
-        u[2 * d + 1] = u01(r.z, r.w);
-    }
     // ---- birth time: smallest m with cdf[m] > u0 * total
     const double total = cdf[S.nt - 1];
     const double thr = u[0] * total;
@@ -388,20 +381,125 @@ __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double*
             w = make_double2(f * amp.x / pdf, f * amp.y / pdf);
         }
     }
+    f[0] = (double)m;
+    f[1] = 0.0;
+    f[2] = 0.0;
+    f[3] = qz;
+    f[4] = kx;
+    f[5] = ky;
+    f[6] = kz;
+    f[7] = nx;
+    f[8] = ny;
+    f[9] = nz;
+    f[10] = w.x;
+    f[11] = w.y;
+    return ok;
+}
+
+__device__ __forceinline__ void uniforms_at(const SampleParams& S, long long j, uint32_t d0,
+                                            double u[6])
+{
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+#pragma unroll
+    for (uint32_t d = 0; d < 3; ++d) {
+        const uint4 r =
+            philox4x32_10(make_uint4((uint32_t)j, (uint32_t)(j >> 32), S.instance, d0 + d), key);
+        u[2 * d] = u01(r.x, r.y);
+        u[2 * d + 1] = u01(r.z, r.w);
+    }
+}
+
+// Initial points distributed ~ |a| (sampling 1): exact rejection with weight
+// correction on the proposal.  A draw of weight w is accepted with
+// alpha = min(1, |w|/M) and carries P w / alpha (= P M w/|w| when |w| <= M),
+// which keeps every weighted mean unbiased for any M.  M = kappa x mean |w|
+// over the first half of a pilot of proposal draws, P = mean alpha over the
+// second half (k_pilot, k_pilot_constants).  Attempt k of trajectory j uses
+// draws 3k..3k+2 (attempt 0 = the plain sampler's draws) and acceptance
+// uniform draw kAccBase + k; pilot draw i uses draws kPilotBase.. of index i.
+constexpr int kPilot = 16384;
+constexpr int kAttempts = 256;
+constexpr uint32_t kAccBase = 1u << 20;
+constexpr uint32_t kPilotBase = 1u << 24;
+
+__global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double* __restrict__ soa,
+                         int* __restrict__ n0_out, unsigned long long* n_invalid,
+                         const double* __restrict__ mp)
+{
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j >= S.n) return;
+    const long long n = S.n;
+    double u[6], f[12];
+    bool ok;
+    if (S.sampling == 0) {
+        // ---- random numbers: Philox4x32-10, key = seed, counter = (j, instance, draw)
+        uniforms_at(S, j, 0u, u);
+        ok = propose(S, j, u, cdf, f);
+    } else {
+        const double M = mp[0], P = mp[1];
+        const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+        ok = false;
+        for (int k = 0; k < kAttempts && !ok; ++k) {
+            uniforms_at(S, j, 3u * (uint32_t)k, u);
+            if (!propose(S, j, u, cdf, f)) continue;
+            const double aw = hypot(f[10], f[11]);
+            const double alpha = M > 0.0 ? fmin(1.0, aw / M) : 0.0;
+            const uint4 r = philox4x32_10(
+                make_uint4((uint32_t)j, (uint32_t)(j >> 32), S.instance, kAccBase + (uint32_t)k),
+                key);
+            if (!(alpha > 0.0) || u01(r.x, r.y) >= alpha) continue;
+            f[10] *= P / alpha;
+            f[11] *= P / alpha;
+            ok = true;
+        }
+        if (!ok) f[10] = f[11] = 0.0;
+    }
     if (!ok) atomicAdd(n_invalid, 1ull);
-    soa[0 * n + j] = (double)m;
-    soa[1 * n + j] = 0.0;
-    soa[2 * n + j] = 0.0;
-    soa[3 * n + j] = qz;
-    soa[4 * n + j] = kx;
-    soa[5 * n + j] = ky;
-    soa[6 * n + j] = kz;
-    soa[7 * n + j] = nx;
-    soa[8 * n + j] = ny;
-    soa[9 * n + j] = nz;
-    soa[10 * n + j] = w.x;
-    soa[11 * n + j] = w.y;
-    n0_out[j] = m;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) soa[q * n + j] = f[q];
+    n0_out[j] = (int)f[0];
+}
+
+// |w| of the pilot draws (sampling 1)
+__global__ void k_pilot(SampleParams S, const double* __restrict__ cdf, double* __restrict__ aw)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kPilot) return;
+    double u[6], f[12];
+    uniforms_at(S, i, kPilotBase, u);
+    propose(S, i, u, cdf, f);
+    aw[i] = hypot(f[10], f[11]);
+}
+
+// M and P from the pilot |w| (one block of 1024 threads): mp[0] = M, mp[1] = P
+__global__ void __launch_bounds__(1024) k_pilot_constants(const double* __restrict__ aw,
+                                                          double kappa, double* __restrict__ mp)
+{
+    __shared__ double part[1024];
+    const int t = threadIdx.x;
+    constexpr int half = kPilot / 2;
+    double acc = 0.0;
+    for (int i = t; i < half; i += 1024) acc += aw[i];
+    part[t] = acc;
+    __syncthreads();
+    for (int off = 512; off > 0; off >>= 1) {
+        if (t < off) part[t] += part[t + off];
+        __syncthreads();
+    }
+    const double M = kappa * part[0] / half;
+    __syncthreads();
+    acc = 0.0;
+    for (int i = half + t; i < kPilot; i += 1024) acc += M > 0.0 ? fmin(1.0, aw[i] / M) : 0.0;
+    part[t] = acc;
+    __syncthreads();
+    for (int off = 512; off > 0; off >>= 1) {
+        if (t < off) part[t] += part[t + off];
+        __syncthreads();
+    }
+    if (t == 0) {
+        mp[0] = M;
+        mp[1] = part[0] / half;
+    }
 }
 
 __global__ void k_n0_from_soa(const double* soa, long long n, int* n0)
@@ -561,9 +659,10 @@ void quadrature_nodes(int K, double* x01, double* w01)
 
 int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, long long n,
                   uint64_t seed, uint32_t instance, const double* cdf, double* soa, int* n0,
-                  unsigned long long* n_invalid, cudaStream_t s)
+                  unsigned long long* n_invalid, double* pilot, cudaStream_t s)
 {
     if (!align_valid(al)) return SFHK_E_INVAL;
+    if (T.desc.sampling == SFHK_SAMPLE_ABS_AMPLITUDE && pilot == nullptr) return SFHK_E_INVAL;
     SampleParams S;
     S.n_nodes = al.kind == SFHK_ALIGN_QUADRATURE ? al.n_nodes : 1;
     for (int k = 0; k < SFHK_MAX_QUAD_NODES; ++k) S.qx[k] = S.qkw[k] = 0.0;
@@ -588,16 +687,28 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
     S.R = T.desc.R;
     S.n_prim = T.desc.n_prim;
     S.ionization = T.desc.ionization;
+    S.sampling = T.desc.sampling;
     S.norm = T.dev.norm;
     for (int k = 0; k < SFHK_MAX_PRIM; ++k) {
         S.pexp[k] = T.desc.prim_exp[k];
         S.pcoef[k] = T.desc.prim_coef[k];
     }
+    double* mp = nullptr;
+    if (S.sampling == SFHK_SAMPLE_ABS_AMPLITUDE) {
+        // pilot: |w| of kPilot proposal draws, then M and P
+        mp = pilot + kPilot;
+        const double kappa = T.desc.sampling_factor > 0.0 ? T.desc.sampling_factor : 5.0;
+        count_launch(2);
+        k_pilot<<<kPilot / 128, 128, 0, s>>>(S, cdf, pilot);
+        k_pilot_constants<<<1, 1024, 0, s>>>(pilot, kappa, mp);
+    }
     count_launch();
-    k_sample<<<grid_for(n, 128), 128, 0, s>>>(S, cdf, soa, n0, n_invalid);
+    k_sample<<<grid_for(n, 128), 128, 0, s>>>(S, cdf, soa, n0, n_invalid, mp);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
 }
+
+size_t sample_pilot_doubles() { return (size_t)kPilot + 2; }
 
 int launch_n0_from_soa(const double* soa, long long n, int* n0, cudaStream_t s)
 {

@@ -37,7 +37,7 @@ class sfhk_target_desc(C.Structure):
                 ("Z_inf", C.c_double), ("Z0", C.c_double), ("alpha", C.c_double),
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
                 ("prim_exp", C.c_double * SFHK_MAX_PRIM), ("prim_coef", C.c_double * SFHK_MAX_PRIM),
-                ("ionization", C.c_int)]
+                ("ionization", C.c_int), ("sampling", C.c_int), ("sampling_factor", C.c_double)]
 
 
 class sfhk_pulse_desc(C.Structure):
@@ -195,6 +195,8 @@ def target_desc(t: dict) -> sfhk_target_desc:
     d.alpha, d.soft_a, d.Ip = float(t["alpha"]), float(t["soft_a"]), float(t["Ip"])
     d.ho_omega = float(t.get("ho_omega", 0.0))
     d.ionization = int(t.get("ionization", 0))
+    d.sampling = int(t.get("sampling", 0))
+    d.sampling_factor = float(t.get("sampling_factor", 0.0))
     for i, (e, c) in enumerate(zip(pe, pc)):
         d.prim_exp[i] = e
         d.prim_coef[i] = c

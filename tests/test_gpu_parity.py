@@ -69,10 +69,17 @@ def test_pulse_grid_matches_oracle(S, ctx):
     ("N2+sfhk2", W.PULSE_1200, W.fixed(0.0), 800, 5, 0),
     ("N2+sfhk2", W.PULSE_PAPER, W.fixed(30.0, 10.0), 600, 6, 1),
     ("H2+sfhk2", W.PULSE_800, W.ISO, 700, 7, 2),
+    ("H2+abs", W.PULSE_800, W.fixed(0.0), 900, 8, 0),
+    ("N2+abs", W.PULSE_1200, W.ISO, 600, 9, 3),
+    ("N2+abs+sfhk2", W.PULSE_1200, W.quadrature(5), 500, 10, 1),
 ])
 def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
-    base, _, variant = name.partition("+")
-    t = W.TARGETS[base] if not variant else W.sfhk2(W.TARGETS[base])
+    base, *variants = name.split("+")
+    t = W.TARGETS[base]
+    if "sfhk2" in variants:
+        t = W.sfhk2(t)
+    if "abs" in variants:
+        t = W.abs_sampled(t, 5.0)
     th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, pulse)
     e = S.sfhk_sample_initial(ctx, th, ph, align, n, seed, inst)
     g = S.sfhk_ensemble_read(e, n)
