@@ -77,6 +77,8 @@ def parse():
                     help="orient-avg: ensemble sizes")
     ap.add_argument("--orient-replicas", type=int, default=6)
     ap.add_argument("--orient-nodes", type=int, default=10)
+    ap.add_argument("--abs-kappa", type=float, default=5.0,
+                    help="orient-avg: envelope factor of the |a|-proportional sampler")
     return ap.parse_args()
 
 
@@ -570,26 +572,39 @@ def run_orient(args):
     K = args.orient_nodes
     ctx = S.sfhk_create(local, 0)
     tgt = S.sfhk_create_target(ctx, W.TARGETS["H2"])
+    tgt_abs = S.sfhk_create_target(ctx, W.abs_sampled(W.TARGETS["H2"], args.abs_kappa))
     pul = S.sfhk_set_pulse(ctx, W.PULSE_800)
     g = S.sfhk_pulse_grid(pul)
     w0 = 45.5633525 / W.PULSE_800["lambda_nm"]          # photon energy (a.u.)
     opts = S.run_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF)
-    methods = {"joint_mc": W.ISO, f"quadrature_{K}": W.quadrature(K),
-               "fixed_0": W.fixed(0.0), "fixed_90": W.fixed(90.0)}
-    averaged = ("joint_mc", f"quadrature_{K}")      # estimates of the same isotropic average
+    # (target, alignment) per method; "_abs": initial points ~ |a| (Sec. II.B)
+    methods = {"joint_mc": (tgt, W.ISO), f"quadrature_{K}": (tgt, W.quadrature(K)),
+               "fixed_0": (tgt, W.fixed(0.0)), "fixed_90": (tgt, W.fixed(90.0)),
+               "joint_mc_abs": (tgt_abs, W.ISO), "fixed_0_abs": (tgt_abs, W.fixed(0.0))}
+    # estimates of the same isotropic average
+    averaged = ("joint_mc", f"quadrature_{K}", "joint_mc_abs")
     dip, yld = {}, {}
     steps_total, ms_total = 0, 0.0
+    cost = {}                                       # [sampling ms, propagation ms, trajectories]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for mi, (name, al) in enumerate(methods.items()):
+    es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for mi, (name, (tg, al)) in enumerate(methods.items()):
         for N in ladder:
             for r in range(R):
-                e = S.sfhk_sample_initial(ctx, tgt, pul, al, N, 1000 + r, 10 * mi + 1)
+                torch.cuda.synchronize()
+                es0.record()
+                e = S.sfhk_sample_initial(ctx, tg, pul, al, N, 1000 + r, 10 * mi + 1)
+                es1.record()
                 torch.cuda.synchronize()
                 e0.record()
                 S.sfhk_propagate(ctx, e, opts)
                 e1.record()
                 vz = S.sfhk_dipole(ctx, e, g["nt"])
                 ms_total += e0.elapsed_time(e1)
+                c = cost.setdefault(name, [0.0, 0.0, 0])
+                c[0] += es0.elapsed_time(es1)
+                c[1] += e0.elapsed_time(e1)
+                c[2] += N
                 steps_total += S.sfhk_stats_get(e)["traj_steps"]
                 S.sfhk_destroy_ensemble(e)
                 om, y, _ = S.sfhk_spectrum(vz, g["dt"], g["t_origin"], 0.5 * g["Tp"], g["nt"] // 2)
@@ -624,6 +639,21 @@ def run_orient(args):
     study["traj_ratio_quadrature_over_mc_dipole"] = (cq["c_dipole"] / cm["c_dipole"]) ** 2
     study["traj_ratio_quadrature_over_mc_plateau_yield"] = (
         (cq["c_plateau_yield"] / cm["c_plateau_yield"]) ** 2)
+    # |a|-proportional sampling: noise per trajectory and cost per trajectory
+    # (sampling + propagation, device time) against the plain proposal
+    for m in methods:
+        c = cost[m]
+        study["methods"][m]["ms_per_1e6_sampling"] = 1e6 * c[0] / c[2]
+        study["methods"][m]["ms_per_1e6_propagation"] = 1e6 * c[1] / c[2]
+    for plain, ab in (("joint_mc", "joint_mc_abs"), ("fixed_0", "fixed_0_abs")):
+        mp_, ma = study["methods"][plain], study["methods"][ab]
+        tp = mp_["ms_per_1e6_sampling"] + mp_["ms_per_1e6_propagation"]
+        ta = ma["ms_per_1e6_sampling"] + ma["ms_per_1e6_propagation"]
+        study[f"abs_sampling_{plain}"] = {
+            "kappa": args.abs_kappa,
+            "trajectory_ratio_for_equal_dipole_noise": (ma["c_dipole"] / mp_["c_dipole"]) ** 2,
+            "device_time_ratio_for_equal_dipole_noise":
+                (ma["c_dipole"] / mp_["c_dipole"]) ** 2 * ta / tp}
     # the paper's accounting: the standard method runs each of the K angles to
     # a fixed-alignment noise level, the joint Monte Carlo reaches that noise
     # on the average directly
@@ -638,6 +668,12 @@ def run_orient(args):
                               cq["rows"][-1]["dipole_rel_noise"]) / np.sqrt(R)
     study["mean_difference_at_nmax"] = float(np.linalg.norm(dq - dm) / np.linalg.norm(iso))
     study["noise_of_that_difference"] = float(noise_of_means)
+    # unbiasedness of the |a| sampler: its mean against the plain joint Monte Carlo
+    ca = study["methods"]["joint_mc_abs"]
+    da = np.mean(dip[("joint_mc_abs", nmax)], axis=0)
+    study["abs_mean_difference_at_nmax"] = float(np.linalg.norm(da - dm) / np.linalg.norm(iso))
+    study["abs_noise_of_that_difference"] = float(
+        np.hypot(cm["rows"][-1]["dipole_rel_noise"], ca["rows"][-1]["dipole_rel_noise"]) / np.sqrt(R))
     value = steps_total / (ms_total * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 0, "ms_per_step": ms_total, "higher_is_better": True, "scaling": "weak",
@@ -648,6 +684,7 @@ def run_orient(args):
     print(json.dumps(line), flush=True)
     S.sfhk_destroy_pulse(pul)
     S.sfhk_destroy_target(tgt)
+    S.sfhk_destroy_target(tgt_abs)
     S.sfhk_destroy(ctx)
     return 0
 
