@@ -414,7 +414,7 @@ __device__ __forceinline__ void uniforms_at(const SampleParams& S, long long j, 
 // alpha = min(1, |w|/M) and carries P w / alpha (= P M w/|w| when |w| <= M),
 // which keeps every weighted mean unbiased for any M.  M = kappa x mean |w|
 // over the first half of a pilot of proposal draws, P = mean alpha over the
-// second half (k_pilot, k_pilot_constants).  Attempt k of trajectory j uses
+// second half (k_pilot, k_pilot_constants), then k_sample_abs.  Attempt k of trajectory j uses
 // draws 3k..3k+2 (attempt 0 = the plain sampler's draws) and acceptance
 // uniform draw kAccBase + k; pilot draw i uses draws kPilotBase.. of index i.
 constexpr int kPilot = 16384;
@@ -423,41 +423,68 @@ constexpr uint32_t kAccBase = 1u << 20;
 constexpr uint32_t kPilotBase = 1u << 24;
 
 __global__ void k_sample(SampleParams S, const double* __restrict__ cdf, double* __restrict__ soa,
-                         int* __restrict__ n0_out, unsigned long long* n_invalid,
-                         const double* __restrict__ mp)
+                         int* __restrict__ n0_out, unsigned long long* n_invalid)
 {
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (j >= S.n) return;
     const long long n = S.n;
+    // ---- random numbers: Philox4x32-10, key = seed, counter = (j, instance, draw)
     double u[6], f[12];
-    bool ok;
-    if (S.sampling == 0) {
-        // ---- random numbers: Philox4x32-10, key = seed, counter = (j, instance, draw)
-        uniforms_at(S, j, 0u, u);
-        ok = propose(S, j, u, cdf, f);
-    } else {
-        const double M = mp[0], P = mp[1];
-        const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-        ok = false;
-        for (int k = 0; k < kAttempts && !ok; ++k) {
-            uniforms_at(S, j, 3u * (uint32_t)k, u);
-            if (!propose(S, j, u, cdf, f)) continue;
+    uniforms_at(S, j, 0u, u);
+    const bool ok = propose(S, j, u, cdf, f);
+    if (!ok) atomicAdd(n_invalid, 1ull);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) soa[q * n + j] = f[q];
+    n0_out[j] = (int)f[0];
+}
+
+// Sampling 1 without lanes idling: a persistent kernel in which every lane
+// makes one proposal draw per iteration for its current trajectory, and a
+// lane whose draw is accepted writes that trajectory and takes the next one
+// from a global counter.  A trajectory's draws depend only on (j, attempt),
+// so the result is the same as attempting each trajectory in turn; what
+// changes is that a warp no longer waits for its slowest lane.
+__global__ void k_sample_abs(SampleParams S, const double* __restrict__ cdf,
+                             double* __restrict__ soa, int* __restrict__ n0_out,
+                             unsigned long long* n_invalid, const double* __restrict__ mp,
+                             unsigned long long* __restrict__ next)
+{
+    const long long n = S.n;
+    const double M = mp[0], P = mp[1];
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+    long long j = (long long)atomicAdd(next, 1ull);
+    int k = 0;
+    while (j < n) {
+        double u[6], f[12];
+        uniforms_at(S, j, 3u * (uint32_t)k, u);
+        bool done = false, ok = false;
+        if (propose(S, j, u, cdf, f)) {
             const double aw = hypot(f[10], f[11]);
             const double alpha = M > 0.0 ? fmin(1.0, aw / M) : 0.0;
             const uint4 r = philox4x32_10(
                 make_uint4((uint32_t)j, (uint32_t)(j >> 32), S.instance, kAccBase + (uint32_t)k),
                 key);
-            if (!(alpha > 0.0) || u01(r.x, r.y) >= alpha) continue;
-            f[10] *= P / alpha;
-            f[11] *= P / alpha;
-            ok = true;
+            if (alpha > 0.0 && u01(r.x, r.y) < alpha) {
+                f[10] *= P / alpha;
+                f[11] *= P / alpha;
+                done = ok = true;
+            }
         }
-        if (!ok) f[10] = f[11] = 0.0;
-    }
-    if (!ok) atomicAdd(n_invalid, 1ull);
+        if (!done && k + 1 >= kAttempts) {
+            done = true;               // no acceptance: invalid, weight 0
+            f[10] = f[11] = 0.0;
+        }
+        if (done) {
+            if (!ok) atomicAdd(n_invalid, 1ull);
 #pragma unroll
-    for (int q = 0; q < 12; ++q) soa[q * n + j] = f[q];
-    n0_out[j] = (int)f[0];
+            for (int q = 0; q < 12; ++q) soa[q * n + j] = f[q];
+            n0_out[j] = (int)f[0];
+            j = (long long)atomicAdd(next, 1ull);
+            k = 0;
+        } else {
+            ++k;
+        }
+    }
 }
 
 // |w| of the pilot draws (sampling 1)
@@ -693,22 +720,34 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
         S.pexp[k] = T.desc.prim_exp[k];
         S.pcoef[k] = T.desc.prim_coef[k];
     }
-    double* mp = nullptr;
     if (S.sampling == SFHK_SAMPLE_ABS_AMPLITUDE) {
-        // pilot: |w| of kPilot proposal draws, then M and P
-        mp = pilot + kPilot;
+        // pilot: |w| of kPilot proposal draws, then M and P; then the
+        // persistent rejection sampler over a trajectory counter
+        double* mp = pilot + kPilot;
+        unsigned long long* next = reinterpret_cast<unsigned long long*>(pilot + kPilot + 2);
         const double kappa = T.desc.sampling_factor > 0.0 ? T.desc.sampling_factor : 5.0;
-        count_launch(2);
+        int dev = 0, sms = 0, occ = 0;
+        SFHK_CUDA_TRY(cudaGetDevice(&dev));
+        SFHK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_abs, 128, 0));
+        long long grid = (long long)sms * (occ > 0 ? occ : 1);
+        const long long need = (n + 127) / 128;
+        if (grid > need) grid = need;
+        SFHK_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
+        count_launch(3);
         k_pilot<<<kPilot / 128, 128, 0, s>>>(S, cdf, pilot);
         k_pilot_constants<<<1, 1024, 0, s>>>(pilot, kappa, mp);
+        k_sample_abs<<<(int)grid, 128, 0, s>>>(S, cdf, soa, n0, n_invalid, mp, next);
+    } else {
+        count_launch();
+        k_sample<<<grid_for(n, 128), 128, 0, s>>>(S, cdf, soa, n0, n_invalid);
     }
-    count_launch();
-    k_sample<<<grid_for(n, 128), 128, 0, s>>>(S, cdf, soa, n0, n_invalid, mp);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
 }
 
-size_t sample_pilot_doubles() { return (size_t)kPilot + 2; }
+// pilot |w| | M, P | trajectory counter
+size_t sample_pilot_doubles() { return (size_t)kPilot + 3; }
 
 int launch_n0_from_soa(const double* soa, long long n, int* n0, cudaStream_t s)
 {
