@@ -58,7 +58,8 @@ class TargetIn(C.Structure):
                 ("Zinf", C.c_double), ("Z0", C.c_double), ("alpha", C.c_double),
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
                 ("pexp", C.c_double * 8), ("pcoef", C.c_double * 8), ("ionization", C.c_int),
-                ("sampling", C.c_int), ("sampling_factor", C.c_double)]
+                ("sampling", C.c_int), ("sampling_factor", C.c_double),
+                ("pkind", C.c_int * 8)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -110,6 +111,7 @@ def lib():
         L.or_abs_sampling_constants.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int,
                                                 C.c_double, C.c_double, C.c_int, C.c_uint64,
                                                 C.c_uint32, _dp]
+        L.or_orbital_values.argtypes = [C.POINTER(TargetIn), _dp, _dp, C.c_int64, _dp]
         L.or_saddle_modified.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
                                          C.c_double, _dp]
         L.or_saddle_modified.restype = C.c_int
@@ -141,9 +143,11 @@ def target_in(t) -> TargetIn:
     T.n_prim = len(t.get("pexp", ()))
     for name in ("R", "Zinf", "Z0", "alpha", "soft_a", "Ip", "ho_omega"):
         setattr(T, name, float(t.get(name, 0.0)))
+    kinds = list(t.get("pkind", [0] * len(t.get("pexp", ()))))
     for i, (e, c) in enumerate(zip(t.get("pexp", ()), t.get("pcoef", ()))):
         T.pexp[i] = e
         T.pcoef[i] = c
+        T.pkind[i] = int(kinds[i]) if i < len(kinds) else 0
     return T
 
 
@@ -370,3 +374,12 @@ def abs_sampling_constants(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance
     lib().or_abs_sampling_constants(C.byref(target_in(t)), C.byref(pulse_in(p)), int(align[0]),
                                     float(align[1]), float(align[2]), k, seed, instance, _p(out))
     return out[0], out[1]
+
+
+def orbital_values(t, nhat, r):
+    """psi0 at the points r (n x 3)."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    out = np.zeros(r.shape[0])
+    lib().or_orbital_values(C.byref(target_in(t)), _p(np.asarray(nhat, float).copy()), _p(r),
+                            r.shape[0], _p(out))
+    return out

@@ -76,6 +76,9 @@ typedef struct {
     int sampling;       /* 0: proposal with weights a/pdf; 1: initial    */
                         /* points distributed ~ |a| (Sec. II.B)           */
     double sampling_factor; /* kappa of the |a| sampler (<= 0: 5)         */
+    int pkind[8];       /* primitive k: 0 s-type e^{-a|x-A|^2}; 1 sigma    */
+                        /* p-type s_c n.(x-A) e^{-a|x-A|^2}, s_c = +-1 for */
+                        /* the centre at +-(R/2) n (gerade combination)   */
 } or_target_in;
 
 /* ------------------------------------------------------------------ */
@@ -402,17 +405,31 @@ void or_hk_det(const double M[36], double gamma, double out[2])
 /* N from <psi0|psi0> = 1 with the Gaussian product overlap              */
 /*   int e^{-a|r-A|^2} e^{-b|r-B|^2} = (pi/(a+b))^{3/2} e^{-ab|A-B|^2/(a+b)}. */
 /* ------------------------------------------------------------------ */
+/* Normalisation of the orbital N sum_c sum_k coef_k phi_{c,k}: overlaps  */
+/* of Gaussians at A, B with exponents a, b (p = a + b, P = (aA + bB)/p,  */
+/* S0 = (pi/p)^{3/2} e^{-ab/p |A-B|^2}):  s-s S0;  s(A)-p(B)               */
+/* s_B n.(P-B) S0;  p(A)-p(B)  s_A s_B [n.(P-A) n.(P-B) + 1/(2p)] S0.      */
+/* Along the axis n.(A-B) = (s_A - s_B) R/2, so no orientation enters.     */
 static double orbital_norm(const or_target_in* T)
 {
     double s = 0.0;
     for (int c1 = 0; c1 < 2; ++c1)
         for (int c2 = 0; c2 < 2; ++c2) {
-            double dist2 = (c1 == c2) ? 0.0 : T->R * T->R;
+            double sA = (c1 == 0) ? 1.0 : -1.0, sB = (c2 == 0) ? 1.0 : -1.0;
+            double nAB = (sA - sB) * 0.5 * T->R;      /* n.(A - B) */
             for (int k1 = 0; k1 < T->n_prim; ++k1)
                 for (int k2 = 0; k2 < T->n_prim; ++k2) {
-                    double a = T->pexp[k1], b = T->pexp[k2];
-                    s += T->pcoef[k1] * T->pcoef[k2] * pow(OR_PI / (a + b), 1.5)
-                         * exp(-a * b / (a + b) * dist2);
+                    double a = T->pexp[k1], b = T->pexp[k2], pp = a + b;
+                    double S0 = pow(OR_PI / pp, 1.5) * exp(-a * b / pp * nAB * nAB);
+                    double nPA = b / pp * (-nAB);       /* n.(P - A) */
+                    double nPB = a / pp * nAB;          /* n.(P - B) */
+                    int p1 = T->pkind[k1], p2 = T->pkind[k2];
+                    double f;
+                    if (!p1 && !p2) f = 1.0;
+                    else if (!p1 && p2) f = sB * nPB;
+                    else if (p1 && !p2) f = sA * nPA;
+                    else f = sA * sB * (nPA * nPB + 0.5 / pp);
+                    s += T->pcoef[k1] * T->pcoef[k2] * f * S0;
                 }
         }
     return 1.0 / sqrt(s);
@@ -420,18 +437,34 @@ static double orbital_norm(const or_target_in* T)
 
 double or_orbital_norm(const or_target_in* T) { return orbital_norm(T); }
 
-double or_orbital_value(const or_target_in* T, const double nhat[3], const double r[3])
+static double orbital_value_n(const or_target_in* T, double N, const double nhat[3],
+                              const double r[3])
 {
-    double N = orbital_norm(T), v = 0.0;
+    double v = 0.0;
     for (int c = 0; c < 2; ++c) {
         double sign = (c == 0) ? 1.0 : -1.0, d2 = 0.0;
         for (int a = 0; a < 3; ++a) {
             double d = r[a] - sign * 0.5 * T->R * nhat[a];
             d2 += d * d;
         }
-        for (int k = 0; k < T->n_prim; ++k) v += T->pcoef[k] * exp(-T->pexp[k] * d2);
+        double nd = 0.0;       /* n.(r - A) */
+        for (int a = 0; a < 3; ++a) nd += nhat[a] * (r[a] - sign * 0.5 * T->R * nhat[a]);
+        for (int k = 0; k < T->n_prim; ++k)
+            v += T->pcoef[k] * (T->pkind[k] ? sign * nd : 1.0) * exp(-T->pexp[k] * d2);
     }
     return N * v;
+}
+
+double or_orbital_value(const or_target_in* T, const double nhat[3], const double r[3])
+{
+    return orbital_value_n(T, orbital_norm(T), nhat, r);
+}
+
+void or_orbital_values(const or_target_in* T, const double nhat[3], const double* r, int64_t n,
+                       double* out)
+{
+    double N = orbital_norm(T);
+    for (int64_t i = 0; i < n; ++i) out[i] = orbital_value_n(T, N, nhat, r + 3 * i);
 }
 
 /* ------------------------------------------------------------------ */
@@ -467,7 +500,17 @@ static cplx recomb(const or_target_in* T, double N, const double nhat[3],
             }
             cplx I0 = pow(OR_PI / c, 1.5) * cexp(c * mm - b * dd - I * pd);
             cplx I1 = (m[2] - d[2]) * I0;
-            total += T->pcoef[k] * (p[2] * I0 + I * gamma * I1);
+            if (T->pkind[k]) {
+                /* sigma p-type: extra factor s_c n.x' (x' = x - A):       */
+                /* int n.x' e = (n.m) I0, int n.x' (x'_z - d_z) e =        */
+                /* [(n.m)(m_z - d_z) + n_z/(2c)] I0                         */
+                cplx nm = nhat[0] * m[0] + nhat[1] * m[1] + nhat[2] * m[2];
+                cplx J0 = nm * I0;
+                cplx J1 = (nm * (m[2] - d[2]) + nhat[2] / (2.0 * c)) * I0;
+                total += sign * T->pcoef[k] * (p[2] * J0 + I * gamma * J1);
+            } else {
+                total += T->pcoef[k] * (p[2] * I0 + I * gamma * I1);
+            }
         }
     }
     return N * pow(gamma / OR_PI, 0.75) * total;
@@ -502,7 +545,16 @@ static void dipole_matrix_element(const or_target_in* T, double N, const double 
         for (int k = 0; k < T->n_prim; ++k) {
             double a = T->pexp[k];
             cplx F = pow(OR_PI / a, 1.5) * cexp(-I * kA - kk / (4.0 * a));
-            tot += T->pcoef[k] * (A[2] - I * kappa[2] / (2.0 * a)) * F;
+            if (T->pkind[k]) {
+                /* sigma p-type: int e^{-i k.x} (x_z + A_z)(n.x) e^{-a x^2} =  */
+                /* [n_z/(2a) - k_z (n.k)/(4a^2) - i A_z (n.k)/(2a)] G           */
+                cplx nk = nhat[0] * kappa[0] + nhat[1] * kappa[1] + nhat[2] * kappa[2];
+                tot += sign * T->pcoef[k] *
+                       (nhat[2] / (2.0 * a) - kappa[2] * nk / (4.0 * a * a) -
+                        I * A[2] * nk / (2.0 * a)) * F;
+            } else {
+                tot += T->pcoef[k] * (A[2] - I * kappa[2] / (2.0 * a)) * F;
+            }
         }
     }
     *mz = N * pow(2.0 * OR_PI, -1.5) * tot;

@@ -35,11 +35,23 @@ def _target(R, Zinf, Z0, alpha, soft_a, Ip, prims):
                 ho_omega=0.0, pexp=[p[0] for p in prims], pcoef=[p[1] for p in prims])
 
 
+# N2 with s-type and sigma p-type primitives (the HOMO 3 sigma_g has p character):
+# (exponent, coefficient, kind), kind 1 = s_c n.(x - A) e^{-a|x-A|^2}
+_N2_SP_PRIMS = ((2.00, 0.40, 0), (0.35, 0.70, 0), (1.20, 0.50, 1), (0.30, 0.35, 1))
+
+
+def _target_sp(R, Zinf, Z0, alpha, soft_a, Ip, prims):
+    t = _target(R, Zinf, Z0, alpha, soft_a, Ip, [(p[0], p[1]) for p in prims])
+    t["pkind"] = [p[2] for p in prims]
+    return t
+
+
 TARGETS = {
     "H2": _target(1.4, 0.5, 0.5, 1.0, 0.1, 0.567, _H2_PRIMS),
     "N2": _target(2.07, 0.5, 7.0, 2.0, 0.1, 0.573, _N2_PRIMS),
     "H2_table1": _target(1.40, 0.5, 1.0, 1.79, 0.0, 15.40 / EV, _H2_PRIMS),
     "N2_table1": _target(2.07, 0.5, 7.0, 1.67, 0.0, 15.54 / EV, _N2_PRIMS),
+    "N2_sp": _target_sp(2.07, 0.5, 7.0, 2.0, 0.1, 0.573, _N2_SP_PRIMS),
 }
 
 
