@@ -93,8 +93,16 @@ enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
  * M = sampling_factor x mean |w| and P = mean alpha from a pilot of 16384
  * draws; every weighted mean stays unbiased for any factor, larger factors
  * give more nearly equal weights (lower variance per propagated trajectory)
- * at about 1/P proposal draws per point. */
+ * at about 1/P proposal draws per point.
+ * prim_kind[k] selects the angular part of primitive k: SFHK_PRIM_S is the
+ * s-type exp(-a |r-R_c|^2); SFHK_PRIM_P_SIGMA is the sigma p-type
+ * s_c n.(r-R_c) exp(-a |r-R_c|^2), s_c = +1 at +(R/2) n and -1 at -(R/2) n,
+ * so that every primitive stays gerade (the 2p_sigma character of the N2
+ * 3 sigma_g orbital, Sec. III.B).  The normalisation, the dipole element of
+ * the sampler and the recombination element take the p-type factor in
+ * closed form.  Errors: SFHK_E_INVAL for any other value. */
 enum { SFHK_IONIZE_SFA = 0, SFHK_IONIZE_MODIFIED = 1 };
+enum { SFHK_PRIM_S = 0, SFHK_PRIM_P_SIGMA = 1 };
 enum { SFHK_SAMPLE_PROPOSAL = 0, SFHK_SAMPLE_ABS_AMPLITUDE = 1 };
 typedef struct {
     int kind;
@@ -107,6 +115,7 @@ typedef struct {
     int ionization;                   /* SFHK_IONIZE_SFA or SFHK_IONIZE_MODIFIED */
     int sampling;                     /* SFHK_SAMPLE_PROPOSAL or SFHK_SAMPLE_ABS_AMPLITUDE */
     double sampling_factor;           /* kappa of the |a| sampler (<= 0: 5) */
+    int prim_kind[SFHK_MAX_PRIM];     /* SFHK_PRIM_S or SFHK_PRIM_P_SIGMA */
 } sfhk_target_desc;
 
 /* Pulse (Sec. II.D / III.A): wavelength (nm), peak intensity (W/cm^2),

@@ -47,28 +47,52 @@ constexpr double kPi = 3.14159265358979323846;
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// 1 / sqrt(<phi|phi>) for phi = sum_c sum_k coef_k g_k(r - R_c), the
+// centres at z_c = s_c R/2 on the axis n.  Two primitives on centres A, B
+// multiply to e^{-ab/p (z_A - z_B)^2} e^{-p |r - P|^2} (p = a + b, P on the
+// axis at z_P = (a z_A + b z_B)/p), whose integral is S0 = (pi/p)^{3/2}
+// e^{-ab/p (z_A - z_B)^2}.  Writing n.(r - A) = n.(r - P) + (z_P - z_A) and
+// using int n.(r-P) e^{-p|r-P|^2} = 0, int [n.(r-P)]^2 e^{-p|r-P|^2} =
+// S0 / (2p): an s-s pair gives S0, an s-p pair s_B (z_P - z_B) S0 and a p-p
+// pair s_A s_B [(z_P - z_A)(z_P - z_B) + 1/(2p)] S0.
 double orbital_norm(const sfhk_target_desc& d)
 {
     double s = 0.0;
     for (int c1 = 0; c1 < 2; ++c1)
         for (int c2 = 0; c2 < 2; ++c2) {
-            const double dist2 = (c1 == c2) ? 0.0 : d.R * d.R;
+            const double s1 = c1 == 0 ? 1.0 : -1.0, s2 = c2 == 0 ? 1.0 : -1.0;
+            const double z1 = 0.5 * s1 * d.R, z2 = 0.5 * s2 * d.R;
             for (int k1 = 0; k1 < d.n_prim; ++k1)
                 for (int k2 = 0; k2 < d.n_prim; ++k2) {
-                    const double a = d.prim_exp[k1], b = d.prim_exp[k2];
-                    s += d.prim_coef[k1] * d.prim_coef[k2] * std::pow(kPi / (a + b), 1.5) *
-                         std::exp(-a * b / (a + b) * dist2);
+                    const double a = d.prim_exp[k1], b = d.prim_exp[k2], pab = a + b;
+                    const double zP = (a * z1 + b * z2) / pab;
+                    const double S0 = std::pow(kPi / pab, 1.5) *
+                                      std::exp(-a * b / pab * (z1 - z2) * (z1 - z2));
+                    const bool p1 = d.prim_kind[k1] == SFHK_PRIM_P_SIGMA;
+                    const bool p2 = d.prim_kind[k2] == SFHK_PRIM_P_SIGMA;
+                    double ang = 1.0;
+                    if (p1 && p2) ang = s1 * s2 * ((zP - z1) * (zP - z2) + 0.5 / pab);
+                    else if (p1) ang = s1 * (zP - z1);
+                    else if (p2) ang = s2 * (zP - z2);
+                    s += d.prim_coef[k1] * d.prim_coef[k2] * ang * S0;
                 }
         }
-    return 1.0 / std::sqrt(s);
+    return s > 0.0 ? 1.0 / std::sqrt(s) : INFINITY;
 }
 
+// Recombination constants per primitive (a its exponent, b = gamma/2,
+// c = a + b): K1 = -ab/c, K2 = -1/(4c), K3 = -a/c and
+// K4 = N coef (gamma/pi)^{3/4} (pi/c)^{3/2} a/c; a sigma p-type primitive
+// adds P1 = b/c, P2 = 1/(2c), P3 = gamma/(2a).
 void fill_recomb(const DevTarget& T, double gamma, DevRecomb& R)
 {
     const double b = 0.5 * gamma;
+    R.has_p = 0;
     for (int k = 0; k < SFHK_MAX_PRIM; ++k) {
+        R.kind[k] = 0;
         if (k >= T.n_prim) {
             R.K1[k] = R.K2[k] = R.K3[k] = R.K4[k] = 0.0;
+            R.P1[k] = R.P2[k] = R.P3[k] = 0.0;
         } else {
             const double a = T.pexp[k], c = a + b;
             R.K1[k] = -a * b / c;
@@ -76,11 +100,19 @@ void fill_recomb(const DevTarget& T, double gamma, DevRecomb& R)
             R.K3[k] = -a / c;
             R.K4[k] = T.norm * T.pcoef[k] * std::pow(gamma / kPi, 0.75) * std::pow(kPi / c, 1.5) *
                       (a / c);
+            R.kind[k] = T.pkind[k];
+            R.P1[k] = b / c;
+            R.P2[k] = 0.5 / c;
+            R.P3[k] = gamma / (2.0 * a);
+            if (T.pkind[k]) R.has_p = 1;
         }
         R.K1f[k] = (float)R.K1[k];
         R.K2f[k] = (float)R.K2[k];
         R.K3f[k] = (float)R.K3[k];
         R.K4f[k] = (float)R.K4[k];
+        R.P1f[k] = (float)R.P1[k];
+        R.P2f[k] = (float)R.P2[k];
+        R.P3f[k] = (float)R.P3[k];
     }
 }
 
@@ -293,7 +325,9 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
         !std::isfinite(d->sampling_factor))
         return SFHK_E_INVAL;
     for (int k = 0; k < d->n_prim; ++k)
-        if (!(d->prim_exp[k] > 0.0) || !std::isfinite(d->prim_coef[k])) return SFHK_E_INVAL;
+        if (!(d->prim_exp[k] > 0.0) || !std::isfinite(d->prim_coef[k]) ||
+            (d->prim_kind[k] != SFHK_PRIM_S && d->prim_kind[k] != SFHK_PRIM_P_SIGMA))
+            return SFHK_E_INVAL;
     if (d->soft_a < 0.0 || d->R < 0.0 || d->alpha < 0.0 || !std::isfinite(d->Ip)) return SFHK_E_INVAL;
     if (d->kind == SFHK_POT_MOLECULE && d->soft_a == 0.0 && d->Z_inf == 0.0 && d->Z0 == 0.0)
         ;  // a field-free "molecule" is allowed
@@ -301,7 +335,10 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
     if (!t) return SFHK_E_NOMEM;
     t->ctx = c;
     t->desc = *d;
-    for (int k = d->n_prim; k < SFHK_MAX_PRIM; ++k) t->desc.prim_exp[k] = t->desc.prim_coef[k] = 0.0;
+    for (int k = d->n_prim; k < SFHK_MAX_PRIM; ++k) {
+        t->desc.prim_exp[k] = t->desc.prim_coef[k] = 0.0;
+        t->desc.prim_kind[k] = SFHK_PRIM_S;
+    }
     DevTarget& T = t->dev;
     std::memset(&T, 0, sizeof T);
     T.kind = d->kind;
@@ -317,6 +354,7 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
     for (int k = 0; k < SFHK_MAX_PRIM; ++k) {
         T.pexp[k] = t->desc.prim_exp[k];
         T.pcoef[k] = t->desc.prim_coef[k];
+        T.pkind[k] = t->desc.prim_kind[k];
     }
     T.norm = orbital_norm(t->desc);
     if (!std::isfinite(T.norm)) {

@@ -465,12 +465,66 @@ __device__ __forceinline__ void prefactor_and_checks(const Mono<R>& M, R gam,
 // per-centre operation).  Both centres are evaluated unless both are beyond
 // the far-field bound; a primitive whose exponent is below kSkipMixed is
 // dropped in its lane.  Per centre and primitive the term is
-//   K4 e^{K1 |d|^2 + K2 |p|^2} (p_z - i g d_z) e^{i K3 p.d}.
+//   K4 e^{K1 |d|^2 + K2 |p|^2} (p_z - i g d_z) e^{i K3 p.d}
+// for an s-type primitive and
+//   s_c K4 e^{K1 |d|^2 + K2 |p|^2} [(P1 n.d + i P2 n.p)(p_z - i g d_z) + i P3 n_z] e^{i K3 p.d}
+// for a sigma p-type one (s_c = +-1 the centre's sign; n the axis, read
+// only when the target has p-type primitives).
 constexpr float kSkipMixed = -30.0f;
+
+// recomb_pair's loop for a target with sigma p-type primitives
+__device__ __forceinline__ C2<float> recomb_pair_sp(const DevInstance& I, const float q[3],
+                                                    const float p[3], float pp, int n_prim, int j,
+                                                    float2 dz, float2 dd, float2 pdd, float2 gdz)
+{
+    C2<float> Rk;
+    float2 P = make_float2(0.0f, 0.0f), Q = P, U = P, Wv = P;
+    const long long n = I.n;
+    const double* nhat = I.soa + 7 * n + j;
+    const float nx = (float)nhat[0], ny = (float)nhat[n], nz = (float)nhat[2 * n];
+    const float hR = (float)I.tgt.half_R;
+    const float nq = nx * q[0] + ny * q[1] + nz * q[2];
+    const float np = nx * p[0] + ny * p[1] + nz * p[2];
+    const float2 snd = make_float2(nq - hR, -nq - hR);          // s_c n.d
+    const float2 snp = make_float2(np, -np);                    // s_c n.p
+    const float2 snz = make_float2(nz, -nz);                    // s_c n_z
+    const float2 pz2 = make_float2(p[2], p[2]);
+#pragma unroll 1
+    for (int k = 0; k < n_prim; ++k) {
+        const float K1 = I.rec.K1f[k], K2 = I.rec.K2f[k], K3 = I.rec.K3f[k], K4 = I.rec.K4f[k];
+        const float2 ex = __ffma2_rn(make_float2(K1, K1), dd, make_float2(K2 * pp, K2 * pp));
+        const float2 arg = __fmul2_rn(make_float2(K3, K3), pdd);
+        float2 mag, sn, cs;
+        mag.x = ex.x > kSkipMixed ? K4 * __expf(ex.x) : 0.0f;
+        mag.y = ex.y > kSkipMixed ? K4 * __expf(ex.y) : 0.0f;
+        __sincosf(arg.x, &sn.x, &cs.x);
+        __sincosf(arg.y, &sn.y, &cs.y);
+        float2 br = pz2, bi = gdz;                              // s-type bracket
+        if (I.rec.kind[k]) {
+            const float P1 = I.rec.P1f[k], P2 = I.rec.P2f[k], P3 = I.rec.P3f[k];
+            const float2 u = __fmul2_rn(make_float2(P1, P1), snd);
+            const float2 v = __fmul2_rn(make_float2(P2, P2), snp);
+            // (u + i v)(p_z + i gdz) + i P3 s_c n_z
+            const float2 vg = __fmul2_rn(v, gdz);
+            br = __ffma2_rn(u, pz2, make_float2(-vg.x, -vg.y));
+            bi = __ffma2_rn(u, gdz, __ffma2_rn(v, pz2, __fmul2_rn(make_float2(P3, P3), snz)));
+        }
+        const float2 A = __fmul2_rn(mag, br);
+        const float2 B = __fmul2_rn(mag, bi);
+        P = __ffma2_rn(A, cs, P);
+        Q = __ffma2_rn(B, sn, Q);
+        U = __ffma2_rn(A, sn, U);
+        Wv = __ffma2_rn(B, cs, Wv);
+    }
+    Rk.x = (P.x + P.y) - (Q.x + Q.y);
+    Rk.y = (U.x + U.y) + (Wv.x + Wv.y);
+    return Rk;
+}
 
 __device__ __forceinline__ C2<float> recomb_pair(const DevInstance& I, const PotConst<float>& K,
                                                  const float q[3], const float p[3], float pp,
-                                                 float gam, float K1max, float K2max, int n_prim)
+                                                 float gam, float K1max, float K2max, int n_prim,
+                                                 int j)
 {
     const float2 dx = make_float2(q[0] - K.cx, q[0] + K.cx);
     const float2 dy = make_float2(q[1] - K.cy, q[1] + K.cy);
@@ -484,6 +538,7 @@ __device__ __forceinline__ C2<float> recomb_pair(const DevInstance& I, const Pot
                                              __fmul2_rn(make_float2(p[0], p[0]), dx)));
     const float2 gdz = __fmul2_rn(make_float2(-gam, -gam), dz);     // -g d_z
     float2 P = make_float2(0.0f, 0.0f), Q = P, U = P, Wv = P;
+    if (I.rec.has_p) return recomb_pair_sp(I, q, p, pp, n_prim, j, dz, dd, pdd, gdz);
 #pragma unroll 1
     for (int k = 0; k < n_prim; ++k) {
         const float K1 = I.rec.K1f[k], K2 = I.rec.K2f[k], K3 = I.rec.K3f[k], K4 = I.rec.K4f[k];
@@ -634,7 +689,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                 }
                 C2<R> Rk = {R(0), R(0)};
                 if constexpr (MIXED) {
-                    Rk = recomb_pair(I, K, q, p, pp, gam, K1max, K2max, n_prim);
+                    Rk = recomb_pair(I, K, q, p, pp, gam, K1max, K2max, n_prim, j);
                 } else {
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
@@ -660,8 +715,21 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                             R sn, cs;
                             if constexpr (MIXED) __sincosf(K3 * pdd, &sn, &cs);
                             else sincos(K3 * pdd, &sn, &cs);
-                            // mag (p_z - i g d_z)(cs + i sn)
-                            const R ar = mag * p[2], ai = -mag * gam * dz;
+                            // mag (p_z - i g d_z)(cs + i sn), or for a sigma p-type
+                            // primitive mag s_c [(P1 n.d + i P2 n.p)(p_z - i g d_z)
+                            // + i P3 n_z](cs + i sn)
+                            R ar = mag * p[2], ai = -mag * gam * dz;
+                            if (I.rec.kind[k]) {
+                                const double* nv = soa + 7 * n + j;
+                                const R nx = R(nv[0]), ny = R(nv[n]), nz = R(nv[2 * n]);
+                                const R sc = c == 0 ? R(1) : R(-1);
+                                const R u = R(I.rec.P1[k]) * (nx * dx + ny * dy + nz * dz);
+                                const R v = R(I.rec.P2[k]) * (nx * p[0] + ny * p[1] + nz * p[2]);
+                                const R br = u * p[2] + v * gam * dz;
+                                const R bi = -u * gam * dz + v * p[2] + R(I.rec.P3[k]) * nz;
+                                ar = sc * mag * br;
+                                ai = sc * mag * bi;
+                            }
                             Rk.x += ar * cs - ai * sn;
                             Rk.y += ar * sn + ai * cs;
                         }

@@ -109,6 +109,7 @@ struct SampleParams {
     int sampling;                             // SFHK_SAMPLE_PROPOSAL / SFHK_SAMPLE_ABS_AMPLITUDE
     double norm;
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
+    int pkind[SFHK_MAX_PRIM];
 };
 
 // sinh x and cosh x - 1 from em = e^x - 1, without cancellation
@@ -345,8 +346,20 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                     // -i kappa.A - kappa.kappa / (4a)
                     const double2 ex = make_double2(kA.y - kk.x / (4.0 * a), -kA.x - kk.y / (4.0 * a));
                     const double2 F = cscale(cexp_(ex), S.pcoef[p] * pow(kPi / a, 1.5));
-                    // (A_z - i kappa_z / (2a))
-                    const double2 f = make_double2(Az + kapz.y / (2.0 * a), -kapz.x / (2.0 * a));
+                    double2 f;
+                    if (S.pkind[p]) {
+                        // sigma p-type, x' = r - A: int e^{-i kappa.r} (A_z + x'_z) s_c n.x'
+                        // e^{-a x'^2} = s_c [n_z/(2a) - kappa_z (n.kappa)/(4a^2)
+                        // - i A_z (n.kappa)/(2a)] F (the derivatives of F in kappa)
+                        const double2 nk = make_double2(nx * kx + ny * ky + nz * kapz.x, nz * kapz.y);
+                        const double2 kn = cmul(kapz, nk);
+                        const double i2a = 0.5 / a, i4a2 = i2a * i2a;
+                        f = make_double2(sgn * (nz * i2a - kn.x * i4a2 + Az * nk.y * i2a),
+                                         sgn * (-kn.y * i4a2 - Az * nk.x * i2a));
+                    } else {
+                        // (A_z - i kappa_z / (2a))
+                        f = make_double2(Az + kapz.y / (2.0 * a), -kapz.x / (2.0 * a));
+                    }
                     mz = cadd(mz, cmul(F, f));
                 }
             }
@@ -719,6 +732,7 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
     for (int k = 0; k < SFHK_MAX_PRIM; ++k) {
         S.pexp[k] = T.desc.prim_exp[k];
         S.pcoef[k] = T.desc.prim_coef[k];
+        S.pkind[k] = T.desc.prim_kind[k];
     }
     if (S.sampling == SFHK_SAMPLE_ABS_AMPLITUDE) {
         // pilot: |w| of kPilot proposal draws, then M and P; then the

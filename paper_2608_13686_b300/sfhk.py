@@ -22,6 +22,7 @@ SFHK_MAX_PRIM = 8
 SFHK_POT_MOLECULE, SFHK_POT_HARMONIC = 0, 1
 SFHK_ALIGN_FIXED, SFHK_ALIGN_ISOTROPIC, SFHK_ALIGN_COS2, SFHK_ALIGN_QUADRATURE = 0, 1, 2, 3
 SFHK_FP64, SFHK_MIXED = 0, 1
+SFHK_PRIM_S, SFHK_PRIM_P_SIGMA = 0, 1
 SOA_FIELDS = 12
 FINAL_FIELDS = 47
 
@@ -37,7 +38,8 @@ class sfhk_target_desc(C.Structure):
                 ("Z_inf", C.c_double), ("Z0", C.c_double), ("alpha", C.c_double),
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
                 ("prim_exp", C.c_double * SFHK_MAX_PRIM), ("prim_coef", C.c_double * SFHK_MAX_PRIM),
-                ("ionization", C.c_int), ("sampling", C.c_int), ("sampling_factor", C.c_double)]
+                ("ionization", C.c_int), ("sampling", C.c_int), ("sampling_factor", C.c_double),
+                ("prim_kind", C.c_int * SFHK_MAX_PRIM)]
 
 
 class sfhk_pulse_desc(C.Structure):
@@ -197,9 +199,11 @@ def target_desc(t: dict) -> sfhk_target_desc:
     d.ionization = int(t.get("ionization", 0))
     d.sampling = int(t.get("sampling", 0))
     d.sampling_factor = float(t.get("sampling_factor", 0.0))
+    kinds = list(t.get("pkind", [SFHK_PRIM_S] * len(pe)))
     for i, (e, c) in enumerate(zip(pe, pc)):
         d.prim_exp[i] = e
         d.prim_coef[i] = c
+        d.prim_kind[i] = int(kinds[i]) if i < len(kinds) else SFHK_PRIM_S
     return d
 
 

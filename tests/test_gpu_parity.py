@@ -72,6 +72,10 @@ def test_pulse_grid_matches_oracle(S, ctx):
     ("H2+abs", W.PULSE_800, W.fixed(0.0), 900, 8, 0),
     ("N2+abs", W.PULSE_1200, W.ISO, 600, 9, 3),
     ("N2+abs+sfhk2", W.PULSE_1200, W.quadrature(5), 500, 10, 1),
+    ("N2_sp", W.PULSE_1200, W.ISO, 700, 11, 0),
+    ("N2_sp", W.PULSE_1200, W.fixed(20.0, 40.0), 500, 12, 2),
+    ("N2_sp+sfhk2", W.PULSE_1200, W.quadrature(4), 500, 13, 1),
+    ("N2_sp+abs", W.PULSE_1200, W.fixed(60.0, 0.0), 400, 14, 0),
 ])
 def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
     base, *variants = name.split("+")
@@ -132,6 +136,7 @@ def _compare_final(fin_g, fin_o, tol):
     ("H2", W.PULSE_800, W.fixed(0.0), 1000),
     ("H2", W.PULSE_800, W.fixed(90.0), 517),
     ("N2", W.PULSE_1200, W.COS2, 700),
+    ("N2_sp", W.PULSE_1200, W.ISO, 600),
 ])
 def test_fp64_propagation_per_trajectory_and_dipole(S, ctx, name, pulse, align, n):
     t = W.TARGETS[name]
@@ -154,6 +159,7 @@ def test_fp64_propagation_per_trajectory_and_dipole(S, ctx, name, pulse, align, 
     ("H2", W.PULSE_800, W.fixed(0.0), 1000),
     ("H2", W.PULSE_800, W.fixed(45.0), 1000),
     ("N2", W.PULSE_1200, W.COS2, 600),
+    ("N2_sp", W.PULSE_1200, W.ISO, 600),
 ])
 def test_mixed_precision_dipole(S, ctx, name, pulse, align, n):
     t = W.TARGETS[name]
@@ -370,3 +376,15 @@ def test_first_returns_match_oracle(S, ctx):
     S.sfhk_destroy_ensemble(e)
     S.sfhk_destroy_pulse(ph)
     S.sfhk_destroy_target(th)
+
+
+def test_ptype_target_validation(S, ctx):
+    """A primitive kind other than s or sigma p is refused; a target whose
+    p-type primitives cancel (R = 0, only p-type) has no normalisable orbital
+    and is refused too."""
+    t = dict(W.TARGETS["N2_sp"], pkind=[0, 0, 2, 1])
+    with pytest.raises(S.SfhkError):
+        S.sfhk_create_target(ctx, t)
+    t = dict(W.TARGETS["N2_sp"], R=0.0, pexp=[1.2], pcoef=[0.5], pkind=[1])
+    with pytest.raises(S.SfhkError):
+        S.sfhk_create_target(ctx, t)
