@@ -59,7 +59,7 @@ class TargetIn(C.Structure):
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
                 ("pexp", C.c_double * 8), ("pcoef", C.c_double * 8), ("ionization", C.c_int),
                 ("sampling", C.c_int), ("sampling_factor", C.c_double),
-                ("pkind", C.c_int * 8)]
+                ("pkind", C.c_int * 8), ("pi_azimuth", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -89,6 +89,7 @@ def lib():
         L.or_trajectory.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), _dp, _dp,
                                     C.c_double, C.c_double, C.c_int, _dp]
         L.or_hk_det.argtypes = [_dp, C.c_double, _dp]
+        L.or_pi_direction.argtypes = [_dp, C.c_double, _dp]
         L.or_orbital_norm.argtypes = [C.POINTER(TargetIn)]
         L.or_orbital_norm.restype = C.c_double
         L.or_orbital_value.argtypes = [C.POINTER(TargetIn), _dp, _dp]
@@ -134,7 +135,8 @@ def pulse_in(p) -> PulseIn:
 
 
 def target_in(t) -> TargetIn:
-    """t: mapping with R, Zinf, Z0, alpha, soft_a, Ip, pexp, pcoef (+ kind, ho_omega)."""
+    """t: mapping with R, Zinf, Z0, alpha, soft_a, Ip, pexp, pcoef (+ kind, ho_omega,
+    ionization, sampling, sampling_factor, pkind, pi_azimuth)."""
     T = TargetIn()
     T.kind = int(t.get("kind", POT_MOLECULE))
     T.ionization = int(t.get("ionization", 0))
@@ -148,6 +150,7 @@ def target_in(t) -> TargetIn:
         T.pexp[i] = e
         T.pcoef[i] = c
         T.pkind[i] = int(kinds[i]) if i < len(kinds) else 0
+    T.pi_azimuth = float(t.get("pi_azimuth", 0.0))
     return T
 
 
@@ -383,3 +386,11 @@ def orbital_values(t, nhat, r):
     lib().or_orbital_values(C.byref(target_in(t)), _p(np.asarray(nhat, float).copy()), _p(r),
                             r.shape[0], _p(out))
     return out
+
+
+def pi_direction(nhat, chi):
+    """Unit vector m perpendicular to the axis n at azimuth chi (pi p-type primitives)."""
+    n = np.ascontiguousarray(nhat, np.float64)
+    m = np.zeros(3)
+    lib().or_pi_direction(_p(n), float(chi), _p(m))
+    return m

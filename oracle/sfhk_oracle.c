@@ -78,7 +78,12 @@ typedef struct {
     double sampling_factor; /* kappa of the |a| sampler (<= 0: 5)         */
     int pkind[8];       /* primitive k: 0 s-type e^{-a|x-A|^2}; 1 sigma    */
                         /* p-type s_c n.(x-A) e^{-a|x-A|^2}, s_c = +-1 for */
-                        /* the centre at +-(R/2) n (gerade combination)   */
+                        /* the centre at +-(R/2) n (gerade combination);  */
+                        /* 2 pi p-type m.(x-A) e^{-a|x-A|^2} on both      */
+                        /* centres with the same sign (1 pi_u, ungerade), */
+                        /* m the unit vector perpendicular to n at        */
+                        /* azimuth pi_azimuth (see pi_direction)          */
+    double pi_azimuth;  /* chi: m = cos(chi) theta_hat + sin(chi) phi_hat */
 } or_target_in;
 
 /* ------------------------------------------------------------------ */
@@ -405,30 +410,80 @@ void or_hk_det(const double M[36], double gamma, double out[2])
 /* N from <psi0|psi0> = 1 with the Gaussian product overlap              */
 /*   int e^{-a|r-A|^2} e^{-b|r-B|^2} = (pi/(a+b))^{3/2} e^{-ab|A-B|^2/(a+b)}. */
 /* ------------------------------------------------------------------ */
-/* Normalisation of the orbital N sum_c sum_k coef_k phi_{c,k}: overlaps  */
-/* of Gaussians at A, B with exponents a, b (p = a + b, P = (aA + bB)/p,  */
-/* S0 = (pi/p)^{3/2} e^{-ab/p |A-B|^2}):  s-s S0;  s(A)-p(B)               */
-/* s_B n.(P-B) S0;  p(A)-p(B)  s_A s_B [n.(P-A) n.(P-B) + 1/(2p)] S0.      */
-/* Along the axis n.(A-B) = (s_A - s_B) R/2, so no orientation enters.     */
+/* Direction m of a pi p-type primitive: the unit vector perpendicular   */
+/* to the axis n = (sin th cos ph, sin th sin ph, cos th) at azimuth chi  */
+/* about n, m = cos(chi) theta_hat + sin(chi) phi_hat with the spherical  */
+/* unit vectors theta_hat = (cos th cos ph, cos th sin ph, -sin th) and   */
+/* phi_hat = (-sin ph, cos ph, 0); on the z axis ph = 0 is taken.  chi = 0 */
+/* puts the lobe in the plane of n and the polarisation axis z, chi =    */
+/* pi/2 perpendicular to that plane.                                      */
+void or_pi_direction(const double nhat[3], double chi, double m[3])
+{
+    double rho = sqrt(nhat[0] * nhat[0] + nhat[1] * nhat[1]);
+    double cp = 1.0, sp = 0.0;
+    if (rho > 0.0) { cp = nhat[0] / rho; sp = nhat[1] / rho; }
+    double th_hat[3] = {nhat[2] * cp, nhat[2] * sp, -rho};
+    double ph_hat[3] = {-sp, cp, 0.0};
+    for (int a = 0; a < 3; ++a) m[a] = cos(chi) * th_hat[a] + sin(chi) * ph_hat[a];
+}
+
+/* Angular factor of primitive k on the centre with sign s (+1 at +(R/2) n): */
+/* s-type none (returns 0); p-type f(x) = sfac u.(x - A) with u, sfac     */
+/* (sigma: u = n, sfac = s; pi: u = m, sfac = 1).                          */
+static int p_factor(const or_target_in* T, int k, const double nhat[3], double s,
+                    double u[3], double* sfac)
+{
+    if (T->pkind[k] == 1) {
+        for (int a = 0; a < 3; ++a) u[a] = nhat[a];
+        *sfac = s;
+        return 1;
+    }
+    if (T->pkind[k] == 2) {
+        or_pi_direction(nhat, T->pi_azimuth, u);
+        *sfac = 1.0;
+        return 1;
+    }
+    return 0;
+}
+
+/* Normalisation of the orbital N sum_c sum_k coef_k phi_{c,k}, written in */
+/* the frame n = z (the norm does not depend on the orientation).  Two     */
+/* Gaussians at A, B with exponents a, b multiply to S0 e^{-p|x-P|^2} with */
+/* p = a + b, P = (aA + bB)/p, S0 = e^{-ab/p |A-B|^2}; with y = x - P a    */
+/* p-type factor is u.y + u.(P - A), and int (u1.y + al1)(u2.y + al2)      */
+/* e^{-p y^2} = [al1 al2 + u1.u2/(2p)] (pi/p)^{3/2} (one factor: al (pi/p)^{3/2}). */
 static double orbital_norm(const or_target_in* T)
 {
+    const double nz[3] = {0.0, 0.0, 1.0};
     double s = 0.0;
     for (int c1 = 0; c1 < 2; ++c1)
         for (int c2 = 0; c2 < 2; ++c2) {
             double sA = (c1 == 0) ? 1.0 : -1.0, sB = (c2 == 0) ? 1.0 : -1.0;
-            double nAB = (sA - sB) * 0.5 * T->R;      /* n.(A - B) */
+            double A[3], B[3];
+            for (int x = 0; x < 3; ++x) { A[x] = sA * 0.5 * T->R * nz[x]; B[x] = sB * 0.5 * T->R * nz[x]; }
             for (int k1 = 0; k1 < T->n_prim; ++k1)
                 for (int k2 = 0; k2 < T->n_prim; ++k2) {
                     double a = T->pexp[k1], b = T->pexp[k2], pp = a + b;
-                    double S0 = pow(OR_PI / pp, 1.5) * exp(-a * b / pp * nAB * nAB);
-                    double nPA = b / pp * (-nAB);       /* n.(P - A) */
-                    double nPB = a / pp * nAB;          /* n.(P - B) */
-                    int p1 = T->pkind[k1], p2 = T->pkind[k2];
+                    double P[3], AB2 = 0.0;
+                    for (int x = 0; x < 3; ++x) {
+                        P[x] = (a * A[x] + b * B[x]) / pp;
+                        AB2 += (A[x] - B[x]) * (A[x] - B[x]);
+                    }
+                    double S0 = pow(OR_PI / pp, 1.5) * exp(-a * b / pp * AB2);
+                    double u1[3], u2[3], f1, f2;
+                    int p1 = p_factor(T, k1, nz, sA, u1, &f1);
+                    int p2 = p_factor(T, k2, nz, sB, u2, &f2);
+                    double al1 = 0.0, al2 = 0.0, uu = 0.0;
+                    for (int x = 0; x < 3; ++x) {
+                        if (p1) al1 += u1[x] * (P[x] - A[x]);
+                        if (p2) al2 += u2[x] * (P[x] - B[x]);
+                        if (p1 && p2) uu += u1[x] * u2[x];
+                    }
                     double f;
                     if (!p1 && !p2) f = 1.0;
-                    else if (!p1 && p2) f = sB * nPB;
-                    else if (p1 && !p2) f = sA * nPA;
-                    else f = sA * sB * (nPA * nPB + 0.5 / pp);
+                    else if (!p1) f = f2 * al2;
+                    else if (!p2) f = f1 * al1;
+                    else f = f1 * f2 * (al1 * al2 + uu / (2.0 * pp));
                     s += T->pcoef[k1] * T->pcoef[k2] * f * S0;
                 }
         }
@@ -447,10 +502,15 @@ static double orbital_value_n(const or_target_in* T, double N, const double nhat
             double d = r[a] - sign * 0.5 * T->R * nhat[a];
             d2 += d * d;
         }
-        double nd = 0.0;       /* n.(r - A) */
-        for (int a = 0; a < 3; ++a) nd += nhat[a] * (r[a] - sign * 0.5 * T->R * nhat[a]);
-        for (int k = 0; k < T->n_prim; ++k)
-            v += T->pcoef[k] * (T->pkind[k] ? sign * nd : 1.0) * exp(-T->pexp[k] * d2);
+        for (int k = 0; k < T->n_prim; ++k) {
+            double u[3], sfac, ang = 1.0;
+            if (p_factor(T, k, nhat, sign, u, &sfac)) {
+                ang = 0.0;       /* sfac u.(r - A) */
+                for (int a = 0; a < 3; ++a) ang += u[a] * (r[a] - sign * 0.5 * T->R * nhat[a]);
+                ang *= sfac;
+            }
+            v += T->pcoef[k] * ang * exp(-T->pexp[k] * d2);
+        }
     }
     return N * v;
 }
@@ -500,14 +560,15 @@ static cplx recomb(const or_target_in* T, double N, const double nhat[3],
             }
             cplx I0 = pow(OR_PI / c, 1.5) * cexp(c * mm - b * dd - I * pd);
             cplx I1 = (m[2] - d[2]) * I0;
-            if (T->pkind[k]) {
-                /* sigma p-type: extra factor s_c n.x' (x' = x - A):       */
-                /* int n.x' e = (n.m) I0, int n.x' (x'_z - d_z) e =        */
-                /* [(n.m)(m_z - d_z) + n_z/(2c)] I0                         */
-                cplx nm = nhat[0] * m[0] + nhat[1] * m[1] + nhat[2] * m[2];
-                cplx J0 = nm * I0;
-                cplx J1 = (nm * (m[2] - d[2]) + nhat[2] / (2.0 * c)) * I0;
-                total += sign * T->pcoef[k] * (p[2] * J0 + I * gamma * J1);
+            double u[3], sfac;
+            if (p_factor(T, k, nhat, sign, u, &sfac)) {
+                /* p-type: extra factor sfac u.x' (x' = x - A):            */
+                /* int u.x' e = (u.m) I0, int u.x' (x'_z - d_z) e =        */
+                /* [(u.m)(m_z - d_z) + u_z/(2c)] I0                         */
+                cplx um = u[0] * m[0] + u[1] * m[1] + u[2] * m[2];
+                cplx J0 = um * I0;
+                cplx J1 = (um * (m[2] - d[2]) + u[2] / (2.0 * c)) * I0;
+                total += sfac * T->pcoef[k] * (p[2] * J0 + I * gamma * J1);
             } else {
                 total += T->pcoef[k] * (p[2] * I0 + I * gamma * I1);
             }
@@ -545,13 +606,14 @@ static void dipole_matrix_element(const or_target_in* T, double N, const double 
         for (int k = 0; k < T->n_prim; ++k) {
             double a = T->pexp[k];
             cplx F = pow(OR_PI / a, 1.5) * cexp(-I * kA - kk / (4.0 * a));
-            if (T->pkind[k]) {
-                /* sigma p-type: int e^{-i k.x} (x_z + A_z)(n.x) e^{-a x^2} =  */
-                /* [n_z/(2a) - k_z (n.k)/(4a^2) - i A_z (n.k)/(2a)] G           */
-                cplx nk = nhat[0] * kappa[0] + nhat[1] * kappa[1] + nhat[2] * kappa[2];
-                tot += sign * T->pcoef[k] *
-                       (nhat[2] / (2.0 * a) - kappa[2] * nk / (4.0 * a * a) -
-                        I * A[2] * nk / (2.0 * a)) * F;
+            double u[3], sfac;
+            if (p_factor(T, k, nhat, sign, u, &sfac)) {
+                /* p-type: int e^{-i k.x} (x_z + A_z)(u.x) e^{-a x^2} =        */
+                /* [u_z/(2a) - k_z (u.k)/(4a^2) - i A_z (u.k)/(2a)] G           */
+                cplx uk = u[0] * kappa[0] + u[1] * kappa[1] + u[2] * kappa[2];
+                tot += sfac * T->pcoef[k] *
+                       (u[2] / (2.0 * a) - kappa[2] * uk / (4.0 * a * a) -
+                        I * A[2] * uk / (2.0 * a)) * F;
             } else {
                 tot += T->pcoef[k] * (A[2] - I * kappa[2] / (2.0 * a)) * F;
             }

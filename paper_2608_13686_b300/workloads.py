@@ -40,9 +40,24 @@ def _target(R, Zinf, Z0, alpha, soft_a, Ip, prims):
 _N2_SP_PRIMS = ((2.00, 0.40, 0), (0.35, 0.70, 0), (1.20, 0.50, 1), (0.30, 0.35, 1))
 
 
-def _target_sp(R, Zinf, Z0, alpha, soft_a, Ip, prims):
+# N2 HOMO-1 1 pi_u (Table II, 17.18 eV): pi p-type primitives, kind 2 =
+# m.(x - A) e^{-a|x-A|^2} with the same sign on both centres, m perpendicular
+# to the axis at azimuth pi_azimuth (0: in the plane of the axis and z)
+_N2_PI_PRIMS = ((1.20, 0.50, 2), (0.30, 0.40, 2))
+
+
+def _target_sp(R, Zinf, Z0, alpha, soft_a, Ip, prims, pi_azimuth=0.0):
     t = _target(R, Zinf, Z0, alpha, soft_a, Ip, [(p[0], p[1]) for p in prims])
     t["pkind"] = [p[2] for p in prims]
+    t["pi_azimuth"] = float(pi_azimuth)
+    return t
+
+
+def pi_component(target, chi):
+    """The same pi target with its lobe at azimuth chi (rad) about the axis;
+    the two degenerate 1 pi_u components are chi = 0 and chi = pi/2."""
+    t = dict(target)
+    t["pi_azimuth"] = float(chi)
     return t
 
 
@@ -52,6 +67,7 @@ TARGETS = {
     "H2_table1": _target(1.40, 0.5, 1.0, 1.79, 0.0, 15.40 / EV, _H2_PRIMS),
     "N2_table1": _target(2.07, 0.5, 7.0, 1.67, 0.0, 15.54 / EV, _N2_PRIMS),
     "N2_sp": _target_sp(2.07, 0.5, 7.0, 2.0, 0.1, 0.573, _N2_SP_PRIMS),
+    "N2_pi": _target_sp(2.07, 0.5, 7.0, 2.0, 0.1, 17.18 / EV, _N2_PI_PRIMS),
 }
 
 
