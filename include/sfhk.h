@@ -98,11 +98,19 @@ enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
  * s-type exp(-a |r-R_c|^2); SFHK_PRIM_P_SIGMA is the sigma p-type
  * s_c n.(r-R_c) exp(-a |r-R_c|^2), s_c = +1 at +(R/2) n and -1 at -(R/2) n,
  * so that every primitive stays gerade (the 2p_sigma character of the N2
- * 3 sigma_g orbital, Sec. III.B).  The normalisation, the dipole element of
- * the sampler and the recombination element take the p-type factor in
- * closed form.  Errors: SFHK_E_INVAL for any other value. */
+ * 3 sigma_g orbital, Sec. III.B); SFHK_PRIM_P_PI is the pi p-type
+ * m.(r-R_c) exp(-a |r-R_c|^2) with the same sign on both centres (the N2
+ * HOMO-1 1 pi_u of Table II, ungerade), m the unit vector perpendicular to n
+ * at azimuth pi_azimuth about n: m = cos(chi) theta_hat + sin(chi) phi_hat,
+ * theta_hat = (cos th cos ph, cos th sin ph, -sin th), phi_hat =
+ * (-sin ph, cos ph, 0) for n = (sin th cos ph, sin th sin ph, cos th) (ph = 0
+ * on the z axis); chi = 0 puts the lobe in the plane of n and the
+ * polarisation axis.  The normalisation, the dipole element of the sampler
+ * and the recombination element take the p-type factor in closed form.
+ * Errors: SFHK_E_INVAL for any other kind, a non-finite pi_azimuth, or an
+ * orbital of zero norm. */
 enum { SFHK_IONIZE_SFA = 0, SFHK_IONIZE_MODIFIED = 1 };
-enum { SFHK_PRIM_S = 0, SFHK_PRIM_P_SIGMA = 1 };
+enum { SFHK_PRIM_S = 0, SFHK_PRIM_P_SIGMA = 1, SFHK_PRIM_P_PI = 2 };
 enum { SFHK_SAMPLE_PROPOSAL = 0, SFHK_SAMPLE_ABS_AMPLITUDE = 1 };
 typedef struct {
     int kind;
@@ -115,7 +123,8 @@ typedef struct {
     int ionization;                   /* SFHK_IONIZE_SFA or SFHK_IONIZE_MODIFIED */
     int sampling;                     /* SFHK_SAMPLE_PROPOSAL or SFHK_SAMPLE_ABS_AMPLITUDE */
     double sampling_factor;           /* kappa of the |a| sampler (<= 0: 5) */
-    int prim_kind[SFHK_MAX_PRIM];     /* SFHK_PRIM_S or SFHK_PRIM_P_SIGMA */
+    int prim_kind[SFHK_MAX_PRIM];     /* SFHK_PRIM_S, _P_SIGMA or _P_PI */
+    double pi_azimuth;                /* chi of the SFHK_PRIM_P_PI lobe (rad) */
 } sfhk_target_desc;
 
 /* Pulse (Sec. II.D / III.A): wavelength (nm), peak intensity (W/cm^2),

@@ -54,7 +54,9 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // e^{-ab/p (z_A - z_B)^2}.  Writing n.(r - A) = n.(r - P) + (z_P - z_A) and
 // using int n.(r-P) e^{-p|r-P|^2} = 0, int [n.(r-P)]^2 e^{-p|r-P|^2} =
 // S0 / (2p): an s-s pair gives S0, an s-p pair s_B (z_P - z_B) S0 and a p-p
-// pair s_A s_B [(z_P - z_A)(z_P - z_B) + 1/(2p)] S0.
+// pair s_A s_B [(z_P - z_A)(z_P - z_B) + 1/(2p)] S0.  A pi p-type factor
+// m.(r - A) has m perpendicular to the axis, so m.(P - A) = 0: it overlaps
+// only another pi primitive (m.m = 1), by S0 / (2p).
 double orbital_norm(const sfhk_target_desc& d)
 {
     double s = 0.0;
@@ -68,10 +70,12 @@ double orbital_norm(const sfhk_target_desc& d)
                     const double zP = (a * z1 + b * z2) / pab;
                     const double S0 = std::pow(kPi / pab, 1.5) *
                                       std::exp(-a * b / pab * (z1 - z2) * (z1 - z2));
-                    const bool p1 = d.prim_kind[k1] == SFHK_PRIM_P_SIGMA;
-                    const bool p2 = d.prim_kind[k2] == SFHK_PRIM_P_SIGMA;
+                    const int t1 = d.prim_kind[k1], t2 = d.prim_kind[k2];
+                    const bool p1 = t1 == SFHK_PRIM_P_SIGMA, p2 = t2 == SFHK_PRIM_P_SIGMA;
                     double ang = 1.0;
-                    if (p1 && p2) ang = s1 * s2 * ((zP - z1) * (zP - z2) + 0.5 / pab);
+                    if (t1 == SFHK_PRIM_P_PI || t2 == SFHK_PRIM_P_PI)
+                        ang = (t1 == t2) ? 0.5 / pab : 0.0;
+                    else if (p1 && p2) ang = s1 * s2 * ((zP - z1) * (zP - z2) + 0.5 / pab);
                     else if (p1) ang = s1 * (zP - z1);
                     else if (p2) ang = s2 * (zP - z2);
                     s += d.prim_coef[k1] * d.prim_coef[k2] * ang * S0;
@@ -88,6 +92,8 @@ void fill_recomb(const DevTarget& T, double gamma, DevRecomb& R)
 {
     const double b = 0.5 * gamma;
     R.has_p = 0;
+    R.cchi = std::cos(T.pi_azimuth);
+    R.schi = std::sin(T.pi_azimuth);
     for (int k = 0; k < SFHK_MAX_PRIM; ++k) {
         R.kind[k] = 0;
         if (k >= T.n_prim) {
@@ -104,7 +110,7 @@ void fill_recomb(const DevTarget& T, double gamma, DevRecomb& R)
             R.P1[k] = b / c;
             R.P2[k] = 0.5 / c;
             R.P3[k] = gamma / (2.0 * a);
-            if (T.pkind[k]) R.has_p = 1;
+            if (T.pkind[k]) R.has_p |= T.pkind[k];    // bit 0 sigma, bit 1 pi
         }
         R.K1f[k] = (float)R.K1[k];
         R.K2f[k] = (float)R.K2[k];
@@ -326,8 +332,10 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
         return SFHK_E_INVAL;
     for (int k = 0; k < d->n_prim; ++k)
         if (!(d->prim_exp[k] > 0.0) || !std::isfinite(d->prim_coef[k]) ||
-            (d->prim_kind[k] != SFHK_PRIM_S && d->prim_kind[k] != SFHK_PRIM_P_SIGMA))
+            (d->prim_kind[k] != SFHK_PRIM_S && d->prim_kind[k] != SFHK_PRIM_P_SIGMA &&
+             d->prim_kind[k] != SFHK_PRIM_P_PI))
             return SFHK_E_INVAL;
+    if (!std::isfinite(d->pi_azimuth)) return SFHK_E_INVAL;
     if (d->soft_a < 0.0 || d->R < 0.0 || d->alpha < 0.0 || !std::isfinite(d->Ip)) return SFHK_E_INVAL;
     if (d->kind == SFHK_POT_MOLECULE && d->soft_a == 0.0 && d->Z_inf == 0.0 && d->Z0 == 0.0)
         ;  // a field-free "molecule" is allowed
@@ -356,6 +364,7 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
         T.pcoef[k] = t->desc.prim_coef[k];
         T.pkind[k] = t->desc.prim_kind[k];
     }
+    T.pi_azimuth = d->pi_azimuth;
     T.norm = orbital_norm(t->desc);
     if (!std::isfinite(T.norm)) {
         delete t;

@@ -174,6 +174,25 @@ struct PotConst {
     int kind, screened;
 };
 
+// Lobe direction of a pi p-type primitive: the unit vector perpendicular to
+// the axis n = (sin th cos ph, sin th sin ph, cos th) at azimuth chi about n,
+// m = cos(chi) theta_hat + sin(chi) phi_hat with theta_hat =
+// (cos th cos ph, cos th sin ph, -sin th) and phi_hat = (-sin ph, cos ph, 0);
+// ph = 0 on the z axis.
+template <typename R>
+__device__ __forceinline__ void pi_direction(R nx, R ny, R nz, R cchi, R schi, R m[3])
+{
+    const R rho = sqrt(nx * nx + ny * ny);
+    R cp = R(1), sp = R(0);
+    if (rho > R(0)) {
+        cp = nx / rho;
+        sp = ny / rho;
+    }
+    m[0] = cchi * nz * cp - schi * sp;
+    m[1] = cchi * nz * sp + schi * cp;
+    m[2] = -cchi * rho;
+}
+
 // Differences of a step's base point from the two centres +-(R/2)n,
 // e_c = (q - c_c) + l, with l the low part of a two-float position (LO; zero
 // in FP64).  The centre is subtracted from the high part first (exact near a

@@ -31,15 +31,17 @@ struct DevTarget {
     double half_R, Zinf, dZ, alpha, a2, Ip, w2;
     double norm;           // orbital normalisation N
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
-    int pkind[SFHK_MAX_PRIM];   // SFHK_PRIM_S / SFHK_PRIM_P_SIGMA
+    int pkind[SFHK_MAX_PRIM];   // SFHK_PRIM_S / SFHK_PRIM_P_SIGMA / SFHK_PRIM_P_PI
+    double pi_azimuth;          // chi of the pi lobe about the axis
 };
 
 struct DevRecomb {
     double K1[SFHK_MAX_PRIM], K2[SFHK_MAX_PRIM], K3[SFHK_MAX_PRIM], K4[SFHK_MAX_PRIM];
     float K1f[SFHK_MAX_PRIM], K2f[SFHK_MAX_PRIM], K3f[SFHK_MAX_PRIM], K4f[SFHK_MAX_PRIM];
-    // sigma p-type primitives only
+    // p-type primitives only
     int has_p;
-    int kind[SFHK_MAX_PRIM];
+    int kind[SFHK_MAX_PRIM];    // 0 s, 1 sigma p, 2 pi p
+    double cchi, schi;          // cos, sin of the pi lobe's azimuth
     double P1[SFHK_MAX_PRIM], P2[SFHK_MAX_PRIM], P3[SFHK_MAX_PRIM];
     float P1f[SFHK_MAX_PRIM], P2f[SFHK_MAX_PRIM], P3f[SFHK_MAX_PRIM];
 };

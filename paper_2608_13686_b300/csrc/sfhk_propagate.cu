@@ -469,7 +469,8 @@ __device__ __forceinline__ void prefactor_and_checks(const Mono<R>& M, R gam,
 // for an s-type primitive and
 //   s_c K4 e^{K1 |d|^2 + K2 |p|^2} [(P1 n.d + i P2 n.p)(p_z - i g d_z) + i P3 n_z] e^{i K3 p.d}
 // for a sigma p-type one (s_c = +-1 the centre's sign; n the axis, read
-// only when the target has p-type primitives).
+// only when the target has p-type primitives), and the same with s_c n
+// replaced by the lobe direction m for a pi p-type one.
 constexpr float kSkipMixed = -30.0f;
 
 // recomb_pair's loop for a target with sigma p-type primitives
@@ -489,6 +490,17 @@ __device__ __forceinline__ C2<float> recomb_pair_sp(const DevInstance& I, const 
     const float2 snp = make_float2(np, -np);                    // s_c n.p
     const float2 snz = make_float2(nz, -nz);                    // s_c n_z
     const float2 pz2 = make_float2(p[2], p[2]);
+    // pi lobe m (m.d = m.q, as m is perpendicular to the axis), both centres
+    float2 md = make_float2(0.0f, 0.0f), mp = md, mz = md;
+    if (I.rec.has_p & 2) {
+        float m[3];
+        pi_direction<float>(nx, ny, nz, (float)I.rec.cchi, (float)I.rec.schi, m);
+        const float mq = m[0] * q[0] + m[1] * q[1] + m[2] * q[2];
+        const float mpp = m[0] * p[0] + m[1] * p[1] + m[2] * p[2];
+        md = make_float2(mq, mq);
+        mp = make_float2(mpp, mpp);
+        mz = make_float2(m[2], m[2]);
+    }
 #pragma unroll 1
     for (int k = 0; k < n_prim; ++k) {
         const float K1 = I.rec.K1f[k], K2 = I.rec.K2f[k], K3 = I.rec.K3f[k], K4 = I.rec.K4f[k];
@@ -500,14 +512,19 @@ __device__ __forceinline__ C2<float> recomb_pair_sp(const DevInstance& I, const 
         __sincosf(arg.x, &sn.x, &cs.x);
         __sincosf(arg.y, &sn.y, &cs.y);
         float2 br = pz2, bi = gdz;                              // s-type bracket
-        if (I.rec.kind[k]) {
+        const int kind = I.rec.kind[k];
+        if (kind) {
+            // sigma: s_c (n.d, n.p, n_z); pi: (m.d, m.p, m_z)
+            const float2 ud = kind == 1 ? snd : md;
+            const float2 up = kind == 1 ? snp : mp;
+            const float2 uz = kind == 1 ? snz : mz;
             const float P1 = I.rec.P1f[k], P2 = I.rec.P2f[k], P3 = I.rec.P3f[k];
-            const float2 u = __fmul2_rn(make_float2(P1, P1), snd);
-            const float2 v = __fmul2_rn(make_float2(P2, P2), snp);
-            // (u + i v)(p_z + i gdz) + i P3 s_c n_z
+            const float2 u = __fmul2_rn(make_float2(P1, P1), ud);
+            const float2 v = __fmul2_rn(make_float2(P2, P2), up);
+            // (u + i v)(p_z + i gdz) + i P3 u_z
             const float2 vg = __fmul2_rn(v, gdz);
             br = __ffma2_rn(u, pz2, make_float2(-vg.x, -vg.y));
-            bi = __ffma2_rn(u, gdz, __ffma2_rn(v, pz2, __fmul2_rn(make_float2(P3, P3), snz)));
+            bi = __ffma2_rn(u, gdz, __ffma2_rn(v, pz2, __fmul2_rn(make_float2(P3, P3), uz)));
         }
         const float2 A = __fmul2_rn(mag, br);
         const float2 B = __fmul2_rn(mag, bi);
@@ -715,18 +732,27 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                             R sn, cs;
                             if constexpr (MIXED) __sincosf(K3 * pdd, &sn, &cs);
                             else sincos(K3 * pdd, &sn, &cs);
-                            // mag (p_z - i g d_z)(cs + i sn), or for a sigma p-type
-                            // primitive mag s_c [(P1 n.d + i P2 n.p)(p_z - i g d_z)
-                            // + i P3 n_z](cs + i sn)
+                            // mag (p_z - i g d_z)(cs + i sn), or for a p-type
+                            // primitive mag s [(P1 u.d + i P2 u.p)(p_z - i g d_z)
+                            // + i P3 u_z](cs + i sn) (sigma: u = n, s = s_c; pi:
+                            // u = m, s = 1)
                             R ar = mag * p[2], ai = -mag * gam * dz;
                             if (I.rec.kind[k]) {
+                                // sigma: u = n, sign s_c; pi: u = m, sign 1
                                 const double* nv = soa + 7 * n + j;
-                                const R nx = R(nv[0]), ny = R(nv[n]), nz = R(nv[2 * n]);
-                                const R sc = c == 0 ? R(1) : R(-1);
-                                const R u = R(I.rec.P1[k]) * (nx * dx + ny * dy + nz * dz);
-                                const R v = R(I.rec.P2[k]) * (nx * p[0] + ny * p[1] + nz * p[2]);
+                                R u3[3] = {R(nv[0]), R(nv[n]), R(nv[2 * n])};
+                                R sc = c == 0 ? R(1) : R(-1);
+                                if (I.rec.kind[k] == 2) {
+                                    R m[3];
+                                    pi_direction<R>(u3[0], u3[1], u3[2], R(I.rec.cchi),
+                                                    R(I.rec.schi), m);
+                                    u3[0] = m[0]; u3[1] = m[1]; u3[2] = m[2];
+                                    sc = R(1);
+                                }
+                                const R u = R(I.rec.P1[k]) * (u3[0] * dx + u3[1] * dy + u3[2] * dz);
+                                const R v = R(I.rec.P2[k]) * (u3[0] * p[0] + u3[1] * p[1] + u3[2] * p[2]);
                                 const R br = u * p[2] + v * gam * dz;
-                                const R bi = -u * gam * dz + v * p[2] + R(I.rec.P3[k]) * nz;
+                                const R bi = -u * gam * dz + v * p[2] + R(I.rec.P3[k]) * u3[2];
                                 ar = sc * mag * br;
                                 ai = sc * mag * bi;
                             }

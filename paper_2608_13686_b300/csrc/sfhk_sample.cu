@@ -110,6 +110,7 @@ struct SampleParams {
     double norm;
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
     int pkind[SFHK_MAX_PRIM];
+    double cchi, schi;                        // pi lobe azimuth (cos, sin)
 };
 
 // sinh x and cosh x - 1 from em = e^x - 1, without cancellation
@@ -348,14 +349,21 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                     const double2 F = cscale(cexp_(ex), S.pcoef[p] * pow(kPi / a, 1.5));
                     double2 f;
                     if (S.pkind[p]) {
-                        // sigma p-type, x' = r - A: int e^{-i kappa.r} (A_z + x'_z) s_c n.x'
-                        // e^{-a x'^2} = s_c [n_z/(2a) - kappa_z (n.kappa)/(4a^2)
-                        // - i A_z (n.kappa)/(2a)] F (the derivatives of F in kappa)
-                        const double2 nk = make_double2(nx * kx + ny * ky + nz * kapz.x, nz * kapz.y);
-                        const double2 kn = cmul(kapz, nk);
+                        // p-type, x' = r - A, factor s u.x' (sigma: u = n, s = s_c;
+                        // pi: u = m, s = 1): int e^{-i kappa.r} (A_z + x'_z) s u.x'
+                        // e^{-a x'^2} = s [u_z/(2a) - kappa_z (u.kappa)/(4a^2)
+                        // - i A_z (u.kappa)/(2a)] F (the derivatives of F in kappa)
+                        double u[3] = {nx, ny, nz}, s = sgn;
+                        if (S.pkind[p] == 2) {
+                            pi_direction<double>(nx, ny, nz, S.cchi, S.schi, u);
+                            s = 1.0;
+                        }
+                        const double2 uk = make_double2(u[0] * kx + u[1] * ky + u[2] * kapz.x,
+                                                        u[2] * kapz.y);
+                        const double2 ku = cmul(kapz, uk);
                         const double i2a = 0.5 / a, i4a2 = i2a * i2a;
-                        f = make_double2(sgn * (nz * i2a - kn.x * i4a2 + Az * nk.y * i2a),
-                                         sgn * (-kn.y * i4a2 - Az * nk.x * i2a));
+                        f = make_double2(s * (u[2] * i2a - ku.x * i4a2 + Az * uk.y * i2a),
+                                         s * (-ku.y * i4a2 - Az * uk.x * i2a));
                     } else {
                         // (A_z - i kappa_z / (2a))
                         f = make_double2(Az + kapz.y / (2.0 * a), -kapz.x / (2.0 * a));
@@ -734,6 +742,8 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
         S.pcoef[k] = T.desc.prim_coef[k];
         S.pkind[k] = T.desc.prim_kind[k];
     }
+    S.cchi = std::cos(T.desc.pi_azimuth);
+    S.schi = std::sin(T.desc.pi_azimuth);
     if (S.sampling == SFHK_SAMPLE_ABS_AMPLITUDE) {
         // pilot: |w| of kPilot proposal draws, then M and P; then the
         // persistent rejection sampler over a trajectory counter

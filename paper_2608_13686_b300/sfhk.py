@@ -22,7 +22,7 @@ SFHK_MAX_PRIM = 8
 SFHK_POT_MOLECULE, SFHK_POT_HARMONIC = 0, 1
 SFHK_ALIGN_FIXED, SFHK_ALIGN_ISOTROPIC, SFHK_ALIGN_COS2, SFHK_ALIGN_QUADRATURE = 0, 1, 2, 3
 SFHK_FP64, SFHK_MIXED = 0, 1
-SFHK_PRIM_S, SFHK_PRIM_P_SIGMA = 0, 1
+SFHK_PRIM_S, SFHK_PRIM_P_SIGMA, SFHK_PRIM_P_PI = 0, 1, 2
 SOA_FIELDS = 12
 FINAL_FIELDS = 47
 
@@ -39,7 +39,7 @@ class sfhk_target_desc(C.Structure):
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
                 ("prim_exp", C.c_double * SFHK_MAX_PRIM), ("prim_coef", C.c_double * SFHK_MAX_PRIM),
                 ("ionization", C.c_int), ("sampling", C.c_int), ("sampling_factor", C.c_double),
-                ("prim_kind", C.c_int * SFHK_MAX_PRIM)]
+                ("prim_kind", C.c_int * SFHK_MAX_PRIM), ("pi_azimuth", C.c_double)]
 
 
 class sfhk_pulse_desc(C.Structure):
@@ -204,6 +204,7 @@ def target_desc(t: dict) -> sfhk_target_desc:
         d.prim_exp[i] = e
         d.prim_coef[i] = c
         d.prim_kind[i] = int(kinds[i]) if i < len(kinds) else SFHK_PRIM_S
+    d.pi_azimuth = float(t.get("pi_azimuth", 0.0))
     return d
 
 

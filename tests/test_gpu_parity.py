@@ -59,6 +59,20 @@ def test_pulse_grid_matches_oracle(S, ctx):
 
 
 # ------------------------------------------------------------------ ionization step
+def _target(name):
+    """A workload target by name, with '+'-separated variants: sfhk2 (modified
+    saddle), abs (sampling ~ |a|), chi90 (the other 1 pi_u component)."""
+    base, *variants = name.split("+")
+    t = W.TARGETS[base]
+    if "sfhk2" in variants:
+        t = W.sfhk2(t)
+    if "abs" in variants:
+        t = W.abs_sampled(t, 5.0)
+    if "chi90" in variants:
+        t = W.pi_component(t, 0.5 * np.pi)
+    return t
+
+
 @pytest.mark.parametrize("name,pulse,align,n,seed,inst", [
     ("H2", W.PULSE_800, W.fixed(0.0), 1000, 0, 0),
     ("H2", W.PULSE_800, W.fixed(45.0, 30.0), 777, 5, 3),
@@ -76,14 +90,13 @@ def test_pulse_grid_matches_oracle(S, ctx):
     ("N2_sp", W.PULSE_1200, W.fixed(20.0, 40.0), 500, 12, 2),
     ("N2_sp+sfhk2", W.PULSE_1200, W.quadrature(4), 500, 13, 1),
     ("N2_sp+abs", W.PULSE_1200, W.fixed(60.0, 0.0), 400, 14, 0),
+    ("N2_pi", W.PULSE_1200, W.ISO, 600, 15, 0),
+    ("N2_pi+chi90", W.PULSE_1200, W.fixed(60.0, 30.0), 500, 16, 1),
+    ("N2_pi+sfhk2", W.PULSE_1200, W.fixed(90.0, 0.0), 500, 17, 2),
+    ("N2_pi+abs", W.PULSE_1200, W.quadrature(6), 400, 18, 0),
 ])
 def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
-    base, *variants = name.split("+")
-    t = W.TARGETS[base]
-    if "sfhk2" in variants:
-        t = W.sfhk2(t)
-    if "abs" in variants:
-        t = W.abs_sampled(t, 5.0)
+    t = _target(name)
     th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, pulse)
     e = S.sfhk_sample_initial(ctx, th, ph, align, n, seed, inst)
     g = S.sfhk_ensemble_read(e, n)
@@ -137,9 +150,11 @@ def _compare_final(fin_g, fin_o, tol):
     ("H2", W.PULSE_800, W.fixed(90.0), 517),
     ("N2", W.PULSE_1200, W.COS2, 700),
     ("N2_sp", W.PULSE_1200, W.ISO, 600),
+    ("N2_pi", W.PULSE_1200, W.ISO, 600),
+    ("N2_pi+chi90", W.PULSE_1200, W.fixed(70.0, 20.0), 500),
 ])
 def test_fp64_propagation_per_trajectory_and_dipole(S, ctx, name, pulse, align, n):
-    t = W.TARGETS[name]
+    t = _target(name)
     soa, _, _ = O.sample(t, pulse, align, seed=11, n=n)
     vz_o, fin_o, bad_o = O.propagate(t, pulse, soa, GAMMA, cutoff=CUT, want_final=True,
                                          stab_cutoff=STAB)
@@ -160,9 +175,10 @@ def test_fp64_propagation_per_trajectory_and_dipole(S, ctx, name, pulse, align, 
     ("H2", W.PULSE_800, W.fixed(45.0), 1000),
     ("N2", W.PULSE_1200, W.COS2, 600),
     ("N2_sp", W.PULSE_1200, W.ISO, 600),
+    ("N2_pi", W.PULSE_1200, W.ISO, 600),
 ])
 def test_mixed_precision_dipole(S, ctx, name, pulse, align, n):
-    t = W.TARGETS[name]
+    t = _target(name)
     soa, _, _ = O.sample(t, pulse, align, seed=12, n=n)
     vz_o, _, _ = O.propagate(t, pulse, soa, GAMMA, cutoff=CUT, stab_cutoff=STAB)
     vz_g, _, _ = _run(S, ctx, t, pulse, soa, S.SFHK_MIXED, dump=False)
@@ -379,7 +395,7 @@ def test_first_returns_match_oracle(S, ctx):
 
 
 def test_ptype_target_validation(S, ctx):
-    """A primitive kind other than s or sigma p is refused; a target whose
+    """A primitive kind other than s, sigma p or pi p is refused; a target whose
     p-type primitives cancel (R = 0, only p-type) has no normalisable orbital
     and is refused too."""
     t = dict(W.TARGETS["N2_sp"], pkind=[0, 0, 2, 1])
@@ -388,3 +404,8 @@ def test_ptype_target_validation(S, ctx):
     t = dict(W.TARGETS["N2_sp"], R=0.0, pexp=[1.2], pcoef=[0.5], pkind=[1])
     with pytest.raises(S.SfhkError):
         S.sfhk_create_target(ctx, t)
+    t = dict(W.TARGETS["N2_pi"], pi_azimuth=float("nan"))
+    with pytest.raises(S.SfhkError):
+        S.sfhk_create_target(ctx, t)
+    # a pi_u orbital is normalisable at R = 0 (a single-centre 2p)
+    S.sfhk_destroy_target(S.sfhk_create_target(ctx, dict(W.TARGETS["N2_pi"], R=0.0)))
