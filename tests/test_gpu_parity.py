@@ -398,7 +398,7 @@ def test_ptype_target_validation(S, ctx):
     """A primitive kind other than s, sigma p or pi p is refused; a target whose
     p-type primitives cancel (R = 0, only p-type) has no normalisable orbital
     and is refused too."""
-    t = dict(W.TARGETS["N2_sp"], pkind=[0, 0, 2, 1])
+    t = dict(W.TARGETS["N2_sp"], pkind=[0, 0, 3, 1])
     with pytest.raises(S.SfhkError):
         S.sfhk_create_target(ctx, t)
     t = dict(W.TARGETS["N2_sp"], R=0.0, pexp=[1.2], pcoef=[0.5], pkind=[1])
