@@ -31,6 +31,7 @@ NY = 43
 
 POT_MOLECULE = 0
 POT_HARMONIC = 1
+POT_POLY = 2
 ALIGN_FIXED, ALIGN_ISO, ALIGN_COS2, ALIGN_QUAD = 0, 1, 2, 3
 
 
@@ -59,7 +60,10 @@ class TargetIn(C.Structure):
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
                 ("pexp", C.c_double * 8), ("pcoef", C.c_double * 8), ("ionization", C.c_int),
                 ("sampling", C.c_int), ("sampling_factor", C.c_double),
-                ("pkind", C.c_int * 8), ("pi_azimuth", C.c_double)]
+                ("pkind", C.c_int * 8), ("pi_azimuth", C.c_double),
+                ("n_centres", C.c_int), ("cpos", (C.c_double * 3) * 8),
+                ("cZinf", C.c_double * 8), ("cZ0", C.c_double * 8), ("calpha", C.c_double * 8),
+                ("pcentre", C.c_int * 8), ("pdir", (C.c_double * 3) * 8)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -102,16 +106,17 @@ def lib():
                                 _dp, _dp]
         L.or_adk_table.argtypes = [C.POINTER(PulseIn), C.c_double, _dp, _dp]
         L.or_sample.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int, C.c_double,
-                                C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_uint64,
-                                C.c_uint64, _dp, _dp]
+                                C.c_double, C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                                C.c_uint64, C.c_uint64, _dp, _dp]
         L.or_quad_nodes.argtypes = [C.c_int, _dp, _dp]
         L.or_propagate_returns.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
                                            C.c_double, C.c_double, _dp, C.c_uint64, C.c_double,
                                            _dp, C.c_double, C.c_double, _dp, C.c_int]
         L.or_propagate_returns.restype = C.c_int
         L.or_abs_sampling_constants.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int,
-                                                C.c_double, C.c_double, C.c_int, C.c_uint64,
-                                                C.c_uint32, _dp]
+                                                C.c_double, C.c_double, C.c_double, C.c_int,
+                                                C.c_uint64, C.c_uint32, _dp]
+        L.or_euler_rotation.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
         L.or_orbital_values.argtypes = [C.POINTER(TargetIn), _dp, _dp, C.c_int64, _dp]
         L.or_saddle_modified.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
                                          C.c_double, _dp]
@@ -151,6 +156,17 @@ def target_in(t) -> TargetIn:
         T.pcoef[i] = c
         T.pkind[i] = int(kinds[i]) if i < len(kinds) else 0
     T.pi_azimuth = float(t.get("pi_azimuth", 0.0))
+    cen = t.get("centres", ())
+    T.n_centres = len(cen)
+    for i, c in enumerate(cen):          # (x, y, z, Zinf, Z0, alpha)
+        for a in range(3):
+            T.cpos[i][a] = c[a]
+        T.cZinf[i], T.cZ0[i], T.calpha[i] = c[3], c[4], c[5]
+    for i, c in enumerate(t.get("pcentre", ())):
+        T.pcentre[i] = int(c)
+    for i, d in enumerate(t.get("pdir", ())):
+        for a in range(3):
+            T.pdir[i][a] = d[a]
     return T
 
 
@@ -277,15 +293,18 @@ def adk_table(p, Ip):
 def sample(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance=0, j_begin=0, n=1,
            eta_force=0):
     """Initial ensemble as a (12, n) field-major array plus aux (tt, S_down).
-    align = (kind, theta, phi[, n_nodes]); n_nodes is the K of the quadrature
-    kind.  eta_force = +-1 fixes the emitting side of the modified saddle
+    align = (kind, theta, phi[, n_nodes[, psi]]); n_nodes is the K of the
+    quadrature kind, psi the third Euler angle of a fixed polyatomic
+    orientation.  For a polyatomic target fields 7..9 hold the Euler angles
+    (phi, theta, psi) instead of the axis.  eta_force = +-1 fixes the emitting side of the modified saddle
     (target ionization 1) with weight 1 instead of drawing it."""
     soa = np.zeros((NFIELDS, n))
     aux = np.zeros((3, n))
     k = int(align[3]) if len(align) > 3 else 0
+    psi = float(align[4]) if len(align) > 4 else 0.0
     bad = lib().or_sample(C.byref(target_in(t)), C.byref(pulse_in(p)), int(align[0]),
-                          float(align[1]), float(align[2]), k, int(eta_force), seed, instance,
-                          j_begin, n, _p(soa), _p(aux))
+                          float(align[1]), float(align[2]), psi, k, int(eta_force), seed,
+                          instance, j_begin, n, _p(soa), _p(aux))
     if bad < 0:
         raise ValueError("bad alignment")
     return soa, aux, bad
@@ -374,8 +393,10 @@ def abs_sampling_constants(t, p, align=(ALIGN_FIXED, 0.0, 0.0), seed=0, instance
     accepted weight P w / alpha."""
     out = np.zeros(2)
     k = int(align[3]) if len(align) > 3 else 0
+    psi = float(align[4]) if len(align) > 4 else 0.0
     lib().or_abs_sampling_constants(C.byref(target_in(t)), C.byref(pulse_in(p)), int(align[0]),
-                                    float(align[1]), float(align[2]), k, seed, instance, _p(out))
+                                    float(align[1]), float(align[2]), psi, k, seed, instance,
+                                    _p(out))
     return out[0], out[1]
 
 
@@ -394,3 +415,10 @@ def pi_direction(nhat, chi):
     m = np.zeros(3)
     lib().or_pi_direction(_p(n), float(chi), _p(m))
     return m
+
+
+def euler_rotation(phi, theta, psi):
+    """Rotation Rz(phi) Ry(theta) Rz(psi), molecular frame -> lab (3x3)."""
+    R = np.zeros(9)
+    lib().or_euler_rotation(float(phi), float(theta), float(psi), _p(R))
+    return R.reshape(3, 3)

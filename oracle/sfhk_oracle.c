@@ -58,7 +58,8 @@ typedef struct {
     double dt;          /* time step (a.u.)                            */
 } or_pulse_in;
 
-enum { OR_POT_MOLECULE = 0, OR_POT_HARMONIC = 1 };
+enum { OR_POT_MOLECULE = 0, OR_POT_HARMONIC = 1, OR_POT_POLY = 2 };
+#define OR_MAX_CENTRES 8
 
 typedef struct {
     int kind;           /* OR_POT_MOLECULE (Eq. 7) or OR_POT_HARMONIC (test) */
@@ -84,6 +85,17 @@ typedef struct {
                         /* m the unit vector perpendicular to n at        */
                         /* azimuth pi_azimuth (see pi_direction)          */
     double pi_azimuth;  /* chi: m = cos(chi) theta_hat + sin(chi) phi_hat */
+    /* OR_POT_POLY: N centres at molecular-frame positions cpos, each    */
+    /* with its own Eq. 7 charges; primitive k sits on centre pcentre[k] */
+    /* only (kind 0 s-type, kind 3 p-type (u.(x-A)) e^{-a|x-A|^2} with u */
+    /* the molecular-frame direction pdir[k] normalised, rotated with    */
+    /* the molecule).  The orientation of a trajectory is then the ZYZ   */
+    /* Euler triple (phi, theta, psi) in place of the axis n.            */
+    int n_centres;
+    double cpos[OR_MAX_CENTRES][3];
+    double cZinf[OR_MAX_CENTRES], cZ0[OR_MAX_CENTRES], calpha[OR_MAX_CENTRES];
+    int pcentre[8];
+    double pdir[8][3];
 } or_target_in;
 
 /* ------------------------------------------------------------------ */
@@ -245,10 +257,77 @@ static double pulse_E_real(const or_pulse* P, double t)
 }
 
 /* ------------------------------------------------------------------ */
-/* Model potential, Eq. 7, for one electron in the field of two centres  */
-/* R_{1,2} = +-(R/2) n (n = molecular axis in the lab frame):            */
-/*   V(r) = - sum_i [Zinf + (Z0 - Zinf) exp(-alpha s_i)] / s_i,          */
-/* with the softening reading s_i = sqrt(|r - R_i|^2 + a^2).             */
+/* Orientation of the molecule in the lab frame.  Diatomic targets: the  */
+/* axis n, centres R_{1,2} = +-(R/2) n.  Polyatomic targets: the ZYZ     */
+/* Euler angles (phi, theta, psi), rotation Rot = Rz(phi) Ry(theta)       */
+/* Rz(psi), centres R_i = Rot x_i for the molecular-frame positions x_i; */
+/* the molecular z axis goes to n = Rot z = (sin th cos ph, sin th sin ph, */
+/* cos th), as for a diatomic.                                           */
+/* ------------------------------------------------------------------ */
+void or_euler_rotation(double ph, double th, double ps, double Rot[9])
+{
+    double Rz1[9] = {cos(ph), -sin(ph), 0.0, sin(ph), cos(ph), 0.0, 0.0, 0.0, 1.0};
+    double Ry[9] = {cos(th), 0.0, sin(th), 0.0, 1.0, 0.0, -sin(th), 0.0, cos(th)};
+    double Rz2[9] = {cos(ps), -sin(ps), 0.0, sin(ps), cos(ps), 0.0, 0.0, 0.0, 1.0};
+    double T1[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T1[3 * i + j] = 0.0;
+            for (int k = 0; k < 3; ++k) T1[3 * i + j] += Rz1[3 * i + k] * Ry[3 * k + j];
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            Rot[3 * i + j] = 0.0;
+            for (int k = 0; k < 3; ++k) Rot[3 * i + j] += T1[3 * i + k] * Rz2[3 * k + j];
+        }
+}
+
+typedef struct {
+    int nc;                          /* centres */
+    double C[OR_MAX_CENTRES][3];     /* lab positions */
+    double Zinf[OR_MAX_CENTRES], dZ[OR_MAX_CENTRES], alpha[OR_MAX_CENTRES];
+    double nhat[3];                  /* molecular axis (diatomic) */
+    double Rot[9];                   /* molecule -> lab (polyatomic) */
+} or_frame;
+
+/* orient: the axis n (diatomic) or the Euler angles (polyatomic) */
+static void make_frame(const or_target_in* T, const double orient[3], or_frame* F)
+{
+    if (T->kind == OR_POT_POLY) {
+        or_euler_rotation(orient[0], orient[1], orient[2], F->Rot);
+        F->nc = T->n_centres;
+        for (int i = 0; i < F->nc; ++i) {
+            for (int a = 0; a < 3; ++a) {
+                F->C[i][a] = 0.0;
+                for (int b = 0; b < 3; ++b) F->C[i][a] += F->Rot[3 * a + b] * T->cpos[i][b];
+            }
+            F->Zinf[i] = T->cZinf[i];
+            F->dZ[i] = T->cZ0[i] - T->cZinf[i];
+            F->alpha[i] = T->calpha[i];
+        }
+        for (int a = 0; a < 3; ++a) F->nhat[a] = F->Rot[3 * a + 2];
+        return;
+    }
+    F->nc = 2;
+    for (int i = 0; i < 2; ++i) {
+        double sign = (i == 0) ? 1.0 : -1.0;
+        for (int a = 0; a < 3; ++a) F->C[i][a] = sign * 0.5 * T->R * orient[a];
+        F->Zinf[i] = T->Zinf;
+        F->dZ[i] = T->Z0 - T->Zinf;
+        F->alpha[i] = T->alpha;
+    }
+    for (int a = 0; a < 3; ++a) F->nhat[a] = orient[a];
+    for (int a = 0; a < 9; ++a) F->Rot[a] = 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Model potential, Eq. 7, for one electron in the field of the centres  */
+/* R_i of the frame:                                                     */
+/*   V(r) = - sum_i [Zinf_i + (Z0_i - Zinf_i) exp(-alpha_i s_i)] / s_i,  */
+/* with the softening reading s_i = sqrt(|r - R_i|^2 + a^2).  Two        */
+/* centres R_{1,2} = +-(R/2) n with common charges for a diatomic (the   */
+/* paper's form); any number, each with its own charges, for the         */
+/* polyatomic generalisation.                                            */
 /* Gradient and Hessian are the analytic derivatives, written out:       */
 /*   with f(s) = -(Zinf + dZ e^{-alpha s})/s,                            */
 /*   f'(s)  = Zinf/s^2 + dZ e^{-alpha s}(alpha/s + 1/s^2),                */
@@ -257,7 +336,7 @@ static double pulse_E_real(const or_pulse* P, double t)
 /* The harmonic test potential V = omega^2 |r|^2 / 2 has closed-form     */
 /* classical and quantum solutions and pins the propagation.             */
 /* ------------------------------------------------------------------ */
-static void potential(const or_target_in* T, const double nhat[3], const double q[3],
+static void potential(const or_target_in* T, const double orient[3], const double q[3],
                       double* V, double grad[3], double hess[9])
 {
     *V = 0.0;
@@ -272,20 +351,21 @@ static void potential(const or_target_in* T, const double nhat[3], const double 
         }
         return;
     }
-    double dZ = T->Z0 - T->Zinf;
-    for (int i = 0; i < 2; ++i) {
-        double sign = (i == 0) ? 1.0 : -1.0;
+    or_frame F;
+    make_frame(T, orient, &F);
+    for (int i = 0; i < F.nc; ++i) {
         double d[3], d2 = 0.0;
         for (int a = 0; a < 3; ++a) {
-            d[a] = q[a] - sign * 0.5 * T->R * nhat[a];
+            d[a] = q[a] - F.C[i][a];
             d2 += d[a] * d[a];
         }
+        double Zinf = F.Zinf[i], dZ = F.dZ[i], alpha = F.alpha[i];
         double s = sqrt(d2 + T->soft_a * T->soft_a);
-        double e = exp(-T->alpha * s);
-        double f = -(T->Zinf + dZ * e) / s;
-        double f1 = T->Zinf / (s * s) + dZ * e * (T->alpha / s + 1.0 / (s * s));
-        double f2 = -2.0 * T->Zinf / (s * s * s)
-                    - dZ * e * (T->alpha * T->alpha / s + 2.0 * T->alpha / (s * s) + 2.0 / (s * s * s));
+        double e = exp(-alpha * s);
+        double f = -(Zinf + dZ * e) / s;
+        double f1 = Zinf / (s * s) + dZ * e * (alpha / s + 1.0 / (s * s));
+        double f2 = -2.0 * Zinf / (s * s * s)
+                    - dZ * e * (alpha * alpha / s + 2.0 * alpha / (s * s) + 2.0 / (s * s * s));
         *V += f;
         for (int a = 0; a < 3; ++a) grad[a] += f1 * d[a] / s;
         for (int a = 0; a < 3; ++a)
@@ -404,11 +484,15 @@ void or_hk_det(const double M[36], double gamma, double out[2])
 }
 
 /* ------------------------------------------------------------------ */
-/* Initial orbital psi0: sigma_g combination of normalised-overall       */
-/* s-type Gaussians on both centres (Sec. II.A, GTO expansion):          */
-/*   psi0(r) = N sum_{c=1,2} sum_k coef_k exp(-a_k |r - R_c|^2).          */
-/* N from <psi0|psi0> = 1 with the Gaussian product overlap              */
-/*   int e^{-a|r-A|^2} e^{-b|r-B|^2} = (pi/(a+b))^{3/2} e^{-ab|A-B|^2/(a+b)}. */
+/* Initial orbital psi0 (Sec. II.A, GTO expansion), a sum of Gaussian    */
+/* primitives placed on the centres:                                     */
+/*   psi0(r) = N sum_{placed i} coef_i f_i(r - A_i) exp(-a_i |r - A_i|^2) */
+/* with f = 1 (s-type) or f(x) = s_i u_i.x (p-type).  Diatomic targets:  */
+/* every primitive k sits on both centres (the sigma_g combination); a    */
+/* sigma p-type one has u = n and s = +-1 on the centre at +-(R/2) n      */
+/* (gerade), a pi p-type one u = m (pi_direction) and s = 1 (ungerade,   */
+/* 1 pi_u).  Polyatomic targets: primitive k sits on centre pcentre[k]    */
+/* only; a p-type one has u = Rot pdir[k]/|pdir[k]| and s = 1.            */
 /* ------------------------------------------------------------------ */
 /* Direction m of a pi p-type primitive: the unit vector perpendicular   */
 /* to the axis n = (sin th cos ph, sin th sin ph, cos th) at azimuth chi  */
@@ -427,104 +511,127 @@ void or_pi_direction(const double nhat[3], double chi, double m[3])
     for (int a = 0; a < 3; ++a) m[a] = cos(chi) * th_hat[a] + sin(chi) * ph_hat[a];
 }
 
-/* Angular factor of primitive k on the centre with sign s (+1 at +(R/2) n): */
-/* s-type none (returns 0); p-type f(x) = sfac u.(x - A) with u, sfac     */
-/* (sigma: u = n, sfac = s; pi: u = m, sfac = 1).                          */
-static int p_factor(const or_target_in* T, int k, const double nhat[3], double s,
-                    double u[3], double* sfac)
+typedef struct {
+    int c;           /* centre index in the frame */
+    double a, coef;  /* exponent, coefficient */
+    int p;           /* 0 s-type, 1 p-type */
+    double u[3];     /* p-type direction (lab) */
+    double s;        /* p-type sign */
+} or_placed;
+
+static int place_primitives(const or_target_in* T, const or_frame* F, or_placed* out)
 {
-    if (T->pkind[k] == 1) {
-        for (int a = 0; a < 3; ++a) u[a] = nhat[a];
-        *sfac = s;
-        return 1;
+    int m = 0;
+    if (T->kind == OR_POT_POLY) {
+        for (int k = 0; k < T->n_prim; ++k) {
+            or_placed P = {T->pcentre[k], T->pexp[k], T->pcoef[k], 0, {0.0, 0.0, 0.0}, 1.0};
+            if (T->pkind[k] == 3) {
+                double len = sqrt(T->pdir[k][0] * T->pdir[k][0] + T->pdir[k][1] * T->pdir[k][1] +
+                                  T->pdir[k][2] * T->pdir[k][2]);
+                P.p = 1;
+                for (int x = 0; x < 3; ++x) {
+                    P.u[x] = 0.0;
+                    for (int y = 0; y < 3; ++y) P.u[x] += F->Rot[3 * x + y] * T->pdir[k][y] / len;
+                }
+            }
+            out[m++] = P;
+        }
+        return m;
     }
-    if (T->pkind[k] == 2) {
-        or_pi_direction(nhat, T->pi_azimuth, u);
-        *sfac = 1.0;
-        return 1;
+    for (int c = 0; c < 2; ++c) {
+        double sign = (c == 0) ? 1.0 : -1.0;
+        for (int k = 0; k < T->n_prim; ++k) {
+            or_placed P = {c, T->pexp[k], T->pcoef[k], 0, {0.0, 0.0, 0.0}, 1.0};
+            if (T->pkind[k] == 1) {
+                P.p = 1;
+                for (int x = 0; x < 3; ++x) P.u[x] = F->nhat[x];
+                P.s = sign;
+            } else if (T->pkind[k] == 2) {
+                P.p = 1;
+                or_pi_direction(F->nhat, T->pi_azimuth, P.u);
+            }
+            out[m++] = P;
+        }
     }
-    return 0;
+    return m;
 }
 
-/* Normalisation of the orbital N sum_c sum_k coef_k phi_{c,k}, written in */
-/* the frame n = z (the norm does not depend on the orientation).  Two     */
+/* Normalisation: 1/sqrt(<psi|psi>) with the overlaps of placed          */
+/* primitives, in the frame of a reference orientation (n = z, or the     */
+/* identity rotation; the norm does not depend on the orientation).  Two  */
 /* Gaussians at A, B with exponents a, b multiply to S0 e^{-p|x-P|^2} with */
 /* p = a + b, P = (aA + bB)/p, S0 = e^{-ab/p |A-B|^2}; with y = x - P a    */
-/* p-type factor is u.y + u.(P - A), and int (u1.y + al1)(u2.y + al2)      */
+/* p-type factor is s (u.y + u.(P - A)), and int (u1.y + al1)(u2.y + al2)  */
 /* e^{-p y^2} = [al1 al2 + u1.u2/(2p)] (pi/p)^{3/2} (one factor: al (pi/p)^{3/2}). */
 static double orbital_norm(const or_target_in* T)
 {
-    const double nz[3] = {0.0, 0.0, 1.0};
+    const double ref[3] = {0.0, 0.0, T->kind == OR_POT_POLY ? 0.0 : 1.0};
+    or_frame F;
+    make_frame(T, ref, &F);
+    or_placed L[16];
+    int m = place_primitives(T, &F, L);
     double s = 0.0;
-    for (int c1 = 0; c1 < 2; ++c1)
-        for (int c2 = 0; c2 < 2; ++c2) {
-            double sA = (c1 == 0) ? 1.0 : -1.0, sB = (c2 == 0) ? 1.0 : -1.0;
-            double A[3], B[3];
-            for (int x = 0; x < 3; ++x) { A[x] = sA * 0.5 * T->R * nz[x]; B[x] = sB * 0.5 * T->R * nz[x]; }
-            for (int k1 = 0; k1 < T->n_prim; ++k1)
-                for (int k2 = 0; k2 < T->n_prim; ++k2) {
-                    double a = T->pexp[k1], b = T->pexp[k2], pp = a + b;
-                    double P[3], AB2 = 0.0;
-                    for (int x = 0; x < 3; ++x) {
-                        P[x] = (a * A[x] + b * B[x]) / pp;
-                        AB2 += (A[x] - B[x]) * (A[x] - B[x]);
-                    }
-                    double S0 = pow(OR_PI / pp, 1.5) * exp(-a * b / pp * AB2);
-                    double u1[3], u2[3], f1, f2;
-                    int p1 = p_factor(T, k1, nz, sA, u1, &f1);
-                    int p2 = p_factor(T, k2, nz, sB, u2, &f2);
-                    double al1 = 0.0, al2 = 0.0, uu = 0.0;
-                    for (int x = 0; x < 3; ++x) {
-                        if (p1) al1 += u1[x] * (P[x] - A[x]);
-                        if (p2) al2 += u2[x] * (P[x] - B[x]);
-                        if (p1 && p2) uu += u1[x] * u2[x];
-                    }
-                    double f;
-                    if (!p1 && !p2) f = 1.0;
-                    else if (!p1) f = f2 * al2;
-                    else if (!p2) f = f1 * al1;
-                    else f = f1 * f2 * (al1 * al2 + uu / (2.0 * pp));
-                    s += T->pcoef[k1] * T->pcoef[k2] * f * S0;
-                }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            const double* A = F.C[L[i].c];
+            const double* B = F.C[L[j].c];
+            double a = L[i].a, b = L[j].a, pp = a + b;
+            double P[3], AB2 = 0.0;
+            for (int x = 0; x < 3; ++x) {
+                P[x] = (a * A[x] + b * B[x]) / pp;
+                AB2 += (A[x] - B[x]) * (A[x] - B[x]);
+            }
+            double S0 = pow(OR_PI / pp, 1.5) * exp(-a * b / pp * AB2);
+            double al1 = 0.0, al2 = 0.0, uu = 0.0;
+            for (int x = 0; x < 3; ++x) {
+                al1 += L[i].u[x] * (P[x] - A[x]);
+                al2 += L[j].u[x] * (P[x] - B[x]);
+                uu += L[i].u[x] * L[j].u[x];
+            }
+            double f;
+            if (!L[i].p && !L[j].p) f = 1.0;
+            else if (!L[i].p) f = L[j].s * al2;
+            else if (!L[j].p) f = L[i].s * al1;
+            else f = L[i].s * L[j].s * (al1 * al2 + uu / (2.0 * pp));
+            s += L[i].coef * L[j].coef * f * S0;
         }
     return 1.0 / sqrt(s);
 }
 
 double or_orbital_norm(const or_target_in* T) { return orbital_norm(T); }
 
-static double orbital_value_n(const or_target_in* T, double N, const double nhat[3],
+static double orbital_value_n(const or_target_in* T, double N, const double orient[3],
                               const double r[3])
 {
+    or_frame F;
+    make_frame(T, orient, &F);
+    or_placed L[16];
+    int m = place_primitives(T, &F, L);
     double v = 0.0;
-    for (int c = 0; c < 2; ++c) {
-        double sign = (c == 0) ? 1.0 : -1.0, d2 = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            double d = r[a] - sign * 0.5 * T->R * nhat[a];
-            d2 += d * d;
+    for (int i = 0; i < m; ++i) {
+        const double* A = F.C[L[i].c];
+        double d2 = 0.0, ang = 1.0;
+        for (int a = 0; a < 3; ++a) d2 += (r[a] - A[a]) * (r[a] - A[a]);
+        if (L[i].p) {
+            ang = 0.0;
+            for (int a = 0; a < 3; ++a) ang += L[i].u[a] * (r[a] - A[a]);
+            ang *= L[i].s;
         }
-        for (int k = 0; k < T->n_prim; ++k) {
-            double u[3], sfac, ang = 1.0;
-            if (p_factor(T, k, nhat, sign, u, &sfac)) {
-                ang = 0.0;       /* sfac u.(r - A) */
-                for (int a = 0; a < 3; ++a) ang += u[a] * (r[a] - sign * 0.5 * T->R * nhat[a]);
-                ang *= sfac;
-            }
-            v += T->pcoef[k] * ang * exp(-T->pexp[k] * d2);
-        }
+        v += L[i].coef * ang * exp(-L[i].a * d2);
     }
     return N * v;
 }
 
-double or_orbital_value(const or_target_in* T, const double nhat[3], const double r[3])
+double or_orbital_value(const or_target_in* T, const double orient[3], const double r[3])
 {
-    return orbital_value_n(T, orbital_norm(T), nhat, r);
+    return orbital_value_n(T, orbital_norm(T), orient, r);
 }
 
-void or_orbital_values(const or_target_in* T, const double nhat[3], const double* r, int64_t n,
+void or_orbital_values(const or_target_in* T, const double orient[3], const double* r, int64_t n,
                        double* out)
 {
     double N = orbital_norm(T);
-    for (int64_t i = 0; i < n; ++i) out[i] = orbital_value_n(T, N, nhat, r + 3 * i);
+    for (int64_t i = 0; i < n; ++i) out[i] = orbital_value_n(T, N, orient, r + 3 * i);
 }
 
 /* ------------------------------------------------------------------ */
@@ -538,49 +645,50 @@ void or_orbital_values(const or_target_in* T, const double nhat[3], const double
 /* so I0 = (pi/c)^{3/2} e^{c m.m - b d.d - i p.d} and                    */
 /* int (z - q_z) (...) = (m_z - d_z) I0.                                 */
 /* ------------------------------------------------------------------ */
-static cplx recomb(const or_target_in* T, double N, const double nhat[3],
+static cplx recomb(const or_target_in* T, double N, const double orient[3],
                    const double q[3], const double p[3], double gamma)
 {
+    or_frame F;
+    make_frame(T, orient, &F);
+    or_placed L[16];
+    int np = place_primitives(T, &F, L);
     double b = 0.5 * gamma;
     cplx total = 0.0;
-    for (int ctr = 0; ctr < 2; ++ctr) {
-        double sign = (ctr == 0) ? 1.0 : -1.0;
+    for (int i = 0; i < np; ++i) {
         double d[3];
-        for (int a = 0; a < 3; ++a) d[a] = q[a] - sign * 0.5 * T->R * nhat[a];
-        for (int k = 0; k < T->n_prim; ++k) {
-            double a = T->pexp[k];
-            double c = a + b;
-            cplx m[3], mm = 0.0;
-            double dd = 0.0, pd = 0.0;
-            for (int i = 0; i < 3; ++i) {
-                m[i] = (2.0 * b * d[i] + I * p[i]) / (2.0 * c);
-                mm += m[i] * m[i];
-                dd += d[i] * d[i];
-                pd += p[i] * d[i];
-            }
-            cplx I0 = pow(OR_PI / c, 1.5) * cexp(c * mm - b * dd - I * pd);
-            cplx I1 = (m[2] - d[2]) * I0;
-            double u[3], sfac;
-            if (p_factor(T, k, nhat, sign, u, &sfac)) {
-                /* p-type: extra factor sfac u.x' (x' = x - A):            */
-                /* int u.x' e = (u.m) I0, int u.x' (x'_z - d_z) e =        */
-                /* [(u.m)(m_z - d_z) + u_z/(2c)] I0                         */
-                cplx um = u[0] * m[0] + u[1] * m[1] + u[2] * m[2];
-                cplx J0 = um * I0;
-                cplx J1 = (um * (m[2] - d[2]) + u[2] / (2.0 * c)) * I0;
-                total += sfac * T->pcoef[k] * (p[2] * J0 + I * gamma * J1);
-            } else {
-                total += T->pcoef[k] * (p[2] * I0 + I * gamma * I1);
-            }
+        for (int a = 0; a < 3; ++a) d[a] = q[a] - F.C[L[i].c][a];
+        double a = L[i].a;
+        double c = a + b;
+        cplx m[3], mm = 0.0;
+        double dd = 0.0, pd = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            m[x] = (2.0 * b * d[x] + I * p[x]) / (2.0 * c);
+            mm += m[x] * m[x];
+            dd += d[x] * d[x];
+            pd += p[x] * d[x];
+        }
+        cplx I0 = pow(OR_PI / c, 1.5) * cexp(c * mm - b * dd - I * pd);
+        cplx I1 = (m[2] - d[2]) * I0;
+        if (L[i].p) {
+            /* p-type: extra factor s u.x' (x' = x - A):                */
+            /* int u.x' e = (u.m) I0, int u.x' (x'_z - d_z) e =        */
+            /* [(u.m)(m_z - d_z) + u_z/(2c)] I0                         */
+            const double* u = L[i].u;
+            cplx um = u[0] * m[0] + u[1] * m[1] + u[2] * m[2];
+            cplx J0 = um * I0;
+            cplx J1 = (um * (m[2] - d[2]) + u[2] / (2.0 * c)) * I0;
+            total += L[i].s * L[i].coef * (p[2] * J0 + I * gamma * J1);
+        } else {
+            total += L[i].coef * (p[2] * I0 + I * gamma * I1);
         }
     }
     return N * pow(gamma / OR_PI, 0.75) * total;
 }
 
-void or_recomb(const or_target_in* T, const double nhat[3], const double q[3],
+void or_recomb(const or_target_in* T, const double orient[3], const double q[3],
                const double p[3], double gamma, double out[2])
 {
-    cplx r = recomb(T, orbital_norm(T), nhat, q, p, gamma);
+    cplx r = recomb(T, orbital_norm(T), orient, q, p, gamma);
     out[0] = creal(r); out[1] = cimag(r);
 }
 
@@ -591,44 +699,45 @@ void or_recomb(const or_target_in* T, const double nhat[3], const double q[3],
 /*   int e^{-i kappa.r} e^{-a|r-A|^2} = (pi/a)^{3/2} e^{-i kappa.A - kappa.kappa/(4a)}, */
 /*   int e^{-i kappa.r} z e^{-a|r-A|^2} = (A_z - i kappa_z/(2a)) x (above). */
 /* ------------------------------------------------------------------ */
-/* only: -1 both centres; 0 the centre at +(R/2) n; 1 the one at -(R/2) n  */
-static void dipole_matrix_element(const or_target_in* T, double N, const double nhat[3],
+/* only: -1 every centre; else that centre alone (diatomic: 0 the centre  */
+/* at +(R/2) n, 1 the one at -(R/2) n)                                   */
+static void dipole_matrix_element(const or_target_in* T, double N, const double orient[3],
                                   const cplx kappa[3], int only, cplx* mz)
 {
+    or_frame F;
+    make_frame(T, orient, &F);
+    or_placed L[16];
+    int np = place_primitives(T, &F, L);
     cplx kk = kappa[0] * kappa[0] + kappa[1] * kappa[1] + kappa[2] * kappa[2];
     cplx tot = 0.0;
-    for (int ctr = 0; ctr < 2; ++ctr) {
-        if (only >= 0 && ctr != only) continue;
-        double sign = (ctr == 0) ? 1.0 : -1.0;
-        double A[3];
-        for (int a = 0; a < 3; ++a) A[a] = sign * 0.5 * T->R * nhat[a];
+    for (int i = 0; i < np; ++i) {
+        if (only >= 0 && L[i].c != only) continue;
+        const double* A = F.C[L[i].c];
         cplx kA = kappa[0] * A[0] + kappa[1] * A[1] + kappa[2] * A[2];
-        for (int k = 0; k < T->n_prim; ++k) {
-            double a = T->pexp[k];
-            cplx F = pow(OR_PI / a, 1.5) * cexp(-I * kA - kk / (4.0 * a));
-            double u[3], sfac;
-            if (p_factor(T, k, nhat, sign, u, &sfac)) {
-                /* p-type: int e^{-i k.x} (x_z + A_z)(u.x) e^{-a x^2} =        */
-                /* [u_z/(2a) - k_z (u.k)/(4a^2) - i A_z (u.k)/(2a)] G           */
-                cplx uk = u[0] * kappa[0] + u[1] * kappa[1] + u[2] * kappa[2];
-                tot += sfac * T->pcoef[k] *
-                       (u[2] / (2.0 * a) - kappa[2] * uk / (4.0 * a * a) -
-                        I * A[2] * uk / (2.0 * a)) * F;
-            } else {
-                tot += T->pcoef[k] * (A[2] - I * kappa[2] / (2.0 * a)) * F;
-            }
+        double a = L[i].a;
+        cplx G = pow(OR_PI / a, 1.5) * cexp(-I * kA - kk / (4.0 * a));
+        if (L[i].p) {
+            /* p-type: int e^{-i k.x} (x_z + A_z)(u.x) e^{-a x^2} =        */
+            /* [u_z/(2a) - k_z (u.k)/(4a^2) - i A_z (u.k)/(2a)] G           */
+            const double* u = L[i].u;
+            cplx uk = u[0] * kappa[0] + u[1] * kappa[1] + u[2] * kappa[2];
+            tot += L[i].s * L[i].coef *
+                   (u[2] / (2.0 * a) - kappa[2] * uk / (4.0 * a * a) -
+                    I * A[2] * uk / (2.0 * a)) * G;
+        } else {
+            tot += L[i].coef * (A[2] - I * kappa[2] / (2.0 * a)) * G;
         }
     }
     *mz = N * pow(2.0 * OR_PI, -1.5) * tot;
 }
 
-void or_dipole_matrix_element(const or_target_in* T, const double nhat[3],
+void or_dipole_matrix_element(const or_target_in* T, const double orient[3],
                               const double kre[3], const double kim[3], double out[2])
 {
     cplx kap[3];
     for (int a = 0; a < 3; ++a) kap[a] = kre[a] + I * kim[a];
     cplx m;
-    dipole_matrix_element(T, orbital_norm(T), nhat, kap, -1, &m);
+    dipole_matrix_element(T, orbital_norm(T), orient, kap, -1, &m);
     out[0] = creal(m); out[1] = cimag(m);
 }
 
@@ -866,7 +975,7 @@ typedef struct {
     const double *W, *cdf;
     double total, N;
     int align_kind, n_nodes, eta_force;
-    double theta, phi;
+    double theta, phi, psi;
     const double *qx, *qw;
 } or_proposal;
 
@@ -900,6 +1009,18 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
         ph = 2.0 * OR_PI * u[4];
     }
     double nhat[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+    /* polyatomic: the orientation is the Euler triple (phi, theta, psi),  */
+    /* psi uniform for the isotropic and cos^2 distributions (Eq. 6 over   */
+    /* all three Euler angles); n = Rot z is the same axis as above        */
+    double orient[3] = {nhat[0], nhat[1], nhat[2]};
+    if (T->kind == OR_POT_POLY) {
+        double ps = Q->psi;
+        if (Q->align_kind == OR_ALIGN_ISO || Q->align_kind == OR_ALIGN_COS2)
+            ps = 2.0 * OR_PI * u[5];
+        orient[0] = ph;
+        orient[1] = th;
+        orient[2] = ps;
+    }
     /* saddle, exit, action, amplitude.  SFHK2: the electron leaves     */
     /* from one centre, eta = +1 (the centre at -(R/2) n) or -1 (the     */
     /* centre at +(R/2) n) with probability 1/2 each (weight x 2), the   */
@@ -928,7 +1049,7 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
         cplx Es = pulse_E(Pp, ts);
         cplx kap[3] = {kx, ky, kz + pulse_A(Pp, ts) - creal(pulse_A(Pp, t0))};
         cplx mz;
-        dipole_matrix_element(T, Q->N, nhat, kap, only, &mz);
+        dipole_matrix_element(T, Q->N, orient, kap, only, &mz);
         cplx curv = Es * kap[2] + cmod * pulse_Edot(Pp, ts);
         cplx a = side_w * Es * mz / csqrt(curv) * cexp(I * (Sd + kz * qz));
         double pdf = (Q->W[n0] / Q->total) / Pp->dt
@@ -939,7 +1060,7 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
         if (Q->align_kind == OR_ALIGN_QUAD) w *= Q->n_nodes * Q->qw[j % (uint64_t)Q->n_nodes];
     }
     double g[12] = {(double)n0, 0.0, 0.0, qz, kx, ky, kz,
-                    nhat[0], nhat[1], nhat[2], creal(w), cimag(w)};
+                    orient[0], orient[1], orient[2], creal(w), cimag(w)};
     for (int q = 0; q < 12; ++q) f[q] = g[q];
     *tt_out = tt;
     *Sd_out = Sd;
@@ -1000,14 +1121,18 @@ static void abs_sampling_constants(const or_proposal* Q, uint64_t seed, uint32_t
 }
 
 void or_abs_sampling_constants(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
-                               double theta, double phi, int n_nodes, uint64_t seed,
+                               double theta, double phi, double psi, int n_nodes, uint64_t seed,
                                uint32_t instance, double out[2]);
 
 int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
-              double theta, double phi, int n_nodes, int eta_force, uint64_t seed,
+              double theta, double phi, double psi, int n_nodes, int eta_force, uint64_t seed,
               uint32_t instance, uint64_t j_begin, uint64_t n, double* soa, double* aux)
 {
     double qx[OR_MAX_QUAD], qw[OR_MAX_QUAD];
+    /* polyatomic targets: no quadrature in cos theta (it relies on the    */
+    /* symmetry of a homonuclear diatomic) and no modified saddle          */
+    if (T->kind == OR_POT_POLY && (align_kind == OR_ALIGN_QUAD || T->ionization == 1))
+        return -1;
     if (align_kind == OR_ALIGN_QUAD) {
         if (n_nodes < 1 || n_nodes > OR_MAX_QUAD) return -1;
         or_quad_nodes(n_nodes, qx, qw);
@@ -1027,6 +1152,7 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
     Q.eta_force = eta_force;
     Q.theta = theta;
     Q.phi = phi;
+    Q.psi = psi;
     Q.qx = qx;
     Q.qw = qw;
     double MP[2] = {0.0, 0.0};
@@ -1073,7 +1199,7 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
 }
 
 void or_abs_sampling_constants(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
-                               double theta, double phi, int n_nodes, uint64_t seed,
+                               double theta, double phi, double psi, int n_nodes, uint64_t seed,
                                uint32_t instance, double out[2])
 {
     double qx[OR_MAX_QUAD], qw[OR_MAX_QUAD];
@@ -1093,6 +1219,7 @@ void or_abs_sampling_constants(const or_target_in* T, const or_pulse_in* Pin, in
     Q.eta_force = 0;
     Q.theta = theta;
     Q.phi = phi;
+    Q.psi = psi;
     Q.qx = qx;
     Q.qw = qw;
     abs_sampling_constants(&Q, seed, instance, out);

@@ -12,6 +12,12 @@ Targets (model potential of Eq. 7, two centres, softened):
     softening 0.1, R = 2.07, Ip = 0.573 a.u.
   * ``H2_table1`` / ``N2_table1``: the paper's Table I parameters with its
     Table II binding energies (15.40 eV, 15.54 eV), unsoftened.
+  * ``N2_sp`` / ``N2_pi``: N2 with sigma p-type primitives (HOMO 3 sigma_g)
+    and the HOMO-1 1 pi_u (pi p-type, Table II 17.18 eV).
+  * ``H2O`` / ``H2O_3a1``: polyatomic targets (the N-centre generalisation of
+    Eq. 7) with water's geometry, the HOMO 1b1 (an O 2p lobe perpendicular to
+    the molecular plane, 12.62 eV) and the HOMO-1 3a1 (O 2p along the C2 axis
+    plus H 1s, 14.74 eV).
 The initial orbital is a sigma_g pair of s-type Gaussian primitives per centre.
 The paper's fitted GTO coefficients are not printed, so these exponents and
 coefficients are synthetic, chosen for a 1s-like shape of roughly the right
@@ -53,6 +59,49 @@ def _target_sp(R, Zinf, Z0, alpha, soft_a, Ip, prims, pi_azimuth=0.0):
     return t
 
 
+POT_POLY = 2
+PRIM_P_DIR = 3
+
+
+def _poly(centres, Ip, prims, soft_a=0.1):
+    """Polyatomic target: centres = ((x, y, z, Z_inf, Z0, alpha), ...) in the
+    molecular frame (bohr); prims = ((centre, exponent, coefficient, p-direction
+    or None), ...), s-type when the direction is None."""
+    return dict(kind=POT_POLY, R=0.0, Zinf=0.0, Z0=0.0, alpha=0.0, soft_a=soft_a, Ip=Ip,
+                ho_omega=0.0, centres=[tuple(map(float, c)) for c in centres],
+                pexp=[p[1] for p in prims], pcoef=[p[2] for p in prims],
+                pkind=[0 if p[3] is None else PRIM_P_DIR for p in prims],
+                pcentre=[int(p[0]) for p in prims],
+                pdir=[(0.0, 0.0, 0.0) if p[3] is None else tuple(map(float, p[3]))
+                      for p in prims])
+
+
+# water: O at the origin, H at (+-1.4305, 0, 1.1075) bohr (r_OH = 1.809 bohr,
+# HOH = 104.5 deg), molecular plane xz, C2 axis z; Z_inf = 1/3 per centre
+# (total asymptotic charge 1), Z0 the nuclear charges, synthetic alpha
+_H2O_CENTRES = ((0.0, 0.0, 0.0, 1.0 / 3.0, 8.0, 2.0),
+                (1.4305, 0.0, 1.1075, 1.0 / 3.0, 1.0, 1.0),
+                (-1.4305, 0.0, 1.1075, 1.0 / 3.0, 1.0, 1.0))
+
+
+def diatomic_as_poly(t):
+    """A diatomic target written as a two-centre polyatomic one: centres at
+    (0, 0, +-R/2) with the diatomic's charges and every primitive on both;
+    a sigma p-type primitive becomes a p-type one along +-z (the sign of its
+    centre).  Sampled and propagated at the Euler angles (phi, theta, psi) it
+    must reproduce the diatomic at the axis n(theta, phi)."""
+    half = 0.5 * t["R"]
+    cen = [(0.0, 0.0, half, t["Zinf"], t["Z0"], t["alpha"]),
+           (0.0, 0.0, -half, t["Zinf"], t["Z0"], t["alpha"])]
+    kinds = t.get("pkind", [0] * len(t["pexp"]))
+    prims = []
+    for c, sgn in ((0, 1.0), (1, -1.0)):
+        for a, co, k in zip(t["pexp"], t["pcoef"], kinds):
+            assert k in (0, 1), "only s and sigma p-type primitives map to the polyatomic form"
+            prims.append((c, a, co, None if k == 0 else (0.0, 0.0, sgn)))
+    return _poly(cen, t["Ip"], prims, t["soft_a"])
+
+
 def pi_component(target, chi):
     """The same pi target with its lobe at azimuth chi (rad) about the axis;
     the two degenerate 1 pi_u components are chi = 0 and chi = pi/2."""
@@ -68,6 +117,13 @@ TARGETS = {
     "N2_table1": _target(2.07, 0.5, 7.0, 1.67, 0.0, 15.54 / EV, _N2_PRIMS),
     "N2_sp": _target_sp(2.07, 0.5, 7.0, 2.0, 0.1, 0.573, _N2_SP_PRIMS),
     "N2_pi": _target_sp(2.07, 0.5, 7.0, 2.0, 0.1, 17.18 / EV, _N2_PI_PRIMS),
+    # HOMO 1b1: O 2p perpendicular to the molecular plane (synthetic exponents)
+    "H2O": _poly(_H2O_CENTRES, 12.62 / EV,
+                 ((0, 1.60, 0.60, (0.0, 1.0, 0.0)), (0, 0.38, 0.50, (0.0, 1.0, 0.0)))),
+    # HOMO-1 3a1: O 2p along the C2 axis (toward the H side) plus H 1s in phase
+    "H2O_3a1": _poly(_H2O_CENTRES, 14.74 / EV,
+                     ((0, 1.60, 0.55, (0.0, 0.0, 1.0)), (0, 0.38, 0.45, (0.0, 0.0, 1.0)),
+                      (1, 1.20, 0.30, None), (2, 1.20, 0.30, None))),
 }
 
 
@@ -121,8 +177,13 @@ STAB_CUTOFF = 1.0e3
 ALIGN_FIXED, ALIGN_ISO, ALIGN_COS2, ALIGN_QUAD = 0, 1, 2, 3
 
 
-def fixed(theta_deg, phi_deg=0.0):
-    return (ALIGN_FIXED, math.radians(theta_deg), math.radians(phi_deg))
+def fixed(theta_deg, phi_deg=0.0, psi_deg=0.0):
+    """Fixed orientation: the axis at (theta, phi); a polyatomic molecule
+    also turned by psi about its own z axis (ZYZ Euler angles)."""
+    if psi_deg == 0.0:
+        return (ALIGN_FIXED, math.radians(theta_deg), math.radians(phi_deg))
+    return (ALIGN_FIXED, math.radians(theta_deg), math.radians(phi_deg), 0,
+            math.radians(psi_deg))
 
 
 def quadrature(n_nodes=10):
