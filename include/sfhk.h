@@ -56,7 +56,9 @@ extern "C" {
 #define SFHK_E_NOTFOUND  -7  /* unknown request id                          */
 #define SFHK_E_CANCELLED -8  /* the request was cancelled                   */
 
-#define SFHK_MAX_PRIM     8  /* s-type Gaussian primitives per centre       */
+#define SFHK_MAX_PRIM     8  /* Gaussian primitives per centre (diatomic) or */
+                             /* in all (polyatomic)                          */
+#define SFHK_MAX_CENTRES  8  /* centres of a polyatomic target               */
 
 /* ---------------------------------------------------------------- handles */
 typedef struct sfhk_ctx sfhk_ctx;
@@ -66,7 +68,7 @@ typedef struct sfhk_ensemble sfhk_ensemble;
 typedef struct sfhk_server sfhk_server;
 
 /* ---------------------------------------------------------------- descriptors */
-enum { SFHK_POT_MOLECULE = 0, SFHK_POT_HARMONIC = 1 };
+enum { SFHK_POT_MOLECULE = 0, SFHK_POT_HARMONIC = 1, SFHK_POT_POLYATOMIC = 2 };
 enum { SFHK_ALIGN_FIXED = 0, SFHK_ALIGN_ISOTROPIC = 1, SFHK_ALIGN_COS2 = 2,
        SFHK_ALIGN_QUADRATURE = 3 };
 #define SFHK_MAX_QUAD_NODES 64
@@ -78,6 +80,18 @@ enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
  * sigma_g combination  N sum_centres sum_k prim_coef[k] exp(-prim_exp[k] |r-R_c|^2)
  * (normalised by the library).  kind = SFHK_POT_HARMONIC replaces V by the
  * test potential ho_omega^2 |r|^2 / 2 (closed-form checks).
+ * kind = SFHK_POT_POLYATOMIC is the N-centre generalisation of Eq. 7 (the
+ * potential summed over the centres): n_centres centres at the
+ * molecular-frame positions centre_pos (bohr), each with its own
+ * centre_Z_inf, centre_Z0, centre_alpha, the common softening soft_a, and
+ * the molecule turned by the ZYZ Euler angles (phi, theta, psi) of each
+ * trajectory, Rot = Rz(phi) Ry(theta) Rz(psi), lab position = Rot x (the
+ * molecular z axis goes to n(theta, phi), as for a diatomic).  The orbital
+ * is N sum_k prim_coef[k] f_k exp(-prim_exp[k] |r - R_{c_k}|^2) with each
+ * primitive on its own centre c_k = prim_centre[k]: f = 1 (SFHK_PRIM_S) or
+ * f = u.(r - R_c) (SFHK_PRIM_P_DIR) with u = Rot d/|d|, d = prim_dir[k]
+ * given in the molecular frame.  R, Z_inf, Z0, alpha, the sigma/pi kinds
+ * and pi_azimuth are not used; ionization must be SFHK_IONIZE_SFA.
  * ionization selects the ionization step of the sampler: SFHK_IONIZE_SFA is
  * the saddle point of Eq. 2 (SFHK1); SFHK_IONIZE_MODIFIED is SFHK2
  * (Sec. III.D): each trajectory leaves from one centre, eta = +1 (the centre
@@ -110,7 +124,7 @@ enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
  * Errors: SFHK_E_INVAL for any other kind, a non-finite pi_azimuth, or an
  * orbital of zero norm. */
 enum { SFHK_IONIZE_SFA = 0, SFHK_IONIZE_MODIFIED = 1 };
-enum { SFHK_PRIM_S = 0, SFHK_PRIM_P_SIGMA = 1, SFHK_PRIM_P_PI = 2 };
+enum { SFHK_PRIM_S = 0, SFHK_PRIM_P_SIGMA = 1, SFHK_PRIM_P_PI = 2, SFHK_PRIM_P_DIR = 3 };
 enum { SFHK_SAMPLE_PROPOSAL = 0, SFHK_SAMPLE_ABS_AMPLITUDE = 1 };
 typedef struct {
     int kind;
@@ -125,6 +139,13 @@ typedef struct {
     double sampling_factor;           /* kappa of the |a| sampler (<= 0: 5) */
     int prim_kind[SFHK_MAX_PRIM];     /* SFHK_PRIM_S, _P_SIGMA or _P_PI */
     double pi_azimuth;                /* chi of the SFHK_PRIM_P_PI lobe (rad) */
+    /* SFHK_POT_POLYATOMIC only */
+    int n_centres;                                /* 1..SFHK_MAX_CENTRES */
+    double centre_pos[SFHK_MAX_CENTRES][3];       /* molecular frame, bohr */
+    double centre_Z_inf[SFHK_MAX_CENTRES], centre_Z0[SFHK_MAX_CENTRES];
+    double centre_alpha[SFHK_MAX_CENTRES];        /* >= 0 */
+    int prim_centre[SFHK_MAX_PRIM];               /* 0..n_centres-1 */
+    double prim_dir[SFHK_MAX_PRIM][3];            /* SFHK_PRIM_P_DIR: nonzero */
 } sfhk_target_desc;
 
 /* Pulse (Sec. II.D / III.A): wavelength (nm), peak intensity (W/cm^2),
@@ -145,11 +166,16 @@ typedef struct {
  * cylindrical and inversion symmetry of a homonuclear diatomic in a linearly
  * polarised field the average over the axis is int_0^1 f(arccos x) dx), phi
  * uniform, and its weight is multiplied by K W_{j mod K} (weights summing to
- * 1), so that the ensemble dipole is sum_k W_k <v_z>_k. */
+ * 1), so that the ensemble dipole is sum_k W_k <v_z>_k.
+ * Polyatomic targets take the full orientation, the Euler angles
+ * (phi, theta, psi): FIXED uses psi below; ISOTROPIC and COS2 draw psi
+ * uniform in [0, 2 pi) (the Haar measure for ISOTROPIC); QUADRATURE is
+ * refused (SFHK_E_INVAL), as it rests on the diatomic's symmetry. */
 typedef struct {
     int kind;
     double theta, phi;                /* radians, FIXED only */
     int n_nodes;                      /* QUADRATURE only: 1..SFHK_MAX_QUAD_NODES */
+    double psi;                       /* radians, FIXED polyatomic only */
 } sfhk_align_desc;
 
 /* Propagation options.
@@ -255,7 +281,8 @@ SFHK_API int sfhk_sample_into(sfhk_ctx* ctx, sfhk_ensemble* e, const sfhk_align_
 /* Ensemble from caller-given initial points (tests, external samplers).
  * soa_host: 12 x n_traj doubles, field-major (soa[f * n_traj + j]):
  *   0 grid index n0 of t0 (integer valued, 0..Nt-1) | 1-3 q0 | 4-6 p0 |
- *   7-9 molecular axis n (unit) | 10-11 weight w (re, im).
+ *   7-9 molecular axis n (unit; for a polyatomic target the Euler angles
+ *   phi, theta, psi) | 10-11 weight w (re, im).
  * n_norm: N of the 1/N normalisation of the dipole (0 = n_traj).
  * Errors: SFHK_E_INVAL (n0 out of range, non-finite entries), SFHK_E_NOMEM. */
 SFHK_API int sfhk_load_ensemble(sfhk_ctx* ctx, const sfhk_target* target, const sfhk_pulse* pulse,
@@ -435,7 +462,8 @@ SFHK_API int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_s
 /* Stops the server thread after its current slice; unfinished requests are dropped. */
 SFHK_API int sfhk_server_destroy(sfhk_server* s);
 /* Queue a request; returns at once with its id.  Errors: SFHK_E_INVAL (bad
- * descriptor), SFHK_E_NOMEM (admission refused: the queue is full, or the
+ * descriptor, or a polyatomic target: the server runs diatomic targets
+ * only), SFHK_E_NOMEM (admission refused: the queue is full, or the
  * request alone needs more than the device-memory budget). */
 SFHK_API int sfhk_submit(sfhk_server* s, const sfhk_request* req, uint64_t* req_id);
 /* SFHK_E_BUSY while the request is queued or running; once it has ended,

@@ -88,6 +88,36 @@ double orbital_norm(const sfhk_target_desc& d)
 // c = a + b): K1 = -ab/c, K2 = -1/(4c), K3 = -a/c and
 // K4 = N coef (gamma/pi)^{3/4} (pi/c)^{3/2} a/c; a sigma p-type primitive
 // adds P1 = b/c, P2 = 1/(2c), P3 = gamma/(2a).
+// 1 / sqrt(<phi|phi>) of a polyatomic orbital phi = sum_k coef_k f_k(r - A_k)
+// e^{-a_k |r - A_k|^2} (molecular frame; f = 1, or u_k.(r - A_k) with u_k the
+// unit p direction).  A pair of primitives multiplies to S0 e^{-p |r - P|^2},
+// p = a + b, P = (a A + b B)/p, S0 = (pi/p)^{3/2} e^{-ab/p |A - B|^2} after
+// integration; with y = r - P a p factor is u.y + u.(P - A), whose odd part
+// integrates to zero and whose square part gives u_1.u_2 / (2p).
+double poly_norm(const sfhk_target_desc& d, const double (*udir)[3])
+{
+    double s = 0.0;
+    for (int i = 0; i < d.n_prim; ++i)
+        for (int j = 0; j < d.n_prim; ++j) {
+            const double* A = d.centre_pos[d.prim_centre[i]];
+            const double* B = d.centre_pos[d.prim_centre[j]];
+            const double a = d.prim_exp[i], b = d.prim_exp[j], pab = a + b;
+            double AB2 = 0.0, ai = 0.0, aj = 0.0, uu = 0.0;
+            for (int x = 0; x < 3; ++x) {
+                const double P = (a * A[x] + b * B[x]) / pab;
+                AB2 += (A[x] - B[x]) * (A[x] - B[x]);
+                ai += udir[i][x] * (P - A[x]);
+                aj += udir[j][x] * (P - B[x]);
+                uu += udir[i][x] * udir[j][x];
+            }
+            const bool pi = d.prim_kind[i] == SFHK_PRIM_P_DIR, pj = d.prim_kind[j] == SFHK_PRIM_P_DIR;
+            const double ang = (pi && pj) ? ai * aj + 0.5 * uu / pab : pi ? ai : pj ? aj : 1.0;
+            s += d.prim_coef[i] * d.prim_coef[j] * ang * std::pow(kPi / pab, 1.5) *
+                 std::exp(-a * b / pab * AB2);
+        }
+    return s > 0.0 ? 1.0 / std::sqrt(s) : INFINITY;
+}
+
 void fill_recomb(const DevTarget& T, double gamma, DevRecomb& R)
 {
     const double b = 0.5 * gamma;
@@ -110,7 +140,7 @@ void fill_recomb(const DevTarget& T, double gamma, DevRecomb& R)
             R.P1[k] = b / c;
             R.P2[k] = 0.5 / c;
             R.P3[k] = gamma / (2.0 * a);
-            if (T.pkind[k]) R.has_p |= T.pkind[k];    // bit 0 sigma, bit 1 pi
+            if (T.pkind[k] == 1 || T.pkind[k] == 2) R.has_p |= T.pkind[k];   // bit 0 sigma, bit 1 pi
         }
         R.K1f[k] = (float)R.K1[k];
         R.K2f[k] = (float)R.K2[k];
@@ -120,6 +150,24 @@ void fill_recomb(const DevTarget& T, double gamma, DevRecomb& R)
         R.P2f[k] = (float)R.P2[k];
         R.P3f[k] = (float)R.P3[k];
     }
+}
+
+// Table rows of the polyatomic kernel for a set of ensembles launched
+// together: 0 for diatomic targets, else the largest n_slots; SFHK_E_INVAL
+// when the set mixes the two.
+int poly_slots(sfhk_ensemble* const* ens, int n_ens, int* slots)
+{
+    int np = 0, mx = 0;
+    for (int i = 0; i < n_ens; ++i) {
+        const DevTarget& T = ens[i]->tgt->dev;
+        if (T.kind == SFHK_POT_POLYATOMIC) {
+            ++np;
+            mx = std::max(mx, std::max(1, T.n_slots));
+        }
+    }
+    if (np != 0 && np != n_ens) return SFHK_E_INVAL;
+    *slots = mx;
+    return SFHK_OK;
 }
 
 int set_device(int dev)
@@ -323,7 +371,9 @@ int sfhk_mem_used(const sfhk_ctx* c, size_t* bytes)
 int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out)
 {
     if (!c || !d || !out) return SFHK_E_INVAL;
-    if (d->kind != SFHK_POT_MOLECULE && d->kind != SFHK_POT_HARMONIC) return SFHK_E_INVAL;
+    if (d->kind != SFHK_POT_MOLECULE && d->kind != SFHK_POT_HARMONIC &&
+        d->kind != SFHK_POT_POLYATOMIC)
+        return SFHK_E_INVAL;
     if (d->n_prim < 1 || d->n_prim > SFHK_MAX_PRIM) return SFHK_E_INVAL;
     if (d->ionization != SFHK_IONIZE_SFA && d->ionization != SFHK_IONIZE_MODIFIED)
         return SFHK_E_INVAL;
@@ -332,10 +382,34 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
         return SFHK_E_INVAL;
     for (int k = 0; k < d->n_prim; ++k)
         if (!(d->prim_exp[k] > 0.0) || !std::isfinite(d->prim_coef[k]) ||
-            (d->prim_kind[k] != SFHK_PRIM_S && d->prim_kind[k] != SFHK_PRIM_P_SIGMA &&
-             d->prim_kind[k] != SFHK_PRIM_P_PI))
+            d->prim_kind[k] < SFHK_PRIM_S || d->prim_kind[k] > SFHK_PRIM_P_DIR)
             return SFHK_E_INVAL;
     if (!std::isfinite(d->pi_azimuth)) return SFHK_E_INVAL;
+    const bool poly = d->kind == SFHK_POT_POLYATOMIC;
+    // p-type along a given direction on polyatomic targets only; sigma and
+    // pi p-type on diatomic targets only
+    for (int k = 0; k < d->n_prim; ++k)
+        if (d->prim_kind[k] != SFHK_PRIM_S && (d->prim_kind[k] == SFHK_PRIM_P_DIR) != poly)
+            return SFHK_E_INVAL;
+    if (poly) {
+        if (d->n_centres < 1 || d->n_centres > SFHK_MAX_CENTRES) return SFHK_E_INVAL;
+        if (d->ionization != SFHK_IONIZE_SFA) return SFHK_E_INVAL;
+        for (int c = 0; c < d->n_centres; ++c) {
+            for (int a = 0; a < 3; ++a)
+                if (!std::isfinite(d->centre_pos[c][a])) return SFHK_E_INVAL;
+            if (!std::isfinite(d->centre_Z_inf[c]) || !std::isfinite(d->centre_Z0[c]) ||
+                !(d->centre_alpha[c] >= 0.0) || !std::isfinite(d->centre_alpha[c]))
+                return SFHK_E_INVAL;
+        }
+        for (int k = 0; k < d->n_prim; ++k) {
+            if (d->prim_centre[k] < 0 || d->prim_centre[k] >= d->n_centres) return SFHK_E_INVAL;
+            if (d->prim_kind[k] == SFHK_PRIM_P_DIR) {
+                const double* u = d->prim_dir[k];
+                const double l2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                if (!(l2 > 0.0) || !std::isfinite(l2)) return SFHK_E_INVAL;
+            }
+        }
+    }
     if (d->soft_a < 0.0 || d->R < 0.0 || d->alpha < 0.0 || !std::isfinite(d->Ip)) return SFHK_E_INVAL;
     if (d->kind == SFHK_POT_MOLECULE && d->soft_a == 0.0 && d->Z_inf == 0.0 && d->Z0 == 0.0)
         ;  // a field-free "molecule" is allowed
@@ -365,7 +439,30 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
         T.pkind[k] = t->desc.prim_kind[k];
     }
     T.pi_azimuth = d->pi_azimuth;
-    T.norm = orbital_norm(t->desc);
+    if (poly) {
+        T.n_centres = d->n_centres;
+        bool any_p = false;
+        for (int c = 0; c < d->n_centres; ++c) {
+            for (int a = 0; a < 3; ++a) T.cpos[c][a] = d->centre_pos[c][a];
+            T.cZinf[c] = d->centre_Z_inf[c];
+            T.cdZ[c] = d->centre_Z0[c] - d->centre_Z_inf[c];
+            T.calpha[c] = d->centre_alpha[c];
+            T.cZinf_f[c] = (float)T.cZinf[c];
+            T.cdZ_f[c] = (float)T.cdZ[c];
+            T.calpha_f[c] = (float)T.calpha[c];
+        }
+        for (int k = 0; k < d->n_prim; ++k) {
+            T.pcentre[k] = d->prim_centre[k];
+            if (d->prim_kind[k] == SFHK_PRIM_P_DIR) {
+                const double* u = d->prim_dir[k];
+                const double l = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                for (int a = 0; a < 3; ++a) T.pdir[k][a] = u[a] / l;
+                any_p = true;
+            }
+        }
+        T.n_slots = T.n_centres + (any_p ? d->n_prim : 0);
+    }
+    T.norm = poly ? poly_norm(t->desc, T.pdir) : orbital_norm(t->desc);
     if (!std::isfinite(T.norm)) {
         delete t;
         return SFHK_E_INVAL;
@@ -584,9 +681,11 @@ int sfhk_propagate(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, void* 
     int bt, var, bps;
     shape(c, *o, &bt, &var, &bps);
     SFHK_CUDA_TRY(record_event(e->ev_start, s));
+    int slots = 0;
+    poly_slots(&e, 1, &slots);
     rc = launch_propagate(o->precision, var, (const DevInstance*)e->inst.p,
                           (const WorkItem*)e->items.p, e->n_items, (unsigned int*)e->qctr.p, bt,
-                          bps, c->sm_count, s);
+                          bps, c->sm_count, s, slots);
     if (rc) return rc;
     SFHK_CUDA_TRY(record_event(e->ev_stop, s));
     SFHK_CUDA_TRY(record_event(e->ev_done, s));
@@ -602,6 +701,8 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
         if (!ens[i] || ens[i]->ctx != c) return SFHK_E_INVAL;
     int rc = check_opts(o);
     if (rc) return rc;
+    int slots = 0;
+    if ((rc = poly_slots(ens, n_ens, &slots))) return rc;
     if ((rc = set_device(c->device))) return rc;
     cudaStream_t s = as_stream(stream);
     long long total_items = 0;
@@ -664,7 +765,7 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
         if (record_event(ens[i]->ev_start, s) != cudaSuccess) rc = SFHK_E_CUDA;
     if (!rc)
         rc = launch_propagate(o->precision, var, d_inst, d_sorted, (int)total_items, d_ctr, bt,
-                              bps, c->sm_count, s);
+                              bps, c->sm_count, s, slots);
     for (int i = 0; i < n_ens && !rc; ++i) {
         if (record_event(ens[i]->ev_stop, s) != cudaSuccess ||
             record_event(ens[i]->ev_done, s) != cudaSuccess)
@@ -688,6 +789,7 @@ struct sfhk_batch {
     unsigned int* d_ctr = nullptr;
     long long total_items = 0;
     int max_nt = 1;
+    int poly_slots = 0;
 };
 
 extern "C" {
@@ -700,10 +802,13 @@ int sfhk_batch_create(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens, const s
         if (!ens[i] || ens[i]->ctx != c) return SFHK_E_INVAL;
     int rc = check_opts(o);
     if (rc) return rc;
+    int slots = 0;
+    if ((rc = poly_slots(ens, n_ens, &slots))) return rc;
     if ((rc = set_device(c->device))) return rc;
     sfhk_batch* b = new (std::nothrow) sfhk_batch;
     if (!b) return SFHK_E_NOMEM;
     b->ctx = c;
+    b->poly_slots = slots;
     b->ens.assign(ens, ens + n_ens);
     b->opts = *o;
     b->opts.dump_final = 0;
@@ -783,7 +888,7 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
     // the kernel is timed with the ensembles' events (also inside a captured graph)
     for (sfhk_ensemble* e : b->ens) SFHK_CUDA_TRY(record_event(e->ev_start, s));
     rc = launch_propagate(b->opts.precision, var, b->d_inst, b->d_sorted, (int)b->total_items,
-                          b->d_ctr, bt, bps, b->ctx->sm_count, s);
+                          b->d_ctr, bt, bps, b->ctx->sm_count, s, b->poly_slots);
     if (rc) return rc;
     for (sfhk_ensemble* e : b->ens) {
         SFHK_CUDA_TRY(record_event(e->ev_stop, s));
@@ -816,6 +921,8 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
     if ((rc = prepare_outputs(e, oo, 0))) return rc;
     const DevInstance I = make_instance(e, oo);
     SFHK_CUDA_TRY(cudaMemcpy(e->inst.p, &I, sizeof I, cudaMemcpyHostToDevice));
+    int slots = 0;
+    poly_slots(&e, 1, &slots);
     const int blocks[3] = {32, 64, 128};
     float best = 3.4e38f;
     int bb = c->tuned[o->precision][0], bv = c->tuned[o->precision][1];
@@ -826,7 +933,7 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
                 SFHK_CUDA_TRY(cudaEventRecord(e->ev_start, 0));
                 rc = launch_propagate(o->precision, v, (const DevInstance*)e->inst.p,
                                       (const WorkItem*)e->items.p, items,
-                                      (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0);
+                                      (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0, slots);
                 if (rc) return rc;
                 SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, 0));
                 SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_stop));

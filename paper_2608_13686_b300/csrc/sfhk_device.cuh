@@ -174,6 +174,23 @@ struct PotConst {
     int kind, screened;
 };
 
+// Rotation of a polyatomic molecule, molecular frame -> lab, from the ZYZ
+// Euler angles (phi, theta, psi): Rot = Rz(phi) Ry(theta) Rz(psi) multiplied
+// out, row-major, given the angles' cosines and sines.  Rot z = n(theta, phi).
+template <typename R>
+__device__ __forceinline__ void euler_rotation(R cph, R sph, R cth, R sth, R cps, R sps, R Rot[9])
+{
+    Rot[0] = cph * cth * cps - sph * sps;
+    Rot[1] = -cph * cth * sps - sph * cps;
+    Rot[2] = cph * sth;
+    Rot[3] = sph * cth * cps + cph * sps;
+    Rot[4] = -sph * cth * sps + cph * cps;
+    Rot[5] = sph * sth;
+    Rot[6] = -sth * cps;
+    Rot[7] = sth * sps;
+    Rot[8] = cth;
+}
+
 // Lobe direction of a pi p-type primitive: the unit vector perpendicular to
 // the axis n = (sin th cos ph, sin th sin ph, cos th) at azimuth chi about n,
 // m = cos(chi) theta_hat + sin(chi) phi_hat with theta_hat =
@@ -323,6 +340,71 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, const R e[2][3],
         H.xz = gd[0][0] * d[0][2] + gd[1][0] * d[1][2];
         H.yz = gd[0][1] * d[0][2] + gd[1][1] * d[1][2];
     }
+}
+
+// Polyatomic potential (Eq. 7 summed over the N centres of the target, each
+// with its own Z_inf, Z0 - Z_inf and alpha): V, F = -grad V and the Hessian
+// at the stage point ((q - c) + l) + o for every centre c.  The centres' lab
+// positions are this lane's rows of a per-warp shared-memory table,
+// tab[(3 c + a) * 32] (the row stride is the warp size, so the 32 lanes read
+// 32 consecutive words).  Per centre, with u = 1/s, s^2 = |d|^2 + a^2:
+//   vc = (Zinf + dZ e^{-alpha s}) u,  g1 = Zinf u^3 + dZ e^{-alpha s}(alpha u^2 + u^3),
+//   g2 = -u^2 [3 Zinf u^3 + dZ e^{-alpha s} u (alpha^2 + 3 alpha u + 3 u^2)],
+//   V = -sum vc,  F = -sum g1 d,  H = (sum g1) I + sum g2 d d^T.
+template <typename R, bool LO, bool OFS, typename Target>
+__device__ __forceinline__ void potential_poly(const Target& T, const R* tab, R a2,
+                                               const R q[3], const R l[3], R ox, R oy, R oz,
+                                               R& V, R& Fx, R& Fy, R& Fz, Sym3<R>& H)
+{
+    constexpr bool F32 = std::is_same<R, float>::value;
+    V = Fx = Fy = Fz = R(0);
+    R gs = R(0), hxx = R(0), hyy = R(0), hzz = R(0), hxy = R(0), hxz = R(0), hyz = R(0);
+    const R o[3] = {ox, oy, oz};
+#pragma unroll 1
+    for (int c = 0; c < T.n_centres; ++c) {
+        R d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R cc = tab[(3 * c + a) * 32];
+            d[a] = LO ? (q[a] - cc) + l[a] : q[a] - cc;
+            if (OFS) d[a] += o[a];
+        }
+        const R Zinf = F32 ? R(T.cZinf_f[c]) : R(T.cZinf[c]);
+        const R dZ = F32 ? R(T.cdZ_f[c]) : R(T.cdZ[c]);
+        const R al = F32 ? R(T.calpha_f[c]) : R(T.calpha[c]);
+        const R s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + a2;
+        const R u = rsqrt_t<R>(s2);
+        const R u2 = u * u, u3 = u2 * u;
+        R vc, g1, g2;
+        if (dZ != R(0)) {
+            const R de = dZ * exp_t<R>(-al * (s2 * u));
+            vc = (Zinf + de) * u;
+            g1 = Zinf * u3 + de * (al * u2 + u3);
+            g2 = -u2 * (R(3) * Zinf * u3 + de * u * (al * al + R(3) * al * u + R(3) * u2));
+        } else {
+            vc = Zinf * u;
+            g1 = Zinf * u3;
+            g2 = R(-3) * Zinf * u3 * u2;
+        }
+        V -= vc;
+        Fx -= g1 * d[0];
+        Fy -= g1 * d[1];
+        Fz -= g1 * d[2];
+        gs += g1;
+        const R gx = g2 * d[0], gy = g2 * d[1], gz = g2 * d[2];
+        hxx += gx * d[0];
+        hyy += gy * d[1];
+        hzz += gz * d[2];
+        hxy += gx * d[1];
+        hxz += gx * d[2];
+        hyz += gy * d[2];
+    }
+    H.xx = hxx + gs;
+    H.yy = hyy + gs;
+    H.zz = hzz + gs;
+    H.xy = hxy;
+    H.xz = hxz;
+    H.yz = hyz;
 }
 
 }  // namespace sfhk

@@ -31,8 +31,16 @@ struct DevTarget {
     double half_R, Zinf, dZ, alpha, a2, Ip, w2;
     double norm;           // orbital normalisation N
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
-    int pkind[SFHK_MAX_PRIM];   // SFHK_PRIM_S / SFHK_PRIM_P_SIGMA / SFHK_PRIM_P_PI
+    int pkind[SFHK_MAX_PRIM];   // SFHK_PRIM_S / _P_SIGMA / _P_PI / _P_DIR
     double pi_azimuth;          // chi of the pi lobe about the axis
+    // polyatomic targets (kind SFHK_POT_POLYATOMIC)
+    int n_centres;
+    int n_slots;                // per-lane table rows: centres, then p directions
+    double cpos[SFHK_MAX_CENTRES][3];                 // molecular frame
+    double cZinf[SFHK_MAX_CENTRES], cdZ[SFHK_MAX_CENTRES], calpha[SFHK_MAX_CENTRES];
+    float cZinf_f[SFHK_MAX_CENTRES], cdZ_f[SFHK_MAX_CENTRES], calpha_f[SFHK_MAX_CENTRES];
+    int pcentre[SFHK_MAX_PRIM];
+    double pdir[SFHK_MAX_PRIM][3];                    // unit, molecular frame
 };
 
 struct DevRecomb {
@@ -159,9 +167,12 @@ int launch_sort_items(const WorkItem* in, int n_items, const int* inst_nt, WorkI
                       cudaStream_t s);
 // propagate (sfhk_propagate.cu)
 constexpr int kPropVariants = 6;   // register-cap variants of the integrator
+// poly_slots > 0: polyatomic instances, launched on the polyatomic kernel
+// with that many table rows per lane (the largest n_slots of the instances)
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
-                     int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s);
+                     int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,
+                     int poly_slots = 0);
 int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm);
 int propagate_variant_maxreg(int variant_index);   // 0 = no cap
 // server slice: items ring[(base + i) & mask], i < n_items; warps stop pulling

@@ -256,38 +256,53 @@ __device__ __forceinline__ void rk4sum3<float>(float a, const float u[3], const 
     z[2] = a * (u[2] + 2.0f * (v[2] + w[2]) + x[2]);
 }
 
+// The field at a stage point base + o: the two-centre potential from the
+// step's centre differences e, or (POLY) the N-centre potential from this
+// lane's column of the centre table.
+template <typename R, bool MIXED, bool POLY, bool OFS>
+__device__ __forceinline__ void field_at(const PotConst<R>& K, const R e[2][3], const DevTarget* T,
+                                         const R* tab, const R q[3], const R ql[3], R ox, R oy,
+                                         R oz, R& V, R F[3], Sym3<R>& H)
+{
+    if constexpr (POLY)
+        potential_poly<R, MIXED, OFS>(*T, tab, K.a2, q, ql, ox, oy, oz, V, F[0], F[1], F[2], H);
+    else
+        potential<R, OFS>(K, e, ox, oy, oz, V, F[0], F[1], F[2], H);
+}
+
 // One RK4 step's stage evaluations from (q, p) (high part q, low part ql):
 // the four stage Hessians and the increments dq, dp, dS of the step.  Stage
 // points are formed as base + offset (see potential()).
-template <typename R, bool MIXED>
+template <typename R, bool MIXED, bool POLY = false>
 __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], const R ql[3],
                                            const R p[3], R E1, R E2, R E4, R h, R h2, R h6,
-                                           Sym3<R> H[4], R dq[3], R dp[3], R& dS)
+                                           Sym3<R> H[4], R dq[3], R dp[3], R& dS,
+                                           const DevTarget* T = nullptr, const R* tab = nullptr)
 {
     R V, F[3], e[2][3];
-    centre_diffs<R, MIXED>(K, q, ql, e);
+    if constexpr (!POLY) centre_diffs<R, MIXED>(K, q, ql, e);
     const R z0 = R(0);
-    potential<R, false>(K, e, z0, z0, z0, V, F[0], F[1], F[2], H[0]);
+    field_at<R, MIXED, POLY, false>(K, e, T, tab, q, ql, z0, z0, z0, V, F, H[0]);
     const R k1p[3] = {F[0], F[1], F[2] - E1};
     const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
     R o[3], p2[3];
     scale3(h2, p, o);
     axpy3(h2, k1p, p, p2);
-    potential<R>(K, e, o[0], o[1], o[2], V, F[0], F[1], F[2], H[1]);
+    field_at<R, MIXED, POLY, true>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[1]);
     const R k2p[3] = {F[0], F[1], F[2] - E2};
     const R k2s =
         R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - (q[2] + o[2]) * E2;
     R p3[3];
     scale3(h2, p2, o);
     axpy3(h2, k2p, p, p3);
-    potential<R>(K, e, o[0], o[1], o[2], V, F[0], F[1], F[2], H[2]);
+    field_at<R, MIXED, POLY, true>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[2]);
     const R k3p[3] = {F[0], F[1], F[2] - E2};
     const R k3s =
         R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - (q[2] + o[2]) * E2;
     R p4[3];
     scale3(h, p3, o);
     axpy3(h, k3p, p, p4);
-    potential<R>(K, e, o[0], o[1], o[2], V, F[0], F[1], F[2], H[3]);
+    field_at<R, MIXED, POLY, true>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[3]);
     const R k4s =
         R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - (q[2] + o[2]) * E4;
     dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
@@ -579,14 +594,64 @@ __device__ __forceinline__ C2<float> recomb_pair(const DevInstance& I, const Pot
     return Rk;
 }
 
+// <psi0|k_z|p,q> of a polyatomic target: every primitive on its own centre
+// (lab position from this lane's column of the table), term
+//   K4 e^{K1 |d|^2 + K2 |p|^2 + i K3 p.d} (p_z - i g d_z)               (s-type)
+//   K4 e^{...} [(P1 u.d + i P2 u.p)(p_z - i g d_z) + i P3 u_z]          (p-type, u)
+// with d = q - A_c; terms below e^skip of their peak are not evaluated.
+template <typename R>
+__device__ __forceinline__ C2<R> recomb_poly(const DevInstance& I, const R* tab, const R q[3],
+                                             const R p[3], R pp, R gam, int n_prim, R skip)
+{
+    constexpr bool F32 = std::is_same<R, float>::value;
+    const int nc = I.tgt.n_centres;
+    C2<R> Rk = {R(0), R(0)};
+#pragma unroll 1
+    for (int k = 0; k < n_prim; ++k) {
+        const int c = I.tgt.pcentre[k];
+        const R dx = q[0] - tab[(3 * c) * 32], dy = q[1] - tab[(3 * c + 1) * 32],
+                dz = q[2] - tab[(3 * c + 2) * 32];
+        const R dd = dx * dx + dy * dy + dz * dz;
+        const R K1 = F32 ? R(I.rec.K1f[k]) : R(I.rec.K1[k]);
+        const R K2 = F32 ? R(I.rec.K2f[k]) : R(I.rec.K2[k]);
+        const R ex = K1 * dd + K2 * pp;
+        if (!(ex > skip)) continue;
+        const R K3 = F32 ? R(I.rec.K3f[k]) : R(I.rec.K3[k]);
+        const R K4 = F32 ? R(I.rec.K4f[k]) : R(I.rec.K4[k]);
+        const R mag = K4 * exp_t<R>(ex);
+        const R pdd = p[0] * dx + p[1] * dy + p[2] * dz;
+        R sn, cs;
+        if constexpr (F32) __sincosf(K3 * pdd, &sn, &cs);
+        else sincos(K3 * pdd, &sn, &cs);
+        R ar = mag * p[2], ai = -mag * gam * dz;
+        if (I.rec.kind[k] == SFHK_PRIM_P_DIR) {
+            const int r = 3 * (nc + k);
+            const R ux = tab[r * 32], uy = tab[(r + 1) * 32], uz = tab[(r + 2) * 32];
+            const R P1 = F32 ? R(I.rec.P1f[k]) : R(I.rec.P1[k]);
+            const R P2 = F32 ? R(I.rec.P2f[k]) : R(I.rec.P2[k]);
+            const R P3 = F32 ? R(I.rec.P3f[k]) : R(I.rec.P3[k]);
+            const R u = P1 * (ux * dx + uy * dy + uz * dz);
+            const R v = P2 * (ux * p[0] + uy * p[1] + uz * p[2]);
+            ar = mag * (u * p[2] + v * gam * dz);
+            ai = mag * (-u * gam * dz + v * p[2] + P3 * uz);
+        }
+        Rk.x += ar * cs - ai * sn;
+        Rk.y += ar * sn + ai * cs;
+    }
+    return Rk;
+}
+
 // per-warp buffer of the chunk's contributions: 32 steps x 32 trajectories,
 // row stride 33
 constexpr int kRedStride = kWarp + 1;
 constexpr int kRedElems = kWarp * kRedStride;
 
-template <bool MIXED>
+// POLY: a polyatomic target; tab is this lane's column of the warp's table
+// of lab-frame centre positions and p directions (rows of 32 words).
+template <bool MIXED, bool POLY = false>
 __device__ __forceinline__ void process_item(const DevInstance& I, const WorkItem& W, int lane,
-                                             typename std::conditional<MIXED, float, double>::type* red)
+                                             typename std::conditional<MIXED, float, double>::type* red,
+                                             typename std::conditional<MIXED, float, double>::type* tab = nullptr)
 {
     using R = typename std::conditional<MIXED, float, double>::type;
 
@@ -619,6 +684,24 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     K.kind = I.tgt.kind;
     K.screened = I.tgt.screened;
     const int n_prim = I.tgt.n_prim;
+    if constexpr (POLY) {
+        // fields 7..9 are the Euler angles: the molecule's lab-frame centres
+        // and p directions, Rot x, into this lane's column of the table
+        K.cx = K.cy = K.cz = R(0);
+        K.kind = 0;
+        double sph, cph, sth, cth, sps, cps, Rot[9];
+        sincos(nh[0], &sph, &cph);
+        sincos(nh[1], &sth, &cth);
+        sincos(nh[2], &sps, &cps);
+        euler_rotation<double>(cph, sph, cth, sth, cps, sps, Rot);
+        const int nc = I.tgt.n_centres;
+        for (int r = 0; r < I.tgt.n_slots; ++r) {
+            const double* x = r < nc ? I.tgt.cpos[r] : I.tgt.pdir[r - nc];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                tab[(3 * r + a) * 32] = R(Rot[3 * a] * x[0] + Rot[3 * a + 1] * x[1] + Rot[3 * a + 2] * x[2]);
+        }
+    }
     const R gam = R(I.gamma), igam = R(I.inv_gamma);
     const R wR = R(wr), wI = R(wi);
     const R cut2 = R(I.cutoff2);            // |det| = |C|^2 threshold (0 = off)
@@ -705,7 +788,9 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     }
                 }
                 C2<R> Rk = {R(0), R(0)};
-                if constexpr (MIXED) {
+                if constexpr (POLY) {
+                    Rk = recomb_poly<R>(I, tab, q, p, pp, gam, n_prim, kSkip);
+                } else if constexpr (MIXED) {
                     Rk = recomb_pair(I, K, q, p, pp, gam, K1max, K2max, n_prim, j);
                 } else {
 #pragma unroll
@@ -786,7 +871,8 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             // ---- one RK4 step to t_{nn+1}
             if (live && status == 0 && nn < nt - 1) {
                 ++steps;
-                stage_eval<R, MIXED>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS);
+                stage_eval<R, MIXED, POLY>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS,
+                                           &I.tgt, tab);
                 if constexpr (MIXED) {
                     acc2x2(q[0], q[1], ql[0], ql[1], dq[0], dq[1]);
                     acc2x2(p[0], p[1], pl[0], pl[1], dp[0], dp[1]);
@@ -882,23 +968,28 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     }
 }
 
-// The persistent loop over the work-item queue.
-template <bool MIXED>
+// The persistent loop over the work-item queue.  POLY: after the blocks'
+// reduction buffers, every warp has a table of `slots` rows x 3 x 32 words.
+template <bool MIXED, bool POLY = false>
 __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ items, int n_items,
-                                          unsigned int* __restrict__ counter)
+                                          unsigned int* __restrict__ counter, int slots = 0)
 {
     using R = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* red = reinterpret_cast<R*>(smem_raw) + (threadIdx.x / kWarp) * kRedElems;
     const int lane = threadIdx.x & (kWarp - 1);
+    R* tab = nullptr;
+    if constexpr (POLY)
+        tab = reinterpret_cast<R*>(smem_raw) + (blockDim.x / kWarp) * kRedElems +
+              (threadIdx.x / kWarp) * (slots * 3 * kWarp) + lane;
     for (;;) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(counter, 1u);
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const WorkItem W = items[it];
-        process_item<MIXED>(insts[W.inst], W, lane, red);
+        process_item<MIXED, POLY>(insts[W.inst], W, lane, red, tab);
     }
 }
 
@@ -960,6 +1051,14 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
                 int n_items, unsigned int* __restrict__ counter)
 {
     run_queue<MIXED>(insts, items, n_items, counter);
+}
+// Polyatomic targets: one launch shape, no register cap.
+template <bool MIXED>
+__global__ void __launch_bounds__(128)
+    k_propagate_poly(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ items,
+                     int n_items, unsigned int* __restrict__ counter, int slots)
+{
+    run_queue<MIXED, true>(insts, items, n_items, counter, slots);
 }
 template <bool MIXED>
 __global__ void __launch_bounds__(128)
@@ -1059,12 +1158,50 @@ int propagate_occupancy(int precision, int variant_index, int block_threads, int
     return SFHK_OK;
 }
 
+namespace {
+
+// Polyatomic launch: the reduction buffers plus every warp's centre table.
+int launch_poly(int precision, const DevInstance* insts, const WorkItem* items, int n_items,
+                unsigned int* item_counter, int block_threads, int blocks_per_sm, int sm_count,
+                int slots, cudaStream_t s)
+{
+    if (slots < 1 || slots > SFHK_MAX_CENTRES + SFHK_MAX_PRIM) return SFHK_E_INVAL;
+    const bool mixed = precision == SFHK_MIXED;
+    const auto fn = mixed ? k_propagate_poly<true> : k_propagate_poly<false>;
+    const size_t elem = mixed ? sizeof(float) : sizeof(double);
+    const size_t smem = red_bytes(precision, block_threads) +
+                        size_t(block_threads / kWarp) * slots * 3 * kWarp * elem;
+    if (smem > 48 * 1024)
+        SFHK_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    int occ = 0;
+    SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_threads, smem));
+    if (occ < 1) occ = 1;
+    const int bps = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
+    const int warps_per_block = block_threads / kWarp;
+    int grid = sm_count * bps;
+    const int grid_cap = (n_items + warps_per_block - 1) / warps_per_block;
+    if (grid > grid_cap) grid = grid_cap;
+    if (grid < 1) grid = 1;
+    SFHK_CUDA_TRY(cudaMemsetAsync(item_counter, 0, sizeof(unsigned int), s));
+    count_launch();
+    fn<<<grid, block_threads, smem, s>>>(insts, items, n_items, item_counter, slots);
+    SFHK_CUDA_TRY(cudaGetLastError());
+    return SFHK_OK;
+}
+
+}  // namespace
+
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
-                     int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s)
+                     int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,
+                     int poly_slots)
 {
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
+    if (poly_slots > 0)
+        return launch_poly(precision, insts, items, n_items, item_counter, block_threads,
+                           blocks_per_sm, sm_count, poly_slots, s);
     int occ = 0;
     int rc = propagate_occupancy(precision, variant_index, block_threads, &occ);
     if (rc) return rc;

@@ -111,6 +111,13 @@ struct SampleParams {
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
     int pkind[SFHK_MAX_PRIM];
     double cchi, schi;                        // pi lobe azimuth (cos, sin)
+    // polyatomic targets: Euler-angle orientation, primitives on their own centres
+    int poly;
+    double psi;                               // third Euler angle (FIXED)
+    int n_centres;
+    double cpos[SFHK_MAX_CENTRES][3];         // molecular frame
+    int pcentre[SFHK_MAX_PRIM];
+    double pdir[SFHK_MAX_PRIM][3];            // unit, molecular frame (p-type)
 };
 
 // sinh x and cosh x - 1 from em = e^x - 1, without cancellation
@@ -171,6 +178,11 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
     sincos(th, &sth, &cth);
     sincos(phv, &sph, &cph);
     const double nx = sth * cph, ny = sth * sph, nz = cth;
+    // polyatomic: the third Euler angle, uniform for the isotropic and cos^2
+    // distributions (the Haar measure over all three angles for isotropic)
+    double psi = S.psi;
+    if (S.poly && (S.align_kind == SFHK_ALIGN_ISOTROPIC || S.align_kind == SFHK_ALIGN_COS2))
+        psi = 2.0 * kPi * u[5];
     // SFHK2: the emitting centre (eta = +1: the one at -(R/2) n, drawn with
     // probability 1/2, weight x 2) and the saddle's offset c = eta (R/2) n_z
     int only = -1;
@@ -335,7 +347,42 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
             const double2 kk = make_double2(kp2 + kapz.x * kapz.x - kapz.y * kapz.y,
                                             2.0 * kapz.x * kapz.y);
             double2 mz = make_double2(0.0, 0.0);
-            for (int c = 0; c < 2; ++c) {
+            if (S.poly) {
+                // each primitive on its own centre A = Rot x_c (lab), s-type
+                // (A_z - i kappa_z/(2a)) F or p-type along u = Rot d:
+                // [u_z/(2a) - kappa_z (u.kappa)/(4a^2) - i A_z (u.kappa)/(2a)] F
+                double sps, cps, Rot[9];
+                sincos(psi, &sps, &cps);
+                euler_rotation<double>(cph, sph, cth, sth, cps, sps, Rot);
+                for (int p = 0; p < S.n_prim; ++p) {
+                    const double* x = S.cpos[S.pcentre[p]];
+                    const double A[3] = {Rot[0] * x[0] + Rot[1] * x[1] + Rot[2] * x[2],
+                                         Rot[3] * x[0] + Rot[4] * x[1] + Rot[5] * x[2],
+                                         Rot[6] * x[0] + Rot[7] * x[1] + Rot[8] * x[2]};
+                    const double2 kA = make_double2(kx * A[0] + ky * A[1] + kapz.x * A[2],
+                                                    kapz.y * A[2]);
+                    const double a = S.pexp[p];
+                    const double2 ex = make_double2(kA.y - kk.x / (4.0 * a), -kA.x - kk.y / (4.0 * a));
+                    const double2 F = cscale(cexp_(ex), S.pcoef[p] * pow(kPi / a, 1.5));
+                    double2 f;
+                    if (S.pkind[p]) {
+                        const double* d = S.pdir[p];
+                        const double uu[3] = {Rot[0] * d[0] + Rot[1] * d[1] + Rot[2] * d[2],
+                                              Rot[3] * d[0] + Rot[4] * d[1] + Rot[5] * d[2],
+                                              Rot[6] * d[0] + Rot[7] * d[1] + Rot[8] * d[2]};
+                        const double2 uk = make_double2(uu[0] * kx + uu[1] * ky + uu[2] * kapz.x,
+                                                        uu[2] * kapz.y);
+                        const double2 ku = cmul(kapz, uk);
+                        const double i2a = 0.5 / a, i4a2 = i2a * i2a;
+                        f = make_double2(uu[2] * i2a - ku.x * i4a2 + A[2] * uk.y * i2a,
+                                         -ku.y * i4a2 - A[2] * uk.x * i2a);
+                    } else {
+                        f = make_double2(A[2] + kapz.y / (2.0 * a), -kapz.x / (2.0 * a));
+                    }
+                    mz = cadd(mz, cmul(F, f));
+                }
+            }
+            for (int c = 0; c < (S.poly ? 0 : 2); ++c) {
                 if (only >= 0 && c != only) continue;
                 const double sgn = c == 0 ? 1.0 : -1.0;
                 const double Ax = sgn * 0.5 * S.R * nx, Ay = sgn * 0.5 * S.R * ny,
@@ -409,9 +456,10 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
     f[4] = kx;
     f[5] = ky;
     f[6] = kz;
-    f[7] = nx;
-    f[8] = ny;
-    f[9] = nz;
+    // orientation: the axis, or the Euler angles of a polyatomic molecule
+    f[7] = S.poly ? phv : nx;
+    f[8] = S.poly ? th : ny;
+    f[9] = S.poly ? psi : nz;
     f[10] = w.x;
     f[11] = w.y;
     return ok;
@@ -711,6 +759,8 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
 {
     if (!align_valid(al)) return SFHK_E_INVAL;
     if (T.desc.sampling == SFHK_SAMPLE_ABS_AMPLITUDE && pilot == nullptr) return SFHK_E_INVAL;
+    const bool poly = T.desc.kind == SFHK_POT_POLYATOMIC;
+    if (poly && (al.kind == SFHK_ALIGN_QUADRATURE || !std::isfinite(al.psi))) return SFHK_E_INVAL;
     SampleParams S;
     S.n_nodes = al.kind == SFHK_ALIGN_QUADRATURE ? al.n_nodes : 1;
     for (int k = 0; k < SFHK_MAX_QUAD_NODES; ++k) S.qx[k] = S.qkw[k] = 0.0;
@@ -744,6 +794,15 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
     }
     S.cchi = std::cos(T.desc.pi_azimuth);
     S.schi = std::sin(T.desc.pi_azimuth);
+    S.poly = poly ? 1 : 0;
+    S.psi = al.psi;
+    S.n_centres = poly ? T.desc.n_centres : 0;
+    for (int c = 0; c < SFHK_MAX_CENTRES; ++c)
+        for (int a = 0; a < 3; ++a) S.cpos[c][a] = poly ? T.desc.centre_pos[c][a] : 0.0;
+    for (int k = 0; k < SFHK_MAX_PRIM; ++k) {
+        S.pcentre[k] = poly ? T.desc.prim_centre[k] : 0;
+        for (int a = 0; a < 3; ++a) S.pdir[k][a] = T.dev.pdir[k][a];
+    }
     if (S.sampling == SFHK_SAMPLE_ABS_AMPLITUDE) {
         // pilot: |w| of kPilot proposal draws, then M and P; then the
         // persistent rejection sampler over a trajectory counter

@@ -470,7 +470,7 @@ int sfhk_submit(sfhk_server* S, const sfhk_request* r, uint64_t* id)
     const int nt = pulse_nt(r->pulse);
     if (nt < 2 || nt > S->max_nt || r->n_traj == 0 || r->n_traj > 2147483647ull ||
         !(r->target.Ip > 0.0) || r->target.n_prim < 1 || r->target.n_prim > SFHK_MAX_PRIM ||
-        !sfhk::align_valid(r->align))
+        r->target.kind == SFHK_POT_POLYATOMIC || !sfhk::align_valid(r->align))
         return SFHK_E_INVAL;
     std::lock_guard<std::mutex> lk(S->mu);
     const size_t est = bytes_estimate(r->n_traj, nt);

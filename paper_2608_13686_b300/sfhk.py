@@ -19,10 +19,11 @@ SFHK_OK = 0
 SFHK_E_INVAL, SFHK_E_NOMEM, SFHK_E_CUDA = -1, -2, -3
 SFHK_E_TIMEOUT, SFHK_E_NUMERIC, SFHK_E_BUSY, SFHK_E_NOTFOUND = -4, -5, -6, -7
 SFHK_MAX_PRIM = 8
-SFHK_POT_MOLECULE, SFHK_POT_HARMONIC = 0, 1
+SFHK_MAX_CENTRES = 8
+SFHK_POT_MOLECULE, SFHK_POT_HARMONIC, SFHK_POT_POLYATOMIC = 0, 1, 2
 SFHK_ALIGN_FIXED, SFHK_ALIGN_ISOTROPIC, SFHK_ALIGN_COS2, SFHK_ALIGN_QUADRATURE = 0, 1, 2, 3
 SFHK_FP64, SFHK_MIXED = 0, 1
-SFHK_PRIM_S, SFHK_PRIM_P_SIGMA, SFHK_PRIM_P_PI = 0, 1, 2
+SFHK_PRIM_S, SFHK_PRIM_P_SIGMA, SFHK_PRIM_P_PI, SFHK_PRIM_P_DIR = 0, 1, 2, 3
 SOA_FIELDS = 12
 FINAL_FIELDS = 47
 
@@ -39,7 +40,13 @@ class sfhk_target_desc(C.Structure):
                 ("soft_a", C.c_double), ("Ip", C.c_double), ("ho_omega", C.c_double),
                 ("prim_exp", C.c_double * SFHK_MAX_PRIM), ("prim_coef", C.c_double * SFHK_MAX_PRIM),
                 ("ionization", C.c_int), ("sampling", C.c_int), ("sampling_factor", C.c_double),
-                ("prim_kind", C.c_int * SFHK_MAX_PRIM), ("pi_azimuth", C.c_double)]
+                ("prim_kind", C.c_int * SFHK_MAX_PRIM), ("pi_azimuth", C.c_double),
+                ("n_centres", C.c_int), ("centre_pos", (C.c_double * 3) * SFHK_MAX_CENTRES),
+                ("centre_Z_inf", C.c_double * SFHK_MAX_CENTRES),
+                ("centre_Z0", C.c_double * SFHK_MAX_CENTRES),
+                ("centre_alpha", C.c_double * SFHK_MAX_CENTRES),
+                ("prim_centre", C.c_int * SFHK_MAX_PRIM),
+                ("prim_dir", (C.c_double * 3) * SFHK_MAX_PRIM)]
 
 
 class sfhk_pulse_desc(C.Structure):
@@ -49,7 +56,7 @@ class sfhk_pulse_desc(C.Structure):
 
 class sfhk_align_desc(C.Structure):
     _fields_ = [("kind", C.c_int), ("theta", C.c_double), ("phi", C.c_double),
-                ("n_nodes", C.c_int)]
+                ("n_nodes", C.c_int), ("psi", C.c_double)]
 
 
 class sfhk_run_opts(C.Structure):
@@ -205,6 +212,17 @@ def target_desc(t: dict) -> sfhk_target_desc:
         d.prim_coef[i] = c
         d.prim_kind[i] = int(kinds[i]) if i < len(kinds) else SFHK_PRIM_S
     d.pi_azimuth = float(t.get("pi_azimuth", 0.0))
+    cen = t.get("centres", ())
+    d.n_centres = len(cen)
+    for i, c in enumerate(cen):          # (x, y, z, Z_inf, Z0, alpha)
+        for a in range(3):
+            d.centre_pos[i][a] = c[a]
+        d.centre_Z_inf[i], d.centre_Z0[i], d.centre_alpha[i] = c[3], c[4], c[5]
+    for i, c in enumerate(t.get("pcentre", ())):
+        d.prim_centre[i] = int(c)
+    for i, u in enumerate(t.get("pdir", ())):
+        for a in range(3):
+            d.prim_dir[i][a] = u[a]
     return d
 
 
@@ -214,8 +232,9 @@ def pulse_desc(p: dict) -> sfhk_pulse_desc:
 
 
 def align_desc(a) -> sfhk_align_desc:
-    """(kind, theta, phi[, n_nodes])"""
-    return sfhk_align_desc(int(a[0]), float(a[1]), float(a[2]), int(a[3]) if len(a) > 3 else 0)
+    """(kind, theta, phi[, n_nodes[, psi]])"""
+    return sfhk_align_desc(int(a[0]), float(a[1]), float(a[2]), int(a[3]) if len(a) > 3 else 0,
+                           float(a[4]) if len(a) > 4 else 0.0)
 
 
 def run_opts(precision=SFHK_FP64, gamma=0.5, cutoff=0.0, dump=False, block_threads=0,
