@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="h2-angles",
-                    choices=["h2-angles", "n2-cos2", "batched", "served", "orient-avg"])
+                    choices=["h2-angles", "n2-cos2", "h2o-iso", "batched", "served",
+                             "orient-avg"])
     ap.add_argument("--n-traj", type=int, default=0,
                     help="trajectories per ensemble (0 = the workload's own)")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
@@ -156,6 +157,13 @@ def workload_instances(name, n_traj=None):
         inst = [dict(target=cfg["target"], pulse=cfg["pulse"], align=cfg["align"], n_traj=n,
                      seed=cfg["seed"], instance=0)]
         return cfg["name"], {"workload": cfg["name"], "target": "N2", "n_traj": n}, inst
+    if name == "h2o-iso":
+        cfg = W.H2O_ISO
+        n = n_traj or cfg["n_traj"]
+        inst = [dict(target=cfg["target"], pulse=cfg["pulse"], align=cfg["align"], n_traj=n,
+                     seed=cfg["seed"], instance=0)]
+        return cfg["name"], {"workload": cfg["name"], "target": "H2O", "n_traj": n,
+                             "centres": len(W.TARGETS["H2O"]["centres"])}, inst
     if name == "batched":
         inst = W.batched_instances(256, seed=0)
         if n_traj:
@@ -349,7 +357,9 @@ def run_ours(args):
             "traffic": (costs.TRAFFIC.get((args.workload, tuned["kernel_variant"] if tuned
                                            else args.kernel_variant))
                         if args.n_traj in (0, 1_000_000) else None),
-            "kernel": "k_propagate<mixed>", "kernel_ms": prop_ms,
+            "kernel": ("k_propagate_poly<mixed>" if any(
+                W.TARGETS[nm].get("kind") == W.POT_POLY for nm in targets)
+                else "k_propagate<mixed>"), "kernel_ms": prop_ms,
             "flops_per_traj_step": {nm: costs.FLOPS_PER_STEP[nm] for nm in targets},
             "peak_basis": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (unit counts, max clock)"}
     if clk.get("sm_mhz"):

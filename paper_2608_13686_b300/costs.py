@@ -28,9 +28,23 @@ Newton step that refines rsqrt are not counted):
 
 Steps near a nucleus also evaluate the Gaussian overlaps, the phase and the
 per-step contribution; they are not counted, so the figure is a lower bound.
+
+Polyatomic targets (N centres, each with its own screened charge), same
+counting:
+
+  potential at one point, per centre: the 15 above plus the screening
+    term 15; accumulation 23: V 1, force 6, sum of g1 1, g2 d 3,
+    Hessian 12; then 3 for the diagonal                     30 N + 23 N + 3
+  stage points, two-float updates, stability matrix, prefactor
+    (as above)                                                      984
+  recombination test per primitive (d 3, |d|^2 5, exponent 3) 11 per
+    primitive, |p|^2 5                                        11 n_prim + 5
+  ---------------------------------------------------------------
+  H2O (3 centres, 2 primitives): 4 x 162 + 984 + 27              1659
+  H2O_3a1 (3 centres, 4 primitives): 4 x 162 + 984 + 49          1681
 """
 
-FLOPS_PER_STEP = {"H2": 1299, "N2": 1419}
+FLOPS_PER_STEP = {"H2": 1299, "N2": 1419, "H2O": 1659, "H2O_3a1": 1681}
 
 # FP32 FMA pipe of a B300: 148 SMs x 128 lanes x 2 flops x 2.032 GHz (max SM clock)
 SMS = 148

@@ -210,6 +210,12 @@ N2_COS2 = dict(name="N2 cos^2-aligned, 1e7 traj, 1200 nm 3 cyc 1.2e14, mixed",
                target="N2", pulse=PULSE_1200, align=COS2, n_traj=10_000_000, seed=0,
                gamma=GAMMA)
 
+# water 1b1 (three centres), isotropic over all three Euler angles, 1e6
+# trajectories, mixed precision
+H2O_ISO = dict(name="H2O 1b1 isotropic (Euler angles), 1e6 traj, 800 nm 3 cyc 1.5e14, mixed",
+               target="H2O", pulse=PULSE_800, align=ISO, n_traj=1_000_000, seed=0,
+               gamma=GAMMA)
+
 
 def batched_instances(n_instances=256, seed=0, n_min=1e4, n_max=1e6):
     """Uneven batch: H2/N2 50/50, N log-uniform in [n_min, n_max],
