@@ -1052,9 +1052,17 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
 {
     run_queue<MIXED>(insts, items, n_items, counter);
 }
-// Polyatomic targets: one launch shape, no register cap.
+// Polyatomic targets, with the same register-cap variants.
 template <bool MIXED>
 __global__ void __launch_bounds__(128)
+    k_propagate_poly_nocap(const DevInstance* __restrict__ insts,
+                           const WorkItem* __restrict__ items, int n_items,
+                           unsigned int* __restrict__ counter, int slots)
+{
+    run_queue<MIXED, true>(insts, items, n_items, counter, slots);
+}
+template <bool MIXED, int MAXREG>
+__global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
     k_propagate_poly(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ items,
                      int n_items, unsigned int* __restrict__ counter, int slots)
 {
@@ -1080,6 +1088,7 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
 }
 
 using KernelFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*);
+using PolyFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*, int);
 using SliceFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, unsigned int, int,
                          unsigned int*, unsigned long long, unsigned long long*);
 
@@ -1095,6 +1104,18 @@ KernelFn variant(int precision, int v)
     static const KernelFn fp64[kPropVariants] = {
         k_propagate_nocap<false>, k_propagate<false, 168>, k_propagate<false, 152>,
         k_propagate<false, 144>, k_propagate<false, 136>, k_propagate<false, 128>};
+    return precision == SFHK_MIXED ? mixed[v] : fp64[v];
+}
+
+PolyFn poly_variant(int precision, int v)
+{
+    static const PolyFn mixed[kPropVariants] = {
+        k_propagate_poly_nocap<true>, k_propagate_poly<true, 168>, k_propagate_poly<true, 152>,
+        k_propagate_poly<true, 144>, k_propagate_poly<true, 136>, k_propagate_poly<true, 128>};
+    static const PolyFn fp64[kPropVariants] = {
+        k_propagate_poly_nocap<false>, k_propagate_poly<false, 168>,
+        k_propagate_poly<false, 152>, k_propagate_poly<false, 144>,
+        k_propagate_poly<false, 136>, k_propagate_poly<false, 128>};
     return precision == SFHK_MIXED ? mixed[v] : fp64[v];
 }
 
@@ -1161,13 +1182,13 @@ int propagate_occupancy(int precision, int variant_index, int block_threads, int
 namespace {
 
 // Polyatomic launch: the reduction buffers plus every warp's centre table.
-int launch_poly(int precision, const DevInstance* insts, const WorkItem* items, int n_items,
-                unsigned int* item_counter, int block_threads, int blocks_per_sm, int sm_count,
-                int slots, cudaStream_t s)
+int launch_poly(int precision, int variant_index, const DevInstance* insts,
+                const WorkItem* items, int n_items, unsigned int* item_counter,
+                int block_threads, int blocks_per_sm, int sm_count, int slots, cudaStream_t s)
 {
     if (slots < 1 || slots > SFHK_MAX_CENTRES + SFHK_MAX_PRIM) return SFHK_E_INVAL;
     const bool mixed = precision == SFHK_MIXED;
-    const auto fn = mixed ? k_propagate_poly<true> : k_propagate_poly<false>;
+    const PolyFn fn = poly_variant(precision, variant_index);
     const size_t elem = mixed ? sizeof(float) : sizeof(double);
     const size_t smem = red_bytes(precision, block_threads) +
                         size_t(block_threads / kWarp) * slots * 3 * kWarp * elem;
@@ -1200,8 +1221,8 @@ int launch_propagate(int precision, int variant_index, const DevInstance* insts,
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
     if (poly_slots > 0)
-        return launch_poly(precision, insts, items, n_items, item_counter, block_threads,
-                           blocks_per_sm, sm_count, poly_slots, s);
+        return launch_poly(precision, variant_index, insts, items, n_items, item_counter,
+                           block_threads, blocks_per_sm, sm_count, poly_slots, s);
     int occ = 0;
     int rc = propagate_occupancy(precision, variant_index, block_threads, &occ);
     if (rc) return rc;
