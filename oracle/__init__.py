@@ -124,8 +124,10 @@ def lib():
         L.or_pulse_Edot_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
         L.or_sample.restype = C.c_int
         L.or_propagate.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
-                                   C.c_double, C.c_double, _dp, C.c_uint64, C.c_double, _dp, _dp,
-                                   C.c_int]
+                                   C.c_double, C.c_double, C.c_double, _dp, C.c_uint64,
+                                   C.c_double, _dp, _dp, C.c_int]
+        L.or_stab_taper_weight.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.or_stab_taper_weight.restype = C.c_double
         L.or_propagate.restype = C.c_int
         L.or_spectrum.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                                   _dp, _dp, _dp, _dp, _dp]
@@ -319,16 +321,22 @@ def quad_nodes(K):
 
 
 def propagate(t, p, soa, gamma, cutoff=0.0, n_norm=0.0, want_final=False, n_threads=0,
-              stab_cutoff=0.0):
+              stab_cutoff=0.0, stab_taper=0.0):
+    """stab_taper = r > 1: the stability filter tapers the contributions
+    smoothly between stab_cutoff and r stab_cutoff (hard cut when 0)."""
     soa = np.ascontiguousarray(soa, dtype=np.float64)
     n = soa.shape[1]
     nt = pulse_derived(p)["nt"]
     vz = np.zeros(nt)
     fin = np.zeros((NFINAL, n)) if want_final else None
     bad = lib().or_propagate(C.byref(target_in(t)), C.byref(pulse_in(p)), gamma, cutoff,
-                             float(stab_cutoff), _p(soa), n, float(n_norm), _p(vz),
-                             _p(fin) if fin is not None else None, n_threads)
+                             float(stab_cutoff), float(stab_taper), _p(soa), n, float(n_norm),
+                             _p(vz), _p(fin) if fin is not None else None, n_threads)
     return vz, fin, bad
+
+
+def stab_taper_weight(Mhat, m0, r):
+    return lib().or_stab_taper_weight(float(Mhat), float(m0), float(r))
 
 
 def spectrum(vz, dt, t_origin, tau_H, n_out):

@@ -1241,6 +1241,15 @@ void or_abs_sampling_constants(const or_target_in* T, const or_pulse_in* Pin, in
 /* the stability matrix exceeds stab_cutoff (stability filter: a chaotic */
 /* trajectory), the trajectory contributes nothing from that step on.    */
 /* The checks run in this order after each step: finiteness, |C|, |M|.   */
+/* Tapered stability filter (stab_taper = r > 1; a reading, the paper is  */
+/* silent): with Mhat_n the running maximum over steps k <= n of the     */
+/* largest |M_ij(t_k)|, m0 = stab_cutoff and m1 = r m0, the contribution  */
+/* at t_n is multiplied by g(Mhat_n) = 1 for Mhat <= m0,                   */
+/* (1 + cos(pi x))/2 with x = ln(Mhat/m0)/ln r for m0 < Mhat < m1, and the */
+/* trajectory stops (status 3) once Mhat >= m1.  The dipole is then a     */
+/* continuous function of M, so a rounding-level change of M changes it   */
+/* by a rounding-level amount (the hard filter, r = 0, can jump by a      */
+/* whole step's contribution).                                            */
 /* final_state (optional): per trajectory, field-major,                  */
 /*   q[3] p[3] M[36] S C_re C_im theta status  (47 fields)                */
 /* status: 0 ok, 1 prefactor-filtered, 2 non-finite, 3 stability-filtered.*/
@@ -1258,8 +1267,15 @@ typedef struct {
     double* returns;
 } or_return_opts;
 
+double or_stab_taper_weight(double Mhat, double m0, double r)
+{
+    if (Mhat <= m0) return 1.0;
+    if (Mhat >= r * m0) return 0.0;
+    return 0.5 * (1.0 + cos(OR_PI * log(Mhat / m0) / log(r)));
+}
+
 static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm,
-                          double gamma, double cutoff, double stab_cutoff,
+                          double gamma, double cutoff, double stab_cutoff, double stab_taper,
                           const double* soa, uint64_t n,
                           uint64_t j, double scale, double* vz, double* final_state,
                           const or_return_opts* ro)
@@ -1279,7 +1295,7 @@ static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm
     }
     for (int a = 0; a < 36; ++a) y[6 + a] = (a % 7 == 0) ? 1.0 : 0.0;
     y[42] = 0.0;
-    double theta = 0.0;
+    double theta = 0.0, Mhat = 0.0;
     cplx det_prev = 1.0;
     cplx C = 1.0;
     int status = 0;
@@ -1296,10 +1312,15 @@ static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm
         for (int a = 0; a < OR_NY; ++a) if (!isfinite(y[a])) finite = 0;
         if (!finite) { status = 2; break; }
         if (cutoff > 0.0 && cabs(C) > cutoff) { status = 1; break; }
+        double g = 1.0;
         if (stab_cutoff > 0.0) {
             double mmax = 0.0;
             for (int a = 0; a < 36; ++a) if (fabs(y[6 + a]) > mmax) mmax = fabs(y[6 + a]);
-            if (mmax > stab_cutoff) { status = 3; break; }
+            if (stab_taper > 1.0) {
+                if (mmax > Mhat) Mhat = mmax;
+                if (Mhat >= stab_taper * stab_cutoff) { status = 3; break; }
+                g = or_stab_taper_weight(Mhat, stab_cutoff, stab_taper);
+            } else if (mmax > stab_cutoff) { status = 3; break; }
         }
         if (ro && ro->returns && !returned) {
             double az = fabs(y[2]);
@@ -1312,7 +1333,7 @@ static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm
         }
         cplx R = recomb(T, Nnorm, nhat, y, y + 3, gamma);
         cplx X = w * C * cexp(I * (y[42] - T->Ip * t)) * R;
-        vz[m] += -2.0 * scale * creal(X);
+        vz[m] += -2.0 * scale * g * creal(X);
     }
     if (final_state) {
         for (int a = 0; a < 42; ++a) final_state[(size_t)a * n + j] = y[a];
@@ -1328,16 +1349,16 @@ static void propagate_one(const or_target_in* T, const or_pulse* P, double Nnorm
  * (0 -> n).  n_threads <= 0 uses all cores.  Returns the count of
  * trajectories that were filtered (either filter) or non-finite.        */
 static int propagate_all(const or_target_in* T, const or_pulse_in* Pin, double gamma,
-                         double cutoff, double stab_cutoff, const double* soa, uint64_t n,
-                         double n_norm, double* vz_out, double* final_state, int n_threads,
-                         const or_return_opts* ro);
+                         double cutoff, double stab_cutoff, double stab_taper, const double* soa,
+                         uint64_t n, double n_norm, double* vz_out, double* final_state,
+                         int n_threads, const or_return_opts* ro);
 
 int or_propagate(const or_target_in* T, const or_pulse_in* Pin, double gamma, double cutoff,
-                 double stab_cutoff, const double* soa, uint64_t n, double n_norm, double* vz_out,
-                 double* final_state, int n_threads)
+                 double stab_cutoff, double stab_taper, const double* soa, uint64_t n,
+                 double n_norm, double* vz_out, double* final_state, int n_threads)
 {
-    return propagate_all(T, Pin, gamma, cutoff, stab_cutoff, soa, n, n_norm, vz_out, final_state,
-                         n_threads, NULL);
+    return propagate_all(T, Pin, gamma, cutoff, stab_cutoff, stab_taper, soa, n, n_norm, vz_out,
+                         final_state, n_threads, NULL);
 }
 
 /* The same, also recording each trajectory's first return (returns: 2 x n). */
@@ -1347,14 +1368,14 @@ int or_propagate_returns(const or_target_in* T, const or_pulse_in* Pin, double g
                          double* returns, int n_threads)
 {
     or_return_opts ro = {r_out, r_in, returns};
-    return propagate_all(T, Pin, gamma, cutoff, stab_cutoff, soa, n, n_norm, vz_out, NULL,
+    return propagate_all(T, Pin, gamma, cutoff, stab_cutoff, 0.0, soa, n, n_norm, vz_out, NULL,
                          n_threads, &ro);
 }
 
 static int propagate_all(const or_target_in* T, const or_pulse_in* Pin, double gamma,
-                         double cutoff, double stab_cutoff, const double* soa, uint64_t n,
-                         double n_norm, double* vz_out, double* final_state, int n_threads,
-                         const or_return_opts* ro)
+                         double cutoff, double stab_cutoff, double stab_taper, const double* soa,
+                         uint64_t n, double n_norm, double* vz_out, double* final_state,
+                         int n_threads, const or_return_opts* ro)
 {
     or_pulse P = or_make_pulse(Pin);
     double Nnorm = orbital_norm(T);
@@ -1373,8 +1394,8 @@ static int propagate_all(const or_target_in* T, const or_pulse_in* Pin, double g
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        propagate_one(T, &P, Nnorm, gamma, cutoff, stab_cutoff, soa, n, (uint64_t)j, scale,
-                      part + (size_t)tid * P.nt, final_state, ro);
+        propagate_one(T, &P, Nnorm, gamma, cutoff, stab_cutoff, stab_taper, soa, n, (uint64_t)j,
+                      scale, part + (size_t)tid * P.nt, final_state, ro);
     }
     for (int t = 0; t < nthr; ++t)
         for (int m = 0; m < P.nt; ++m) vz_out[m] += part[(size_t)t * P.nt + m];
