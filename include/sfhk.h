@@ -214,6 +214,19 @@ typedef struct {
     double return_r_out, return_r_in; /* the return: first step with |q_z| <
                                          r_in after one with |q_z| > r_out
                                          (0 < r_in < r_out) */
+    double stability_taper;           /* 0: the stability filter is a hard cut.
+                                         r > 1: a taper (a reading, the paper
+                                         is silent): with Mhat the running
+                                         maximum of max |M_ij| over the steps so
+                                         far and m0 = stability_cutoff, each
+                                         contribution is weighted by 1 for
+                                         Mhat <= m0, (1 + cos(pi x))/2 with
+                                         x = ln(Mhat/m0)/ln r up to r m0, and
+                                         the trajectory stops once Mhat >= r m0.
+                                         The dipole is then continuous in M, so
+                                         FP32 rounding of M moves it by a
+                                         rounding-level amount instead of a
+                                         whole step's contribution. */
 } sfhk_run_opts;
 
 /* Per-ensemble counters of the last propagation. */
@@ -420,6 +433,7 @@ typedef struct {
                                    request whose work (items x Nt) is smaller than
                                    the work still queued goes to the front of the
                                    ring, so short requests overtake long ones      */
+    double stability_taper;     /* as in sfhk_run_opts                              */
 } sfhk_server_opts;
 
 typedef struct {

@@ -257,6 +257,10 @@ DevInstance make_instance(sfhk_ensemble* e, const sfhk_run_opts& o)
     I.inv_gamma = 1.0 / o.gamma;
     I.cutoff2 = o.prefactor_cutoff > 0.0 ? o.prefactor_cutoff * o.prefactor_cutoff : 0.0;
     I.stab_cut = o.stability_cutoff > 0.0 ? o.stability_cutoff : 0.0;
+    // tapered stability filter: stop at r m0, weight by the taper above m0
+    const bool taper = I.stab_cut > 0.0 && o.stability_taper > 1.0;
+    I.stab_hi = taper ? o.stability_taper * I.stab_cut : 0.0;
+    I.inv_log_taper = taper ? 1.0 / std::log(o.stability_taper) : 0.0;
     I.done_items = nullptr;
     I.cancel = nullptr;
     return I;
@@ -270,6 +274,9 @@ int check_opts(const sfhk_run_opts* o)
     if (o->precision != SFHK_FP64 && o->precision != SFHK_MIXED) return SFHK_E_INVAL;
     if (!(o->gamma > 0.0) || !std::isfinite(o->gamma)) return SFHK_E_INVAL;
     if (o->prefactor_cutoff < 0.0 || o->stability_cutoff < 0.0) return SFHK_E_INVAL;
+    if (!(o->stability_taper == 0.0 || o->stability_taper > 1.0) ||
+        !std::isfinite(o->stability_taper))
+        return SFHK_E_INVAL;
     if (o->block_threads < 0 || o->block_threads > 128 || o->block_threads % 32) return SFHK_E_INVAL;
     if (o->blocks_per_sm < 0) return SFHK_E_INVAL;
     if (o->kernel_variant < 0 || o->kernel_variant > kPropVariants) return SFHK_E_INVAL;

@@ -77,6 +77,8 @@ struct DevInstance {
     double gamma, inv_gamma;
     double cutoff2;        // cutoff^2 on |det| (0 = off), |C|^2 = |det|
     double stab_cut;       // cutoff on max |M_ij| (0 = off)
+    double stab_hi;        // tapered filter: stop at this running max (0 = hard cut)
+    double inv_log_taper;  // 1 / ln(stab_hi / stab_cut)
     unsigned int* done_items;   // server: work items of this instance finished (or null)
     const int* cancel;          // server: nonzero = skip the remaining items (or null)
 };

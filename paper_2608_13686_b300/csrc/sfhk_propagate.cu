@@ -441,7 +441,7 @@ template <typename R>
 __device__ __forceinline__ void prefactor_and_checks(const Mono<R>& M, R gam,
                                                      R igam, C2<R>& Cp, const R q[3],
                                                      const R p[3], R S, R cut2, R stab,
-                                                     int& status)
+                                                     R stab_hi, R& Mhat, int& status)
 {
     C2<R> B[9];
 #pragma unroll
@@ -472,7 +472,27 @@ __device__ __forceinline__ void prefactor_and_checks(const Mono<R>& M, R gam,
                      isfinite(p[1]) && isfinite(p[2]) && isfinite(S) && isfinite(rdet);
     if (!fin) status = 2;
     else if (cut2 > R(0) && rdet > cut2) status = 1;
-    else if (stab > R(0) && max_abs_M(M) > stab) status = 3;
+    else if (stab > R(0)) {
+        const R mm = max_abs_M(M);
+        if (stab_hi > R(0)) {
+            // tapered filter: running maximum, stop at the taper's end
+            Mhat = fmax(Mhat, mm);
+            if (Mhat >= stab_hi) status = 3;
+        } else if (mm > stab) {
+            status = 3;
+        }
+    }
+}
+
+// Weight of the tapered stability filter for a running maximum Mhat above
+// the cutoff m0: (1 + cos(pi ln(Mhat/m0) / ln r)) / 2.
+template <typename R>
+__device__ __forceinline__ R taper_weight(R Mhat, R m0, R inv_log_r)
+{
+    if constexpr (std::is_same<R, float>::value)
+        return 0.5f * (1.0f + __cosf(3.14159265f * __logf(Mhat / m0) * inv_log_r));
+    else
+        return 0.5 * (1.0 + cos(3.141592653589793 * log(Mhat / m0) * inv_log_r));
 }
 
 // <psi0|k_z|p,q> summed over both centres and the primitives, FP32, with the
@@ -706,6 +726,8 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     const R wR = R(wr), wI = R(wi);
     const R cut2 = R(I.cutoff2);            // |det| = |C|^2 threshold (0 = off)
     const R stab = R(I.stab_cut);
+    const R stab_hi = R(I.stab_hi);           // tapered filter (0 = hard cut)
+    R Mhat = R(0);                            // running max of max |M_ij| (tapered filter)
     // far-field bound of the recombination exponent over the primitives:
     // K1 |d|^2 + K2 |p|^2 <= K1max |d|^2 + K2max |p|^2 (all K1, K2 < 0)
     R K1max = R(-1e30), K2max = R(-1e30);
@@ -773,7 +795,8 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             const C2<R> ph = {shfl(phl.x, s), shfl(phl.y, s)};
             const bool live = (nn >= n0) && status == 0;
             // ---- prefactor at t_nn (C = 1 at birth) and the checks
-            if (live) prefactor_and_checks(M, gam, igam, Cp, q, p, S, cut2, stab, status);
+            if (live)
+                prefactor_and_checks(M, gam, igam, Cp, q, p, S, cut2, stab, stab_hi, Mhat, status);
             // ---- contribution at t_nn: Re[w C e^{iS} e^{-i Ip t} <psi0|k_z|p,q>]
             R x = R(0);
             if (live && status == 0) {
@@ -863,6 +886,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     const C2<R> a = cm(cm(C2<R>{wR, wI}, Cp), eS);
                     const C2<R> b = cm(a, ph);
                     x = b.x * Rk.x - b.y * Rk.y;
+                    if (Mhat > stab) x *= taper_weight<R>(Mhat, stab, R(I.inv_log_taper));
                 }
             }
             // ---- this step's contribution, summed over the warp after the chunk

@@ -391,6 +391,9 @@ int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** o
 {
     if (!opts || !out) return SFHK_E_INVAL;
     if (opts->precision != SFHK_FP64 && opts->precision != SFHK_MIXED) return SFHK_E_INVAL;
+    if (!(opts->stability_taper == 0.0 || opts->stability_taper > 1.0) ||
+        !std::isfinite(opts->stability_taper))
+        return SFHK_E_INVAL;
     if (!(opts->gamma > 0.0) || opts->prefactor_cutoff < 0.0 || opts->stability_cutoff < 0.0 ||
         opts->slice_ms < 0.0 || opts->max_pending < 0 || opts->max_active < 0)
         return SFHK_E_INVAL;
@@ -406,6 +409,7 @@ int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** o
     S->ro.gamma = opts->gamma;
     S->ro.prefactor_cutoff = opts->prefactor_cutoff;
     S->ro.stability_cutoff = opts->stability_cutoff;
+    S->ro.stability_taper = opts->stability_taper;
     int rc = sfhk_create(&S->ctx, device, 0);
     if (rc) {
         delete S;

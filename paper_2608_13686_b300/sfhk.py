@@ -64,7 +64,7 @@ class sfhk_run_opts(C.Structure):
                 ("dump_final", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
                 ("stability_cutoff", C.c_double), ("kernel_variant", C.c_int),
                 ("record_returns", C.c_int), ("return_r_out", C.c_double),
-                ("return_r_in", C.c_double)]
+                ("return_r_in", C.c_double), ("stability_taper", C.c_double)]
 
 
 class sfhk_stats(C.Structure):
@@ -78,7 +78,8 @@ class sfhk_server_opts(C.Structure):
     _fields_ = [("device_mem_budget", C.c_size_t), ("max_pending", C.c_int),
                 ("max_active", C.c_int), ("precision", C.c_int), ("gamma", C.c_double),
                 ("prefactor_cutoff", C.c_double), ("stability_cutoff", C.c_double),
-                ("slice_ms", C.c_double), ("spectrum", C.c_int), ("fifo", C.c_int)]
+                ("slice_ms", C.c_double), ("spectrum", C.c_int), ("fifo", C.c_int),
+                ("stability_taper", C.c_double)]
 
 
 class sfhk_request(C.Structure):
@@ -238,11 +239,15 @@ def align_desc(a) -> sfhk_align_desc:
 
 
 def run_opts(precision=SFHK_FP64, gamma=0.5, cutoff=0.0, dump=False, block_threads=0,
-             blocks_per_sm=0, stab_cutoff=0.0, kernel_variant=0, returns=None) -> sfhk_run_opts:
-    """returns = (r_out, r_in) records each trajectory's first return."""
+             blocks_per_sm=0, stab_cutoff=0.0, kernel_variant=0, returns=None,
+             stab_taper=0.0) -> sfhk_run_opts:
+    """returns = (r_out, r_in) records each trajectory's first return;
+    stab_taper = r > 1 tapers the stability filter between stab_cutoff and
+    r stab_cutoff (0: hard cut)."""
     r_out, r_in = returns if returns else (0.0, 0.0)
     return sfhk_run_opts(precision, gamma, cutoff, int(dump), block_threads, blocks_per_sm,
-                         stab_cutoff, kernel_variant, int(bool(returns)), r_out, r_in)
+                         stab_cutoff, kernel_variant, int(bool(returns)), r_out, r_in,
+                         stab_taper)
 
 
 # ------------------------------------------------------------------ C-ABI calls

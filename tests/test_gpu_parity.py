@@ -409,3 +409,36 @@ def test_ptype_target_validation(S, ctx):
         S.sfhk_create_target(ctx, t)
     # a pi_u orbital is normalisable at R = 0 (a single-centre 2p)
     S.sfhk_destroy_target(S.sfhk_create_target(ctx, dict(W.TARGETS["N2_pi"], R=0.0)))
+
+
+@pytest.mark.parametrize("name,pulse,align,n", [
+    ("H2", W.PULSE_800, W.fixed(0.0), 1000),
+    ("N2", W.PULSE_1200, W.COS2, 600),
+    ("H2O", W.PULSE_800, W.ISO, 500),
+])
+def test_tapered_stability_filter(S, ctx, name, pulse, align, n):
+    """The tapered stability filter (weight 1 -> 0 between the cutoff and twice
+    it, in the running maximum of |M|): FP64 and mixed dipoles against the
+    oracle's, and the FP64 per-trajectory stop status."""
+    t = W.TARGETS[name]
+    soa, _, _ = O.sample(t, pulse, align, seed=13, n=n)
+    vz_o, fin_o, _ = O.propagate(t, pulse, soa, GAMMA, cutoff=CUT, want_final=True,
+                                 stab_cutoff=STAB, stab_taper=2.0)
+    th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, pulse)
+    e = S.sfhk_load_ensemble(ctx, th, ph, soa)
+    nt = S.sfhk_pulse_grid(ph)["nt"]
+    for prec, tol in ((S.SFHK_FP64, 1e-9), (S.SFHK_MIXED, 1e-4)):
+        S.sfhk_propagate(ctx, e, S.run_opts(prec, GAMMA, CUT, prec == S.SFHK_FP64,
+                                            stab_cutoff=STAB, stab_taper=2.0))
+        vz = S.sfhk_dipole(ctx, e, nt)
+        err = _rel_l2(vz, vz_o)
+        print(f"taper {name} prec {prec}: {err:.3e}")
+        assert err <= tol
+        if prec == S.SFHK_FP64:
+            assert np.array_equal(S.sfhk_final_state(e, n)[46], fin_o[46])
+    with pytest.raises(S.SfhkError):
+        S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB,
+                                            stab_taper=0.5))
+    S.sfhk_destroy_ensemble(e)
+    S.sfhk_destroy_pulse(ph)
+    S.sfhk_destroy_target(th)
