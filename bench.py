@@ -188,7 +188,7 @@ def oracle_sample_run(instances, n_per):
         m = min(n_per, i["n_traj"])
         soa, _, _ = O.sample(t, p, i["align"], seed=i["seed"], instance=i["instance"], n=m)
         vz, fin, _ = O.propagate(t, p, soa, W.GAMMA, cutoff=W.CUTOFF, want_final=False,
-                                 stab_cutoff=W.STAB_CUTOFF)
+                                 stab_cutoff=W.STAB_CUTOFF, stab_taper=W.STAB_TAPER)
         O.spectrum(vz, d["dt"], d["t_origin"], 0.5 * d["Tp"], d["nt"] // 2)
         steps += int(np.sum(d["nt"] - 1 - soa[0]))
     return time.perf_counter() - t0, steps
@@ -297,6 +297,7 @@ def run_ours(args):
             dist.barrier()
 
     mixed = S.run_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                       stab_taper=W.STAB_TAPER,
                        block_threads=args.block, kernel_variant=args.kernel_variant)
     # launch shape (block size x register-cap variant) chosen by the autotuner
     # on the first ensemble, untimed
@@ -392,7 +393,8 @@ def run_ours(args):
     # the plain FP64 GPU path on the same workload, and the dipole difference
     fp64 = None
     if not args.no_fp64:
-        o64 = S.run_opts(S.SFHK_FP64, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF)
+        o64 = S.run_opts(S.SFHK_FP64, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                         stab_taper=W.STAB_TAPER)
         b64 = S.sfhk_batch_create(ctx, ens, o64)
         step(b64)
         barrier()
@@ -462,7 +464,8 @@ def run_ours(args):
     if rank == 0:
         conf = dict(conf)
         conf.update({"dt": grids[0]["dt"], "gamma": W.GAMMA, "prefactor_cutoff": W.CUTOFF,
-                     "stability_cutoff": W.STAB_CUTOFF, "traj_steps_per_step": traj_steps,
+                     "stability_cutoff": W.STAB_CUTOFF, "stability_taper": W.STAB_TAPER,
+                     "traj_steps_per_step": traj_steps,
                      "l2": "inputs larger than L2 (trajectory SoA, 96 B per trajectory)",
                      "cuda_graph": graph is not None,
                      "parallelism": f"replicas x{world}"})
@@ -512,7 +515,8 @@ def run_served(args):
         if max_requests:
             reqs = reqs[:max_requests]
         srv = S.sfhk_server_create(local, S.server_opts(
-            S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF, budget=args.serve_budget,
+            S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF, stab_taper=W.STAB_TAPER,
+            budget=args.serve_budget,
             slice_ms=args.slice_ms, max_pending=args.max_pending))
         ids, rejected = [], 0
         t0 = time.perf_counter()
@@ -586,7 +590,8 @@ def run_orient(args):
     pul = S.sfhk_set_pulse(ctx, W.PULSE_800)
     g = S.sfhk_pulse_grid(pul)
     w0 = 45.5633525 / W.PULSE_800["lambda_nm"]          # photon energy (a.u.)
-    opts = S.run_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF)
+    opts = S.run_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                      stab_taper=W.STAB_TAPER)
     # (target, alignment) per method; "_abs": initial points ~ |a| (Sec. II.B)
     methods = {"joint_mc": (tgt, W.ISO), f"quadrature_{K}": (tgt, W.quadrature(K)),
                "fixed_0": (tgt, W.fixed(0.0)), "fixed_90": (tgt, W.fixed(90.0)),

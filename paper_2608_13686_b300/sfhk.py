@@ -420,9 +420,10 @@ SFHK_NOALLOC_MAX_NT = 32768
 
 # ------------------------------------------------------------------ serving
 def server_opts(precision=SFHK_MIXED, gamma=0.5, cutoff=0.0, stab_cutoff=0.0, budget=0,
-                max_pending=0, max_active=0, slice_ms=0.0, spectrum=True, fifo=False):
+                max_pending=0, max_active=0, slice_ms=0.0, spectrum=True, fifo=False,
+                stab_taper=0.0):
     return sfhk_server_opts(budget, max_pending, max_active, precision, gamma, cutoff,
-                            stab_cutoff, slice_ms, int(spectrum), int(fifo))
+                            stab_cutoff, slice_ms, int(spectrum), int(fifo), stab_taper)
 
 
 def request(target: dict, pulse: dict, align, n_traj, seed=0, instance=0) -> sfhk_request:
