@@ -59,6 +59,6 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 # dram__bytes_read.sum + dram__bytes_write.sum per full-size launch of the
 # dominant kernel, keyed by (workload, kernel variant), from an ncu capture of
 # the current kernel: H2 0/45/90 deg captured at 3 x 2e5 trajectories with the
-# 168-register variant in 32-thread blocks (62.3 MB read + 2.4 MB written) and
+# 168-register variant in 32-thread blocks (63.3 MB read + 3.0 MB written) and
 # scaled by trajectories to 3 x 1e6.
-TRAFFIC = {("h2-angles", 2): 324.0e6}
+TRAFFIC = {("h2-angles", 2): 331.0e6}
