@@ -300,10 +300,11 @@ def run_ours(args):
                        stab_taper=W.STAB_TAPER,
                        block_threads=args.block, kernel_variant=args.kernel_variant)
     # launch shape (block size x register-cap variant) chosen by the autotuner
-    # on the first ensemble, untimed
+    # on the largest ensemble, untimed
     tuned = None
     if not args.no_tune and not (args.block and args.kernel_variant):
-        tuned = S.sfhk_autotune(ctx, ens[0], mixed, max_items=0)
+        big = max(range(len(instances)), key=lambda k: instances[k]["n_traj"])
+        tuned = S.sfhk_autotune(ctx, ens[big], mixed, max_items=0)
     # a prepared batch: each step only enqueues device work
     batch = S.sfhk_batch_create(ctx, ens, mixed)
     for _ in range(args.warmup):
