@@ -78,6 +78,8 @@ def parse():
                     help="orient-avg: ensemble sizes")
     ap.add_argument("--orient-replicas", type=int, default=6)
     ap.add_argument("--orient-nodes", type=int, default=10)
+    ap.add_argument("--orient-target", default="H2", choices=["H2", "H2O"],
+                    help="orient-avg: the target (H2O: polyatomic, Euler-angle averaging)")
     ap.add_argument("--abs-kappa", type=float, default=5.0,
                     help="orient-avg: envelope factor of the |a|-proportional sampler")
     return ap.parse_args()
@@ -586,8 +588,10 @@ def run_orient(args):
     R = args.orient_replicas
     K = args.orient_nodes
     ctx = S.sfhk_create(local, 0)
-    tgt = S.sfhk_create_target(ctx, W.TARGETS["H2"])
-    tgt_abs = S.sfhk_create_target(ctx, W.abs_sampled(W.TARGETS["H2"], args.abs_kappa))
+    tname = args.orient_target
+    poly = W.TARGETS[tname].get("kind") == W.POT_POLY
+    tgt = S.sfhk_create_target(ctx, W.TARGETS[tname])
+    tgt_abs = S.sfhk_create_target(ctx, W.abs_sampled(W.TARGETS[tname], args.abs_kappa))
     pul = S.sfhk_set_pulse(ctx, W.PULSE_800)
     g = S.sfhk_pulse_grid(pul)
     w0 = 45.5633525 / W.PULSE_800["lambda_nm"]          # photon energy (a.u.)
@@ -599,6 +603,13 @@ def run_orient(args):
                "joint_mc_abs": (tgt_abs, W.ISO), "fixed_0_abs": (tgt_abs, W.fixed(0.0))}
     # estimates of the same isotropic average
     averaged = ("joint_mc", f"quadrature_{K}", "joint_mc_abs")
+    if poly:
+        # polyatomic: the joint Monte Carlo over all three Euler angles against
+        # two fixed orientations (no cos-theta quadrature for a polyatomic)
+        methods = {"joint_mc": (tgt, W.ISO), "fixed_0": (tgt, W.fixed(0.0)),
+                   "fixed_90": (tgt, W.fixed(90.0, 0.0, 90.0)),
+                   "joint_mc_abs": (tgt_abs, W.ISO), "fixed_0_abs": (tgt_abs, W.fixed(0.0))}
+        averaged = ("joint_mc", "joint_mc_abs")
     dip, yld = {}, {}
     steps_total, ms_total = 0, 0.0
     cost = {}                                       # [sampling ms, propagation ms, trajectories]
@@ -634,8 +645,8 @@ def run_orient(args):
     for m in methods:
         refs[m] = iso if m in averaged else np.mean(dip[(m, nmax)], axis=0)
         yrefs[m] = yiso if m in averaged else np.mean([y[band] for y in yld[(m, nmax)]], axis=0)
-    study = {"target": "H2", "pulse": "800 nm, 3 cycles, 1.5e14 W/cm^2", "replicas": R,
-             "ladder": ladder, "quadrature_nodes": K, "methods": {}}
+    study = {"target": tname, "pulse": "800 nm, 3 cycles, 1.5e14 W/cm^2", "replicas": R,
+             "ladder": ladder, "quadrature_nodes": None if poly else K, "methods": {}}
     for m in methods:
         rows, cs, cys = [], [], []
         for N in ladder:
@@ -651,10 +662,12 @@ def run_orient(args):
         study["methods"][m] = {"rows": rows, "c_dipole": float(np.median(cs)),
                                "c_plateau_yield": float(np.median(cys))}
     mq = f"quadrature_{K}"
-    cm, cq = study["methods"]["joint_mc"], study["methods"][mq]
-    study["traj_ratio_quadrature_over_mc_dipole"] = (cq["c_dipole"] / cm["c_dipole"]) ** 2
-    study["traj_ratio_quadrature_over_mc_plateau_yield"] = (
-        (cq["c_plateau_yield"] / cm["c_plateau_yield"]) ** 2)
+    cm = study["methods"]["joint_mc"]
+    if not poly:
+        cq = study["methods"][mq]
+        study["traj_ratio_quadrature_over_mc_dipole"] = (cq["c_dipole"] / cm["c_dipole"]) ** 2
+        study["traj_ratio_quadrature_over_mc_plateau_yield"] = (
+            (cq["c_plateau_yield"] / cm["c_plateau_yield"]) ** 2)
     # |a|-proportional sampling: noise per trajectory and cost per trajectory
     # (sampling + propagation, device time) against the plain proposal
     for m in methods:
@@ -676,14 +689,18 @@ def run_orient(args):
     for fa in ("fixed_0", "fixed_90"):
         cf = study["methods"][fa]
         study[f"mc_cost_over_{fa}"] = (cm["c_dipole"] / cf["c_dipole"]) ** 2
-        study[f"standard_{K}_angles_over_mc_at_{fa}_noise"] = K * (cf["c_dipole"]
-                                                                    / cm["c_dipole"]) ** 2
-    dq = np.mean(dip[(mq, nmax)], axis=0)
+        study[f"mc_cost_over_{fa}_plateau_yield"] = (
+            (cm["c_plateau_yield"] / cf["c_plateau_yield"]) ** 2)
+        if not poly:
+            study[f"standard_{K}_angles_over_mc_at_{fa}_noise"] = K * (cf["c_dipole"]
+                                                                        / cm["c_dipole"]) ** 2
     dm = np.mean(dip[("joint_mc", nmax)], axis=0)
-    noise_of_means = np.hypot(cm["rows"][-1]["dipole_rel_noise"],
-                              cq["rows"][-1]["dipole_rel_noise"]) / np.sqrt(R)
-    study["mean_difference_at_nmax"] = float(np.linalg.norm(dq - dm) / np.linalg.norm(iso))
-    study["noise_of_that_difference"] = float(noise_of_means)
+    if not poly:
+        dq = np.mean(dip[(mq, nmax)], axis=0)
+        noise_of_means = np.hypot(cm["rows"][-1]["dipole_rel_noise"],
+                                  cq["rows"][-1]["dipole_rel_noise"]) / np.sqrt(R)
+        study["mean_difference_at_nmax"] = float(np.linalg.norm(dq - dm) / np.linalg.norm(iso))
+        study["noise_of_that_difference"] = float(noise_of_means)
     # unbiasedness of the |a| sampler: its mean against the plain joint Monte Carlo
     ca = study["methods"]["joint_mc_abs"]
     da = np.mean(dip[("joint_mc_abs", nmax)], axis=0)
@@ -694,7 +711,7 @@ def run_orient(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 0, "ms_per_step": ms_total, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-            "config": {"workload": "orientation averaging study, H2 isotropic",
+            "config": {"workload": f"orientation averaging study, {tname} isotropic",
                        "ladder": ladder, "replicas": R},
             "orientation_study": study}
     print(json.dumps(line), flush=True)
