@@ -454,9 +454,7 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
             T.cZinf[c] = d->centre_Z_inf[c];
             T.cdZ[c] = d->centre_Z0[c] - d->centre_Z_inf[c];
             T.calpha[c] = d->centre_alpha[c];
-            T.cZinf_f[c] = (float)T.cZinf[c];
-            T.cdZ_f[c] = (float)T.cdZ[c];
-            T.calpha_f[c] = (float)T.calpha[c];
+            T.cq_f[c] = make_float4((float)T.cZinf[c], (float)T.cdZ[c], (float)T.calpha[c], 0.0f);
         }
         for (int k = 0; k < d->n_prim; ++k) {
             T.pcentre[k] = d->prim_centre[k];

@@ -342,12 +342,45 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, const R e[2][3],
     }
 }
 
+// Row r of this lane's column of the per-warp centre table: FP32 rows are
+// float4 (x, y, z, 0), one 16-byte shared load, 32 rows of lanes apart; FP64
+// rows are three doubles, 32 apart.  kTabWords: words per row and lane.
+template <typename R>
+constexpr int kTabWords = std::is_same<R, float>::value ? 4 : 3;
+
+template <typename R>
+__device__ __forceinline__ void tab_row(const R* tab, int r, R& x, R& y, R& z)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        const float4 v = reinterpret_cast<const float4*>(tab)[r * 32];
+        x = v.x;
+        y = v.y;
+        z = v.z;
+    } else {
+        x = tab[(3 * r) * 32];
+        y = tab[(3 * r + 1) * 32];
+        z = tab[(3 * r + 2) * 32];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void tab_store(R* tab, int r, R x, R y, R z)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        reinterpret_cast<float4*>(tab)[r * 32] = make_float4(x, y, z, 0.0f);
+    } else {
+        tab[(3 * r) * 32] = x;
+        tab[(3 * r + 1) * 32] = y;
+        tab[(3 * r + 2) * 32] = z;
+    }
+}
+
 // Polyatomic potential (Eq. 7 summed over the N centres of the target, each
 // with its own Z_inf, Z0 - Z_inf and alpha): V, F = -grad V and the Hessian
 // at the stage point ((q - c) + l) + o for every centre c.  The centres' lab
-// positions are this lane's rows of a per-warp shared-memory table,
-// tab[(3 c + a) * 32] (the row stride is the warp size, so the 32 lanes read
-// 32 consecutive words).  Per centre, with u = 1/s, s^2 = |d|^2 + a^2:
+// positions are this lane's rows of a per-warp shared-memory table (tab_row;
+// the lanes of a warp read consecutive words).  Per centre, with u = 1/s,
+// s^2 = |d|^2 + a^2:
 //   vc = (Zinf + dZ e^{-alpha s}) u,  g1 = Zinf u^3 + dZ e^{-alpha s}(alpha u^2 + u^3),
 //   g2 = -u^2 [3 Zinf u^3 + dZ e^{-alpha s} u (alpha^2 + 3 alpha u + 3 u^2)],
 //   V = -sum vc,  F = -sum g1 d,  H = (sum g1) I + sum g2 d d^T.
@@ -362,16 +395,24 @@ __device__ __forceinline__ void potential_poly(const Target& T, const R* tab, R 
     const R o[3] = {ox, oy, oz};
 #pragma unroll 1
     for (int c = 0; c < T.n_centres; ++c) {
-        R d[3];
+        R cc[3], d[3];
+        tab_row(tab, c, cc[0], cc[1], cc[2]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const R cc = tab[(3 * c + a) * 32];
-            d[a] = LO ? (q[a] - cc) + l[a] : q[a] - cc;
+            d[a] = LO ? (q[a] - cc[a]) + l[a] : q[a] - cc[a];
             if (OFS) d[a] += o[a];
         }
-        const R Zinf = F32 ? R(T.cZinf_f[c]) : R(T.cZinf[c]);
-        const R dZ = F32 ? R(T.cdZ_f[c]) : R(T.cdZ[c]);
-        const R al = F32 ? R(T.calpha_f[c]) : R(T.calpha[c]);
+        R Zinf, dZ, al;
+        if constexpr (F32) {
+            const float4 k = T.cq_f[c];           // one 16-byte load
+            Zinf = k.x;
+            dZ = k.y;
+            al = k.z;
+        } else {
+            Zinf = T.cZinf[c];
+            dZ = T.cdZ[c];
+            al = T.calpha[c];
+        }
         const R s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + a2;
         const R u = rsqrt_t<R>(s2);
         const R u2 = u * u, u3 = u2 * u;

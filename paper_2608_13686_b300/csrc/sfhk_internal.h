@@ -38,7 +38,7 @@ struct DevTarget {
     int n_slots;                // per-lane table rows: centres, then p directions
     double cpos[SFHK_MAX_CENTRES][3];                 // molecular frame
     double cZinf[SFHK_MAX_CENTRES], cdZ[SFHK_MAX_CENTRES], calpha[SFHK_MAX_CENTRES];
-    float cZinf_f[SFHK_MAX_CENTRES], cdZ_f[SFHK_MAX_CENTRES], calpha_f[SFHK_MAX_CENTRES];
+    float4 cq_f[SFHK_MAX_CENTRES];                    // (Z_inf, dZ, alpha, 0) in FP32
     int pcentre[SFHK_MAX_PRIM];
     double pdir[SFHK_MAX_PRIM][3];                    // unit, molecular frame
 };

@@ -629,8 +629,9 @@ __device__ __forceinline__ C2<R> recomb_poly(const DevInstance& I, const R* tab,
 #pragma unroll 1
     for (int k = 0; k < n_prim; ++k) {
         const int c = I.tgt.pcentre[k];
-        const R dx = q[0] - tab[(3 * c) * 32], dy = q[1] - tab[(3 * c + 1) * 32],
-                dz = q[2] - tab[(3 * c + 2) * 32];
+        R cx, cy, cz;
+        tab_row(tab, c, cx, cy, cz);
+        const R dx = q[0] - cx, dy = q[1] - cy, dz = q[2] - cz;
         const R dd = dx * dx + dy * dy + dz * dz;
         const R K1 = F32 ? R(I.rec.K1f[k]) : R(I.rec.K1[k]);
         const R K2 = F32 ? R(I.rec.K2f[k]) : R(I.rec.K2[k]);
@@ -645,8 +646,8 @@ __device__ __forceinline__ C2<R> recomb_poly(const DevInstance& I, const R* tab,
         else sincos(K3 * pdd, &sn, &cs);
         R ar = mag * p[2], ai = -mag * gam * dz;
         if (I.rec.kind[k] == SFHK_PRIM_P_DIR) {
-            const int r = 3 * (nc + k);
-            const R ux = tab[r * 32], uy = tab[(r + 1) * 32], uz = tab[(r + 2) * 32];
+            R ux, uy, uz;
+            tab_row(tab, nc + k, ux, uy, uz);
             const R P1 = F32 ? R(I.rec.P1f[k]) : R(I.rec.P1[k]);
             const R P2 = F32 ? R(I.rec.P2f[k]) : R(I.rec.P2[k]);
             const R P3 = F32 ? R(I.rec.P3f[k]) : R(I.rec.P3[k]);
@@ -717,9 +718,11 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         const int nc = I.tgt.n_centres;
         for (int r = 0; r < I.tgt.n_slots; ++r) {
             const double* x = r < nc ? I.tgt.cpos[r] : I.tgt.pdir[r - nc];
+            R v[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                tab[(3 * r + a) * 32] = R(Rot[3 * a] * x[0] + Rot[3 * a + 1] * x[1] + Rot[3 * a + 2] * x[2]);
+                v[a] = R(Rot[3 * a] * x[0] + Rot[3 * a + 1] * x[1] + Rot[3 * a + 2] * x[2]);
+            tab_store(tab, r, v[0], v[1], v[2]);
         }
     }
     const R gam = R(I.gamma), igam = R(I.inv_gamma);
@@ -993,7 +996,9 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
 }
 
 // The persistent loop over the work-item queue.  POLY: after the blocks'
-// reduction buffers, every warp has a table of `slots` rows x 3 x 32 words.
+// reduction buffers, every warp has a table of `slots` rows x kTabWords x 32
+// words (this lane's column starts kTabWords words per lane in for FP32
+// float4 rows, one word for the FP64 rows).
 template <bool MIXED, bool POLY = false>
 __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ items, int n_items,
@@ -1006,7 +1011,8 @@ __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
     R* tab = nullptr;
     if constexpr (POLY)
         tab = reinterpret_cast<R*>(smem_raw) + (blockDim.x / kWarp) * kRedElems +
-              (threadIdx.x / kWarp) * (slots * 3 * kWarp) + lane;
+              (threadIdx.x / kWarp) * (slots * kTabWords<R> * kWarp) +
+              lane * (MIXED ? kTabWords<R> : 1);
     for (;;) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(counter, 1u);
@@ -1215,7 +1221,7 @@ int launch_poly(int precision, int variant_index, const DevInstance* insts,
     const PolyFn fn = poly_variant(precision, variant_index);
     const size_t elem = mixed ? sizeof(float) : sizeof(double);
     const size_t smem = red_bytes(precision, block_threads) +
-                        size_t(block_threads / kWarp) * slots * 3 * kWarp * elem;
+                        size_t(block_threads / kWarp) * slots * (mixed ? 4 : 3) * kWarp * elem;
     if (smem > 48 * 1024)
         SFHK_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
