@@ -62,5 +62,5 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 # 168-register variant in 32-thread blocks (63.3 MB read + 3.0 MB written) and
 # scaled by trajectories to 3 x 1e6.
 # H2O 1b1 isotropic: captured at 2e5 trajectories with the 128-register
-# variant in 64-thread blocks (19.8 MB read + 0.18 MB written), scaled to 1e6.
-TRAFFIC = {("h2-angles", 2): 331.0e6, ("h2o-iso", 6): 100.1e6}
+# variant in 64-thread blocks (19.8 MB read + 0.19 MB written), scaled to 1e6.
+TRAFFIC = {("h2-angles", 2): 331.0e6, ("h2o-iso", 6): 100.0e6}
