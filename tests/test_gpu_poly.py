@@ -177,3 +177,43 @@ def test_polyatomic_validation(S, ctx):
         S.sfhk_create_target(ctx, dict(W.TARGETS["N2"], pkind=[3, 0]))
     S.sfhk_destroy_pulse(ph)
     S.sfhk_destroy_target(th)
+
+
+def _eight_centre_target():
+    """Eight centres on a distorted cube, eight p-type primitives (one per
+    centre, directions not normalised): the largest table (16 rows per lane)."""
+    rng = np.random.default_rng(5)
+    cen = []
+    for k in range(8):
+        x = np.array([(k & 1) * 2.0 - 1.0, ((k >> 1) & 1) * 2.0 - 1.0, ((k >> 2) & 1) * 2.0 - 1.0])
+        x = 1.3 * x + 0.1 * rng.normal(size=3)
+        cen.append((*x, 1.0 / 8.0, 1.0 + k % 3, 1.0 + 0.2 * k))
+    prims = [(k, 0.6 + 0.1 * k, 0.3 + 0.05 * k, tuple(rng.normal(size=3) * 2.0)) for k in range(8)]
+    return W._poly(cen, 0.5, prims)
+
+
+def test_largest_polyatomic_target(S, ctx):
+    """SFHK_MAX_CENTRES centres and SFHK_MAX_PRIM p-type primitives, in
+    128-thread blocks: the FP64 kernel then needs more than 48 KB of dynamic
+    shared memory (the opt-in path).  Sampler, FP64 and mixed dipoles against
+    the oracle."""
+    t = _eight_centre_target()
+    p = W.PULSE_800
+    n = 256
+    th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, p)
+    e = S.sfhk_sample_initial(ctx, th, ph, W.ISO, n, 3, 0)
+    g = S.sfhk_ensemble_read(e, n)
+    o, _, _ = O.sample(t, p, W.ISO, seed=3, n=n)
+    assert np.array_equal(g[0], o[0])
+    w_g, w_o = g[10] + 1j * g[11], o[10] + 1j * o[11]
+    assert np.all(np.abs(w_g - w_o) <= 1e-10 * np.abs(w_o) + 1e-300)
+    vz_o, _, _ = O.propagate(t, p, o, GAMMA, cutoff=CUT, stab_cutoff=STAB,
+                             stab_taper=W.STAB_TAPER)
+    nt = S.sfhk_pulse_grid(ph)["nt"]
+    for prec, tol in ((S.SFHK_FP64, 1e-9), (S.SFHK_MIXED, 1e-4)):
+        S.sfhk_propagate(ctx, e, S.run_opts(prec, GAMMA, CUT, block_threads=128,
+                                            stab_cutoff=STAB, stab_taper=W.STAB_TAPER))
+        assert _rel_l2(S.sfhk_dipole(ctx, e, nt), vz_o) <= tol, prec
+    S.sfhk_destroy_ensemble(e)
+    S.sfhk_destroy_pulse(ph)
+    S.sfhk_destroy_target(th)
