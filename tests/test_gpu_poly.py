@@ -186,8 +186,8 @@ def _eight_centre_target():
     cen = []
     for k in range(8):
         x = np.array([(k & 1) * 2.0 - 1.0, ((k >> 1) & 1) * 2.0 - 1.0, ((k >> 2) & 1) * 2.0 - 1.0])
-        x = 1.3 * x + 0.1 * rng.normal(size=3)
-        cen.append((*x, 1.0 / 8.0, 1.0 + k % 3, 1.0 + 0.2 * k))
+        x = 1.6 * x + 0.1 * rng.normal(size=3)
+        cen.append((*x, 1.0 / 8.0, 1.0 + 0.25 * (k % 3), 1.0))
     prims = [(k, 0.6 + 0.1 * k, 0.3 + 0.05 * k, tuple(rng.normal(size=3) * 2.0)) for k in range(8)]
     return W._poly(cen, 0.5, prims)
 
