@@ -35,7 +35,9 @@ MIX = [("H2", W.PULSE_800, W.fixed(10.0), 3000, 1),
        ("N2", W.pulse(1000.0, 1.6e14, 2), W.COS2, 2500, 2),
        ("H2", W.pulse(1400.0, 1.0e14, 4), W.fixed(70.0), 700, 3),
        ("N2", W.PULSE_1200, W.fixed(40.0), 4100, 4),
-       ("H2", W.pulse(900.0, 1.9e14, 3), W.COS2, 33, 5)]
+       ("H2", W.pulse(900.0, 1.9e14, 3), W.COS2, 33, 5),
+       ("N2_sp", W.PULSE_1200, W.ISO, 900, 6),
+       ("N2_pi", W.pulse(1000.0, 1.4e14, 3), W.fixed(60.0), 600, 7)]
 
 
 def _alone(S, ctx, name, pulse, align, n, inst, prec):
@@ -140,4 +142,13 @@ def test_cancel(S):
     with pytest.raises(S.SfhkError) as e:
         S.sfhk_poll(srv, 987654321)
     assert e.value.code == S.SFHK_E_NOTFOUND
+    S.sfhk_server_destroy(srv)
+
+
+def test_polyatomic_request_is_refused(S):
+    """The server runs diatomic targets only (the polyatomic kernel is a
+    separate launch); a polyatomic request is refused at submission."""
+    srv = S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF))
+    with pytest.raises(S.SfhkError):
+        S.sfhk_submit(srv, S.request(W.TARGETS["H2O"], W.PULSE_800, W.ISO, 100, 1, 0))
     S.sfhk_server_destroy(srv)
