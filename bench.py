@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="h2-angles",
-                    choices=["h2-angles", "n2-cos2", "h2o-iso", "batched", "served",
-                             "orient-avg"])
+                    choices=["h2-angles", "n2-cos2", "n2sp-iso", "h2o-iso", "batched",
+                             "served", "orient-avg"])
     ap.add_argument("--n-traj", type=int, default=0,
                     help="trajectories per ensemble (0 = the workload's own)")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
@@ -159,6 +159,12 @@ def workload_instances(name, n_traj=None):
         inst = [dict(target=cfg["target"], pulse=cfg["pulse"], align=cfg["align"], n_traj=n,
                      seed=cfg["seed"], instance=0)]
         return cfg["name"], {"workload": cfg["name"], "target": "N2", "n_traj": n}, inst
+    if name == "n2sp-iso":
+        cfg = W.N2SP_ISO
+        n = n_traj or cfg["n_traj"]
+        inst = [dict(target=cfg["target"], pulse=cfg["pulse"], align=cfg["align"], n_traj=n,
+                     seed=cfg["seed"], instance=0)]
+        return cfg["name"], {"workload": cfg["name"], "target": "N2_sp", "n_traj": n}, inst
     if name == "h2o-iso":
         cfg = W.H2O_ISO
         n = n_traj or cfg["n_traj"]

@@ -42,9 +42,14 @@ counting:
   ---------------------------------------------------------------
   H2O (3 centres, 2 primitives): 4 x 162 + 984 + 27              1659
   H2O_3a1 (3 centres, 4 primitives): 4 x 162 + 984 + 49          1681
+
+Diatomic targets with more primitives add the per-primitive exponent of the
+recombination test (3 per primitive and centre): N2_sp (4 primitives, two of
+them p-type) 1419 + 2 x 2 x 3 = 1431; N2_pi (2 primitives) 1419.
 """
 
-FLOPS_PER_STEP = {"H2": 1299, "N2": 1419, "H2O": 1659, "H2O_3a1": 1681}
+FLOPS_PER_STEP = {"H2": 1299, "N2": 1419, "N2_sp": 1431, "N2_pi": 1419, "H2O": 1659,
+                  "H2O_3a1": 1681}
 
 # FP32 FMA pipe of a B300: 148 SMs x 128 lanes x 2 flops x 2.032 GHz (max SM clock)
 SMS = 148

@@ -217,6 +217,12 @@ N2_COS2 = dict(name="N2 cos^2-aligned, 1e7 traj, 1200 nm 3 cyc 1.2e14, mixed",
                target="N2", pulse=PULSE_1200, align=COS2, n_traj=10_000_000, seed=0,
                gamma=GAMMA)
 
+# N2 with sigma p-type primitives in the HOMO, isotropic, 1e6 trajectories, mixed
+N2SP_ISO = dict(name="N2 3sigma_g with 2p_sigma primitives, isotropic, 1e6 traj, 1200 nm 3 cyc "
+                     "1.2e14, mixed",
+                target="N2_sp", pulse=PULSE_1200, align=ISO, n_traj=1_000_000, seed=0,
+                gamma=GAMMA)
+
 # water 1b1 (three centres), isotropic over all three Euler angles, 1e6
 # trajectories, mixed precision
 H2O_ISO = dict(name="H2O 1b1 isotropic (Euler angles), 1e6 traj, 800 nm 3 cyc 1.5e14, mixed",
