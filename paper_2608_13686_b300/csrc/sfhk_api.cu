@@ -929,27 +929,41 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
     int slots = 0;
     poly_slots(&e, 1, &slots);
     const int blocks[3] = {32, 64, 128};
-    float best = 3.4e38f;
-    int bb = c->tuned[o->precision][0], bv = c->tuned[o->precision][1];
+    // one timed launch per shape (after a warm-up launch), then the three
+    // fastest shapes timed twice more: launch times of close shapes differ by
+    // about 1 %, the size of the run-to-run spread
+    auto time_shape = [&](int v, int b, float* ms) -> int {
+        SFHK_CUDA_TRY(cudaEventRecord(e->ev_start, 0));
+        const int r = launch_propagate(o->precision, v, (const DevInstance*)e->inst.p,
+                                       (const WorkItem*)e->items.p, items,
+                                       (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0, slots);
+        if (r) return r;
+        SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, 0));
+        SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_stop));
+        SFHK_CUDA_TRY(cudaEventElapsedTime(ms, e->ev_start, e->ev_stop));
+        return SFHK_OK;
+    };
+    struct Shape { float ms; int v, b; };
+    std::vector<Shape> shapes;
     for (int v = 0; v < kPropVariants; ++v)
         for (int b : blocks) {
             float ms = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {      // first launch warms up
-                SFHK_CUDA_TRY(cudaEventRecord(e->ev_start, 0));
-                rc = launch_propagate(o->precision, v, (const DevInstance*)e->inst.p,
-                                      (const WorkItem*)e->items.p, items,
-                                      (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0, slots);
-                if (rc) return rc;
-                SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, 0));
-                SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_stop));
-                SFHK_CUDA_TRY(cudaEventElapsedTime(&ms, e->ev_start, e->ev_stop));
-            }
-            if (ms < best) {
-                best = ms;
-                bb = b;
-                bv = v;
-            }
+            for (int rep = 0; rep < 2; ++rep)        // the first launch warms up
+                if ((rc = time_shape(v, b, &ms))) return rc;
+            shapes.push_back({ms, v, b});
         }
+    std::sort(shapes.begin(), shapes.end(),
+              [](const Shape& x, const Shape& y) { return x.ms < y.ms; });
+    const size_t top = std::min<size_t>(3, shapes.size());
+    for (size_t k = 0; k < top; ++k)
+        for (int rep = 0; rep < 2; ++rep) {
+            float ms = 0.0f;
+            if ((rc = time_shape(shapes[k].v, shapes[k].b, &ms))) return rc;
+            shapes[k].ms = std::min(shapes[k].ms, ms);
+        }
+    std::sort(shapes.begin(), shapes.begin() + top,
+              [](const Shape& x, const Shape& y) { return x.ms < y.ms; });
+    const int bb = shapes[0].b, bv = shapes[0].v;
     c->tuned[o->precision][0] = bb;
     c->tuned[o->precision][1] = bv;
     c->tuned[o->precision][2] = 0;
