@@ -8,18 +8,25 @@
 // steps.  Per step and lane:
 //   1. prefactor C = sqrt(det[(M_qq + M_pp - i g M_qp + (i/g) M_pq)/2]) on a
 //      continuous branch (sign chosen so that C moves by less than a right
-//      angle from the previous step), the finiteness check and the prefactor
-//      filter;
-//   2. contribution x = Re[w C e^{iS} e^{-i Ip t_n} <psi0|k_z|p,q>];
-//   3. warp sum of x (shuffles), kept by lane (n mod 32);
-//   4. one RK4 step of (q, p, S) collecting the four stage Hessians, then the
+//      angle from the previous step), the finiteness check, the prefactor
+//      filter and the stability filter (hard, or tapered in the running
+//      maximum of |M|);
+//   2. contribution x = Re[w C e^{iS} e^{-i Ip t_n} <psi0|k_z|p,q>] (times the
+//      taper weight), stored in the warp's shared-memory tile at (step, lane);
+//   3. one RK4 step of (q, p, S) collecting the four stage Hessians, then the
 //      six stability-matrix columns advanced by the same RK4 with those
 //      Hessians (identical to RK4 on the full 43-component system because the
 //      columns obey the linear system dMq/dt = Mp, dMp/dt = -Hess V(q(t)) Mq).
-// After each chunk every lane adds its bin, scaled by -2/N, into the FP64
-// dipole with one atomic: no per-trajectory time series reaches HBM.  The
-// field E at the chunk's half steps and e^{-i Ip t_n} are loaded once per
-// chunk (one element per lane) and broadcast by shuffles.
+// After each chunk lane l sums row l of the tile (step nb + l over the 32
+// trajectories) and adds it, scaled by -2/N, into the FP64 dipole with one
+// atomic: no per-trajectory time series reaches HBM.  The field E at the
+// chunk's half steps and e^{-i Ip t_n} are loaded once per chunk (one element
+// per lane) and broadcast by shuffles.
+//
+// Diatomic targets run k_propagate (two centres at +-(R/2) n, in the lanes of
+// float2 values in FP32); polyatomic targets run k_propagate_poly, the same
+// integrator with the N-centre potential over a per-warp table of the
+// molecule's lab-frame centres.
 //
 // Precision policies
 //   FP64:  everything in double.
