@@ -352,6 +352,8 @@ int sfhk_create(sfhk_ctx** out, int device, size_t budget)
     SFHK_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
     if (prop.major != 10 || prop.minor != 3) return SFHK_E_CUDA;
     SFHK_CUDA_TRY(cudaSetDevice(device));
+    int rc = configure_kernels();
+    if (rc) return rc;
     sfhk_ctx* c = new (std::nothrow) sfhk_ctx;
     if (!c) return SFHK_E_NOMEM;
     c->device = device;

@@ -169,6 +169,8 @@ int launch_sort_items(const WorkItem* in, int n_items, const int* inst_nt, WorkI
                       cudaStream_t s);
 // propagate (sfhk_propagate.cu)
 constexpr int kPropVariants = 6;   // register-cap variants of the integrator
+// once per device, at context creation: kernel attributes (shared memory)
+int configure_kernels();
 // poly_slots > 0: polyatomic instances, launched on the polyatomic kernel
 // with that many table rows per lane (the largest n_slots of the instances)
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,

@@ -1229,9 +1229,7 @@ int launch_poly(int precision, int variant_index, const DevInstance* insts,
     const size_t elem = mixed ? sizeof(float) : sizeof(double);
     const size_t smem = red_bytes(precision, block_threads) +
                         size_t(block_threads / kWarp) * slots * (mixed ? 4 : 3) * kWarp * elem;
-    if (smem > 48 * 1024)
-        SFHK_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
+    // above 48 KB the kernels rely on the limit raised by configure_kernels()
     int occ = 0;
     SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_threads, smem));
     if (occ < 1) occ = 1;
@@ -1249,6 +1247,25 @@ int launch_poly(int precision, int variant_index, const DevInstance* insts,
 }
 
 }  // namespace
+
+// Raise the dynamic shared-memory limit of the polyatomic kernels to their
+// largest launch (128 threads, SFHK_MAX_CENTRES + SFHK_MAX_PRIM table rows),
+// once per device at context creation, so that no launch (in a captured
+// graph either) changes a function attribute.
+int configure_kernels()
+{
+    for (int prec = 0; prec < 2; ++prec) {
+        const size_t elem = prec == SFHK_MIXED ? sizeof(float) : sizeof(double);
+        const size_t smem = red_bytes(prec, 128) + size_t(128 / kWarp) *
+                                                       (SFHK_MAX_CENTRES + SFHK_MAX_PRIM) *
+                                                       (prec == SFHK_MIXED ? 4 : 3) * kWarp * elem;
+        for (int v = 0; v < kPropVariants; ++v)
+            SFHK_CUDA_TRY(cudaFuncSetAttribute(poly_variant(prec, v),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+    }
+    return SFHK_OK;
+}
 
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
