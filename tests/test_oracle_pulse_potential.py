@@ -58,6 +58,8 @@ def test_paper_laser_numbers():
     assert (t1["Zinf"], t1["Z0"], t1["alpha"], t1["R"]) == tuple(
         GOLD["table1"]["N2"][k] for k in ("Zinf", "Z0", "alpha", "R"))
     assert t1["Ip"] * EV == pytest.approx(GOLD["table2"]["N2_3sigma_g"])
+    # the HOMO-1 target binds with Table II's 1 pi_u energy
+    assert W.TARGETS["N2_pi"]["Ip"] * EV == pytest.approx(GOLD["table2"]["N2_1pi_u"])
 
 
 def test_time_grid():
