@@ -63,7 +63,8 @@ class TargetIn(C.Structure):
                 ("pkind", C.c_int * 8), ("pi_azimuth", C.c_double),
                 ("n_centres", C.c_int), ("cpos", (C.c_double * 3) * 8),
                 ("cZinf", C.c_double * 8), ("cZ0", C.c_double * 8), ("calpha", C.c_double * 8),
-                ("pcentre", C.c_int * 8), ("pdir", (C.c_double * 3) * 8)]
+                ("pcentre", C.c_int * 8), ("pdir", (C.c_double * 3) * 8),
+                ("proposal_mix", C.c_double), ("proposal_floor", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -169,6 +170,8 @@ def target_in(t) -> TargetIn:
     for i, d in enumerate(t.get("pdir", ())):
         for a in range(3):
             T.pdir[i][a] = d[a]
+    T.proposal_mix = float(t.get("proposal_mix", 0.0))
+    T.proposal_floor = float(t.get("proposal_floor", 0.0))
     return T
 
 

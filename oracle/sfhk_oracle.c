@@ -96,6 +96,10 @@ typedef struct {
     double cZinf[OR_MAX_CENTRES], cZ0[OR_MAX_CENTRES], calpha[OR_MAX_CENTRES];
     int pcentre[8];
     double pdir[8][3];
+    double proposal_mix;    /* eps in [0, 1): defensive share of the time   */
+                            /* proposal, uniform over the grid              */
+    double proposal_floor;  /* f in [0, 1]: the k_perp width is at least    */
+                            /* sigma(f E0), the width for a field f E0      */
 } or_target_in;
 
 /* ------------------------------------------------------------------ */
@@ -964,6 +968,31 @@ void or_adk_table(const or_pulse_in* Pin, double Ip, double* W, double* cdf)
     }
 }
 
+/* Time table of the proposal.  Plain: the ADK weights (or_adk_table).    */
+/* Defensive (proposal_mix = eps > 0, a reading): W_n = (1 - eps) e_n /     */
+/* sum e + eps / Nt, a share eps spread uniformly over the grid.  The ADK   */
+/* exponent falls much faster than the SFA amplitude where the field is     */
+/* weak (Keldysh parameter above 1), which gives w = a / pdf a heavy tail;  */
+/* the uniform share bounds the time factor of 1/pdf by Nt dt / eps, and    */
+/* the floor on the k_perp width (proposal_floor) keeps the momentum factor */
+/* bounded where sigma(t0) ~ sqrt|E(t0)| would vanish.  Any eps and floor   */
+/* leave every weighted mean unbiased, since w = a / pdf uses the density  */
+/* actually sampled.                                                       */
+static void defensive_table(const or_target_in* T, const or_pulse_in* Pin, double* W,
+                            double* cdf)
+{
+    or_adk_table(Pin, T->Ip, W, cdf);
+    double eps = T->proposal_mix;
+    if (!(eps > 0.0)) return;
+    or_pulse P = or_make_pulse(Pin);
+    double sum = cdf[P.nt - 1], acc = 0.0;
+    for (int n = 0; n < P.nt; ++n) {
+        W[n] = (1.0 - eps) * W[n] / sum + eps / P.nt;
+        acc += W[n];
+        cdf[n] = acc;
+    }
+}
+
 /* One draw of the proposal and its amplitude: t0, k_perp, axis from the  */
 /* six uniforms u, then saddle, exit, action, amplitude and the weight     */
 /* w = a / pdf (node weight of the quadrature alignment included).         */
@@ -992,6 +1021,8 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
     double t0 = Pp->t_origin + n0 * Pp->dt;
     double Et0 = pulse_E_real(Pp, t0);
     double sigma = sqrt(fabs(Et0) / (2.0 * sqrt(2.0 * T->Ip)));
+    if (T->proposal_floor > 0.0)      /* defensive floor on the k_perp width */
+        sigma = fmax(sigma, sqrt(T->proposal_floor * Pp->E0 / (2.0 * sqrt(2.0 * T->Ip))));
     double r = sqrt(-2.0 * log(u[1]));
     double kx = sigma * r * cos(2.0 * OR_PI * u[2]);
     double ky = sigma * r * sin(2.0 * OR_PI * u[2]);
@@ -1058,6 +1089,17 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
         w = a / pdf;
         /* node weight, times K for the 1/N over all K nodes' trajectories */
         if (Q->align_kind == OR_ALIGN_QUAD) w *= Q->n_nodes * Q->qw[j % (uint64_t)Q->n_nodes];
+        /* a birth where the field all but vanishes (reached only through   */
+        /* the defensive share: the pulse's ends) has a saddle so far up    */
+        /* the imaginary axis that it overflows; its amplitude is zero in   */
+        /* effect, and it counts as a draw without a root                   */
+        if (!isfinite(kz) || !isfinite(qz) || !isfinite(creal(w)) || !isfinite(cimag(w))) {
+            sok = 1;
+            kz = qz = 0.0;
+            w = 0.0;
+            Sd = 0.0;
+            tt = 0.0;
+        }
     }
     double g[12] = {(double)n0, 0.0, 0.0, qz, kx, ky, kz,
                     orient[0], orient[1], orient[2], creal(w), cimag(w)};
@@ -1142,7 +1184,7 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
     Q.P = or_make_pulse(Pin);
     double* W = (double*)malloc(sizeof(double) * Q.P.nt);
     double* cdf = (double*)malloc(sizeof(double) * Q.P.nt);
-    or_adk_table(Pin, T->Ip, W, cdf);
+    defensive_table(T, Pin, W, cdf);
     Q.W = W;
     Q.cdf = cdf;
     Q.total = cdf[Q.P.nt - 1];
@@ -1209,7 +1251,7 @@ void or_abs_sampling_constants(const or_target_in* T, const or_pulse_in* Pin, in
     Q.P = or_make_pulse(Pin);
     double* W = (double*)malloc(sizeof(double) * Q.P.nt);
     double* cdf = (double*)malloc(sizeof(double) * Q.P.nt);
-    or_adk_table(Pin, T->Ip, W, cdf);
+    defensive_table(T, Pin, W, cdf);
     Q.W = W;
     Q.cdf = cdf;
     Q.total = cdf[Q.P.nt - 1];
