@@ -970,14 +970,17 @@ void or_adk_table(const or_pulse_in* Pin, double Ip, double* W, double* cdf)
 
 /* Time table of the proposal.  Plain: the ADK weights (or_adk_table).    */
 /* Defensive (proposal_mix = eps > 0, a reading): W_n = (1 - eps) e_n /     */
-/* sum e + eps / Nt, a share eps spread uniformly over the grid.  The ADK   */
-/* exponent falls much faster than the SFA amplitude where the field is     */
-/* weak (Keldysh parameter above 1), which gives w = a / pdf a heavy tail;  */
-/* the uniform share bounds the time factor of 1/pdf by Nt dt / eps, and    */
-/* the floor on the k_perp width (proposal_floor) keeps the momentum factor */
-/* bounded where sigma(t0) ~ sqrt|E(t0)| would vanish.  Any eps and floor   */
-/* leave every weighted mean unbiased, since w = a / pdf uses the density  */
-/* actually sampled.                                                       */
+/* sum e + eps u_n, with u_n = 1 / N_u on the N_u grid points where |E(t_n)| */
+/* >= OR_DEF_FIELD E0 and 0 elsewhere.  The ADK exponent falls much faster   */
+/* than the SFA amplitude where the field is weak (Keldysh parameter above  */
+/* 1), which gives w = a / pdf a heavy tail; the uniform share bounds the   */
+/* time factor of 1/pdf there, and the floor on the k_perp width            */
+/* (proposal_floor) keeps the momentum factor bounded.  Below OR_DEF_FIELD   */
+/* E0 (the pulse's ends) both weights are zero in effect and the saddle's   */
+/* imaginary time would overflow, so the share leaves those points out.     */
+/* Any eps and floor leave every weighted mean unbiased, since w = a / pdf  */
+/* uses the density actually sampled.                                       */
+#define OR_DEF_FIELD 1e-2
 static void defensive_table(const or_target_in* T, const or_pulse_in* Pin, double* W,
                             double* cdf)
 {
@@ -986,8 +989,12 @@ static void defensive_table(const or_target_in* T, const or_pulse_in* Pin, doubl
     if (!(eps > 0.0)) return;
     or_pulse P = or_make_pulse(Pin);
     double sum = cdf[P.nt - 1], acc = 0.0;
+    int nu = 0;
+    for (int n = 0; n < P.nt; ++n)
+        nu += fabs(pulse_E_real(&P, P.t_origin + n * P.dt)) >= OR_DEF_FIELD * P.E0;
     for (int n = 0; n < P.nt; ++n) {
-        W[n] = (1.0 - eps) * W[n] / sum + eps / P.nt;
+        int in = fabs(pulse_E_real(&P, P.t_origin + n * P.dt)) >= OR_DEF_FIELD * P.E0;
+        W[n] = (1.0 - eps) * W[n] / sum + (in ? eps / nu : 0.0);
         acc += W[n];
         cdf[n] = acc;
     }

@@ -4,10 +4,12 @@ grid, and the k_perp width has a floor sigma(f E0).  The weights stay
 w = a / pdf with the density actually sampled, so every weighted mean is
 unchanged in expectation while the weights of weak-field births are bounded.
 
-Pins: eps = f = 0 is the plain sampler, bit for bit; w * pdf equals the
-amplitude assembled from the separately pinned pieces, with the mixture
-density written out here; weighted means agree with the plain sampler within
-their statistical error; the uniform share shows up in the birth times."""
+The uniform share covers the grid points where |E(t_n)| >= 1e-2 E0 (below
+that both weights vanish in effect).  Pins: eps = f = 0 is the plain sampler,
+bit for bit; w * pdf equals the amplitude assembled from the separately
+pinned pieces, with the mixture density written out here; weighted means
+agree with the plain sampler within their statistical error; the uniform
+share shows up in the birth times and never below the field threshold."""
 import math
 
 import numpy as np
@@ -35,7 +37,8 @@ def test_weight_is_amplitude_over_the_mixture_density():
     t = _defensive(T)
     d = O.pulse_derived(P)
     Wt, cdf = O.adk_table(P, t["Ip"])
-    nt = len(Wt)
+    Eg = np.abs(O.pulse_E(P, d["t_origin"] + np.arange(len(Wt)) * d["dt"]))
+    inside = Eg >= 1e-2 * d["E0"]
     soa, _, bad = O.sample(t, P, W.fixed(30.0, 10.0), seed=11, n=200)
     assert bad == 0
     s_floor2 = FLOOR * d["E0"] / (2 * math.sqrt(2 * t["Ip"]))
@@ -45,7 +48,7 @@ def test_weight_is_amplitude_over_the_mixture_density():
         a, _, _ = _amplitude(t, P, soa[7:10, j], n0, kx, ky)
         E = abs(O.pulse_E(P, [d["t_origin"] + n0 * d["dt"]])[0])
         sig2 = max(E / (2 * math.sqrt(2 * t["Ip"])), s_floor2)
-        p_t = (1 - EPS) * Wt[n0] / cdf[-1] + EPS / nt
+        p_t = (1 - EPS) * Wt[n0] / cdf[-1] + (EPS / inside.sum() if inside[n0] else 0.0)
         pdf = p_t / d["dt"] * math.exp(-(kx * kx + ky * ky) / (2 * sig2)) / (2 * math.pi * sig2)
         w = soa[10, j] + 1j * soa[11, j]
         assert abs(w * pdf - a) <= 1e-12 * abs(a)     # (a = 0 at the pulse's ends)
@@ -69,11 +72,16 @@ def test_uniform_share_in_the_birth_times():
     the uniform share: their fraction is eps times the fraction of such grid
     points."""
     n = 20000
+    d = O.pulse_derived(P)
     Wt, _ = O.adk_table(P, T["Ip"])
-    weak = Wt < 1e-9 * Wt.max()
-    sd, _, _ = O.sample(_defensive(T), P, W.fixed(0.0), seed=5, n=n)
-    got = weak[sd[0].astype(int)].mean()
-    expect = EPS * weak.mean()
+    Eg = np.abs(O.pulse_E(P, d["t_origin"] + np.arange(len(Wt)) * d["dt"]))
+    inside = Eg >= 1e-2 * d["E0"]
+    weak = (Wt < 1e-9 * Wt.max()) & inside
+    sd, _, bad = O.sample(_defensive(T), P, W.fixed(0.0), seed=5, n=n)
+    born = sd[0].astype(int)
+    got = weak[born].mean()
+    expect = EPS * weak.sum() / inside.sum()
     assert abs(got - expect) <= 5 * math.sqrt(expect * (1 - expect) / n)
+    assert np.all(inside[born]) and bad == 0
     sp, _, _ = O.sample(T, P, W.fixed(0.0), seed=5, n=n)
     assert weak[sp[0].astype(int)].mean() == 0.0
