@@ -146,16 +146,6 @@ typedef struct {
     double centre_alpha[SFHK_MAX_CENTRES];        /* >= 0 */
     int prim_centre[SFHK_MAX_PRIM];               /* 0..n_centres-1 */
     double prim_dir[SFHK_MAX_PRIM][3];            /* SFHK_PRIM_P_DIR: nonzero */
-    /* Defensive proposal (not in the paper; 0 and 0 give the plain sampler):
-     * proposal_mix = eps in [0, 1) mixes the ADK time weights with a uniform
-     * share eps over the N_u grid points where |E(t_n)| >= 1e-2 E0,
-     * W_n = (1 - eps) e_n / sum e + eps / N_u there, and
-     * proposal_floor = f in [0, 1] keeps the k_perp width at least the width
-     * for a field f E0.  The weights stay w = a / pdf of the density sampled
-     * (unbiased); the ADK exponent falls much faster than the SFA amplitude
-     * at weak fields, and the uniform share bounds those births' weights.
-     * A birth whose saddle overflows counts as a draw without a root. */
-    double proposal_mix, proposal_floor;
 } sfhk_target_desc;
 
 /* Pulse (Sec. II.D / III.A): wavelength (nm), peak intensity (W/cm^2),

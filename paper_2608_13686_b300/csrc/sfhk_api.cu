@@ -190,7 +190,7 @@ int ensemble_alloc(sfhk_ensemble* e, long long n, int nt)
     if ((rc = c->alloc(e->phf, sizeof(float2) * nt))) return rc;
     if ((rc = c->alloc(e->vz, sizeof(double) * nt))) return rc;
     if ((rc = c->alloc(e->counters, sizeof(unsigned long long) * 8))) return rc;
-    if ((rc = c->alloc(e->cdf, sizeof(double) * (nt + 2)))) return rc;
+    if ((rc = c->alloc(e->cdf, sizeof(double) * nt))) return rc;
     if ((rc = c->alloc(e->hist, sizeof(int) * nt))) return rc;
     if ((rc = c->alloc(e->inst, sizeof(DevInstance)))) return rc;
     if ((rc = c->alloc(e->qctr, sizeof(unsigned int) * 4))) return rc;
@@ -394,9 +394,6 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
             d->prim_kind[k] < SFHK_PRIM_S || d->prim_kind[k] > SFHK_PRIM_P_DIR)
             return SFHK_E_INVAL;
     if (!std::isfinite(d->pi_azimuth)) return SFHK_E_INVAL;
-    if (!(d->proposal_mix >= 0.0 && d->proposal_mix < 1.0) ||
-        !(d->proposal_floor >= 0.0 && d->proposal_floor <= 1.0))
-        return SFHK_E_INVAL;
     const bool poly = d->kind == SFHK_POT_POLYATOMIC;
     // p-type along a given direction on polyatomic targets only; sigma and
     // pi p-type on diatomic targets only
@@ -573,7 +570,7 @@ int sfhk_sample_initial(sfhk_ctx* c, const sfhk_target* t, const sfhk_pulse* p,
     cudaStream_t s = as_stream(stream);
     unsigned long long* cnt = (unsigned long long*)e->counters.p;
     if (cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 8, s) != cudaSuccess) rc = SFHK_E_CUDA;
-    if (!rc) rc = launch_adk_cdf(*p, t->desc.Ip, t->desc.proposal_mix, (double*)e->cdf.p, s);
+    if (!rc) rc = launch_adk_cdf(*p, t->desc.Ip, (double*)e->cdf.p, s);
     if (!rc)
         rc = launch_sample(*t, *p, *al, e->n, seed, instance, (const double*)e->cdf.p,
                            (double*)e->soa.p, (int*)e->n0.p, cnt + 3, (double*)e->pilot.p, s);

@@ -149,10 +149,7 @@ inline void count_launch(int k = 1) { g_launches.fetch_add((unsigned long long)k
 // sample / sort (sfhk_sample.cu)
 int launch_field_table(const Pulse& P, double* Eh, float* Ehf, cudaStream_t s);
 int launch_phase_table(const Pulse& P, double Ip, double2* ph, float2* phf, cudaStream_t s);
-// cdf: Nt + 2 doubles; with eps > 0 the mixed weights' running sum, in
-// cdf[Nt] the sum of the plain ADK weights and in cdf[Nt + 1] the number of
-// grid points the uniform share covers
-int launch_adk_cdf(const Pulse& P, double Ip, double eps, double* cdf, cudaStream_t s);
+int launch_adk_cdf(const Pulse& P, double Ip, double* cdf, cudaStream_t s);
 // alignment descriptor within its documented ranges
 bool align_valid(const sfhk_align_desc& al);
 // pilot: sample_pilot_doubles() doubles of scratch, used when the target

@@ -58,14 +58,11 @@ __global__ void k_phase_table(double Ip, double t_origin, double dt, int nt, dou
     phf[n] = make_float2((float)c, (float)-s);
 }
 
-// the defensive share of the time proposal covers |E(t_n)| >= kDefField E0
-constexpr double kDefField = 1e-2;
-
 // ADK weights and their inclusive prefix sum, one block of 1024 threads:
 // contiguous chunks, chunk totals scanned in shared memory.
 __global__ void __launch_bounds__(1024) k_adk_cdf(double omega, double E0, double Tp, double cep,
                                                   double t_origin, double dt, int nt, double Ip,
-                                                  double eps, double* cdf)
+                                                  double* cdf)
 {
     __shared__ double part[1024];
     const int tid = threadIdx.x;
@@ -92,36 +89,6 @@ __global__ void __launch_bounds__(1024) k_adk_cdf(double omega, double E0, doubl
     __syncthreads();
     const double off = part[tid];
     for (int n = b; n < e; ++n) cdf[n] += off;
-    if (eps > 0.0) {
-        // defensive mixture: running sum of (1 - eps) e_n / sum e + eps u_n,
-        // u_n = 1 / N_u on the grid points with |E| >= kDefField E0; the plain
-        // sum is kept in cdf[nt] and N_u in cdf[nt + 1] for the density of a
-        // draw.  Inclusion counts per chunk, scanned like the weights.
-        __syncthreads();
-        const double raw = cdf[nt - 1];
-        int cnt = 0;
-        for (int n = b; n < e; ++n)
-            cnt += fabs(field_direct(omega, E0, Tp, cep, t_origin + n * dt)) >= kDefField * E0;
-        part[tid] = (double)cnt;
-        __syncthreads();
-        if (tid == 0) {
-            double run = 0.0;
-            for (int i = 0; i < 1024; ++i) {
-                const double v = part[i];
-                part[i] = run;
-                run += v;
-            }
-            cdf[nt + 1] = run;
-        }
-        __syncthreads();
-        const double nu = cdf[nt + 1];
-        double u = part[tid];
-        for (int n = b; n < e; ++n) {
-            u += fabs(field_direct(omega, E0, Tp, cep, t_origin + n * dt)) >= kDefField * E0;
-            cdf[n] = (1.0 - eps) * (cdf[n] / raw) + eps * (u / nu);
-        }
-        if (tid == 0) cdf[nt] = raw;
-    }
 }
 
 struct SampleParams {
@@ -145,7 +112,6 @@ struct SampleParams {
     int pkind[SFHK_MAX_PRIM];
     double cchi, schi;                        // pi lobe azimuth (cos, sin)
     // polyatomic targets: Euler-angle orientation, primitives on their own centres
-    double mix, sfloor;                       // defensive proposal (0, 0: plain)
     int poly;
     double psi;                               // third Euler angle (FIXED)
     int n_centres;
@@ -191,8 +157,7 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
     const double t0 = S.t_origin + m * S.dt;
     const double Et0 = field_direct(S.omega, S.E0, S.Tp, S.P.cep, t0);
     const double sqrt2Ip = sqrt(2.0 * S.Ip);
-    double sigma = sqrt(fabs(Et0) / (2.0 * sqrt2Ip));
-    if (S.sfloor > 0.0) sigma = fmax(sigma, sqrt(S.sfloor * S.E0 / (2.0 * sqrt2Ip)));
+    const double sigma = sqrt(fabs(Et0) / (2.0 * sqrt2Ip));
     const double rr = sqrt(-2.0 * log(u[1]));
     double sb, cb;
     sincos(2.0 * kPi * u[2], &sb, &cb);
@@ -475,23 +440,13 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
             const double2 eiz = cexp_(make_double2(-Z.y, Z.x));        // e^{iZ}
             const double2 amp = cmul(cdiv(num, den), eiz);
             const double cst = 2.0 * pow(2.0 * S.Ip, 1.5) / 3.0;
-            double Wm = exp(-cst / fabs(Et0));
-            if (S.mix > 0.0)
-                Wm = (1.0 - S.mix) * (Wm / cdf[S.nt]) +
-                     (fabs(Et0) >= kDefField * S.E0 ? S.mix / cdf[S.nt + 1] : 0.0);
+            const double Wm = exp(-cst / fabs(Et0));
             const double pdf = (Wm / total) / S.dt * exp(-kp2 / (2.0 * sigma * sigma)) /
                                (2.0 * kPi * sigma * sigma);
             // the quadrature node's weight K W_k (1 otherwise)
             const double f = side_w *
                              (S.align_kind == SFHK_ALIGN_QUADRATURE ? S.qkw[j % S.n_nodes] : 1.0);
             w = make_double2(f * amp.x / pdf, f * amp.y / pdf);
-            // a saddle that overflowed (a birth where the field all but
-            // vanishes): a draw without a root
-            if (!isfinite(kz) || !isfinite(qz) || !isfinite(w.x) || !isfinite(w.y)) {
-                ok = false;
-                kz = qz = 0.0;
-                w = make_double2(0.0, 0.0);
-            }
         }
     }
     f[0] = (double)m;
@@ -747,11 +702,10 @@ int launch_phase_table(const Pulse& P, double Ip, double2* ph, float2* phf, cuda
     return SFHK_OK;
 }
 
-int launch_adk_cdf(const Pulse& P, double Ip, double eps, double* cdf, cudaStream_t s)
+int launch_adk_cdf(const Pulse& P, double Ip, double* cdf, cudaStream_t s)
 {
     count_launch();
-    k_adk_cdf<<<1, 1024, 0, s>>>(P.omega, P.E0, P.Tp, P.desc.cep, P.t_origin, P.dt, P.nt, Ip,
-                                 eps, cdf);
+    k_adk_cdf<<<1, 1024, 0, s>>>(P.omega, P.E0, P.Tp, P.desc.cep, P.t_origin, P.dt, P.nt, Ip, cdf);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
 }
@@ -840,8 +794,6 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
     }
     S.cchi = std::cos(T.desc.pi_azimuth);
     S.schi = std::sin(T.desc.pi_azimuth);
-    S.mix = T.desc.proposal_mix;
-    S.sfloor = T.desc.proposal_floor;
     S.poly = poly ? 1 : 0;
     S.psi = al.psi;
     S.n_centres = poly ? T.desc.n_centres : 0;

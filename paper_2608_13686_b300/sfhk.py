@@ -46,8 +46,7 @@ class sfhk_target_desc(C.Structure):
                 ("centre_Z0", C.c_double * SFHK_MAX_CENTRES),
                 ("centre_alpha", C.c_double * SFHK_MAX_CENTRES),
                 ("prim_centre", C.c_int * SFHK_MAX_PRIM),
-                ("prim_dir", (C.c_double * 3) * SFHK_MAX_PRIM),
-                ("proposal_mix", C.c_double), ("proposal_floor", C.c_double)]
+                ("prim_dir", (C.c_double * 3) * SFHK_MAX_PRIM)]
 
 
 class sfhk_pulse_desc(C.Structure):
@@ -225,8 +224,6 @@ def target_desc(t: dict) -> sfhk_target_desc:
     for i, u in enumerate(t.get("pdir", ())):
         for a in range(3):
             d.prim_dir[i][a] = u[a]
-    d.proposal_mix = float(t.get("proposal_mix", 0.0))
-    d.proposal_floor = float(t.get("proposal_floor", 0.0))
     return d
 
 

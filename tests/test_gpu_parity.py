@@ -61,8 +61,7 @@ def test_pulse_grid_matches_oracle(S, ctx):
 # ------------------------------------------------------------------ ionization step
 def _target(name):
     """A workload target by name, with '+'-separated variants: sfhk2 (modified
-    saddle), abs (sampling ~ |a|), chi90 (the other 1 pi_u component), def
-    (the defensive proposal: a 5 % uniform share in time, k_perp width floor)."""
+    saddle), abs (sampling ~ |a|), chi90 (the other 1 pi_u component)."""
     base, *variants = name.split("+")
     t = W.TARGETS[base]
     if "sfhk2" in variants:
@@ -71,8 +70,6 @@ def _target(name):
         t = W.abs_sampled(t, 5.0)
     if "chi90" in variants:
         t = W.pi_component(t, 0.5 * np.pi)
-    if "def" in variants:
-        t = dict(t, proposal_mix=0.05, proposal_floor=0.3)
     return t
 
 
@@ -97,8 +94,6 @@ def _target(name):
     ("N2_pi+chi90", W.PULSE_1200, W.fixed(60.0, 30.0), 500, 16, 1),
     ("N2_pi+sfhk2", W.PULSE_1200, W.fixed(90.0, 0.0), 500, 17, 2),
     ("N2_pi+abs", W.PULSE_1200, W.quadrature(6), 400, 18, 0),
-    ("H2+def", W.PULSE_800, W.ISO, 1500, 19, 0),
-    ("N2+def+abs", W.PULSE_1200, W.fixed(30.0), 500, 20, 1),
 ])
 def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
     t = _target(name)
@@ -447,10 +442,3 @@ def test_tapered_stability_filter(S, ctx, name, pulse, align, n):
     S.sfhk_destroy_ensemble(e)
     S.sfhk_destroy_pulse(ph)
     S.sfhk_destroy_target(th)
-
-
-def test_defensive_proposal_options_are_validated(S, ctx):
-    for bad in (dict(W.TARGETS["H2"], proposal_mix=1.0), dict(W.TARGETS["H2"], proposal_mix=-0.1),
-                dict(W.TARGETS["H2"], proposal_floor=1.5)):
-        with pytest.raises(S.SfhkError):
-            S.sfhk_create_target(ctx, bad)
