@@ -229,7 +229,7 @@ def run_reference(args):
     n = 32
     sec, _ = oracle_sample_run(instances, n)
     # each step a bounded sample sized so the whole run stays within minutes
-    per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
+    per_step_s = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
     n = int(max(16, min(100000, n * per_step_s / max(sec, 1e-3))))
     for _ in range(args.warmup):
         oracle_sample_run(instances, n)
