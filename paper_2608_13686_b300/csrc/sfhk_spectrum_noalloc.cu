@@ -6,7 +6,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
-#include <mutex>
 
 #include "sfhk_internal.h"
 
@@ -14,7 +13,6 @@ namespace sfhk {
 namespace {
 
 constexpr size_t kScratchPerPoint = sizeof(double2) + sizeof(double);   // twiddle + window
-constexpr int kMaxDevices = 256;
 
 // Scratch of the no-allocation spectrum: the twiddle table (Nt double2)
 // followed by the windowed samples (Nt doubles).  Every GPU that loads the
@@ -23,32 +21,23 @@ constexpr int kMaxDevices = 256;
 static __device__ __align__(256) unsigned char g_spectrum_scratch[SFHK_NOALLOC_MAX_NT *
                                                                   kScratchPerPoint];
 
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 // Device address of the scratch on the current device.  The array's name is
-// only a host-side stand-in for the symbol; the address has to be looked up
-// once per device, with that device current.
+// only a host-side stand-in for the symbol, so host code has to ask the
+// runtime for the address with the device current.  The lookup allocates
+// nothing and is repeated on every call: an address kept from an earlier call
+// would go stale once the device's primary context is reset or recreated
+// (the module, and with it the array, is then loaded anew).
 int scratch_address(void** out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_spectrum_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        std::fprintf(stderr, "sfhk: cudaGetSymbolAddress of the spectrum scratch failed: %s\n",
+                     cudaGetErrorString(e));
         cudaGetLastError();
         return SFHK_E_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_spectrum_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            std::fprintf(stderr, "sfhk: cudaGetSymbolAddress of the spectrum scratch failed: %s\n",
-                         cudaGetErrorString(e));
-            cudaGetLastError();
-            return SFHK_E_CUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return SFHK_OK;
 }
 
