@@ -1116,11 +1116,12 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
     return sok == 0 ? 0 : 1;
 }
 
-/* Initial points distributed ~ |a| (target sampling 1; the sampling of   */
-/* Sec. II.B, "distributed according to |sin(beta) <W|r.E|psi0>|", with    */
-/* the axis measure in the proposal).  Exact rejection with weight        */
-/* correction on top of the proposal: a draw with weight w is accepted    */
-/* with alpha = min(1, |w|/M) and then carries P alpha-corrected weight    */
+/* Initial points distributed ~ |a| (target sampling 1; Sec. II.B draws    */
+/* the initial points, Euler angles included, with density proportional   */
+/* to |sin(beta) <W| r.E(t_s) |psi0>|; here with the axis measure in the  */
+/* proposal).  Exact rejection with weight correction on top of the        */
+/* proposal: a draw with weight w is accepted with alpha = min(1, |w|/M)  */
+/* and then carries the alpha-corrected weight                            */
 /*   omega = P w / alpha,  P = E[alpha]  (= P M w/|w| whenever |w| <= M),   */
 /* so that E[omega f] over accepted draws is the integral of a f for any  */
 /* M.  M is kappa times the mean |w| over the first half of a pilot of     */
@@ -1130,7 +1131,11 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
 /* attempt k of trajectory j uses draws 3k..3k+2 (attempt 0 = the plain    */
 /* sampler's), its acceptance uniform draw OR_ACC_BASE + k, pilot draw i   */
 /* the trajectory index i with draws OR_PILOT_BASE.. .  A trajectory with */
-/* no acceptance in OR_ATTEMPTS attempts gets w = 0 (invalid).            */
+/* no acceptance in K = OR_ATTEMPTS attempts gets w = 0 (invalid); as     */
+/* every attempt is accepted with the same probability P, that happens    */
+/* with probability (1 - P)^K, and the kept weights are divided by        */
+/* 1 - (1 - P)^K so that the mean over all N trajectories (invalid ones    */
+/* included, the 1/N of the dipole) stays unbiased for any kappa.         */
 #define OR_PILOT 16384
 #define OR_ATTEMPTS 256
 #define OR_ACC_BASE (1u << 20)
@@ -1205,7 +1210,11 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
     Q.qx = qx;
     Q.qw = qw;
     double MP[2] = {0.0, 0.0};
-    if (T->sampling == 1) abs_sampling_constants(&Q, seed, instance, MP);
+    double keep = 0.0;   /* weight factor of an accepted draw: P / (1 - (1-P)^K) */
+    if (T->sampling == 1) {
+        abs_sampling_constants(&Q, seed, instance, MP);
+        if (MP[1] > 0.0) keep = MP[1] / -expm1(OR_ATTEMPTS * log1p(-MP[1]));
+    }
     int bad = 0;
     for (uint64_t jj = 0; jj < n; ++jj) {
         uint64_t j = j_begin + jj;
@@ -1220,8 +1229,8 @@ int or_sample(const or_target_in* T, const or_pulse_in* Pin, int align_kind,
                 double aw = hypot(f[10], f[11]);
                 double alpha = (MP[0] > 0.0) ? fmin(1.0, aw / MP[0]) : 0.0;
                 if (!(alpha > 0.0) || acc_uniform(seed, instance, j, k) >= alpha) continue;
-                f[10] *= MP[1] / alpha;
-                f[11] *= MP[1] / alpha;
+                f[10] *= keep / alpha;
+                f[11] *= keep / alpha;
                 inval = 0;
                 break;
             }

@@ -486,6 +486,11 @@ __device__ __forceinline__ void uniforms_at(const SampleParams& S, long long j, 
 // second half (k_pilot, k_pilot_constants), then k_sample_abs.  Attempt k of trajectory j uses
 // draws 3k..3k+2 (attempt 0 = the plain sampler's draws) and acceptance
 // uniform draw kAccBase + k; pilot draw i uses draws kPilotBase.. of index i.
+// A trajectory still unaccepted after kAttempts = K attempts gets weight 0;
+// every attempt succeeds with the same probability P, so that happens with
+// probability (1 - P)^K and the kept weights carry the extra factor
+// 1 / (1 - (1 - P)^K), which keeps the mean over all N trajectories (the
+// dipole's 1/N counts the unaccepted ones) unbiased for any kappa.
 constexpr int kPilot = 16384;
 constexpr int kAttempts = 256;
 constexpr uint32_t kAccBase = 1u << 20;
@@ -519,7 +524,7 @@ __global__ void k_sample_abs(SampleParams S, const double* __restrict__ cdf,
                              unsigned long long* __restrict__ next)
 {
     const long long n = S.n;
-    const double M = mp[0], P = mp[1];
+    const double M = mp[0], keep = mp[1];
     const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
     long long j = (long long)atomicAdd(next, 1ull);
     int k = 0;
@@ -534,8 +539,8 @@ __global__ void k_sample_abs(SampleParams S, const double* __restrict__ cdf,
                 make_uint4((uint32_t)j, (uint32_t)(j >> 32), S.instance, kAccBase + (uint32_t)k),
                 key);
             if (alpha > 0.0 && u01(r.x, r.y) < alpha) {
-                f[10] *= P / alpha;
-                f[11] *= P / alpha;
+                f[10] *= keep / alpha;
+                f[11] *= keep / alpha;
                 done = ok = true;
             }
         }
@@ -567,7 +572,8 @@ __global__ void k_pilot(SampleParams S, const double* __restrict__ cdf, double* 
     aw[i] = hypot(f[10], f[11]);
 }
 
-// M and P from the pilot |w| (one block of 1024 threads): mp[0] = M, mp[1] = P
+// M and P from the pilot |w| (one block of 1024 threads): mp[0] = M,
+// mp[1] = P / (1 - (1 - P)^kAttempts), the factor of an accepted draw's weight
 __global__ void __launch_bounds__(1024) k_pilot_constants(const double* __restrict__ aw,
                                                           double kappa, double* __restrict__ mp)
 {
@@ -593,8 +599,9 @@ __global__ void __launch_bounds__(1024) k_pilot_constants(const double* __restri
         __syncthreads();
     }
     if (t == 0) {
+        const double P = part[0] / half;
         mp[0] = M;
-        mp[1] = part[0] / half;
+        mp[1] = P > 0.0 ? P / -expm1((double)kAttempts * log1p(-P)) : 0.0;
     }
 }
 

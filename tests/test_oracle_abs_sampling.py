@@ -34,7 +34,8 @@ def test_weight_rule_and_bound():
     first = np.all(sa[0:10] == sp[0:10], axis=0)          # attempt 0 accepted
     assert first.sum() > 0.05 * n
     alpha = np.minimum(1.0, np.abs(wp[first]) / M)
-    assert np.allclose(wa[first], P * wp[first] / alpha, rtol=1e-13, atol=0.0)
+    keep = P / (1.0 - (1.0 - P) ** 256)
+    assert np.allclose(wa[first], keep * wp[first] / alpha, rtol=1e-13, atol=0.0)
 
 
 @pytest.mark.parametrize("align,kappa", [(W.fixed(0.0), 5.0), (W.ISO, 2.0)])
@@ -55,3 +56,32 @@ def test_variance_per_point_is_lower():
     sa, _, _ = O.sample(W.abs_sampled(T, 5.0), P_, W.fixed(0.0), seed=31, n=n)
     sp, _, _ = O.sample(T, P_, W.fixed(0.0), seed=32, n=n)
     assert np.var(_w(sa)) < 0.5 * np.var(_w(sp))
+
+
+def test_unbiased_at_a_large_factor_with_the_attempt_cap():
+    """At kappa = 150 an attempt is accepted with P ~ 0.0064, so about 19 % of
+    the trajectories exhaust their 256 attempts and get weight 0.  Every
+    attempt has the same acceptance probability, so the invalid count is
+    binomial with q = (1 - P)^256, and the kept weights must carry the factor
+    1 / (1 - q) for the mean over all N trajectories to stay unbiased.
+
+    The means compared are of |w| g (the phase of an accepted weight is the
+    proposal's, so E[|omega| g] = int |a| g under both samplers), which have
+    a definite sign and resolve the factor: dropping it (the planted mistake,
+    applied here as the multiplication by 1 - q) moves the g = 1 mean by
+    about 16 standard errors."""
+    kappa, na, npl = 150.0, 3000, 200000
+    ta = W.abs_sampled(T, kappa)
+    _, P = O.abs_sampling_constants(ta, P_, W.fixed(0.0), seed=21)
+    q = (1.0 - P) ** 256
+    assert 0.1 < q < 0.3
+    sa, _, bad = O.sample(ta, P_, W.fixed(0.0), seed=21, n=na)
+    sp, _, _ = O.sample(T, P_, W.fixed(0.0), seed=22, n=npl)
+    assert abs(bad - na * q) <= 5.0 * np.sqrt(na * q * (1.0 - q))
+    funcs = [lambda s: np.ones(s.shape[1]), lambda s: np.abs(s[6]), lambda s: np.abs(s[3])]
+    for i, g in enumerate(funcs):
+        xa, xp = np.abs(_w(sa)) * g(sa), np.abs(_w(sp)) * g(sp)
+        se = np.hypot(np.std(xa) / np.sqrt(na), np.std(xp) / np.sqrt(npl))
+        assert abs(xa.mean() - xp.mean()) <= 4.0 * se
+        if i == 0:
+            assert abs((1.0 - q) * xa.mean() - xp.mean()) >= 8.0 * se
