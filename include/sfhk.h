@@ -103,11 +103,14 @@ enum { SFHK_FP64 = 0, SFHK_MIXED = 1 };
  * draws them from the ADK-time x Gaussian-k_perp x alignment proposal with
  * weight w = a/pdf; SFHK_SAMPLE_ABS_AMPLITUDE distributes them ~ |a|
  * (Sec. II.B) by exact rejection with weight correction on that proposal: a
- * draw is kept with probability alpha = min(1, |w|/M) and weighs P w/alpha,
- * M = sampling_factor x mean |w| and P = mean alpha from a pilot of 16384
- * draws; every weighted mean stays unbiased for any factor, larger factors
- * give more nearly equal weights (lower variance per propagated trajectory)
- * at about 1/P proposal draws per point.
+ * draw is kept with probability alpha = min(1, |w|/M) and weighs
+ * P w / (alpha (1 - (1-P)^256)), M = sampling_factor x mean |w| and P = mean
+ * alpha from a pilot of 16384 draws; a trajectory not accepted within 256
+ * draws gets weight 0 (it happens with probability (1-P)^256, which the
+ * factor 1/(1 - (1-P)^256) of the kept weights makes up for), so every
+ * weighted mean stays unbiased for any factor.  Larger factors give more
+ * nearly equal weights (lower variance per propagated trajectory) at about
+ * 1/P proposal draws per point.
  * prim_kind[k] selects the angular part of primitive k: SFHK_PRIM_S is the
  * s-type exp(-a |r-R_c|^2); SFHK_PRIM_P_SIGMA is the sigma p-type
  * s_c n.(r-R_c) exp(-a |r-R_c|^2), s_c = +1 at +(R/2) n and -1 at -(R/2) n,
@@ -227,6 +230,19 @@ typedef struct {
                                          FP32 rounding of M moves it by a
                                          rounding-level amount instead of a
                                          whole step's contribution. */
+    int check_nonfinite;              /* 1: the synchronising calls on the
+                                         ensemble (sfhk_dipole, sfhk_stats_get)
+                                         return SFHK_E_NUMERIC when more than
+                                         max_nonfinite trajectories stopped on a
+                                         non-finite state or prefactor; 0 (the
+                                         default): no limit, the count is only
+                                         reported.  A non-finite trajectory
+                                         stops contributing at that step either
+                                         way, so the dipole itself stays finite;
+                                         the limit tells a caller that the
+                                         estimate lost more trajectories to
+                                         overflow than it accepts. */
+    uint64_t max_nonfinite;           /* the count tolerated when checking */
 } sfhk_run_opts;
 
 /* Per-ensemble counters of the last propagation. */
@@ -352,13 +368,19 @@ SFHK_API int sfhk_autotune(sfhk_ctx* ctx, sfhk_ensemble* e, const sfhk_run_opts*
 
 /* Dipole v_z(t_n), n = 0..Nt-1, of the last propagation, copied to the host
  * after waiting for it.  nt must equal the pulse's Nt.  Also returns the
- * grid origin and step (either may be NULL).  Errors: SFHK_E_INVAL. */
+ * grid origin and step (either may be NULL).  Errors: SFHK_E_INVAL;
+ * SFHK_E_NUMERIC (nothing written) when that propagation ran with
+ * check_nonfinite and more than max_nonfinite trajectories went non-finite.
+ * sfhk_propagate itself is asynchronous and cannot see the count; the check
+ * happens here and in sfhk_stats_get. */
 SFHK_API int sfhk_dipole(sfhk_ctx* ctx, sfhk_ensemble* e, double* vz_host, size_t nt,
                 double* t_origin, double* dt);
 /* Device pointer of the same dipole (valid until the ensemble is destroyed or
  * propagated again). */
 SFHK_API int sfhk_dipole_device(sfhk_ensemble* e, const double** vz_dev, size_t* nt);
-/* Counters of the last propagation (waits for it). */
+/* Counters of the last propagation (waits for it).  Returns SFHK_E_NUMERIC
+ * under the same condition as sfhk_dipole, and in that case, unlike other
+ * errors, still fills *out, so that the caller sees the counts. */
 SFHK_API int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out);
 /* Final per-trajectory state of the last propagation run with dump_final,
  * 47 x n_traj doubles, field-major: q[3] p[3] M[36] (6x6 row-major,
@@ -434,6 +456,9 @@ typedef struct {
                                    the work still queued goes to the front of the
                                    ring, so short requests overtake long ones      */
     double stability_taper;     /* as in sfhk_run_opts                              */
+    int check_nonfinite;        /* as in sfhk_run_opts, per request: a request     */
+    uint64_t max_nonfinite;     /* with more non-finite trajectories ends with     */
+                                /* status SFHK_E_NUMERIC and no dipole             */
 } sfhk_server_opts;
 
 typedef struct {
@@ -461,6 +486,7 @@ typedef struct {
     size_t spec_capacity;
     double t_submit, t_admit, t_done;
     uint64_t traj_steps, n_filtered, n_unstable;
+    uint64_t n_nonfinite;       /* trajectories stopped on a non-finite state      */
 } sfhk_result;
 
 typedef struct {
@@ -502,9 +528,12 @@ SFHK_API int sfhk_server_stats_get(sfhk_server* s, sfhk_server_stats* out);
  * for every output it wants (n_out doubles each; NULL skips one).
  * Scratch: a fixed file-scope device array of SFHK_NOALLOC_MAX_NT x 24 bytes
  * (768 KiB), held on every GPU that loads the library until the process
- * exits.  The first call on a device looks up that array's device address
- * (once per device, with the device current); it calls no allocator.  Every
- * call shares the one array, so calls that overlap on the GPU (different
+ * exits.  Every call looks up that array's device address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing), so an address is
+ * never reused across a reset of the device's context; the first call on a
+ * device may also load the library's device code there, so make that first
+ * call before any stream capture.  It calls no allocator.  Every call
+ * shares the one array, so calls that overlap on the GPU (different
  * streams, or other host threads) race on it; serialise them.  Each call
  * overwrites all the scratch it reads, so no state carries over.
  * Asynchronous on `stream`.  Errors: SFHK_E_INVAL (nt < 2,

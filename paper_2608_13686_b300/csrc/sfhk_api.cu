@@ -283,7 +283,16 @@ int check_opts(const sfhk_run_opts* o)
     if (o->record_returns && !(o->return_r_in > 0.0 && o->return_r_out > o->return_r_in &&
                                std::isfinite(o->return_r_out)))
         return SFHK_E_INVAL;
+    if (o->check_nonfinite != 0 && o->check_nonfinite != 1) return SFHK_E_INVAL;
     return SFHK_OK;
+}
+
+// the non-finite limit that sfhk_dipole / sfhk_stats_get apply to the
+// ensemble's last propagation
+void set_nonfinite_limit(sfhk_ensemble* e, const sfhk_run_opts& o)
+{
+    e->check_nonfinite = o.check_nonfinite != 0;
+    e->max_nonfinite = (unsigned long long)o.max_nonfinite;
 }
 
 }  // namespace
@@ -697,6 +706,7 @@ int sfhk_propagate(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, void* 
     SFHK_CUDA_TRY(record_event(e->ev_stop, s));
     SFHK_CUDA_TRY(record_event(e->ev_done, s));
     e->have_result = true;
+    set_nonfinite_limit(e, *o);
     return SFHK_OK;
 }
 
@@ -778,6 +788,7 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
             record_event(ens[i]->ev_done, s) != cudaSuccess)
             rc = SFHK_E_CUDA;
         ens[i]->have_result = true;
+        set_nonfinite_limit(ens[i], *o);
     }
     cudaFreeAsync(scratch, s);
     return rc;
@@ -886,6 +897,7 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
         off += e->n_items;
         e->dumped = false;
         e->have_result = true;
+        set_nonfinite_limit(e, b->opts);
     }
     rc = launch_sort_items(b->d_items, (int)b->total_items, b->d_nt, b->d_sorted, b->d_keys,
                            b->d_perm, b->d_hist, b->max_nt, s);
@@ -985,6 +997,11 @@ int sfhk_dipole(sfhk_ctx* c, sfhk_ensemble* e, double* vz_host, size_t nt, doubl
     int rc = set_device(c->device);
     if (rc) return rc;
     SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_done));
+    if (e->check_nonfinite) {
+        unsigned long long h[2] = {0, 0};
+        SFHK_CUDA_TRY(cudaMemcpy(h, e->counters.p, sizeof h, cudaMemcpyDeviceToHost));
+        if (h[1] > e->max_nonfinite) return SFHK_E_NUMERIC;
+    }
     SFHK_CUDA_TRY(cudaMemcpy(vz_host, e->vz.p, sizeof(double) * nt, cudaMemcpyDeviceToHost));
     if (t_origin) *t_origin = e->pulse->t_origin;
     if (dt) *dt = e->pulse->dt;
@@ -1021,6 +1038,9 @@ int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out)
         out->kernel_ms = ms;
     else
         cudaGetLastError();
+    // over the caller's limit: the counters are still returned
+    if (e->have_result && e->check_nonfinite && out->n_nonfinite > e->max_nonfinite)
+        return SFHK_E_NUMERIC;
     return SFHK_OK;
 }
 

@@ -138,6 +138,8 @@ struct Ensemble {
     bool returns_kept = false;
     bool have_result = false;
     bool sampled = false;          // created by the device sampler
+    bool check_nonfinite = false;  // limit of the last propagation's non-finite count
+    unsigned long long max_nonfinite = 0;
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr, ev_done = nullptr;
 };
 

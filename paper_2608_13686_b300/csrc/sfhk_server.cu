@@ -42,7 +42,7 @@ struct Req {
     int nt = 0;
     double t_origin = 0, dt = 0;
     std::vector<double> vz, yield, phase;
-    uint64_t traj_steps = 0, n_filtered = 0, n_unstable = 0;
+    uint64_t traj_steps = 0, n_filtered = 0, n_unstable = 0, n_nonfinite = 0;
 };
 
 size_t bytes_estimate(uint64_t n, int nt)
@@ -271,8 +271,15 @@ void harvest(sfhk_server* S)
             }
             if (cudaStreamSynchronize(S->s) != cudaSuccess) status = SFHK_E_CUDA;
             q->n_filtered = c[0];
+            q->n_nonfinite = c[1];
             q->traj_steps = c[2];
             q->n_unstable = c[4];
+            if (status == SFHK_OK && S->o.check_nonfinite && c[1] > S->o.max_nonfinite) {
+                status = SFHK_E_NUMERIC;       // over the limit: no dipole or spectrum
+                q->vz.clear();
+                q->yield.clear();
+                q->phase.clear();
+            }
             std::lock_guard<std::mutex> lk(S->mu);
             S->st.traj_steps += c[2];
         }
@@ -380,6 +387,7 @@ int copy_result(Req& q, sfhk_result* r)
     r->traj_steps = q.traj_steps;
     r->n_filtered = q.n_filtered;
     r->n_unstable = q.n_unstable;
+    r->n_nonfinite = q.n_nonfinite;
     return SFHK_OK;
 }
 
@@ -395,7 +403,8 @@ int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** o
         !std::isfinite(opts->stability_taper))
         return SFHK_E_INVAL;
     if (!(opts->gamma > 0.0) || opts->prefactor_cutoff < 0.0 || opts->stability_cutoff < 0.0 ||
-        opts->slice_ms < 0.0 || opts->max_pending < 0 || opts->max_active < 0)
+        opts->slice_ms < 0.0 || opts->max_pending < 0 || opts->max_active < 0 ||
+        (opts->check_nonfinite != 0 && opts->check_nonfinite != 1))
         return SFHK_E_INVAL;
     sfhk_server* S = new (std::nothrow) sfhk_server;
     if (!S) return SFHK_E_NOMEM;

@@ -64,7 +64,8 @@ class sfhk_run_opts(C.Structure):
                 ("dump_final", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
                 ("stability_cutoff", C.c_double), ("kernel_variant", C.c_int),
                 ("record_returns", C.c_int), ("return_r_out", C.c_double),
-                ("return_r_in", C.c_double), ("stability_taper", C.c_double)]
+                ("return_r_in", C.c_double), ("stability_taper", C.c_double),
+                ("check_nonfinite", C.c_int), ("max_nonfinite", C.c_uint64)]
 
 
 class sfhk_stats(C.Structure):
@@ -79,7 +80,8 @@ class sfhk_server_opts(C.Structure):
                 ("max_active", C.c_int), ("precision", C.c_int), ("gamma", C.c_double),
                 ("prefactor_cutoff", C.c_double), ("stability_cutoff", C.c_double),
                 ("slice_ms", C.c_double), ("spectrum", C.c_int), ("fifo", C.c_int),
-                ("stability_taper", C.c_double)]
+                ("stability_taper", C.c_double), ("check_nonfinite", C.c_int),
+                ("max_nonfinite", C.c_uint64)]
 
 
 class sfhk_request(C.Structure):
@@ -95,7 +97,7 @@ class sfhk_result(C.Structure):
                 ("phase", C.POINTER(C.c_double)), ("spec_capacity", C.c_size_t),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
                 ("traj_steps", C.c_uint64), ("n_filtered", C.c_uint64),
-                ("n_unstable", C.c_uint64)]
+                ("n_unstable", C.c_uint64), ("n_nonfinite", C.c_uint64)]
 
 
 class sfhk_server_stats(C.Structure):
@@ -240,14 +242,17 @@ def align_desc(a) -> sfhk_align_desc:
 
 def run_opts(precision=SFHK_FP64, gamma=0.5, cutoff=0.0, dump=False, block_threads=0,
              blocks_per_sm=0, stab_cutoff=0.0, kernel_variant=0, returns=None,
-             stab_taper=0.0) -> sfhk_run_opts:
+             stab_taper=0.0, max_nonfinite=None) -> sfhk_run_opts:
     """returns = (r_out, r_in) records each trajectory's first return;
     stab_taper = r > 1 tapers the stability filter between stab_cutoff and
-    r stab_cutoff (0: hard cut)."""
+    r stab_cutoff (0: hard cut); max_nonfinite = n makes sfhk_dipole and
+    sfhk_stats_get fail with SFHK_E_NUMERIC above n non-finite trajectories
+    (None: no limit)."""
     r_out, r_in = returns if returns else (0.0, 0.0)
     return sfhk_run_opts(precision, gamma, cutoff, int(dump), block_threads, blocks_per_sm,
                          stab_cutoff, kernel_variant, int(bool(returns)), r_out, r_in,
-                         stab_taper)
+                         stab_taper, int(max_nonfinite is not None),
+                         int(max_nonfinite or 0))
 
 
 # ------------------------------------------------------------------ C-ABI calls
@@ -381,9 +386,17 @@ def sfhk_dipole_device(ens):
 
 
 def sfhk_stats_get(ens):
+    """Counters of the last propagation.  Over the non-finite limit the call
+    raises SfhkError(SFHK_E_NUMERIC) whose .stats holds the counters."""
     s = sfhk_stats()
-    _check(_load().sfhk_stats_get(ens, C.byref(s)), "sfhk_stats_get")
-    return {f: getattr(s, f) for f, _ in sfhk_stats._fields_}
+    rc = _load().sfhk_stats_get(ens, C.byref(s))
+    d = {f: getattr(s, f) for f, _ in sfhk_stats._fields_}
+    if rc == SFHK_E_NUMERIC:
+        err = SfhkError(rc, "sfhk_stats_get")
+        err.stats = d
+        raise err
+    _check(rc, "sfhk_stats_get")
+    return d
 
 
 def sfhk_returns(ens, n):
@@ -421,9 +434,10 @@ SFHK_NOALLOC_MAX_NT = 32768
 # ------------------------------------------------------------------ serving
 def server_opts(precision=SFHK_MIXED, gamma=0.5, cutoff=0.0, stab_cutoff=0.0, budget=0,
                 max_pending=0, max_active=0, slice_ms=0.0, spectrum=True, fifo=False,
-                stab_taper=0.0):
+                stab_taper=0.0, max_nonfinite=None):
     return sfhk_server_opts(budget, max_pending, max_active, precision, gamma, cutoff,
-                            stab_cutoff, slice_ms, int(spectrum), int(fifo), stab_taper)
+                            stab_cutoff, slice_ms, int(spectrum), int(fifo), stab_taper,
+                            int(max_nonfinite is not None), int(max_nonfinite or 0))
 
 
 def request(target: dict, pulse: dict, align, n_traj, seed=0, instance=0) -> sfhk_request:
@@ -468,7 +482,7 @@ class Result:
                     vz=self.vz[:c.nt].copy(), yield_=self.yield_[:c.n_out].copy(),
                     phase=self.phase[:c.n_out].copy(), t_submit=c.t_submit, t_admit=c.t_admit,
                     t_done=c.t_done, traj_steps=c.traj_steps, n_filtered=c.n_filtered,
-                    n_unstable=c.n_unstable)
+                    n_unstable=c.n_unstable, n_nonfinite=c.n_nonfinite)
 
 
 def sfhk_poll(server, rid, res: Result = None):
