@@ -61,13 +61,17 @@ def test_pulse_grid_matches_oracle(S, ctx):
 # ------------------------------------------------------------------ ionization step
 def _target(name):
     """A workload target by name, with '+'-separated variants: sfhk2 (modified
-    saddle), abs (sampling ~ |a|), chi90 (the other 1 pi_u component)."""
+    saddle), abs (sampling ~ |a|), abs150 (the same at kappa = 150, where
+    about a fifth of the trajectories exhaust their attempts), chi90 (the
+    other 1 pi_u component)."""
     base, *variants = name.split("+")
     t = W.TARGETS[base]
     if "sfhk2" in variants:
         t = W.sfhk2(t)
     if "abs" in variants:
         t = W.abs_sampled(t, 5.0)
+    if "abs150" in variants:
+        t = W.abs_sampled(t, 150.0)
     if "chi90" in variants:
         t = W.pi_component(t, 0.5 * np.pi)
     return t
@@ -94,6 +98,7 @@ def _target(name):
     ("N2_pi+chi90", W.PULSE_1200, W.fixed(60.0, 30.0), 500, 16, 1),
     ("N2_pi+sfhk2", W.PULSE_1200, W.fixed(90.0, 0.0), 500, 17, 2),
     ("N2_pi+abs", W.PULSE_1200, W.quadrature(6), 400, 18, 0),
+    ("H2+abs150", W.PULSE_800, W.fixed(0.0), 400, 21, 0),
 ])
 def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
     t = _target(name)
