@@ -12,9 +12,12 @@ data.  Every other function is pinned by the tests in ``tests/test_oracle_*``.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
+import shutil
 import subprocess
+import tempfile
 import threading
 
 import numpy as np
@@ -51,7 +54,8 @@ def build(force: bool = False) -> str:
 
 class PulseIn(C.Structure):
     _fields_ = [("lambda_nm", C.c_double), ("intensity", C.c_double),
-                ("n_cycles", C.c_double), ("cep", C.c_double), ("dt", C.c_double)]
+                ("n_cycles", C.c_double), ("cep", C.c_double), ("dt", C.c_double),
+                ("t_center", C.c_double)]
 
 
 class TargetIn(C.Structure):
@@ -79,67 +83,110 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        u32p = C.POINTER(C.c_uint32)
-        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
-        L.or_uniforms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, _dp]
-        L.or_pulse_derive.argtypes = [C.POINTER(PulseIn), _dp, C.POINTER(C.c_int)]
-        L.or_pulse_A_real.argtypes = [C.POINTER(PulseIn), C.c_double]
-        L.or_pulse_A_real.restype = C.c_double
-        L.or_pulse_E_real.argtypes = [C.POINTER(PulseIn), C.c_double]
-        L.or_pulse_E_real.restype = C.c_double
-        L.or_pulse_E_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
-        L.or_pulse_A_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
-        L.or_potential.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp]
-        L.or_trajectory.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), _dp, _dp,
-                                    C.c_double, C.c_double, C.c_int, _dp]
-        L.or_hk_det.argtypes = [_dp, C.c_double, _dp]
-        L.or_pi_direction.argtypes = [_dp, C.c_double, _dp]
-        L.or_orbital_norm.argtypes = [C.POINTER(TargetIn)]
-        L.or_orbital_norm.restype = C.c_double
-        L.or_orbital_value.argtypes = [C.POINTER(TargetIn), _dp, _dp]
-        L.or_orbital_value.restype = C.c_double
-        L.or_recomb.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp, C.c_double, _dp]
-        L.or_dipole_matrix_element.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp, _dp]
-        L.or_saddle.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double, _dp]
-        L.or_saddle.restype = C.c_int
-        L.or_tunnel.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
-                                _dp, _dp]
-        L.or_adk_table.argtypes = [C.POINTER(PulseIn), C.c_double, _dp, _dp]
-        L.or_sample.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int, C.c_double,
-                                C.c_double, C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
-                                C.c_uint64, C.c_uint64, _dp, _dp]
-        L.or_quad_nodes.argtypes = [C.c_int, _dp, _dp]
-        L.or_propagate_returns.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
-                                           C.c_double, C.c_double, _dp, C.c_uint64, C.c_double,
-                                           _dp, C.c_double, C.c_double, _dp, C.c_int]
-        L.or_propagate_returns.restype = C.c_int
-        L.or_abs_sampling_constants.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int,
-                                                C.c_double, C.c_double, C.c_double, C.c_int,
-                                                C.c_uint64, C.c_uint32, _dp]
-        L.or_euler_rotation.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
-        L.or_orbital_values.argtypes = [C.POINTER(TargetIn), _dp, _dp, C.c_int64, _dp]
-        L.or_saddle_modified.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
-                                         C.c_double, _dp]
-        L.or_saddle_modified.restype = C.c_int
-        L.or_pulse_Edot_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
-        L.or_sample.restype = C.c_int
-        L.or_propagate.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
-                                   C.c_double, C.c_double, C.c_double, _dp, C.c_uint64,
-                                   C.c_double, _dp, _dp, C.c_int]
-        L.or_stab_taper_weight.argtypes = [C.c_double, C.c_double, C.c_double]
-        L.or_stab_taper_weight.restype = C.c_double
-        L.or_propagate.restype = C.c_int
-        L.or_spectrum.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
-                                  _dp, _dp, _dp, _dp, _dp]
-        _lib = L
+        _lib = _configure(C.CDLL(_LIB))
     return _lib
+
+
+def _configure(L):
+    """Declare the argument and result types of the oracle's exports."""
+    u32p = C.POINTER(C.c_uint32)
+    L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.or_uniforms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, _dp]
+    L.or_pulse_derive.argtypes = [C.POINTER(PulseIn), _dp, C.POINTER(C.c_int)]
+    L.or_pulse_A_real.argtypes = [C.POINTER(PulseIn), C.c_double]
+    L.or_pulse_A_real.restype = C.c_double
+    L.or_pulse_E_real.argtypes = [C.POINTER(PulseIn), C.c_double]
+    L.or_pulse_E_real.restype = C.c_double
+    L.or_pulse_E_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
+    L.or_pulse_A_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
+    L.or_potential.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp]
+    L.or_trajectory.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), _dp, _dp,
+                                C.c_double, C.c_double, C.c_int, _dp]
+    L.or_hk_det.argtypes = [_dp, C.c_double, _dp]
+    L.or_pi_direction.argtypes = [_dp, C.c_double, _dp]
+    L.or_orbital_norm.argtypes = [C.POINTER(TargetIn)]
+    L.or_orbital_norm.restype = C.c_double
+    L.or_orbital_value.argtypes = [C.POINTER(TargetIn), _dp, _dp]
+    L.or_orbital_value.restype = C.c_double
+    L.or_recomb.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp, C.c_double, _dp]
+    L.or_dipole_matrix_element.argtypes = [C.POINTER(TargetIn), _dp, _dp, _dp, _dp]
+    L.or_saddle.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double, _dp]
+    L.or_saddle.restype = C.c_int
+    L.or_tunnel.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
+                            _dp, _dp]
+    L.or_adk_table.argtypes = [C.POINTER(PulseIn), C.c_double, _dp, _dp]
+    L.or_sample.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int, C.c_double,
+                            C.c_double, C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                            C.c_uint64, C.c_uint64, _dp, _dp]
+    L.or_quad_nodes.argtypes = [C.c_int, _dp, _dp]
+    L.or_propagate_returns.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
+                                       C.c_double, C.c_double, _dp, C.c_uint64, C.c_double,
+                                       _dp, C.c_double, C.c_double, _dp, C.c_int]
+    L.or_propagate_returns.restype = C.c_int
+    L.or_abs_sampling_constants.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_int,
+                                            C.c_double, C.c_double, C.c_double, C.c_int,
+                                            C.c_uint64, C.c_uint32, _dp]
+    L.or_euler_rotation.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+    L.or_orbital_values.argtypes = [C.POINTER(TargetIn), _dp, _dp, C.c_int64, _dp]
+    L.or_saddle_modified.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, C.c_double,
+                                     C.c_double, _dp]
+    L.or_saddle_modified.restype = C.c_int
+    L.or_pulse_Edot_complex.argtypes = [C.POINTER(PulseIn), C.c_double, C.c_double, _dp]
+    L.or_sample.restype = C.c_int
+    L.or_propagate.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), C.c_double,
+                               C.c_double, C.c_double, C.c_double, _dp, C.c_uint64,
+                               C.c_double, _dp, _dp, C.c_int]
+    L.or_stab_taper_weight.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.or_stab_taper_weight.restype = C.c_double
+    L.or_propagate.restype = C.c_int
+    L.or_spectrum.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                              _dp, _dp, _dp, _dp, _dp]
+    L.or_ionization_step.argtypes = [C.POINTER(TargetIn), C.POINTER(PulseIn), _dp,
+                                     C.c_double, C.c_double, C.c_double, C.c_int, _dp]
+    L.or_ionization_step.restype = C.c_int
+    return L
+
+
+@contextlib.contextmanager
+def mutated(edits):
+    """Build a copy of the oracle with a planted mistake and make every
+    function of this module use it inside the ``with`` block.
+
+    edits: (old, new) source replacements; each ``old`` must occur exactly
+    once in sfhk_oracle.c.  Tests use this to show that a pin fails when the
+    term it guards is changed.  The copy is compiled like the oracle itself,
+    in a temporary directory that is removed afterwards."""
+    global _lib
+    src = open(_SRC).read()
+    for old, new in edits:
+        if src.count(old) != 1:
+            raise ValueError(f"mutation site not found exactly once: {old!r}")
+        src = src.replace(old, new)
+    d = tempfile.mkdtemp(prefix="oracle_mut_")
+    try:
+        c_path, so_path = os.path.join(d, "mut.c"), os.path.join(d, "libmut.so")
+        with open(c_path, "w") as f:
+            f.write(src)
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                        "-std=gnu11", "-o", so_path, c_path, "-lm"], check=True)
+        with _lock:
+            saved = lib()
+            _lib = _configure(C.CDLL(so_path))
+        try:
+            yield
+        finally:
+            with _lock:
+                _lib = saved
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
 
 
 # ---------------------------------------------------------------- inputs
 def pulse_in(p) -> PulseIn:
-    """p: mapping with lambda_nm, intensity, n_cycles, cep, dt."""
-    return PulseIn(p["lambda_nm"], p["intensity"], p["n_cycles"], p.get("cep", 0.0), p["dt"])
+    """p: mapping with lambda_nm, intensity, n_cycles, cep, dt (+ t_center, the
+    time of the pulse centre, 0 by default)."""
+    return PulseIn(p["lambda_nm"], p["intensity"], p["n_cycles"], p.get("cep", 0.0), p["dt"],
+                   p.get("t_center", 0.0))
 
 
 def target_in(t) -> TargetIn:
@@ -433,3 +480,22 @@ def euler_rotation(phi, theta, psi):
     R = np.zeros(9)
     lib().or_euler_rotation(float(phi), float(theta), float(psi), _p(R))
     return R.reshape(3, 3)
+
+
+def ionization_step(t, p, orient, t0, kx, ky, eta=0):
+    """The sampler's ionization step for one initial point (t0 on or off the
+    grid, k_perp = (kx, ky)): dict with the saddle's tt, kz, the exit qz, the
+    tunnelling action Sd, curv = E(t_s) kappa_z (+ c dE/dt for SFHK2), the
+    dipole element mz = <kappa|z|psi0> and the amplitude a; None without a
+    saddle root.  eta = +-1 picks the emitting centre of an SFHK2 target."""
+    out = np.zeros(11)
+    rc = lib().or_ionization_step(C.byref(target_in(t)), C.byref(pulse_in(p)),
+                                  _p(np.asarray(orient, float).copy()), float(t0), float(kx),
+                                  float(ky), int(eta), _p(out))
+    if rc < 0:
+        raise ValueError("eta must be +-1 for an SFHK2 target")
+    if rc:
+        return None
+    return dict(tt=out[0], kz=out[1], qz=out[2], Sd=complex(out[3], out[4]),
+                curv=complex(out[5], out[6]), mz=complex(out[7], out[8]),
+                a=complex(out[9], out[10]))

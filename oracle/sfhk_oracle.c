@@ -56,6 +56,9 @@ typedef struct {
     double n_cycles;    /* sin^2 envelope: total duration in cycles    */
     double cep;         /* carrier-envelope phase (rad)                */
     double dt;          /* time step (a.u.)                            */
+    double t_center;    /* time of the pulse centre (0: the centred     */
+                        /* axis of the reading below); every time of    */
+                        /* the method moves with it                     */
 } or_pulse_in;
 
 enum { OR_POT_MOLECULE = 0, OR_POT_HARMONIC = 1, OR_POT_POLY = 2 };
@@ -164,9 +167,12 @@ void or_uniforms(uint64_t seed, uint32_t instance, uint64_t j, double u[6])
 /*   A(t) = -(E0/omega) cos^2(pi t/Tp) sin(omega t + cep), E = -dA/dt,   */
 /*   linear polarisation along z.                                        */
 /* Time grid t_n = -Tp/2 + n dt, n = 0..Nt-1, Nt = floor(Tp/dt) + 1.      */
+/* A pulse centred at t_c instead (t_center; a test of the time-origin    */
+/* invariance of the dipole) is A(t - t_c), E(t - t_c) on the grid         */
+/* t_n = t_c - Tp/2 + n dt.                                               */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    double omega, E0, Tp, cep, dt, t_origin;
+    double omega, E0, Tp, cep, dt, t_origin, tc;
     int nt;
 } or_pulse;
 
@@ -176,7 +182,7 @@ void or_pulse_derive(const or_pulse_in* in, double out[6], int* nt)
     double E0 = sqrt(in->intensity / 3.50944758e16);
     double Tp = in->n_cycles * 2.0 * OR_PI / omega;
     out[0] = omega; out[1] = E0; out[2] = Tp; out[3] = in->cep; out[4] = in->dt;
-    out[5] = -0.5 * Tp;
+    out[5] = in->t_center - 0.5 * Tp;
     *nt = (int)floor(Tp / in->dt * (1.0 + 1e-12)) + 1;
 }
 
@@ -184,13 +190,14 @@ static or_pulse or_make_pulse(const or_pulse_in* in)
 {
     double d[6]; int nt;
     or_pulse_derive(in, d, &nt);
-    or_pulse P = {d[0], d[1], d[2], d[3], d[4], d[5], nt};
+    or_pulse P = {d[0], d[1], d[2], d[3], d[4], d[5], in->t_center, nt};
     return P;
 }
 
 /* A(tau) and E(tau) for complex tau, straight from the definition above.  */
 static cplx pulse_A(const or_pulse* P, cplx tau)
 {
+    tau -= P->tc;
     cplx c = ccos(OR_PI * tau / P->Tp);
     return -(P->E0 / P->omega) * c * c * csin(P->omega * tau + P->cep);
 }
@@ -200,6 +207,7 @@ static cplx pulse_E(const or_pulse* P, cplx tau)
     /* E = -dA/dtau, differentiated by hand:
      * dA/dtau = -(E0/w)[ -(pi/Tp) sin(2 pi tau/Tp) sin(w tau+cep)
      *                    + w cos^2(pi tau/Tp) cos(w tau+cep) ]              */
+    tau -= P->tc;
     cplx c = ccos(OR_PI * tau / P->Tp);
     cplx s2 = csin(2.0 * OR_PI * tau / P->Tp);
     cplx ph = P->omega * tau + P->cep;
@@ -211,6 +219,7 @@ static cplx pulse_E(const or_pulse* P, cplx tau)
  *   - (2 pi^2 E0 / (w Tp^2)) cos(2 pi tau/Tp) sin(ph),  ph = w tau + cep.   */
 static cplx pulse_Edot(const or_pulse* P, cplx tau)
 {
+    tau -= P->tc;
     cplx c = ccos(OR_PI * tau / P->Tp);
     cplx s2 = csin(2.0 * OR_PI * tau / P->Tp);
     cplx c2 = ccos(2.0 * OR_PI * tau / P->Tp);
@@ -229,14 +238,14 @@ void or_pulse_Edot_complex(const or_pulse_in* in, double tr, double ti, double o
 double or_pulse_A_real(const or_pulse_in* in, double t)
 {
     or_pulse P = or_make_pulse(in);
-    if (fabs(t) > 0.5 * P.Tp) return 0.0;
+    if (fabs(t - P.tc) > 0.5 * P.Tp) return 0.0;
     return creal(pulse_A(&P, t));
 }
 
 double or_pulse_E_real(const or_pulse_in* in, double t)
 {
     or_pulse P = or_make_pulse(in);
-    if (fabs(t) > 0.5 * P.Tp) return 0.0;
+    if (fabs(t - P.tc) > 0.5 * P.Tp) return 0.0;
     return creal(pulse_E(&P, t));
 }
 
@@ -256,7 +265,7 @@ void or_pulse_A_complex(const or_pulse_in* in, double tr, double ti, double out[
 
 static double pulse_E_real(const or_pulse* P, double t)
 {
-    if (fabs(t) > 0.5 * P->Tp) return 0.0;
+    if (fabs(t - P->tc) > 0.5 * P->Tp) return 0.0;
     return creal(pulse_E(P, t));
 }
 
@@ -934,6 +943,75 @@ void or_tunnel(const or_pulse_in* Pin, double Ip, double t0, double tt, const do
     out[0] = qz; out[1] = creal(S); out[2] = cimag(S);
 }
 
+/* The ionization step for one initial point (Sec. II.A, Eqs. 1-2):      */
+/* the saddle t_s = t0 + i tt with k_z (Eq. 2; for SFHK2, target          */
+/* ionization 1, the modified saddle of Sec. III.D with c = eta (R/2) n_z),*/
+/* the tunnel exit q_z and the tunnelling action S_down (text after Eq. 2),*/
+/* and the amplitude of the second line of Eq. 1,                         */
+/*   a = side_w E(t_s) <kappa| z |psi0> / sqrt(curv) e^{i(S_down + k.q0)}, */
+/* kappa = k + A(t_s) - A(t0), curv = E(t_s) kappa_z + c dE/dt(t_s) (the   */
+/* curvature of the whole phase at the saddle; E kappa_z for SFHK1), the   */
+/* principal square root (reading); k.q0 = k_z q_z, the exit lying on the  */
+/* polarisation axis.  `only` >= 0 keeps one centre's part of the dipole   */
+/* element (SFHK2).  Returns 0, or 1 when the saddle has no root.          */
+typedef struct {
+    double tt, kz, qz;
+    cplx Sd, curv, mz, a;
+} or_ionization;
+
+static int ionization_step(const or_target_in* T, const or_pulse* Pp, double N,
+                           const double orient[3], double t0, double kx, double ky, double cmod,
+                           int only, double side_w, or_ionization* out)
+{
+    double tt = 0.0, kz = 0.0, qz = 0.0;
+    cplx Sd = 0.0;
+    int sok = (T->ionization == 1)
+                  ? saddle_modified(Pp, T->Ip, t0, kx * kx + ky * ky, cmod, &tt, &kz)
+                  : saddle(Pp, T->Ip, t0, kx * kx + ky * ky, &tt, &kz);
+    memset(out, 0, sizeof *out);
+    if (sok != 0) return 1;
+    double k[3] = {kx, ky, kz};
+    tunnel_exit_and_action(Pp, T->Ip, t0, tt, k, &qz, &Sd);
+    cplx ts = t0 + I * tt;
+    cplx Es = pulse_E(Pp, ts);
+    cplx kap[3] = {kx, ky, kz + pulse_A(Pp, ts) - creal(pulse_A(Pp, t0))};
+    cplx mz;
+    dipole_matrix_element(T, N, orient, kap, only, &mz);
+    cplx curv = Es * kap[2] + cmod * pulse_Edot(Pp, ts);
+    out->tt = tt;
+    out->kz = kz;
+    out->qz = qz;
+    out->Sd = Sd;
+    out->curv = curv;
+    out->mz = mz;
+    out->a = side_w * Es * mz / csqrt(curv) * cexp(I * (Sd + kz * qz));
+    return 0;
+}
+
+/* The same for the tests: orient is the axis (or the Euler angles of a    */
+/* polyatomic target); eta = +-1 picks the emitting centre of an SFHK2      */
+/* target (weight 1), 0 for SFHK1.  out: tt, kz, qz, S_down (re, im),     */
+/* curv (re, im), <kappa|z|psi0> (re, im), a (re, im).                    */
+int or_ionization_step(const or_target_in* T, const or_pulse_in* Pin, const double orient[3],
+                       double t0, double kx, double ky, int eta, double out[11])
+{
+    or_pulse P = or_make_pulse(Pin);
+    double cmod = 0.0;
+    int only = -1;
+    if (T->ionization == 1) {
+        if (eta != 1 && eta != -1) return -1;
+        only = (eta > 0) ? 1 : 0;
+        double nz = (T->kind == OR_POT_POLY) ? 0.0 : orient[2];
+        cmod = eta * 0.5 * T->R * nz;
+    }
+    or_ionization ion;
+    int rc = ionization_step(T, &P, orbital_norm(T), orient, t0, kx, ky, cmod, only, 1.0, &ion);
+    double v[11] = {ion.tt, ion.kz, ion.qz, creal(ion.Sd), cimag(ion.Sd), creal(ion.curv),
+                    cimag(ion.curv), creal(ion.mz), cimag(ion.mz), creal(ion.a), cimag(ion.a)};
+    for (int i = 0; i < 11; ++i) out[i] = v[i];
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Initial ensemble (Sec. II.A sampling paragraph and Eq. 6), in the     */
 /* proposal form: t0 drawn on the time grid with probability             */
@@ -1077,19 +1155,14 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
         cmod = eta * 0.5 * T->R * cos(th);
         side_w = Q->eta_force ? 1.0 : 2.0;
     }
-    int sok = (T->ionization == 1)
-                  ? saddle_modified(Pp, T->Ip, t0, kx * kx + ky * ky, cmod, &tt, &kz)
-                  : saddle(Pp, T->Ip, t0, kx * kx + ky * ky, &tt, &kz);
+    or_ionization ion;
+    int sok = ionization_step(T, Pp, Q->N, orient, t0, kx, ky, cmod, only, side_w, &ion);
     if (sok == 0) {
-        double k[3] = {kx, ky, kz};
-        tunnel_exit_and_action(Pp, T->Ip, t0, tt, k, &qz, &Sd);
-        cplx ts = t0 + I * tt;
-        cplx Es = pulse_E(Pp, ts);
-        cplx kap[3] = {kx, ky, kz + pulse_A(Pp, ts) - creal(pulse_A(Pp, t0))};
-        cplx mz;
-        dipole_matrix_element(T, Q->N, orient, kap, only, &mz);
-        cplx curv = Es * kap[2] + cmod * pulse_Edot(Pp, ts);
-        cplx a = side_w * Es * mz / csqrt(curv) * cexp(I * (Sd + kz * qz));
+        tt = ion.tt;
+        kz = ion.kz;
+        qz = ion.qz;
+        Sd = ion.Sd;
+        cplx a = ion.a;
         double pdf = (Q->W[n0] / Q->total) / Pp->dt
                      * exp(-(kx * kx + ky * ky) / (2.0 * sigma * sigma))
                      / (2.0 * OR_PI * sigma * sigma);
