@@ -32,9 +32,10 @@
 //   FP64:  everything in double.
 //   MIXED: q, p, M, the stage arithmetic, the determinant and the
 //          recombination element in float; q and p accumulated as two-float
-//          pairs (compensated RK4 update), the action S as a two-float pair,
-//          its phase reduced modulo 2 pi in two-float before sincos, the warp
-//          sum as two-float, the cross-warp reduction in FP64 atomics.
+//          pairs kept normalised at every step (compensated RK4 update), the
+//          action S as a two-float pair, its phase reduced modulo 2 pi in
+//          two-float before sincos, the warp sum as two-float, the
+//          cross-warp reduction in FP64 atomics.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -169,36 +170,38 @@ __device__ __forceinline__ R max_abs_M(const Mono<R>& M)
     return fmax3(a, b, fmax(c, d));
 }
 
-// (hi, lo) += x with Dekker's FastTwoSum; lo is left unnormalised (it only
-// collects rounding errors, a few ulp of hi) and folded back by renorm()
-// every 32 steps of the trajectory.
+// (hi, lo) += x, keeping the pair normalised (|lo| <= ulp(hi)/2, hi the
+// correctly rounded value of hi + lo): the increment first takes up the low
+// part, t = x + lo, and Dekker's FastTwoSum then splits hi + t into the new
+// pair.  The stage arithmetic reads only hi, so hi must carry the pair's
+// value at every step: with the low part left to collect rounding errors
+// over many steps, hi lags the true state by several ulp, and a chaotic
+// trajectory amplifies that lag (measured on an H2 trajectory that ends with
+// max |M| = 2e3: 5e-4 relative error of its prefactor against 3e-5 with
+// the pair kept normalised, the floor set by the FP32 force evaluation).
+// Same four operations as the unnormalised update; the rounding of t loses
+// about an ulp of the increment, as its FP32 evaluation already does.
 __device__ __forceinline__ void acc2(float& hi, float& lo, float x)
 {
-    const float s = __fadd_rn(hi, x);
-    const float e = __fsub_rn(x, __fsub_rn(s, hi));
+    const float t = __fadd_rn(x, lo);
+    const float s = __fadd_rn(hi, t);
+    lo = __fsub_rn(t, __fsub_rn(s, hi));
     hi = s;
-    lo = __fadd_rn(lo, e);
 }
-// the same for two pairs at once (f32x2); s - hi and x - t as FMAs with -1,
-// which round exactly like the subtractions
+// the same for two pairs at once (f32x2); s - hi and t - (s - hi) as FMAs
+// with -1, which round exactly like the subtractions
 __device__ __forceinline__ void acc2x2(float& h0, float& h1, float& l0, float& l1, float x0,
                                        float x1)
 {
     const float2 m1 = make_float2(-1.0f, -1.0f);
-    const float2 hi = make_float2(h0, h1), x = make_float2(x0, x1);
-    const float2 s = __fadd2_rn(hi, x);
-    const float2 e = __ffma2_rn(__ffma2_rn(hi, m1, s), m1, x);
-    const float2 lo = __fadd2_rn(make_float2(l0, l1), e);
+    const float2 hi = make_float2(h0, h1);
+    const float2 t = __fadd2_rn(make_float2(x0, x1), make_float2(l0, l1));
+    const float2 s = __fadd2_rn(hi, t);
+    const float2 lo = __ffma2_rn(__ffma2_rn(hi, m1, s), m1, t);
     h0 = s.x;
     h1 = s.y;
     l0 = lo.x;
     l1 = lo.y;
-}
-__device__ __forceinline__ void renorm(float& hi, float& lo)
-{
-    const float s = __fadd_rn(hi, lo);
-    lo = __fsub_rn(lo, __fsub_rn(s, hi));
-    hi = s;
 }
 
 template <typename R>
@@ -920,16 +923,6 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                 }
                 if constexpr (MIXED) {
                     acc2(S, Sl, dS);
-                    // fold the low parts back every 32 of this trajectory's own
-                    // steps, so its arithmetic does not depend on its work item
-                    if ((steps & 31) == 0) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            renorm(q[a], ql[a]);
-                            renorm(p[a], pl[a]);
-                        }
-                        renorm(S, Sl);
-                    }
                 } else {
                     S += dS;
                 }
