@@ -75,23 +75,59 @@ def test_prefactor_filter_drops_from_threshold_on():
     assert bad >= 1 and np.all(fin_f[46][fin_f[46] != 0] == 1)
 
 
-def test_stability_filter_removes_unresolved_trajectories():
-    """Trajectories beyond the workloads' stability filter (max|M| > 1e3) are
-    not resolved by RK4 at dt = 0.05: halving dt changes the unfiltered H2
-    dipole several-fold, the filtered one far less."""
-    t, p = W.TARGETS["H2"], W.PULSE_800
-    p2 = dict(p)
-    p2["dt"] = 0.5 * p["dt"]
-    soa, _, _ = O.sample(t, p, W.fixed(0.0), seed=12, n=1000)
+def _dt_change(t, p, al, n, seed, **filt):
+    """Relative change of the n-trajectory dipole when dt is halved (the same
+    births on the finer grid, the finer dipole read at the coarser times)."""
+    p2 = dict(p, dt=0.5 * p["dt"])
+    soa, _, _ = O.sample(t, p, al, seed=seed, n=n)
     soa2 = soa.copy()
-    soa2[0] = 2 * soa[0]            # same birth times on the finer grid
+    soa2[0] = 2 * soa[0]
+    v1, _, _ = O.propagate(t, p, soa, W.GAMMA, **filt)
+    v2, _, _ = O.propagate(t, p2, soa2, W.GAMMA, **filt)
+    b = v2[::2][: len(v1)]
+    return float(np.linalg.norm(v1 - b) / np.linalg.norm(b))
 
-    def conv(stab):
-        v1, _, _ = O.propagate(t, p, soa, W.GAMMA, cutoff=W.CUTOFF, stab_cutoff=stab)
-        v2, _, _ = O.propagate(t, p2, soa2, W.GAMMA, cutoff=W.CUTOFF, stab_cutoff=stab)
-        a, b = v1, v2[::2][: len(v1)]
-        return np.linalg.norm(a - b) / np.linalg.norm(b)
 
-    unfiltered, filtered = conv(0.0), conv(W.STAB_CUTOFF)
+def _study():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "dt_resolution.json")))["cases"]
+
+
+FILT = dict(cutoff=W.CUTOFF, stab_cutoff=W.STAB_CUTOFF, stab_taper=W.STAB_TAPER)
+
+
+def test_filtered_n2_dipole_is_resolved_at_the_prescribed_step():
+    """N2 (1200 nm, cos^2 axis) with the workloads' filters: halving dt moves
+    a 1000-trajectory dipole by less than 2 % of its Monte Carlo noise at that
+    size (c_noise / sqrt(N), c_noise from the 2e4-trajectory oracle study in
+    tests/golden/dt_resolution.json, where the change was 1.6e-3 of the
+    noise).  With the prefactor filter only, the unresolved chaotic
+    trajectories move it by a sizeable fraction of the noise."""
+    n = 1000
+    c_noise = _study()["N2"]["workloads"]["c_noise"]
+    noise = c_noise / np.sqrt(n)
+    t, p, al = W.TARGETS["N2"], W.PULSE_1200, W.COS2
+    assert _dt_change(t, p, al, n, 12, **FILT) <= 0.02 * noise
+    assert _dt_change(t, p, al, n, 12, cutoff=W.CUTOFF) >= 0.3 * noise
+
+
+def test_stability_filter_removes_unresolved_trajectories():
+    """H2 along the field: the trajectories beyond the stability filter
+    (max|M| > 1e3) are not resolved by RK4 at dt = 0.05, and halving dt
+    moves the prefactor-filtered dipole several-fold.  With the workloads'
+    filters the change is much smaller but, per trajectory, of the size of
+    the Monte Carlo spread (head-on passes through the softened nuclei are
+    under-resolved without a large |M|; the 2e4-trajectory study measured a
+    change of 0.9 times the sample noise, consistent with zero in the mean):
+    it stays below 1.5 times the noise at N = 1000."""
+    n = 1000
+    study = _study()["H2"]
+    noise = study["workloads"]["c_noise"] / np.sqrt(n)
+    t, p, al = W.TARGETS["H2"], W.PULSE_800, W.fixed(0.0)
+    unfiltered = _dt_change(t, p, al, n, 12, cutoff=W.CUTOFF)
+    filtered = _dt_change(t, p, al, n, 12, **FILT)
     assert unfiltered > 1.0
     assert filtered < 0.25 * unfiltered
+    assert filtered <= 1.5 * noise
