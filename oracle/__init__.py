@@ -68,7 +68,8 @@ class TargetIn(C.Structure):
                 ("n_centres", C.c_int), ("cpos", (C.c_double * 3) * 8),
                 ("cZinf", C.c_double * 8), ("cZ0", C.c_double * 8), ("calpha", C.c_double * 8),
                 ("pcentre", C.c_int * 8), ("pdir", (C.c_double * 3) * 8),
-                ("proposal_mix", C.c_double), ("proposal_floor", C.c_double)]
+                ("proposal_mix", C.c_double), ("proposal_floor", C.c_double),
+                ("origin", C.c_double * 3)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -219,6 +220,8 @@ def target_in(t) -> TargetIn:
             T.pdir[i][a] = d[a]
     T.proposal_mix = float(t.get("proposal_mix", 0.0))
     T.proposal_floor = float(t.get("proposal_floor", 0.0))
+    for a, x in enumerate(t.get("origin", (0.0, 0.0, 0.0))):
+        T.origin[a] = float(x)
     return T
 
 

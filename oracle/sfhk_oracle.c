@@ -103,6 +103,10 @@ typedef struct {
                             /* proposal, uniform over the grid              */
     double proposal_floor;  /* f in [0, 1]: the k_perp width is at least    */
                             /* sigma(f E0), the width for a field f E0      */
+    double origin[3];       /* lab position of the molecule: every centre   */
+                            /* and primitive moved by it, the tunnel exit   */
+                            /* measured from it (0: the molecule at the     */
+                            /* origin, as the paper places it)              */
 } or_target_in;
 
 /* ------------------------------------------------------------------ */
@@ -319,12 +323,14 @@ static void make_frame(const or_target_in* T, const double orient[3], or_frame* 
             F->alpha[i] = T->calpha[i];
         }
         for (int a = 0; a < 3; ++a) F->nhat[a] = F->Rot[3 * a + 2];
+        for (int i = 0; i < F->nc; ++i)
+            for (int a = 0; a < 3; ++a) F->C[i][a] += T->origin[a];
         return;
     }
     F->nc = 2;
     for (int i = 0; i < 2; ++i) {
         double sign = (i == 0) ? 1.0 : -1.0;
-        for (int a = 0; a < 3; ++a) F->C[i][a] = sign * 0.5 * T->R * orient[a];
+        for (int a = 0; a < 3; ++a) F->C[i][a] = sign * 0.5 * T->R * orient[a] + T->origin[a];
         F->Zinf[i] = T->Zinf;
         F->dZ[i] = T->Z0 - T->Zinf;
         F->alpha[i] = T->alpha;
@@ -951,9 +957,10 @@ void or_tunnel(const or_pulse_in* Pin, double Ip, double t0, double tt, const do
 /*   a = side_w E(t_s) <kappa| z |psi0> / sqrt(curv) e^{i(S_down + k.q0)}, */
 /* kappa = k + A(t_s) - A(t0), curv = E(t_s) kappa_z + c dE/dt(t_s) (the   */
 /* curvature of the whole phase at the saddle; E kappa_z for SFHK1), the   */
-/* principal square root (reading); k.q0 = k_z q_z, the exit lying on the  */
-/* polarisation axis.  `only` >= 0 keeps one centre's part of the dipole   */
-/* element (SFHK2).  Returns 0, or 1 when the saddle has no root.          */
+/* principal square root (reading); q0 = origin + q_z z^, the exit lying   */
+/* on the polarisation axis through the molecule's position (k.q0 = k_z q_z */
+/* for a molecule at the origin).  `only` >= 0 keeps one centre's part of  */
+/* the dipole element (SFHK2).  Returns 0, or 1 when the saddle has no root. */
 typedef struct {
     double tt, kz, qz;
     cplx Sd, curv, mz, a;
@@ -984,7 +991,8 @@ static int ionization_step(const or_target_in* T, const or_pulse* Pp, double N,
     out->Sd = Sd;
     out->curv = curv;
     out->mz = mz;
-    out->a = side_w * Es * mz / csqrt(curv) * cexp(I * (Sd + kz * qz));
+    const double kq = kx * T->origin[0] + ky * T->origin[1] + kz * (T->origin[2] + qz);
+    out->a = side_w * Es * mz / csqrt(curv) * cexp(I * (Sd + kq));
     return 0;
 }
 
@@ -1181,7 +1189,7 @@ static int propose(const or_proposal* Q, uint64_t j, const double u[6], double f
             tt = 0.0;
         }
     }
-    double g[12] = {(double)n0, 0.0, 0.0, qz, kx, ky, kz,
+    double g[12] = {(double)n0, T->origin[0], T->origin[1], T->origin[2] + qz, kx, ky, kz,
                     orient[0], orient[1], orient[2], creal(w), cimag(w)};
     for (int q = 0; q < 12; ++q) f[q] = g[q];
     *tt_out = tt;
@@ -1518,7 +1526,7 @@ static int propagate_all(const or_target_in* T, const or_pulse_in* Pin, double g
 #endif
     double* part = (double*)calloc((size_t)nthr * P.nt, sizeof(double));
 #ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 16) num_threads(nthr)
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthr)
 #endif
     for (int64_t j = 0; j < (int64_t)n; ++j) {
         int tid = 0;

@@ -15,7 +15,10 @@ what the physics and the paper fix, not by re-deriving the oracle's formulas:
   sqrt(2 Ip + k_perp^2) exp(-2 (2 Ip + k_perp^2)^{3/2} / (3 |E|)) at small
   Keldysh parameter (the tunnelling exponent and the prefactor's power);
 * the SFHK2 Gaussian-integration factor against a finite-difference
-  derivative of the modified saddle function (Sec. III.D, Eq. 9).
+  derivative of the modified saddle function (Sec. III.D, Eq. 9);
+* translation invariance perpendicular to the field: the k.q0 phase of the
+  amplitude (Eq. 1) against the e^{-i kappa.r} of its dipole element and
+  the coherent states of the recombination element.
 
 Each test also builds the oracle with the term it guards changed (a planted
 mistake, oracle.mutated) and checks that the pin then fails.
@@ -36,6 +39,7 @@ FLIP_SDOWN_REAL = [("*Sdown = Ip * (t0 + I * tt) - (-I * intK);",
 DROP_SQRT = [("out->a = side_w * Es * mz / csqrt(curv)", "out->a = side_w * Es * mz")]
 FLIP_TUNNEL_EXPONENT = [("*Sdown = Ip * (t0 + I * tt) - (-I * intK);",
                          "*Sdown = Ip * (t0 - I * tt) - (-I * intK);")]
+FLIP_KQ = [("cexp(I * (Sd + kq))", "cexp(I * (Sd - kq))")]
 DROP_CURVATURE_TERM = [("cplx curv = Es * kap[2] + cmod * pulse_Edot(Pp, ts);",
                         "cplx curv = Es * kap[2];")]
 
@@ -266,3 +270,35 @@ def test_sfhk2_curvature_is_the_derivative_of_the_modified_saddle_function():
     with O.mutated(DROP_CURVATURE_TERM):
         assert check() > 1e-3
     assert d["nt"] > 0
+
+
+# ------------------------------------------------------------------ translation
+def _translated_dipole(origin, n=256):
+    t = dict(W.TARGETS["H2"], origin=origin)
+    soa, _, _ = O.sample(t, W.PULSE_800, W.fixed(30.0, 40.0), seed=9, n=n)
+    vz, _, _ = O.propagate(t, W.PULSE_800, soa, GAMMA, cutoff=CUT, stab_cutoff=STAB,
+                           stab_taper=TAPER)
+    return vz, soa
+
+
+def test_dipole_is_invariant_under_a_translation_across_the_field():
+    """The molecule moved by d = (2.5, -1.5, 0), perpendicular to the
+    polarisation: E(t).r does not change, so the length-gauge Hamiltonian is
+    exactly translated and v_z must be unchanged.  In the method that takes
+    three conventions agreeing: the dipole element <kappa| z |psi0> of the
+    moved orbital gains e^{-i k_perp.d}, the amplitude's e^{i k.q0} (Eq. 1,
+    the exit q0 moving with the molecule) gains e^{+i k_perp.d}, and the
+    recombination element of the moved orbital with the moved coherent state
+    is unchanged.  (Along the field the SFA dipole is not invariant: the
+    bound state's Stark phase E(t).d is left out of <psi0 e^{i Ip t}|.)
+
+    Planted mistake: the k.q0 phase with the opposite sign, which leaves the
+    time origin, the cutoff and the static limit untouched."""
+    v0, s0 = _translated_dipole((0.0, 0.0, 0.0))
+    v1, s1 = _translated_dipole((2.5, -1.5, 0.0))
+    assert np.allclose(s1[1:4] - s0[1:4], np.array([[2.5], [-1.5], [0.0]]), atol=1e-12)
+    assert _rel(v1, v0) <= 1e-10
+    with O.mutated(FLIP_KQ):
+        m0, _ = _translated_dipole((0.0, 0.0, 0.0))
+        m1, _ = _translated_dipole((2.5, -1.5, 0.0))
+    assert _rel(m1, m0) > 0.1
