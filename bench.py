@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gabor", action="store_true", help="skip the Gabor-map measurement")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the N2 cos^2, 256-instance batch and served-stream lines")
     ap.add_argument("--block", type=int, default=0, help="pin the integrator's block size")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the step eagerly instead of replaying its CUDA graph")
@@ -184,73 +186,159 @@ def workload_instances(name, n_traj=None):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample_run(instances, n_per):
-    """The oracle over the first n_per trajectories of each instance: sampling,
-    propagation, dipole and spectrum.  Returns (seconds, traj_steps)."""
+def host_threads():
+    """Host threads the oracle's OpenMP loop uses (the process's CPU set)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_run(instances, n_per, n_threads=0, keep=False):
+    """The oracle over the first n_per trajectories of each instance: sampling
+    (serial), propagation with the dipole sum (OpenMP over trajectories, all
+    host threads unless n_threads) and the spectrum (a serial DFT, once per
+    ensemble), each timed.  Returns the times and the sample's trajectory-steps
+    (with keep, also the sample's dipoles)."""
     import oracle as O
-    t0 = time.perf_counter()
+    t_samp = t_prop = t_dft = 0.0
     steps = 0
+    vzs = []
     for i in instances:
         t, p = W.TARGETS[i["target"]], i["pulse"]
         d = O.pulse_derived(p)
         m = min(n_per, i["n_traj"])
+        c0 = time.perf_counter()
         soa, _, _ = O.sample(t, p, i["align"], seed=i["seed"], instance=i["instance"], n=m)
-        vz, fin, _ = O.propagate(t, p, soa, W.GAMMA, cutoff=W.CUTOFF, want_final=False,
-                                 stab_cutoff=W.STAB_CUTOFF, stab_taper=W.STAB_TAPER)
+        c1 = time.perf_counter()
+        vz, _, _ = O.propagate(t, p, soa, W.GAMMA, cutoff=W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                               stab_taper=W.STAB_TAPER, n_threads=n_threads)
+        c2 = time.perf_counter()
         O.spectrum(vz, d["dt"], d["t_origin"], 0.5 * d["Tp"], d["nt"] // 2)
+        c3 = time.perf_counter()
+        t_samp += c1 - c0
+        t_prop += c2 - c1
+        t_dft += c3 - c2
         steps += int(np.sum(d["nt"] - 1 - soa[0]))
-    return time.perf_counter() - t0, steps
+        if keep:
+            vzs.append(vz)
+    n_traj = sum(min(n_per, i["n_traj"]) for i in instances)
+    return {"t_sample": t_samp, "t_prop": t_prop, "t_dft": t_dft, "traj_steps": steps,
+            "n_traj": n_traj, "n_ensembles": len(instances), "vz": vzs}
 
 
-def cpu_baseline(target_s, instances):
+def workload_rate(meas, full_traj, full_steps, n_ens):
+    """Trajectory-steps/s of the whole workload from a sample's timings:
+    sampling scales with the trajectories, propagation with the
+    trajectory-steps, the spectra with the ensembles."""
+    t = (meas["t_sample"] / meas["n_traj"] * full_traj
+         + meas["t_prop"] / meas["traj_steps"] * full_steps
+         + meas["t_dft"] / meas["n_ensembles"] * n_ens)
+    return full_steps / t
+
+
+def full_workload_size(instances, steps_per_traj):
+    n = sum(i["n_traj"] for i in instances)
+    return n, n * steps_per_traj
+
+
+def cpu_baseline(target_s, instances, small):
+    """The oracle on the host cores: all threads on a bounded sample of the
+    workload (at least 16 trajectories per thread and ensemble), one thread
+    on a smaller one, and the small 4096-trajectory workload in full on all
+    threads and sampled on one."""
     import oracle as O
     O.build()
+    thr = host_threads()
     inst = instances[:3]
-    n = 32
-    sec, st = oracle_sample_run(inst, n)
-    n = int(max(32, min(200000, n * target_s / max(sec, 1e-3))))
-    sec, st = oracle_sample_run(inst, n)
-    cores = os.cpu_count()
-    return {"value": st / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n} trajectories of each of the first {len(inst)} ensembles of the "
-                      f"workload (sampling + FP64 RK4 propagation + dipole + DFT), {sec:.1f} s, "
-                      f"OpenMP over {cores} host threads",
-            "seconds": sec, "traj_steps": st}
+    probe = oracle_sample_run(inst, 16 * thr)
+    per_traj = probe["traj_steps"] / probe["n_traj"]
+    # size the all-thread sample to about target_s of propagation
+    n = int(max(16 * thr, min(200000, 16 * thr * target_s / max(probe["t_prop"], 1e-3))))
+    meas = oracle_sample_run(inst, n, keep=True)
+    full_n, full_steps = full_workload_size(instances, per_traj)
+    value = workload_rate(meas, full_n, full_steps, len(instances))
+    one = oracle_sample_run(inst, 24, n_threads=1)
+    small_all = oracle_sample_run(small, small[0]["n_traj"])
+    small_one = oracle_sample_run(small, 96, n_threads=1)
+    s_n, s_steps = full_workload_size(small, small_all["traj_steps"] / small_all["n_traj"])
+    # the oracle's dipoles of two prefixes, for the comparison with the GPU
+    # paths on the same draws: the sample above, and 1e4 trajectories of the
+    # N2 cos^2 workload
+    cfg = W.N2_COS2
+    n2 = [dict(target=cfg["target"], pulse=cfg["pulse"], align=cfg["align"], n_traj=10_000,
+               seed=cfg["seed"], instance=0)]
+    n2_run = oracle_sample_run(n2, 10_000, keep=True)
+    dipoles = {"headline": (inst, n, meas["vz"]), "n2_cos2": (n2, 10_000, n2_run["vz"])}
+    return {"_oracle_dipoles": dipoles, "value": value, "unit": UNIT, "cores": thr,
+            "kind": "oracle",
+            "sample": f"first {n} trajectories of each of the first {len(inst)} ensembles "
+                      f"(device-free FP64 oracle: serial sampling, OpenMP propagation and "
+                      f"dipole sum over {thr} host threads, serial DFT per ensemble), "
+                      f"{meas['t_sample'] + meas['t_prop'] + meas['t_dft']:.1f} s; value = the "
+                      f"whole workload's trajectory-steps over the time the sample's per-"
+                      f"trajectory, per-step and per-ensemble costs add up to",
+            "sample_rate": meas["traj_steps"] / (meas["t_sample"] + meas["t_prop"]
+                                                 + meas["t_dft"]),
+            "propagation_rate_all_threads": meas["traj_steps"] / meas["t_prop"],
+            "propagation_rate_one_thread": one["traj_steps"] / one["t_prop"],
+            "dft_s_per_ensemble": meas["t_dft"] / meas["n_ensembles"],
+            "small_workload": {
+                "workload": small[0]["label"], "all_threads_full_run_s":
+                    small_all["t_sample"] + small_all["t_prop"] + small_all["t_dft"],
+                "all_threads_rate": workload_rate(small_all, s_n, s_steps, 1),
+                "one_thread_rate": workload_rate(small_one, s_n, s_steps, 1),
+                "one_thread_sample": "96 trajectories"},
+            "threads": thr, "os_cpu_count": os.cpu_count()}
+
+
+def small_instances():
+    cfg = W.SMALL
+    return [dict(target=cfg["target"], pulse=cfg["pulse"], align=cfg["align"],
+                 n_traj=cfg["n_traj"], seed=cfg["seed"], instance=0, label=cfg["name"])]
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores, each step a bounded sample of the
+    workload; one host process, whatever the number of ranks (the other
+    ranks exit at once)."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
     label, conf, instances = workload_instances(args.workload, args.n_traj)
-    instances = instances[:3]
     import oracle as O
     O.build()
-    n = 32
-    sec, _ = oracle_sample_run(instances, n)
-    # each step a bounded sample sized so the whole run stays within minutes
+    thr = host_threads()
+    inst = instances[:3]
+    probe = oracle_sample_run(inst, 16 * thr)
+    per_traj = probe["traj_steps"] / probe["n_traj"]
+    # each step's propagation sized so that the whole run stays within minutes
     per_step_s = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
-    n = int(max(16, min(100000, n * per_step_s / max(sec, 1e-3))))
+    n = int(max(16 * thr, min(100000, 16 * thr * per_step_s / max(probe["t_prop"], 1e-3))))
+    full_n, full_steps = full_workload_size(instances, per_traj)
     for _ in range(args.warmup):
-        oracle_sample_run(instances, n)
-    times, steps = [], 0
+        oracle_sample_run(inst, n)
+    rates, secs, samp = [], [], []
     for _ in range(args.steps):
-        s, st = oracle_sample_run(instances, n)
-        times.append(s)
-        steps += st
-    total = sum(times)
-    value = steps / total
-    cores = os.cpu_count()
+        m = oracle_sample_run(inst, n)
+        rates.append(workload_rate(m, full_n, full_steps, len(instances)))
+        secs.append(m["t_sample"] + m["t_prop"] + m["t_dft"])
+        samp.append(m["traj_steps"] / secs[-1])
+    value = float(np.mean(rates))
     conf = dict(conf)
-    conf.update({"sample_per_ensemble": n, "parallelism": "none (CPU oracle)"})
+    conf.update({"sample_per_ensemble": n, "parallelism": f"none (CPU oracle, {thr} threads)"})
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": conf,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "n_gpus": 1, "host_processes": 1, "ranks_launched": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": conf,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": f"first {n} trajectories of each of the first "
-                                       f"{len(instances)} ensembles per step"},
+                                       f"{len(inst)} ensembles per step; value = the whole "
+                                       f"workload's trajectory-steps over the time the "
+                                       f"sample's per-trajectory, per-step and per-ensemble "
+                                       f"costs add up to",
+                             "sample_rate": float(np.mean(samp))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -258,6 +346,342 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU path
+_T_START = time.perf_counter()
+
+
+def progress(what):
+    """Elapsed wall time after each part of the run, on stderr."""
+    sys.stderr.write(f"[bench] {what} done at {time.perf_counter() - _T_START:.1f} s\n")
+    sys.stderr.flush()
+
+
+def measure_peaks(S, device):
+    """FMA throughput of the FP32 and FP64 pipes (sfhk_fma_peak), each timed
+    for about 0.3 s with the clock sampled beside it."""
+    out = {}
+    for kind, name, iters in ((0, "fp32_ffma", 8_000_000), (1, "fp32_ffma2", 4_000_000),
+                              (2, "fp64_dfma", 120_000)):
+        clk = ClockSampler(device)
+        clk.start()
+        tf, ms = S.sfhk_fma_peak(kind, iters, device)
+        out[name] = {"tflops": tf, "ms": ms, "clocks": clk.stop()}
+    out["fp32_tflops"] = max(out["fp32_ffma"]["tflops"], out["fp32_ffma2"]["tflops"])
+    out["fp64_tflops"] = out["fp64_dfma"]["tflops"]
+    out["how"] = ("sfhk_fma_peak: 4 x 256 threads per SM, 8 independent FMA chains per "
+                  "thread, one warm-up and one timed launch (CUDA events)")
+    return out
+
+
+def roofline(stats, instances, kernel_ms, peak_tflops, peak_basis, kernel):
+    """Algorithmic flops of a launch (the method's count, costs.py) over the
+    kernel's event-timed duration, against a measured peak."""
+    flops = sum(costs.algorithmic_flops(i["target"], s["traj_steps"], s["recomb_evals"])
+                for i, s in zip(instances, stats))
+    executed = sum(costs.EXECUTED_FLOPS_PER_STEP[i["target"]] * s["traj_steps"]
+                   for i, s in zip(instances, stats))
+    steps = sum(s["traj_steps"] for s in stats)
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "kernel": kernel, "kernel_ms": kernel_ms,
+            "flops_per_traj_step": flops / max(steps, 1),
+            "recomb_fraction": sum(s["recomb_evals"] for s in stats) / max(steps, 1),
+            "peak_basis": peak_basis,
+            "executed_flops_per_traj_step": executed / max(steps, 1),
+            "executed_frac": executed / (kernel_ms * 1e-3) / 1e12 / peak_tflops}
+
+
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def sub_n2_cos2(S, torch, ctx, stream, local, peaks, args):
+    """N2 with the cos^2-weighted axis, 1e7 trajectories, mixed precision:
+    device sampling, one propagation launch and the spectrum per step; the
+    FP64 path and the mixed path on the first 2e5 of the same draws."""
+    cfg = W.N2_COS2
+    sp = stream.cuda_stream
+    th = S.sfhk_create_target(ctx, W.TARGETS["N2"])
+    ph = S.sfhk_set_pulse(ctx, cfg["pulse"])
+    g = S.sfhk_pulse_grid(ph)
+    n = cfg["n_traj"]
+    e = S.sfhk_sample_initial(ctx, th, ph, cfg["align"], n, cfg["seed"], 0, sp)
+    spec = torch.empty((3, g["nt"] // 2), dtype=torch.float64, device="cuda")
+    mixed = S.run_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                       stab_taper=W.STAB_TAPER)
+
+    def step():
+        S.sfhk_sample_into(ctx, e, cfg["align"], cfg["seed"], 0, sp)
+        S.sfhk_propagate(ctx, e, mixed, sp)
+        vz_ptr, _ = S.sfhk_dipole_device(e)
+        S.sfhk_spectrum_device(vz_ptr, g["nt"], g["dt"], g["t_origin"], 0.5 * g["Tp"],
+                               spec[0].data_ptr(), spec[1].data_ptr(), spec[2].data_ptr(),
+                               g["nt"] // 2, sp)
+
+    with torch.cuda.stream(stream):
+        step()
+    torch.cuda.synchronize()
+    steps = 2
+    ev = _events(torch, steps + 1)
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = S.sfhk_launch_count()
+    ev[0].record(stream)
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = (S.sfhk_launch_count() - l0) // steps
+    clocks = clk.stop()
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    st = S.sfhk_stats_get(e)
+    ms_step = float(np.mean(ms))
+    roof = roofline([st], [dict(target="N2")], st["kernel_ms"], peaks["fp32_tflops"],
+                    "measured FP32 FMA peak (sfhk_fma_peak)", "k_propagate<mixed>")
+    S.sfhk_destroy_ensemble(e)
+    # the first 2e5 trajectories of the same draws in both precisions
+    n_sub = 200_000
+    es = S.sfhk_sample_initial(ctx, th, ph, cfg["align"], n_sub, cfg["seed"], 0, sp)
+    out = {}
+    for prec in (S.SFHK_MIXED, S.SFHK_FP64):
+        S.sfhk_propagate(ctx, es, S.run_opts(prec, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                                             stab_taper=W.STAB_TAPER), sp)
+        vz = S.sfhk_dipole(ctx, es, g["nt"])
+        s2 = S.sfhk_stats_get(es)
+        out[prec] = (vz, s2["traj_steps"] / (s2["kernel_ms"] * 1e-3), s2)
+    S.sfhk_destroy_ensemble(es)
+    vm, v64 = out[S.SFHK_MIXED][0], out[S.SFHK_FP64][0]
+    s64 = out[S.SFHK_FP64][2]
+    r64 = roofline([s64], [dict(target="N2")], s64["kernel_ms"], peaks["fp64_tflops"],
+                   "measured FP64 FMA peak (sfhk_fma_peak)", "k_propagate<fp64>")
+    S.sfhk_destroy_pulse(ph)
+    S.sfhk_destroy_target(th)
+    return {"workload": cfg["name"], "n_traj": n, "steps": steps, "warmup": 1,
+            "value": st["traj_steps"] / (ms_step * 1e-3), "unit": UNIT, "ms_per_step": ms_step,
+            "ms_per_step_all": ms, "spectra_per_s": 1.0 / (ms_step * 1e-3),
+            "traj_steps_per_step": st["traj_steps"], "gpu_launches": launches,
+            "roofline": roof, "clocks": clocks,
+            "fp64_path_sub_sample": {
+                "sample": f"the first {n_sub} trajectories of the same draws",
+                "fp64_traj_steps_per_s": out[S.SFHK_FP64][1],
+                "mixed_traj_steps_per_s": out[S.SFHK_MIXED][1],
+                "dipole_rel_l2_mixed_vs_fp64": float(np.linalg.norm(vm - v64)
+                                                     / np.linalg.norm(v64)),
+                "fp64_roofline": r64}}
+
+
+def sub_batched(S, torch, ctx, stream, local, peaks, args):
+    """256 uneven H2/N2 instances (about 6e7 trajectories) in one persistent
+    launch per step, the launch shape chosen by the autotuner on the largest
+    instance; each step re-samples every instance on the device, propagates
+    the batch and takes the 256 spectra, captured as one CUDA graph.  The
+    FP64 path against the mixed one on 8 of the instances (every 32nd, at most
+    2e4 trajectories each)."""
+    sp = stream.cuda_stream
+    insts = W.batched_instances(256, seed=0)
+    tg = {nm: S.sfhk_create_target(ctx, W.TARGETS[nm]) for nm in ("H2", "N2")}
+    pulses, grids, ens, spec = [], [], [], []
+    for i in insts:
+        ph = S.sfhk_set_pulse(ctx, i["pulse"])
+        pulses.append(ph)
+        g = S.sfhk_pulse_grid(ph)
+        grids.append(g)
+        ens.append(S.sfhk_sample_initial(ctx, tg[i["target"]], ph, i["align"], i["n_traj"],
+                                         i["seed"], i["instance"], sp))
+        spec.append(torch.empty((3, g["nt"] // 2), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    mixed = S.run_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                       stab_taper=W.STAB_TAPER)
+    big = max(range(len(insts)), key=lambda k: insts[k]["n_traj"])
+    tuned = S.sfhk_autotune(ctx, ens[big], mixed, max_items=8192)
+    batch = S.sfhk_batch_create(ctx, ens, mixed)
+
+    def step():
+        for i, e in zip(insts, ens):
+            S.sfhk_sample_into(ctx, e, i["align"], i["seed"], i["instance"], sp)
+        S.sfhk_batch_launch(batch, sp)
+        for e, g, o in zip(ens, grids, spec):
+            vz_ptr, _ = S.sfhk_dipole_device(e)
+            S.sfhk_spectrum_device(vz_ptr, g["nt"], g["dt"], g["t_origin"], 0.5 * g["Tp"],
+                                   o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(),
+                                   g["nt"] // 2, sp)
+
+    with torch.cuda.stream(stream):
+        step()
+    torch.cuda.synchronize()
+    l_cap = S.sfhk_launch_count()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step()
+    launches = S.sfhk_launch_count() - l_cap
+    steps = 2
+    ev = _events(torch, steps + 1)
+    clk = ClockSampler(local)
+    clk.start()
+    ev[0].record(stream)
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            graph.replay()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    st = [S.sfhk_stats_get(e) for e in ens]
+    traj_steps = sum(s["traj_steps"] for s in st)
+    ms_step = float(np.mean(ms))
+    roof = roofline(st, insts, st[0]["kernel_ms"], peaks["fp32_tflops"],
+                    "measured FP32 FMA peak (sfhk_fma_peak)", "k_propagate<mixed>")
+    del graph
+    S.sfhk_batch_destroy(batch)
+    for e in ens:
+        S.sfhk_destroy_ensemble(e)
+    # FP64 against mixed on a sub-sample of the instances
+    sub = [dict(i, n_traj=min(i["n_traj"], 20000)) for i in insts[::32]]
+    sens = [S.sfhk_sample_initial(ctx, tg[i["target"]], pulses[32 * k], i["align"], i["n_traj"],
+                                  i["seed"], i["instance"], sp) for k, i in enumerate(sub)]
+    res = {}
+    for prec in (S.SFHK_MIXED, S.SFHK_FP64):
+        b = S.sfhk_batch_create(ctx, sens, S.run_opts(prec, W.GAMMA, W.CUTOFF,
+                                                      stab_cutoff=W.STAB_CUTOFF,
+                                                      stab_taper=W.STAB_TAPER))
+        S.sfhk_batch_launch(b, sp)
+        torch.cuda.synchronize()
+        s2 = [S.sfhk_stats_get(e) for e in sens]
+        res[prec] = ([S.sfhk_dipole(ctx, e, grids[32 * k]["nt"]) for k, e in enumerate(sens)],
+                     sum(x["traj_steps"] for x in s2) / (s2[0]["kernel_ms"] * 1e-3))
+        S.sfhk_batch_destroy(b)
+    for e in sens:
+        S.sfhk_destroy_ensemble(e)
+    errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            for a, b in zip(res[S.SFHK_MIXED][0], res[S.SFHK_FP64][0])]
+    for ph in pulses:
+        S.sfhk_destroy_pulse(ph)
+    for t in tg.values():
+        S.sfhk_destroy_target(t)
+    label = "256 H2/N2 instances, N log-uniform 1e4-1e6, 800-1600 nm, 2-4 cycles, one launch"
+    return {"workload": label, "instances": len(insts),
+            "n_traj_total": sum(i["n_traj"] for i in insts), "steps": steps, "warmup": 1,
+            "value": traj_steps / (ms_step * 1e-3), "unit": UNIT, "ms_per_step": ms_step,
+            "ms_per_step_all": ms, "spectra_per_s": len(insts) / (ms_step * 1e-3),
+            "traj_steps_per_step": traj_steps, "gpu_launches": launches,
+            "cuda_graph": True, "autotuned": tuned, "roofline": roof, "clocks": clocks,
+            "fp64_path_sub_sample": {
+                "sample": "every 32nd instance (8), at most 2e4 trajectories each, one launch",
+                "fp64_traj_steps_per_s": res[S.SFHK_FP64][1],
+                "mixed_traj_steps_per_s": res[S.SFHK_MIXED][1],
+                "dipole_rel_l2_mixed_vs_fp64": {"max": max(errs),
+                                                "median": float(np.median(errs))}}}
+
+
+def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None,
+              max_requests=None, slice_ms=50.0, budget=16 << 30):
+    """One Poisson stream (or a given request list) through the server; the
+    latencies, spectra/s and trajectory-steps/s of the completed requests."""
+    prec = S.SFHK_MIXED if prec is None else prec
+    reqs = requests if requests is not None else W.request_stream(rate_hz=rate,
+                                                                  duration_s=duration, seed=0)
+    if max_requests:
+        reqs = reqs[:max_requests]
+    clk = ClockSampler(local)
+    srv = S.sfhk_server_create(local, S.server_opts(
+        prec, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF, stab_taper=W.STAB_TAPER, budget=budget,
+        slice_ms=slice_ms, max_pending=max_pending))
+    ids, rejected = [], 0
+    clk.start()
+    t0 = time.perf_counter()
+    for r in reqs:
+        wait = r.get("arrival_s", 0.0) - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        try:
+            ids.append((S.sfhk_submit(srv, S.request(W.TARGETS[r["target"]], r["pulse"],
+                                                     r["align"], r["n_traj"], r["seed"],
+                                                     r["instance"])), r))
+        except S.SfhkError:
+            rejected += 1
+    lat, adm, steps, done, dips = [], [], 0, 0, []
+    res = S.Result()
+    for i, r in ids:
+        out = S.sfhk_wait(srv, i, 3600.0, res)
+        if out["status"] == S.SFHK_OK:
+            lat.append(out["t_done"] - out["t_submit"])
+            adm.append(out["t_admit"] - out["t_submit"])
+            steps += out["traj_steps"]
+            done += 1
+            dips.append(out["vz"])
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    stt = S.sfhk_server_stats_get(srv)
+    S.sfhk_server_destroy(srv)
+    lat = np.array(lat) if lat else np.array([np.nan])
+    adm = np.array(adm) if adm else np.array([np.nan])
+    return {"rate_hz": rate, "requests": len(reqs), "completed": done, "rejected": rejected,
+            "wall_s": wall, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)),
+            "admission_wait_p50_s": float(np.percentile(adm, 50)),
+            "admission_wait_p99_s": float(np.percentile(adm, 99)), "slice_ms": slice_ms,
+            "max_pending": max_pending, "spectra_per_s": done / wall,
+            "traj_steps_per_s": steps / wall,
+            "gpu_busy_frac": stt["gpu_busy_s"] / max(stt["uptime_s"], 1e-9),
+            "slices": stt["slices"], "clocks": clocks}, dips
+
+
+def sub_served(S, local, args):
+    """The Poisson request stream at 200 requests/s (overloaded by
+    construction: each request is drawn like a batched instance), with at
+    most 64 requests waiting for admission, and a sweep of rates around the
+    saturation point; then 16 requests of at most 2e4 trajectories served by
+    an FP64 and a mixed-precision server, submitted at once."""
+    main, _ = serve_run(S, local, 200.0, 20.0)
+    sweep = [serve_run(S, local, r, 15.0)[0] for r in (10.0, 20.0, 30.0)]
+    few = [dict(r, n_traj=min(r["n_traj"], 20000), arrival_s=0.0)
+           for r in W.request_stream(rate_hz=200.0, duration_s=1.0, seed=0)[:16]]
+    m, dm = serve_run(S, local, 0.0, 0.0, requests=few, max_pending=4096)
+    f, df = serve_run(S, local, 0.0, 0.0, prec=S.SFHK_FP64, requests=few, max_pending=4096)
+    errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(dm, df)]
+    return {"workload": "Poisson 200 requests/s for 20 s, requests drawn like the 256-instance "
+                        "batch, mixed precision, at most 64 waiting for admission",
+            "value": main["traj_steps_per_s"], "unit": UNIT, "p50_s": main["p50_s"],
+            "p99_s": main["p99_s"], "spectra_per_s": main["spectra_per_s"], "served": main,
+            "rate_sweep": sweep,
+            "fp64_path_sub_sample": {
+                "sample": "the first 16 requests, at most 2e4 trajectories each, submitted at once",
+                "fp64": {k: f[k] for k in ("spectra_per_s", "traj_steps_per_s", "wall_s")},
+                "mixed": {k: m[k] for k in ("spectra_per_s", "traj_steps_per_s", "wall_s")},
+                "dipole_rel_l2_mixed_vs_fp64": {"max": max(errs) if errs else None,
+                                                "median": float(np.median(errs)) if errs
+                                                else None}}}
+
+
+def gpu_vs_oracle(S, ctx, dipoles, stream):
+    """The GPU's mixed and FP64 dipoles of the prefixes the CPU-baseline leg
+    ran through the oracle (the same draws: device sampling of the first n
+    trajectories of each ensemble), against the oracle's: relative L2."""
+    sp = stream.cuda_stream
+    out = {}
+    for key, (insts, n, vz_o) in dipoles.items():
+        rows = []
+        for i, vo in zip(insts, vz_o):
+            th = S.sfhk_create_target(ctx, W.TARGETS[i["target"]])
+            ph = S.sfhk_set_pulse(ctx, i["pulse"])
+            nt = S.sfhk_pulse_grid(ph)["nt"]
+            m = min(n, i["n_traj"])
+            e = S.sfhk_sample_initial(ctx, th, ph, i["align"], m, i["seed"], i["instance"], sp)
+            err = {}
+            for name, prec in (("mixed", S.SFHK_MIXED), ("fp64", S.SFHK_FP64)):
+                S.sfhk_propagate(ctx, e, S.run_opts(prec, W.GAMMA, W.CUTOFF,
+                                                    stab_cutoff=W.STAB_CUTOFF,
+                                                    stab_taper=W.STAB_TAPER), sp)
+                vz = S.sfhk_dipole(ctx, e, nt)
+                err[name] = float(np.linalg.norm(vz - vo) / np.linalg.norm(vo))
+            rows.append(err)
+            S.sfhk_destroy_ensemble(e)
+            S.sfhk_destroy_pulse(ph)
+            S.sfhk_destroy_target(th)
+        out[key] = {"n_traj_per_ensemble": n, "dipole_rel_l2_vs_oracle": rows}
+    return out
+
+
 def run_ours(args):
     world, rank, local = dist_setup()
     import torch
@@ -269,6 +693,10 @@ def run_ours(args):
     _build.build()
     from paper_2608_13686_b300 import sfhk as S
 
+    # the extra workloads (N2 cos^2, the 256-instance batch, the served
+    # stream) run on one GPU only, after the headline
+    extras = world == 1 and rank == 0 and args.workload == "h2-angles" and not args.no_extras
+    peaks = measure_peaks(S, local)
     label, conf, instances = workload_instances(args.workload, args.n_traj)
     ctx = S.sfhk_create(local, 0)
     stream = torch.cuda.Stream()
@@ -332,7 +760,7 @@ def run_ours(args):
     clock = ClockSampler(local)
     clock.start()
     l0 = S.sfhk_launch_count()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev = _events(torch, args.steps + 1)
     barrier()
     ev[0].record(stream)
     for k in range(args.steps):
@@ -357,23 +785,16 @@ def run_ours(args):
     spectra_per_s = world * len(instances) / (ms * 1e-3)
     vz_mixed = [S.sfhk_dipole(ctx, e, g["nt"]) for e, g in zip(ens, grids)]
 
-    # roofline of the propagation kernel (FP32 FMA pipe)
-    flops = sum(costs.FLOPS_PER_STEP[i["target"]] * s["traj_steps"]
-                for i, s in zip(instances, st))
-    achieved = flops / (prop_ms * 1e-3) / 1e12
-    peak = costs.fp32_peak_tflops()
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak,
-            "traffic": (costs.TRAFFIC.get((args.workload, tuned["kernel_variant"] if tuned
-                                           else args.kernel_variant))
-                        if args.n_traj in (0, 1_000_000) else None),
-            "kernel": ("k_propagate_poly<mixed>" if any(
-                W.TARGETS[nm].get("kind") == W.POT_POLY for nm in targets)
-                else "k_propagate<mixed>"), "kernel_ms": prop_ms,
-            "flops_per_traj_step": {nm: costs.FLOPS_PER_STEP[nm] for nm in targets},
-            "peak_basis": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (unit counts, max clock)"}
-    if clk.get("sm_mhz"):
-        roof["peak_at_median_clock"] = costs.fp32_peak_tflops(clk["sm_mhz"])
+    # roofline of the propagation kernel: the method's flops (costs.py, with
+    # the measured recombination evaluations) against the measured FP32 peak
+    poly = any(W.TARGETS[nm].get("kind") == W.POT_POLY for nm in targets)
+    roof = roofline(st, instances, prop_ms, peaks["fp32_tflops"],
+                    "measured FP32 FMA peak (sfhk_fma_peak, burst of about 0.3 s)",
+                    "k_propagate_poly<mixed>" if poly else "k_propagate<mixed>")
+    roof["traffic"] = (costs.TRAFFIC.get((args.workload, tuned["kernel_variant"] if tuned
+                                          else args.kernel_variant))
+                       if args.n_traj in (0, 1_000_000) else None)
+    roof["peak_unit_counts"] = costs.fp32_peak_tflops(clk["sm_mhz"] or costs.MAX_SM_MHZ)
 
     # e2e through the public API with host buffers (dipole and spectrum to host)
     def e2e_step():
@@ -399,15 +820,14 @@ def run_ours(args):
     e2e = {"value": world * traj_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3, "steps": n_e2e}
 
-    # the plain FP64 GPU path on the same workload, and the dipole difference
+    # the plain FP64 GPU path on the same workload (one timed step), the
+    # dipole difference, and its roofline against the measured FP64 peak
     fp64 = None
     if not args.no_fp64:
         o64 = S.run_opts(S.SFHK_FP64, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
                          stab_taper=W.STAB_TAPER)
         b64 = S.sfhk_batch_create(ctx, ens, o64)
-        step(b64)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch, 2)
         e0.record(stream)
         step(b64)
         e1.record(stream)
@@ -419,10 +839,13 @@ def run_ours(args):
         S.sfhk_batch_destroy(b64)
         errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(vz_mixed, vz64)]
         fp64 = {"value": world * ts64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
-                "kernel_ms": st64[0]["kernel_ms"], "steps": 1, "warmup": 1,
+                "kernel_ms": st64[0]["kernel_ms"], "steps": 1, "warmup": 0,
                 "dipole_rel_l2_mixed_vs_fp64": errs if len(errs) <= 8 else
                 {"max": max(errs), "median": float(np.median(errs))},
-                "speedup_mixed_over_fp64": (traj_steps / ms) / (ts64 / ms64)}
+                "speedup_mixed_over_fp64": (traj_steps / ms) / (ts64 / ms64),
+                "roofline": roofline(st64, instances, st64[0]["kernel_ms"], peaks["fp64_tflops"],
+                                     "measured FP64 FMA peak (sfhk_fma_peak)",
+                                     "k_propagate<fp64>")}
 
     # Gabor time-frequency maps of the step's dipoles (Sec. III.D analysis,
     # outside the timed step): 512 window centres over the pulse x 512
@@ -444,7 +867,7 @@ def run_ours(args):
                                     ws, n_w, o.data_ptr(), sp)
         gabor_all()
         barrier()
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0, g1 = _events(torch, 2)
         reps = 5
         g0.record(stream)
         for _ in range(reps):
@@ -461,14 +884,34 @@ def run_ours(args):
             hi = np.clip(np.floor((tm + 8.6 * sg - g["t_origin"]) / g["dt"]), -1, g["nt"] - 1)
             samples += int(np.sum(np.maximum(hi - lo + 1, 0)))
         gfl = 10.0 * samples * n_w
+        gt = gfl / (gms * 1e-3) / 1e12
         gabor = {"ms": gms, "maps": len(ens), "map": [n_t, n_w], "sigma": "1/(3 w0)",
-                 "kernel": "k_gabor (FP64)", "achieved_tflops": gfl / (gms * 1e-3) / 1e12,
-                 "fp64_peak_nominal_tflops": 1.25,
-                 "frac_of_fp64_nominal": gfl / (gms * 1e-3) / 1e12 / 1.25}
+                 "kernel": "k_gabor (FP64)", "achieved_tflops": gt,
+                 "peak_fp64_measured_tflops": peaks["fp64_tflops"],
+                 "frac": gt / peaks["fp64_tflops"]}
+
+    used_graph = graph is not None
+    if graph is not None:
+        del graph
+    S.sfhk_batch_destroy(batch)
+    for e in ens:
+        S.sfhk_destroy_ensemble(e)
+    progress("headline")
+
+    extra = {}
+    if extras:
+        extra["n2_cos2"] = sub_n2_cos2(S, torch, ctx, stream, local, peaks, args)
+        progress("n2_cos2")
+        extra["batched"] = sub_batched(S, torch, ctx, stream, local, peaks, args)
+        progress("batched")
+        extra["served"] = sub_served(S, local, args)
+        progress("served")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_seconds, instances)
+        cpu = cpu_baseline(args.cpu_seconds, instances, small_instances())
+        cpu["oracle_checks"] = gpu_vs_oracle(S, ctx, cpu.pop("_oracle_dipoles"), stream)
+        progress("cpu_baseline")
 
     if rank == 0:
         conf = dict(conf)
@@ -476,7 +919,7 @@ def run_ours(args):
                      "stability_cutoff": W.STAB_CUTOFF, "stability_taper": W.STAB_TAPER,
                      "traj_steps_per_step": traj_steps,
                      "l2": "inputs larger than L2 (trajectory SoA, 96 B per trajectory)",
-                     "cuda_graph": graph is not None,
+                     "cuda_graph": used_graph,
                      "parallelism": f"replicas x{world}"})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -487,15 +930,11 @@ def run_ours(args):
                 "ms_per_step_all": ms_steps,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "fp64_path": fp64, "gabor": gabor, "gpu_launches": launches // args.steps,
-                "autotuned": tuned, "clocks": clk,
+                "autotuned": tuned, "clocks": clk, "peaks_measured": peaks,
                 "filtered_frac": sum(s["n_filtered"] + s["n_unstable"] for s in st)
                 / sum(i["n_traj"] for i in instances)}
+        line.update(extra)
         print(json.dumps(line), flush=True)
-    if graph is not None:
-        del graph
-    S.sfhk_batch_destroy(batch)
-    for e in ens:
-        S.sfhk_destroy_ensemble(e)
     for ph in pulses:
         S.sfhk_destroy_pulse(ph)
     for th in targets.values():
@@ -517,46 +956,11 @@ def run_served(args):
     from paper_2608_13686_b300 import _build
     _build.build()
     from paper_2608_13686_b300 import sfhk as S
-    import threading as th
 
     def one_run(rate, duration, max_requests=None):
-        reqs = W.request_stream(rate_hz=rate, duration_s=duration, seed=0)
-        if max_requests:
-            reqs = reqs[:max_requests]
-        srv = S.sfhk_server_create(local, S.server_opts(
-            S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF, stab_taper=W.STAB_TAPER,
-            budget=args.serve_budget,
-            slice_ms=args.slice_ms, max_pending=args.max_pending))
-        ids, rejected = [], 0
-        t0 = time.perf_counter()
-        for r in reqs:
-            wait = r["arrival_s"] - (time.perf_counter() - t0)
-            if wait > 0:
-                time.sleep(wait)
-            try:
-                ids.append(S.sfhk_submit(srv, S.request(W.TARGETS[r["target"]], r["pulse"],
-                                                        r["align"], r["n_traj"], r["seed"],
-                                                        r["instance"])))
-            except S.SfhkError:
-                rejected += 1
-        lat, steps, done = [], 0, 0
-        res = S.Result()
-        for i in ids:
-            out = S.sfhk_wait(srv, i, 3600.0, res)
-            if out["status"] == S.SFHK_OK:
-                lat.append(out["t_done"] - out["t_submit"])
-                steps += out["traj_steps"]
-                done += 1
-        wall = time.perf_counter() - t0
-        stt = S.sfhk_server_stats_get(srv)
-        S.sfhk_server_destroy(srv)
-        lat = np.array(lat) if lat else np.array([np.nan])
-        return {"rate_hz": rate, "requests": len(reqs), "completed": done,
-                "rejected": rejected, "wall_s": wall,
-                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                "spectra_per_s": done / wall, "traj_steps_per_s": steps / wall,
-                "gpu_busy_frac": stt["gpu_busy_s"] / max(stt["uptime_s"], 1e-9),
-                "slices": stt["slices"]}
+        return serve_run(S, local, rate, duration, max_pending=args.max_pending,
+                         max_requests=max_requests, slice_ms=args.slice_ms,
+                         budget=args.serve_budget)[0]
 
     sweep = [one_run(r, args.sweep_seconds) for r in args.sweep_rates]
     main = one_run(args.rate, args.duration, args.max_requests)
@@ -566,7 +970,8 @@ def run_served(args):
             "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": {"workload": f"Poisson {args.rate} req/s for {args.duration} s, requests "
                                    "drawn like the 256-instance batch, mixed precision",
-                       "slice_ms": args.slice_ms, "budget_bytes": args.serve_budget},
+                       "slice_ms": args.slice_ms, "budget_bytes": args.serve_budget,
+                       "max_pending": args.max_pending},
             "p50_s": main["p50_s"], "p99_s": main["p99_s"],
             "spectra_per_s": main["spectra_per_s"], "served": main, "rate_sweep": sweep}
     print(json.dumps(line), flush=True)

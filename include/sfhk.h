@@ -255,6 +255,11 @@ typedef struct {
     uint64_t traj_steps;      /* RK4 steps actually integrated                */
     int nt;                   /* time-grid length                             */
     float kernel_ms;          /* duration of the propagation kernel (events)  */
+    uint64_t recomb_evals;    /* trajectory-steps at which the recombination  */
+                              /* element was evaluated (its Gaussian overlaps */
+                              /* above e^-30 of their peak in FP32, e^-200 in */
+                              /* FP64) and the contribution formed; the other */
+                              /* steps contribute zero without that work      */
 } sfhk_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -549,6 +554,19 @@ SFHK_API const char* sfhk_strerror(int code);
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts).  For accounting of launches in a timed region. */
 SFHK_API int sfhk_launch_count(uint64_t* out);
+
+/* Throughput of the device's FMA pipes: the measured denominators of the
+ * integrators' rooflines (a measurement utility, not a step of the method).
+ * kind 0 = FP32 FMA, 1 = packed FP32 FMA pairs (one f32x2 instruction, two
+ * FMAs), 2 = FP64 FMA.  One warm-up and one timed launch, each thread
+ * running 8 independent FMA recurrences for `iters` rounds, 4 blocks of 256
+ * threads per SM, timed with CUDA events on a private stream.  *tflops
+ * receives 2 x FMAs / duration (an FMA counts 2 flops); *ms the duration
+ * (may be NULL).  Synchronous; allocates (and frees) SMs x 8 KiB of device
+ * memory for the result sink.  The clock is whatever the GPU runs at
+ * meanwhile: sample it beside the call.  Errors: SFHK_E_INVAL (kind outside
+ * 0..2, iters < 1, null tflops), SFHK_E_CUDA. */
+SFHK_API int sfhk_fma_peak(int device, int kind, int iters, double* tflops, float* ms);
 
 #ifdef __cplusplus
 }

@@ -313,7 +313,7 @@ int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s)
     SFHK_CUDA_TRY(cudaMemsetAsync(e->vz.p, 0, sizeof(double) * e->pulse->nt, s));
     SFHK_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(unsigned long long) * 3, s));
     SFHK_CUDA_TRY(cudaMemsetAsync((unsigned long long*)e->counters.p + 4, 0,
-                                  sizeof(unsigned long long), s));
+                                  sizeof(unsigned long long) * 2, s));
     e->dumped = o.dump_final != 0;
     return SFHK_OK;
 }
@@ -890,7 +890,7 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
         SFHK_CUDA_TRY(cudaMemsetAsync(e->vz.p, 0, sizeof(double) * e->pulse->nt, s));
         SFHK_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(unsigned long long) * 3, s));
         SFHK_CUDA_TRY(cudaMemsetAsync((unsigned long long*)e->counters.p + 4, 0,
-                                      sizeof(unsigned long long), s));
+                                      sizeof(unsigned long long) * 2, s));
         rc = launch_build_items((const int*)e->perm.p, (const int*)e->n0.p, e->n, (int)i,
                                 b->d_items + off, s);
         if (rc) return rc;
@@ -1022,7 +1022,7 @@ int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out)
     int rc = set_device(e->ctx->device);
     if (rc) return rc;
     std::memset(out, 0, sizeof *out);
-    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
     if (e->have_result) SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_done));
     SFHK_CUDA_TRY(cudaDeviceSynchronize());
     SFHK_CUDA_TRY(cudaMemcpy(h, e->counters.p, sizeof h, cudaMemcpyDeviceToHost));
@@ -1032,6 +1032,7 @@ int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out)
     out->traj_steps = h[2];
     out->n_invalid = h[3];
     out->n_unstable = h[4];
+    out->recomb_evals = h[5];
     out->nt = e->pulse->nt;
     float ms = 0.0f;
     if (e->have_result && cudaEventElapsedTime(&ms, e->ev_start, e->ev_stop) == cudaSuccess)

@@ -69,7 +69,8 @@ struct DevInstance {
     double* dump;          // 47 x n or null
     double* returns;       // 2 x n first returns (step, energy) or null
     double ret_out, ret_in;
-    unsigned long long* counters;   // [filtered, nonfinite, steps, invalid, unstable]
+    unsigned long long* counters;   // [filtered, nonfinite, steps, invalid, unstable,
+                                    //  recombination evaluations]
     long long n;
     int nt;
     double dt, t_origin;

@@ -933,7 +933,12 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         // in MIXED; rows are 33 apart so that both the writes above and these
         // reads hit 32 different banks
         __syncwarp();
-        if (__any_sync(kFull, contributed) && lane < send) {
+        // the recombination evaluations of the chunk are its nonzero
+        // contributions, counted here so that no counter stays live in the
+        // step loop
+        const bool any = __any_sync(kFull, contributed);
+        unsigned int n_nz = 0;
+        if (any && lane < send) {
             const R* row = red + lane * kRedStride;
             if constexpr (MIXED) {
                 float sv = 0.0f, ev = 0.0f;
@@ -942,15 +947,23 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
                     float t;
                     two_sum(sv, row[k], sv, t);
                     ev += t;
+                    n_nz += row[k] != 0.0f;
                 }
                 if (sv != 0.0f || ev != 0.0f)
                     atomicAdd(&I.vz[nb + lane], I.scale * (double(sv) + double(ev)));
             } else {
                 double sv = 0.0;
 #pragma unroll 8
-                for (int k = 0; k < kWarp; ++k) sv += row[k];
+                for (int k = 0; k < kWarp; ++k) {
+                    sv += row[k];
+                    n_nz += row[k] != 0.0;
+                }
                 if (sv != 0.0) atomicAdd(&I.vz[nb + lane], I.scale * sv);
             }
+        }
+        if (any) {
+            const unsigned int tot = __reduce_add_sync(kFull, n_nz);
+            if (lane == 0 && tot) atomicAdd(&I.counters[5], (unsigned long long)tot);
         }
         __syncwarp();
         if (!__any_sync(kFull, has && status == 0)) break;

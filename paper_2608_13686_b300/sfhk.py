@@ -72,7 +72,7 @@ class sfhk_stats(C.Structure):
     _fields_ = [("n_traj", C.c_uint64), ("n_invalid", C.c_uint64), ("n_filtered", C.c_uint64),
                 ("n_nonfinite", C.c_uint64), ("n_unstable", C.c_uint64),
                 ("traj_steps", C.c_uint64), ("nt", C.c_int),
-                ("kernel_ms", C.c_float)]
+                ("kernel_ms", C.c_float), ("recomb_evals", C.c_uint64)]
 
 
 class sfhk_server_opts(C.Structure):
@@ -138,6 +138,7 @@ def _load():
         "sfhk_sample_into": ([_vp, _vp, C.POINTER(sfhk_align_desc), C.c_uint64, C.c_uint32, _vp],
                              C.c_int),
         "sfhk_launch_count": ([C.POINTER(C.c_uint64)], C.c_int),
+        "sfhk_fma_peak": ([C.c_int, C.c_int, C.c_int, _dp, C.POINTER(C.c_float)], C.c_int),
         "sfhk_load_ensemble": ([_vp, _vp, _vp, _dp, C.c_uint64, C.c_double, C.POINTER(_vp)],
                                C.c_int),
         "sfhk_ensemble_read": ([_vp, _dp, C.c_uint64], C.c_int),
@@ -545,5 +546,14 @@ EXPORTED = [
     "sfhk_launch_count", "sfhk_autotune", "sfhk_spectrum_noalloc", "sfhk_server_create",
     "sfhk_server_destroy", "sfhk_submit", "sfhk_poll", "sfhk_wait", "sfhk_cancel",
     "sfhk_server_stats_get", "sfhk_batch_create", "sfhk_batch_launch", "sfhk_batch_destroy",
-    "sfhk_gabor", "sfhk_returns",
+    "sfhk_gabor", "sfhk_returns", "sfhk_fma_peak",
 ]
+
+
+def sfhk_fma_peak(kind, iters, device=0):
+    """Measured FMA throughput (TFLOP/s, ms): kind 0 FP32, 1 packed FP32 pairs,
+    2 FP64."""
+    tf, ms = C.c_double(), C.c_float()
+    _check(_load().sfhk_fma_peak(device, kind, iters, C.byref(tf), C.byref(ms)), "sfhk_fma_peak")
+    return tf.value, ms.value
+

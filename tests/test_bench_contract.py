@@ -1,7 +1,8 @@
 """The benchmark's JSON-line contract, checked on the CPU through its
 reference arm (the oracle timed on the host): one line with the contract's
 keys, alone and under torchrun with two ranks (rank 0 prints, the other exits
-without work)."""
+without work).  The line always describes one host process (n_gpus 1),
+whatever the number of ranks launched, and says how many were."""
 import json
 import os
 import socket
@@ -18,14 +19,16 @@ def _lines(out):
     return [json.loads(ln) for ln in out.splitlines() if ln.startswith("{")]
 
 
-def _check(line, n_gpus):
+def _check(line, ranks):
     assert KEYS <= set(line)
-    assert line["impl"] == "reference" and line["n_gpus"] == n_gpus
+    assert line["impl"] == "reference" and line["n_gpus"] == 1
+    assert line["host_processes"] == 1 and line["ranks_launched"] == ranks
     assert line["value"] > 0 and line["unit"] == "trajectory-steps/s"
     assert line["higher_is_better"] is True and line["scaling"] == "weak"
     assert line["config"]["workload"].startswith("H2")
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert 0 < cb["sample_rate"] <= 1.5 * line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
 
 

@@ -103,10 +103,17 @@ def test_small_workload_end_to_end(S, ctx, h2_oracle):
     vz = S.sfhk_dipole(ctx, e, nt)
     assert _rel(vz, h2_oracle["vz_small"]) <= 1e-9
     _compare_final(S.sfhk_final_state(e, N_SMALL), h2_oracle["fin"][:, :N_SMALL], 1e-10)
+    st64 = S.sfhk_stats_get(e)
     S.sfhk_propagate(ctx, e, _opts(S, S.SFHK_MIXED))
     err = _rel(S.sfhk_dipole(ctx, e, nt), h2_oracle["vz_small"])
     print(f"small workload, mixed vs oracle: {err:.3e}")
     assert err <= 1e-4
+    # recombination evaluations: at most one per integrated step and birth,
+    # nearly the same in both precisions (their e^-30 and e^-200 thresholds)
+    st = S.sfhk_stats_get(e)
+    for x in (st, st64):
+        assert 0 < x["recomb_evals"] <= x["traj_steps"] + N_SMALL
+    assert abs(st["recomb_evals"] - st64["recomb_evals"]) <= 0.05 * st64["recomb_evals"]
     S.sfhk_destroy_ensemble(e)
     S.sfhk_destroy_pulse(ph)
     S.sfhk_destroy_target(th)
