@@ -154,19 +154,22 @@ void fill_recomb(const DevTarget& T, double gamma, DevRecomb& R)
 
 // Table rows of the polyatomic kernel for a set of ensembles launched
 // together: 0 for diatomic targets, else the largest n_slots; SFHK_E_INVAL
-// when the set mixes the two.
-int poly_slots(sfhk_ensemble* const* ens, int n_ens, int* slots)
+// when the set mixes the two.  nc (may be null): the centre count the
+// polyatomic targets share, 0 when they differ.
+int poly_slots(sfhk_ensemble* const* ens, int n_ens, int* slots, int* nc)
 {
-    int np = 0, mx = 0;
+    int np = 0, mx = 0, common = -1;
     for (int i = 0; i < n_ens; ++i) {
         const DevTarget& T = ens[i]->tgt->dev;
         if (T.kind == SFHK_POT_POLYATOMIC) {
             ++np;
             mx = std::max(mx, std::max(1, T.n_slots));
+            common = (common < 0 || common == T.n_centres) ? T.n_centres : 0;
         }
     }
     if (np != 0 && np != n_ens) return SFHK_E_INVAL;
     *slots = mx;
+    if (nc) *nc = common > 0 ? common : 0;
     return SFHK_OK;
 }
 
@@ -697,11 +700,11 @@ int sfhk_propagate(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, void* 
     int bt, var, bps;
     shape(c, *o, &bt, &var, &bps);
     SFHK_CUDA_TRY(record_event(e->ev_start, s));
-    int slots = 0;
-    poly_slots(&e, 1, &slots);
+    int slots = 0, nc = 0;
+    poly_slots(&e, 1, &slots, &nc);
     rc = launch_propagate(o->precision, var, (const DevInstance*)e->inst.p,
                           (const WorkItem*)e->items.p, e->n_items, (unsigned int*)e->qctr.p, bt,
-                          bps, c->sm_count, s, slots);
+                          bps, c->sm_count, s, slots, nc);
     if (rc) return rc;
     SFHK_CUDA_TRY(record_event(e->ev_stop, s));
     SFHK_CUDA_TRY(record_event(e->ev_done, s));
@@ -718,8 +721,8 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
         if (!ens[i] || ens[i]->ctx != c) return SFHK_E_INVAL;
     int rc = check_opts(o);
     if (rc) return rc;
-    int slots = 0;
-    if ((rc = poly_slots(ens, n_ens, &slots))) return rc;
+    int slots = 0, nc = 0;
+    if ((rc = poly_slots(ens, n_ens, &slots, &nc))) return rc;
     if ((rc = set_device(c->device))) return rc;
     cudaStream_t s = as_stream(stream);
     long long total_items = 0;
@@ -782,7 +785,7 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
         if (record_event(ens[i]->ev_start, s) != cudaSuccess) rc = SFHK_E_CUDA;
     if (!rc)
         rc = launch_propagate(o->precision, var, d_inst, d_sorted, (int)total_items, d_ctr, bt,
-                              bps, c->sm_count, s, slots);
+                              bps, c->sm_count, s, slots, nc);
     for (int i = 0; i < n_ens && !rc; ++i) {
         if (record_event(ens[i]->ev_stop, s) != cudaSuccess ||
             record_event(ens[i]->ev_done, s) != cudaSuccess)
@@ -808,6 +811,7 @@ struct sfhk_batch {
     long long total_items = 0;
     int max_nt = 1;
     int poly_slots = 0;
+    int poly_nc = 0;                 // common centre count of the polyatomic targets
 };
 
 extern "C" {
@@ -820,13 +824,14 @@ int sfhk_batch_create(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens, const s
         if (!ens[i] || ens[i]->ctx != c) return SFHK_E_INVAL;
     int rc = check_opts(o);
     if (rc) return rc;
-    int slots = 0;
-    if ((rc = poly_slots(ens, n_ens, &slots))) return rc;
+    int slots = 0, nc = 0;
+    if ((rc = poly_slots(ens, n_ens, &slots, &nc))) return rc;
     if ((rc = set_device(c->device))) return rc;
     sfhk_batch* b = new (std::nothrow) sfhk_batch;
     if (!b) return SFHK_E_NOMEM;
     b->ctx = c;
     b->poly_slots = slots;
+    b->poly_nc = nc;
     b->ens.assign(ens, ens + n_ens);
     b->opts = *o;
     b->opts.dump_final = 0;
@@ -907,7 +912,7 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
     // the kernel is timed with the ensembles' events (also inside a captured graph)
     for (sfhk_ensemble* e : b->ens) SFHK_CUDA_TRY(record_event(e->ev_start, s));
     rc = launch_propagate(b->opts.precision, var, b->d_inst, b->d_sorted, (int)b->total_items,
-                          b->d_ctr, bt, bps, b->ctx->sm_count, s, b->poly_slots);
+                          b->d_ctr, bt, bps, b->ctx->sm_count, s, b->poly_slots, b->poly_nc);
     if (rc) return rc;
     for (sfhk_ensemble* e : b->ens) {
         SFHK_CUDA_TRY(record_event(e->ev_stop, s));
@@ -940,8 +945,8 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
     if ((rc = prepare_outputs(e, oo, 0))) return rc;
     const DevInstance I = make_instance(e, oo);
     SFHK_CUDA_TRY(cudaMemcpy(e->inst.p, &I, sizeof I, cudaMemcpyHostToDevice));
-    int slots = 0;
-    poly_slots(&e, 1, &slots);
+    int slots = 0, nc = 0;
+    poly_slots(&e, 1, &slots, &nc);
     const int blocks[3] = {32, 64, 128};
     // one timed launch per shape (after a warm-up launch), then the three
     // fastest shapes timed twice more: launch times of close shapes differ by
@@ -950,7 +955,8 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
         SFHK_CUDA_TRY(cudaEventRecord(e->ev_start, 0));
         const int r = launch_propagate(o->precision, v, (const DevInstance*)e->inst.p,
                                        (const WorkItem*)e->items.p, items,
-                                       (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0, slots);
+                                       (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0, slots,
+                                       nc);
         if (r) return r;
         SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, 0));
         SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_stop));

@@ -384,68 +384,94 @@ __device__ __forceinline__ void tab_store(R* tab, int r, R x, R y, R z)
 //   vc = (Zinf + dZ e^{-alpha s}) u,  g1 = Zinf u^3 + dZ e^{-alpha s}(alpha u^2 + u^3),
 //   g2 = -u^2 [3 Zinf u^3 + dZ e^{-alpha s} u (alpha^2 + 3 alpha u + 3 u^2)],
 //   V = -sum vc,  F = -sum g1 d,  H = (sum g1) I + sum g2 d d^T.
-template <typename R, bool LO, bool OFS, typename Target>
+template <typename R>
+struct PolyAcc {
+    R V, Fx, Fy, Fz, gs, hxx, hyy, hzz, hxy, hxz, hyz;
+};
+
+// one centre's terms added to the sums.  BRANCH: skip the screening terms
+// of a centre whose dZ is 0 (the generic loop); without it they are
+// computed and vanish through dZ = 0 exactly (the unrolled loops, where a
+// branch per centre costs more than the arithmetic it saves)
+template <typename R, bool LO, bool OFS, bool BRANCH, typename Target>
+__device__ __forceinline__ void poly_centre(const Target& T, const R* tab, int c, R a2,
+                                            const R q[3], const R l[3], const R o[3],
+                                            PolyAcc<R>& A)
+{
+    constexpr bool F32 = std::is_same<R, float>::value;
+    R cc[3], d[3];
+    tab_row(tab, c, cc[0], cc[1], cc[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d[a] = LO ? (q[a] - cc[a]) + l[a] : q[a] - cc[a];
+        if (OFS) d[a] += o[a];
+    }
+    R Zinf, dZ, al;
+    if constexpr (F32) {
+        const float4 k = T.cq_f[c];           // one 16-byte load
+        Zinf = k.x;
+        dZ = k.y;
+        al = k.z;
+    } else {
+        Zinf = T.cZinf[c];
+        dZ = T.cdZ[c];
+        al = T.calpha[c];
+    }
+    const R s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + a2;
+    const R u = rsqrt_t<R>(s2);
+    const R u2 = u * u, u3 = u2 * u;
+    R vc, g1, g2;
+    if (!BRANCH || dZ != R(0)) {
+        const R de = dZ * exp_t<R>(-al * (s2 * u));
+        vc = (Zinf + de) * u;
+        g1 = Zinf * u3 + de * (al * u2 + u3);
+        g2 = -u2 * (R(3) * Zinf * u3 + de * u * (al * al + R(3) * al * u + R(3) * u2));
+    } else {
+        vc = Zinf * u;
+        g1 = Zinf * u3;
+        g2 = R(-3) * Zinf * u3 * u2;
+    }
+    A.V -= vc;
+    A.Fx -= g1 * d[0];
+    A.Fy -= g1 * d[1];
+    A.Fz -= g1 * d[2];
+    A.gs += g1;
+    const R gx = g2 * d[0], gy = g2 * d[1], gz = g2 * d[2];
+    A.hxx += gx * d[0];
+    A.hyy += gy * d[1];
+    A.hzz += gz * d[2];
+    A.hxy += gx * d[1];
+    A.hxz += gx * d[2];
+    A.hyz += gy * d[2];
+}
+
+// NC > 0: the target has exactly NC centres (the loop unrolled); 0: any
+// number (a loop over T.n_centres)
+template <typename R, bool LO, bool OFS, int NC, typename Target>
 __device__ __forceinline__ void potential_poly(const Target& T, const R* tab, R a2,
                                                const R q[3], const R l[3], R ox, R oy, R oz,
                                                R& V, R& Fx, R& Fy, R& Fz, Sym3<R>& H)
 {
-    constexpr bool F32 = std::is_same<R, float>::value;
-    V = Fx = Fy = Fz = R(0);
-    R gs = R(0), hxx = R(0), hyy = R(0), hzz = R(0), hxy = R(0), hxz = R(0), hyz = R(0);
+    PolyAcc<R> A = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     const R o[3] = {ox, oy, oz};
-#pragma unroll 1
-    for (int c = 0; c < T.n_centres; ++c) {
-        R cc[3], d[3];
-        tab_row(tab, c, cc[0], cc[1], cc[2]);
+    if constexpr (NC > 0) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            d[a] = LO ? (q[a] - cc[a]) + l[a] : q[a] - cc[a];
-            if (OFS) d[a] += o[a];
-        }
-        R Zinf, dZ, al;
-        if constexpr (F32) {
-            const float4 k = T.cq_f[c];           // one 16-byte load
-            Zinf = k.x;
-            dZ = k.y;
-            al = k.z;
-        } else {
-            Zinf = T.cZinf[c];
-            dZ = T.cdZ[c];
-            al = T.calpha[c];
-        }
-        const R s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + a2;
-        const R u = rsqrt_t<R>(s2);
-        const R u2 = u * u, u3 = u2 * u;
-        R vc, g1, g2;
-        if (dZ != R(0)) {
-            const R de = dZ * exp_t<R>(-al * (s2 * u));
-            vc = (Zinf + de) * u;
-            g1 = Zinf * u3 + de * (al * u2 + u3);
-            g2 = -u2 * (R(3) * Zinf * u3 + de * u * (al * al + R(3) * al * u + R(3) * u2));
-        } else {
-            vc = Zinf * u;
-            g1 = Zinf * u3;
-            g2 = R(-3) * Zinf * u3 * u2;
-        }
-        V -= vc;
-        Fx -= g1 * d[0];
-        Fy -= g1 * d[1];
-        Fz -= g1 * d[2];
-        gs += g1;
-        const R gx = g2 * d[0], gy = g2 * d[1], gz = g2 * d[2];
-        hxx += gx * d[0];
-        hyy += gy * d[1];
-        hzz += gz * d[2];
-        hxy += gx * d[1];
-        hxz += gx * d[2];
-        hyz += gy * d[2];
+        for (int c = 0; c < NC; ++c) poly_centre<R, LO, OFS, false>(T, tab, c, a2, q, l, o, A);
+    } else {
+#pragma unroll 1
+        for (int c = 0; c < T.n_centres; ++c)
+            poly_centre<R, LO, OFS, true>(T, tab, c, a2, q, l, o, A);
     }
-    H.xx = hxx + gs;
-    H.yy = hyy + gs;
-    H.zz = hzz + gs;
-    H.xy = hxy;
-    H.xz = hxz;
-    H.yz = hyz;
+    V = A.V;
+    Fx = A.Fx;
+    Fy = A.Fy;
+    Fz = A.Fz;
+    H.xx = A.hxx + A.gs;
+    H.yy = A.hyy + A.gs;
+    H.zz = A.hzz + A.gs;
+    H.xy = A.hxy;
+    H.xz = A.hxz;
+    H.yz = A.hyz;
 }
 
 }  // namespace sfhk

@@ -179,7 +179,7 @@ int configure_kernels();
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,
-                     int poly_slots = 0);
+                     int poly_slots = 0, int poly_nc = 0);
 int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm);
 int propagate_variant_maxreg(int variant_index);   // 0 = no cap
 // server slice: items ring[(base + i) & mask], i < n_items; warps stop pulling

@@ -269,13 +269,14 @@ __device__ __forceinline__ void rk4sum3<float>(float a, const float u[3], const 
 // The field at a stage point base + o: the two-centre potential from the
 // step's centre differences e, or (POLY) the N-centre potential from this
 // lane's column of the centre table.
-template <typename R, bool MIXED, bool POLY, bool OFS>
+template <typename R, bool MIXED, bool POLY, bool OFS, int NC = 0>
 __device__ __forceinline__ void field_at(const PotConst<R>& K, const R e[2][3], const DevTarget* T,
                                          const R* tab, const R q[3], const R ql[3], R ox, R oy,
                                          R oz, R& V, R F[3], Sym3<R>& H)
 {
     if constexpr (POLY)
-        potential_poly<R, MIXED, OFS>(*T, tab, K.a2, q, ql, ox, oy, oz, V, F[0], F[1], F[2], H);
+        potential_poly<R, MIXED, OFS, NC>(*T, tab, K.a2, q, ql, ox, oy, oz, V, F[0], F[1], F[2],
+                                          H);
     else
         potential<R, OFS>(K, e, ox, oy, oz, V, F[0], F[1], F[2], H);
 }
@@ -283,7 +284,7 @@ __device__ __forceinline__ void field_at(const PotConst<R>& K, const R e[2][3], 
 // One RK4 step's stage evaluations from (q, p) (high part q, low part ql):
 // the four stage Hessians and the increments dq, dp, dS of the step.  Stage
 // points are formed as base + offset (see potential()).
-template <typename R, bool MIXED, bool POLY = false>
+template <typename R, bool MIXED, bool POLY = false, int NC = 0>
 __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], const R ql[3],
                                            const R p[3], R E1, R E2, R E4, R h, R h2, R h6,
                                            Sym3<R> H[4], R dq[3], R dp[3], R& dS,
@@ -292,27 +293,27 @@ __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], c
     R V, F[3], e[2][3];
     if constexpr (!POLY) centre_diffs<R, MIXED>(K, q, ql, e);
     const R z0 = R(0);
-    field_at<R, MIXED, POLY, false>(K, e, T, tab, q, ql, z0, z0, z0, V, F, H[0]);
+    field_at<R, MIXED, POLY, false, NC>(K, e, T, tab, q, ql, z0, z0, z0, V, F, H[0]);
     const R k1p[3] = {F[0], F[1], F[2] - E1};
     const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
     R o[3], p2[3];
     scale3(h2, p, o);
     axpy3(h2, k1p, p, p2);
-    field_at<R, MIXED, POLY, true>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[1]);
+    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[1]);
     const R k2p[3] = {F[0], F[1], F[2] - E2};
     const R k2s =
         R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - (q[2] + o[2]) * E2;
     R p3[3];
     scale3(h2, p2, o);
     axpy3(h2, k2p, p, p3);
-    field_at<R, MIXED, POLY, true>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[2]);
+    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[2]);
     const R k3p[3] = {F[0], F[1], F[2] - E2};
     const R k3s =
         R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - (q[2] + o[2]) * E2;
     R p4[3];
     scale3(h, p3, o);
     axpy3(h, k3p, p, p4);
-    field_at<R, MIXED, POLY, true>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[3]);
+    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[3]);
     const R k4s =
         R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - (q[2] + o[2]) * E4;
     dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
@@ -678,8 +679,9 @@ constexpr int kRedStride = kWarp + 1;
 constexpr int kRedElems = kWarp * kRedStride;
 
 // POLY: a polyatomic target; tab is this lane's column of the warp's table
-// of lab-frame centre positions and p directions (rows of 32 words).
-template <bool MIXED, bool POLY = false>
+// of lab-frame centre positions and p directions (rows of 32 words); NC > 0:
+// every such target of the launch has exactly NC centres.
+template <bool MIXED, bool POLY = false, int NC = 0>
 __device__ __forceinline__ void process_item(const DevInstance& I, const WorkItem& W, int lane,
                                              typename std::conditional<MIXED, float, double>::type* red,
                                              typename std::conditional<MIXED, float, double>::type* tab = nullptr)
@@ -908,7 +910,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             // ---- one RK4 step to t_{nn+1}
             if (live && status == 0 && nn < nt - 1) {
                 ++steps;
-                stage_eval<R, MIXED, POLY>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS,
+                stage_eval<R, MIXED, POLY, NC>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS,
                                            &I.tgt, tab);
                 if constexpr (MIXED) {
                     acc2x2(q[0], q[1], ql[0], ql[1], dq[0], dq[1]);
@@ -1012,7 +1014,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
 // reduction buffers, every warp has a table of `slots` rows x kTabWords x 32
 // words (this lane's column starts kTabWords words per lane in for FP32
 // float4 rows, one word for the FP64 rows).
-template <bool MIXED, bool POLY = false>
+template <bool MIXED, bool POLY = false, int NC = 0>
 __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ items, int n_items,
                                           unsigned int* __restrict__ counter, int slots = 0)
@@ -1032,7 +1034,7 @@ __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const WorkItem W = items[it];
-        process_item<MIXED, POLY>(insts[W.inst], W, lane, red, tab);
+        process_item<MIXED, POLY, NC>(insts[W.inst], W, lane, red, tab);
     }
 }
 
@@ -1095,21 +1097,23 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
 {
     run_queue<MIXED>(insts, items, n_items, counter);
 }
-// Polyatomic targets, with the same register-cap variants.
-template <bool MIXED>
+// Polyatomic targets, with the same register-cap variants; NC = 3: every
+// target of the launch has three centres (loop over the centres unrolled),
+// 0: any number.
+template <bool MIXED, int NC>
 __global__ void __launch_bounds__(128)
     k_propagate_poly_nocap(const DevInstance* __restrict__ insts,
                            const WorkItem* __restrict__ items, int n_items,
                            unsigned int* __restrict__ counter, int slots)
 {
-    run_queue<MIXED, true>(insts, items, n_items, counter, slots);
+    run_queue<MIXED, true, NC>(insts, items, n_items, counter, slots);
 }
-template <bool MIXED, int MAXREG>
+template <bool MIXED, int MAXREG, int NC>
 __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
     k_propagate_poly(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ items,
                      int n_items, unsigned int* __restrict__ counter, int slots)
 {
-    run_queue<MIXED, true>(insts, items, n_items, counter, slots);
+    run_queue<MIXED, true, NC>(insts, items, n_items, counter, slots);
 }
 template <bool MIXED>
 __global__ void __launch_bounds__(128)
@@ -1150,16 +1154,27 @@ KernelFn variant(int precision, int v)
     return precision == SFHK_MIXED ? mixed[v] : fp64[v];
 }
 
-PolyFn poly_variant(int precision, int v)
+// centre counts with a specialised (unrolled) polyatomic kernel
+constexpr int kPolyNC[2] = {0, 3};
+
+template <int NC>
+PolyFn poly_variant_nc(int precision, int v)
 {
     static const PolyFn mixed[kPropVariants] = {
-        k_propagate_poly_nocap<true>, k_propagate_poly<true, 168>, k_propagate_poly<true, 152>,
-        k_propagate_poly<true, 144>, k_propagate_poly<true, 136>, k_propagate_poly<true, 128>};
+        k_propagate_poly_nocap<true, NC>, k_propagate_poly<true, 168, NC>,
+        k_propagate_poly<true, 152, NC>, k_propagate_poly<true, 144, NC>,
+        k_propagate_poly<true, 136, NC>, k_propagate_poly<true, 128, NC>};
     static const PolyFn fp64[kPropVariants] = {
-        k_propagate_poly_nocap<false>, k_propagate_poly<false, 168>,
-        k_propagate_poly<false, 152>, k_propagate_poly<false, 144>,
-        k_propagate_poly<false, 136>, k_propagate_poly<false, 128>};
+        k_propagate_poly_nocap<false, NC>, k_propagate_poly<false, 168, NC>,
+        k_propagate_poly<false, 152, NC>, k_propagate_poly<false, 144, NC>,
+        k_propagate_poly<false, 136, NC>, k_propagate_poly<false, 128, NC>};
     return precision == SFHK_MIXED ? mixed[v] : fp64[v];
+}
+
+// nc: the common centre count of the launch's targets (0 when they differ)
+PolyFn poly_variant(int precision, int v, int nc)
+{
+    return nc == 3 ? poly_variant_nc<3>(precision, v) : poly_variant_nc<0>(precision, v);
 }
 
 SliceFn slice_variant(int precision, int v)
@@ -1227,11 +1242,12 @@ namespace {
 // Polyatomic launch: the reduction buffers plus every warp's centre table.
 int launch_poly(int precision, int variant_index, const DevInstance* insts,
                 const WorkItem* items, int n_items, unsigned int* item_counter,
-                int block_threads, int blocks_per_sm, int sm_count, int slots, cudaStream_t s)
+                int block_threads, int blocks_per_sm, int sm_count, int slots, int nc,
+                cudaStream_t s)
 {
     if (slots < 1 || slots > SFHK_MAX_CENTRES + SFHK_MAX_PRIM) return SFHK_E_INVAL;
     const bool mixed = precision == SFHK_MIXED;
-    const PolyFn fn = poly_variant(precision, variant_index);
+    const PolyFn fn = poly_variant(precision, variant_index, nc);
     const size_t elem = mixed ? sizeof(float) : sizeof(double);
     const size_t smem = red_bytes(precision, block_threads) +
                         size_t(block_threads / kWarp) * slots * (mixed ? 4 : 3) * kWarp * elem;
@@ -1266,9 +1282,10 @@ int configure_kernels()
                                                        (SFHK_MAX_CENTRES + SFHK_MAX_PRIM) *
                                                        (prec == SFHK_MIXED ? 4 : 3) * kWarp * elem;
         for (int v = 0; v < kPropVariants; ++v)
-            SFHK_CUDA_TRY(cudaFuncSetAttribute(poly_variant(prec, v),
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem));
+            for (int nc : kPolyNC)
+                SFHK_CUDA_TRY(cudaFuncSetAttribute(poly_variant(prec, v, nc),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem));
     }
     return SFHK_OK;
 }
@@ -1276,13 +1293,13 @@ int configure_kernels()
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,
-                     int poly_slots)
+                     int poly_slots, int poly_nc)
 {
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
     if (poly_slots > 0)
         return launch_poly(precision, variant_index, insts, items, n_items, item_counter,
-                           block_threads, blocks_per_sm, sm_count, poly_slots, s);
+                           block_threads, blocks_per_sm, sm_count, poly_slots, poly_nc, s);
     int occ = 0;
     int rc = propagate_occupancy(precision, variant_index, block_threads, &occ);
     if (rc) return rc;

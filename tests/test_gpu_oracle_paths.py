@@ -108,12 +108,14 @@ def test_small_workload_end_to_end(S, ctx, h2_oracle):
     err = _rel(S.sfhk_dipole(ctx, e, nt), h2_oracle["vz_small"])
     print(f"small workload, mixed vs oracle: {err:.3e}")
     assert err <= 1e-4
-    # recombination evaluations: at most one per integrated step and birth,
-    # nearly the same in both precisions (their e^-30 and e^-200 thresholds)
+    # recombination evaluations: at most one per integrated step and birth;
+    # FP64 skips an overlap only below e^-200 of its peak, mixed precision
+    # below e^-30, so mixed precision evaluates fewer (1 % slack for the
+    # trajectories whose paths differ in the last digits)
     st = S.sfhk_stats_get(e)
     for x in (st, st64):
         assert 0 < x["recomb_evals"] <= x["traj_steps"] + N_SMALL
-    assert abs(st["recomb_evals"] - st64["recomb_evals"]) <= 0.05 * st64["recomb_evals"]
+    assert st["recomb_evals"] <= 1.01 * st64["recomb_evals"]
     S.sfhk_destroy_ensemble(e)
     S.sfhk_destroy_pulse(ph)
     S.sfhk_destroy_target(th)

@@ -161,6 +161,34 @@ def test_batch_of_polyatomic_ensembles(S, ctx):
         S.sfhk_destroy_ensemble(e)
 
 
+def test_batch_mixing_centre_counts_uses_the_generic_kernel(S, ctx):
+    """H2O (three centres: alone it runs the kernel unrolled for three
+    centres) batched with N2 written as a two-centre polyatomic: the batch
+    runs the kernel for any number of centres, and each dipole equals the
+    one of its ensemble alone (FP64 to the oracle's tolerance, the two
+    kernels summing the centres in a different order; mixed precision to
+    1e-5)."""
+    cases = [(W.TARGETS["H2O"], W.PULSE_800, W.ISO, 300, 1),
+             (W.diatomic_as_poly(W.TARGETS["N2"]), W.pulse(1000.0, 1.4e14, 2), W.COS2, 200, 2)]
+    hs, ens, nts = [], [], []
+    for t, p, al, n, seed in cases:
+        th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, p)
+        hs += [th, ph]
+        ens.append(S.sfhk_sample_initial(ctx, th, ph, al, n, seed, seed))
+        nts.append(S.sfhk_pulse_grid(ph)["nt"])
+    for prec, tol in ((S.SFHK_FP64, 1e-9), (S.SFHK_MIXED, 1e-5)):
+        opts = S.run_opts(prec, GAMMA, CUT, stab_cutoff=STAB, stab_taper=W.STAB_TAPER)
+        alone = []
+        for e, nt in zip(ens, nts):
+            S.sfhk_propagate(ctx, e, opts)
+            alone.append(S.sfhk_dipole(ctx, e, nt))
+        S.sfhk_propagate_batch(ctx, ens, opts)
+        for e, nt, a in zip(ens, nts, alone):
+            assert _rel_l2(S.sfhk_dipole(ctx, e, nt), a) <= tol, prec
+    for e in ens:
+        S.sfhk_destroy_ensemble(e)
+
+
 def test_polyatomic_validation(S, ctx):
     t = W.TARGETS["H2O_3a1"]
     th, ph = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, W.PULSE_800)
