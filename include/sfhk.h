@@ -437,10 +437,12 @@ SFHK_API int sfhk_gabor(const double* vz, size_t nt, double dt, double t_origin,
  * its trajectories as independent CPU jobs).  A host thread owned by the
  * server admits submitted requests (one target, pulse, alignment and
  * trajectory count each) in arrival order while its device-memory budget,
- * its instance slots and its work ring have room, samples each admitted
+ * its instance slots and its work rings have room, samples each admitted
  * request on the device, and appends its work items (32 trajectories, longest
- * first) to one device ring.  The GPU runs the integrator as a sequence of
- * persistent slices over that ring: a slice's warps stop taking new items
+ * first) to a device ring: one for diatomic targets, one for polyatomic ones.
+ * The GPU runs the integrator as a sequence of persistent slices over those
+ * rings (each slice launches the diatomic and then the polyatomic integrator
+ * over the rings that have work): a slice's warps stop taking new items
  * once `slice_ms` has passed (an item once taken runs to its end) and every
  * request that arrived meanwhile joins the next slice, so the work of
  * requests of different sizes, targets and pulses runs on the device
@@ -506,9 +508,12 @@ typedef struct {
 SFHK_API int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** out);
 /* Stops the server thread after its current slice; unfinished requests are dropped. */
 SFHK_API int sfhk_server_destroy(sfhk_server* s);
-/* Queue a request; returns at once with its id.  Errors: SFHK_E_INVAL (bad
- * descriptor, or a polyatomic target: the server runs diatomic targets
- * only), SFHK_E_NOMEM (admission refused: the queue is full, or the
+/* Queue a request; returns at once with its id.  Diatomic and polyatomic
+ * targets are both served: their work items go to two device rings, and each
+ * slice runs the diatomic and the polyatomic integrator in turn over them.
+ * Errors: SFHK_E_INVAL (bad descriptor; for a polyatomic target also a
+ * quadrature alignment or the modified saddle, which rest on the diatomic's
+ * symmetry), SFHK_E_NOMEM (admission refused: the queue is full, or the
  * request alone needs more than the device-memory budget). */
 SFHK_API int sfhk_submit(sfhk_server* s, const sfhk_request* req, uint64_t* req_id);
 /* SFHK_E_BUSY while the request is queued or running; once it has ended,

@@ -117,9 +117,10 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 
 # dram__bytes_read.sum + dram__bytes_write.sum per full-size launch of the
 # dominant kernel, keyed by (workload, kernel variant), from an ncu capture of
-# the kernel: H2 0/45/90 deg captured at 3 x 2e5 trajectories with the
-# 168-register variant in 32-thread blocks (63.3 MB read + 3.0 MB written) and
-# scaled by trajectories to 3 x 1e6.
-# H2O 1b1 isotropic: captured at 2e5 trajectories with the 128-register
-# variant in 64-thread blocks (19.8 MB read + 0.19 MB written), scaled to 1e6.
-TRAFFIC = {("h2-angles", 2): 331.0e6, ("h2o-iso", 6): 100.0e6}
+# the current kernel, scaled by the trajectories to the full size (the
+# traffic is the initial-point SoA read once, 99 B per trajectory):
+# H2 0/45/90 deg captured at 3 x 5e4 trajectories with the 168-register
+# variant in 32-thread blocks (14.9 MB read, 0 written), scaled to 3 x 1e6;
+# H2O 1b1 isotropic (three-centre kernel) captured at 1e5 trajectories with
+# the 168-register variant in 64-thread blocks (9.84 MB read), scaled to 1e6.
+TRAFFIC = {("h2-angles", 2): 298.1e6, ("h2o-iso", 2): 98.4e6}

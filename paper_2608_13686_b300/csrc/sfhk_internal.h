@@ -184,12 +184,14 @@ int propagate_occupancy(int precision, int variant_index, int block_threads, int
 int propagate_variant_maxreg(int variant_index);   // 0 = no cap
 // server slice: items ring[(base + i) & mask], i < n_items; warps stop pulling
 // new items slice_ns after the first warp started (0 = no limit); *t0 must be
-// zero before the launch; *counter ends >= the number of items taken
+// zero before the launch; *counter ends >= the number of items taken.
+// poly_slots > 0: the ring holds polyatomic requests' items, whose centre
+// tables have that many rows per lane
 int launch_propagate_slice(int precision, int variant_index, const DevInstance* insts,
                            const WorkItem* ring, unsigned int mask, unsigned int base,
                            int n_items, unsigned int* counter, unsigned long long slice_ns,
                            unsigned long long* t0, int block_threads, int sm_count,
-                           cudaStream_t s);
+                           cudaStream_t s, int poly_slots = 0);
 
 // spectrum (sfhk_spectrum.cu)
 // Gabor map (sfhk_gabor.cu)

@@ -1050,18 +1050,25 @@ __device__ __forceinline__ unsigned long long global_ns()
 // runs to its end), count finished items per instance, and skip the items of
 // cancelled instances.  No thread waits on another: a warp only ever reads
 // the clock and an atomic counter.
-template <bool MIXED>
+// POLY: the ring holds polyatomic requests' items, and every warp has its
+// centre table of `slots` rows after the reduction buffers (as run_queue).
+template <bool MIXED, bool POLY = false>
 __device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ ring, unsigned int mask,
                                           unsigned int base, int n_items,
                                           unsigned int* __restrict__ counter,
                                           unsigned long long slice_ns,
-                                          unsigned long long* __restrict__ t0)
+                                          unsigned long long* __restrict__ t0, int slots = 0)
 {
     using R = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* red = reinterpret_cast<R*>(smem_raw) + (threadIdx.x / kWarp) * kRedElems;
     const int lane = threadIdx.x & (kWarp - 1);
+    R* tab = nullptr;
+    if constexpr (POLY)
+        tab = reinterpret_cast<R*>(smem_raw) + (blockDim.x / kWarp) * kRedElems +
+              (threadIdx.x / kWarp) * (slots * kTabWords<R> * kWarp) +
+              lane * (MIXED ? kTabWords<R> : 1);
     unsigned long long deadline = 0;
     if (lane == 0 && slice_ns) {
         const unsigned long long now = global_ns();
@@ -1076,7 +1083,7 @@ __device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
         if (it >= n_items) break;
         const WorkItem W = ring[(base + (unsigned int)it) & mask];
         const DevInstance& I = insts[W.inst];
-        if (I.cancel == nullptr || *I.cancel == 0) process_item<MIXED>(I, W, lane, red);
+        if (I.cancel == nullptr || *I.cancel == 0) process_item<MIXED, POLY>(I, W, lane, red, tab);
         if (lane == 0 && I.done_items != nullptr) atomicAdd(I.done_items, 1u);
     }
 }
@@ -1134,10 +1141,33 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
     run_slice<MIXED>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
 }
 
+template <bool MIXED>
+__global__ void __launch_bounds__(128)
+    k_propagate_slice_poly_nocap(const DevInstance* __restrict__ insts,
+                                 const WorkItem* __restrict__ ring, unsigned int mask,
+                                 unsigned int base, int n_items,
+                                 unsigned int* __restrict__ counter, unsigned long long slice_ns,
+                                 unsigned long long* __restrict__ t0, int slots)
+{
+    run_slice<MIXED, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, slots);
+}
+template <bool MIXED, int MAXREG>
+__global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
+    k_propagate_slice_poly(const DevInstance* __restrict__ insts,
+                           const WorkItem* __restrict__ ring, unsigned int mask,
+                           unsigned int base, int n_items, unsigned int* __restrict__ counter,
+                           unsigned long long slice_ns, unsigned long long* __restrict__ t0,
+                           int slots)
+{
+    run_slice<MIXED, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, slots);
+}
+
 using KernelFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*);
 using PolyFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*, int);
 using SliceFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, unsigned int, int,
                          unsigned int*, unsigned long long, unsigned long long*);
+using SlicePolyFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, unsigned int,
+                             int, unsigned int*, unsigned long long, unsigned long long*, int);
 
 // variants: index 0 = no register cap, then at most 168, 152, 144, 136, 128
 // registers per thread (12 to 16 resident warps per SM)
@@ -1190,6 +1220,19 @@ SliceFn slice_variant(int precision, int v)
     return precision == SFHK_MIXED ? mixed[v] : fp64[v];
 }
 
+SlicePolyFn slice_poly_variant(int precision, int v)
+{
+    static const SlicePolyFn mixed[kPropVariants] = {
+        k_propagate_slice_poly_nocap<true>, k_propagate_slice_poly<true, 168>,
+        k_propagate_slice_poly<true, 152>, k_propagate_slice_poly<true, 144>,
+        k_propagate_slice_poly<true, 136>, k_propagate_slice_poly<true, 128>};
+    static const SlicePolyFn fp64[kPropVariants] = {
+        k_propagate_slice_poly_nocap<false>, k_propagate_slice_poly<false, 168>,
+        k_propagate_slice_poly<false, 152>, k_propagate_slice_poly<false, 144>,
+        k_propagate_slice_poly<false, 136>, k_propagate_slice_poly<false, 128>};
+    return precision == SFHK_MIXED ? mixed[v] : fp64[v];
+}
+
 // dynamic shared memory of a block: one contribution buffer per warp
 size_t red_bytes(int precision, int block_threads)
 {
@@ -1203,14 +1246,26 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
                            const WorkItem* ring, unsigned int mask, unsigned int base,
                            int n_items, unsigned int* counter, unsigned long long slice_ns,
                            unsigned long long* t0, int block_threads, int sm_count,
-                           cudaStream_t s)
+                           cudaStream_t s, int poly_slots)
 {
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     if (variant_index < 0 || variant_index >= kPropVariants || n_items <= 0) return SFHK_E_INVAL;
+    if (poly_slots < 0 || poly_slots > SFHK_MAX_CENTRES + SFHK_MAX_PRIM) return SFHK_E_INVAL;
+    const bool poly = poly_slots > 0;
+    const bool mixed = precision == SFHK_MIXED;
+    const size_t elem = mixed ? sizeof(float) : sizeof(double);
+    // the polyatomic slices also hold every warp's centre table
+    const size_t smem = red_bytes(precision, block_threads) +
+                        (poly ? size_t(block_threads / kWarp) * poly_slots * (mixed ? 4 : 3) *
+                                    kWarp * elem
+                              : 0);
     int occ = 0;
-    const size_t smem = red_bytes(precision, block_threads);
-    SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, slice_variant(precision, variant_index), block_threads, smem));
+    if (poly)
+        SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, slice_poly_variant(precision, variant_index), block_threads, smem));
+    else
+        SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, slice_variant(precision, variant_index), block_threads, smem));
     if (occ < 1) occ = 1;
     const int warps_per_block = block_threads / kWarp;
     int grid = sm_count * occ;
@@ -1219,8 +1274,12 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
     SFHK_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
     SFHK_CUDA_TRY(cudaMemsetAsync(t0, 0, sizeof(unsigned long long), s));
     count_launch();
-    slice_variant(precision, variant_index)<<<grid, block_threads, smem, s>>>(
-        insts, ring, mask, base, n_items, counter, slice_ns, t0);
+    if (poly)
+        slice_poly_variant(precision, variant_index)<<<grid, block_threads, smem, s>>>(
+            insts, ring, mask, base, n_items, counter, slice_ns, t0, poly_slots);
+    else
+        slice_variant(precision, variant_index)<<<grid, block_threads, smem, s>>>(
+            insts, ring, mask, base, n_items, counter, slice_ns, t0);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
 }
@@ -1281,11 +1340,15 @@ int configure_kernels()
         const size_t smem = red_bytes(prec, 128) + size_t(128 / kWarp) *
                                                        (SFHK_MAX_CENTRES + SFHK_MAX_PRIM) *
                                                        (prec == SFHK_MIXED ? 4 : 3) * kWarp * elem;
-        for (int v = 0; v < kPropVariants; ++v)
+        for (int v = 0; v < kPropVariants; ++v) {
             for (int nc : kPolyNC)
                 SFHK_CUDA_TRY(cudaFuncSetAttribute(poly_variant(prec, v, nc),
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)smem));
+            SFHK_CUDA_TRY(cudaFuncSetAttribute(slice_poly_variant(prec, v),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        }
     }
     return SFHK_OK;
 }

@@ -2,9 +2,10 @@
 // "serving").  One host thread per server owns a private context and runs
 //   admit -> slice -> harvest
 // in a loop: admitted requests are sampled on the device and their work items
-// appended to a device ring; a slice is one launch of the integrator over the
-// ring's unprocessed items that stops taking items after slice_ms; finished
-// requests are copied out and their device memory released.
+// appended to a device ring (one for diatomic targets, one for polyatomic
+// ones, whose integrator is a separate kernel); a slice is one launch of the
+// integrator over each ring's unprocessed items that stops taking items after
+// slice_ms; finished requests are copied out and their device memory released.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +26,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// per-ring counters and slice start times share one small buffer each, one
+// entry every kCtrStride bytes
+constexpr size_t kCtrStride = 64;
+
 enum ReqState { kPending = 0, kActive = 1, kEnded = 2 };
 
 struct Req {
@@ -43,6 +48,8 @@ struct Req {
     double t_origin = 0, dt = 0;
     std::vector<double> vz, yield, phase;
     uint64_t traj_steps = 0, n_filtered = 0, n_unstable = 0, n_nonfinite = 0;
+    int ring = 0;                    // 0: diatomic target, 1: polyatomic
+    int poly_slots = 0;              // centre-table rows of a polyatomic target
 };
 
 size_t bytes_estimate(uint64_t n, int nt)
@@ -78,17 +85,21 @@ struct sfhk_server {
     Clock::time_point t_start;
     // device side
     cudaStream_t s = nullptr;
-    sfhk::DeviceBuf insts, ring, done, cancelf, ctr, t0, spec;
+    sfhk::DeviceBuf insts, done, cancelf, ctr, t0, spec;   // ctr, t0: one slot per ring
     unsigned int ring_cap = 0, mask = 0;
-    // ring positions, monotonic except that head steps back when a short
-    // request is put in front; they start far from zero so that this is
-    // possible even before the first slice has taken anything
-    uint64_t head = uint64_t(1) << 40, tail = uint64_t(1) << 40;
-    double queued_work = 0;          // items x Nt not yet taken (estimate)
+    // work rings: [0] diatomic, [1] polyatomic targets.  Positions are
+    // monotonic except that head steps back when a short request is put in
+    // front; they start far from zero so that this is possible even before
+    // the first slice has taken anything
+    struct Ring {
+        sfhk::DeviceBuf items;
+        uint64_t head = uint64_t(1) << 40, tail = uint64_t(1) << 40;
+        double queued_work = 0;      // items x Nt not yet taken (estimate)
+    } rings[2];
     std::vector<int> free_slots;
     std::vector<uint64_t> slot_req;
     unsigned int* h_done = nullptr;   // pinned
-    unsigned int* h_ctr = nullptr;
+    unsigned int* h_ctr = nullptr;    // pinned, one counter per ring (kCtrStride apart)
     int max_nt = 0;
     size_t base_bytes = 0;            // the server's own device buffers
     // stats
@@ -151,7 +162,8 @@ void admit(sfhk_server* S)
                 continue;
             }
             const uint64_t items = (q->r.n_traj + 31) / 32;
-            if (S->tail - S->head + items > S->ring_cap) return;
+            const auto& G = S->rings[q->r.target.kind == SFHK_POT_POLYATOMIC ? 1 : 0];
+            if (G.tail - G.head + items > S->ring_cap) return;
             const size_t est = bytes_estimate(q->r.n_traj, pulse_nt(q->r.pulse));
             size_t used = 0;
             sfhk_mem_used(S->ctx, &used);
@@ -180,8 +192,11 @@ void admit(sfhk_server* S)
                 rc = SFHK_E_CUDA;
         }
         if (!rc) {
-            // work items of this request (instance = its slot), appended to the ring
+            // work items of this request (instance = its slot), appended to its ring
             sfhk_ensemble* e = q->ens;
+            q->ring = q->tgt->dev.kind == SFHK_POT_POLYATOMIC ? 1 : 0;
+            q->poly_slots = q->ring ? std::max(1, q->tgt->dev.n_slots) : 0;
+            auto& G = S->rings[q->ring];
             rc = sfhk::launch_build_items((const int*)e->perm.p, (const int*)e->n0.p, e->n, slot,
                                           (sfhk::WorkItem*)e->items.p, S->s);
             const unsigned int n = (unsigned int)e->n_items;
@@ -191,13 +206,12 @@ void admit(sfhk_server* S)
             uint64_t pos;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
-                front = !S->o.fifo && S->tail > S->head && work < S->queued_work &&
-                        S->head >= n;
-                pos = front ? S->head - n : S->tail;
+                front = !S->o.fifo && G.tail > G.head && work < G.queued_work && G.head >= n;
+                pos = front ? G.head - n : G.tail;
             }
             const unsigned int at = (unsigned int)(pos & S->mask);
             const unsigned int first = std::min(n, S->ring_cap - at);
-            sfhk::WorkItem* ring = (sfhk::WorkItem*)S->ring.p;
+            sfhk::WorkItem* ring = (sfhk::WorkItem*)G.items.p;
             const sfhk::WorkItem* src = (const sfhk::WorkItem*)e->items.p;
             if (!rc && cudaMemcpyAsync(ring + at, src, sizeof(sfhk::WorkItem) * first,
                                        cudaMemcpyDeviceToDevice, S->s) != cudaSuccess)
@@ -212,9 +226,9 @@ void admit(sfhk_server* S)
                 q->t_origin = q->pul->t_origin;
                 q->dt = q->pul->dt;
                 std::lock_guard<std::mutex> lk(S->mu);
-                if (front) S->head -= n;
-                else S->tail += n;
-                S->queued_work += work;
+                if (front) G.head -= n;
+                else G.tail += n;
+                G.queued_work += work;
                 q->state = kActive;
                 q->t_admit = S->now();
             }
@@ -290,15 +304,17 @@ void harvest(sfhk_server* S)
 
 void run_slice(sfhk_server* S)
 {
-    uint64_t n64;
+    uint64_t n64[2];
+    int slots = 0;                   // centre-table rows the polyatomic slice needs
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        n64 = S->tail - S->head;
+        for (int k = 0; k < 2; ++k) n64[k] = S->rings[k].tail - S->rings[k].head;
         // cancellations of running requests reach the device before the slice
         for (size_t slot = 0; slot < S->slot_req.size(); ++slot) {
             const uint64_t id = S->slot_req[slot];
             if (!id) continue;
             Req* q = S->reqs[id].get();
+            if (q->state == kActive) slots = std::max(slots, q->poly_slots);
             if (q->cancel) {
                 static const int one = 1;
                 cudaMemcpyAsync((int*)S->cancelf.p + slot, &one, sizeof(int),
@@ -306,21 +322,32 @@ void run_slice(sfhk_server* S)
             }
         }
     }
-    if (n64 == 0) return;
-    const int n = (int)std::min<uint64_t>(n64, 0x7fffffffu);
+    if (n64[0] == 0 && n64[1] == 0) return;
+    if (n64[1] > 0 && slots < 1) slots = 1;
     int bt = S->ctx->tuned[S->ro.precision][0];
     int var = S->ctx->tuned[S->ro.precision][1];
     const auto t_a = Clock::now();
-    int rc = sfhk::launch_propagate_slice(
-        S->ro.precision, var, (const sfhk::DevInstance*)S->insts.p,
-        (const sfhk::WorkItem*)S->ring.p, S->mask, (unsigned int)(S->head & S->mask), n,
-        (unsigned int*)S->ctr.p, (unsigned long long)(S->o.slice_ms * 1e6),
-        (unsigned long long*)S->t0.p, bt, S->ctx->sm_count, S->s);
-    if (!rc &&
-        (cudaMemcpyAsync(S->h_ctr, S->ctr.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, S->s) !=
-             cudaSuccess ||
-         cudaMemcpyAsync(S->h_done, S->done.p, sizeof(unsigned int) * S->slot_req.size(),
-                         cudaMemcpyDeviceToHost, S->s) != cudaSuccess))
+    int rc = SFHK_OK;
+    int n[2] = {0, 0};
+    // one slice of each ring that has work, one after the other on the
+    // server's stream (each kernel fills the GPU while it runs)
+    for (int k = 0; k < 2 && !rc; ++k) {
+        if (n64[k] == 0) continue;
+        auto& G = S->rings[k];
+        n[k] = (int)std::min<uint64_t>(n64[k], 0x7fffffffu);
+        unsigned int* ctr = (unsigned int*)((char*)S->ctr.p + k * kCtrStride);
+        rc = sfhk::launch_propagate_slice(
+            S->ro.precision, var, (const sfhk::DevInstance*)S->insts.p,
+            (const sfhk::WorkItem*)G.items.p, S->mask, (unsigned int)(G.head & S->mask), n[k],
+            ctr, (unsigned long long)(S->o.slice_ms * 1e6),
+            (unsigned long long*)((char*)S->t0.p + k * kCtrStride), bt, S->ctx->sm_count, S->s,
+            k == 1 ? slots : 0);
+        if (!rc && cudaMemcpyAsync((char*)S->h_ctr + k * kCtrStride, ctr, sizeof(unsigned int),
+                                   cudaMemcpyDeviceToHost, S->s) != cudaSuccess)
+            rc = SFHK_E_CUDA;
+    }
+    if (!rc && cudaMemcpyAsync(S->h_done, S->done.p, sizeof(unsigned int) * S->slot_req.size(),
+                               cudaMemcpyDeviceToHost, S->s) != cudaSuccess)
         rc = SFHK_E_CUDA;
     if (!rc && cudaStreamSynchronize(S->s) != cudaSuccess) rc = SFHK_E_CUDA;
     const double busy = std::chrono::duration<double>(Clock::now() - t_a).count();
@@ -328,9 +355,15 @@ void run_slice(sfhk_server* S)
     ++S->st.slices;
     S->st.gpu_busy_s += busy;
     if (!rc) {
-        const uint64_t taken = std::min<uint64_t>(*S->h_ctr, (uint64_t)n);
-        S->queued_work = taken >= n64 ? 0.0 : S->queued_work * double(n64 - taken) / double(n64);
-        S->head += taken;
+        for (int k = 0; k < 2; ++k) {
+            if (n64[k] == 0) continue;
+            auto& G = S->rings[k];
+            const unsigned int got = *(const unsigned int*)((const char*)S->h_ctr + k * kCtrStride);
+            const uint64_t taken = std::min<uint64_t>(got, (uint64_t)n[k]);
+            G.queued_work =
+                taken >= n64[k] ? 0.0 : G.queued_work * double(n64[k] - taken) / double(n64[k]);
+            G.head += taken;
+        }
     }
 }
 
@@ -347,7 +380,7 @@ void loop(sfhk_server* S)
         bool work;
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            work = S->tail > S->head;
+            work = S->rings[0].tail > S->rings[0].head || S->rings[1].tail > S->rings[1].head;
         }
         if (work) {
             run_slice(S);
@@ -425,14 +458,15 @@ int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** o
         return rc;
     }
     S->max_nt = (1 << 16);
-    S->ring_cap = 1u << 22;                  // work items (64 MiB)
+    S->ring_cap = 1u << 22;                  // work items per ring (64 MiB)
     S->mask = S->ring_cap - 1;
     sfhk::Ctx* c = S->ctx;
     if ((rc = c->alloc(S->insts, sizeof(sfhk::DevInstance) * S->o.max_active)) ||
-        (rc = c->alloc(S->ring, sizeof(sfhk::WorkItem) * (size_t)S->ring_cap)) ||
+        (rc = c->alloc(S->rings[0].items, sizeof(sfhk::WorkItem) * (size_t)S->ring_cap)) ||
+        (rc = c->alloc(S->rings[1].items, sizeof(sfhk::WorkItem) * (size_t)S->ring_cap)) ||
         (rc = c->alloc(S->done, sizeof(unsigned int) * S->o.max_active)) ||
         (rc = c->alloc(S->cancelf, sizeof(int) * S->o.max_active)) ||
-        (rc = c->alloc(S->ctr, 256)) || (rc = c->alloc(S->t0, 256)) ||
+        (rc = c->alloc(S->ctr, 2 * kCtrStride)) || (rc = c->alloc(S->t0, 2 * kCtrStride)) ||
         (rc = c->alloc(S->spec, sizeof(double) * 5 * (size_t)S->max_nt))) {
         sfhk_destroy(S->ctx);
         delete S;
@@ -441,7 +475,7 @@ int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** o
     if (cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaHostAlloc((void**)&S->h_done, sizeof(unsigned int) * S->o.max_active,
                       cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void**)&S->h_ctr, 64, cudaHostAllocDefault) != cudaSuccess) {
+        cudaHostAlloc((void**)&S->h_ctr, 2 * kCtrStride, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         sfhk_destroy(S->ctx);
         delete S;
@@ -467,7 +501,8 @@ int sfhk_server_destroy(sfhk_server* S)
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
     sfhk::Ctx* c = S->ctx;
-    for (sfhk::DeviceBuf* b : {&S->insts, &S->ring, &S->done, &S->cancelf, &S->ctr, &S->t0, &S->spec})
+    for (sfhk::DeviceBuf* b : {&S->insts, &S->rings[0].items, &S->rings[1].items, &S->done,
+                               &S->cancelf, &S->ctr, &S->t0, &S->spec})
         c->release(*b);
     if (S->s) cudaStreamDestroy(S->s);
     if (S->h_done) cudaFreeHost(S->h_done);
@@ -483,7 +518,9 @@ int sfhk_submit(sfhk_server* S, const sfhk_request* r, uint64_t* id)
     const int nt = pulse_nt(r->pulse);
     if (nt < 2 || nt > S->max_nt || r->n_traj == 0 || r->n_traj > 2147483647ull ||
         !(r->target.Ip > 0.0) || r->target.n_prim < 1 || r->target.n_prim > SFHK_MAX_PRIM ||
-        r->target.kind == SFHK_POT_POLYATOMIC || !sfhk::align_valid(r->align))
+        !sfhk::align_valid(r->align) ||
+        (r->target.kind == SFHK_POT_POLYATOMIC &&
+         (r->align.kind == SFHK_ALIGN_QUADRATURE || r->target.ionization != SFHK_IONIZE_SFA)))
         return SFHK_E_INVAL;
     std::lock_guard<std::mutex> lk(S->mu);
     const size_t est = bytes_estimate(r->n_traj, nt);

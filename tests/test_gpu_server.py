@@ -145,10 +145,31 @@ def test_cancel(S):
     S.sfhk_server_destroy(srv)
 
 
-def test_polyatomic_request_is_refused(S):
-    """The server runs diatomic targets only (the polyatomic kernel is a
-    separate launch); a polyatomic request is refused at submission."""
-    srv = S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF))
-    with pytest.raises(S.SfhkError):
-        S.sfhk_submit(srv, S.request(W.TARGETS["H2O"], W.PULSE_800, W.ISO, 100, 1, 0))
-    S.sfhk_server_destroy(srv)
+def test_polyatomic_requests_are_served_with_diatomic_ones(S):
+    """Polyatomic requests (their own ring and integrator kernel) served in one
+    stream with diatomic ones, each result against the FP64 oracle on the same
+    draws: 1e-9 in FP64, 1e-4 in mixed precision.  A polyatomic request with a
+    quadrature alignment is refused at submission."""
+    import oracle as O
+    mix = [(W.TARGETS["H2O"], W.PULSE_800, W.ISO, 700, 1),
+           (W.TARGETS["H2"], W.PULSE_800, W.fixed(30.0), 1500, 2),
+           (W.TARGETS["H2O_3a1"], W.pulse(1000.0, 1.2e14, 2), W.fixed(50.0, 20.0, 70.0), 400, 3),
+           (W.TARGETS["N2"], W.PULSE_1200, W.COS2, 900, 4)]
+    ref = []
+    for t, p, al, n, inst in mix:
+        soa, _, _ = O.sample(t, p, al, seed=7, instance=inst, n=n)
+        ref.append(O.propagate(t, p, soa, W.GAMMA, cutoff=W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
+                               stab_taper=W.STAB_TAPER)[0])
+    for prec, tol in ((S.SFHK_FP64, 1e-9), (S.SFHK_MIXED, 1e-4)):
+        srv = S.sfhk_server_create(0, S.server_opts(prec, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
+                                                    slice_ms=5.0, stab_taper=W.STAB_TAPER))
+        with pytest.raises(S.SfhkError):
+            S.sfhk_submit(srv, S.request(W.TARGETS["H2O"], W.PULSE_800, W.quadrature(4), 64, 1, 0))
+        ids = [S.sfhk_submit(srv, S.request(t, p, al, n, 7, inst)) for t, p, al, n, inst in mix]
+        res = [S.sfhk_wait(srv, i, 300.0) for i in ids]
+        S.sfhk_server_destroy(srv)
+        for (t, p, al, n, inst), r, v in zip(mix, res, ref):
+            assert r["status"] == S.SFHK_OK
+            err = _rel(r["vz"], v)
+            print(f"served kind {t.get('kind', 0)} n={n} precision {prec}: {err:.3e}")
+            assert err <= tol, (inst, prec)
