@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--sweep-seconds", type=float, default=20.0)
     ap.add_argument("--slice-ms", type=float, default=50.0)
     ap.add_argument("--max-pending", type=int, default=4096)
+    ap.add_argument("--max-reorder-s", type=float, default=1.0,
+                    help="served: short-first admission only while no admitted request is older")
+    ap.add_argument("--max-queued-s", type=float, default=1.0,
+                    help="served: admit while the queued work is below this many seconds")
     ap.add_argument("--serve-budget", type=int, default=16 << 30)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -574,7 +578,8 @@ def sub_batched(S, torch, ctx, stream, local, peaks, args):
 
 
 def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None,
-              max_requests=None, slice_ms=50.0, budget=16 << 30):
+              max_requests=None, slice_ms=50.0, budget=16 << 30, max_reorder_s=1.0,
+              max_queued_s=1.0):
     """One Poisson stream (or a given request list) through the server; the
     latencies, spectra/s and trajectory-steps/s of the completed requests."""
     prec = S.SFHK_MIXED if prec is None else prec
@@ -585,7 +590,8 @@ def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None
     clk = ClockSampler(local)
     srv = S.sfhk_server_create(local, S.server_opts(
         prec, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF, stab_taper=W.STAB_TAPER, budget=budget,
-        slice_ms=slice_ms, max_pending=max_pending))
+        slice_ms=slice_ms, max_pending=max_pending, max_reorder_s=max_reorder_s,
+        max_queued_s=max_queued_s))
     ids, rejected = [], 0
     clk.start()
     t0 = time.perf_counter()
@@ -620,7 +626,9 @@ def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None
             "p99_s": float(np.percentile(lat, 99)),
             "admission_wait_p50_s": float(np.percentile(adm, 50)),
             "admission_wait_p99_s": float(np.percentile(adm, 99)), "slice_ms": slice_ms,
-            "max_pending": max_pending, "spectra_per_s": done / wall,
+            "max_pending": max_pending, "max_reorder_s": max_reorder_s,
+            "max_queued_s": max_queued_s,
+            "spectra_per_s": done / wall,
             "traj_steps_per_s": steps / wall,
             "gpu_busy_frac": stt["gpu_busy_s"] / max(stt["uptime_s"], 1e-9),
             "slices": stt["slices"], "clocks": clocks}, dips
@@ -629,9 +637,10 @@ def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None
 def sub_served(S, local, args):
     """The Poisson request stream at 200 requests/s (overloaded by
     construction: each request is drawn like a batched instance), with at
-    most 64 requests waiting for admission, and a sweep of rates around the
-    saturation point; then 16 requests of at most 2e4 trajectories served by
-    an FP64 and a mixed-precision server, submitted at once."""
+    most 64 requests waiting for admission and short-first admission limited
+    to requests younger than 1 s, and a sweep of rates around the saturation
+    point; then 16 requests of at most 2e4 trajectories served by an FP64 and
+    a mixed-precision server, submitted at once."""
     main, _ = serve_run(S, local, 200.0, 20.0)
     sweep = [serve_run(S, local, r, 15.0)[0] for r in (10.0, 20.0, 30.0)]
     few = [dict(r, n_traj=min(r["n_traj"], 20000), arrival_s=0.0)
@@ -640,7 +649,8 @@ def sub_served(S, local, args):
     f, df = serve_run(S, local, 0.0, 0.0, prec=S.SFHK_FP64, requests=few, max_pending=4096)
     errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(dm, df)]
     return {"workload": "Poisson 200 requests/s for 20 s, requests drawn like the 256-instance "
-                        "batch, mixed precision, at most 64 waiting for admission",
+                        "batch, mixed precision, at most 64 waiting for admission, short-first "
+                        "up to an age of 1 s",
             "value": main["traj_steps_per_s"], "unit": UNIT, "p50_s": main["p50_s"],
             "p99_s": main["p99_s"], "spectra_per_s": main["spectra_per_s"], "served": main,
             "rate_sweep": sweep,
@@ -960,7 +970,8 @@ def run_served(args):
     def one_run(rate, duration, max_requests=None):
         return serve_run(S, local, rate, duration, max_pending=args.max_pending,
                          max_requests=max_requests, slice_ms=args.slice_ms,
-                         budget=args.serve_budget)[0]
+                         budget=args.serve_budget, max_reorder_s=args.max_reorder_s,
+                         max_queued_s=args.max_queued_s)[0]
 
     sweep = [one_run(r, args.sweep_seconds) for r in args.sweep_rates]
     main = one_run(args.rate, args.duration, args.max_requests)
@@ -971,7 +982,8 @@ def run_served(args):
             "config": {"workload": f"Poisson {args.rate} req/s for {args.duration} s, requests "
                                    "drawn like the 256-instance batch, mixed precision",
                        "slice_ms": args.slice_ms, "budget_bytes": args.serve_budget,
-                       "max_pending": args.max_pending},
+                       "max_pending": args.max_pending, "max_reorder_s": args.max_reorder_s,
+                       "max_queued_s": args.max_queued_s},
             "p50_s": main["p50_s"], "p99_s": main["p99_s"],
             "spectra_per_s": main["spectra_per_s"], "served": main, "rate_sweep": sweep}
     print(json.dumps(line), flush=True)

@@ -437,7 +437,8 @@ SFHK_API int sfhk_gabor(const double* vz, size_t nt, double dt, double t_origin,
  * its trajectories as independent CPU jobs).  A host thread owned by the
  * server admits submitted requests (one target, pulse, alignment and
  * trajectory count each) in arrival order while its device-memory budget,
- * its instance slots and its work rings have room, samples each admitted
+ * its instance slots, its work rings and its admission horizon have room,
+ * samples each admitted
  * request on the device, and appends its work items (32 trajectories, longest
  * first) to a device ring: one for diatomic targets, one for polyatomic ones.
  * The GPU runs the integrator as a sequence of persistent slices over those
@@ -466,6 +467,22 @@ typedef struct {
     int check_nonfinite;        /* as in sfhk_run_opts, per request: a request     */
     uint64_t max_nonfinite;     /* with more non-finite trajectories ends with     */
                                 /* status SFHK_E_NUMERIC and no dipole             */
+    double max_reorder_s;       /* age limit of short-first (0 = none): while an   */
+                                /* admitted request of the same kind (diatomic or  */
+                                /* polyatomic) has waited longer than this since   */
+                                /* its admission, new requests go to the tail, so  */
+                                /* that under overload the largest requests are    */
+                                /* not overtaken without bound                     */
+    double max_queued_s;        /* admission horizon (0 = none): a request is      */
+                                /* admitted only while the work queued on its ring */
+                                /* is below this many seconds at the rate the      */
+                                /* server measured over its last slices (any       */
+                                /* request is admitted before the first slice, and */
+                                /* into an empty ring); the rest wait in the       */
+                                /* pending queue, bounded by max_pending, so that  */
+                                /* under overload latency stays near the horizon   */
+                                /* plus the pending queue's wait instead of the    */
+                                /* whole resident backlog                          */
 } sfhk_server_opts;
 
 typedef struct {

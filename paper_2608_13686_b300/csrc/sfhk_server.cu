@@ -95,6 +95,7 @@ struct sfhk_server {
         sfhk::DeviceBuf items;
         uint64_t head = uint64_t(1) << 40, tail = uint64_t(1) << 40;
         double queued_work = 0;      // items x Nt not yet taken (estimate)
+        double rate = 0;             // work taken per second of slice time (smoothed; 0 = none yet)
     } rings[2];
     std::vector<int> free_slots;
     std::vector<uint64_t> slot_req;
@@ -142,6 +143,21 @@ void end_request(sfhk_server* S, Req& q, int status)
     S->cv_done.notify_all();
 }
 
+// whether an admitted request on ring k has waited longer than the age limit
+// of short-first (caller holds the lock)
+bool aged(sfhk_server* S, int k)
+{
+    if (!(S->o.max_reorder_s > 0.0)) return false;
+    const double now = S->now();
+    for (uint64_t id : S->slot_req) {
+        if (!id) continue;
+        const Req* r = S->reqs[id].get();
+        if (r->state == kActive && r->ring == k && now - r->t_admit > S->o.max_reorder_s)
+            return true;
+    }
+    return false;
+}
+
 // admit queued requests while slots, ring space and memory allow
 void admit(sfhk_server* S)
 {
@@ -151,19 +167,30 @@ void admit(sfhk_server* S)
         {
             std::lock_guard<std::mutex> lk(S->mu);
             if (S->pending.empty() || S->free_slots.empty()) return;
-            q = S->reqs[S->pending.front()].get();
-            if (q->cancel) {
-                S->pending.pop_front();
-                q->status = SFHK_E_CANCELLED;
-                q->state = kEnded;
-                q->t_done = S->now();
+            // cancelled requests leave the queue wherever they are
+            for (auto it = S->pending.begin(); it != S->pending.end();) {
+                Req* c = S->reqs[*it].get();
+                if (!c->cancel) {
+                    ++it;
+                    continue;
+                }
+                c->status = SFHK_E_CANCELLED;
+                c->state = kEnded;
+                c->t_done = S->now();
                 ++S->st.cancelled;
                 S->cv_done.notify_all();
-                continue;
+                it = S->pending.erase(it);
             }
+            if (S->pending.empty()) return;
+            // admission in arrival order (short-first acts on the ring)
+            q = S->reqs[S->pending.front()].get();
             const uint64_t items = (q->r.n_traj + 31) / 32;
             const auto& G = S->rings[q->r.target.kind == SFHK_POT_POLYATOMIC ? 1 : 0];
             if (G.tail - G.head + items > S->ring_cap) return;
+            // admission horizon: enough work is already queued on this ring
+            if (S->o.max_queued_s > 0.0 && G.tail > G.head && G.rate > 0.0 &&
+                G.queued_work >= S->o.max_queued_s * G.rate)
+                return;
             const size_t est = bytes_estimate(q->r.n_traj, pulse_nt(q->r.pulse));
             size_t used = 0;
             sfhk_mem_used(S->ctx, &used);
@@ -201,12 +228,14 @@ void admit(sfhk_server* S)
                                           (sfhk::WorkItem*)e->items.p, S->s);
             const unsigned int n = (unsigned int)e->n_items;
             const double work = double(n) * q->pul->nt;
-            // short-first: in front of the queued items when smaller than them
+            // short-first: in front of the queued items when smaller than them,
+            // unless a request of this ring has waited past the age limit
             bool front;
             uint64_t pos;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
-                front = !S->o.fifo && G.tail > G.head && work < G.queued_work && G.head >= n;
+                front = !S->o.fifo && G.tail > G.head && work < G.queued_work && G.head >= n &&
+                        !aged(S, q->ring);
                 pos = front ? G.head - n : G.tail;
             }
             const unsigned int at = (unsigned int)(pos & S->mask);
@@ -360,8 +389,15 @@ void run_slice(sfhk_server* S)
             auto& G = S->rings[k];
             const unsigned int got = *(const unsigned int*)((const char*)S->h_ctr + k * kCtrStride);
             const uint64_t taken = std::min<uint64_t>(got, (uint64_t)n[k]);
+            const double before = G.queued_work;
             G.queued_work =
                 taken >= n64[k] ? 0.0 : G.queued_work * double(n64[k] - taken) / double(n64[k]);
+            // the ring's rate over a slice that did not run out of work
+            // (a drained ring says nothing about how fast it goes)
+            if (taken < n64[k] && busy > 0.0) {
+                const double r = (before - G.queued_work) / busy;
+                G.rate = G.rate > 0.0 ? 0.7 * G.rate + 0.3 * r : r;
+            }
             G.head += taken;
         }
     }
@@ -437,7 +473,8 @@ int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** o
         return SFHK_E_INVAL;
     if (!(opts->gamma > 0.0) || opts->prefactor_cutoff < 0.0 || opts->stability_cutoff < 0.0 ||
         opts->slice_ms < 0.0 || opts->max_pending < 0 || opts->max_active < 0 ||
-        (opts->check_nonfinite != 0 && opts->check_nonfinite != 1))
+        (opts->check_nonfinite != 0 && opts->check_nonfinite != 1) ||
+        !(opts->max_reorder_s >= 0.0) || !(opts->max_queued_s >= 0.0))
         return SFHK_E_INVAL;
     sfhk_server* S = new (std::nothrow) sfhk_server;
     if (!S) return SFHK_E_NOMEM;

@@ -81,7 +81,8 @@ class sfhk_server_opts(C.Structure):
                 ("prefactor_cutoff", C.c_double), ("stability_cutoff", C.c_double),
                 ("slice_ms", C.c_double), ("spectrum", C.c_int), ("fifo", C.c_int),
                 ("stability_taper", C.c_double), ("check_nonfinite", C.c_int),
-                ("max_nonfinite", C.c_uint64)]
+                ("max_nonfinite", C.c_uint64), ("max_reorder_s", C.c_double),
+                ("max_queued_s", C.c_double)]
 
 
 class sfhk_request(C.Structure):
@@ -435,10 +436,11 @@ SFHK_NOALLOC_MAX_NT = 32768
 # ------------------------------------------------------------------ serving
 def server_opts(precision=SFHK_MIXED, gamma=0.5, cutoff=0.0, stab_cutoff=0.0, budget=0,
                 max_pending=0, max_active=0, slice_ms=0.0, spectrum=True, fifo=False,
-                stab_taper=0.0, max_nonfinite=None):
+                stab_taper=0.0, max_nonfinite=None, max_reorder_s=0.0, max_queued_s=0.0):
     return sfhk_server_opts(budget, max_pending, max_active, precision, gamma, cutoff,
                             stab_cutoff, slice_ms, int(spectrum), int(fifo), stab_taper,
-                            int(max_nonfinite is not None), int(max_nonfinite or 0))
+                            int(max_nonfinite is not None), int(max_nonfinite or 0),
+                            float(max_reorder_s), float(max_queued_s))
 
 
 def request(target: dict, pulse: dict, align, n_traj, seed=0, instance=0) -> sfhk_request:

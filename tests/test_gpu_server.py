@@ -5,7 +5,10 @@
   reduction order; mixed precision: 1e-5, the slice kernel being a separate
   compilation of the same integrator);
 * requests that arrive while another one is running join the running work
-  (admitted before the long one ends) and finish first when they are short;
+  (admitted before the long one ends) and finish first when they are short,
+  unless a request admitted earlier has waited longer than the age limit;
+* with an admission horizon, a burst waits in the pending queue and is
+  admitted as the queued work drains;
 * admission follows the device-memory budget; a request larger than the
   budget is refused at submission; cancellation ends a request.
 """
@@ -97,6 +100,72 @@ def test_short_request_joins_a_running_long_one(S):
     assert short["t_admit"] < long["t_done"]      # admitted while the long one ran
     assert short["t_done"] < long["t_done"]       # and finished first
     assert long["t_done"] - short["t_done"] > 0.3 * (long["t_done"] - long["t_admit"])
+
+
+def test_age_limit_bounds_reordering(S):
+    """With an age limit on short-first, a short request submitted after a long
+    one has been admitted for longer than the limit goes to the tail: it no
+    longer finishes well before the long one (compare the test above)."""
+    srv = S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
+                                                slice_ms=10.0, max_reorder_s=0.05))
+    long_id = S.sfhk_submit(srv, S.request(W.TARGETS["N2"], W.pulse(1600.0, 1.0e14, 4), W.COS2,
+                                           1_000_000, 1, 0))
+    t0 = time.time()
+    while S.sfhk_server_stats_get(srv)["active"] < 1 and time.time() - t0 < 60:
+        time.sleep(0.005)
+    time.sleep(0.2)
+    short_id = S.sfhk_submit(srv, S.request(W.TARGETS["H2"], W.PULSE_800, W.fixed(0.0), 2000,
+                                            1, 1))
+    short = S.sfhk_wait(srv, short_id, 300.0)
+    long = S.sfhk_wait(srv, long_id, 300.0)
+    S.sfhk_server_destroy(srv)
+    assert short["status"] == S.SFHK_OK and long["status"] == S.SFHK_OK
+    span = long["t_done"] - long["t_admit"]
+    assert short["t_done"] > long["t_done"] - 0.15 * span
+    with pytest.raises(S.SfhkError):
+        S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, max_reorder_s=-1.0))
+
+
+def _burst_behind_a_long_request(S, **opts):
+    """A long request runs for a few slices; then 30 shorter ones arrive at
+    once.  Returns the largest number of requests resident at once after the
+    burst and every request's result."""
+    srv = S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
+                                                slice_ms=10.0, **opts))
+    ids = [S.sfhk_submit(srv, S.request(W.TARGETS["N2"], W.pulse(1600.0, 1.0e14, 4), W.COS2,
+                                        1_000_000, 1, 0))]
+    t0 = time.time()
+    while S.sfhk_server_stats_get(srv)["slices"] < 5 and time.time() - t0 < 60:
+        time.sleep(0.005)
+    ids += [S.sfhk_submit(srv, S.request(W.TARGETS["H2"], W.PULSE_800, W.fixed(0.0), 100_000,
+                                         2 + i, 1 + i)) for i in range(30)]
+    peak = 0
+    t0 = time.time()
+    while time.time() - t0 < 300:
+        st = S.sfhk_server_stats_get(srv)
+        peak = max(peak, st["active"])
+        if st["completed"] + st["failed"] + st["cancelled"] >= len(ids):
+            break
+        time.sleep(0.002)
+    res = [S.sfhk_wait(srv, i, 300.0) for i in ids]
+    S.sfhk_server_destroy(srv)
+    return peak, res
+
+
+def test_admission_horizon_bounds_resident_work(S):
+    """With an admission horizon of 50 ms, a burst of 30 requests arriving
+    behind a long one waits in the pending queue and is admitted a few at a
+    time as the queued work drains; without it all are admitted at once.
+    Every request completes either way."""
+    peak, res = _burst_behind_a_long_request(S, max_queued_s=0.05)
+    assert all(r["status"] == S.SFHK_OK for r in res)
+    assert peak <= 8
+    assert max(r["t_admit"] - r["t_submit"] for r in res[1:]) > 0.05
+    peak0, res0 = _burst_behind_a_long_request(S)
+    assert all(r["status"] == S.SFHK_OK for r in res0)
+    assert peak0 >= 25
+    with pytest.raises(S.SfhkError):
+        S.sfhk_server_create(0, S.server_opts(S.SFHK_MIXED, W.GAMMA, max_queued_s=-1.0))
 
 
 def test_admission_by_memory_budget_and_refusal(S):
