@@ -121,6 +121,7 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 # traffic is the initial-point SoA read once, 99 B per trajectory):
 # H2 0/45/90 deg captured at 3 x 5e4 trajectories with the 168-register
 # variant in 32-thread blocks (14.9 MB read, 0 written), scaled to 3 x 1e6;
-# H2O 1b1 isotropic (three-centre kernel) captured at 1e5 trajectories with
-# the 168-register variant in 64-thread blocks (9.84 MB read), scaled to 1e6.
-TRAFFIC = {("h2-angles", 2): 298.1e6, ("h2o-iso", 2): 98.4e6}
+# H2O 1b1 isotropic (three-centre kernel, centres 0 and 1 packed) captured at
+# 1e5 trajectories with the 168-register variant in 32-thread blocks (9.83 MB
+# read), scaled to 1e6.
+TRAFFIC = {("h2-angles", 2): 298.1e6, ("h2o-iso", 2): 98.3e6}

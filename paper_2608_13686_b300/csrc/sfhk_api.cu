@@ -470,6 +470,11 @@ int sfhk_create_target(sfhk_ctx* c, const sfhk_target_desc* d, sfhk_target** out
             T.calpha[c] = d->centre_alpha[c];
             T.cq_f[c] = make_float4((float)T.cZinf[c], (float)T.cdZ[c], (float)T.calpha[c], 0.0f);
         }
+        for (int c = 0; c + 1 < d->n_centres; c += 2) {
+            const float4 a = T.cq_f[c], b = T.cq_f[c + 1];
+            T.cq2_f[c / 2][0] = make_float4(a.x, b.x, a.y, b.y);
+            T.cq2_f[c / 2][1] = make_float4(a.z, b.z, 0.0f, 0.0f);
+        }
         for (int k = 0; k < d->n_prim; ++k) {
             T.pcentre[k] = d->prim_centre[k];
             if (d->prim_kind[k] == SFHK_PRIM_P_DIR) {

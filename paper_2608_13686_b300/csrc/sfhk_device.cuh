@@ -474,4 +474,89 @@ __device__ __forceinline__ void potential_poly(const Target& T, const R* tab, R 
     H.yz = A.hyz;
 }
 
+// Three centres in FP32 (the unrolled three-centre kernel): centres 0 and 1
+// side by side in the lanes of float2 values, so that each of their
+// per-centre operations is one f32x2 instruction, and centre 2 alone.  The
+// base differences e_c = (q - c) + l are formed once per RK4 step from the
+// lane's table rows (centre subtracted from the high part first, as in
+// centre_diffs) and shared by the step's four stages.
+struct Poly3Base {
+    float2 x, y, z;        // centres 0 and 1
+    float x2, y2, z2;      // centre 2
+};
+
+__device__ __forceinline__ void poly3_base(const float* tab, const float q[3], const float l[3],
+                                           Poly3Base& B)
+{
+    float c0[3], c1[3], c2[3];
+    tab_row(tab, 0, c0[0], c0[1], c0[2]);
+    tab_row(tab, 1, c1[0], c1[1], c1[2]);
+    tab_row(tab, 2, c2[0], c2[1], c2[2]);
+    B.x = make_float2((q[0] - c0[0]) + l[0], (q[0] - c1[0]) + l[0]);
+    B.y = make_float2((q[1] - c0[1]) + l[1], (q[1] - c1[1]) + l[1]);
+    B.z = make_float2((q[2] - c0[2]) + l[2], (q[2] - c1[2]) + l[2]);
+    B.x2 = (q[0] - c2[0]) + l[0];
+    B.y2 = (q[1] - c2[1]) + l[1];
+    B.z2 = (q[2] - c2[2]) + l[2];
+}
+
+// V, F and the Hessian at the stage point base + o (OFS; else the base
+// point), the same terms as poly_centre summed over the three centres
+template <bool OFS, typename Target>
+__device__ __forceinline__ void potential_poly3(const Target& T, const Poly3Base& B, float a2,
+                                                float ox, float oy, float oz, float& V,
+                                                float& Fx, float& Fy, float& Fz, Sym3<float>& H)
+{
+    float2 dx = B.x, dy = B.y, dz = B.z;
+    float d2x = B.x2, d2y = B.y2, d2z = B.z2;
+    if (OFS) {
+        dx = __fadd2_rn(dx, make_float2(ox, ox));
+        dy = __fadd2_rn(dy, make_float2(oy, oy));
+        dz = __fadd2_rn(dz, make_float2(oz, oz));
+        d2x += ox;
+        d2y += oy;
+        d2z += oz;
+    }
+    // centres 0 and 1
+    const float4 k0 = T.cq2_f[0][0], k1 = T.cq2_f[0][1];
+    const float2 zi = make_float2(k0.x, k0.y), dZ = make_float2(k0.z, k0.w),
+                 al = make_float2(k1.x, k1.y);
+    const float2 s2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(a2, a2))));
+    const float2 u = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
+    const float2 u2 = __fmul2_rn(u, u), u3 = __fmul2_rn(u2, u);
+    const float2 sr = __fmul2_rn(s2, u);
+    const float2 de = __fmul2_rn(dZ, make_float2(__expf(-al.x * sr.x), __expf(-al.y * sr.y)));
+    const float2 vc = __fmul2_rn(__fadd2_rn(zi, de), u);
+    const float2 g1 = __ffma2_rn(de, __ffma2_rn(al, u2, u3), __fmul2_rn(zi, u3));
+    const float2 three = make_float2(3.0f, 3.0f);
+    const float2 poly = __ffma2_rn(three, u2, __ffma2_rn(__fmul2_rn(three, al), u, __fmul2_rn(al, al)));
+    const float2 g2n =          // -g2
+        __fmul2_rn(u2, __ffma2_rn(__fmul2_rn(de, u), poly, __fmul2_rn(__fmul2_rn(three, zi), u3)));
+    // centre 2
+    const float4 k2 = T.cq_f[2];
+    const float zi2 = k2.x, dZ2 = k2.y, al2 = k2.z;
+    const float s22 = d2z * d2z + (d2y * d2y + (d2x * d2x + a2));
+    const float v = rsqrtf(s22);
+    const float v2 = v * v, v3 = v2 * v;
+    const float de2 = dZ2 * __expf(-al2 * (s22 * v));
+    const float vc2 = (zi2 + de2) * v;
+    const float g12 = de2 * (al2 * v2 + v3) + zi2 * v3;
+    const float g2n2 =
+        v2 * ((de2 * v) * (3.0f * v2 + (3.0f * al2 * v + al2 * al2)) + 3.0f * zi2 * v3);
+    // sums over the centres: V = -sum vc, F = -sum g1 d, H = (sum g1) I - sum g2n d d^T
+    V = -(vc.x + vc.y + vc2);
+    Fx = -(g1.x * dx.x + g1.y * dx.y + g12 * d2x);
+    Fy = -(g1.x * dy.x + g1.y * dy.y + g12 * d2y);
+    Fz = -(g1.x * dz.x + g1.y * dz.y + g12 * d2z);
+    const float gs = g1.x + g1.y + g12;
+    const float2 gx = __fmul2_rn(g2n, dx), gy = __fmul2_rn(g2n, dy), gz = __fmul2_rn(g2n, dz);
+    const float gx2 = g2n2 * d2x, gy2 = g2n2 * d2y, gz2 = g2n2 * d2z;
+    H.xx = gs - (gx.x * dx.x + gx.y * dx.y + gx2 * d2x);
+    H.yy = gs - (gy.x * dy.x + gy.y * dy.y + gy2 * d2y);
+    H.zz = gs - (gz.x * dz.x + gz.y * dz.y + gz2 * d2z);
+    H.xy = -(gx.x * dy.x + gx.y * dy.y + gx2 * d2y);
+    H.xz = -(gx.x * dz.x + gx.y * dz.y + gx2 * d2z);
+    H.yz = -(gy.x * dz.x + gy.y * dz.y + gy2 * d2z);
+}
+
 }  // namespace sfhk

@@ -39,6 +39,8 @@ struct DevTarget {
     double cpos[SFHK_MAX_CENTRES][3];                 // molecular frame
     double cZinf[SFHK_MAX_CENTRES], cdZ[SFHK_MAX_CENTRES], calpha[SFHK_MAX_CENTRES];
     float4 cq_f[SFHK_MAX_CENTRES];                    // (Z_inf, dZ, alpha, 0) in FP32
+    // centres 2k and 2k+1 side by side: (Zinf, Zinf', dZ, dZ'), (alpha, alpha', 0, 0)
+    float4 cq2_f[SFHK_MAX_CENTRES / 2][2];
     int pcentre[SFHK_MAX_PRIM];
     double pdir[SFHK_MAX_PRIM][3];                    // unit, molecular frame
 };

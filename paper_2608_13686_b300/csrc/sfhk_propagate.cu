@@ -269,12 +269,19 @@ __device__ __forceinline__ void rk4sum3<float>(float a, const float u[3], const 
 // The field at a stage point base + o: the two-centre potential from the
 // step's centre differences e, or (POLY) the N-centre potential from this
 // lane's column of the centre table.
+// the packed three-centre form serves mixed-precision three-centre targets
+template <typename R, bool MIXED, bool POLY, int NC>
+constexpr bool kPoly3 = POLY && MIXED && NC == 3 && std::is_same<R, float>::value;
+
 template <typename R, bool MIXED, bool POLY, bool OFS, int NC = 0>
 __device__ __forceinline__ void field_at(const PotConst<R>& K, const R e[2][3], const DevTarget* T,
-                                         const R* tab, const R q[3], const R ql[3], R ox, R oy,
-                                         R oz, R& V, R F[3], Sym3<R>& H)
+                                         const R* tab, const Poly3Base& B3, const R q[3],
+                                         const R ql[3], R ox, R oy, R oz, R& V, R F[3],
+                                         Sym3<R>& H)
 {
-    if constexpr (POLY)
+    if constexpr (kPoly3<R, MIXED, POLY, NC>)
+        potential_poly3<OFS>(*T, B3, K.a2, ox, oy, oz, V, F[0], F[1], F[2], H);
+    else if constexpr (POLY)
         potential_poly<R, MIXED, OFS, NC>(*T, tab, K.a2, q, ql, ox, oy, oz, V, F[0], F[1], F[2],
                                           H);
     else
@@ -291,29 +298,31 @@ __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], c
                                            const DevTarget* T = nullptr, const R* tab = nullptr)
 {
     R V, F[3], e[2][3];
+    Poly3Base B3;
     if constexpr (!POLY) centre_diffs<R, MIXED>(K, q, ql, e);
+    if constexpr (kPoly3<R, MIXED, POLY, NC>) poly3_base(tab, q, ql, B3);
     const R z0 = R(0);
-    field_at<R, MIXED, POLY, false, NC>(K, e, T, tab, q, ql, z0, z0, z0, V, F, H[0]);
+    field_at<R, MIXED, POLY, false, NC>(K, e, T, tab, B3, q, ql, z0, z0, z0, V, F, H[0]);
     const R k1p[3] = {F[0], F[1], F[2] - E1};
     const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
     R o[3], p2[3];
     scale3(h2, p, o);
     axpy3(h2, k1p, p, p2);
-    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[1]);
+    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[1]);
     const R k2p[3] = {F[0], F[1], F[2] - E2};
     const R k2s =
         R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - (q[2] + o[2]) * E2;
     R p3[3];
     scale3(h2, p2, o);
     axpy3(h2, k2p, p, p3);
-    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[2]);
+    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[2]);
     const R k3p[3] = {F[0], F[1], F[2] - E2};
     const R k3s =
         R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - (q[2] + o[2]) * E2;
     R p4[3];
     scale3(h, p3, o);
     axpy3(h, k3p, p, p4);
-    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, q, ql, o[0], o[1], o[2], V, F, H[3]);
+    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[3]);
     const R k4s =
         R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - (q[2] + o[2]) * E4;
     dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
