@@ -637,8 +637,9 @@ def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None
 def sub_served(S, local, args):
     """The Poisson request stream at 200 requests/s (overloaded by
     construction: each request is drawn like a batched instance), with at
-    most 64 requests waiting for admission and short-first admission limited
-    to requests younger than 1 s, and a sweep of rates around the saturation
+    most 64 requests waiting for admission, an admission horizon of 1 s of
+    queued work and short-first admission limited to requests younger than
+    1 s, and a sweep of rates around the saturation
     point; then 16 requests of at most 2e4 trajectories served by an FP64 and
     a mixed-precision server, submitted at once."""
     main, _ = serve_run(S, local, 200.0, 20.0)
@@ -649,8 +650,8 @@ def sub_served(S, local, args):
     f, df = serve_run(S, local, 0.0, 0.0, prec=S.SFHK_FP64, requests=few, max_pending=4096)
     errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(dm, df)]
     return {"workload": "Poisson 200 requests/s for 20 s, requests drawn like the 256-instance "
-                        "batch, mixed precision, at most 64 waiting for admission, short-first "
-                        "up to an age of 1 s",
+                        "batch, mixed precision, at most 64 waiting for admission, admission "
+                        "horizon 1 s, short-first up to an age of 1 s",
             "value": main["traj_steps_per_s"], "unit": UNIT, "p50_s": main["p50_s"],
             "p99_s": main["p99_s"], "spectra_per_s": main["spectra_per_s"], "served": main,
             "rate_sweep": sweep,
