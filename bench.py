@@ -398,10 +398,39 @@ def _events(torch, n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
+def stored_oracle(workload):
+    """(v_z rows, metadata) of the oracle's stored run of a whole workload
+    (written once by tests/golden/full_oracle.py; read here, not run), or
+    None when it is absent or was computed for another configuration."""
+    import importlib.util
+    path = os.path.join(ROOT, "tests", "golden", "full_oracle.py")
+    if not os.path.exists(path):
+        return None
+    spec = importlib.util.spec_from_file_location("full_oracle", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.load(workload)
+
+
+def vs_stored_oracle(workload, dipoles):
+    """Relative L2 of each dipole against the oracle's stored run of the same
+    draws, or None without a stored run."""
+    stored = stored_oracle(workload)
+    if stored is None:
+        return None
+    vz_o, meta = stored
+    return {"dipole_rel_l2_mixed_vs_oracle": [float(np.linalg.norm(v - o) / np.linalg.norm(o))
+                                              for v, o in zip(dipoles, vz_o)],
+            "oracle_run": {"n_traj_per_ensemble": meta["n_traj"],
+                           "ensembles": meta["ensembles"], "wall_s": meta["wall_s"],
+                           "threads": meta["threads"], "sha256": meta["sha256"]}}
+
+
 def sub_n2_cos2(S, torch, ctx, stream, local, peaks, args):
     """N2 with the cos^2-weighted axis, 1e7 trajectories, mixed precision:
     device sampling, one propagation launch and the spectrum per step; the
-    FP64 path and the mixed path on the first 2e5 of the same draws."""
+    whole dipole against the oracle's stored run of the same draws; the FP64
+    path and the mixed path on the first 2e5 of the same draws."""
     cfg = W.N2_COS2
     sp = stream.cuda_stream
     th = S.sfhk_create_target(ctx, W.TARGETS["N2"])
@@ -442,6 +471,9 @@ def sub_n2_cos2(S, torch, ctx, stream, local, peaks, args):
     ms_step = float(np.mean(ms))
     roof = roofline([st], [dict(target="N2")], st["kernel_ms"], peaks["fp32_tflops"],
                     "measured FP32 FMA peak (sfhk_fma_peak)", "k_propagate<mixed>")
+    # the whole 1e7-trajectory dipole against the oracle's run of the same
+    # draws, stored once by its script under tests/golden (read, not run)
+    vs_oracle = vs_stored_oracle("n2-cos2", [S.sfhk_dipole(ctx, e, g["nt"])])
     S.sfhk_destroy_ensemble(e)
     # the first 2e5 trajectories of the same draws in both precisions
     n_sub = 200_000
@@ -464,7 +496,7 @@ def sub_n2_cos2(S, torch, ctx, stream, local, peaks, args):
             "value": st["traj_steps"] / (ms_step * 1e-3), "unit": UNIT, "ms_per_step": ms_step,
             "ms_per_step_all": ms, "spectra_per_s": 1.0 / (ms_step * 1e-3),
             "traj_steps_per_step": st["traj_steps"], "gpu_launches": launches,
-            "roofline": roof, "clocks": clocks,
+            "roofline": roof, "clocks": clocks, "full_vs_oracle": vs_oracle,
             "fp64_path_sub_sample": {
                 "sample": f"the first {n_sub} trajectories of the same draws",
                 "fp64_traj_steps_per_s": out[S.SFHK_FP64][1],
@@ -795,6 +827,12 @@ def run_ours(args):
     value = world * traj_steps / (ms * 1e-3)
     spectra_per_s = world * len(instances) / (ms * 1e-3)
     vz_mixed = [S.sfhk_dipole(ctx, e, g["nt"]) for e, g in zip(ens, grids)]
+    # rank 0's draws are the stored oracle run's (seed 0): the whole dipoles
+    # against it, at the workload's own size
+    full_vs_oracle = (vs_stored_oracle(args.workload, vz_mixed)
+                      if rank == 0 and args.n_traj == 0 and args.workload in ("h2-angles",
+                                                                              "n2-cos2")
+                      else None)
 
     # roofline of the propagation kernel: the method's flops (costs.py, with
     # the measured recombination evaluations) against the measured FP32 peak
@@ -940,7 +978,8 @@ def run_ours(args):
                 "spectra_per_s": spectra_per_s,
                 "ms_per_step_all": ms_steps,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "fp64_path": fp64, "gabor": gabor, "gpu_launches": launches // args.steps,
+                "fp64_path": fp64, "full_vs_oracle": full_vs_oracle, "gabor": gabor,
+                "gpu_launches": launches // args.steps,
                 "autotuned": tuned, "clocks": clk, "peaks_measured": peaks,
                 "filtered_frac": sum(s["n_filtered"] + s["n_unstable"] for s in st)
                 / sum(i["n_traj"] for i in instances)}
