@@ -260,6 +260,12 @@ typedef struct {
                               /* above e^-30 of their peak in FP32, e^-200 in */
                               /* FP64) and the contribution formed; the other */
                               /* steps contribute zero without that work      */
+    int fixed_params;         /* 1: the launch ran the integrator compiled    */
+                              /* with the method's dt = 0.05, gamma = 0.5 and */
+                              /* the filters |C| <= 1e4, stability taper      */
+                              /* 1e3..2e3 as constants (mixed precision,      */
+                              /* diatomic; chosen when every instance of the  */
+                              /* launch has exactly these values)             */
 } sfhk_stats;
 
 /* ---------------------------------------------------------------- context */

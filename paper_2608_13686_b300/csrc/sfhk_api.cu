@@ -709,8 +709,9 @@ int sfhk_propagate(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, void* 
     poly_slots(&e, 1, &slots, &nc);
     rc = launch_propagate(o->precision, var, (const DevInstance*)e->inst.p,
                           (const WorkItem*)e->items.p, e->n_items, (unsigned int*)e->qctr.p, bt,
-                          bps, c->sm_count, s, slots, nc);
+                          bps, c->sm_count, s, slots, nc, fixed_params(I));
     if (rc) return rc;
+    e->fixed = o->precision == SFHK_MIXED && slots == 0 && fixed_params(I);
     SFHK_CUDA_TRY(record_event(e->ev_stop, s));
     SFHK_CUDA_TRY(record_event(e->ev_done, s));
     e->have_result = true;
@@ -790,8 +791,12 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
         if (record_event(ens[i]->ev_start, s) != cudaSuccess) rc = SFHK_E_CUDA;
     if (!rc)
         rc = launch_propagate(o->precision, var, d_inst, d_sorted, (int)total_items, d_ctr, bt,
-                              bps, c->sm_count, s, slots, nc);
+                              bps, c->sm_count, s, slots, nc,
+                              std::all_of(hI.begin(), hI.end(), fixed_params));
+    const bool fixed = o->precision == SFHK_MIXED && slots == 0 &&
+                       std::all_of(hI.begin(), hI.end(), fixed_params);
     for (int i = 0; i < n_ens && !rc; ++i) {
+        ens[i]->fixed = fixed;
         if (record_event(ens[i]->ev_stop, s) != cudaSuccess ||
             record_event(ens[i]->ev_done, s) != cudaSuccess)
             rc = SFHK_E_CUDA;
@@ -817,6 +822,7 @@ struct sfhk_batch {
     int max_nt = 1;
     int poly_slots = 0;
     int poly_nc = 0;                 // common centre count of the polyatomic targets
+    bool fixed = false;              // every instance has FixedParams' values
 };
 
 extern "C" {
@@ -876,6 +882,7 @@ int sfhk_batch_create(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens, const s
         hI[i] = make_instance(ens[i], b->opts);
         hnt[i] = ens[i]->pulse->nt;
     }
+    b->fixed = std::all_of(hI.begin(), hI.end(), fixed_params);
     if (cudaMemcpy(b->d_inst, hI.data(), sizeof(DevInstance) * n_ens, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(b->d_nt, hnt.data(), sizeof(int) * n_ens, cudaMemcpyHostToDevice) !=
@@ -907,6 +914,7 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
         off += e->n_items;
         e->dumped = false;
         e->have_result = true;
+        e->fixed = b->opts.precision == SFHK_MIXED && b->poly_slots == 0 && b->fixed;
         set_nonfinite_limit(e, b->opts);
     }
     rc = launch_sort_items(b->d_items, (int)b->total_items, b->d_nt, b->d_sorted, b->d_keys,
@@ -917,7 +925,8 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
     // the kernel is timed with the ensembles' events (also inside a captured graph)
     for (sfhk_ensemble* e : b->ens) SFHK_CUDA_TRY(record_event(e->ev_start, s));
     rc = launch_propagate(b->opts.precision, var, b->d_inst, b->d_sorted, (int)b->total_items,
-                          b->d_ctr, bt, bps, b->ctx->sm_count, s, b->poly_slots, b->poly_nc);
+                          b->d_ctr, bt, bps, b->ctx->sm_count, s, b->poly_slots, b->poly_nc,
+                          b->fixed);
     if (rc) return rc;
     for (sfhk_ensemble* e : b->ens) {
         SFHK_CUDA_TRY(record_event(e->ev_stop, s));
@@ -961,7 +970,7 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
         const int r = launch_propagate(o->precision, v, (const DevInstance*)e->inst.p,
                                        (const WorkItem*)e->items.p, items,
                                        (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0, slots,
-                                       nc);
+                                       nc, fixed_params(I));
         if (r) return r;
         SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, 0));
         SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_stop));
@@ -1044,6 +1053,7 @@ int sfhk_stats_get(sfhk_ensemble* e, sfhk_stats* out)
     out->n_invalid = h[3];
     out->n_unstable = h[4];
     out->recomb_evals = h[5];
+    out->fixed_params = e->have_result && e->fixed ? 1 : 0;
     out->nt = e->pulse->nt;
     float ms = 0.0f;
     if (e->have_result && cudaEventElapsedTime(&ms, e->ev_start, e->ev_stop) == cudaSuccess)

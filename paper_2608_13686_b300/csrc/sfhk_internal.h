@@ -140,6 +140,7 @@ struct Ensemble {
     bool dumped = false;
     bool returns_kept = false;
     bool have_result = false;
+    bool fixed = false;          // the last launch ran the FixedParams integrator
     bool sampled = false;          // created by the device sampler
     bool check_nonfinite = false;  // limit of the last propagation's non-finite count
     unsigned long long max_nonfinite = 0;
@@ -176,13 +177,25 @@ int launch_sort_items(const WorkItem* in, int n_items, const int* inst_nt, WorkI
 constexpr int kPropVariants = 6;   // register-cap variants of the integrator
 // once per device, at context creation: kernel attributes (shared memory)
 int configure_kernels();
+// The method's prescribed RK4 step and Herman-Kluk width (dt = 0.05,
+// gamma = 0.5) with the workloads' filters (prefactor |C| <= 1e4, stability
+// taper from max|M| = 1e3 to 2e3).  A mixed-precision diatomic launch whose
+// every instance has exactly these values runs an instantiation of the
+// integrator compiled with them as constants (the same arithmetic; the
+// constants then take no registers); any other values run the generic one.
+struct FixedParams {
+    static constexpr double dt = 0.05, gamma = 0.5, cutoff = 1e4, stab = 1e3, taper = 2.0;
+};
+bool fixed_params(const DevInstance& I);     // host: I has exactly FixedParams' values
 // poly_slots > 0: polyatomic instances, launched on the polyatomic kernel
-// with that many table rows per lane (the largest n_slots of the instances)
+// with that many table rows per lane (the largest n_slots of the instances);
+// fixed: every instance has FixedParams' values (fixed_params)
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,
-                     int poly_slots = 0, int poly_nc = 0);
-int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm);
+                     int poly_slots = 0, int poly_nc = 0, bool fixed = false);
+int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm,
+                        bool fixed = false);
 int propagate_variant_maxreg(int variant_index);   // 0 = no cap
 // server slice: items ring[(base + i) & mask], i < n_items; warps stop pulling
 // new items slice_ns after the first warp started (0 = no limit); *t0 must be

@@ -690,7 +690,7 @@ constexpr int kRedElems = kWarp * kRedStride;
 // POLY: a polyatomic target; tab is this lane's column of the warp's table
 // of lab-frame centre positions and p directions (rows of 32 words); NC > 0:
 // every such target of the launch has exactly NC centres.
-template <bool MIXED, bool POLY = false, int NC = 0>
+template <bool MIXED, bool POLY = false, int NC = 0, bool FIXED = false>
 __device__ __forceinline__ void process_item(const DevInstance& I, const WorkItem& W, int lane,
                                              typename std::conditional<MIXED, float, double>::type* red,
                                              typename std::conditional<MIXED, float, double>::type* tab = nullptr)
@@ -746,11 +746,15 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
             tab_store(tab, r, v[0], v[1], v[2]);
         }
     }
-    const R gam = R(I.gamma), igam = R(I.inv_gamma);
+    // FIXED: the launch's instances all have FixedParams' values, which are
+    // then compile-time constants (equal to the instance's, value for value)
+    using F = FixedParams;
+    const R gam = FIXED ? R(F::gamma) : R(I.gamma);
+    const R igam = FIXED ? R(1.0 / F::gamma) : R(I.inv_gamma);
     const R wR = R(wr), wI = R(wi);
-    const R cut2 = R(I.cutoff2);            // |det| = |C|^2 threshold (0 = off)
-    const R stab = R(I.stab_cut);
-    const R stab_hi = R(I.stab_hi);           // tapered filter (0 = hard cut)
+    const R cut2 = FIXED ? R(F::cutoff * F::cutoff) : R(I.cutoff2);   // |det| = |C|^2 threshold (0 = off)
+    const R stab = FIXED ? R(F::stab) : R(I.stab_cut);
+    const R stab_hi = FIXED ? R(F::taper * F::stab) : R(I.stab_hi);   // tapered filter (0 = hard cut)
     R Mhat = R(0);                            // running max of max |M_ij| (tapered filter)
     // far-field bound of the recombination exponent over the primitives:
     // K1 |d|^2 + K2 |p|^2 <= K1max |d|^2 + K2max |p|^2 (all K1, K2 < 0)
@@ -785,8 +789,9 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     int status = 0;                 // 0 alive, 1 prefactor filter, 2 non-finite, 3 stability filter
     unsigned int steps = 0;          // RK4 steps taken (< Nt)
 
-    const R h = R(I.dt), h2 = R(0.5 * I.dt), h6 = R(I.dt / 6.0);
-    const R hh4 = R(I.dt * I.dt / 4.0), hh2 = R(I.dt * I.dt / 2.0), hh6 = R(I.dt * I.dt / 6.0);
+    const double dt = FIXED ? F::dt : I.dt;
+    const R h = R(dt), h2 = R(0.5 * dt), h6 = R(dt / 6.0);
+    const R hh4 = R(dt * dt / 4.0), hh2 = R(dt * dt / 2.0), hh6 = R(dt * dt / 6.0);
     const int nE = 2 * nt - 1;
 
     // Carried only within a step: the stage Hessians and increments.
@@ -1023,7 +1028,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
 // reduction buffers, every warp has a table of `slots` rows x kTabWords x 32
 // words (this lane's column starts kTabWords words per lane in for FP32
 // float4 rows, one word for the FP64 rows).
-template <bool MIXED, bool POLY = false, int NC = 0>
+template <bool MIXED, bool POLY = false, int NC = 0, bool FIXED = false>
 __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ items, int n_items,
                                           unsigned int* __restrict__ counter, int slots = 0)
@@ -1043,7 +1048,7 @@ __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const WorkItem W = items[it];
-        process_item<MIXED, POLY, NC>(insts[W.inst], W, lane, red, tab);
+        process_item<MIXED, POLY, NC, FIXED>(insts[W.inst], W, lane, red, tab);
     }
 }
 
@@ -1113,6 +1118,22 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
 {
     run_queue<MIXED>(insts, items, n_items, counter);
 }
+// The mixed-precision diatomic integrator with FixedParams' values compiled
+// in, with the same register-cap variants
+__global__ void __launch_bounds__(128)
+    k_propagate_fixed_nocap(const DevInstance* __restrict__ insts,
+                            const WorkItem* __restrict__ items, int n_items,
+                            unsigned int* __restrict__ counter)
+{
+    run_queue<true, false, 0, true>(insts, items, n_items, counter);
+}
+template <int MAXREG>
+__global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
+    k_propagate_fixed(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ items,
+                      int n_items, unsigned int* __restrict__ counter)
+{
+    run_queue<true, false, 0, true>(insts, items, n_items, counter);
+}
 // Polyatomic targets, with the same register-cap variants; NC = 3: every
 // target of the launch has three centres (loop over the centres unrolled),
 // 0: any number.
@@ -1181,6 +1202,14 @@ using SlicePolyFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, 
 // variants: index 0 = no register cap, then at most 168, 152, 144, 136, 128
 // registers per thread (12 to 16 resident warps per SM)
 constexpr int kVariantMaxReg[kPropVariants] = {0, 168, 152, 144, 136, 128};
+
+KernelFn fixed_variant(int v)
+{
+    static const KernelFn fn[kPropVariants] = {
+        k_propagate_fixed_nocap, k_propagate_fixed<168>, k_propagate_fixed<152>,
+        k_propagate_fixed<144>, k_propagate_fixed<136>, k_propagate_fixed<128>};
+    return fn[v];
+}
 
 KernelFn variant(int precision, int v)
 {
@@ -1295,14 +1324,30 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
 
 int propagate_variant_maxreg(int v) { return (v >= 0 && v < kPropVariants) ? kVariantMaxReg[v] : 0; }
 
-int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm)
+// the kernel of a diatomic launch: the FixedParams instantiation when every
+// instance has those values (mixed precision only)
+static KernelFn diatomic_kernel(int precision, int v, bool fixed)
+{
+    return fixed && precision == SFHK_MIXED ? fixed_variant(v) : variant(precision, v);
+}
+
+int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm,
+                        bool fixed)
 {
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, variant(precision, variant_index), block_threads,
+        blocks_per_sm, diatomic_kernel(precision, variant_index, fixed), block_threads,
         red_bytes(precision, block_threads)));
     return SFHK_OK;
+}
+
+bool fixed_params(const DevInstance& I)
+{
+    using F = FixedParams;
+    return I.tgt.kind != SFHK_POT_POLYATOMIC && I.dt == F::dt && I.gamma == F::gamma &&
+           I.inv_gamma == 1.0 / F::gamma && I.cutoff2 == F::cutoff * F::cutoff &&
+           I.stab_cut == F::stab && I.stab_hi == F::taper * F::stab;
 }
 
 namespace {
@@ -1365,7 +1410,7 @@ int configure_kernels()
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,
-                     int poly_slots, int poly_nc)
+                     int poly_slots, int poly_nc, bool fixed)
 {
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
@@ -1373,7 +1418,7 @@ int launch_propagate(int precision, int variant_index, const DevInstance* insts,
         return launch_poly(precision, variant_index, insts, items, n_items, item_counter,
                            block_threads, blocks_per_sm, sm_count, poly_slots, poly_nc, s);
     int occ = 0;
-    int rc = propagate_occupancy(precision, variant_index, block_threads, &occ);
+    int rc = propagate_occupancy(precision, variant_index, block_threads, &occ, fixed);
     if (rc) return rc;
     if (occ < 1) occ = 1;
     const int bps = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
@@ -1384,8 +1429,9 @@ int launch_propagate(int precision, int variant_index, const DevInstance* insts,
     if (grid < 1) grid = 1;
     SFHK_CUDA_TRY(cudaMemsetAsync(item_counter, 0, sizeof(unsigned int), s));
     count_launch();
-    variant(precision, variant_index)<<<grid, block_threads, red_bytes(precision, block_threads),
-                                        s>>>(insts, items, n_items, item_counter);
+    diatomic_kernel(precision, variant_index, fixed)<<<grid, block_threads,
+                                                       red_bytes(precision, block_threads), s>>>(
+        insts, items, n_items, item_counter);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
 }

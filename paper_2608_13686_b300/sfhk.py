@@ -72,7 +72,8 @@ class sfhk_stats(C.Structure):
     _fields_ = [("n_traj", C.c_uint64), ("n_invalid", C.c_uint64), ("n_filtered", C.c_uint64),
                 ("n_nonfinite", C.c_uint64), ("n_unstable", C.c_uint64),
                 ("traj_steps", C.c_uint64), ("nt", C.c_int),
-                ("kernel_ms", C.c_float), ("recomb_evals", C.c_uint64)]
+                ("kernel_ms", C.c_float), ("recomb_evals", C.c_uint64),
+                ("fixed_params", C.c_int)]
 
 
 class sfhk_server_opts(C.Structure):

@@ -17,7 +17,10 @@
   against the oracle's propagation of each of them alone;
 * the non-finite limit (SFHK_E_NUMERIC) on an ensemble in which some
   trajectories overflow, and the dipole of the rest against the oracle;
-* the unfiltered FP64 path on an ensemble without prefactor blow-up.
+* the unfiltered FP64 path on an ensemble without prefactor blow-up;
+* the integrator compiled with the prescribed dt, gamma and the workloads'
+  filters: chosen exactly when every instance has those values, equal to the
+  generic integrator on the same ensemble (1e-7) and to the oracle.
 
 Tolerances are those of the other parity tests: relative L2 1e-9 (FP64) and
 1e-4 (mixed) for dipoles; |dy| <= 1e-10 max(1, |M|) per FP64 trajectory.
@@ -383,3 +386,38 @@ def test_unfiltered_fp64_on_an_ensemble_without_blowup(S, ctx):
     S.sfhk_destroy_ensemble(e)
     S.sfhk_destroy_pulse(ph)
     S.sfhk_destroy_target(th)
+
+
+def test_fixed_parameter_integrator(S, ctx):
+    """The mixed integrator compiled with dt = 0.05, gamma = 0.5 and the
+    workloads' filters as constants runs exactly when every instance of a
+    launch has those values, and gives the generic integrator's dipole: an H2
+    ensemble propagated alone (specialised), in a batch with an ensemble on
+    another time step (generic for the whole launch), and with the hard
+    stability filter (generic), against each other and the oracle."""
+    t = W.TARGETS["H2"]
+    p, p2 = W.PULSE_800, dict(W.PULSE_800, dt=0.04)
+    th, ph, ph2 = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, p), S.sfhk_set_pulse(ctx, p2)
+    nt = S.sfhk_pulse_grid(ph)["nt"]
+    e = S.sfhk_sample_initial(ctx, th, ph, W.fixed(30.0), 3000, 5, 0)
+    e2 = S.sfhk_sample_initial(ctx, th, ph2, W.fixed(30.0), 300, 6, 0)
+    tapered = S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB, stab_taper=TAPER)
+    S.sfhk_propagate(ctx, e, tapered)
+    assert S.sfhk_stats_get(e)["fixed_params"] == 1
+    v_fixed = S.sfhk_dipole(ctx, e, nt)
+    S.sfhk_propagate_batch(ctx, [e, e2], tapered)
+    assert S.sfhk_stats_get(e)["fixed_params"] == 0
+    v_generic = S.sfhk_dipole(ctx, e, nt)
+    assert _rel(v_fixed, v_generic) <= 1e-7
+    S.sfhk_propagate_batch(ctx, [e], tapered)
+    assert S.sfhk_stats_get(e)["fixed_params"] == 1
+    S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB))
+    assert S.sfhk_stats_get(e)["fixed_params"] == 0
+    S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_FP64, GAMMA, CUT, stab_cutoff=STAB,
+                                        stab_taper=TAPER))
+    assert S.sfhk_stats_get(e)["fixed_params"] == 0
+    soa, _, _ = O.sample(t, p, W.fixed(30.0), seed=5, n=3000)      # the same draws
+    vz_o, _, _ = O.propagate(t, p, soa, GAMMA, cutoff=CUT, stab_cutoff=STAB, stab_taper=TAPER)
+    assert _rel(v_fixed, vz_o) <= 1e-4
+    S.sfhk_destroy_ensemble(e)
+    S.sfhk_destroy_ensemble(e2)
