@@ -264,8 +264,9 @@ typedef struct {
                               /* with the method's dt = 0.05, gamma = 0.5 and */
                               /* the filters |C| <= 1e4, stability taper      */
                               /* 1e3..2e3 as constants (mixed precision,      */
-                              /* diatomic; chosen when every instance of the  */
-                              /* launch has exactly these values)             */
+                              /* diatomic or three-centre targets; chosen     */
+                              /* when every instance of the launch has        */
+                              /* exactly these values)                        */
 } sfhk_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -179,17 +179,24 @@ constexpr int kPropVariants = 6;   // register-cap variants of the integrator
 int configure_kernels();
 // The method's prescribed RK4 step and Herman-Kluk width (dt = 0.05,
 // gamma = 0.5) with the workloads' filters (prefactor |C| <= 1e4, stability
-// taper from max|M| = 1e3 to 2e3).  A mixed-precision diatomic launch whose
-// every instance has exactly these values runs an instantiation of the
-// integrator compiled with them as constants (the same arithmetic; the
-// constants then take no registers); any other values run the generic one.
+// taper from max|M| = 1e3 to 2e3).  A mixed-precision launch of diatomic or
+// three-centre targets whose every instance has exactly these values runs an
+// instantiation of the integrator compiled with them as constants (the same
+// arithmetic; the constants then take no registers); any other launch runs
+// the generic one.
 struct FixedParams {
     static constexpr double dt = 0.05, gamma = 0.5, cutoff = 1e4, stab = 1e3, taper = 2.0;
 };
 bool fixed_params(const DevInstance& I);     // host: I has exactly FixedParams' values
+// whether a launch runs the FixedParams instantiation: every instance has
+// the values (all_fixed), mixed precision, diatomic or three-centre targets
+inline bool runs_fixed(int precision, int poly_slots, int poly_nc, bool all_fixed)
+{
+    return all_fixed && precision == SFHK_MIXED && (poly_slots == 0 || poly_nc == 3);
+}
 // poly_slots > 0: polyatomic instances, launched on the polyatomic kernel
 // with that many table rows per lane (the largest n_slots of the instances);
-// fixed: every instance has FixedParams' values (fixed_params)
+// fixed: the launch runs the FixedParams instantiation (runs_fixed)
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,

@@ -1134,6 +1134,22 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
 {
     run_queue<true, false, 0, true>(insts, items, n_items, counter);
 }
+// the three-centre polyatomic integrator with FixedParams' values compiled in
+__global__ void __launch_bounds__(128)
+    k_propagate_poly_fixed_nocap(const DevInstance* __restrict__ insts,
+                                 const WorkItem* __restrict__ items, int n_items,
+                                 unsigned int* __restrict__ counter, int slots)
+{
+    run_queue<true, true, 3, true>(insts, items, n_items, counter, slots);
+}
+template <int MAXREG>
+__global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
+    k_propagate_poly_fixed(const DevInstance* __restrict__ insts,
+                           const WorkItem* __restrict__ items, int n_items,
+                           unsigned int* __restrict__ counter, int slots)
+{
+    run_queue<true, true, 3, true>(insts, items, n_items, counter, slots);
+}
 // Polyatomic targets, with the same register-cap variants; NC = 3: every
 // target of the launch has three centres (loop over the centres unrolled),
 // 0: any number.
@@ -1239,9 +1255,15 @@ PolyFn poly_variant_nc(int precision, int v)
     return precision == SFHK_MIXED ? mixed[v] : fp64[v];
 }
 
-// nc: the common centre count of the launch's targets (0 when they differ)
-PolyFn poly_variant(int precision, int v, int nc)
+// nc: the common centre count of the launch's targets (0 when they differ);
+// fixed: every instance has FixedParams' values (used for three centres in
+// mixed precision)
+PolyFn poly_variant(int precision, int v, int nc, bool fixed = false)
 {
+    static const PolyFn fixed3[kPropVariants] = {
+        k_propagate_poly_fixed_nocap, k_propagate_poly_fixed<168>, k_propagate_poly_fixed<152>,
+        k_propagate_poly_fixed<144>, k_propagate_poly_fixed<136>, k_propagate_poly_fixed<128>};
+    if (fixed && nc == 3 && precision == SFHK_MIXED) return fixed3[v];
     return nc == 3 ? poly_variant_nc<3>(precision, v) : poly_variant_nc<0>(precision, v);
 }
 
@@ -1345,7 +1367,7 @@ int propagate_occupancy(int precision, int variant_index, int block_threads, int
 bool fixed_params(const DevInstance& I)
 {
     using F = FixedParams;
-    return I.tgt.kind != SFHK_POT_POLYATOMIC && I.dt == F::dt && I.gamma == F::gamma &&
+    return I.dt == F::dt && I.gamma == F::gamma &&
            I.inv_gamma == 1.0 / F::gamma && I.cutoff2 == F::cutoff * F::cutoff &&
            I.stab_cut == F::stab && I.stab_hi == F::taper * F::stab;
 }
@@ -1356,11 +1378,11 @@ namespace {
 int launch_poly(int precision, int variant_index, const DevInstance* insts,
                 const WorkItem* items, int n_items, unsigned int* item_counter,
                 int block_threads, int blocks_per_sm, int sm_count, int slots, int nc,
-                cudaStream_t s)
+                bool fixed, cudaStream_t s)
 {
     if (slots < 1 || slots > SFHK_MAX_CENTRES + SFHK_MAX_PRIM) return SFHK_E_INVAL;
     const bool mixed = precision == SFHK_MIXED;
-    const PolyFn fn = poly_variant(precision, variant_index, nc);
+    const PolyFn fn = poly_variant(precision, variant_index, nc, fixed);
     const size_t elem = mixed ? sizeof(float) : sizeof(double);
     const size_t smem = red_bytes(precision, block_threads) +
                         size_t(block_threads / kWarp) * slots * (mixed ? 4 : 3) * kWarp * elem;
@@ -1396,9 +1418,10 @@ int configure_kernels()
                                                        (prec == SFHK_MIXED ? 4 : 3) * kWarp * elem;
         for (int v = 0; v < kPropVariants; ++v) {
             for (int nc : kPolyNC)
-                SFHK_CUDA_TRY(cudaFuncSetAttribute(poly_variant(prec, v, nc),
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem));
+                for (bool fixed : {false, true})
+                    SFHK_CUDA_TRY(cudaFuncSetAttribute(poly_variant(prec, v, nc, fixed),
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)smem));
             SFHK_CUDA_TRY(cudaFuncSetAttribute(slice_poly_variant(prec, v),
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
@@ -1416,7 +1439,8 @@ int launch_propagate(int precision, int variant_index, const DevInstance* insts,
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
     if (poly_slots > 0)
         return launch_poly(precision, variant_index, insts, items, n_items, item_counter,
-                           block_threads, blocks_per_sm, sm_count, poly_slots, poly_nc, s);
+                           block_threads, blocks_per_sm, sm_count, poly_slots, poly_nc, fixed,
+                           s);
     int occ = 0;
     int rc = propagate_occupancy(precision, variant_index, block_threads, &occ, fixed);
     if (rc) return rc;

@@ -421,3 +421,29 @@ def test_fixed_parameter_integrator(S, ctx):
     assert _rel(v_fixed, vz_o) <= 1e-4
     S.sfhk_destroy_ensemble(e)
     S.sfhk_destroy_ensemble(e2)
+
+
+def test_fixed_parameter_three_centre_integrator(S, ctx):
+    """The same for the three-centre polyatomic integrator: H2O 1b1 at fixed
+    Euler angles, specialised alone, generic in a batch with an ensemble on
+    another time step; equal to each other (1e-7) and to the oracle (1e-4)."""
+    t = W.TARGETS["H2O"]
+    p, p2 = W.PULSE_800, dict(W.PULSE_800, dt=0.04)
+    th, ph, ph2 = S.sfhk_create_target(ctx, t), S.sfhk_set_pulse(ctx, p), S.sfhk_set_pulse(ctx, p2)
+    nt = S.sfhk_pulse_grid(ph)["nt"]
+    al = W.fixed(63.0, 23.0, 40.0)
+    e = S.sfhk_sample_initial(ctx, th, ph, al, 2000, 7, 0)
+    e2 = S.sfhk_sample_initial(ctx, th, ph2, al, 200, 8, 0)
+    tapered = S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB, stab_taper=TAPER)
+    S.sfhk_propagate(ctx, e, tapered)
+    assert S.sfhk_stats_get(e)["fixed_params"] == 1
+    v_fixed = S.sfhk_dipole(ctx, e, nt)
+    S.sfhk_propagate_batch(ctx, [e, e2], tapered)
+    assert S.sfhk_stats_get(e)["fixed_params"] == 0
+    v_generic = S.sfhk_dipole(ctx, e, nt)
+    assert _rel(v_fixed, v_generic) <= 1e-7
+    soa, _, _ = O.sample(t, p, al, seed=7, n=2000)
+    vz_o, _, _ = O.propagate(t, p, soa, GAMMA, cutoff=CUT, stab_cutoff=STAB, stab_taper=TAPER)
+    assert _rel(v_fixed, vz_o) <= 1e-4
+    S.sfhk_destroy_ensemble(e)
+    S.sfhk_destroy_ensemble(e2)
