@@ -208,12 +208,13 @@ int propagate_variant_maxreg(int variant_index);   // 0 = no cap
 // new items slice_ns after the first warp started (0 = no limit); *t0 must be
 // zero before the launch; *counter ends >= the number of items taken.
 // poly_slots > 0: the ring holds polyatomic requests' items, whose centre
-// tables have that many rows per lane
+// tables have that many rows per lane; fixed (diatomic, mixed precision):
+// every request in the ring has FixedParams' values
 int launch_propagate_slice(int precision, int variant_index, const DevInstance* insts,
                            const WorkItem* ring, unsigned int mask, unsigned int base,
                            int n_items, unsigned int* counter, unsigned long long slice_ns,
                            unsigned long long* t0, int block_threads, int sm_count,
-                           cudaStream_t s, int poly_slots = 0);
+                           cudaStream_t s, int poly_slots = 0, bool fixed = false);
 
 // spectrum (sfhk_spectrum.cu)
 // Gabor map (sfhk_gabor.cu)

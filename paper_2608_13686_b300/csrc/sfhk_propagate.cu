@@ -1066,7 +1066,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 // the clock and an atomic counter.
 // POLY: the ring holds polyatomic requests' items, and every warp has its
 // centre table of `slots` rows after the reduction buffers (as run_queue).
-template <bool MIXED, bool POLY = false>
+template <bool MIXED, bool POLY = false, bool FIXED = false>
 __device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ ring, unsigned int mask,
                                           unsigned int base, int n_items,
@@ -1097,7 +1097,8 @@ __device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
         if (it >= n_items) break;
         const WorkItem W = ring[(base + (unsigned int)it) & mask];
         const DevInstance& I = insts[W.inst];
-        if (I.cancel == nullptr || *I.cancel == 0) process_item<MIXED, POLY>(I, W, lane, red, tab);
+        if (I.cancel == nullptr || *I.cancel == 0)
+            process_item<MIXED, POLY, 0, FIXED>(I, W, lane, red, tab);
         if (lane == 0 && I.done_items != nullptr) atomicAdd(I.done_items, 1u);
     }
 }
@@ -1187,6 +1188,26 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
     run_slice<MIXED>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
 }
 
+// the mixed diatomic slice with FixedParams' values compiled in
+__global__ void __launch_bounds__(128)
+    k_propagate_slice_fixed_nocap(const DevInstance* __restrict__ insts,
+                                  const WorkItem* __restrict__ ring, unsigned int mask,
+                                  unsigned int base, int n_items,
+                                  unsigned int* __restrict__ counter, unsigned long long slice_ns,
+                                  unsigned long long* __restrict__ t0)
+{
+    run_slice<true, false, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
+}
+template <int MAXREG>
+__global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
+    k_propagate_slice_fixed(const DevInstance* __restrict__ insts,
+                            const WorkItem* __restrict__ ring, unsigned int mask,
+                            unsigned int base, int n_items, unsigned int* __restrict__ counter,
+                            unsigned long long slice_ns, unsigned long long* __restrict__ t0)
+{
+    run_slice<true, false, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(128)
     k_propagate_slice_poly_nocap(const DevInstance* __restrict__ insts,
@@ -1267,8 +1288,13 @@ PolyFn poly_variant(int precision, int v, int nc, bool fixed = false)
     return nc == 3 ? poly_variant_nc<3>(precision, v) : poly_variant_nc<0>(precision, v);
 }
 
-SliceFn slice_variant(int precision, int v)
+SliceFn slice_variant(int precision, int v, bool fixed = false)
 {
+    static const SliceFn fixed_fn[kPropVariants] = {
+        k_propagate_slice_fixed_nocap, k_propagate_slice_fixed<168>,
+        k_propagate_slice_fixed<152>, k_propagate_slice_fixed<144>,
+        k_propagate_slice_fixed<136>, k_propagate_slice_fixed<128>};
+    if (fixed && precision == SFHK_MIXED) return fixed_fn[v];
     static const SliceFn mixed[kPropVariants] = {
         k_propagate_slice_nocap<true>, k_propagate_slice<true, 168>,
         k_propagate_slice<true, 152>, k_propagate_slice<true, 144>,
@@ -1306,7 +1332,7 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
                            const WorkItem* ring, unsigned int mask, unsigned int base,
                            int n_items, unsigned int* counter, unsigned long long slice_ns,
                            unsigned long long* t0, int block_threads, int sm_count,
-                           cudaStream_t s, int poly_slots)
+                           cudaStream_t s, int poly_slots, bool fixed)
 {
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     if (variant_index < 0 || variant_index >= kPropVariants || n_items <= 0) return SFHK_E_INVAL;
@@ -1325,7 +1351,7 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
             &occ, slice_poly_variant(precision, variant_index), block_threads, smem));
     else
         SFHK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, slice_variant(precision, variant_index), block_threads, smem));
+            &occ, slice_variant(precision, variant_index, fixed), block_threads, smem));
     if (occ < 1) occ = 1;
     const int warps_per_block = block_threads / kWarp;
     int grid = sm_count * occ;
@@ -1338,7 +1364,7 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
         slice_poly_variant(precision, variant_index)<<<grid, block_threads, smem, s>>>(
             insts, ring, mask, base, n_items, counter, slice_ns, t0, poly_slots);
     else
-        slice_variant(precision, variant_index)<<<grid, block_threads, smem, s>>>(
+        slice_variant(precision, variant_index, fixed)<<<grid, block_threads, smem, s>>>(
             insts, ring, mask, base, n_items, counter, slice_ns, t0);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;

@@ -50,6 +50,8 @@ struct Req {
     uint64_t traj_steps = 0, n_filtered = 0, n_unstable = 0, n_nonfinite = 0;
     int ring = 0;                    // 0: diatomic target, 1: polyatomic
     int poly_slots = 0;              // centre-table rows of a polyatomic target
+    bool fixed = false;              // has the fixed parameters (sfhk::fixed_params)
+    bool generic = false;            // counted in its ring's n_generic
 };
 
 size_t bytes_estimate(uint64_t n, int nt)
@@ -96,6 +98,8 @@ struct sfhk_server {
         uint64_t head = uint64_t(1) << 40, tail = uint64_t(1) << 40;
         double queued_work = 0;      // items x Nt not yet taken (estimate)
         double rate = 0;             // work taken per second of slice time (smoothed; 0 = none yet)
+        int n_generic = 0;           // active requests without the fixed parameters: while
+                                     // there are any, the slice runs the generic integrator
     } rings[2];
     std::vector<int> free_slots;
     std::vector<uint64_t> slot_req;
@@ -132,6 +136,11 @@ void end_request(sfhk_server* S, Req& q, int status)
     q.status = status;
     q.state = kEnded;
     q.t_done = S->now();
+    // a request ends once all its items have been taken, so none is left in the ring
+    if (q.generic) {
+        --S->rings[q.ring].n_generic;
+        q.generic = false;
+    }
     if (q.slot >= 0) {
         S->slot_req[q.slot] = 0;
         S->free_slots.push_back(q.slot);
@@ -209,6 +218,7 @@ void admit(sfhk_server* S)
         if (!rc) rc = sfhk::prepare_outputs(q->ens, S->ro, S->s);
         if (!rc) {
             sfhk::DevInstance I = sfhk::make_instance(q->ens, S->ro);
+            q->fixed = sfhk::fixed_params(I);
             I.done_items = (unsigned int*)S->done.p + slot;
             I.cancel = (const int*)S->cancelf.p + slot;
             if (cudaMemcpyAsync((sfhk::DevInstance*)S->insts.p + slot, &I, sizeof I,
@@ -258,6 +268,10 @@ void admit(sfhk_server* S)
                 if (front) G.head -= n;
                 else G.tail += n;
                 G.queued_work += work;
+                if (!q->fixed) {
+                    q->generic = true;
+                    ++G.n_generic;
+                }
                 q->state = kActive;
                 q->t_admit = S->now();
             }
@@ -335,9 +349,11 @@ void run_slice(sfhk_server* S)
 {
     uint64_t n64[2];
     int slots = 0;                   // centre-table rows the polyatomic slice needs
+    bool fixed = false;              // every diatomic request has the fixed parameters
     {
         std::lock_guard<std::mutex> lk(S->mu);
         for (int k = 0; k < 2; ++k) n64[k] = S->rings[k].tail - S->rings[k].head;
+        fixed = S->rings[0].n_generic == 0;
         // cancellations of running requests reach the device before the slice
         for (size_t slot = 0; slot < S->slot_req.size(); ++slot) {
             const uint64_t id = S->slot_req[slot];
@@ -370,7 +386,7 @@ void run_slice(sfhk_server* S)
             (const sfhk::WorkItem*)G.items.p, S->mask, (unsigned int)(G.head & S->mask), n[k],
             ctr, (unsigned long long)(S->o.slice_ms * 1e6),
             (unsigned long long*)((char*)S->t0.p + k * kCtrStride), bt, S->ctx->sm_count, S->s,
-            k == 1 ? slots : 0);
+            k == 1 ? slots : 0, k == 0 && fixed);
         if (!rc && cudaMemcpyAsync((char*)S->h_ctr + k * kCtrStride, ctr, sizeof(unsigned int),
                                    cudaMemcpyDeviceToHost, S->s) != cudaSuccess)
             rc = SFHK_E_CUDA;

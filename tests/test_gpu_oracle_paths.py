@@ -11,7 +11,9 @@
 * a prepared batch of three uneven mixed-precision ensembles and its CUDA
   graph replay: every ensemble's dipole against the oracle;
 * the served requests (continuous batching, the workloads' tapered
-  stability filter): every result against the oracle;
+  stability filter, one request on another time step so that the slices
+  switch between the generic and the fixed-parameter integrator): every
+  result against the oracle;
 * the benchmark's own workload (1e6 trajectories, autotuned launch shape):
   trajectories drawn at random from the full-size run, their final states
   against the oracle's propagation of each of them alone;
@@ -207,7 +209,10 @@ MIX = [("H2", W.PULSE_800, W.fixed(10.0), 3000, 1),
        ("N2", W.PULSE_1200, W.fixed(40.0), 4100, 4),
        ("H2", W.pulse(900.0, 1.9e14, 3), W.COS2, 33, 5),
        ("N2_sp", W.PULSE_1200, W.ISO, 900, 6),
-       ("N2_pi", W.pulse(1000.0, 1.4e14, 3), W.fixed(60.0), 600, 7)]
+       ("N2_pi", W.pulse(1000.0, 1.4e14, 3), W.fixed(60.0), 600, 7),
+       # another time step: while it is served the slices run the generic
+       # integrator, the others the one compiled with the fixed parameters
+       ("H2", dict(W.PULSE_800, dt=0.04), W.fixed(20.0), 800, 8)]
 
 
 @pytest.fixture(scope="module")
