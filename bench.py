@@ -398,6 +398,13 @@ def _events(torch, n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
+def mixed_kernel_name(stats, poly=False):
+    """The mixed-precision integrator a launch ran: the instantiation with the
+    fixed parameters compiled in, or the generic one (sfhk_stats.fixed_params)."""
+    fixed = all(s.get("fixed_params") for s in stats)
+    return ("k_propagate_poly" if poly else "k_propagate") + ("_fixed" if fixed else "") + "<mixed>"
+
+
 def stored_oracle(workload):
     """(v_z rows, metadata) of the oracle's stored run of a whole workload
     (written once by tests/golden/full_oracle.py; read here, not run), or
@@ -470,7 +477,7 @@ def sub_n2_cos2(S, torch, ctx, stream, local, peaks, args):
     st = S.sfhk_stats_get(e)
     ms_step = float(np.mean(ms))
     roof = roofline([st], [dict(target="N2")], st["kernel_ms"], peaks["fp32_tflops"],
-                    "measured FP32 FMA peak (sfhk_fma_peak)", "k_propagate<mixed>")
+                    "measured FP32 FMA peak (sfhk_fma_peak)", mixed_kernel_name([st]))
     # the whole 1e7-trajectory dipole against the oracle's run of the same
     # draws, stored once by its script under tests/golden (read, not run)
     vs_oracle = vs_stored_oracle("n2-cos2", [S.sfhk_dipole(ctx, e, g["nt"])])
@@ -566,7 +573,7 @@ def sub_batched(S, torch, ctx, stream, local, peaks, args):
     traj_steps = sum(s["traj_steps"] for s in st)
     ms_step = float(np.mean(ms))
     roof = roofline(st, insts, st[0]["kernel_ms"], peaks["fp32_tflops"],
-                    "measured FP32 FMA peak (sfhk_fma_peak)", "k_propagate<mixed>")
+                    "measured FP32 FMA peak (sfhk_fma_peak)", mixed_kernel_name(st))
     del graph
     S.sfhk_batch_destroy(batch)
     for e in ens:
@@ -839,7 +846,7 @@ def run_ours(args):
     poly = any(W.TARGETS[nm].get("kind") == W.POT_POLY for nm in targets)
     roof = roofline(st, instances, prop_ms, peaks["fp32_tflops"],
                     "measured FP32 FMA peak (sfhk_fma_peak, burst of about 0.3 s)",
-                    "k_propagate_poly<mixed>" if poly else "k_propagate<mixed>")
+                    mixed_kernel_name(st, poly))
     roof["traffic"] = (costs.TRAFFIC.get((args.workload, tuned["kernel_variant"] if tuned
                                           else args.kernel_variant))
                        if args.n_traj in (0, 1_000_000) else None)

@@ -118,10 +118,11 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 # dram__bytes_read.sum + dram__bytes_write.sum per full-size launch of the
 # dominant kernel, keyed by (workload, kernel variant), from an ncu capture of
 # the current kernel, scaled by the trajectories to the full size (the
-# traffic is the initial-point SoA read once, 99 B per trajectory):
-# H2 0/45/90 deg captured at 3 x 5e4 trajectories with the 168-register
-# variant in 32-thread blocks (14.9 MB read, 0 written), scaled to 3 x 1e6;
-# H2O 1b1 isotropic (three-centre kernel, centres 0 and 1 packed) captured at
-# 1e5 trajectories with the 168-register variant in 32-thread blocks (9.83 MB
-# read), scaled to 1e6.
-TRAFFIC = {("h2-angles", 2): 298.1e6, ("h2o-iso", 2): 98.3e6}
+# traffic is the initial-point SoA read once, about 100 B per trajectory):
+# H2 0/45/90 deg captured at 3 x 5e4 trajectories with the fixed-parameter
+# integrator in 32-thread blocks, uncapped (variant 1) and at 168 registers
+# (variant 2), the autotuner's two choices (15.12 MB read either way, 0
+# written), scaled to 3 x 1e6; H2O 1b1 isotropic (three-centre
+# fixed-parameter kernel) captured at 1e5 trajectories with the
+# 168-register variant (2) in 64-thread blocks (9.83 MB read), scaled to 1e6.
+TRAFFIC = {("h2-angles", 1): 302.4e6, ("h2-angles", 2): 302.5e6, ("h2o-iso", 2): 98.3e6}
