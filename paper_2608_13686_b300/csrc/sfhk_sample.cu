@@ -109,6 +109,10 @@ struct SampleParams {
     int sampling;                             // SFHK_SAMPLE_PROPOSAL / SFHK_SAMPLE_ABS_AMPLITUDE
     double norm;
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
+    // per-draw constants formed once on the host: coef_p (pi/a_p)^{3/2},
+    // N (2 pi)^{-3/2}, the ADK exponent's 2 (2 Ip)^{3/2} / 3, sqrt(2 Ip)
+    double pfac[SFHK_MAX_PRIM];
+    double mz_scale, adk_c, sqrt2Ip;
     int pkind[SFHK_MAX_PRIM];
     double cchi, schi;                        // pi lobe azimuth (cos, sin)
     // polyatomic targets: Euler-angle orientation, primitives on their own centres
@@ -156,8 +160,7 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
     const int m = lo;
     const double t0 = S.t_origin + m * S.dt;
     const double Et0 = field_direct(S.omega, S.E0, S.Tp, S.P.cep, t0);
-    const double sqrt2Ip = sqrt(2.0 * S.Ip);
-    const double sigma = sqrt(fabs(Et0) / (2.0 * sqrt2Ip));
+    const double sigma = sqrt(fabs(Et0) / (2.0 * S.sqrt2Ip));
     const double rr = sqrt(-2.0 * log(u[1]));
     double sb, cb;
     sincos(2.0 * kPi * u[2], &sb, &cb);
@@ -209,14 +212,19 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
         double ac[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) ac[q] = S.P.a[q] * cthm[q];
-        // Y(s) - Y* and Y'(s), sinh and cosh from one exponential per term
+        // Y(s) - Y* and Y'(s); the terms' exponentials e^{k_q s} for k = w,
+        // w + W, w - W as products of e^{w s} and e^{W s} (two exponentials
+        // and two reciprocals per evaluation)
+        const double kW = S.P.k[1] - S.P.k[0];
         auto g = [&](double s, double* dg) {
+            const double e0 = exp(S.P.k[0] * s), eW = exp(kW * s);
+            const double ie0 = 1.0 / e0, ieW = 1.0 / eW;
+            const double e[3] = {e0, e0 * eW, e0 * ieW}, ie[3] = {ie0, ie0 * ieW, ie0 * eW};
             double y = 0.0, yp = 0.0;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const double e = exp(S.P.k[q] * s), ie = 1.0 / e;
-                y += ac[q] * (e - ie);
-                yp += ac[q] * S.P.k[q] * (e + ie);
+                y += ac[q] * (e[q] - ie[q]);
+                yp += ac[q] * S.P.k[q] * (e[q] + ie[q]);
             }
             *dg = 0.5 * yp;
             return 0.5 * y - Ystar;
@@ -363,7 +371,7 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                                                     kapz.y * A[2]);
                     const double a = S.pexp[p];
                     const double2 ex = make_double2(kA.y - kk.x / (4.0 * a), -kA.x - kk.y / (4.0 * a));
-                    const double2 F = cscale(cexp_(ex), S.pcoef[p] * pow(kPi / a, 1.5));
+                    const double2 F = cscale(cexp_(ex), S.pfac[p]);
                     double2 f;
                     if (S.pkind[p]) {
                         const double* d = S.pdir[p];
@@ -393,7 +401,7 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                     const double a = S.pexp[p];
                     // -i kappa.A - kappa.kappa / (4a)
                     const double2 ex = make_double2(kA.y - kk.x / (4.0 * a), -kA.x - kk.y / (4.0 * a));
-                    const double2 F = cscale(cexp_(ex), S.pcoef[p] * pow(kPi / a, 1.5));
+                    const double2 F = cscale(cexp_(ex), S.pfac[p]);
                     double2 f;
                     if (S.pkind[p]) {
                         // p-type, x' = r - A, factor s u.x' (sigma: u = n, s = s_c;
@@ -418,7 +426,7 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                     mz = cadd(mz, cmul(F, f));
                 }
             }
-            mz = cscale(mz, S.norm * pow(2.0 * kPi, -1.5));
+            mz = cscale(mz, S.mz_scale);
             // amplitude and weight
             const double2 num = cmul(Es, mz);
             double2 curv = cmul(Es, kapz);
@@ -439,8 +447,7 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
             const double2 Z = make_double2(Sd.x + kz * qz, Sd.y);     // S_down + k.q0
             const double2 eiz = cexp_(make_double2(-Z.y, Z.x));        // e^{iZ}
             const double2 amp = cmul(cdiv(num, den), eiz);
-            const double cst = 2.0 * pow(2.0 * S.Ip, 1.5) / 3.0;
-            const double Wm = exp(-cst / fabs(Et0));
+            const double Wm = exp(-S.adk_c / fabs(Et0));
             const double pdf = (Wm / total) / S.dt * exp(-kp2 / (2.0 * sigma * sigma)) /
                                (2.0 * kPi * sigma * sigma);
             // the quadrature node's weight K W_k (1 otherwise)
@@ -798,7 +805,11 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
         S.pexp[k] = T.desc.prim_exp[k];
         S.pcoef[k] = T.desc.prim_coef[k];
         S.pkind[k] = T.desc.prim_kind[k];
+        S.pfac[k] = S.pexp[k] > 0.0 ? S.pcoef[k] * std::pow(kPi / S.pexp[k], 1.5) : 0.0;
     }
+    S.mz_scale = S.norm * std::pow(2.0 * kPi, -1.5);
+    S.adk_c = 2.0 * std::pow(2.0 * S.Ip, 1.5) / 3.0;
+    S.sqrt2Ip = std::sqrt(2.0 * S.Ip);
     S.cchi = std::cos(T.desc.pi_azimuth);
     S.schi = std::sin(T.desc.pi_azimuth);
     S.poly = poly ? 1 : 0;
