@@ -63,9 +63,13 @@ def _target(name):
     """A workload target by name, with '+'-separated variants: sfhk2 (modified
     saddle), abs (sampling ~ |a|), abs150 (the same at kappa = 150, where
     about a fifth of the trajectories exhaust their attempts), chi90 (the
-    other 1 pi_u component)."""
+    other 1 pi_u component), 8prim (SFHK_MAX_PRIM s-type primitives per
+    centre)."""
     base, *variants = name.split("+")
     t = W.TARGETS[base]
+    if "8prim" in variants:
+        t = dict(t, pexp=[3.0, 1.8, 1.3, 0.9, 0.6, 0.4, 0.25, 0.15],
+                 pcoef=[0.05, 0.1, 0.2, 0.3, 0.3, 0.2, 0.1, 0.05])
     if "sfhk2" in variants:
         t = W.sfhk2(t)
     if "abs" in variants:
@@ -99,6 +103,11 @@ def _target(name):
     ("N2_pi+sfhk2", W.PULSE_1200, W.fixed(90.0, 0.0), 500, 17, 2),
     ("N2_pi+abs", W.PULSE_1200, W.quadrature(6), 400, 18, 0),
     ("H2+abs150", W.PULSE_800, W.fixed(0.0), 400, 21, 0),
+    # the largest sizes the interface declares: SFHK_MAX_QUAD_NODES nodes,
+    # SFHK_MAX_PRIM primitives per centre, and a long pulse (Nt = 26477)
+    ("H2", W.PULSE_800, W.quadrature(64), 640, 22, 0),
+    ("H2+8prim", W.PULSE_800, W.fixed(20.0), 500, 23, 0),
+    ("H2", W.pulse(2400.0, 0.8e14, 4), W.fixed(0.0), 300, 24, 0),
 ])
 def test_sampler_matches_oracle(S, ctx, name, pulse, align, n, seed, inst):
     t = _target(name)
@@ -157,6 +166,8 @@ def _compare_final(fin_g, fin_o, tol):
     ("N2_sp", W.PULSE_1200, W.ISO, 600),
     ("N2_pi", W.PULSE_1200, W.ISO, 600),
     ("N2_pi+chi90", W.PULSE_1200, W.fixed(70.0, 20.0), 500),
+    ("H2+8prim", W.PULSE_800, W.fixed(20.0), 400),
+    ("H2", W.pulse(2400.0, 0.8e14, 4), W.fixed(0.0), 200),
 ])
 def test_fp64_propagation_per_trajectory_and_dipole(S, ctx, name, pulse, align, n):
     t = _target(name)
@@ -181,6 +192,8 @@ def test_fp64_propagation_per_trajectory_and_dipole(S, ctx, name, pulse, align, 
     ("N2", W.PULSE_1200, W.COS2, 600),
     ("N2_sp", W.PULSE_1200, W.ISO, 600),
     ("N2_pi", W.PULSE_1200, W.ISO, 600),
+    ("H2+8prim", W.PULSE_800, W.fixed(20.0), 400),
+    ("H2", W.pulse(2400.0, 0.8e14, 4), W.fixed(0.0), 200),
 ])
 def test_mixed_precision_dipole(S, ctx, name, pulse, align, n):
     t = _target(name)
