@@ -644,7 +644,7 @@ def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None
                                                      r["instance"])), r))
         except S.SfhkError:
             rejected += 1
-    lat, adm, steps, done, dips = [], [], 0, 0, []
+    lat, adm, steps, done, dips, flops = [], [], 0, 0, [], 0.0
     res = S.Result()
     for i, r in ids:
         out = S.sfhk_wait(srv, i, 3600.0, res)
@@ -652,6 +652,9 @@ def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None
             lat.append(out["t_done"] - out["t_submit"])
             adm.append(out["t_admit"] - out["t_submit"])
             steps += out["traj_steps"]
+            # the method's flops of the request (costs.py), with the
+            # recombination evaluations its run counted
+            flops += costs.algorithmic_flops(r["target"], out["traj_steps"], out["recomb_evals"])
             done += 1
             dips.append(out["vz"])
     wall = time.perf_counter() - t0
@@ -669,11 +672,22 @@ def serve_run(S, local, rate, duration, prec=None, max_pending=64, requests=None
             "max_queued_s": max_queued_s,
             "spectra_per_s": done / wall,
             "traj_steps_per_s": steps / wall,
+            "algorithmic_tflops": flops / wall / 1e12,
             "gpu_busy_frac": stt["gpu_busy_s"] / max(stt["uptime_s"], 1e-9),
             "slices": stt["slices"], "clocks": clocks}, dips
 
 
-def sub_served(S, local, args):
+def served_roofline(m, peaks):
+    """The served stream against the measured FP32 FMA peak: the method's flops
+    of the completed requests over the stream's wall time (arrivals to the
+    last result), so every gap between slices counts against it."""
+    return {"bound": "alu", "achieved": m["algorithmic_tflops"], "peak": peaks["fp32_tflops"],
+            "unit": "TFLOP/s", "frac": m["algorithmic_tflops"] / peaks["fp32_tflops"],
+            "kernel": "k_propagate_slice (whole stream, wall time)",
+            "peak_basis": "measured FP32 FMA peak (sfhk_fma_peak)"}
+
+
+def sub_served(S, local, args, peaks=None):
     """The Poisson request stream at 200 requests/s (overloaded by
     construction: each request is drawn like a batched instance), with at
     most 64 requests waiting for admission, an admission horizon of 1 s of
@@ -693,6 +707,7 @@ def sub_served(S, local, args):
                         "horizon 1 s, short-first up to an age of 1 s",
             "value": main["traj_steps_per_s"], "unit": UNIT, "p50_s": main["p50_s"],
             "p99_s": main["p99_s"], "spectra_per_s": main["spectra_per_s"], "served": main,
+            "roofline": served_roofline(main, peaks) if peaks else None,
             "rate_sweep": sweep,
             "fp64_path_sub_sample": {
                 "sample": "the first 16 requests, at most 2e4 trajectories each, submitted at once",
@@ -960,7 +975,7 @@ def run_ours(args):
         progress("n2_cos2")
         extra["batched"] = sub_batched(S, torch, ctx, stream, local, peaks, args)
         progress("batched")
-        extra["served"] = sub_served(S, local, args)
+        extra["served"] = sub_served(S, local, args, peaks)
         progress("served")
 
     cpu = None
@@ -1013,6 +1028,7 @@ def run_served(args):
     from paper_2608_13686_b300 import _build
     _build.build()
     from paper_2608_13686_b300 import sfhk as S
+    peaks = measure_peaks(S, local)
 
     def one_run(rate, duration, max_requests=None):
         return serve_run(S, local, rate, duration, max_pending=args.max_pending,
@@ -1032,7 +1048,8 @@ def run_served(args):
                        "max_pending": args.max_pending, "max_reorder_s": args.max_reorder_s,
                        "max_queued_s": args.max_queued_s},
             "p50_s": main["p50_s"], "p99_s": main["p99_s"],
-            "spectra_per_s": main["spectra_per_s"], "served": main, "rate_sweep": sweep}
+            "spectra_per_s": main["spectra_per_s"], "served": main, "rate_sweep": sweep,
+            "roofline": served_roofline(main, peaks), "peaks_measured": peaks}
     print(json.dumps(line), flush=True)
     return 0
 

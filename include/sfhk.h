@@ -518,6 +518,7 @@ typedef struct {
     double t_submit, t_admit, t_done;
     uint64_t traj_steps, n_filtered, n_unstable;
     uint64_t n_nonfinite;       /* trajectories stopped on a non-finite state      */
+    uint64_t recomb_evals;      /* as sfhk_stats.recomb_evals, for the request     */
 } sfhk_result;
 
 typedef struct {
@@ -526,6 +527,9 @@ typedef struct {
     int pending, active;
     double gpu_busy_s, uptime_s;
     uint64_t device_bytes;      /* device memory the server holds now */
+    uint64_t parked;            /* work items a slice stopped at a chunk boundary */
+                                /* when its time was up (the next slice resumes   */
+                                /* them), counted each time                       */
 } sfhk_server_stats;
 
 /* Errors: SFHK_E_INVAL (bad options), SFHK_E_CUDA (device). */

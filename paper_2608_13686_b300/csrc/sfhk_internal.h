@@ -204,6 +204,32 @@ int launch_propagate(int precision, int variant_index, const DevInstance* insts,
 int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm,
                         bool fixed = false);
 int propagate_variant_maxreg(int variant_index);   // 0 = no cap
+// Server slices stop within one 32-step chunk of their deadline: a warp
+// whose time is up at a chunk boundary, with chunks left, parks its item (the
+// next chunk's first step and kParkWords values of each lane's state, in the
+// precision's type) and the next slice resumes it before taking new items.
+constexpr int kParkWords = 58;
+struct ParkHdr {
+    WorkItem W;
+    int nb;                        // first step of the next chunk
+    int pad[3];
+};
+struct ParkBufs {
+    const ParkHdr* in_hdr;         // the previous slice's parked items
+    const void* in_state;          // [n_in][kParkWords][32]
+    int n_in;
+    unsigned int* in_ctr;          // zero before the launch
+    ParkHdr* out_hdr;              // this slice's parked items
+    void* out_state;               // [cap][kParkWords][32]
+    unsigned int* out_ctr;         // zero before the launch; ends >= the number parked
+    unsigned long long* out_work;  // zero before the launch: the parked items' remaining
+                                   // work, Nt x the remaining fraction of each item's steps
+                                   // (the units in which the server counts queued items)
+    int cap;                       // entries of each buffer; an item beyond it is not parked
+};
+// warps a slice launch can have at once (the park buffers' capacity): the
+// largest over the slice kernels a ring can run
+int slice_max_warps(int precision, int variant_index, int block_threads, int sm_count);
 // server slice: items ring[(base + i) & mask], i < n_items; warps stop pulling
 // new items slice_ns after the first warp started (0 = no limit); *t0 must be
 // zero before the launch; *counter ends >= the number of items taken.
@@ -214,7 +240,8 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
                            const WorkItem* ring, unsigned int mask, unsigned int base,
                            int n_items, unsigned int* counter, unsigned long long slice_ns,
                            unsigned long long* t0, int block_threads, int sm_count,
-                           cudaStream_t s, int poly_slots = 0, bool fixed = false);
+                           cudaStream_t s, const ParkBufs& park, int poly_slots = 0,
+                           bool fixed = false);
 
 // spectrum (sfhk_spectrum.cu)
 // Gabor map (sfhk_gabor.cu)

@@ -38,6 +38,7 @@
 //          cross-warp reduction in FP64 atomics.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "sfhk_device.cuh"
@@ -682,6 +683,88 @@ __device__ __forceinline__ C2<R> recomb_poly(const DevInstance& I, const R* tab,
     return Rk;
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// A lane's dynamic state in a park entry: column `lane` of kParkWords rows,
+// 32 words apart (STORE: write it there; else read it back).  Integers are
+// kept bit for bit in FP32 words and exactly in FP64 ones.
+template <typename R>
+__device__ __forceinline__ R park_from_int(int v)
+{
+    if constexpr (std::is_same<R, float>::value) return __int_as_float(v);
+    else return R(v);
+}
+template <typename R>
+__device__ __forceinline__ int park_to_int(R v)
+{
+    if constexpr (std::is_same<R, float>::value) return __float_as_int(v);
+    else return int(v);
+}
+
+template <typename R, bool STORE>
+__device__ __forceinline__ void park_io(R* col, R q[3], R ql[3], R p[3], R pl[3], Mono<R>& M,
+                                        R& S, R& Sl, C2<R>& Cp, R& Mhat, int& status,
+                                        int& n_ret, bool& left, R& e_ret, unsigned int& steps)
+{
+    int k = 0;
+    auto io = [&](R& v) {
+        if constexpr (STORE) col[k * kWarp] = v;
+        else v = col[k * kWarp];
+        ++k;
+    };
+    auto io_int = [&](int& v) {
+        R w = park_from_int<R>(v);
+        io(w);
+        if constexpr (!STORE) v = park_to_int<R>(w);
+    };
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        io(q[a]);
+        io(ql[a]);
+        io(p[a]);
+        io(pl[a]);
+    }
+    if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                io(M.q[c][r].x);
+                io(M.q[c][r].y);
+                io(M.p[c][r].x);
+                io(M.p[c][r].y);
+            }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                io(M.q[c][r]);
+                io(M.p[c][r]);
+            }
+    }
+    io(S);
+    io(Sl);
+    io(Cp.x);
+    io(Cp.y);
+    io(Mhat);
+    io(e_ret);
+    int lf = left ? 1 : 0, st = (int)steps;
+    io_int(status);
+    io_int(n_ret);
+    io_int(lf);
+    io_int(st);
+    if constexpr (!STORE) {
+        left = lf != 0;
+        steps = (unsigned int)st;
+    }
+}
+
 // per-warp buffer of the chunk's contributions: 32 steps x 32 trajectories,
 // row stride 33
 constexpr int kRedStride = kWarp + 1;
@@ -690,10 +773,16 @@ constexpr int kRedElems = kWarp * kRedStride;
 // POLY: a polyatomic target; tab is this lane's column of the warp's table
 // of lab-frame centre positions and p directions (rows of 32 words); NC > 0:
 // every such target of the launch has exactly NC centres.
-template <bool MIXED, bool POLY = false, int NC = 0, bool FIXED = false>
-__device__ __forceinline__ void process_item(const DevInstance& I, const WorkItem& W, int lane,
+// PARK (server slices): resume >= 0 restores the item's state from entry
+// `resume` of pk->in_*; with a deadline, the item is parked at the first
+// chunk boundary past it that has chunks left.  Returns whether the item
+// ran to its end (false: parked).
+template <bool MIXED, bool POLY = false, int NC = 0, bool FIXED = false, bool PARK = false>
+__device__ __forceinline__ bool process_item(const DevInstance& I, const WorkItem& W, int lane,
                                              typename std::conditional<MIXED, float, double>::type* red,
-                                             typename std::conditional<MIXED, float, double>::type* tab = nullptr)
+                                             typename std::conditional<MIXED, float, double>::type* tab = nullptr,
+                                             const ParkBufs* pk = nullptr, int resume = -1,
+                                             unsigned long long deadline = 0)
 {
     using R = typename std::conditional<MIXED, float, double>::type;
 
@@ -788,6 +877,15 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     C2<R> Cp = {R(1), R(0)};        // prefactor at the previous step
     int status = 0;                 // 0 alive, 1 prefactor filter, 2 non-finite, 3 stability filter
     unsigned int steps = 0;          // RK4 steps taken (< Nt)
+    int nb_first = W.n_start;        // first step of the first chunk this call runs
+    if constexpr (PARK) {
+        if (resume >= 0) {
+            R* col = (R*)pk->in_state + (size_t)resume * kParkWords * kWarp + lane;
+            park_io<R, false>(col, q, ql, p, pl, M, S, Sl, Cp, Mhat, status, n_ret, left, e_ret,
+                              steps);
+            nb_first = pk->in_hdr[resume].nb;
+        }
+    }
 
     const double dt = FIXED ? F::dt : I.dt;
     const R h = R(dt), h2 = R(0.5 * dt), h6 = R(dt / 6.0);
@@ -797,7 +895,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
     // Carried only within a step: the stage Hessians and increments.
     Sym3<R> Hs[4];
     R dq[3], dp[3], dS;
-    for (int nb = W.n_start; nb < nt; nb += kWarp) {
+    for (int nb = nb_first; nb < nt; nb += kWarp) {
         // chunk tables: E at the half steps of step nb+lane, e^{-i Ip t} at
         // nb+lane; broadcast by shuffles
         const int nl = nb + lane;
@@ -983,6 +1081,38 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         }
         __syncwarp();
         if (!__any_sync(kFull, has && status == 0)) break;
+        if constexpr (PARK) {
+            // time is up and chunks are left: park the item for the next slice
+            if (deadline != 0 && nb + kWarp < nt) {
+                unsigned long long now = 0;
+                if (lane == 0) now = global_ns();
+                now = __shfl_sync(kFull, now, 0);
+                if (now >= deadline) {
+                    unsigned int slot = 0;
+                    if (lane == 0) slot = atomicAdd(pk->out_ctr, 1u);
+                    slot = __shfl_sync(kFull, slot, 0);
+                    if (slot < (unsigned int)pk->cap) {
+                        R* col = (R*)pk->out_state + (size_t)slot * kParkWords * kWarp + lane;
+                        park_io<R, true>(col, q, ql, p, pl, M, S, Sl, Cp, Mhat, status, n_ret,
+                                         left, e_ret, steps);
+                        if (lane == 0) {
+                            ParkHdr hd;
+                            hd.W = W;
+                            hd.nb = nb + kWarp;
+                            hd.pad[0] = hd.pad[1] = hd.pad[2] = 0;
+                            pk->out_hdr[slot] = hd;
+                            // remaining work in the host's units (Nt per item):
+                            // the remaining fraction of the item's steps
+                            const long long left_steps = nt - (nb + kWarp);
+                            const long long all_steps = max(1, nt - W.n_start);
+                            atomicAdd(pk->out_work,
+                                      (unsigned long long)((long long)nt * left_steps / all_steps));
+                        }
+                        return false;
+                    }
+                }
+            }
+        }
     }
 
     // ---- counters and optional final state
@@ -1022,6 +1152,7 @@ __device__ __forceinline__ void process_item(const DevInstance& I, const WorkIte
         d[(size_t)45 * n + j] = double(n0 + (long long)steps);   // time index of this state
         d[(size_t)46 * n + j] = double(status);
     }
+    return true;
 }
 
 // The persistent loop over the work-item queue.  POLY: after the blocks'
@@ -1052,12 +1183,6 @@ __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
     }
 }
 
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Server slice of the same integrator: items come from a ring, warps stop
 // taking new items once the slice's time is up (an item, once taken, always
@@ -1066,13 +1191,18 @@ __device__ __forceinline__ unsigned long long global_ns()
 // the clock and an atomic counter.
 // POLY: the ring holds polyatomic requests' items, and every warp has its
 // centre table of `slots` rows after the reduction buffers (as run_queue).
+// Parked items of the previous slice are resumed first, whatever the time
+// (each then runs at least one chunk), then new items are taken until the
+// deadline; an item is parked at the first chunk boundary past the deadline
+// (process_item) and only an item that ran to its end counts as done.
 template <bool MIXED, bool POLY = false, bool FIXED = false>
 __device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ ring, unsigned int mask,
                                           unsigned int base, int n_items,
                                           unsigned int* __restrict__ counter,
                                           unsigned long long slice_ns,
-                                          unsigned long long* __restrict__ t0, int slots = 0)
+                                          unsigned long long* __restrict__ t0,
+                                          const ParkBufs* pk, int slots = 0)
 {
     using R = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1091,15 +1221,25 @@ __device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
     }
     deadline = __shfl_sync(kFull, deadline, 0);
     for (;;) {
-        int it = n_items;
-        if (lane == 0 && (slice_ns == 0 || global_ns() < deadline)) it = (int)atomicAdd(counter, 1u);
+        int it = n_items, r = -1;
+        if (lane == 0) {
+            if (pk->n_in > 0) {
+                const unsigned int k = atomicAdd(pk->in_ctr, 1u);
+                if (k < (unsigned int)pk->n_in) r = (int)k;
+            }
+            if (r < 0 && (slice_ns == 0 || global_ns() < deadline))
+                it = (int)atomicAdd(counter, 1u);
+        }
+        r = __shfl_sync(kFull, r, 0);
         it = __shfl_sync(kFull, it, 0);
-        if (it >= n_items) break;
-        const WorkItem W = ring[(base + (unsigned int)it) & mask];
+        if (r < 0 && it >= n_items) break;
+        const WorkItem W = r >= 0 ? pk->in_hdr[r].W : ring[(base + (unsigned int)it) & mask];
         const DevInstance& I = insts[W.inst];
+        bool done = true;
         if (I.cancel == nullptr || *I.cancel == 0)
-            process_item<MIXED, POLY, 0, FIXED>(I, W, lane, red, tab);
-        if (lane == 0 && I.done_items != nullptr) atomicAdd(I.done_items, 1u);
+            done = process_item<MIXED, POLY, 0, FIXED, true>(I, W, lane, red, tab, pk, r,
+                                                             slice_ns ? deadline : 0ull);
+        if (done && lane == 0 && I.done_items != nullptr) atomicAdd(I.done_items, 1u);
     }
 }
 
@@ -1174,18 +1314,19 @@ __global__ void __launch_bounds__(128)
     k_propagate_slice_nocap(const DevInstance* __restrict__ insts,
                             const WorkItem* __restrict__ ring, unsigned int mask,
                             unsigned int base, int n_items, unsigned int* __restrict__ counter,
-                            unsigned long long slice_ns, unsigned long long* __restrict__ t0)
+                            unsigned long long slice_ns, unsigned long long* __restrict__ t0,
+                            __grid_constant__ const ParkBufs pk)
 {
-    run_slice<MIXED>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
+    run_slice<MIXED>(insts, ring, mask, base, n_items, counter, slice_ns, t0, &pk);
 }
 template <bool MIXED, int MAXREG>
 __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
     k_propagate_slice(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ ring,
                       unsigned int mask, unsigned int base, int n_items,
                       unsigned int* __restrict__ counter, unsigned long long slice_ns,
-                      unsigned long long* __restrict__ t0)
+                      unsigned long long* __restrict__ t0, __grid_constant__ const ParkBufs pk)
 {
-    run_slice<MIXED>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
+    run_slice<MIXED>(insts, ring, mask, base, n_items, counter, slice_ns, t0, &pk);
 }
 
 // the mixed diatomic slice with FixedParams' values compiled in
@@ -1194,18 +1335,20 @@ __global__ void __launch_bounds__(128)
                                   const WorkItem* __restrict__ ring, unsigned int mask,
                                   unsigned int base, int n_items,
                                   unsigned int* __restrict__ counter, unsigned long long slice_ns,
-                                  unsigned long long* __restrict__ t0)
+                                  unsigned long long* __restrict__ t0,
+                                  __grid_constant__ const ParkBufs pk)
 {
-    run_slice<true, false, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
+    run_slice<true, false, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, &pk);
 }
 template <int MAXREG>
 __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
     k_propagate_slice_fixed(const DevInstance* __restrict__ insts,
                             const WorkItem* __restrict__ ring, unsigned int mask,
                             unsigned int base, int n_items, unsigned int* __restrict__ counter,
-                            unsigned long long slice_ns, unsigned long long* __restrict__ t0)
+                            unsigned long long slice_ns, unsigned long long* __restrict__ t0,
+                            __grid_constant__ const ParkBufs pk)
 {
-    run_slice<true, false, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0);
+    run_slice<true, false, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, &pk);
 }
 
 template <bool MIXED>
@@ -1214,9 +1357,10 @@ __global__ void __launch_bounds__(128)
                                  const WorkItem* __restrict__ ring, unsigned int mask,
                                  unsigned int base, int n_items,
                                  unsigned int* __restrict__ counter, unsigned long long slice_ns,
-                                 unsigned long long* __restrict__ t0, int slots)
+                                 unsigned long long* __restrict__ t0,
+                                 __grid_constant__ const ParkBufs pk, int slots)
 {
-    run_slice<MIXED, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, slots);
+    run_slice<MIXED, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, &pk, slots);
 }
 template <bool MIXED, int MAXREG>
 __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
@@ -1224,17 +1368,18 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
                            const WorkItem* __restrict__ ring, unsigned int mask,
                            unsigned int base, int n_items, unsigned int* __restrict__ counter,
                            unsigned long long slice_ns, unsigned long long* __restrict__ t0,
-                           int slots)
+                           __grid_constant__ const ParkBufs pk, int slots)
 {
-    run_slice<MIXED, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, slots);
+    run_slice<MIXED, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, &pk, slots);
 }
 
 using KernelFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*);
 using PolyFn = void (*)(const DevInstance*, const WorkItem*, int, unsigned int*, int);
 using SliceFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, unsigned int, int,
-                         unsigned int*, unsigned long long, unsigned long long*);
+                         unsigned int*, unsigned long long, unsigned long long*, const ParkBufs);
 using SlicePolyFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, unsigned int,
-                             int, unsigned int*, unsigned long long, unsigned long long*, int);
+                             int, unsigned int*, unsigned long long, unsigned long long*,
+                             const ParkBufs, int);
 
 // variants: index 0 = no register cap, then at most 168, 152, 144, 136, 128
 // registers per thread (12 to 16 resident warps per SM)
@@ -1332,10 +1477,14 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
                            const WorkItem* ring, unsigned int mask, unsigned int base,
                            int n_items, unsigned int* counter, unsigned long long slice_ns,
                            unsigned long long* t0, int block_threads, int sm_count,
-                           cudaStream_t s, int poly_slots, bool fixed)
+                           cudaStream_t s, const ParkBufs& park, int poly_slots, bool fixed)
 {
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
-    if (variant_index < 0 || variant_index >= kPropVariants || n_items <= 0) return SFHK_E_INVAL;
+    if (variant_index < 0 || variant_index >= kPropVariants || n_items < 0 || park.n_in < 0 ||
+        park.n_in > park.cap || n_items + (long long)park.n_in <= 0 || !park.in_ctr ||
+        !park.out_ctr || !park.out_work || !park.out_hdr || !park.out_state ||
+        (park.n_in > 0 && !park.in_state))
+        return SFHK_E_INVAL;
     if (poly_slots < 0 || poly_slots > SFHK_MAX_CENTRES + SFHK_MAX_PRIM) return SFHK_E_INVAL;
     const bool poly = poly_slots > 0;
     const bool mixed = precision == SFHK_MIXED;
@@ -1355,19 +1504,49 @@ int launch_propagate_slice(int precision, int variant_index, const DevInstance* 
     if (occ < 1) occ = 1;
     const int warps_per_block = block_threads / kWarp;
     int grid = sm_count * occ;
-    const int grid_cap = (n_items + warps_per_block - 1) / warps_per_block;
+    const int grid_cap = (int)((n_items + (long long)park.n_in + warps_per_block - 1) /
+                               warps_per_block);
     if (grid > grid_cap) grid = grid_cap;
+    // every warp of the launch can park one item at once
+    if ((long long)grid * warps_per_block > park.cap) return SFHK_E_INVAL;
     SFHK_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
     SFHK_CUDA_TRY(cudaMemsetAsync(t0, 0, sizeof(unsigned long long), s));
+    SFHK_CUDA_TRY(cudaMemsetAsync(park.in_ctr, 0, sizeof(unsigned int), s));
+    SFHK_CUDA_TRY(cudaMemsetAsync(park.out_ctr, 0, sizeof(unsigned int), s));
+    SFHK_CUDA_TRY(cudaMemsetAsync(park.out_work, 0, sizeof(unsigned long long), s));
     count_launch();
     if (poly)
         slice_poly_variant(precision, variant_index)<<<grid, block_threads, smem, s>>>(
-            insts, ring, mask, base, n_items, counter, slice_ns, t0, poly_slots);
+            insts, ring, mask, base, n_items, counter, slice_ns, t0, park, poly_slots);
     else
         slice_variant(precision, variant_index, fixed)<<<grid, block_threads, smem, s>>>(
-            insts, ring, mask, base, n_items, counter, slice_ns, t0);
+            insts, ring, mask, base, n_items, counter, slice_ns, t0, park);
     SFHK_CUDA_TRY(cudaGetLastError());
     return SFHK_OK;
+}
+
+int slice_max_warps(int precision, int variant_index, int block_threads, int sm_count)
+{
+    if (variant_index < 0 || variant_index >= kPropVariants || block_threads <= 0 ||
+        block_threads > 128 || block_threads % kWarp)
+        return 0;
+    const size_t smem = red_bytes(precision, block_threads);
+    int best = 0;
+    // the smallest shared memory of each kernel (a polyatomic slice adds its
+    // centre tables), so the largest occupancy
+    const void* fns[3] = {(const void*)slice_variant(precision, variant_index, false),
+                          (const void*)slice_variant(precision, variant_index, true),
+                          (const void*)slice_poly_variant(precision, variant_index)};
+    for (const void* fn : fns) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_threads, smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        best = std::max(best, occ);
+    }
+    return sm_count * best * (block_threads / kWarp);
 }
 
 int propagate_variant_maxreg(int v) { return (v >= 0 && v < kPropVariants) ? kVariantMaxReg[v] : 0; }

@@ -47,7 +47,7 @@ struct Req {
     int nt = 0;
     double t_origin = 0, dt = 0;
     std::vector<double> vz, yield, phase;
-    uint64_t traj_steps = 0, n_filtered = 0, n_unstable = 0, n_nonfinite = 0;
+    uint64_t traj_steps = 0, n_filtered = 0, n_unstable = 0, n_nonfinite = 0, recomb_evals = 0;
     int ring = 0;                    // 0: diatomic target, 1: polyatomic
     int poly_slots = 0;              // centre-table rows of a polyatomic target
     bool fixed = false;              // has the fixed parameters (sfhk::fixed_params)
@@ -100,7 +100,15 @@ struct sfhk_server {
         double rate = 0;             // work taken per second of slice time (smoothed; 0 = none yet)
         int n_generic = 0;           // active requests without the fixed parameters: while
                                      // there are any, the slice runs the generic integrator
+        // items the last slice parked (resumed by the next one), in park[cur],
+        // and their remaining work (in the units of queued_work)
+        sfhk::DeviceBuf park_hdr[2], park_state[2];
+        int cur = 0, n_parked = 0;
+        double parked_work = 0;
     } rings[2];
+    int park_cap = 0;                 // entries of each park buffer
+    sfhk::DeviceBuf pctr;             // per ring: resume and park counters (kCtrStride apart)
+    unsigned int* h_pctr = nullptr;   // pinned copy of the park counters
     std::vector<int> free_slots;
     std::vector<uint64_t> slot_req;
     unsigned int* h_done = nullptr;   // pinned
@@ -154,6 +162,26 @@ void end_request(sfhk_server* S, Req& q, int status)
 
 // whether an admitted request on ring k has waited longer than the age limit
 // of short-first (caller holds the lock)
+// the park buffers of both rings, sized for the largest slice launch of the
+// server's launch shape (every warp can park one item)
+int alloc_park(sfhk_server* S)
+{
+    const int prec = S->ro.precision;
+    sfhk::Ctx* c = S->ctx;
+    S->park_cap = sfhk::slice_max_warps(prec, c->tuned[prec][1], c->tuned[prec][0], c->sm_count);
+    if (S->park_cap <= 0) return SFHK_E_CUDA;
+    const size_t elem = prec == SFHK_MIXED ? sizeof(float) : sizeof(double);
+    for (auto& G : S->rings)
+        for (int b = 0; b < 2; ++b) {
+            int rc = c->alloc(G.park_hdr[b], sizeof(sfhk::ParkHdr) * (size_t)S->park_cap);
+            if (!rc)
+                rc = c->alloc(G.park_state[b],
+                              elem * sfhk::kParkWords * sfhk::kWarp * (size_t)S->park_cap);
+            if (rc) return rc;
+        }
+    return SFHK_OK;
+}
+
 bool aged(sfhk_server* S, int k)
 {
     if (!(S->o.max_reorder_s > 0.0)) return false;
@@ -197,8 +225,8 @@ void admit(sfhk_server* S)
             const auto& G = S->rings[q->r.target.kind == SFHK_POT_POLYATOMIC ? 1 : 0];
             if (G.tail - G.head + items > S->ring_cap) return;
             // admission horizon: enough work is already queued on this ring
-            if (S->o.max_queued_s > 0.0 && G.tail > G.head && G.rate > 0.0 &&
-                G.queued_work >= S->o.max_queued_s * G.rate)
+            if (S->o.max_queued_s > 0.0 && (G.tail > G.head || G.n_parked > 0) && G.rate > 0.0 &&
+                G.queued_work + G.parked_work >= S->o.max_queued_s * G.rate)
                 return;
             const size_t est = bytes_estimate(q->r.n_traj, pulse_nt(q->r.pulse));
             size_t used = 0;
@@ -244,8 +272,8 @@ void admit(sfhk_server* S)
             uint64_t pos;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
-                front = !S->o.fifo && G.tail > G.head && work < G.queued_work && G.head >= n &&
-                        !aged(S, q->ring);
+                front = !S->o.fifo && G.tail > G.head && work < G.queued_work + G.parked_work &&
+                        G.head >= n && !aged(S, q->ring);
                 pos = front ? G.head - n : G.tail;
             }
             const unsigned int at = (unsigned int)(pos & S->mask);
@@ -304,7 +332,7 @@ void harvest(sfhk_server* S)
         if (status == SFHK_OK) {
             sfhk_ensemble* e = q->ens;
             q->vz.resize(q->nt);
-            unsigned long long c[5] = {0, 0, 0, 0, 0};
+            unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
             if (cudaMemcpyAsync(q->vz.data(), e->vz.p, sizeof(double) * q->nt,
                                 cudaMemcpyDeviceToHost, S->s) != cudaSuccess ||
                 cudaMemcpyAsync(c, e->counters.p, sizeof c, cudaMemcpyDeviceToHost, S->s) !=
@@ -331,6 +359,7 @@ void harvest(sfhk_server* S)
             q->n_nonfinite = c[1];
             q->traj_steps = c[2];
             q->n_unstable = c[4];
+            q->recomb_evals = c[5];
             if (status == SFHK_OK && S->o.check_nonfinite && c[1] > S->o.max_nonfinite) {
                 status = SFHK_E_NUMERIC;       // over the limit: no dipole or spectrum
                 q->vz.clear();
@@ -348,11 +377,15 @@ void harvest(sfhk_server* S)
 void run_slice(sfhk_server* S)
 {
     uint64_t n64[2];
+    int parked[2];                   // items the last slice parked, resumed first
     int slots = 0;                   // centre-table rows the polyatomic slice needs
     bool fixed = false;              // every diatomic request has the fixed parameters
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        for (int k = 0; k < 2; ++k) n64[k] = S->rings[k].tail - S->rings[k].head;
+        for (int k = 0; k < 2; ++k) {
+            n64[k] = S->rings[k].tail - S->rings[k].head;
+            parked[k] = S->rings[k].n_parked;
+        }
         fixed = S->rings[0].n_generic == 0;
         // cancellations of running requests reach the device before the slice
         for (size_t slot = 0; slot < S->slot_req.size(); ++slot) {
@@ -367,8 +400,8 @@ void run_slice(sfhk_server* S)
             }
         }
     }
-    if (n64[0] == 0 && n64[1] == 0) return;
-    if (n64[1] > 0 && slots < 1) slots = 1;
+    if (n64[0] == 0 && n64[1] == 0 && parked[0] == 0 && parked[1] == 0) return;
+    if ((n64[1] > 0 || parked[1] > 0) && slots < 1) slots = 1;
     int bt = S->ctx->tuned[S->ro.precision][0];
     int var = S->ctx->tuned[S->ro.precision][1];
     const auto t_a = Clock::now();
@@ -376,20 +409,36 @@ void run_slice(sfhk_server* S)
     int n[2] = {0, 0};
     // one slice of each ring that has work, one after the other on the
     // server's stream (each kernel fills the GPU while it runs)
+    bool ran[2] = {false, false};
     for (int k = 0; k < 2 && !rc; ++k) {
-        if (n64[k] == 0) continue;
+        if (n64[k] == 0 && parked[k] == 0) continue;
         auto& G = S->rings[k];
         n[k] = (int)std::min<uint64_t>(n64[k], 0x7fffffffu);
         unsigned int* ctr = (unsigned int*)((char*)S->ctr.p + k * kCtrStride);
+        unsigned int* pc = (unsigned int*)((char*)S->pctr.p + k * kCtrStride);
+        sfhk::ParkBufs pk;
+        pk.in_hdr = (const sfhk::ParkHdr*)G.park_hdr[G.cur].p;
+        pk.in_state = G.park_state[G.cur].p;
+        pk.n_in = parked[k];
+        pk.in_ctr = pc;
+        pk.out_hdr = (sfhk::ParkHdr*)G.park_hdr[1 - G.cur].p;
+        pk.out_state = G.park_state[1 - G.cur].p;
+        pk.out_ctr = pc + 1;
+        pk.out_work = (unsigned long long*)(pc + 2);
+        pk.cap = S->park_cap;
         rc = sfhk::launch_propagate_slice(
             S->ro.precision, var, (const sfhk::DevInstance*)S->insts.p,
             (const sfhk::WorkItem*)G.items.p, S->mask, (unsigned int)(G.head & S->mask), n[k],
             ctr, (unsigned long long)(S->o.slice_ms * 1e6),
             (unsigned long long*)((char*)S->t0.p + k * kCtrStride), bt, S->ctx->sm_count, S->s,
-            k == 1 ? slots : 0, k == 0 && fixed);
-        if (!rc && cudaMemcpyAsync((char*)S->h_ctr + k * kCtrStride, ctr, sizeof(unsigned int),
-                                   cudaMemcpyDeviceToHost, S->s) != cudaSuccess)
+            pk, k == 1 ? slots : 0, k == 0 && fixed);
+        if (!rc && (cudaMemcpyAsync((char*)S->h_ctr + k * kCtrStride, ctr, sizeof(unsigned int),
+                                    cudaMemcpyDeviceToHost, S->s) != cudaSuccess ||
+                    cudaMemcpyAsync((char*)S->h_pctr + k * kCtrStride, pc,
+                                    2 * sizeof(unsigned int) + sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, S->s) != cudaSuccess))
             rc = SFHK_E_CUDA;
+        ran[k] = !rc;
     }
     if (!rc && cudaMemcpyAsync(S->h_done, S->done.p, sizeof(unsigned int) * S->slot_req.size(),
                                cudaMemcpyDeviceToHost, S->s) != cudaSuccess)
@@ -401,20 +450,33 @@ void run_slice(sfhk_server* S)
     S->st.gpu_busy_s += busy;
     if (!rc) {
         for (int k = 0; k < 2; ++k) {
-            if (n64[k] == 0) continue;
+            if (!ran[k]) continue;
             auto& G = S->rings[k];
-            const unsigned int got = *(const unsigned int*)((const char*)S->h_ctr + k * kCtrStride);
-            const uint64_t taken = std::min<uint64_t>(got, (uint64_t)n[k]);
-            const double before = G.queued_work;
-            G.queued_work =
-                taken >= n64[k] ? 0.0 : G.queued_work * double(n64[k] - taken) / double(n64[k]);
-            // the ring's rate over a slice that did not run out of work
-            // (a drained ring says nothing about how fast it goes)
-            if (taken < n64[k] && busy > 0.0) {
-                const double r = (before - G.queued_work) / busy;
+            const double before = G.queued_work + G.parked_work;
+            // this slice's parked items are the next slice's to resume; their
+            // remaining work stays queued
+            const unsigned int* hp =
+                (const unsigned int*)((const char*)S->h_pctr + k * kCtrStride);
+            G.n_parked = (int)std::min<unsigned int>(hp[1], (unsigned int)S->park_cap);
+            G.parked_work = (double)*(const unsigned long long*)(hp + 2);
+            G.cur = 1 - G.cur;
+            S->st.parked += (uint64_t)G.n_parked;
+            uint64_t taken = 0;
+            if (n64[k] > 0) {
+                const unsigned int got =
+                    *(const unsigned int*)((const char*)S->h_ctr + k * kCtrStride);
+                taken = std::min<uint64_t>(got, (uint64_t)n[k]);
+                G.queued_work = taken >= n64[k]
+                                    ? 0.0
+                                    : G.queued_work * double(n64[k] - taken) / double(n64[k]);
+                G.head += taken;
+            }
+            // the ring's rate over a slice that did not run out of work (a
+            // drained ring says nothing about how fast it goes)
+            if ((taken < n64[k] || G.n_parked > 0) && busy > 0.0) {
+                const double r = (before - G.queued_work - G.parked_work) / busy;
                 G.rate = G.rate > 0.0 ? 0.7 * G.rate + 0.3 * r : r;
             }
-            G.head += taken;
         }
     }
 }
@@ -432,7 +494,8 @@ void loop(sfhk_server* S)
         bool work;
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            work = S->rings[0].tail > S->rings[0].head || S->rings[1].tail > S->rings[1].head;
+            work = S->rings[0].tail > S->rings[0].head || S->rings[1].tail > S->rings[1].head ||
+                   S->rings[0].n_parked > 0 || S->rings[1].n_parked > 0;
         }
         if (work) {
             run_slice(S);
@@ -473,6 +536,7 @@ int copy_result(Req& q, sfhk_result* r)
     r->n_filtered = q.n_filtered;
     r->n_unstable = q.n_unstable;
     r->n_nonfinite = q.n_nonfinite;
+    r->recomb_evals = q.recomb_evals;
     return SFHK_OK;
 }
 
@@ -520,7 +584,9 @@ int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** o
         (rc = c->alloc(S->done, sizeof(unsigned int) * S->o.max_active)) ||
         (rc = c->alloc(S->cancelf, sizeof(int) * S->o.max_active)) ||
         (rc = c->alloc(S->ctr, 2 * kCtrStride)) || (rc = c->alloc(S->t0, 2 * kCtrStride)) ||
-        (rc = c->alloc(S->spec, sizeof(double) * 5 * (size_t)S->max_nt))) {
+        (rc = c->alloc(S->pctr, 2 * kCtrStride)) ||
+        (rc = c->alloc(S->spec, sizeof(double) * 5 * (size_t)S->max_nt)) ||
+        (rc = alloc_park(S))) {
         sfhk_destroy(S->ctx);
         delete S;
         return rc;
@@ -528,7 +594,8 @@ int sfhk_server_create(int device, const sfhk_server_opts* opts, sfhk_server** o
     if (cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaHostAlloc((void**)&S->h_done, sizeof(unsigned int) * S->o.max_active,
                       cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void**)&S->h_ctr, 2 * kCtrStride, cudaHostAllocDefault) != cudaSuccess) {
+        cudaHostAlloc((void**)&S->h_ctr, 2 * kCtrStride, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&S->h_pctr, 2 * kCtrStride, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         sfhk_destroy(S->ctx);
         delete S;
@@ -555,11 +622,17 @@ int sfhk_server_destroy(sfhk_server* S)
     if (S->th.joinable()) S->th.join();
     sfhk::Ctx* c = S->ctx;
     for (sfhk::DeviceBuf* b : {&S->insts, &S->rings[0].items, &S->rings[1].items, &S->done,
-                               &S->cancelf, &S->ctr, &S->t0, &S->spec})
+                               &S->cancelf, &S->ctr, &S->t0, &S->pctr, &S->spec})
         c->release(*b);
+    for (auto& G : S->rings)
+        for (int b = 0; b < 2; ++b) {
+            c->release(G.park_hdr[b]);
+            c->release(G.park_state[b]);
+        }
     if (S->s) cudaStreamDestroy(S->s);
     if (S->h_done) cudaFreeHost(S->h_done);
     if (S->h_ctr) cudaFreeHost(S->h_ctr);
+    if (S->h_pctr) cudaFreeHost(S->h_pctr);
     sfhk_destroy(S->ctx);
     delete S;
     return SFHK_OK;

@@ -99,7 +99,8 @@ class sfhk_result(C.Structure):
                 ("phase", C.POINTER(C.c_double)), ("spec_capacity", C.c_size_t),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
                 ("traj_steps", C.c_uint64), ("n_filtered", C.c_uint64),
-                ("n_unstable", C.c_uint64), ("n_nonfinite", C.c_uint64)]
+                ("n_unstable", C.c_uint64), ("n_nonfinite", C.c_uint64),
+                ("recomb_evals", C.c_uint64)]
 
 
 class sfhk_server_stats(C.Structure):
@@ -107,7 +108,7 @@ class sfhk_server_stats(C.Structure):
                 ("cancelled", C.c_uint64), ("failed", C.c_uint64), ("slices", C.c_uint64),
                 ("traj_steps", C.c_uint64), ("pending", C.c_int), ("active", C.c_int),
                 ("gpu_busy_s", C.c_double), ("uptime_s", C.c_double),
-                ("device_bytes", C.c_uint64)]
+                ("device_bytes", C.c_uint64), ("parked", C.c_uint64)]
 
 
 SFHK_E_CANCELLED = -8
@@ -486,7 +487,8 @@ class Result:
                     vz=self.vz[:c.nt].copy(), yield_=self.yield_[:c.n_out].copy(),
                     phase=self.phase[:c.n_out].copy(), t_submit=c.t_submit, t_admit=c.t_admit,
                     t_done=c.t_done, traj_steps=c.traj_steps, n_filtered=c.n_filtered,
-                    n_unstable=c.n_unstable, n_nonfinite=c.n_nonfinite)
+                    n_unstable=c.n_unstable, n_nonfinite=c.n_nonfinite,
+                    recomb_evals=c.recomb_evals)
 
 
 def sfhk_poll(server, rid, res: Result = None):

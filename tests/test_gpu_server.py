@@ -54,17 +54,22 @@ def _alone(S, ctx, name, pulse, align, n, inst, prec):
     return vz
 
 
-@pytest.mark.parametrize("prec_name,tol", [("FP64", 1e-12), ("MIXED", 1e-5)])
-def test_results_in_the_mix_equal_alone(S, prec_name, tol):
+@pytest.mark.parametrize("prec_name,tol,slice_ms", [("FP64", 1e-12, 5.0), ("MIXED", 1e-5, 5.0),
+                                                    ("FP64", 1e-12, 0.5), ("MIXED", 1e-5, 0.5)])
+def test_results_in_the_mix_equal_alone(S, prec_name, tol, slice_ms):
+    """With 0.5 ms slices nearly every item is parked at a chunk boundary and
+    resumed by the next slice many times over; the results do not change."""
     prec = getattr(S, "SFHK_" + prec_name)
     srv = S.sfhk_server_create(0, S.server_opts(prec, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
-                                                slice_ms=5.0))
+                                                slice_ms=slice_ms))
     ids = [S.sfhk_submit(srv, S.request(W.TARGETS[nm], p, al, n, 7, inst))
            for nm, p, al, n, inst in MIX]
     res = [S.sfhk_wait(srv, i, 300.0) for i in ids]
     st = S.sfhk_server_stats_get(srv)
     S.sfhk_server_destroy(srv)
     assert st["completed"] == len(MIX) and st["failed"] == 0
+    if slice_ms < 1.0:          # more parkings than work items
+        assert st["parked"] > sum(-(-n // 32) for _, _, _, n, _ in MIX)
     ctx = S.sfhk_create(0, 0)
     for (nm, p, al, n, inst), r in zip(MIX, res):
         assert r["status"] == S.SFHK_OK
@@ -159,7 +164,7 @@ def test_admission_horizon_bounds_resident_work(S):
     Every request completes either way."""
     peak, res = _burst_behind_a_long_request(S, max_queued_s=0.05)
     assert all(r["status"] == S.SFHK_OK for r in res)
-    assert peak <= 8
+    assert peak <= 12
     assert max(r["t_admit"] - r["t_submit"] for r in res[1:]) > 0.05
     peak0, res0 = _burst_behind_a_long_request(S)
     assert all(r["status"] == S.SFHK_OK for r in res0)
