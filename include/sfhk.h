@@ -445,14 +445,17 @@ SFHK_API int sfhk_gabor(const double* vz, size_t nt, double dt, double t_origin,
  * server admits submitted requests (one target, pulse, alignment and
  * trajectory count each) in arrival order while its device-memory budget,
  * its instance slots, its work rings and its admission horizon have room,
- * samples each admitted
- * request on the device, and appends its work items (32 trajectories, longest
- * first) to a device ring: one for diatomic targets, one for polyatomic ones.
- * The GPU runs the integrator as a sequence of persistent slices over those
- * rings (each slice launches the diatomic and then the polyatomic integrator
- * over the rings that have work): a slice's warps stop taking new items
- * once `slice_ms` has passed (an item once taken runs to its end) and every
- * request that arrived meanwhile joins the next slice, so the work of
+ * samples each admitted request on the device, and appends its work items
+ * (32 trajectories, longest first) to a device ring: one for diatomic
+ * targets, one for polyatomic ones.  The GPU runs the integrator as a
+ * sequence of persistent slices over those rings (each slice launches the
+ * diatomic and then the polyatomic integrator over the rings that have
+ * work): once `slice_ms` has passed, a warp takes no new item and parks the
+ * one it runs at its next 32-step chunk boundary (the state of its
+ * trajectories goes to a device buffer; the next slice resumes parked items
+ * before it takes new ones, with the same arithmetic), so a slice ends
+ * within one chunk of its deadline, and every request that arrived
+ * meanwhile joins the next slice, so the work of
  * requests of different sizes, targets and pulses runs on the device
  * together.  A request is done when all its items are; the server then
  * copies its dipole (and spectrum) to host memory and frees its device state,
