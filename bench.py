@@ -536,7 +536,7 @@ def sub_batched(S, torch, ctx, stream, local, peaks, args):
     mixed = S.run_opts(S.SFHK_MIXED, W.GAMMA, W.CUTOFF, stab_cutoff=W.STAB_CUTOFF,
                        stab_taper=W.STAB_TAPER)
     big = max(range(len(insts)), key=lambda k: insts[k]["n_traj"])
-    tuned = S.sfhk_autotune(ctx, ens[big], mixed, max_items=8192)
+    tuned = S.sfhk_autotune(ctx, ens[big], mixed, max_items=0)
     batch = S.sfhk_batch_create(ctx, ens, mixed)
 
     def step():
