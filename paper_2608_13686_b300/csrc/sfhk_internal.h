@@ -108,8 +108,11 @@ struct Ctx {
     std::atomic<size_t> used{0};
     std::mutex mu;
     // tuned launch shape per precision: [block_threads, variant, blocks_per_sm]
-    // (before tuning: 128 threads, the variant capped at 3 blocks per SM)
-    int tuned[2][3] = {{128, 2, 0}, {128, 2, 0}};
+    // (variant: index into 0 = no cap, 168, 152, ... registers; blocks per SM
+    // 0 = as many as fit).  Before tuning: 128 threads, FP64 at the 152-
+    // register cap, mixed precision at 168 (the fixed-parameter kernels spill
+    // 20 B there against 104 B at 152)
+    int tuned[2][3] = {{128, 2, 0}, {128, 1, 0}};
     int alloc(DeviceBuf& b, size_t bytes);
     void release(DeviceBuf& b);
 };
