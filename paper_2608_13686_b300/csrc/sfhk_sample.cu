@@ -113,6 +113,9 @@ struct SampleParams {
     // N (2 pi)^{-3/2}, the ADK exponent's 2 (2 Ip)^{3/2} / 3, sqrt(2 Ip)
     double pfac[SFHK_MAX_PRIM];
     double mz_scale, adk_c, sqrt2Ip;
+    // reciprocals of the pulse's frequencies k_q and of k_q -+ k_r (0 where
+    // the frequency is 0)
+    double ik[3], ikd[3][3], iks[3][3];
     int pkind[SFHK_MAX_PRIM];
     double cchi, schi;                        // pi lobe azimuth (cos, sin)
     // polyatomic targets: Euler-angle orientation, primitives on their own centres
@@ -124,22 +127,25 @@ struct SampleParams {
     double pdir[SFHK_MAX_PRIM][3];            // unit, molecular frame (p-type)
 };
 
-// sinh x and cosh x - 1 from em = e^x - 1, without cancellation
-__device__ __forceinline__ void sh_cm1(double em, double& sh, double& cm1)
+// sinh x and cosh x - 1 from em = e^x - 1 and r = 1 / e^x (formed once by
+// the caller), without cancellation
+__device__ __forceinline__ void sh_cm1(double em, double r, double& sh, double& cm1)
 {
-    const double d = 0.5 / (em + 1.0);
+    const double d = 0.5 * r;
     sh = em * (em + 2.0) * d;
     cm1 = em * em * d;
 }
 
 // int_0^T cos(al + i be s) ds = (cos(al) sinh(x) - i sin(al) (cosh x - 1)) / be,
-// x = be T, given cos(al), sin(al) and em = e^x - 1
-__device__ __forceinline__ double2 int_cos(double ca, double sa, double be, double em, double T)
+// x = be T, given cos(al), sin(al), ibe = 1/be (0 for be = 0), em = e^x - 1
+// and r = 1 / e^x
+__device__ __forceinline__ double2 int_cos(double ca, double sa, double ibe, double em, double r,
+                                           double T)
 {
-    if (be == 0.0) return make_double2(T * ca, 0.0);
+    if (ibe == 0.0) return make_double2(T * ca, 0.0);
     double sh, cm1;
-    sh_cm1(em, sh, cm1);
-    return make_double2(ca * sh / be, -sa * cm1 / be);
+    sh_cm1(em, r, sh, cm1);
+    return make_double2(ca * sh * ibe, -sa * cm1 * ibe);
 }
 
 // One draw of the proposal from the six uniforms u (trajectory index j for
@@ -295,21 +301,27 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
             ok = solve(g, -Ystar, &tt);     // g(0) = -Y*
         }
         if (ok) {
-            // ---- k_z, exit and action in closed form; em[q] = e^{k_q tt} - 1
-            double em[3];
+            // ---- k_z, exit and action in closed form; em[q] = e^{k_q tt} - 1,
+            // ir[q] = e^{-k_q tt}: the one division per term, every other
+            // quotient a product with it or with the pulse's 1/k (host)
+            double em[3], ep[3], ir[3], shq[3], cmq[3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) em[q] = expm1(S.P.k[q] * tt);
+            for (int q = 0; q < 3; ++q) {
+                em[q] = expm1(S.P.k[q] * tt);
+                ep[q] = 1.0 + em[q];
+                ir[q] = 1.0 / ep[q];
+                sh_cm1(em[q], ir[q], shq[q], cmq[q]);
+            }
             double At0 = 0.0, dRe = 0.0, q0 = 0.0, Yt = 0.0;
             double2 Es = make_double2(0.0, 0.0);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const double a = S.P.a[q], k = S.P.k[q];
-                double sh, cm1;
-                sh_cm1(em[q], sh, cm1);
+                const double sh = shq[q], cm1 = cmq[q];
                 At0 += a * sthm[q];
                 dRe += a * sthm[q] * cm1;                  // Re A(t_s) - A(t0)
                 Yt += a * cthm[q] * sh;                    // Im A(t_s)
-                if (k != 0.0) q0 += a * cthm[q] * cm1 / k; // int_0^tt Im A(t0+is) ds
+                if (k != 0.0) q0 += a * cthm[q] * cm1 * S.ik[q];   // int_0^tt Im A(t0+is) ds
                 // E(t_s) = -sum a k cos(th + i k tt)
                 Es.x -= a * k * cthm[q] * (cm1 + 1.0);
                 Es.y += a * k * sthm[q] * sh;
@@ -331,20 +343,22 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                 if (k == 0.0) {
                     is = make_double2(tt * sthm[q], 0.0);
                 } else {
-                    double sh, cm1;
-                    sh_cm1(em[q], sh, cm1);
-                    is = make_double2(sthm[q] * sh / k, cthm[q] * cm1 / k);
+                    is = make_double2(sthm[q] * shq[q] * S.ik[q], cthm[q] * cmq[q] * S.ik[q]);
                 }
                 IB = cadd(IB, cscale(is, 2.0 * cp * S.P.a[q]));
 #pragma unroll
                 for (int r = q; r < 3; ++r) {
                     const double cc = cthm[q] * cthm[r], ss = sthm[q] * sthm[r];
                     const double sc = sthm[q] * cthm[r], cs = cthm[q] * sthm[r];
-                    const double emd = (em[q] - em[r]) / (1.0 + em[r]);
+                    // e^{(k_q - k_r) tt} - 1 and e^{(k_q + k_r) tt} - 1, with their
+                    // reciprocal exponentials e^{-(k_q -+ k_r) tt}
+                    const double emd = (em[q] - em[r]) * ir[r];
                     const double ems = em[q] + em[r] + em[q] * em[r];
-                    const double2 d1 = q == r ? make_double2(tt, 0.0)
-                                              : int_cos(cc + ss, sc - cs, S.P.k[q] - S.P.k[r], emd, tt);
-                    const double2 d2 = int_cos(cc - ss, sc + cs, S.P.k[q] + S.P.k[r], ems, tt);
+                    const double2 d1 =
+                        q == r ? make_double2(tt, 0.0)
+                               : int_cos(cc + ss, sc - cs, S.ikd[q][r], emd, ep[r] * ir[q], tt);
+                    const double2 d2 =
+                        int_cos(cc - ss, sc + cs, S.iks[q][r], ems, ir[q] * ir[r], tt);
                     const double f = (q == r ? 0.5 : 1.0) * S.P.a[q] * S.P.a[r];
                     IB = cadd(IB, cscale(csub(d1, d2), f));
                 }
@@ -435,11 +449,9 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                 double2 Ed = make_double2(0.0, 0.0);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    double sh, cm1;
-                    sh_cm1(em[q], sh, cm1);
                     const double ak2 = S.P.a[q] * S.P.k[q] * S.P.k[q];
-                    Ed.x += ak2 * sthm[q] * (cm1 + 1.0);
-                    Ed.y += ak2 * cthm[q] * sh;
+                    Ed.x += ak2 * sthm[q] * (cmq[q] + 1.0);
+                    Ed.y += ak2 * cthm[q] * shq[q];
                 }
                 curv = cadd(curv, cscale(Ed, cmod));
             }
@@ -783,6 +795,14 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
         for (int k = 0; k < al.n_nodes; ++k) S.qkw[k] *= al.n_nodes;
     }
     S.P = pulse_terms(P.omega, P.E0, P.Tp, P.desc.cep);
+    for (int q = 0; q < 3; ++q) {
+        S.ik[q] = S.P.k[q] != 0.0 ? 1.0 / S.P.k[q] : 0.0;
+        for (int r = 0; r < 3; ++r) {
+            const double d = S.P.k[q] - S.P.k[r], m = S.P.k[q] + S.P.k[r];
+            S.ikd[q][r] = d != 0.0 ? 1.0 / d : 0.0;
+            S.iks[q][r] = m != 0.0 ? 1.0 / m : 0.0;
+        }
+    }
     S.omega = P.omega;
     S.E0 = P.E0;
     S.Tp = P.Tp;
