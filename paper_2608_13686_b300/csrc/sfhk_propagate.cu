@@ -1185,10 +1185,9 @@ __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
 
 
 // Server slice of the same integrator: items come from a ring, warps stop
-// taking new items once the slice's time is up (an item, once taken, always
-// runs to its end), count finished items per instance, and skip the items of
-// cancelled instances.  No thread waits on another: a warp only ever reads
-// the clock and an atomic counter.
+// taking new items once the slice's time is up, count finished items per
+// instance, and skip the items of cancelled instances.  No thread waits on
+// another: a warp only ever reads the clock and atomic counters.
 // POLY: the ring holds polyatomic requests' items, and every warp has its
 // centre table of `slots` rows after the reduction buffers (as run_queue).
 // Parked items of the previous slice are resumed first, whatever the time
