@@ -228,11 +228,14 @@ def test_cancel(S):
     S.sfhk_server_destroy(srv)
 
 
-def test_polyatomic_requests_are_served_with_diatomic_ones(S):
+@pytest.mark.parametrize("slice_ms", [5.0, 0.5])
+def test_polyatomic_requests_are_served_with_diatomic_ones(S, slice_ms):
     """Polyatomic requests (their own ring and integrator kernel) served in one
     stream with diatomic ones, each result against the FP64 oracle on the same
-    draws: 1e-9 in FP64, 1e-4 in mixed precision.  A polyatomic request with a
-    quadrature alignment is refused at submission."""
+    draws: 1e-9 in FP64, 1e-4 in mixed precision; with 0.5 ms slices the
+    items of both rings are parked and resumed many times (a resumed
+    polyatomic item rebuilds its lanes' centre table).  A polyatomic request
+    with a quadrature alignment is refused at submission."""
     import oracle as O
     mix = [(W.TARGETS["H2O"], W.PULSE_800, W.ISO, 700, 1),
            (W.TARGETS["H2"], W.PULSE_800, W.fixed(30.0), 1500, 2),
@@ -245,12 +248,15 @@ def test_polyatomic_requests_are_served_with_diatomic_ones(S):
                                stab_taper=W.STAB_TAPER)[0])
     for prec, tol in ((S.SFHK_FP64, 1e-9), (S.SFHK_MIXED, 1e-4)):
         srv = S.sfhk_server_create(0, S.server_opts(prec, W.GAMMA, W.CUTOFF, W.STAB_CUTOFF,
-                                                    slice_ms=5.0, stab_taper=W.STAB_TAPER))
+                                                    slice_ms=slice_ms, stab_taper=W.STAB_TAPER))
         with pytest.raises(S.SfhkError):
             S.sfhk_submit(srv, S.request(W.TARGETS["H2O"], W.PULSE_800, W.quadrature(4), 64, 1, 0))
         ids = [S.sfhk_submit(srv, S.request(t, p, al, n, 7, inst)) for t, p, al, n, inst in mix]
         res = [S.sfhk_wait(srv, i, 300.0) for i in ids]
+        st = S.sfhk_server_stats_get(srv)
         S.sfhk_server_destroy(srv)
+        if slice_ms < 1.0:          # more parkings than work items
+            assert st["parked"] > sum(-(-n // 32) for _, _, _, n, _ in mix)
         for (t, p, al, n, inst), r, v in zip(mix, res, ref):
             assert r["status"] == S.SFHK_OK
             err = _rel(r["vz"], v)
