@@ -710,9 +710,9 @@ int sfhk_propagate(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, void* 
     rc = launch_propagate(o->precision, var, (const DevInstance*)e->inst.p,
                           (const WorkItem*)e->items.p, e->n_items, (unsigned int*)e->qctr.p, bt,
                           bps, c->sm_count, s, slots, nc,
-                          runs_fixed(o->precision, slots, nc, fixed_params(I)));
+                          fixed_form(&I, 1, o->precision, slots, nc));
     if (rc) return rc;
-    e->fixed = runs_fixed(o->precision, slots, nc, fixed_params(I));
+    e->fixed = fixed_form(&I, 1, o->precision, slots, nc) != kPotAny;
     SFHK_CUDA_TRY(record_event(e->ev_stop, s));
     SFHK_CUDA_TRY(record_event(e->ev_done, s));
     e->have_result = true;
@@ -793,10 +793,8 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
     if (!rc)
         rc = launch_propagate(o->precision, var, d_inst, d_sorted, (int)total_items, d_ctr, bt,
                               bps, c->sm_count, s, slots, nc,
-                              runs_fixed(o->precision, slots, nc,
-                                         std::all_of(hI.begin(), hI.end(), fixed_params)));
-    const bool fixed =
-        runs_fixed(o->precision, slots, nc, std::all_of(hI.begin(), hI.end(), fixed_params));
+                              fixed_form(hI.data(), n_ens, o->precision, slots, nc));
+    const bool fixed = fixed_form(hI.data(), n_ens, o->precision, slots, nc) != kPotAny;
     for (int i = 0; i < n_ens && !rc; ++i) {
         ens[i]->fixed = fixed;
         if (record_event(ens[i]->ev_stop, s) != cudaSuccess ||
@@ -824,7 +822,7 @@ struct sfhk_batch {
     int max_nt = 1;
     int poly_slots = 0;
     int poly_nc = 0;                 // common centre count of the polyatomic targets
-    bool fixed = false;              // every instance has FixedParams' values
+    int fixed = kPotAny;             // the FixedParams instantiation it runs (fixed_form)
 };
 
 extern "C" {
@@ -884,8 +882,7 @@ int sfhk_batch_create(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens, const s
         hI[i] = make_instance(ens[i], b->opts);
         hnt[i] = ens[i]->pulse->nt;
     }
-    b->fixed = runs_fixed(b->opts.precision, b->poly_slots, b->poly_nc,
-                          std::all_of(hI.begin(), hI.end(), fixed_params));
+    b->fixed = fixed_form(hI.data(), n_ens, b->opts.precision, b->poly_slots, b->poly_nc);
     if (cudaMemcpy(b->d_inst, hI.data(), sizeof(DevInstance) * n_ens, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(b->d_nt, hnt.data(), sizeof(int) * n_ens, cudaMemcpyHostToDevice) !=
@@ -917,7 +914,7 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
         off += e->n_items;
         e->dumped = false;
         e->have_result = true;
-        e->fixed = b->fixed;
+        e->fixed = b->fixed != kPotAny;
         set_nonfinite_limit(e, b->opts);
     }
     rc = launch_sort_items(b->d_items, (int)b->total_items, b->d_nt, b->d_sorted, b->d_keys,
@@ -973,7 +970,7 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
         const int r = launch_propagate(o->precision, v, (const DevInstance*)e->inst.p,
                                        (const WorkItem*)e->items.p, items,
                                        (unsigned int*)e->qctr.p, b, 0, c->sm_count, 0, slots,
-                                       nc, runs_fixed(o->precision, slots, nc, fixed_params(I)));
+                                       nc, fixed_form(&I, 1, o->precision, slots, nc));
         if (r) return r;
         SFHK_CUDA_TRY(cudaEventRecord(e->ev_stop, 0));
         SFHK_CUDA_TRY(cudaEventSynchronize(e->ev_stop));

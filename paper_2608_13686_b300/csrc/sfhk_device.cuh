@@ -11,6 +11,8 @@
 
 #include <cstdint>
 
+#include "sfhk_internal.h"
+
 namespace sfhk {
 
 // ------------------------------------------------------------------ Philox4x32-10
@@ -232,11 +234,17 @@ __device__ __forceinline__ void centre_diffs(const PotConst<R>& K, const R q[3],
 // base point's centre differences e (centre_diffs) and the RK4 stage offset
 // o; OFS = false: the stage point is the base point itself (o ignored).  The
 // harmonic test potential (R = 0) reads the position from e[0].
-template <typename R, bool OFS = true>
+// PK, the form of the potential when it is known at compile time (kPot*,
+// sfhk_internal.h); each form runs the same arithmetic as the run-time
+// branches it replaces.
+
+template <typename R, bool OFS = true, int PK = kPotAny>
 __device__ __forceinline__ void potential(const PotConst<R>& K, const R e[2][3], R ox, R oy,
                                           R oz, R& V, R& Fx, R& Fy, R& Fz, Sym3<R>& H)
 {
-    if (K.kind != 0) {            // harmonic test potential
+    // the screening of a molecular target (K.screened when decided at run time)
+    const bool screened = PK == kPotBare ? false : PK == kPotScreened ? true : K.screened != 0;
+    if (PK == kPotAny && K.kind != 0) {            // harmonic test potential
         const R x = OFS ? e[0][0] + ox : e[0][0];
         const R y = OFS ? e[0][1] + oy : e[0][1];
         const R z = OFS ? e[0][2] + oz : e[0][2];
@@ -264,7 +272,7 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, const R e[2][3],
         const float2 u2 = __fmul2_rn(u, u), u3 = __fmul2_rn(u2, u);
         const float2 zi = make_float2(K.Zinf, K.Zinf);
         float2 vc, g1, g2n;        // g2n = -g2
-        if (K.screened) {
+        if (screened) {
             const float2 sr = __fmul2_rn(s2, u);
             const float2 e = make_float2(__expf(-K.alpha * sr.x), __expf(-K.alpha * sr.y));
             const float2 de = __fmul2_rn(make_float2(K.dZ, K.dZ), e);
@@ -308,7 +316,7 @@ __device__ __forceinline__ void potential(const PotConst<R>& K, const R e[2][3],
             const R s2 = dx * dx + dy * dy + dz * dz + K.a2;
             R u = rsqrt_t<R>(s2);
             const R u2 = u * u, u3 = u2 * u;
-            if (K.screened) {
+            if (screened) {
                 const R e = exp_t<R>(-K.alpha * (s2 * u));
                 const R de = K.dZ * e;
                 vc[c] = (K.Zinf + de) * u;

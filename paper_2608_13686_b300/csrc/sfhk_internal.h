@@ -14,6 +14,13 @@
 
 namespace sfhk {
 
+// The form of the two-centre potential an integrator is compiled for:
+// kPotAny decides the kind (molecular or the harmonic test potential) and
+// the screening per instance at run time; kPotMolecule is the molecular
+// potential with the screening decided per instance; kPotBare and
+// kPotScreened fix the screening for the whole launch as well.
+constexpr int kPotAny = 0, kPotBare = 1, kPotScreened = 2, kPotMolecule = 3;
+
 constexpr int kWarp = 32;
 constexpr int kFinalFields = 47;   // see sfhk_final_state
 constexpr int kSoaFields = 12;     // see sfhk_load_ensemble
@@ -191,21 +198,30 @@ struct FixedParams {
     static constexpr double dt = 0.05, gamma = 0.5, cutoff = 1e4, stab = 1e3, taper = 2.0;
 };
 bool fixed_params(const DevInstance& I);     // host: I has exactly FixedParams' values
-// whether a launch runs the FixedParams instantiation: every instance has
-// the values (all_fixed), mixed precision, diatomic or three-centre targets
-inline bool runs_fixed(int precision, int poly_slots, int poly_nc, bool all_fixed)
+// the FixedParams instantiation a launch runs, as the form of its potential
+// (kPotAny: the generic integrator): every instance has the values, mixed
+// precision, diatomic targets (their screening: all bare, all screened, or
+// decided per instance) or three-centre ones (any form other than kPotAny)
+inline int fixed_form(const DevInstance* inst, int n, int precision, int poly_slots, int poly_nc)
 {
-    return all_fixed && precision == SFHK_MIXED && (poly_slots == 0 || poly_nc == 3);
+    if (precision != SFHK_MIXED || n < 1 || (poly_slots > 0 && poly_nc != 3)) return kPotAny;
+    int n_screened = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!fixed_params(inst[i])) return kPotAny;
+        n_screened += inst[i].tgt.screened != 0;
+    }
+    if (poly_slots > 0) return kPotMolecule;
+    return n_screened == 0 ? kPotBare : n_screened == n ? kPotScreened : kPotMolecule;
 }
 // poly_slots > 0: polyatomic instances, launched on the polyatomic kernel
 // with that many table rows per lane (the largest n_slots of the instances);
-// fixed: the launch runs the FixedParams instantiation (runs_fixed)
+// fixed: the FixedParams instantiation the launch runs (fixed_form)
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,
-                     int poly_slots = 0, int poly_nc = 0, bool fixed = false);
+                     int poly_slots = 0, int poly_nc = 0, int fixed = kPotAny);
 int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm,
-                        bool fixed = false);
+                        int fixed = kPotAny);
 int propagate_variant_maxreg(int variant_index);   // 0 = no cap
 // Server slices stop within one 32-step chunk of their deadline: a warp
 // whose time is up at a chunk boundary, with chunks left, parks its item (the

@@ -274,7 +274,7 @@ __device__ __forceinline__ void rk4sum3<float>(float a, const float u[3], const 
 template <typename R, bool MIXED, bool POLY, int NC>
 constexpr bool kPoly3 = POLY && MIXED && NC == 3 && std::is_same<R, float>::value;
 
-template <typename R, bool MIXED, bool POLY, bool OFS, int NC = 0>
+template <typename R, bool MIXED, bool POLY, bool OFS, int NC = 0, int PK = kPotAny>
 __device__ __forceinline__ void field_at(const PotConst<R>& K, const R e[2][3], const DevTarget* T,
                                          const R* tab, const Poly3Base& B3, const R q[3],
                                          const R ql[3], R ox, R oy, R oz, R& V, R F[3],
@@ -286,13 +286,13 @@ __device__ __forceinline__ void field_at(const PotConst<R>& K, const R e[2][3], 
         potential_poly<R, MIXED, OFS, NC>(*T, tab, K.a2, q, ql, ox, oy, oz, V, F[0], F[1], F[2],
                                           H);
     else
-        potential<R, OFS>(K, e, ox, oy, oz, V, F[0], F[1], F[2], H);
+        potential<R, OFS, PK>(K, e, ox, oy, oz, V, F[0], F[1], F[2], H);
 }
 
 // One RK4 step's stage evaluations from (q, p) (high part q, low part ql):
 // the four stage Hessians and the increments dq, dp, dS of the step.  Stage
 // points are formed as base + offset (see potential()).
-template <typename R, bool MIXED, bool POLY = false, int NC = 0>
+template <typename R, bool MIXED, bool POLY = false, int NC = 0, int PK = kPotAny>
 __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], const R ql[3],
                                            const R p[3], R E1, R E2, R E4, R h, R h2, R h6,
                                            Sym3<R> H[4], R dq[3], R dp[3], R& dS,
@@ -303,27 +303,27 @@ __device__ __forceinline__ void stage_eval(const PotConst<R>& K, const R q[3], c
     if constexpr (!POLY) centre_diffs<R, MIXED>(K, q, ql, e);
     if constexpr (kPoly3<R, MIXED, POLY, NC>) poly3_base(tab, q, ql, B3);
     const R z0 = R(0);
-    field_at<R, MIXED, POLY, false, NC>(K, e, T, tab, B3, q, ql, z0, z0, z0, V, F, H[0]);
+    field_at<R, MIXED, POLY, false, NC, PK>(K, e, T, tab, B3, q, ql, z0, z0, z0, V, F, H[0]);
     const R k1p[3] = {F[0], F[1], F[2] - E1};
     const R k1s = R(0.5) * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - V - q[2] * E1;
     R o[3], p2[3];
     scale3(h2, p, o);
     axpy3(h2, k1p, p, p2);
-    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[1]);
+    field_at<R, MIXED, POLY, true, NC, PK>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[1]);
     const R k2p[3] = {F[0], F[1], F[2] - E2};
     const R k2s =
         R(0.5) * (p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]) - V - (q[2] + o[2]) * E2;
     R p3[3];
     scale3(h2, p2, o);
     axpy3(h2, k2p, p, p3);
-    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[2]);
+    field_at<R, MIXED, POLY, true, NC, PK>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[2]);
     const R k3p[3] = {F[0], F[1], F[2] - E2};
     const R k3s =
         R(0.5) * (p3[0] * p3[0] + p3[1] * p3[1] + p3[2] * p3[2]) - V - (q[2] + o[2]) * E2;
     R p4[3];
     scale3(h, p3, o);
     axpy3(h, k3p, p, p4);
-    field_at<R, MIXED, POLY, true, NC>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[3]);
+    field_at<R, MIXED, POLY, true, NC, PK>(K, e, T, tab, B3, q, ql, o[0], o[1], o[2], V, F, H[3]);
     const R k4s =
         R(0.5) * (p4[0] * p4[0] + p4[1] * p4[1] + p4[2] * p4[2]) - V - (q[2] + o[2]) * E4;
     dS = h6 * (k1s + R(2) * (k2s + k3s) + k4s);
@@ -777,7 +777,8 @@ constexpr int kRedElems = kWarp * kRedStride;
 // `resume` of pk->in_*; with a deadline, the item is parked at the first
 // chunk boundary past it that has chunks left.  Returns whether the item
 // ran to its end (false: parked).
-template <bool MIXED, bool POLY = false, int NC = 0, bool FIXED = false, bool PARK = false>
+template <bool MIXED, bool POLY = false, int NC = 0, bool FIXED = false, bool PARK = false,
+          int PK = kPotAny>
 __device__ __forceinline__ bool process_item(const DevInstance& I, const WorkItem& W, int lane,
                                              typename std::conditional<MIXED, float, double>::type* red,
                                              typename std::conditional<MIXED, float, double>::type* tab = nullptr,
@@ -1022,7 +1023,7 @@ __device__ __forceinline__ bool process_item(const DevInstance& I, const WorkIte
             // ---- one RK4 step to t_{nn+1}
             if (live && status == 0 && nn < nt - 1) {
                 ++steps;
-                stage_eval<R, MIXED, POLY, NC>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS,
+                stage_eval<R, MIXED, POLY, NC, PK>(K, q, ql, p, E1, E2, E4, h, h2, h6, Hs, dq, dp, dS,
                                            &I.tgt, tab);
                 if constexpr (MIXED) {
                     acc2x2(q[0], q[1], ql[0], ql[1], dq[0], dq[1]);
@@ -1159,7 +1160,7 @@ __device__ __forceinline__ bool process_item(const DevInstance& I, const WorkIte
 // reduction buffers, every warp has a table of `slots` rows x kTabWords x 32
 // words (this lane's column starts kTabWords words per lane in for FP32
 // float4 rows, one word for the FP64 rows).
-template <bool MIXED, bool POLY = false, int NC = 0, bool FIXED = false>
+template <bool MIXED, bool POLY = false, int NC = 0, bool FIXED = false, int PK = kPotAny>
 __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ items, int n_items,
                                           unsigned int* __restrict__ counter, int slots = 0)
@@ -1179,7 +1180,7 @@ __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const WorkItem W = items[it];
-        process_item<MIXED, POLY, NC, FIXED>(insts[W.inst], W, lane, red, tab);
+        process_item<MIXED, POLY, NC, FIXED, false, PK>(insts[W.inst], W, lane, red, tab);
     }
 }
 
@@ -1194,7 +1195,7 @@ __device__ __forceinline__ void run_queue(const DevInstance* __restrict__ insts,
 // (each then runs at least one chunk), then new items are taken until the
 // deadline; an item is parked at the first chunk boundary past the deadline
 // (process_item) and only an item that ran to its end counts as done.
-template <bool MIXED, bool POLY = false, bool FIXED = false>
+template <bool MIXED, bool POLY = false, bool FIXED = false, int PK = kPotAny>
 __device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
                                           const WorkItem* __restrict__ ring, unsigned int mask,
                                           unsigned int base, int n_items,
@@ -1236,7 +1237,7 @@ __device__ __forceinline__ void run_slice(const DevInstance* __restrict__ insts,
         const DevInstance& I = insts[W.inst];
         bool done = true;
         if (I.cancel == nullptr || *I.cancel == 0)
-            done = process_item<MIXED, POLY, 0, FIXED, true>(I, W, lane, red, tab, pk, r,
+            done = process_item<MIXED, POLY, 0, FIXED, true, PK>(I, W, lane, red, tab, pk, r,
                                                              slice_ns ? deadline : 0ull);
         if (done && lane == 0 && I.done_items != nullptr) atomicAdd(I.done_items, 1u);
     }
@@ -1259,20 +1260,23 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
     run_queue<MIXED>(insts, items, n_items, counter);
 }
 // The mixed-precision diatomic integrator with FixedParams' values compiled
-// in, with the same register-cap variants
+// in, for the molecular two-centre potential (PK: the screening known for
+// the whole launch, kPotBare or kPotScreened, or decided per instance,
+// kPotMolecule), with the same register-cap variants
+template <int PK>
 __global__ void __launch_bounds__(128)
     k_propagate_fixed_nocap(const DevInstance* __restrict__ insts,
                             const WorkItem* __restrict__ items, int n_items,
                             unsigned int* __restrict__ counter)
 {
-    run_queue<true, false, 0, true>(insts, items, n_items, counter);
+    run_queue<true, false, 0, true, PK>(insts, items, n_items, counter);
 }
-template <int MAXREG>
+template <int MAXREG, int PK>
 __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
     k_propagate_fixed(const DevInstance* __restrict__ insts, const WorkItem* __restrict__ items,
                       int n_items, unsigned int* __restrict__ counter)
 {
-    run_queue<true, false, 0, true>(insts, items, n_items, counter);
+    run_queue<true, false, 0, true, PK>(insts, items, n_items, counter);
 }
 // the three-centre polyatomic integrator with FixedParams' values compiled in
 __global__ void __launch_bounds__(128)
@@ -1337,7 +1341,8 @@ __global__ void __launch_bounds__(128)
                                   unsigned long long* __restrict__ t0,
                                   __grid_constant__ const ParkBufs pk)
 {
-    run_slice<true, false, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, &pk);
+    run_slice<true, false, true, kPotMolecule>(insts, ring, mask, base, n_items, counter, slice_ns,
+                                              t0, &pk);
 }
 template <int MAXREG>
 __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
@@ -1347,7 +1352,8 @@ __global__ void __launch_bounds__(128) __maxnreg__(MAXREG)
                             unsigned long long slice_ns, unsigned long long* __restrict__ t0,
                             __grid_constant__ const ParkBufs pk)
 {
-    run_slice<true, false, true>(insts, ring, mask, base, n_items, counter, slice_ns, t0, &pk);
+    run_slice<true, false, true, kPotMolecule>(insts, ring, mask, base, n_items, counter, slice_ns,
+                                              t0, &pk);
 }
 
 template <bool MIXED>
@@ -1384,12 +1390,21 @@ using SlicePolyFn = void (*)(const DevInstance*, const WorkItem*, unsigned int, 
 // registers per thread (12 to 16 resident warps per SM)
 constexpr int kVariantMaxReg[kPropVariants] = {0, 168, 152, 144, 136, 128};
 
-KernelFn fixed_variant(int v)
+template <int PK>
+KernelFn fixed_variant_pk(int v)
 {
     static const KernelFn fn[kPropVariants] = {
-        k_propagate_fixed_nocap, k_propagate_fixed<168>, k_propagate_fixed<152>,
-        k_propagate_fixed<144>, k_propagate_fixed<136>, k_propagate_fixed<128>};
+        k_propagate_fixed_nocap<PK>, k_propagate_fixed<168, PK>, k_propagate_fixed<152, PK>,
+        k_propagate_fixed<144, PK>, k_propagate_fixed<136, PK>, k_propagate_fixed<128, PK>};
     return fn[v];
+}
+
+// pk: the launch's potential form (kPotBare, kPotScreened or kPotMolecule)
+KernelFn fixed_variant(int v, int pk)
+{
+    return pk == kPotBare       ? fixed_variant_pk<kPotBare>(v)
+           : pk == kPotScreened ? fixed_variant_pk<kPotScreened>(v)
+                                : fixed_variant_pk<kPotMolecule>(v);
 }
 
 KernelFn variant(int precision, int v)
@@ -1550,15 +1565,17 @@ int slice_max_warps(int precision, int variant_index, int block_threads, int sm_
 
 int propagate_variant_maxreg(int v) { return (v >= 0 && v < kPropVariants) ? kVariantMaxReg[v] : 0; }
 
-// the kernel of a diatomic launch: the FixedParams instantiation when every
-// instance has those values (mixed precision only)
-static KernelFn diatomic_kernel(int precision, int v, bool fixed)
+// the kernel of a diatomic launch: the FixedParams instantiation of the
+// launch's potential form when every instance has those values (fixed, a
+// kPot* form; mixed precision only), else the generic one
+static KernelFn diatomic_kernel(int precision, int v, int fixed)
 {
-    return fixed && precision == SFHK_MIXED ? fixed_variant(v) : variant(precision, v);
+    return fixed != kPotAny && precision == SFHK_MIXED ? fixed_variant(v, fixed)
+                                                      : variant(precision, v);
 }
 
 int propagate_occupancy(int precision, int variant_index, int block_threads, int* blocks_per_sm,
-                        bool fixed)
+                        int fixed)
 {
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
@@ -1571,7 +1588,7 @@ int propagate_occupancy(int precision, int variant_index, int block_threads, int
 bool fixed_params(const DevInstance& I)
 {
     using F = FixedParams;
-    return I.dt == F::dt && I.gamma == F::gamma &&
+    return I.tgt.kind != SFHK_POT_HARMONIC && I.dt == F::dt && I.gamma == F::gamma &&
            I.inv_gamma == 1.0 / F::gamma && I.cutoff2 == F::cutoff * F::cutoff &&
            I.stab_cut == F::stab && I.stab_hi == F::taper * F::stab;
 }
@@ -1637,14 +1654,14 @@ int configure_kernels()
 int launch_propagate(int precision, int variant_index, const DevInstance* insts,
                      const WorkItem* items, int n_items, unsigned int* item_counter,
                      int block_threads, int blocks_per_sm, int sm_count, cudaStream_t s,
-                     int poly_slots, int poly_nc, bool fixed)
+                     int poly_slots, int poly_nc, int fixed)
 {
     if (block_threads <= 0 || block_threads > 128 || block_threads % kWarp) return SFHK_E_INVAL;
     if (variant_index < 0 || variant_index >= kPropVariants) return SFHK_E_INVAL;
     if (poly_slots > 0)
         return launch_poly(precision, variant_index, insts, items, n_items, item_counter,
-                           block_threads, blocks_per_sm, sm_count, poly_slots, poly_nc, fixed,
-                           s);
+                           block_threads, blocks_per_sm, sm_count, poly_slots, poly_nc,
+                           fixed != kPotAny, s);
     int occ = 0;
     int rc = propagate_occupancy(precision, variant_index, block_threads, &occ, fixed);
     if (rc) return rc;

@@ -452,3 +452,38 @@ def test_fixed_parameter_three_centre_integrator(S, ctx):
     assert _rel(v_fixed, vz_o) <= 1e-4
     S.sfhk_destroy_ensemble(e)
     S.sfhk_destroy_ensemble(e2)
+
+
+def test_fixed_parameter_integrator_potential_forms(S, ctx):
+    """The fixed-parameter integrator comes in three forms of the two-centre
+    potential, chosen from the launch's instances: unscreened (H2 alone),
+    screened (N2 alone) and the screening decided per instance (H2 and N2 in
+    one batch).  Each gives the generic integrator's dipoles on the same
+    ensembles (the generic one forced by an extra ensemble on another time
+    step) to 1e-7, and the N2 dipole agrees with the oracle."""
+    p, p2 = W.PULSE_800, dict(W.PULSE_800, dt=0.04)
+    th2, tn2 = S.sfhk_create_target(ctx, W.TARGETS["H2"]), S.sfhk_create_target(ctx, W.TARGETS["N2"])
+    ph, ph2 = S.sfhk_set_pulse(ctx, p), S.sfhk_set_pulse(ctx, p2)
+    nt = S.sfhk_pulse_grid(ph)["nt"]
+    eh = S.sfhk_sample_initial(ctx, th2, ph, W.fixed(20.0), 2000, 9, 0)
+    en = S.sfhk_sample_initial(ctx, tn2, ph, W.COS2, 2000, 10, 0)
+    ex = S.sfhk_sample_initial(ctx, th2, ph2, W.fixed(20.0), 200, 11, 0)
+    tapered = S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB, stab_taper=TAPER)
+
+    def dipoles(batch, keep):
+        S.sfhk_propagate_batch(ctx, batch, tapered)
+        return [S.sfhk_dipole(ctx, e, nt) for e in keep], S.sfhk_stats_get(keep[0])["fixed_params"]
+
+    for batch in ([eh], [en], [eh, en]):
+        v_fixed, f1 = dipoles(batch, batch)
+        v_gen, f0 = dipoles(batch + [ex], batch)
+        assert f1 == 1 and f0 == 0
+        for a, b in zip(v_fixed, v_gen):
+            assert _rel(a, b) <= 1e-7
+    soa, _, _ = O.sample(W.TARGETS["N2"], p, W.COS2, seed=10, n=2000)
+    vz_o, _, _ = O.propagate(W.TARGETS["N2"], p, soa, GAMMA, cutoff=CUT, stab_cutoff=STAB,
+                             stab_taper=TAPER)
+    S.sfhk_propagate(ctx, en, tapered)
+    assert _rel(S.sfhk_dipole(ctx, en, nt), vz_o) <= 1e-4
+    for e in (eh, en, ex):
+        S.sfhk_destroy_ensemble(e)
