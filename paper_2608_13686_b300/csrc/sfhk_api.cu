@@ -323,11 +323,14 @@ int prepare_outputs(sfhk_ensemble* e, const sfhk_run_opts& o, cudaStream_t s)
 
 namespace {
 
-void shape(Ctx* c, const sfhk_run_opts& o, int* bt, int* var, int* bps)
+// the launch shape: the run options' where set, else the context's tuned
+// shape for the precision and the launch's integrator form (fixed_form)
+void shape(Ctx* c, const sfhk_run_opts& o, int form, int* bt, int* var, int* bps)
 {
-    *bt = o.block_threads > 0 ? o.block_threads : c->tuned[o.precision][0];
-    *var = o.kernel_variant > 0 ? o.kernel_variant - 1 : c->tuned[o.precision][1];
-    *bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : c->tuned[o.precision][2];
+    const int* t = c->tuned[o.precision][form];
+    *bt = o.block_threads > 0 ? o.block_threads : t[0];
+    *var = o.kernel_variant > 0 ? o.kernel_variant - 1 : t[1];
+    *bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : t[2];
 }
 
 }  // namespace
@@ -702,11 +705,11 @@ int sfhk_propagate(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, void* 
     if ((rc = prepare_outputs(e, *o, s))) return rc;
     const DevInstance I = make_instance(e, *o);
     SFHK_CUDA_TRY(cudaMemcpyAsync(e->inst.p, &I, sizeof I, cudaMemcpyHostToDevice, s));
-    int bt, var, bps;
-    shape(c, *o, &bt, &var, &bps);
-    SFHK_CUDA_TRY(record_event(e->ev_start, s));
     int slots = 0, nc = 0;
     poly_slots(&e, 1, &slots, &nc);
+    int bt, var, bps;
+    shape(c, *o, fixed_form(&I, 1, o->precision, slots, nc), &bt, &var, &bps);
+    SFHK_CUDA_TRY(record_event(e->ev_start, s));
     rc = launch_propagate(o->precision, var, (const DevInstance*)e->inst.p,
                           (const WorkItem*)e->items.p, e->n_items, (unsigned int*)e->qctr.p, bt,
                           bps, c->sm_count, s, slots, nc,
@@ -787,7 +790,7 @@ int sfhk_propagate_batch(sfhk_ctx* c, sfhk_ensemble* const* ens, int n_ens,
         rc = launch_sort_items(d_items, (int)total_items, d_nt, d_sorted, d_keys, d_perm, d_hist,
                                max_nt, s);
     int bt, var, bps;
-    shape(c, *o, &bt, &var, &bps);
+    shape(c, *o, fixed_form(hI.data(), n_ens, o->precision, slots, nc), &bt, &var, &bps);
     for (int i = 0; i < n_ens && !rc; ++i)
         if (record_event(ens[i]->ev_start, s) != cudaSuccess) rc = SFHK_E_CUDA;
     if (!rc)
@@ -921,7 +924,7 @@ int sfhk_batch_launch(sfhk_batch* b, void* stream)
                            b->d_perm, b->d_hist, b->max_nt, s);
     if (rc) return rc;
     int bt, var, bps;
-    shape(b->ctx, b->opts, &bt, &var, &bps);
+    shape(b->ctx, b->opts, b->fixed, &bt, &var, &bps);
     // the kernel is timed with the ensembles' events (also inside a captured graph)
     for (sfhk_ensemble* e : b->ens) SFHK_CUDA_TRY(record_event(e->ev_start, s));
     rc = launch_propagate(b->opts.precision, var, b->d_inst, b->d_sorted, (int)b->total_items,
@@ -998,9 +1001,11 @@ int sfhk_autotune(sfhk_ctx* c, sfhk_ensemble* e, const sfhk_run_opts* o, int max
     std::sort(shapes.begin(), shapes.begin() + top,
               [](const Shape& x, const Shape& y) { return x.ms < y.ms; });
     const int bb = shapes[0].b, bv = shapes[0].v;
-    c->tuned[o->precision][0] = bb;
-    c->tuned[o->precision][1] = bv;
-    c->tuned[o->precision][2] = 0;
+    // the shape of the form the ensemble's launches run
+    int* t = c->tuned[o->precision][fixed_form(&I, 1, o->precision, slots, nc)];
+    t[0] = bb;
+    t[1] = bv;
+    t[2] = 0;
     e->have_result = false;
     if (choice) {
         choice[0] = bb;

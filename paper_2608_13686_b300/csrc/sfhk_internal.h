@@ -114,12 +114,15 @@ struct Ctx {
     size_t budget = 0;
     std::atomic<size_t> used{0};
     std::mutex mu;
-    // tuned launch shape per precision: [block_threads, variant, blocks_per_sm]
-    // (variant: index into 0 = no cap, 168, 152, ... registers; blocks per SM
-    // 0 = as many as fit).  Before tuning: 128 threads, FP64 at the 152-
-    // register cap, mixed precision at 168 (the fixed-parameter kernels spill
-    // 20 B there against 104 B at 152)
-    int tuned[2][3] = {{128, 2, 0}, {128, 1, 0}};
+    // tuned launch shape per precision and form of the launch's integrator
+    // (kPotAny: the generic one; else the fixed-parameter one of that
+    // potential form, whose register needs differ): [block_threads, variant,
+    // blocks_per_sm] (variant: index into 0 = no cap, 168, 152, ... registers;
+    // blocks per SM 0 = as many as fit).  Before tuning: 128 threads, FP64 at
+    // the 152-register cap, mixed precision at 168 (the fixed-parameter kernels
+    // spill at most 20 B there, up to 112 B at 152)
+    int tuned[2][4][3] = {{{128, 2, 0}, {128, 2, 0}, {128, 2, 0}, {128, 2, 0}},
+                          {{128, 1, 0}, {128, 1, 0}, {128, 1, 0}, {128, 1, 0}}};
     int alloc(DeviceBuf& b, size_t bytes);
     void release(DeviceBuf& b);
 };

@@ -168,7 +168,8 @@ int alloc_park(sfhk_server* S)
 {
     const int prec = S->ro.precision;
     sfhk::Ctx* c = S->ctx;
-    S->park_cap = sfhk::slice_max_warps(prec, c->tuned[prec][1], c->tuned[prec][0], c->sm_count);
+    const int* t = c->tuned[prec][sfhk::kPotAny];    // the server's slices use this shape
+    S->park_cap = sfhk::slice_max_warps(prec, t[1], t[0], c->sm_count);
     if (S->park_cap <= 0) return SFHK_E_CUDA;
     const size_t elem = prec == SFHK_MIXED ? sizeof(float) : sizeof(double);
     for (auto& G : S->rings)
@@ -402,8 +403,8 @@ void run_slice(sfhk_server* S)
     }
     if (n64[0] == 0 && n64[1] == 0 && parked[0] == 0 && parked[1] == 0) return;
     if ((n64[1] > 0 || parked[1] > 0) && slots < 1) slots = 1;
-    int bt = S->ctx->tuned[S->ro.precision][0];
-    int var = S->ctx->tuned[S->ro.precision][1];
+    int bt = S->ctx->tuned[S->ro.precision][sfhk::kPotAny][0];
+    int var = S->ctx->tuned[S->ro.precision][sfhk::kPotAny][1];
     const auto t_a = Clock::now();
     int rc = SFHK_OK;
     int n[2] = {0, 0};
