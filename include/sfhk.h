@@ -264,9 +264,11 @@ typedef struct {
                               /* with the method's dt = 0.05, gamma = 0.5 and */
                               /* the filters |C| <= 1e4, stability taper      */
                               /* 1e3..2e3 as constants (mixed precision,      */
-                              /* diatomic or three-centre targets; chosen     */
-                              /* when every instance of the launch has        */
-                              /* exactly these values)                        */
+                              /* molecular diatomic or three-centre targets,  */
+                              /* the diatomic potential's screening compiled  */
+                              /* in too when all instances agree; chosen when */
+                              /* every instance of the launch has exactly     */
+                              /* these values)                                */
 } sfhk_stats;
 
 /* ---------------------------------------------------------------- context */
