@@ -268,7 +268,8 @@ typedef struct {
                               /* the diatomic potential's screening compiled  */
                               /* in too when all instances agree; chosen when */
                               /* every instance of the launch has exactly     */
-                              /* these values)                                */
+                              /* these values and no first returns are        */
+                              /* recorded)                                    */
 } sfhk_stats;
 
 /* ---------------------------------------------------------------- context */

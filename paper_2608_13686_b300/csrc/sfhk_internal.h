@@ -200,7 +200,9 @@ int configure_kernels();
 struct FixedParams {
     static constexpr double dt = 0.05, gamma = 0.5, cutoff = 1e4, stab = 1e3, taper = 2.0;
 };
-bool fixed_params(const DevInstance& I);     // host: I has exactly FixedParams' values
+// host: I has exactly FixedParams' values, a molecular target and no
+// first-return record (the fixed-parameter integrators keep no such record)
+bool fixed_params(const DevInstance& I);
 // the FixedParams instantiation a launch runs, as the form of its potential
 // (kPotAny: the generic integrator): every instance has the values, mixed
 // precision, diatomic targets (their screening: all bare, all screened, or

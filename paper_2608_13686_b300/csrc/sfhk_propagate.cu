@@ -869,7 +869,9 @@ __device__ __forceinline__ bool process_item(const DevInstance& I, const WorkIte
     }
     Mono<R> M;
     M.identity(gam);
-    double* const ret = I.returns;  // first returns (optional)
+    // first returns (optional; the fixed-parameter integrators do not record
+    // them, fixed_params sends such launches to the generic one)
+    double* const ret = FIXED ? nullptr : I.returns;
     const R r_out = R(I.ret_out), r_in = R(I.ret_in);
     bool left = false;
     int n_ret = -1;
@@ -1588,7 +1590,8 @@ int propagate_occupancy(int precision, int variant_index, int block_threads, int
 bool fixed_params(const DevInstance& I)
 {
     using F = FixedParams;
-    return I.tgt.kind != SFHK_POT_HARMONIC && I.dt == F::dt && I.gamma == F::gamma &&
+    return I.tgt.kind != SFHK_POT_HARMONIC && I.returns == nullptr && I.dt == F::dt &&
+           I.gamma == F::gamma &&
            I.inv_gamma == 1.0 / F::gamma && I.cutoff2 == F::cutoff * F::cutoff &&
            I.stab_cut == F::stab && I.stab_hi == F::taper * F::stab;
 }

@@ -418,6 +418,10 @@ def test_fixed_parameter_integrator(S, ctx):
     assert S.sfhk_stats_get(e)["fixed_params"] == 1
     S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB))
     assert S.sfhk_stats_get(e)["fixed_params"] == 0
+    # a launch that records first returns runs the generic integrator
+    S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_MIXED, GAMMA, CUT, stab_cutoff=STAB,
+                                        stab_taper=TAPER, returns=(5.0, 2.0)))
+    assert S.sfhk_stats_get(e)["fixed_params"] == 0
     S.sfhk_propagate(ctx, e, S.run_opts(S.SFHK_FP64, GAMMA, CUT, stab_cutoff=STAB,
                                         stab_taper=TAPER))
     assert S.sfhk_stats_get(e)["fixed_params"] == 0
