@@ -120,10 +120,10 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 # the current kernel, scaled by the trajectories to the full size (the
 # traffic is the initial-point SoA read once, about 100 B per trajectory):
 # H2 0/45/90 deg captured at 3 x 5e4 trajectories with the fixed-parameter
-# integrator of the unscreened two-centre potential in 32-thread blocks,
-# uncapped (variant 1: 14.87 MB read, 0 written) and at 168 registers
-# (variant 2: 15.19 MB), the autotuner's two choices, scaled to 3 x 1e6;
-# H2O 1b1 isotropic (three-centre fixed-parameter kernel) captured at 1e5
-# trajectories with the 168-register variant (2) in 64-thread blocks (9.83 MB
-# read), scaled to 1e6.
-TRAFFIC = {("h2-angles", 1): 297.5e6, ("h2-angles", 2): 303.8e6, ("h2o-iso", 2): 98.3e6}
+# integrator of the unscreened two-centre potential (no first-return record)
+# in 32-thread blocks, uncapped (variant 1: 14.86 MB read, 0 written) and at
+# 168 registers (variant 2: 14.85 MB), the autotuner's two choices, scaled to
+# 3 x 1e6; H2O 1b1 isotropic (three-centre fixed-parameter kernel) captured
+# at 1e5 trajectories with the 168-register variant (2) in 64-thread blocks
+# (9.90 MB read), scaled to 1e6.
+TRAFFIC = {("h2-angles", 1): 297.1e6, ("h2-angles", 2): 297.1e6, ("h2o-iso", 2): 99.0e6}
