@@ -193,7 +193,7 @@ int ensemble_alloc(sfhk_ensemble* e, long long n, int nt)
     if ((rc = c->alloc(e->phf, sizeof(float2) * nt))) return rc;
     if ((rc = c->alloc(e->vz, sizeof(double) * nt))) return rc;
     if ((rc = c->alloc(e->counters, sizeof(unsigned long long) * 8))) return rc;
-    if ((rc = c->alloc(e->cdf, sizeof(double) * nt))) return rc;
+    if ((rc = c->alloc(e->cdf, sizeof(double) * cdf_doubles(nt)))) return rc;
     if ((rc = c->alloc(e->hist, sizeof(int) * nt))) return rc;
     if ((rc = c->alloc(e->inst, sizeof(DevInstance)))) return rc;
     if ((rc = c->alloc(e->qctr, sizeof(unsigned int) * 4))) return rc;

@@ -169,6 +169,15 @@ inline void count_launch(int k = 1) { g_launches.fetch_add((unsigned long long)k
 int launch_field_table(const Pulse& P, double* Eh, float* Ehf, cudaStream_t s);
 int launch_phase_table(const Pulse& P, double Ip, double2* ph, float2* phf, cudaStream_t s);
 int launch_adk_cdf(const Pulse& P, double Ip, double* cdf, cudaStream_t s);
+// The same launch writes, after the nt CDF values, the part of a proposal
+// draw that depends only on its birth step m (Sec. II.B): row m, at
+// cdf + birth_tab_offset(nt) + kBirthTab * m, holds E(t_m), the transverse
+// width sigma_m = sqrt(|E|/(2 sqrt(2 Ip))), 1/(2 sigma_m^2), the birth-time
+// density W_m / (pi dt sum_n W_n), and sin, cos of k_q t_m + cep for the
+// pulse's three terms.  Rows start on a 16-byte boundary.
+constexpr int kBirthTab = 10;
+__host__ __device__ inline size_t birth_tab_offset(int nt) { return (size_t)((nt + 1) & ~1); }
+inline size_t cdf_doubles(int nt) { return birth_tab_offset(nt) + (size_t)kBirthTab * nt; }
 // alignment descriptor within its documented ranges
 bool align_valid(const sfhk_align_desc& al);
 // pilot: sample_pilot_doubles() doubles of scratch, used when the target

@@ -59,22 +59,38 @@ __global__ void k_phase_table(double Ip, double t_origin, double dt, int nt, dou
 }
 
 // ADK weights and their inclusive prefix sum, one block of 1024 threads:
-// contiguous chunks, chunk totals scanned in shared memory.
+// contiguous chunks, chunk totals scanned in shared memory.  The same pass
+// fills the per-birth-step table after the CDF (row layout at kBirthTab):
+// the field, the transverse width, the pulse terms' phases, and W_m, scaled
+// by 1 / (pi dt total) once the total is known.
 __global__ void __launch_bounds__(1024) k_adk_cdf(double omega, double E0, double Tp, double cep,
                                                   double t_origin, double dt, int nt, double Ip,
                                                   double* cdf)
 {
     __shared__ double part[1024];
+    __shared__ double s_total;
     const int tid = threadIdx.x;
     const int chunk = (nt + 1023) / 1024;
     const int b = tid * chunk, e = min(nt, b + chunk);
     const double cst = 2.0 * pow(2.0 * Ip, 1.5) / 3.0;
+    const double sqrt2Ip = sqrt(2.0 * Ip);
+    const PulseTerms PT = pulse_terms(omega, E0, Tp, cep);
+    double* tab = cdf + birth_tab_offset(nt);
     double acc = 0.0;
     for (int n = b; n < e; ++n) {
-        const double f = fabs(field_direct(omega, E0, Tp, cep, t_origin + n * dt));
+        const double t = t_origin + n * dt;
+        const double E = field_direct(omega, E0, Tp, cep, t);
+        const double f = fabs(E);
         const double w = f > 0.0 ? exp(-cst / f) : 0.0;
         acc += w;
         cdf[n] = acc;
+        double* row = tab + (size_t)kBirthTab * n;
+        row[0] = E;
+        row[1] = sqrt(f / (2.0 * sqrt2Ip));
+        row[2] = f > 0.0 ? sqrt2Ip / f : 0.0;
+        row[3] = w;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sincos(PT.k[q] * t + PT.cep, &row[4 + 2 * q], &row[5 + 2 * q]);
     }
     part[tid] = acc;
     __syncthreads();
@@ -85,10 +101,15 @@ __global__ void __launch_bounds__(1024) k_adk_cdf(double omega, double E0, doubl
             part[i] = run;
             run += v;
         }
+        s_total = run;
     }
     __syncthreads();
     const double off = part[tid];
-    for (int n = b; n < e; ++n) cdf[n] += off;
+    const double sc = s_total > 0.0 ? 1.0 / (kPi * dt * s_total) : 0.0;
+    for (int n = b; n < e; ++n) {
+        cdf[n] += off;
+        tab[(size_t)kBirthTab * n + 3] *= sc;
+    }
 }
 
 struct SampleParams {
@@ -109,10 +130,14 @@ struct SampleParams {
     int sampling;                             // SFHK_SAMPLE_PROPOSAL / SFHK_SAMPLE_ABS_AMPLITUDE
     double norm;
     double pexp[SFHK_MAX_PRIM], pcoef[SFHK_MAX_PRIM];
-    // per-draw constants formed once on the host: coef_p (pi/a_p)^{3/2},
-    // N (2 pi)^{-3/2}, the ADK exponent's 2 (2 Ip)^{3/2} / 3, sqrt(2 Ip)
+    // per-draw constants formed once on the host: coef_p (pi/a_p)^{3/2} and
+    // N (2 pi)^{-3/2}
     double pfac[SFHK_MAX_PRIM];
-    double mz_scale, adk_c, sqrt2Ip;
+    double mz_scale;
+    // 1/(2 a_p) and 1/(4 a_p) of the primitives' exponents (0 for an unused slot)
+    double i2a[SFHK_MAX_PRIM], i4a[SFHK_MAX_PRIM];
+    // a fixed axis (SFHK_ALIGN_FIXED): sin, cos of theta and phi
+    double fsth, fcth, fsph, fcph;
     // reciprocals of the pulse's frequencies k_q and of k_q -+ k_r (0 where
     // the frequency is 0)
     double ik[3], ikd[3][3], iks[3][3];
@@ -165,8 +190,10 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
     }
     const int m = lo;
     const double t0 = S.t_origin + m * S.dt;
-    const double Et0 = field_direct(S.omega, S.E0, S.Tp, S.P.cep, t0);
-    const double sigma = sqrt(fabs(Et0) / (2.0 * S.sqrt2Ip));
+    // what depends on the birth step alone, from the table after the CDF
+    const double* brow = cdf + birth_tab_offset(S.nt) + (size_t)kBirthTab * m;
+    const double Et0 = brow[0];
+    const double sigma = brow[1];
     const double rr = sqrt(-2.0 * log(u[1]));
     double sb, cb;
     sincos(2.0 * kPi * u[2], &sb, &cb);
@@ -183,9 +210,11 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
         th = acos(S.qx[j % S.n_nodes]);
         phv = 2.0 * kPi * u[4];
     }
-    double sth, cth, sph, cph;
-    sincos(th, &sth, &cth);
-    sincos(phv, &sph, &cph);
+    double sth = S.fsth, cth = S.fcth, sph = S.fsph, cph = S.fcph;
+    if (S.align_kind != SFHK_ALIGN_FIXED) {
+        sincos(th, &sth, &cth);
+        sincos(phv, &sph, &cph);
+    }
     const double nx = sth * cph, ny = sth * sph, nz = cth;
     // polyatomic: the third Euler angle, uniform for the isotropic and cos^2
     // distributions (the Haar measure over all three angles for isotropic)
@@ -209,7 +238,10 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
     double tt = 0.0;
     double cthm[3], sthm[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) sincos(S.P.k[q] * t0 + S.P.cep, &sthm[q], &cthm[q]);
+    for (int q = 0; q < 3; ++q) {
+        sthm[q] = brow[4 + 2 * q];
+        cthm[q] = brow[5 + 2 * q];
+    }
     const double kp2 = kx * kx + ky * ky;
     const double target = 2.0 * S.Ip + kp2;
     if (ok) {
@@ -383,8 +415,8 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                                          Rot[6] * x[0] + Rot[7] * x[1] + Rot[8] * x[2]};
                     const double2 kA = make_double2(kx * A[0] + ky * A[1] + kapz.x * A[2],
                                                     kapz.y * A[2]);
-                    const double a = S.pexp[p];
-                    const double2 ex = make_double2(kA.y - kk.x / (4.0 * a), -kA.x - kk.y / (4.0 * a));
+                    const double i4a = S.i4a[p];
+                    const double2 ex = make_double2(kA.y - kk.x * i4a, -kA.x - kk.y * i4a);
                     const double2 F = cscale(cexp_(ex), S.pfac[p]);
                     double2 f;
                     if (S.pkind[p]) {
@@ -395,11 +427,11 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                         const double2 uk = make_double2(uu[0] * kx + uu[1] * ky + uu[2] * kapz.x,
                                                         uu[2] * kapz.y);
                         const double2 ku = cmul(kapz, uk);
-                        const double i2a = 0.5 / a, i4a2 = i2a * i2a;
+                        const double i2a = S.i2a[p], i4a2 = i2a * i2a;
                         f = make_double2(uu[2] * i2a - ku.x * i4a2 + A[2] * uk.y * i2a,
                                          -ku.y * i4a2 - A[2] * uk.x * i2a);
                     } else {
-                        f = make_double2(A[2] + kapz.y / (2.0 * a), -kapz.x / (2.0 * a));
+                        f = make_double2(A[2] + kapz.y * S.i2a[p], -kapz.x * S.i2a[p]);
                     }
                     mz = cadd(mz, cmul(F, f));
                 }
@@ -412,9 +444,9 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                 // kappa.A (complex)
                 const double2 kA = make_double2(kx * Ax + ky * Ay + kapz.x * Az, kapz.y * Az);
                 for (int p = 0; p < S.n_prim; ++p) {
-                    const double a = S.pexp[p];
+                    const double i4a = S.i4a[p];
                     // -i kappa.A - kappa.kappa / (4a)
-                    const double2 ex = make_double2(kA.y - kk.x / (4.0 * a), -kA.x - kk.y / (4.0 * a));
+                    const double2 ex = make_double2(kA.y - kk.x * i4a, -kA.x - kk.y * i4a);
                     const double2 F = cscale(cexp_(ex), S.pfac[p]);
                     double2 f;
                     if (S.pkind[p]) {
@@ -430,12 +462,12 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
                         const double2 uk = make_double2(u[0] * kx + u[1] * ky + u[2] * kapz.x,
                                                         u[2] * kapz.y);
                         const double2 ku = cmul(kapz, uk);
-                        const double i2a = 0.5 / a, i4a2 = i2a * i2a;
+                        const double i2a = S.i2a[p], i4a2 = i2a * i2a;
                         f = make_double2(s * (u[2] * i2a - ku.x * i4a2 + Az * uk.y * i2a),
                                          s * (-ku.y * i4a2 - Az * uk.x * i2a));
                     } else {
                         // (A_z - i kappa_z / (2a))
-                        f = make_double2(Az + kapz.y / (2.0 * a), -kapz.x / (2.0 * a));
+                        f = make_double2(Az + kapz.y * S.i2a[p], -kapz.x * S.i2a[p]);
                     }
                     mz = cadd(mz, cmul(F, f));
                 }
@@ -459,13 +491,15 @@ __device__ __forceinline__ bool propose(const SampleParams& S, long long j, cons
             const double2 Z = make_double2(Sd.x + kz * qz, Sd.y);     // S_down + k.q0
             const double2 eiz = cexp_(make_double2(-Z.y, Z.x));        // e^{iZ}
             const double2 amp = cmul(cdiv(num, den), eiz);
-            const double Wm = exp(-S.adk_c / fabs(Et0));
-            const double pdf = (Wm / total) / S.dt * exp(-kp2 / (2.0 * sigma * sigma)) /
-                               (2.0 * kPi * sigma * sigma);
+            // proposal density: W_m / (total dt) for the birth step times the
+            // Gaussian of k_perp, e^{-kp2/(2 sigma^2)} / (2 pi sigma^2)
+            const double i2s2 = brow[2];
+            const double pdf = brow[3] * i2s2 * exp(-kp2 * i2s2);
             // the quadrature node's weight K W_k (1 otherwise)
             const double f = side_w *
                              (S.align_kind == SFHK_ALIGN_QUADRATURE ? S.qkw[j % S.n_nodes] : 1.0);
-            w = make_double2(f * amp.x / pdf, f * amp.y / pdf);
+            const double fp = f / pdf;
+            w = make_double2(fp * amp.x, fp * amp.y);
         }
     }
     f[0] = (double)m;
@@ -826,10 +860,14 @@ int launch_sample(const Target& T, const Pulse& P, const sfhk_align_desc& al, lo
         S.pcoef[k] = T.desc.prim_coef[k];
         S.pkind[k] = T.desc.prim_kind[k];
         S.pfac[k] = S.pexp[k] > 0.0 ? S.pcoef[k] * std::pow(kPi / S.pexp[k], 1.5) : 0.0;
+        S.i2a[k] = S.pexp[k] > 0.0 ? 0.5 / S.pexp[k] : 0.0;
+        S.i4a[k] = S.pexp[k] > 0.0 ? 0.25 / S.pexp[k] : 0.0;
     }
+    S.fsth = std::sin(al.theta);
+    S.fcth = std::cos(al.theta);
+    S.fsph = std::sin(al.phi);
+    S.fcph = std::cos(al.phi);
     S.mz_scale = S.norm * std::pow(2.0 * kPi, -1.5);
-    S.adk_c = 2.0 * std::pow(2.0 * S.Ip, 1.5) / 3.0;
-    S.sqrt2Ip = std::sqrt(2.0 * S.Ip);
     S.cchi = std::cos(T.desc.pi_azimuth);
     S.schi = std::sin(T.desc.pi_azimuth);
     S.poly = poly ? 1 : 0;
