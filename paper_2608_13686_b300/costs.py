@@ -125,5 +125,9 @@ def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ) -> float:
 # 168 registers (variant 2: 14.85 MB), the autotuner's two choices, scaled to
 # 3 x 1e6; H2O 1b1 isotropic (three-centre fixed-parameter kernel) captured
 # at 1e5 trajectories with the 168-register variant (2) in 64-thread blocks
-# (9.90 MB read), scaled to 1e6.
-TRAFFIC = {("h2-angles", 1): 297.1e6, ("h2-angles", 2): 297.1e6, ("h2o-iso", 2): 99.0e6}
+# (9.90 MB read), scaled to 1e6; N2 cos^2 (fixed-parameter integrator of the
+# screened two-centre potential) captured at 1e5 trajectories with the
+# 168-register variant (2) in 128-thread blocks, the shape its bench line runs
+# (10.24 MB read, 0 written), scaled to 1e7.
+TRAFFIC = {("h2-angles", 1): 297.1e6, ("h2-angles", 2): 297.1e6, ("h2o-iso", 2): 99.0e6,
+           ("n2-cos2", 2): 1024.1e6}
